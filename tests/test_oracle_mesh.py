@@ -1,0 +1,237 @@
+"""Pins of the oracle's forest and ghost-pattern classification (Sec. 2.2,
+Sec. 2.5) against hand enumeration, closed forms and independent geometry.
+CPU only."""
+import itertools
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def load_table(name):
+    rows = []
+    for line in open(os.path.join(GOLDEN, name)):
+        line = line.split("#")[0].strip()
+        if line:
+            rows.append([int(x) for x in line.split()])
+    return np.array(rows, dtype=np.int32)
+
+
+def spec2(**kw):
+    base = dict(ndim=2, N=4, ng=1, ntrees=(2, 1, 1), periodic=(0, 0, 1), max_level=2)
+    base.update(kw)
+    return synth.MeshSpec(**base)
+
+
+def test_hand_enumerated_pattern_2d():
+    """Golden: a 2x1 brick with tree 0 refined once (derivation in the file)."""
+    m = oracle.Mesh(spec2(), 0)
+    m2 = m.adapt(np.array([1, 0], dtype=np.int8))
+    lev, g = m2.blocks()
+    assert lev.tolist() == [1, 1, 1, 1, 0]
+    assert g[:, :2].tolist() == [[0, 0], [1, 0], [0, 1], [1, 1], [1, 0]]
+    np.testing.assert_array_equal(m2.pattern(), load_table("pattern_2d_brick2x1.txt"))
+
+
+def test_hand_enumerated_refinement_faces_3d():
+    """2x1x1 brick, tree 0 refined: the root of tree 1 receives restriction
+    from the four level-1 blocks with x=1, at offsets (y bit, z bit)."""
+    sp = synth.MeshSpec(ndim=3, N=4, ng=1, ntrees=(2, 1, 1), periodic=(0, 0, 0), max_level=1)
+    m = oracle.Mesh(sp, 0).adapt(np.array([1, 0], dtype=np.int8))
+    lev, g = m.blocks()
+    assert lev.tolist() == [1] * 8 + [0]
+    # Morton order inside tree 0, x lowest bit
+    assert g[:8].tolist() == [[x, y, z] for z in (0, 1) for y in (0, 1) for x in (0, 1)]
+    pat = m.pattern()
+    f2c = pat[pat[:, 0] == oracle.KIND_F2C]
+    assert f2c[:, 1:5].tolist() == [[0, 8, 1, 0], [0, 8, 3, 1], [0, 8, 5, 2], [0, 8, 7, 3]]
+    c2f = pat[pat[:, 0] == oracle.KIND_C2F]
+    assert c2f[:, 1:5].tolist() == [[1, 1, 8, 0], [1, 3, 8, 1], [1, 5, 8, 2], [1, 7, 8, 3]]
+
+
+def morton_decode(n, ndim, bits):
+    c = [0, 0, 0]
+    for b in range(bits):
+        for d in range(ndim):
+            c[d] |= ((n >> (ndim * b + d)) & 1) << b
+    return c
+
+
+@pytest.mark.parametrize("ndim,ntrees,level", [(2, (3, 2, 1), 3), (3, (2, 1, 2), 2)])
+def test_leaf_order_closed_form(ndim, ntrees, level):
+    """Uniform forest: block n = tree-major (row-major trees), Morton inside."""
+    sp = synth.MeshSpec(ndim=ndim, N=4, ng=1, ntrees=ntrees, max_level=level)
+    lev, g = oracle.Mesh(sp, level).blocks()
+    per_tree = 1 << (ndim * level)
+    for n in range(len(lev)):
+        t, mo = divmod(n, per_tree)
+        tx = t % ntrees[0]
+        ty = (t // ntrees[0]) % ntrees[1]
+        tz = t // (ntrees[0] * ntrees[1])
+        loc = morton_decode(mo, ndim, level)
+        exp = [tx * (1 << level) + loc[0], ty * (1 << level) + loc[1], (tz * (1 << level) + loc[2]) if ndim == 3 else 0]
+        assert g[n].tolist() == exp
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_uniform_periodic_pattern_closed_form(ndim):
+    """Every face of a uniform periodic mesh is SRL with the (g +- e_d) mod E neighbour."""
+    level = 2
+    ntrees = (2, 3, 1) if ndim == 2 else (2, 1, 2)
+    sp = synth.MeshSpec(ndim=ndim, N=4, ng=2, ntrees=ntrees, periodic=(1, 1, 1), max_level=level)
+    m = oracle.Mesh(sp, level)
+    lev, g = m.blocks()
+    index = {tuple(g[b]): b for b in range(len(lev))}
+    pat = m.pattern()
+    assert len(pat) == 2 * ndim * len(lev)
+    assert np.all(pat[:, 0] == oracle.KIND_SRL)
+    E = [ntrees[d] << level for d in range(3)]
+    for kind, face, dst, src, off, aux in pat:
+        d, side = divmod(face, 2)
+        q = list(g[dst])
+        q[d] = (q[d] + (1 if side else -1)) % E[d]
+        assert src == index[tuple(q)]
+        assert off == 0 and aux == 0
+
+
+def leaf_boxes(sp, lev, g):
+    """Integer boxes [lo, hi) of every leaf in units of the finest block."""
+    L = sp.max_level
+    size = 1 << (L - lev.astype(np.int64))
+    lo = g[:, :sp.ndim] * size[:, None]
+    return lo, lo + size[:, None]
+
+
+def touches(sp, alo, ahi, blo, bhi):
+    """Closed boxes intersect (periodic images included) and are distinct."""
+    ext = [sp.ntrees[d] << sp.max_level for d in range(sp.ndim)]
+    for shift in itertools.product(*[(-1, 0, 1) if sp.periodic[d] else (0,) for d in range(sp.ndim)]):
+        ok = True
+        for d in range(sp.ndim):
+            s = shift[d] * ext[d]
+            if blo[d] + s > ahi[d] or bhi[d] + s < alo[d]:
+                ok = False
+                break
+        if ok:
+            return True
+    return False
+
+
+def random_meshes(ndim, seed, rounds=4):
+    rng = np.random.default_rng(seed)
+    if ndim == 2:
+        sp = synth.MeshSpec(ndim=2, N=4, ng=2, ntrees=(3, 2, 1), periodic=(rng.integers(2), rng.integers(2), 1), max_level=4)
+    else:
+        sp = synth.MeshSpec(ndim=3, N=4, ng=2, ntrees=(2, 1, 2), periodic=tuple(int(x) for x in rng.integers(0, 2, 3)), max_level=3)
+    m = oracle.Mesh(sp, 1)
+    out = []
+    for _ in range(rounds):
+        flags = rng.choice(np.array([-1, 0, 1], dtype=np.int8), size=m.n, p=[0.35, 0.4, 0.25])
+        nm = m.adapt(flags)
+        out.append((m, flags, nm))
+        m = nm
+    return sp, out
+
+
+@pytest.mark.parametrize("ndim,seed", [(2, s) for s in range(6)] + [(3, s) for s in range(3)])
+def test_adapt_balance_coverage(ndim, seed):
+    sp, seq = random_meshes(ndim, seed)
+    for old, flags, new in seq:
+        lev, g = new.blocks()
+        lo, hi = leaf_boxes(sp, lev, g)
+        # coverage: volumes add up to the brick and leaves do not overlap
+        vol = np.prod(hi - lo, axis=1).sum()
+        assert vol == np.prod([sp.ntrees[d] << sp.max_level for d in range(ndim)])
+        for a in range(len(lev)):
+            for b in range(a + 1, len(lev)):
+                assert np.any(np.minimum(hi[a], hi[b]) <= np.maximum(lo[a], lo[b])), "overlap"
+        # full (corner) 2:1 balance, checked pairwise by geometry
+        for a in range(len(lev)):
+            for b in range(a + 1, len(lev)):
+                if abs(int(lev[a]) - int(lev[b])) > 1:
+                    assert not touches(sp, lo[a], hi[a], lo[b], hi[b])
+        assert new.balanced()
+        # each new leaf is within one level of the old leaf at its position;
+        # refine flags below max_level are honoured, keep flags never coarsen
+        olev, og = old.blocks()
+        olo, ohi = leaf_boxes(sp, olev, og)
+        for b in range(len(lev)):
+            c = lo[b]
+            hit = [a for a in range(len(olev)) if np.all(olo[a] <= c) and np.all(c < ohi[a])]
+            assert len(hit) == 1
+            a = hit[0]
+            assert abs(int(lev[b]) - int(olev[a])) <= 1
+            if flags[a] > 0 and olev[a] < sp.max_level:
+                assert lev[b] == olev[a] + 1
+            if flags[a] >= 0:
+                assert lev[b] >= olev[a]
+
+
+@pytest.mark.parametrize("ndim,seed", [(2, s) for s in range(6)] + [(3, s) for s in range(3)])
+def test_pattern_invariants(ndim, seed):
+    """Classification checked against box geometry, and every receiving face
+    covered exactly once; SRL and F2C/C2F entries are reciprocal."""
+    sp, seq = random_meshes(ndim, seed, rounds=3)
+    m = seq[-1][2]
+    lev, g = m.blocks()
+    lo, hi = leaf_boxes(sp, lev, g)
+    pat = m.pattern()
+    ext = [sp.ntrees[d] << sp.max_level for d in range(ndim)]
+    per_face = {}
+    for kind, face, dst, src, off, aux in pat:
+        per_face.setdefault((dst, face), []).append((kind, src, off))
+    assert len(per_face) == 2 * ndim * len(lev)
+    srl = set()
+    f2c = set()
+    c2f = set()
+    nbc = 0
+    for (dst, face), items in per_face.items():
+        d, side = divmod(face, 2)
+        kinds = {k for k, _, _ in items}
+        assert len(kinds) == 1
+        k = kinds.pop()
+        on_boundary = (lo[dst][d] == 0 and side == 0) or (hi[dst][d] == ext[d] and side == 1)
+        if k == oracle.KIND_BC:
+            assert on_boundary and not sp.periodic[d] and len(items) == 1
+            nbc += 1
+            continue
+        assert not (on_boundary and not sp.periodic[d])
+        if k == oracle.KIND_F2C:
+            assert len(items) == 2 ** (ndim - 1)
+            assert sorted(o for _, _, o in items) == list(range(2 ** (ndim - 1)))
+        else:
+            assert len(items) == 1
+        for _, src, off in items:
+            exp_lev = {oracle.KIND_SRL: 0, oracle.KIND_F2C: 1, oracle.KIND_C2F: -1}[k]
+            assert lev[src] - lev[dst] == exp_lev
+            # src lies across `face`: shift dst's box by its own size along d
+            size = hi[dst][d] - lo[dst][d]
+            probe_lo = lo[dst].copy()
+            probe_lo[d] = (probe_lo[d] + (size if side else -1)) % ext[d]
+            inside = all(lo[src][e] <= probe_lo[e] < hi[src][e] for e in range(ndim) if e == d)
+            assert inside
+            tds = [e for e in range(ndim) if e != d]
+            if k == oracle.KIND_SRL:
+                assert all(lo[src][e] == lo[dst][e] for e in tds)
+                srl.add((dst, face, src))
+            elif k == oracle.KIND_F2C:
+                pos = [(lo[src][e] - lo[dst][e]) // (hi[src][e] - lo[src][e]) for e in tds]
+                assert off == sum(p << i for i, p in enumerate(pos))
+                f2c.add((dst, face, src, off))
+            else:
+                pos = [(lo[dst][e] - lo[src][e]) // (hi[dst][e] - lo[dst][e]) for e in tds]
+                assert off == sum(p << i for i, p in enumerate(pos))
+                c2f.add((dst, face, src, off))
+    for dst, face, src in srl:
+        assert (src, face ^ 1, dst) in srl
+    assert {(s, f ^ 1, d, o) for d, f, s, o in f2c} == c2f
+    bc = pat[pat[:, 0] == oracle.KIND_BC]
+    assert bc[:, 5].tolist() == list(range(nbc))
+    # canonical order
+    keys = [tuple(r) for r in pat[:, [0, 1, 2, 4]]]
+    assert keys == sorted(keys)

@@ -1,0 +1,314 @@
+"""Pins of the oracle's numerics against what the paper and the mathematics
+fix: exactness of ghost filling / prolongation / restriction for a linear
+field (Sec. 4.3), free-stream preservation, conservation with flux fixing
+(Sec. 2.6, Eq. 12), agreement of a uniformly refined AMR mesh with a single
+level grid, the exact Riemann solution of a shock tube (Sec. 3.5), second
+order on a smooth exact solution (Sec. 4.1.2) and Toro's printed star states.
+CPU only."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import riemann
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- Riemann --
+
+def test_exact_riemann_matches_printed_star_states():
+    for line in open(os.path.join(GOLDEN, "toro_star_states.txt")):
+        line = line.split("#")[0].strip()
+        if not line:
+            continue
+        a, b = line.split("|")
+        rl, ul, pl, rr, ur, pr = map(float, a.split())
+        ps, us, rsl, rsr = map(float, b.split())
+        p, u = riemann.star_state((rl, ul, pl), (rr, ur, pr))
+        # printed with 5-6 significant digits
+        assert abs(p - ps) <= 6e-5 * abs(ps) + 1e-5
+        assert abs(u - us) <= 6e-5 * abs(us) + 1e-5
+        eps = 1e-9
+        rho_l = riemann.sample((rl, ul, pl), (rr, ur, pr), u - eps)[0]
+        rho_r = riemann.sample((rl, ul, pl), (rr, ur, pr), u + eps)[0]
+        assert abs(rho_l - rsl) <= 6e-5 * rsl + 1e-5
+        assert abs(rho_r - rsr) <= 6e-5 * rsr + 1e-5
+
+
+# ---------------------------------------------------------------- helpers --
+
+def heun_to(mesh, u, t_end, bc_data=None, fixed_dt=None):
+    t = 0.0
+    u1 = np.zeros_like(u)
+    while t < t_end * (1 - 1e-14):
+        mesh.fill_ghosts(u, bc_data)
+        dt = min(mesh.dt(u) if fixed_dt is None else fixed_dt, t_end - t)
+        oracle.heun_step(mesh, u, u1, dt=dt, bc_data=bc_data)
+        t += dt
+    return u
+
+
+def interior(spec, u):
+    nb = u.shape[0]
+    v = u.reshape((nb, spec.nvar) + (spec.side,) * spec.ndim)
+    sl = tuple(slice(spec.ng, spec.ng + spec.N) for _ in range(spec.ndim))
+    return v[(slice(None), slice(None)) + sl]
+
+
+def face_ghost_mask(spec):
+    m = np.zeros((spec.side,) * spec.ndim, dtype=bool)
+    rng = range(spec.side)
+    for idx in np.ndindex(*m.shape):
+        out = sum(1 for c in idx if c < spec.ng or c >= spec.ng + spec.N)
+        m[idx] = out <= 1
+    return m.reshape(-1)
+
+
+# ------------------------------------------------- P2: linear solution test --
+
+def linear_case(ndim, ng, ref, max_level):
+    """Refine toward r_ref one level at a time, then derefine (Sec. 4.3)."""
+    sp = synth.MeshSpec(ndim=ndim, N=8, ng=ng, ntrees=(1, 1, 1), periodic=(0, 0, 0),
+                        max_level=max_level, bc_type=(3,) * 6)
+    r_ref = [0.5 + 0.49 * c for c in ref]
+    mask = face_ghost_mask(sp)
+    m = oracle.Mesh(sp, 0)
+    lev, g = m.blocks()
+    u = synth.linear_field(sp, lev, g)
+    worst = 0.0
+
+    def check(mesh, u):
+        lev, g = mesh.blocks()
+        pat = mesh.pattern()
+        bce = [(f, d) for k, f, d, s, o, a in pat if k == oracle.KIND_BC]
+        bc = synth.linear_face_values(sp, lev, g, bce)
+        mesh.fill_ghosts(u, bc)
+        exact = synth.linear_field(sp, lev, g, with_ghosts=True)
+        err = np.abs(u - exact)[:, :, mask].max()
+        return err / np.abs(exact[:, :, mask]).max()
+
+    worst = max(worst, check(m, u))
+    for _ in range(max_level):
+        lev, g = m.blocks()
+        m2 = m.adapt(synth.point_flags(sp, lev, g, r_ref, max_level))
+        u = m.transfer(u, m2)
+        m = m2
+        worst = max(worst, check(m, u))
+    while True:
+        lev, g = m.blocks()
+        top = lev.max()
+        if top == 0:
+            break
+        m2 = m.adapt(np.where(lev == top, -1, 0).astype(np.int8))
+        assert m2.blocks()[0].max() == top - 1
+        u = m.transfer(u, m2)
+        m = m2
+        worst = max(worst, check(m, u))
+    return worst
+
+
+@pytest.mark.parametrize("ng", [1, 2, 3, 4])
+def test_linear_solution_exact_2d(ng):
+    """phi = x + 2y (+3z): ghosts, prolongation and restriction are exact up
+    to rounding; the paper's bound is 1e-15 (Sec. 4.3), i.e. a few ulp of the
+    largest value."""
+    for i in (-1, 0, 1):
+        for j in (-1, 0, 1):
+            assert linear_case(2, ng, (i, j, 0), 7) < 4.5e-16 * 8
+
+
+@pytest.mark.parametrize("ng", [1, 2, 3, 4])
+def test_linear_solution_exact_3d(ng):
+    refs = [(-1, -1, -1), (0, 0, 0), (1, 0, -1), (1, 1, 0)]
+    for ref in refs:
+        assert linear_case(3, ng, ref, 3) < 4.5e-16 * 8
+
+
+# ---------------------------------------------------- P3: free stream --
+
+def amr_mesh(sp, centre, levels, radii):
+    m = oracle.Mesh(sp, 0)
+    for _ in range(levels):
+        lev, g = m.blocks()
+        m = m.adapt(synth.ball_flags(sp, lev, g, centre, radii))
+    return m
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_free_stream_bit_exact(ndim):
+    """A uniform flow stays bit-identical on a 3-level periodic AMR mesh."""
+    if ndim == 2:
+        sp = synth.MeshSpec(ndim=2, N=8, ng=2, ntrees=(4, 4, 1), max_level=2)
+    else:
+        sp = synth.MeshSpec(ndim=3, N=8, ng=2, ntrees=(4, 4, 4), max_level=2)
+    centre, radii = ((0.4, 0.55), (0.3, 0.15)) if ndim == 2 else ((0.5, 0.5, 0.5), (0.15, 0.05))
+    m = amr_mesh(sp, centre, 2, radii)
+    lev, g = m.blocks()
+    assert set(lev.tolist()) == {0, 1, 2}
+    rho = np.ones([m.n] + [sp.side] * ndim)
+    vel = [0.3 * rho, -0.2 * rho, 0.1 * rho][:ndim]
+    u = synth.mask_interior(sp, synth.primitive_to_state(sp, rho, vel, 0.7 * rho))
+    u0 = u.copy()
+    oracle.run_heun(m, u, 10)
+    np.testing.assert_array_equal(interior(sp, u), interior(sp, u0))
+
+
+# ----------------------------------------------------- P4: conservation --
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_conservation_periodic_amr(ndim):
+    """Flux fixing makes the scheme conservative across refinement faces:
+    sum of U dV drifts only by rounding (Eq. 12, Sec. 2.6)."""
+    if ndim == 2:
+        sp = synth.MeshSpec(ndim=2, N=8, ng=2, ntrees=(4, 4, 1), max_level=2)
+        m = amr_mesh(sp, (0.5, 0.5), 2, (0.3, 0.15))
+        lev, g = m.blocks()
+        u = synth.kelvin_helmholtz(sp, lev, g, seed=3)
+    else:
+        sp = synth.MeshSpec(ndim=3, N=8, ng=2, ntrees=(4, 4, 4), max_level=2)
+        m = amr_mesh(sp, (0.45, 0.5, 0.55), 2, (0.15, 0.05))
+        assert set(m.blocks()[0].tolist()) == {0, 1, 2}
+        lev, g = m.blocks()
+        u = synth.fourier3d(sp, lev, g, seed=2)
+    s0 = m.conserved(u)
+    scale = m.conserved(np.abs(u))
+    oracle.run_heun(m, u, 20)
+    drift = np.abs(m.conserved(u) - s0) / scale
+    assert drift.max() < 1e-13
+
+
+# ---------------------------------------- P6: uniform AMR == single level --
+
+def test_uniform_refined_equals_single_level():
+    """8x8 trees refined once == 16x16 trees at level 0 (same 256^2 cells),
+    bit-identical after 100 Kelvin-Helmholtz steps."""
+    spA = synth.MeshSpec(ndim=2, N=16, ng=2, ntrees=(8, 8, 1), max_level=1)
+    spB = synth.MeshSpec(ndim=2, N=16, ng=2, ntrees=(16, 16, 1), max_level=0)
+    mA = oracle.Mesh(spA, 1)
+    mB = oracle.Mesh(spB, 0)
+    levA, gA = mA.blocks()
+    levB, gB = mB.blocks()
+    uA = synth.kelvin_helmholtz(spA, levA, gA, seed=0)
+    uB = synth.kelvin_helmholtz(spB, levB, gB, seed=0)
+    dA = oracle.run_heun(mA, uA, 100)
+    dB = oracle.run_heun(mB, uB, 100)
+    assert dA == dB
+    iB = {tuple(gB[b][:2]): b for b in range(mB.n)}
+    perm = [iB[tuple(gA[b][:2])] for b in range(mA.n)]
+    np.testing.assert_array_equal(interior(spA, uA), interior(spB, uB[perm]))
+
+
+# ---------------------------------------------------- P5: shock tube --
+
+def sod_l1(ncell, axis=0, ndim=2, t_end=0.2, fixed_dt=None):
+    n_t = ncell // 16
+    if ndim == 2:
+        ntrees = [1, 1, 1]
+        ntrees[axis] = n_t
+        sp = synth.MeshSpec(ndim=2, N=16, ng=2, ntrees=tuple(ntrees), periodic=(1, 1, 1), max_level=0,
+                            bc_type=(0, 0, 0, 0, 0, 0))
+    else:
+        ntrees = [1, 1, 1]
+        ntrees[axis] = n_t
+        sp = synth.MeshSpec(ndim=3, N=16, ng=2, ntrees=tuple(ntrees), periodic=(1, 1, 1), max_level=0)
+    per = [1, 1, 1]
+    per[axis] = 0
+    bct = [0] * 6
+    bct[2 * axis] = bct[2 * axis + 1] = synth.BC_NEUMANN
+    sp.periodic = tuple(per)
+    sp.length = tuple(1.0 if d == axis else 16.0 / ncell for d in range(3))
+    sp.bc_type = tuple(bct)
+    m = oracle.Mesh(sp, 0)
+    lev, g = m.blocks()
+    u = synth.shock_tube(sp, lev, g, axis=axis)
+    heun_to(m, u, t_end, fixed_dt=fixed_dt)
+    X = synth.cell_centres(sp, lev, g, with_ghosts=False)
+    rho = interior(sp, u)[:, 0]
+    dx = 1.0 / ncell
+    exact = riemann.cell_average_density((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), X[axis] - 0.5 * dx, dx, 0.5, t_end)
+    return np.abs(rho - exact).mean(), rho, X[axis]
+
+
+def test_sod_against_exact_riemann():
+    errs = []
+    for n in (128, 256, 512):
+        e, rho, x = sod_l1(n)
+        errs.append(e)
+        # y-invariance: every row identical
+        r = rho.reshape(rho.shape[0], 16, 16)
+        assert np.all(r == r[:, :1, :])
+    assert errs[-1] < 1e-2
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert min(orders) >= 0.6, orders
+
+
+def test_shock_tube_axis_permutation_3d():
+    """The same tube along x, y and z gives bit-identical profiles (catches
+    transposed indices and misplaced velocity components)."""
+    profs = []
+    for axis in range(3):
+        # fixed dt: the CFL sum over dimensions is order dependent
+        e, rho, x = sod_l1(64, axis=axis, ndim=3, t_end=0.1, fixed_dt=0.1 / 64)
+        assert e < 0.03
+        # rho: [block, k, j, i]; blocks follow the tube axis in order
+        lines = np.moveaxis(rho, 3 - axis, -1)          # tube axis last
+        assert np.all(lines == lines[:, :1, :1, :])     # transverse invariance
+        profs.append(lines[:, 0, 0, :].reshape(-1))
+    np.testing.assert_array_equal(profs[0], profs[1])
+    np.testing.assert_array_equal(profs[0], profs[2])
+
+
+# ---------------------------------------------- P7: smooth solution order --
+
+def test_density_wave_second_order():
+    errs = []
+    for ntr in (2, 4, 8):
+        sp = synth.MeshSpec(ndim=2, N=16, ng=2, ntrees=(ntr, ntr, 1), max_level=0, cfl=0.4)
+        m = oracle.Mesh(sp, 0)
+        lev, g = m.blocks()
+        u = synth.density_wave(sp, lev, g)
+        t_end = 0.25
+        heun_to(m, u, t_end)
+        exact = synth.density_wave_exact(sp, lev, g, t_end)
+        sl = slice(sp.ng, sp.ng + sp.N)
+        exact = exact[:, sl, sl]
+        errs.append(np.abs(interior(sp, u)[:, 0] - exact).mean())
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert orders[-1] >= 1.8, orders
+
+
+# ---------------------------------------------------------- dt & flags --
+
+def test_dt_closed_form():
+    sp = synth.MeshSpec(ndim=3, N=8, ng=2, ntrees=(2, 1, 1), max_level=1, length=(2.0, 1.0, 0.5))
+    m = oracle.Mesh(sp, 0).adapt(np.array([1, 0], dtype=np.int8))
+    lev, g = m.blocks()
+    rho = np.full([m.n] + [sp.side] * 3, 1.3)
+    vel = [0.2 * np.ones_like(rho), -0.4 * np.ones_like(rho), 0.1 * np.ones_like(rho)]
+    u = synth.primitive_to_state(sp, rho, vel, 0.9 * np.ones_like(rho))
+    c = math.sqrt(1.4 * 0.9 / 1.3)
+    # finest cells (level 1): dx = (2/2/16, 1/16, 0.5/16)
+    dxs = [2.0 / 2 / 8 / 2, 1.0 / 8 / 2, 0.5 / 8 / 2]
+    exp = sum((abs(v) + c) / dxs[d] for d, v in enumerate((0.2, -0.4, 0.1)))
+    assert m.max_speed(u) == pytest.approx(exp, rel=1e-14)
+
+
+def test_lohner_flags_closed_form():
+    """Linear data gives E = 0 everywhere (derefine); a density jump gives
+    E = |b - a| / (eps_abs + |b - a| + eps (3|a| + |b|)) at the jump (refine)."""
+    sp = synth.MeshSpec(ndim=2, N=8, ng=2, ntrees=(4, 1, 1), periodic=(0, 1, 1), max_level=1,
+                        bc_type=(2, 2, 0, 0, 0, 0), length=(1.0, 0.25, 1.0))
+    m = oracle.Mesh(sp, 0)
+    lev, g = m.blocks()
+    u = synth.shock_tube(sp, lev, g, x0=0.5)
+    m.fill_ghosts(u)
+    flags = m.lohner_flags(u)
+    # blocks 1 and 2 touch the jump at x = 0.5; blocks 0 and 3 are uniform
+    assert flags.tolist() == [-1, 1, 1, -1]
+    a, b = 1.0, 0.125
+    E = abs(b - a) / (1e-10 + abs(b - a) + 1e-2 * (3 * a + b))
+    assert E > 5e-2
