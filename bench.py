@@ -1,0 +1,366 @@
+#!/usr/bin/env python3
+"""Benchmark of the block-AMR hot path: cell-updates/s per Runge-Kutta stage,
+ghost fill included (the paper's GCUPS with an n-stage scheme counted as n
+updates per cell, Sec. 5.1).
+
+Default workload (N=1): 3D Euler on a uniform periodic 256^3 mesh tiled as
+4096 blocks of 16^3 cells, 2 ghost layers, seeded random smooth density and
+velocity field (8 Fourier modes), Heun / SSP-RK2, CFL 0.5.  The headline
+`value` is the FP32 form (FP32 state, FP64 dt reduction) replaying one step
+as a CUDA graph; `fp64_plain` is the plain FP64 form with separate launches;
+`block_sizes` repeats the FP32 form with 8^3 and 32^3 blocks.
+
+One process per GPU (torchrun for N>1).  The mesh does not shard: each rank
+advances its own replica (weak scaling), and `value` sums all ranks' cell
+updates over the slowest rank's time.
+
+`--impl reference` times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "cell-updates/s per RK stage incl. ghost fill (FP32 batched vs FP64 plain), % HBM peak"
+UNIT = "cell-updates/s"
+
+
+def workload_spec(block_n=16, cells=256, ndim=3):
+    nt = cells // block_n
+    return synth.MeshSpec(ndim=ndim, N=block_n, ng=2, ntrees=(nt, nt, nt if ndim == 3 else 1), max_level=0)
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+# ---------------------------------------------------------------- clocks --
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------ the GPU arm --
+
+def algorithmic_stage_bytes(spec, esize):
+    """Bytes a stage must move per block (Sec. 3.1 Eq. 4 with Heun): stage 1
+    reads the derivative state's interior and face ghosts and writes the
+    output; stage 2 also reads the previous state's interior."""
+    N, V, d, ng = spec.N, spec.nvar, spec.ndim, spec.ng
+    interior = N ** d
+    halo = 2 * d * N ** (d - 1) * ng
+    s1 = (interior + halo) * V * esize + interior * V * esize
+    s2 = s1 + interior * V * esize
+    return s1, s2
+
+
+def stage_kernel_hash():
+    h = hashlib.sha256()
+    for f in ("stage.cuh", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2605_07612_b300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profile(workload):
+    p = os.path.join(ROOT, "profiles", "stage_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    ent = d.get(workload)
+    if not ent or ent.get("kernel_hash") != stage_kernel_hash():
+        return None
+    return ent.get("bytes_per_launch")
+
+
+def run_ours(args, rank, world, dist):
+    import torch
+    import paper_2605_07612_b300 as amr
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def make(spec, precision):
+        f = amr.Forest(spec, 0, precision=precision)
+        lev, g = f.blocks()
+        u = synth.fourier3d(spec, lev, g, seed=1 + rank) if spec.ndim == 3 else synth.kelvin_helmholtz(spec, lev, g)
+        f.set_state(0, u.astype(f.dtype))
+        f.compute_dt(0, stream=stream)
+        return f
+
+    def time_steps(f, steps, warmup, graph):
+        f.step(warmup, use_graph=graph, stream=stream)
+        stream.synchronize()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        l0 = f.launch_count()
+        e0.record(stream)
+        f.step(steps, use_graph=graph, stream=stream)
+        e1.record(stream)
+        stream.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        launches = f.launch_count() - l0
+        if dist is not None:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, launches
+
+    spec = workload_spec(16)
+    cells = spec.ntrees[0] * spec.ntrees[1] * spec.ntrees[2] * spec.N ** 3
+    f = make(spec, 32)
+    state_bytes = f.n * spec.nvar * spec.ncell * 4
+    with ClockSampler(dev) as clk:
+        ms, launches = time_steps(f, args.steps, args.warmup, True)
+    clocks = clk.summary()
+    st = f.sync_status()
+    if st != amr.AMR_OK:
+        raise SystemExit("device status %d after the timed steps" % st)
+    value = 2.0 * cells * args.steps * world / (ms * 1e-3)
+
+    # dominant kernel (the stage) timed per launch on its own stream
+    s1b, s2b = algorithmic_stage_bytes(spec, 4)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    t1 = t2 = 0.0
+    reps = max(3, args.steps // 2)
+    f.step(1, stream=stream)
+    for _ in range(reps):
+        f.fill_ghosts(0, stream=stream)
+        ev[0].record(stream)
+        f.advance_stage(1, 0, [0], [1.0], 1.0, stream=stream)
+        ev[1].record(stream)
+        f.fill_ghosts(1, stream=stream)
+        ev[2].record(stream)
+        f.advance_stage(0, 1, [0, 1], [0.5, 0.5], 0.5, update_dt=True, stream=stream)
+        ev[3].record(stream)
+        stream.synchronize()
+        t1 += ev[0].elapsed_time(ev[1])
+        t2 += ev[2].elapsed_time(ev[3])
+    t1 /= reps
+    t2 /= reps
+    per_launch_bytes = f.n * (s1b + s2b) / 2.0
+    achieved = per_launch_bytes / ((t1 + t2) / 2.0 * 1e-3) / 1e9
+    peak, peak_src = measured_peaks()
+    traffic = traffic_from_profile("uniform3d-256-b16-fp32")
+
+    # end to end through host buffers: every step copies the state in from
+    # pinned host memory and the result back out
+    host = torch.empty(state_bytes // 4, dtype=torch.float32).pin_memory()
+    f.get_state(0, out=host, stream=stream)
+    e2e_steps = max(2, min(args.steps, 5))
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        f.set_state(0, host, stream=stream)
+        f.step(1, use_graph=True, stream=stream)
+        f.get_state(0, out=host, stream=stream)
+    e1.record(stream)
+    stream.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    e2e_val = 2.0 * cells * e2e_steps * world / (e2e_ms * 1e-3)
+    del f
+    torch.cuda.empty_cache()
+
+    extras = {}
+    if not args.no_extras:
+        # plain FP64 form: separate launches, no graph
+        f64 = make(spec, 64)
+        ms64, _ = time_steps(f64, max(2, args.steps // 4), 1, False)
+        v64 = 2.0 * cells * max(2, args.steps // 4) * world / (ms64 * 1e-3)
+        extras["fp64_plain"] = {"value": v64, "unit": UNIT, "ms_per_step": ms64 / max(2, args.steps // 4),
+                                "speedup_fp32_graph_over_fp64_plain": value / v64}
+        del f64
+        torch.cuda.empty_cache()
+        bs = {}
+        for bn in (8, 32):
+            sp = workload_spec(bn)
+            fb = make(sp, 32)
+            msb, _ = time_steps(fb, args.steps, args.warmup, True)
+            bs["%d^3" % bn] = {"value": 2.0 * cells * args.steps * world / (msb * 1e-3), "blocks": fb.n,
+                               "ms_per_step": msb / args.steps}
+            del fb
+            torch.cuda.empty_cache()
+        extras["block_sizes"] = bs
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "uniform3d-256-b16-fp32", "mesh": "256^3 cells, 4096 blocks of 16^3, 2 ghost layers, periodic",
+                   "scheme": "Euler, MUSCL-minmod, Rusanov/Einfeldt, Heun (2 stages), CFL 0.5",
+                   "form": "FP32 state, FP64 dt reduction, one step replayed as a CUDA graph",
+                   "parallelism": "replicas x%d (one mesh per GPU)" % world,
+                   "l2": "inputs larger than L2 (%.2f GB state per slot)" % (state_bytes / 1e9)},
+        "roofline": {"bound": "hbm", "kernel": "k_stage (FP32, 16^3)", "achieved": achieved, "peak": peak,
+                     "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "algorithmic_bytes_per_launch": per_launch_bytes,
+                     "avg_launch_ms": (t1 + t2) / 2.0},
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
+                "steps": e2e_steps},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    line.update(extras)
+    return line
+
+
+# ------------------------------------------------------- CPU oracle arm --
+
+def oracle_sample(seconds_hint=15.0):
+    """FP64 oracle on a bounded sample of the workload: the same 16^3 blocks
+    and initial field, 4x4x4 blocks (64 blocks, 262144 cells), whole Heun
+    steps, on every host core the oracle's OpenMP uses."""
+    import oracle
+    spec = workload_spec(16, cells=64)
+    m = oracle.Mesh(spec, 0)
+    lev, g = m.blocks()
+    u = synth.fourier3d(spec, lev, g, seed=1)
+    cells = m.n * spec.N ** 3
+    oracle.heun_step(m, u, np.zeros_like(u))     # warm-up
+    steps = 0
+    t0 = time.perf_counter()
+    u1 = np.zeros_like(u)
+    while True:
+        oracle.heun_step(m, u, u1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el > seconds_hint or steps >= 2000:
+            break
+    return {"value": 2.0 * cells * steps / el, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+            "sample": "3D 64^3 cells as 4x4x4 periodic blocks of 16^3 (same seeded Fourier field), %d Heun steps, FP64" % steps,
+            "seconds": el}
+
+
+def run_reference(args):
+    per = []
+    for _ in range(args.warmup):
+        oracle_sample(2.0)
+    for _ in range(args.steps):
+        per.append(oracle_sample(max(2.0, 60.0 / max(args.steps, 1))))
+    val = sum(p["value"] for p in per) / len(per)
+    cpu = dict(per[-1])
+    cpu["value"] = val
+    return {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "uniform3d-256-b16-fp32", "sample": cpu["sample"]},
+        "cpu_baseline": cpu,
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as td
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        td.init_process_group("nccl")
+        dist = td
+    line = run_ours(args, rank, world, dist)
+    if rank == 0:
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = oracle_sample()
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

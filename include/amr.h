@@ -1,0 +1,247 @@
+/*
+ * amr.h -- C ABI of the B300 block-AMR hot path.
+ *
+ * The library keeps a quadtree/octree forest of N^d-cell blocks on the host
+ * and the block data on one GPU, and executes the per-time-step work of the
+ * method of "foap4: adaptive mesh refinement with OpenACC, MPI, and p4est":
+ * the ghost-cell pattern (same-level copies, fine-to-coarse restriction,
+ * coarse-to-fine limited prolongation, physical boundaries; Sec. 2.5) and the
+ * explicit finite-volume Runge-Kutta update of the Euler equations with flux
+ * fixing at refinement boundaries (Sec. 2.6, Sec. 3.1-3.5).
+ *
+ * Conventions shared by every call:
+ *  - Every call returns an amr_status and never aborts the process.  The
+ *    message of the last failure of a forest is available from
+ *    amr_last_error().  Errors found on the device (non-physical states,
+ *    expired device waits) are latched in a device status word and reported
+ *    by amr_sync_status().
+ *  - The forest owns every host and device buffer it allocates (through the
+ *    dev_alloc/dev_free hook of amr_config when given, cudaMalloc otherwise).
+ *    Pointers passed in are borrowed for the duration of the call only.
+ *    Streams are owned by the caller; an amr_stream is a cudaStream_t (NULL =
+ *    the legacy default stream).
+ *  - Block data layout is Eq. 2 of the paper, uu(i, j, k, ivar, iblock) with
+ *    i fastest and ghost layers included: element (i, j, k, v, b) of state
+ *    slot s sits at index
+ *        (((s * max_blocks + b) * n_var + v) * S + (k + ng)) * S + j + ng) * S + i + ng
+ *    with S = block_n + 2 n_ghost and i, j, k in [-ng, block_n + ng)
+ *    (k absent in 2D).  Elements are float (precision 32) or double (64).
+ *  - Blocks are numbered in leaf order: trees row-major (x fastest), Morton
+ *    order inside a tree with x the lowest bit (Sec. 2.2: the n-th quadrant
+ *    is the n-th block).
+ *  - A forest is not thread safe; distinct forests are independent.
+ */
+#ifndef AMR_B300_H
+#define AMR_B300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    AMR_OK = 0,
+    AMR_EINVAL = 1,      /* invalid argument or configuration */
+    AMR_ENOMEM = 2,      /* host or device allocation failed */
+    AMR_ECAPACITY = 3,   /* a regrid would exceed max_blocks; mesh and data unchanged */
+    AMR_ECUDA = 4,       /* a CUDA runtime call failed */
+    AMR_ETIMEOUT = 5,    /* a bounded device wait expired */
+    AMR_EBOUNDS = 6,     /* a checked index fell outside its buffer */
+    AMR_ENONPHYS = 7,    /* density or pressure <= 0 met by a stage */
+    AMR_ESTATE = 8       /* call out of order (e.g. no ghost pattern yet) */
+} amr_status;
+
+/* Physical boundary kinds per face direction (Sec. 2.4). */
+typedef enum {
+    AMR_BC_PERIODIC = 0,   /* through the connectivity; the dimension must be periodic */
+    AMR_BC_DIRICHLET = 1,  /* uniform value bc_val[face][var] */
+    AMR_BC_NEUMANN = 2,    /* uniform outward normal derivative bc_val[face][var] */
+    AMR_BC_DATA = 3        /* Dirichlet values per boundary-face cell, amr_set_bc_data() */
+} amr_bc;
+
+/* Ghost-strip kinds by direction of data flow (Sec. 2.5). */
+typedef enum {
+    AMR_GHOST_SRL = 0,     /* same refinement level: copy */
+    AMR_GHOST_F2C = 1,     /* fine -> coarse: restriction into the coarse block's ghosts */
+    AMR_GHOST_BC = 2,      /* physical boundary */
+    AMR_GHOST_C2F = 3      /* coarse -> fine: limited prolongation, second round */
+} amr_ghost_kind;
+
+typedef struct amr_forest amr_forest;
+typedef void *amr_stream;  /* cudaStream_t */
+
+typedef void *(*amr_dev_alloc_fn)(size_t bytes, void *ctx);
+typedef void (*amr_dev_free_fn)(void *ptr, void *ctx);
+
+/* Problem statement.  Sec. 2.2 (brick of trees, max refinement), Sec. 2.3
+ * (N^d blocks, N even and N >= n_ghost; this library also needs
+ * N >= 2 n_ghost so that a coarse ghost layer maps inside one fine block),
+ * Sec. 2.3 static capacity max_blocks x n_states blocks (Sec. 3.1),
+ * Sec. 2.4 boundary kinds in the face order -x, +x, -y, +y, -z, +z. */
+typedef struct {
+    int ndim;              /* 2 or 3 */
+    int block_n;           /* N: 8, 16 or 32 */
+    int n_ghost;           /* ghost layers, 1..4 (the Euler stage needs >= 2) */
+    int n_var;             /* ndim + 2 (rho, rho v, E) */
+    int ntrees[3];         /* brick of trees (unused entries 1) */
+    int periodic[3];
+    double lo[3], len[3];  /* domain corner and extent */
+    int max_level;         /* finest level, <= 12 */
+    int max_blocks;        /* capacity in blocks per state slot */
+    int n_states;          /* state slots (Heun needs 2) */
+    int precision;         /* 32 or 64 */
+    double gamma, cfl;
+    int bc[6];             /* amr_bc per face direction */
+    double bc_val[6][8];   /* per face direction and variable */
+    amr_dev_alloc_fn dev_alloc;   /* optional allocation hook (NULL: cudaMalloc) */
+    amr_dev_free_fn dev_free;
+    void *alloc_ctx;
+    int host_only;         /* 1: mesh and ghost pattern only -- no device memory
+                              is touched; calls on block data return AMR_ESTATE
+                              and amr_flag_and_regrid needs explicit flags */
+} amr_config;
+
+/* One canonical ghost-pattern entry: one per (receiving block, face), and one
+ * per fine source block for F2C.  face = direction from dst towards src;
+ * offset = position of the fine block inside the coarse face (bit 0 along the
+ * lower tangential dimension); aux = boundary-face index for BC entries
+ * (row of the bc_data array), else 0; src = -1 for BC.  Entries are sorted by
+ * (kind, face, dst, offset) -- the paper sorts its index arrays by neighbour
+ * type, face direction, receiving block and hanging offset (Sec. 2.5). */
+typedef struct {
+    int32_t kind, face, dst, src, offset, aux;
+} amr_ghost_entry;
+
+/* One forward-Euler sub-step of Eq. 4 (Sec. 3.1):
+ *   u(s_out) = w_dt * dt * F(u(s_deriv)) + sum_i w_prev[i] u(s_prev[i])
+ * dt is the device-resident time step of the forest.  update_dt = 1 marks
+ * the last stage of a step: the stage also reduces the CFL limit of its own
+ * output (after flux fixing) into the next dt. */
+typedef struct {
+    int s_out, s_deriv;
+    int n_prev;
+    int s_prev[4];
+    double w_prev[4];
+    double w_dt;
+    int update_dt;
+} amr_stage;
+
+/* Refinement-criterion constants of Eq. 5 (Sec. 3.3).  The criterion is
+ * evaluated on density and pressure; a cell's value is the larger one. */
+typedef struct {
+    double c_refine, c_derefine, eps, eps_abs;
+} amr_flag_params;
+
+/* Creates the brick of Sec. 2.2 refined uniformly to init_level, allocates
+ * n_states x max_blocks blocks of device state (Sec. 2.3 static allocation;
+ * zero-filled) and builds the ghost pattern.  *out receives the forest.
+ * Errors: AMR_EINVAL (bad config), AMR_ECAPACITY (init mesh larger than
+ * max_blocks), AMR_ENOMEM, AMR_ECUDA. */
+amr_status amr_create_forest(const amr_config *cfg, int init_level, amr_forest **out);
+
+/* Frees everything the forest owns.  NULL is accepted. */
+amr_status amr_destroy_forest(amr_forest *f);
+
+/* Number of leaf blocks. */
+amr_status amr_n_blocks(const amr_forest *f, int64_t *n);
+
+/* Level and integer block coordinates (at the block's own level, counted over
+ * the whole brick; coords[3b+2] = 0 in 2D) of the first min(cap, n) blocks
+ * in block order (Sec. 2.2).  Either array may be NULL.  *n = block count. */
+amr_status amr_get_blocks(const amr_forest *f, int32_t *level, int64_t *coords, int64_t cap, int64_t *n);
+
+/* Classifies every block face as SRL / F2C / C2F / BC from the forest's face
+ * connectivity and uploads the index lists to the device (Sec. 2.5: built on
+ * the CPU, executed on the GPU).  A no-op when the mesh revision has not
+ * changed since the last build (Sec. 2.2 mesh revision number). */
+amr_status amr_build_ghost_pattern(amr_forest *f);
+
+/* Copies the canonical pattern (see amr_ghost_entry) into out[0..cap).
+ * *n = total number of entries (call with cap = 0 to size the buffer). */
+amr_status amr_get_ghost_pattern(const amr_forest *f, amr_ghost_entry *out, int64_t cap, int64_t *n);
+
+/* Copies n_blocks blocks of state slot s (layout above, ghosts included) from
+ * src, which is a host pointer (on_device = 0) or a device pointer of the
+ * current device (on_device = 1).  Ordered on `stream`; host copies are
+ * complete when the call returns. */
+amr_status amr_set_state(amr_forest *f, int s, const void *src, int on_device, amr_stream stream);
+
+/* Copies n_blocks blocks of state slot s into dst (host or device pointer);
+ * host copies are complete when the call returns. */
+amr_status amr_get_state(const amr_forest *f, int s, void *dst, int on_device, amr_stream stream);
+
+/* Device pointer of state slot s (max_blocks blocks); valid until the forest
+ * is destroyed. */
+amr_status amr_state_ptr(const amr_forest *f, int s, void **ptr);
+
+/* Dirichlet values for the AMR_BC_DATA faces (Sec. 2.4, Eq. 3 bc_data):
+ * host array [n_bf][n_var][N^(d-1)] in double, n_bf = number of BC entries of
+ * the current pattern in canonical order (row = entry's aux), face-cell index
+ * with the lower tangential dimension fastest.  Must be set again after a
+ * regrid (the paper refreshes it through a callback; out of scope here). */
+amr_status amr_set_bc_data(amr_forest *f, const double *values, int64_t n_values);
+
+/* Fills the face ghost cells of state slot s: round 1 (SRL copies, physical
+ * boundaries, F2C restriction), then round 2 (C2F limited prolongation, which
+ * reads round-1 ghosts of the coarse blocks) -- Sec. 2.5.  Edge and corner
+ * ghost cells are not filled (Sec. 2.1). */
+amr_status amr_fill_ghosts(amr_forest *f, int s, amr_stream stream);
+
+/* Sets the device time step to cfl / max over leaf cells of
+ * sum_d (|v_d| + c) / dx_d of state slot s (Sec. 3.2, step 2c). */
+amr_status amr_compute_dt(amr_forest *f, int s, amr_stream stream);
+
+/* Overwrites / reads the device time step (read synchronises `stream`). */
+amr_status amr_set_dt(amr_forest *f, double dt, amr_stream stream);
+amr_status amr_get_dt(amr_forest *f, double *dt, amr_stream stream);
+
+/* One stage of Eq. 4 on every block: primitive reconstruction with the minmod
+ * limiter, Rusanov fluxes with Einfeldt wave speeds, divergence, Runge-Kutta
+ * combination (Sec. 3.2), then flux fixing at refinement boundaries (Sec. 2.6)
+ * with the stage's time step w_dt * dt.  s_deriv's ghosts must be filled.
+ * s_out may equal one of s_prev. */
+amr_status amr_advance_stage(amr_forest *f, const amr_stage *st, amr_stream stream);
+
+/* n_steps steps of Heun's method (Eq. 5-6) on slot 0 (slot 1 as the stage
+ * state): fill ghosts, stage 1, fill ghosts, stage 2 with the dt update.
+ * use_graph = 1 captures one step in a CUDA graph on first use and replays it
+ * (re-captured after a regrid).  The dt must be set (amr_compute_dt). */
+amr_status amr_step(amr_forest *f, int n_steps, int use_graph, amr_stream stream);
+
+/* Integral of every conserved variable over the leaves of slot s, summed in
+ * double on the device in a fixed order (Eq. 12).  Synchronises `stream`. */
+amr_status amr_conserved(amr_forest *f, int s, double *sums, amr_stream stream);
+
+/* Refinement flags of slot s from the criterion of Eq. 5 (ghosts must be
+ * filled): +1 refine, -1 derefine, 0 keep, per block.  Copied to flags_out
+ * (host, n_blocks entries); synchronises `stream`. */
+amr_status amr_flag(amr_forest *f, int s, const amr_flag_params *prm, int8_t *flags_out, amr_stream stream);
+
+/* Adapts the mesh (Sec. 2.2): flags from `flags` (host, one per block) or,
+ * when flags is NULL, from amr_flag() on slot 0 after a ghost fill; refine,
+ * coarsen (a family only when all of its children are flagged -1), 2:1
+ * balance across faces, edges and corners; then, if the mesh changed, moves
+ * slot 0's data to the new blocks on the GPU (copy / prolong / restrict) and
+ * rebuilds the ghost pattern.  Slot 0's ghosts are filled first.  Other slots
+ * are scratch afterwards.  AMR_ECAPACITY leaves mesh and data unchanged.
+ * *changed (may be NULL) = 1 when the mesh changed. */
+amr_status amr_flag_and_regrid(amr_forest *f, const amr_flag_params *prm, const int8_t *flags,
+                               int *changed, amr_stream stream);
+
+/* Reads and clears the device status word (synchronises `stream`): AMR_OK or
+ * the first device-side error (AMR_ENONPHYS, AMR_ETIMEOUT, AMR_EBOUNDS). */
+amr_status amr_sync_status(amr_forest *f, amr_stream stream);
+
+/* Message of the last failed call on f ("" if none).  Never NULL. */
+const char *amr_last_error(const amr_forest *f);
+
+/* Kernel launches issued by the library since the forest was created. */
+amr_status amr_launch_count(const amr_forest *f, int64_t *n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AMR_B300_H */

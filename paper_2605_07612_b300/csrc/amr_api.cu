@@ -1,0 +1,750 @@
+// C ABI of the B300 block-AMR library (declared in include/amr.h).
+// Host orchestration only: every arithmetic step of the hot path runs in the
+// kernels of ghost.cuh, stage.cuh and misc.cuh.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/amr.h"
+#include "common.cuh"
+#include "forest.hpp"
+#include "ghost.cuh"
+#include "misc.cuh"
+#include "pattern.hpp"
+#include "stage.cuh"
+
+using namespace amrb;
+
+namespace {
+
+struct DBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+};
+
+}  // namespace
+
+struct amr_forest {
+    amr_config cfg{};
+    Forest forest;
+    Pattern pat;
+    uint64_t pattern_rev = ~0ull;
+    Geom geom{};
+    int esize = 8;
+    size_t block_bytes = 0;
+    void *state = nullptr;
+    DBuf r1, r2, info, fix, fix_start, bflux, bcdata, sc, partial, sums, flags, ops, level;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    uint64_t graph_rev = ~0ull;
+    int64_t graph_nodes = 0;
+    bool capturing = false;
+    int64_t launches = 0;
+    std::string err;
+};
+
+namespace {
+
+amr_status fail(amr_forest *f, amr_status s, const char *fmt, ...) {
+    if (f) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        f->err = buf;
+    }
+    return s;
+}
+
+#define CU(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) return fail(f, AMR_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+void *dev_alloc(amr_forest *f, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (f->cfg.dev_alloc) return f->cfg.dev_alloc(bytes, f->cfg.alloc_ctx);
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void dev_free(amr_forest *f, void *p) {
+    if (!p) return;
+    if (f->cfg.dev_free) f->cfg.dev_free(p, f->cfg.alloc_ctx);
+    else cudaFree(p);
+}
+
+amr_status ensure(amr_forest *f, DBuf &b, size_t bytes) {
+    if (b.cap >= bytes && b.p) return AMR_OK;
+    size_t want = std::max<size_t>(bytes + bytes / 4, 256);
+    void *p = dev_alloc(f, want);
+    if (!p) return fail(f, AMR_ENOMEM, "device allocation of %zu bytes failed", want);
+    dev_free(f, b.p);
+    b.p = p;
+    b.cap = want;
+    f->graph_rev = ~0ull;   // pointers moved: a captured graph is stale
+    return AMR_OK;
+}
+
+template <class T>
+amr_status upload(amr_forest *f, DBuf &b, const std::vector<T> &v) {
+    amr_status s = ensure(f, b, sizeof(T) * std::max<size_t>(v.size(), 1));
+    if (s != AMR_OK) return s;
+    if (!v.empty()) CU(cudaMemcpy(b.p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+    return AMR_OK;
+}
+
+int64_t nblocks(const amr_forest *f) { return int64_t(f->forest.leaves.size()); }
+
+void *slot_ptr(const amr_forest *f, int s) { return static_cast<char *>(f->state) + size_t(s) * f->cfg.max_blocks * f->block_bytes; }
+
+void fill_geom(amr_forest *f) {
+    const amr_config &c = f->cfg;
+    Geom &g = f->geom;
+    g.N = c.block_n;
+    g.ng = c.n_ghost;
+    g.S = c.block_n + 2 * c.n_ghost;
+    g.D = c.ndim;
+    g.V = c.n_var;
+    g.ncell = 1;
+    for (int d = 0; d < c.ndim; ++d) g.ncell *= g.S;
+    g.bstride = g.ncell * g.V;
+    for (int l = 0; l < kMaxLevels; ++l)
+        for (int d = 0; d < 3; ++d) {
+            // same evaluation order as a plain len / ntrees / (N 2^l)
+            const double dx = c.len[d] / double(c.ntrees[d]) / (double(c.block_n) * double(1ll << l));
+            g.dx[l][d] = dx;
+            g.inv_dx[l][d] = 1.0 / dx;
+        }
+}
+
+amr_status validate(const amr_config *c, std::string &why) {
+    char b[256];
+    auto bad = [&](const char *m) { why = m; return AMR_EINVAL; };
+    if (c->ndim != 2 && c->ndim != 3) return bad("ndim must be 2 or 3");
+    if (c->block_n != 8 && c->block_n != 16 && c->block_n != 32) return bad("block_n must be 8, 16 or 32");
+    if (c->n_ghost < 1 || c->n_ghost > 4) return bad("n_ghost must be 1..4");
+    if (c->block_n < 2 * c->n_ghost) return bad("block_n must be >= 2 n_ghost");
+    if (c->n_var != c->ndim + 2) return bad("n_var must be ndim + 2 (Euler)");
+    if (c->max_level < 0 || c->max_level >= kMaxLevels) return bad("max_level must be 0..12");
+    if (c->max_blocks < 1 || c->n_states < 1) return bad("max_blocks and n_states must be >= 1");
+    if (c->precision != 32 && c->precision != 64) return bad("precision must be 32 or 64");
+    if (!(c->gamma > 1.0) || !(c->cfl > 0.0)) return bad("gamma must be > 1 and cfl > 0");
+    for (int d = 0; d < c->ndim; ++d) {
+        if (c->ntrees[d] < 1 || (int64_t(c->ntrees[d]) << c->max_level) >= (1 << 19)) return bad("ntrees x 2^max_level must be < 2^19");
+        if (!(c->len[d] > 0.0)) return bad("len must be > 0");
+        for (int s = 0; s < 2; ++s) {
+            int t = c->bc[2 * d + s];
+            if (!c->periodic[d] && (t < 1 || t > 3)) {
+                snprintf(b, sizeof b, "face %d of a non-periodic dimension needs a Dirichlet/Neumann/data boundary", 2 * d + s);
+                why = b;
+                return AMR_EINVAL;
+            }
+        }
+    }
+    return AMR_OK;
+}
+
+// ------------------------------------------------------------ pattern upload
+amr_status upload_pattern(amr_forest *f) {
+    if (f->pattern_rev == f->forest.revision) return AMR_OK;
+    std::string why;
+    if (!build_pattern(f->forest, f->pat, why)) return fail(f, AMR_ESTATE, "%s", why.c_str());
+    if (f->cfg.host_only) {
+        f->pattern_rev = f->forest.revision;
+        return AMR_OK;
+    }
+    amr_status s;
+    if ((s = upload(f, f->r1, f->pat.round1)) != AMR_OK) return s;
+    if ((s = upload(f, f->r2, f->pat.round2)) != AMR_OK) return s;
+    if ((s = upload(f, f->info, f->pat.info)) != AMR_OK) return s;
+    if ((s = upload(f, f->fix, f->pat.fix)) != AMR_OK) return s;
+    if ((s = upload(f, f->fix_start, f->pat.fix_start)) != AMR_OK) return s;
+    std::vector<int32_t> lev(f->forest.leaves.size());
+    for (size_t b = 0; b < lev.size(); ++b) lev[b] = f->forest.leaves[b].lev;
+    if ((s = upload(f, f->level, lev)) != AMR_OK) return s;
+    const size_t nface = f->cfg.ndim == 3 ? size_t(f->cfg.block_n) * f->cfg.block_n : size_t(f->cfg.block_n);
+    if ((s = ensure(f, f->bflux, size_t(std::max(f->pat.n_slots, 1)) * f->cfg.n_var * nface * f->esize)) != AMR_OK) return s;
+    if ((s = ensure(f, f->bcdata, size_t(std::max(f->pat.n_bc, 1)) * f->cfg.n_var * nface * f->esize)) != AMR_OK) return s;
+    f->pattern_rev = f->forest.revision;
+    return AMR_OK;
+}
+
+// ------------------------------------------------------------------ launches
+template <class real, int D>
+amr_status launch_ghosts(amr_forest *f, int s, cudaStream_t st) {
+    GhostArgs<real> a{};
+    a.u = static_cast<real *>(slot_ptr(f, s));
+    a.bcdata = static_cast<const real *>(f->bcdata.p);
+    a.level = static_cast<const int32_t *>(f->level.p);
+    for (int q = 0; q < 6; ++q) {
+        a.bc_type[q] = f->cfg.bc[q];
+        for (int v = 0; v < 8; ++v) a.bc_val[q][v] = real(f->cfg.bc_val[q][v]);
+    }
+    for (int round = 0; round < 2; ++round) {
+        const auto &lst = round == 0 ? f->pat.round1 : f->pat.round2;
+        if (lst.empty()) continue;
+        a.list = static_cast<const Entry *>(round == 0 ? f->r1.p : f->r2.p);
+        a.n = int(lst.size());
+        const int grid = (a.n + 7) / 8;
+        k_ghost<real, D><<<grid, 256, 0, st>>>(a, f->geom);
+        ++f->launches;
+    }
+    CU(cudaGetLastError());
+    return AMR_OK;
+}
+
+template <class real, int D, int N, int NG>
+amr_status launch_stage_t(amr_forest *f, const StageArgs<real> &a, cudaStream_t st) {
+    constexpr int T = N < 16 ? N : 16;
+    using Sh = StageShape<real, D, N, NG, T>;
+    static bool attr_done = false;
+    const size_t smem = Sh::smem_bytes();
+    if (!attr_done) {
+        CU(cudaFuncSetAttribute(k_stage<real, D, N, NG, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        attr_done = true;
+    }
+    const int64_t grid = nblocks(f) * Sh::TILES;
+    if (grid > 0) {
+        k_stage<real, D, N, NG, T><<<unsigned(grid), Sh::NT, smem, st>>>(a, f->geom);
+        ++f->launches;
+    }
+    CU(cudaGetLastError());
+    return AMR_OK;
+}
+
+template <class real, int D>
+amr_status launch_stage(amr_forest *f, const StageArgs<real> &a, cudaStream_t st) {
+    const int N = f->cfg.block_n, NG = f->cfg.n_ghost;
+#define AMR_STAGE_CASE(n_, g_) \
+    if (N == n_ && NG == g_) return launch_stage_t<real, D, n_, g_>(f, a, st);
+    AMR_STAGE_CASE(8, 2)
+    AMR_STAGE_CASE(16, 2)
+    AMR_STAGE_CASE(32, 2)
+    AMR_STAGE_CASE(8, 3)
+    AMR_STAGE_CASE(16, 3)
+    AMR_STAGE_CASE(32, 3)
+#undef AMR_STAGE_CASE
+    return fail(f, AMR_EINVAL, "the Euler stage needs n_ghost 2 or 3 (got %d)", NG);
+}
+
+template <class real, int D>
+amr_status run_stage(amr_forest *f, const amr_stage *stg, cudaStream_t st) {
+    StageArgs<real> a{};
+    a.out = static_cast<real *>(slot_ptr(f, stg->s_out));
+    a.deriv = static_cast<const real *>(slot_ptr(f, stg->s_deriv));
+    a.nprev = stg->n_prev;
+    for (int q = 0; q < stg->n_prev; ++q) {
+        a.prev[q] = static_cast<const real *>(slot_ptr(f, stg->s_prev[q]));
+        a.wprev[q] = real(stg->w_prev[q]);
+    }
+    a.w_dt = stg->w_dt;
+    a.sc_in = static_cast<const DevScalars *>(f->sc.p);
+    a.sc = static_cast<DevScalars *>(f->sc.p);
+    a.info = static_cast<const BlockInfo *>(f->info.p);
+    a.bflux = static_cast<real *>(f->bflux.p);
+    a.update_dt = stg->update_dt;
+    a.gamma = real(f->cfg.gamma);
+    amr_status s = launch_stage<real, D>(f, a, st);
+    if (s != AMR_OK) return s;
+    const int nfix = int(f->pat.fix_start.size()) - 1;
+    if (nfix > 0) {
+        FixArgs<real> x{};
+        x.u = a.out;
+        x.info = a.info;
+        x.fix = static_cast<const FixFace *>(f->fix.p);
+        x.fix_start = static_cast<const int32_t *>(f->fix_start.p);
+        x.bflux = a.bflux;
+        x.w_dt = stg->w_dt;
+        x.sc = a.sc;
+        x.update_dt = stg->update_dt;
+        x.gamma = a.gamma;
+        const int nface = D == 3 ? f->cfg.block_n * f->cfg.block_n : f->cfg.block_n;
+        k_fluxfix<real, D><<<nfix, std::max(32, std::min(nface, 1024)), 0, st>>>(x, f->geom);
+        ++f->launches;
+    }
+    if (stg->update_dt) {
+        k_dt_commit<<<1, 32, 0, st>>>(static_cast<DevScalars *>(f->sc.p), f->cfg.cfl);
+        ++f->launches;
+    }
+    CU(cudaGetLastError());
+    return AMR_OK;
+}
+
+// dispatch on precision and dimension
+template <template <class, int> class Fn, class... Args>
+amr_status dispatch(amr_forest *f, Args &&...args) {
+    if (f->cfg.precision == 64) {
+        if (f->cfg.ndim == 3) return Fn<double, 3>::run(f, args...);
+        return Fn<double, 2>::run(f, args...);
+    }
+    if (f->cfg.ndim == 3) return Fn<float, 3>::run(f, args...);
+    return Fn<float, 2>::run(f, args...);
+}
+
+template <class real, int D>
+struct GhostFn {
+    static amr_status run(amr_forest *f, int s, cudaStream_t st) { return launch_ghosts<real, D>(f, s, st); }
+};
+template <class real, int D>
+struct StageFn {
+    static amr_status run(amr_forest *f, const amr_stage *stg, cudaStream_t st) { return run_stage<real, D>(f, stg, st); }
+};
+template <class real, int D>
+struct MaxSpeedFn {
+    static amr_status run(amr_forest *f, int s, cudaStream_t st) {
+        if (nblocks(f) > 0) {
+            k_maxspeed<real, D><<<unsigned(nblocks(f)), 256, 0, st>>>(static_cast<const real *>(slot_ptr(f, s)),
+                                                                     static_cast<const BlockInfo *>(f->info.p),
+                                                                     static_cast<DevScalars *>(f->sc.p), f->geom, real(f->cfg.gamma));
+            ++f->launches;
+        }
+        k_dt_commit<<<1, 32, 0, st>>>(static_cast<DevScalars *>(f->sc.p), f->cfg.cfl);
+        ++f->launches;
+        CU(cudaGetLastError());
+        return AMR_OK;
+    }
+};
+template <class real, int D>
+struct ConservedFn {
+    static amr_status run(amr_forest *f, int s, cudaStream_t st) {
+        amr_status r = ensure(f, f->partial, sizeof(double) * std::max<int64_t>(nblocks(f), 1) * f->cfg.n_var);
+        if (r != AMR_OK) return r;
+        if ((r = ensure(f, f->sums, sizeof(double) * 8)) != AMR_OK) return r;
+        if (nblocks(f) > 0) {
+            k_conserved_block<real, D><<<unsigned(nblocks(f)), 256, 0, st>>>(static_cast<const real *>(slot_ptr(f, s)),
+                                                                            static_cast<const BlockInfo *>(f->info.p),
+                                                                            static_cast<double *>(f->partial.p), f->geom);
+            ++f->launches;
+        }
+        k_conserved_final<<<1, 1024, 0, st>>>(static_cast<const double *>(f->partial.p), int(nblocks(f)), f->cfg.n_var,
+                                              static_cast<double *>(f->sums.p));
+        ++f->launches;
+        CU(cudaGetLastError());
+        return AMR_OK;
+    }
+};
+template <class real, int D>
+struct FlagFn {
+    static amr_status run(amr_forest *f, int s, const amr_flag_params *p, cudaStream_t st) {
+        amr_status r = ensure(f, f->flags, std::max<int64_t>(nblocks(f), 1));
+        if (r != AMR_OK) return r;
+        if (nblocks(f) > 0) {
+            k_flags<real, D><<<unsigned(nblocks(f)), 256, 0, st>>>(static_cast<const real *>(slot_ptr(f, s)), f->geom, f->cfg.gamma,
+                                                                  p->c_refine, p->c_derefine, p->eps, p->eps_abs,
+                                                                  static_cast<int8_t *>(f->flags.p));
+            ++f->launches;
+        }
+        CU(cudaGetLastError());
+        return AMR_OK;
+    }
+};
+template <class real, int D>
+struct TransferFn {
+    static amr_status run(amr_forest *f, const void *uold, int n_new, cudaStream_t st) {
+        if (n_new > 0) {
+            k_transfer<real, D><<<unsigned(n_new), 256, 0, st>>>(static_cast<const real *>(uold), static_cast<real *>(slot_ptr(f, 0)),
+                                                                static_cast<const TransferOp *>(f->ops.p), f->geom);
+            ++f->launches;
+        }
+        CU(cudaGetLastError());
+        return AMR_OK;
+    }
+};
+
+amr_status heun_step(amr_forest *f, cudaStream_t st) {
+    amr_stage s1{1, 0, 1, {0, 0, 0, 0}, {1.0, 0, 0, 0}, 1.0, 0};
+    amr_stage s2{0, 1, 2, {0, 1, 0, 0}, {0.5, 0.5, 0, 0}, 0.5, 1};
+    amr_status r;
+    if ((r = dispatch<GhostFn>(f, 0, st)) != AMR_OK) return r;
+    if ((r = dispatch<StageFn>(f, &s1, st)) != AMR_OK) return r;
+    if ((r = dispatch<GhostFn>(f, 1, st)) != AMR_OK) return r;
+    return dispatch<StageFn>(f, &s2, st);
+}
+
+bool valid_slot(const amr_forest *f, int s) { return s >= 0 && s < f->cfg.n_states; }
+
+#define NEED_DEVICE(f) \
+    do {               \
+        if ((f)->cfg.host_only) return fail(f, AMR_ESTATE, "host-only forest has no block data"); \
+    } while (0)
+
+}  // namespace
+
+// =================================================================== C ABI
+extern "C" {
+
+amr_status amr_create_forest(const amr_config *cfg, int init_level, amr_forest **out) {
+    if (!cfg || !out) return AMR_EINVAL;
+    *out = nullptr;
+    std::string why;
+    if (validate(cfg, why) != AMR_OK) return AMR_EINVAL;
+    if (init_level < 0 || init_level > cfg->max_level) return AMR_EINVAL;
+    amr_forest *f = new (std::nothrow) amr_forest();
+    if (!f) return AMR_ENOMEM;
+    f->cfg = *cfg;
+    f->esize = cfg->precision / 8;
+    fill_geom(f);
+    f->block_bytes = size_t(f->geom.bstride) * f->esize;
+    Geometry G;
+    G.ndim = cfg->ndim;
+    for (int d = 0; d < 3; ++d) {
+        G.ntrees[d] = d < cfg->ndim ? cfg->ntrees[d] : 1;
+        G.periodic[d] = d < cfg->ndim ? (cfg->periodic[d] ? 1 : 0) : 1;
+    }
+    G.max_level = cfg->max_level;
+    int64_t n0 = 1;
+    for (int d = 0; d < cfg->ndim; ++d) n0 *= G.extent(d, init_level);
+    if (n0 > cfg->max_blocks) {
+        delete f;
+        return AMR_ECAPACITY;
+    }
+    f->forest.init_uniform(G, init_level);
+    if (cfg->host_only) {
+        amr_status s = upload_pattern(f);
+        if (s != AMR_OK) {
+            delete f;
+            return s;
+        }
+        *out = f;
+        return AMR_OK;
+    }
+    const size_t bytes = size_t(cfg->n_states) * cfg->max_blocks * f->block_bytes;
+    f->state = dev_alloc(f, bytes);
+    amr_status s = AMR_OK;
+    if (!f->state) s = AMR_ENOMEM;
+    if (s == AMR_OK && cudaMemset(f->state, 0, bytes) != cudaSuccess) s = AMR_ECUDA;
+    if (s == AMR_OK) s = ensure(f, f->sc, sizeof(DevScalars));
+    if (s == AMR_OK && cudaMemset(f->sc.p, 0, sizeof(DevScalars)) != cudaSuccess) s = AMR_ECUDA;
+    if (s == AMR_OK) s = upload_pattern(f);
+    if (s == AMR_OK && cudaStreamCreateWithFlags(&f->cap_stream, cudaStreamNonBlocking) != cudaSuccess) s = AMR_ECUDA;
+    if (s != AMR_OK) {
+        cudaGetLastError();
+        amr_destroy_forest(f);
+        return s;
+    }
+    *out = f;
+    return AMR_OK;
+}
+
+amr_status amr_destroy_forest(amr_forest *f) {
+    if (!f) return AMR_OK;
+    if (f->gexec) cudaGraphExecDestroy(f->gexec);
+    if (f->cap_stream) cudaStreamDestroy(f->cap_stream);
+    for (DBuf *b : {&f->r1, &f->r2, &f->info, &f->fix, &f->fix_start, &f->bflux, &f->bcdata, &f->sc, &f->partial, &f->sums,
+                    &f->flags, &f->ops, &f->level})
+        dev_free(f, b->p);
+    dev_free(f, f->state);
+    delete f;
+    return AMR_OK;
+}
+
+amr_status amr_n_blocks(const amr_forest *f, int64_t *n) {
+    if (!f || !n) return AMR_EINVAL;
+    *n = nblocks(f);
+    return AMR_OK;
+}
+
+amr_status amr_get_blocks(const amr_forest *f, int32_t *level, int64_t *coords, int64_t cap, int64_t *n) {
+    if (!f || cap < 0) return AMR_EINVAL;
+    const int64_t nb = nblocks(f);
+    if (n) *n = nb;
+    for (int64_t b = 0; b < std::min(cap, nb); ++b) {
+        const Leaf &l = f->forest.leaves[size_t(b)];
+        if (level) level[b] = l.lev;
+        if (coords)
+            for (int d = 0; d < 3; ++d) coords[3 * b + d] = d < f->cfg.ndim ? l.g[d] : 0;
+    }
+    return AMR_OK;
+}
+
+amr_status amr_build_ghost_pattern(amr_forest *f) {
+    if (!f) return AMR_EINVAL;
+    return upload_pattern(f);
+}
+
+amr_status amr_get_ghost_pattern(const amr_forest *f, amr_ghost_entry *out, int64_t cap, int64_t *n) {
+    if (!f || cap < 0 || (cap > 0 && !out)) return AMR_EINVAL;
+    if (f->pattern_rev != f->forest.revision) return AMR_ESTATE;
+    const auto &e = f->pat.entries;
+    if (n) *n = int64_t(e.size());
+    for (int64_t i = 0; i < std::min<int64_t>(cap, int64_t(e.size())); ++i)
+        out[i] = {e[i].kind, e[i].face, e[i].dst, e[i].src, e[i].offset, e[i].aux};
+    return AMR_OK;
+}
+
+amr_status amr_set_state(amr_forest *f, int s, const void *src, int on_device, amr_stream stream) {
+    if (!f || !src || !valid_slot(f, s)) return AMR_EINVAL;
+    NEED_DEVICE(f);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t bytes = size_t(nblocks(f)) * f->block_bytes;
+    CU(cudaMemcpyAsync(slot_ptr(f, s), src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    if (!on_device) CU(cudaStreamSynchronize(st));
+    return AMR_OK;
+}
+
+amr_status amr_get_state(const amr_forest *fc, int s, void *dst, int on_device, amr_stream stream) {
+    amr_forest *f = const_cast<amr_forest *>(fc);
+    if (!f || !dst || !valid_slot(f, s)) return AMR_EINVAL;
+    NEED_DEVICE(f);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t bytes = size_t(nblocks(f)) * f->block_bytes;
+    CU(cudaMemcpyAsync(dst, slot_ptr(f, s), bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    if (!on_device) CU(cudaStreamSynchronize(st));
+    return AMR_OK;
+}
+
+amr_status amr_state_ptr(const amr_forest *f, int s, void **ptr) {
+    if (!f || !ptr || !valid_slot(f, s)) return AMR_EINVAL;
+    if (f->cfg.host_only) return AMR_ESTATE;
+    *ptr = slot_ptr(f, s);
+    return AMR_OK;
+}
+
+amr_status amr_set_bc_data(amr_forest *f, const double *values, int64_t n_values) {
+    if (!f || (n_values > 0 && !values)) return AMR_EINVAL;
+    NEED_DEVICE(f);
+    amr_status r = upload_pattern(f);
+    if (r != AMR_OK) return r;
+    const int64_t nface = f->cfg.ndim == 3 ? int64_t(f->cfg.block_n) * f->cfg.block_n : f->cfg.block_n;
+    const int64_t need = int64_t(f->pat.n_bc) * f->cfg.n_var * nface;
+    if (n_values != need) return fail(f, AMR_EINVAL, "bc_data needs %lld values, got %lld", (long long)need, (long long)n_values);
+    if (need == 0) return AMR_OK;
+    if (f->cfg.precision == 64) {
+        CU(cudaMemcpy(f->bcdata.p, values, sizeof(double) * need, cudaMemcpyHostToDevice));
+    } else {
+        std::vector<float> tmp(values, values + need);
+        CU(cudaMemcpy(f->bcdata.p, tmp.data(), sizeof(float) * need, cudaMemcpyHostToDevice));
+    }
+    return AMR_OK;
+}
+
+amr_status amr_fill_ghosts(amr_forest *f, int s, amr_stream stream) {
+    if (!f || !valid_slot(f, s)) return AMR_EINVAL;
+    NEED_DEVICE(f);
+    amr_status r = upload_pattern(f);
+    if (r != AMR_OK) return r;
+    return dispatch<GhostFn>(f, s, static_cast<cudaStream_t>(stream));
+}
+
+amr_status amr_compute_dt(amr_forest *f, int s, amr_stream stream) {
+    if (!f || !valid_slot(f, s)) return AMR_EINVAL;
+    NEED_DEVICE(f);
+    return dispatch<MaxSpeedFn>(f, s, static_cast<cudaStream_t>(stream));
+}
+
+amr_status amr_set_dt(amr_forest *f, double dt, amr_stream stream) {
+    if (!f || !(dt >= 0.0)) return AMR_EINVAL;
+    NEED_DEVICE(f);
+    CU(cudaMemcpyAsync(f->sc.p, &dt, sizeof(double), cudaMemcpyHostToDevice, static_cast<cudaStream_t>(stream)));
+    CU(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    return AMR_OK;
+}
+
+amr_status amr_get_dt(amr_forest *f, double *dt, amr_stream stream) {
+    if (!f || !dt) return AMR_EINVAL;
+    NEED_DEVICE(f);
+    CU(cudaMemcpyAsync(dt, f->sc.p, sizeof(double), cudaMemcpyDeviceToHost, static_cast<cudaStream_t>(stream)));
+    CU(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    return AMR_OK;
+}
+
+amr_status amr_advance_stage(amr_forest *f, const amr_stage *st, amr_stream stream) {
+    if (!f || !st) return AMR_EINVAL;
+    NEED_DEVICE(f);
+    if (!valid_slot(f, st->s_out) || !valid_slot(f, st->s_deriv) || st->n_prev < 0 || st->n_prev > 4) return AMR_EINVAL;
+    for (int q = 0; q < st->n_prev; ++q)
+        if (!valid_slot(f, st->s_prev[q])) return AMR_EINVAL;
+    if (st->s_out == st->s_deriv) return fail(f, AMR_EINVAL, "s_out must differ from s_deriv");
+    if (f->cfg.n_ghost < 2) return fail(f, AMR_EINVAL, "the Euler stage needs n_ghost >= 2");
+    amr_status r = upload_pattern(f);
+    if (r != AMR_OK) return r;
+    return dispatch<StageFn>(f, st, static_cast<cudaStream_t>(stream));
+}
+
+amr_status amr_step(amr_forest *f, int n_steps, int use_graph, amr_stream stream) {
+    if (!f || n_steps < 0) return AMR_EINVAL;
+    NEED_DEVICE(f);
+    if (f->cfg.n_states < 2) return fail(f, AMR_EINVAL, "Heun's method needs n_states >= 2");
+    if (f->cfg.n_ghost < 2) return fail(f, AMR_EINVAL, "the Euler stage needs n_ghost >= 2");
+    amr_status r = upload_pattern(f);
+    if (r != AMR_OK) return r;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (!use_graph) {
+        for (int i = 0; i < n_steps; ++i)
+            if ((r = heun_step(f, st)) != AMR_OK) return r;
+        return AMR_OK;
+    }
+    if (!f->gexec || f->graph_rev != f->forest.revision) {
+        if (f->gexec) {
+            cudaGraphExecDestroy(f->gexec);
+            f->gexec = nullptr;
+        }
+        // capture one step on the library's own stream, after the caller's
+        // stream has drained (capture needs a non-legacy stream)
+        CU(cudaStreamSynchronize(st));
+        const int64_t before = f->launches;
+        CU(cudaStreamBeginCapture(f->cap_stream, cudaStreamCaptureModeThreadLocal));
+        r = heun_step(f, f->cap_stream);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(f->cap_stream, &graph);
+        if (r != AMR_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return r;
+        }
+        if (e != cudaSuccess) return fail(f, AMR_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+        f->graph_nodes = f->launches - before;
+        f->launches = before;
+        e = cudaGraphInstantiate(&f->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return fail(f, AMR_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+        f->graph_rev = f->forest.revision;
+    }
+    for (int i = 0; i < n_steps; ++i) {
+        CU(cudaGraphLaunch(f->gexec, st));
+        f->launches += f->graph_nodes;
+    }
+    return AMR_OK;
+}
+
+amr_status amr_conserved(amr_forest *f, int s, double *sums, amr_stream stream) {
+    if (!f || !sums || !valid_slot(f, s)) return AMR_EINVAL;
+    NEED_DEVICE(f);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    amr_status r = dispatch<ConservedFn>(f, s, st);
+    if (r != AMR_OK) return r;
+    CU(cudaMemcpyAsync(sums, f->sums.p, sizeof(double) * f->cfg.n_var, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    return AMR_OK;
+}
+
+amr_status amr_flag(amr_forest *f, int s, const amr_flag_params *p, int8_t *flags_out, amr_stream stream) {
+    if (!f || !p || !flags_out || !valid_slot(f, s)) return AMR_EINVAL;
+    NEED_DEVICE(f);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    amr_status r = dispatch<FlagFn>(f, s, p, st);
+    if (r != AMR_OK) return r;
+    if (nblocks(f) > 0) CU(cudaMemcpyAsync(flags_out, f->flags.p, size_t(nblocks(f)), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    return AMR_OK;
+}
+
+amr_status amr_flag_and_regrid(amr_forest *f, const amr_flag_params *p, const int8_t *flags, int *changed, amr_stream stream) {
+    if (!f || (!flags && !p)) return AMR_EINVAL;
+    if (changed) *changed = 0;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    amr_status r = AMR_OK;
+    if (f->cfg.host_only) {
+        if (!flags) return fail(f, AMR_ESTATE, "host-only forest: regrid needs explicit flags");
+        std::vector<int8_t> fl(flags, flags + nblocks(f));
+        std::vector<Leaf> nl = f->forest.adapted(fl);
+        bool same = nl.size() == f->forest.leaves.size();
+        for (size_t i = 0; same && i < nl.size(); ++i) same = pack_key(nl[i]) == pack_key(f->forest.leaves[i]);
+        if (same) return AMR_OK;
+        if (int64_t(nl.size()) > f->cfg.max_blocks)
+            return fail(f, AMR_ECAPACITY, "regrid needs %zu blocks, capacity is %d", nl.size(), f->cfg.max_blocks);
+        f->forest.assign(std::move(nl));
+        if ((r = upload_pattern(f)) != AMR_OK) return r;
+        if (changed) *changed = 1;
+        return AMR_OK;
+    }
+    r = amr_fill_ghosts(f, 0, stream);
+    if (r != AMR_OK) return r;
+    const int64_t nb = nblocks(f);
+    std::vector<int8_t> fl(size_t(std::max<int64_t>(nb, 1)));
+    if (flags) std::copy(flags, flags + nb, fl.begin());
+    else if ((r = amr_flag(f, 0, p, fl.data(), stream)) != AMR_OK) return r;
+    fl.resize(size_t(nb));
+    std::vector<Leaf> nl = f->forest.adapted(fl);
+    bool same = nl.size() == f->forest.leaves.size();
+    for (size_t i = 0; same && i < nl.size(); ++i) same = pack_key(nl[i]) == pack_key(f->forest.leaves[i]);
+    if (same) return AMR_OK;
+    if (int64_t(nl.size()) > f->cfg.max_blocks)
+        return fail(f, AMR_ECAPACITY, "regrid needs %zu blocks, capacity is %d", nl.size(), f->cfg.max_blocks);
+    // old -> new map (Sec. 2.2: copied, refined and coarsened blocks)
+    const int D = f->cfg.ndim;
+    std::vector<TransferOp> ops(nl.size());
+    for (size_t b = 0; b < nl.size(); ++b) {
+        const Leaf &l = nl[b];
+        TransferOp op{};
+        int o = f->forest.find(l.lev, l.g[0], l.g[1], l.g[2]);
+        if (o >= 0) {
+            op.kind = 0;
+            op.src[0] = o;
+        } else if (l.lev > 0 && (o = f->forest.find(l.lev - 1, l.g[0] >> 1, l.g[1] >> 1, D == 3 ? l.g[2] >> 1 : 0)) >= 0) {
+            op.kind = 1;
+            op.src[0] = o;
+            op.pos = int(l.g[0] & 1) | int(l.g[1] & 1) << 1 | (D == 3 ? int(l.g[2] & 1) << 2 : 0);
+        } else {
+            op.kind = 2;
+            for (int c = 0; c < (1 << D); ++c) {
+                int s = f->forest.find(l.lev + 1, 2 * l.g[0] + (c & 1), 2 * l.g[1] + ((c >> 1) & 1),
+                                       D == 3 ? 2 * l.g[2] + ((c >> 2) & 1) : 0);
+                if (s < 0) return fail(f, AMR_ESTATE, "regrid: block %zu changed by more than one level", b);
+                op.src[c] = s;
+            }
+        }
+        ops[b] = op;
+    }
+    // temporary copy of the old blocks (slot 1 when available)
+    void *tmp = nullptr;
+    bool own_tmp = false;
+    const size_t old_bytes = size_t(nb) * f->block_bytes;
+    if (f->cfg.n_states >= 2) {
+        tmp = slot_ptr(f, 1);
+    } else {
+        tmp = dev_alloc(f, old_bytes);
+        if (!tmp) return fail(f, AMR_ENOMEM, "regrid: no room for the old blocks");
+        own_tmp = true;
+    }
+    if ((r = upload(f, f->ops, ops)) != AMR_OK) return r;
+    CU(cudaMemcpyAsync(tmp, slot_ptr(f, 0), old_bytes, cudaMemcpyDeviceToDevice, st));
+    r = dispatch<TransferFn>(f, static_cast<const void *>(tmp), int(nl.size()), st);
+    if (own_tmp) {
+        cudaStreamSynchronize(st);
+        dev_free(f, tmp);
+    }
+    if (r != AMR_OK) return r;
+    f->forest.assign(std::move(nl));
+    if ((r = upload_pattern(f)) != AMR_OK) return r;
+    CU(cudaStreamSynchronize(st));
+    if (changed) *changed = 1;
+    return AMR_OK;
+}
+
+amr_status amr_sync_status(amr_forest *f, amr_stream stream) {
+    if (!f) return AMR_EINVAL;
+    NEED_DEVICE(f);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    DevScalars h{};
+    CU(cudaMemcpyAsync(&h, f->sc.p, sizeof h, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    if (h.status != 0) {
+        const int zero = 0;
+        CU(cudaMemcpy(static_cast<char *>(f->sc.p) + offsetof(DevScalars, status), &zero, sizeof zero, cudaMemcpyHostToDevice));
+        return fail(f, amr_status(h.status), "device reported status %d", h.status);
+    }
+    return AMR_OK;
+}
+
+const char *amr_last_error(const amr_forest *f) { return f ? f->err.c_str() : "null forest"; }
+
+amr_status amr_launch_count(const amr_forest *f, int64_t *n) {
+    if (!f || !n) return AMR_EINVAL;
+    *n = f->launches;
+    return AMR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,61 @@
+// Shared device definitions of the B300 block-AMR kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "pattern.hpp"
+
+namespace amrb {
+
+constexpr int kMaxLevels = 13;
+
+// Rounded operations that the compiler may not contract into an FMA; used
+// where a result must match a plain IEEE evaluation order bit for bit.
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+
+// minmod of Eq. 1 with theta = 1: zero unless both slopes have the same
+// strict sign, else the one of smaller magnitude.
+template <class T>
+__device__ __forceinline__ T minmod(T a, T b) {
+    T lo = a < b ? a : b, hi = a < b ? b : a;
+    return (a > T(0) && b > T(0)) ? lo : ((a < T(0) && b < T(0)) ? hi : T(0));
+}
+
+// Geometry of one forest as seen by the kernels.
+struct Geom {
+    int N, ng, S, D, V;
+    int64_t ncell;          // S^D
+    int64_t bstride;        // V * ncell
+    double dx[kMaxLevels][3];
+    double inv_dx[kMaxLevels][3];
+};
+
+// Device-resident scalars of a forest.
+struct DevScalars {
+    double dt;
+    unsigned long long maxspeed_bits;   // max of a non-negative double, as bits
+    int status;                         // first device-side error (amr_status)
+    int pad;
+};
+
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long *p, double v) {
+    atomicMax(p, (unsigned long long)__double_as_longlong(v));
+}
+
+__device__ __forceinline__ void raise_status(int *p, int code) { atomicCAS(p, 0, code); }
+
+// Offset of cell (i, j, k) inside one variable of a block (ghosts included,
+// i fastest); k is ignored in 2D.
+template <class real>
+__device__ __forceinline__ int64_t cell_index(const Geom &g, int i, int j, int k) {
+    const int64_t kk = (g.D == 3) ? int64_t(k + g.ng) * g.S : int64_t(0);
+    return (kk + (j + g.ng)) * g.S + (i + g.ng);
+}
+
+}  // namespace amrb

@@ -1,0 +1,135 @@
+// Ghost-pattern executor (Sec. 2.5).  One warp per pattern entry ("strip");
+// the lanes walk the strip's ghost cells with x fastest so that both the
+// gather and the scatter are coalesced along rows.  Round 1 executes SRL,
+// F2C and BC entries (they read interior cells only); round 2 executes C2F
+// entries, whose limited prolongation reads round-1 ghosts of the coarse
+// block (the tangential neighbours at the face edge and the ghost layer
+// facing the fine block).  Only face ghost cells are written (Sec. 2.1).
+#pragma once
+
+#include "common.cuh"
+
+namespace amrb {
+
+template <class real>
+struct GhostArgs {
+    real *u;                 // state slot, max_blocks blocks
+    const Entry *list;
+    int n;
+    const real *bcdata;      // [n_bc][V][N^(D-1)]
+    int bc_type[6];
+    real bc_val[6][8];
+    const int32_t *level;    // per block (BlockInfo would do; a plain array keeps loads small)
+};
+
+// Restriction (Sec. 2.2): mean of the 2^D fine cells starting at fine index
+// (fi, fj, fk), summed x-pairs, then y-pairs, then z-pairs, then scaled.
+template <class real, int D>
+__device__ __forceinline__ real restrict_at(const real *fb, const Geom &g, int fi, int fj, int fk) {
+    const int S = g.S;
+    const real *p = fb + cell_index<real>(g, fi, fj, fk);
+    real s00 = p[0] + p[1];
+    real s10 = p[S] + p[S + 1];
+    real s0 = s00 + s10;
+    if (D == 3) {
+        const real *q = p + int64_t(S) * S;
+        real s01 = q[0] + q[1];
+        real s11 = q[S] + q[S + 1];
+        real s1 = s01 + s11;
+        return (s0 + s1) * real(0.125);
+    }
+    return s0 * real(0.25);
+}
+
+// Limited prolongation (Sec. 2.2, Eq. 1 with theta = 1): the fine value at
+// sub-position sub_d (0 lower, 1 upper half) of coarse cell (ci, cj, ck) is
+// u_c + sum_d (+-1/4) minmod(u_c - u_{c-e_d}, u_{c+e_d} - u_c), the
+// corrections summed left to right before being added to u_c.
+template <class real, int D>
+__device__ __forceinline__ real prolong_at(const real *cb, const Geom &g, int ci, int cj, int ck, int si, int sj, int sk) {
+    const int64_t S = g.S;
+    const real *p = cb + cell_index<real>(g, ci, cj, ck);
+    const real uc = p[0];
+    real t = (si ? real(0.25) : real(-0.25)) * minmod<real>(uc - p[-1], p[1] - uc);
+    t = t + (sj ? real(0.25) : real(-0.25)) * minmod<real>(uc - p[-S], p[S] - uc);
+    if (D == 3) t = t + (sk ? real(0.25) : real(-0.25)) * minmod<real>(uc - p[-S * S], p[S * S] - uc);
+    return uc + t;
+}
+
+template <class real, int D>
+__global__ void __launch_bounds__(256) k_ghost(GhostArgs<real> a, Geom g) {
+    const int warp = int((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (warp >= a.n) return;
+    const Entry e = a.list[warp];
+    const int N = g.N, ng = g.ng;
+    const int nd = e.face >> 1, side = e.face & 1;
+    // ghost box of this strip in dst-local coordinates
+    int lo[3] = {0, 0, 0}, ext[3] = {N, N, D == 3 ? N : 1};
+    lo[nd] = side ? N : -ng;
+    ext[nd] = ng;
+    int tdim[2] = {-1, -1};
+    for (int d = 0, c = 0; d < D; ++d)
+        if (d != nd) tdim[c++] = d;
+    int off[3] = {0, 0, 0};   // tangential position of the fine block (F2C/C2F)
+    off[tdim[0]] = e.offset & 1;
+    if (D == 3) off[tdim[1]] = (e.offset >> 1) & 1;
+    if (e.kind == KIND_F2C) {
+        for (int c = 0; c < D - 1; ++c) {
+            lo[tdim[c]] = off[tdim[c]] * (N / 2);
+            ext[tdim[c]] = N / 2;
+        }
+    }
+    const int ncells = ext[0] * ext[1] * ext[2];
+    const int total = ncells * g.V;
+    real *dstb = a.u + int64_t(e.dst) * g.bstride;
+    const real *srcb = e.src >= 0 ? a.u + int64_t(e.src) * g.bstride : nullptr;
+    for (int idx = lane; idx < total; idx += 32) {
+        int v = idx / ncells, c = idx - v * ncells;
+        int x[3];
+        x[0] = lo[0] + c % ext[0];
+        c /= ext[0];
+        x[1] = lo[1] + c % ext[1];
+        x[2] = (D == 3) ? lo[2] + c / ext[1] : 0;
+        real val;
+        if (e.kind == KIND_SRL) {
+            int y[3] = {x[0], x[1], x[2]};
+            y[nd] += side ? -N : N;
+            val = srcb[int64_t(v) * g.ncell + cell_index<real>(g, y[0], y[1], y[2])];
+        } else if (e.kind == KIND_F2C) {
+            int y[3] = {0, 0, 0};
+            for (int d = 0; d < D; ++d) y[d] = 2 * x[d] - off[d] * N;
+            y[nd] = side ? 2 * (x[nd] - N) : 2 * x[nd] + N;
+            val = restrict_at<real, D>(srcb + int64_t(v) * g.ncell, g, y[0], y[1], y[2]);
+        } else if (e.kind == KIND_C2F) {
+            int y[3] = {0, 0, 0}, s[3] = {0, 0, 0};
+            for (int d = 0; d < D; ++d) {
+                y[d] = off[d] * (N / 2) + (x[d] >> 1);
+                s[d] = x[d] & 1;
+            }
+            const int xn = side ? x[nd] - N : x[nd];
+            y[nd] = side ? (xn >> 1) : N + (xn >> 1);
+            s[nd] = xn & 1;
+            val = prolong_at<real, D>(srcb + int64_t(v) * g.ncell, g, y[0], y[1], y[2], s[0], s[1], s[2]);
+        } else {  // physical boundary (Sec. 2.4)
+            const int k = side ? x[nd] - N + 1 : -x[nd];          // layer 1..ng
+            int y[3] = {x[0], x[1], x[2]};
+            y[nd] = side ? N - k : k - 1;                          // mirror cell
+            const real um = dstb[int64_t(v) * g.ncell + cell_index<real>(g, y[0], y[1], y[2])];
+            const int ty = a.bc_type[e.face];
+            if (ty == 1) {
+                val = real(2) * a.bc_val[e.face][v] - um;
+            } else if (ty == 2) {
+                const real h = mul_rn(real(2 * k - 1), real(g.dx[a.level[e.dst]][nd]));
+                val = add_rn(um, mul_rn(h, a.bc_val[e.face][v]));
+            } else {
+                const int t = x[tdim[0]] + (D == 3 ? N * x[tdim[1]] : 0);
+                const int64_t nface = (D == 3) ? int64_t(N) * N : N;
+                val = real(2) * a.bcdata[(int64_t(e.aux) * g.V + v) * nface + t] - um;
+            }
+        }
+        dstb[int64_t(v) * g.ncell + cell_index<real>(g, x[0], x[1], x[2])] = val;
+    }
+}
+
+}  // namespace amrb

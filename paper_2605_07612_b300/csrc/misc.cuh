@@ -1,0 +1,304 @@
+// Kernels around the stage: flux fixing (Sec. 2.6), the CFL time step
+// (Sec. 3.2), conserved integrals (Eq. 12), the refinement criterion of
+// Eq. 5 (Sec. 3.3) and the data transfer after a mesh change (Sec. 2.2).
+#pragma once
+
+#include "common.cuh"
+#include "ghost.cuh"
+
+namespace amrb {
+
+// ---------------------------------------------------------------- flux fix
+// One CTA per coarse block with refinement faces; its faces are processed in
+// face order (-x, +x, -y, +y, -z, +z) with a barrier in between, so a cell on
+// two such faces receives both corrections in a fixed order.  The correction
+// of coarse cell c next to face f is
+//   u_c += sign(f) * (w_dt dt / dx_n) * (F_coarse - mean of the fine fluxes)
+// with sign +1 on high faces and -1 on low faces; the fine mean sums pairs
+// along the lower tangential dimension first.
+template <class real>
+struct FixArgs {
+    real *u;
+    const BlockInfo *info;
+    const FixFace *fix;
+    const int32_t *fix_start;
+    const real *bflux;
+    double w_dt;
+    DevScalars *sc;
+    int update_dt;
+    real gamma;
+};
+
+template <class real, int D>
+__global__ void k_fluxfix(FixArgs<real> a, Geom g) {
+    const int N = g.N, V = g.V;
+    const int nface = (D == 3) ? N * N : N;
+    const int first = a.fix_start[blockIdx.x], last = a.fix_start[blockIdx.x + 1];
+    const int b = a.fix[first].block;
+    const int lev = a.info[b].level;
+    const real dt_eff = real(a.w_dt * a.sc->dt);
+    real *ub = a.u + int64_t(b) * g.bstride;
+    real vmax = real(0);
+    for (int q = first; q < last; ++q) {
+        const FixFace ff = a.fix[q];
+        const int n = ff.face >> 1, side = ff.face & 1;
+        int td[2] = {-1, -1};
+        for (int d = 0, c = 0; d < D; ++d)
+            if (d != n) td[c++] = d;
+        const real coef = dt_eff * real(g.inv_dx[lev][n]);
+        for (int t = threadIdx.x; t < nface; t += blockDim.x) {
+            const int t0 = t % N, t1 = (D == 3) ? t / N : 0;
+            const int o0 = t0 >= N / 2, o1 = (D == 3) ? (t1 >= N / 2) : 0;
+            const int slot = ff.fslot[o0 | (o1 << 1)];
+            const int f0 = 2 * (t0 - o0 * (N / 2)), f1 = 2 * (t1 - o1 * (N / 2));
+            int x[3] = {0, 0, 0};
+            x[n] = side ? N - 1 : 0;
+            x[td[0]] = t0;
+            if (D == 3) x[td[1]] = t1;
+            const int64_t cell = cell_index<real>(g, x[0], x[1], x[2]);
+            real U[5];
+            for (int v = 0; v < V; ++v) {
+                const real *fb = a.bflux + (int64_t(slot) * V + v) * nface;
+                real mean;
+                if (D == 3) {
+                    mean = ((fb[f0 + N * f1] + fb[f0 + 1 + N * f1]) + (fb[f0 + N * (f1 + 1)] + fb[f0 + 1 + N * (f1 + 1)])) *
+                           real(0.25);
+                } else {
+                    mean = (fb[f0] + fb[f0 + 1]) * real(0.5);
+                }
+                const real Fc = a.bflux[(int64_t(ff.cslot) * V + v) * nface + t];
+                const real corr = coef * (Fc - mean);
+                real &u = ub[int64_t(v) * g.ncell + cell];
+                u = side ? u + corr : u - corr;
+                U[v] = u;
+            }
+            (void)U;
+        }
+        __syncthreads();
+    }
+    if (!a.update_dt) return;
+    // CFL limit of every corrected cell (cells on two faces count twice)
+    for (int q = first; q < last; ++q) {
+        const FixFace ff = a.fix[q];
+        const int n = ff.face >> 1, side = ff.face & 1;
+        int td[2] = {-1, -1};
+        for (int d = 0, c = 0; d < D; ++d)
+            if (d != n) td[c++] = d;
+        for (int t = threadIdx.x; t < nface; t += blockDim.x) {
+            int x[3] = {0, 0, 0};
+            x[n] = side ? N - 1 : 0;
+            x[td[0]] = t % N;
+            if (D == 3) x[td[1]] = t / N;
+            const int64_t cell = cell_index<real>(g, x[0], x[1], x[2]);
+            real U[5];
+            for (int v = 0; v < V; ++v) U[v] = ub[int64_t(v) * g.ncell + cell];
+            const real rho = U[0], ir = real(1) / rho;
+            real ke = real(0);
+            for (int d = 0; d < D; ++d) ke += U[1 + d] * U[1 + d] * ir;
+            const real p = (a.gamma - real(1)) * (U[D + 1] - real(0.5) * ke);
+            const real c = sqrt(a.gamma * p / rho);
+            real s = real(0);
+            for (int d = 0; d < D; ++d) s += (fabs(U[1 + d] * ir) + c) * real(g.inv_dx[lev][d]);
+            vmax = s > vmax ? s : vmax;
+        }
+    }
+    double m = double(vmax);
+    for (int s = 16; s > 0; s >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, s));
+    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(&a.sc->maxspeed_bits, m);
+}
+
+// ------------------------------------------------------------------- CFL dt
+// max over interior cells of sum_d (|v_d| + c) / dx_d (Sec. 3.2 step 2c)
+template <class real, int D>
+__global__ void k_maxspeed(const real *u, const BlockInfo *info, DevScalars *sc, Geom g, real gam) {
+    const int b = blockIdx.x;
+    const int N = g.N;
+    const int ncell = (D == 3) ? N * N * N : N * N;
+    const int lev = info[b].level;
+    const real *ub = u + int64_t(b) * g.bstride;
+    real vmax = real(0);
+    for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+        const int i = c % N, j = (c / N) % N, k = (D == 3) ? c / (N * N) : 0;
+        const int64_t cell = cell_index<real>(g, i, j, k);
+        real U[5];
+        for (int v = 0; v < g.V; ++v) U[v] = ub[int64_t(v) * g.ncell + cell];
+        const real rho = U[0], ir = real(1) / rho;
+        real ke = real(0);
+        for (int d = 0; d < D; ++d) ke += U[1 + d] * U[1 + d] * ir;
+        const real p = (gam - real(1)) * (U[D + 1] - real(0.5) * ke);
+        const real cs = sqrt(gam * p / rho);
+        real s = real(0);
+        for (int d = 0; d < D; ++d) s += (fabs(U[1 + d] * ir) + cs) * real(g.inv_dx[lev][d]);
+        vmax = s > vmax ? s : vmax;
+    }
+    double m = double(vmax);
+    for (int s = 16; s > 0; s >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, s));
+    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(&sc->maxspeed_bits, m);
+}
+
+// dt = cfl / max speed; resets the accumulator for the next reduction
+__global__ void k_dt_commit(DevScalars *sc, double cfl) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        const double m = __longlong_as_double((long long)sc->maxspeed_bits);
+        sc->dt = (m > 0.0) ? cfl / m : 0.0;
+        sc->maxspeed_bits = 0ull;
+    }
+}
+
+// --------------------------------------------------------- conserved sums
+// Per block and variable: sum of u over interior cells in a fixed order
+// (a fixed cell -> thread map, then a fixed shared-memory tree), times the
+// cell volume.  Then k_conserved_final sums blocks in a fixed tree order.
+template <class real, int D>
+__global__ void __launch_bounds__(256) k_conserved_block(const real *u, const BlockInfo *info, double *partial, Geom g) {
+    __shared__ double red[256];
+    const int b = blockIdx.x;
+    const int N = g.N;
+    const int ncell = (D == 3) ? N * N * N : N * N;
+    const int lev = info[b].level;
+    double vol = 1.0;
+    for (int d = 0; d < D; ++d) vol *= g.dx[lev][d];
+    for (int v = 0; v < g.V; ++v) {
+        const real *ub = u + int64_t(b) * g.bstride + int64_t(v) * g.ncell;
+        double s = 0.0;
+        for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+            const int i = c % N, j = (c / N) % N, k = (D == 3) ? c / (N * N) : 0;
+            s += double(ub[cell_index<real>(g, i, j, k)]);
+        }
+        red[threadIdx.x] = s;
+        __syncthreads();
+        for (int w = 128; w > 0; w >>= 1) {
+            if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) partial[int64_t(b) * g.V + v] = red[0] * vol;
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_conserved_final(const double *partial, int nb, int V, double *out) {
+    __shared__ double red[1024];
+    for (int v = 0; v < V; ++v) {
+        double s = 0.0;
+        for (int b = threadIdx.x; b < nb; b += blockDim.x) s += partial[int64_t(b) * V + v];
+        red[threadIdx.x] = s;
+        __syncthreads();
+        for (int w = 512; w > 0; w >>= 1) {
+            if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[v] = red[0];
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------- flags
+// Simplified Lohner estimator (Eq. 5) on density and pressure, evaluated in
+// double with every operation rounded as written (no contraction), so that
+// the flag decision is the same as a plain double evaluation of the formula
+// on the same stored values.  Per block: +1 if some cell exceeds c_ref, -1 if
+// every cell is below c_deref, else 0.
+template <class real, int D>
+__device__ __forceinline__ void dprim_rn(const real *ub, const Geom &g, int64_t cell, double gam, double &rho, double &p) {
+    double U[5];
+    for (int v = 0; v < g.V; ++v) U[v] = double(ub[int64_t(v) * g.ncell + cell]);
+    rho = U[0];
+    double ke = 0.0;
+    for (int d = 0; d < D; ++d) {
+        const double w = __ddiv_rn(U[1 + d], rho);
+        ke = __dadd_rn(ke, __dmul_rn(w, w));
+    }
+    ke = __dmul_rn(__dmul_rn(0.5, rho), ke);
+    p = __dmul_rn(gam - 1.0, __dsub_rn(U[D + 1], ke));
+}
+
+__device__ __forceinline__ double lohner_1d(double um, double u0, double up, double eps, double eps_abs) {
+    const double num = fabs(__dadd_rn(__dsub_rn(um, __dmul_rn(2.0, u0)), up));
+    const double ustar = __dadd_rn(__dadd_rn(fabs(um), __dmul_rn(2.0, fabs(u0))), fabs(up));
+    double den = __dadd_rn(eps_abs, fabs(__dsub_rn(u0, um)));
+    den = __dadd_rn(den, fabs(__dsub_rn(up, u0)));
+    den = __dadd_rn(den, __dmul_rn(eps, ustar));
+    return __ddiv_rn(num, den);
+}
+
+template <class real, int D>
+__global__ void __launch_bounds__(256) k_flags(const real *u, Geom g, double gam, double c_ref, double c_deref, double eps,
+                                               double eps_abs, int8_t *flags) {
+    const int b = blockIdx.x;
+    const int N = g.N;
+    const int ncell = (D == 3) ? N * N * N : N * N;
+    const real *ub = u + int64_t(b) * g.bstride;
+    int any_ref = 0, all_deref = 1;
+    for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+        const int x[3] = {c % N, (c / N) % N, (D == 3) ? c / (N * N) : 0};
+        double r[3][3], pp[3][3];
+        for (int n = 0; n < D; ++n)
+            for (int q = -1; q <= 1; ++q) {
+                int y[3] = {x[0], x[1], x[2]};
+                y[n] += q;
+                dprim_rn<real, D>(ub, g, cell_index<real>(g, y[0], y[1], y[2]), gam, r[n][q + 1], pp[n][q + 1]);
+            }
+        double cellmax = 0.0;
+        for (int which = 0; which < 2; ++which) {
+            double e2 = 0.0;
+            for (int n = 0; n < D; ++n) {
+                const double *val = which == 0 ? r[n] : pp[n];
+                const double e = lohner_1d(val[0], val[1], val[2], eps, eps_abs);
+                e2 = __dadd_rn(e2, __dmul_rn(e, e));
+            }
+            const double E = __dsqrt_rn(e2);
+            cellmax = E > cellmax ? E : cellmax;
+        }
+        any_ref |= cellmax > c_ref;
+        all_deref &= cellmax < c_deref;
+    }
+    any_ref = __syncthreads_or(any_ref);
+    all_deref = __syncthreads_and(all_deref);
+    if (threadIdx.x == 0) flags[b] = any_ref ? 1 : (all_deref ? -1 : 0);
+}
+
+// ---------------------------------------------------------- regrid transfer
+// For each new block: kind 0 copy old block src[0]; kind 1 prolong from old
+// parent src[0] (child position `pos`, bit d = upper half along d), reading
+// the parent's ghost cells at its edge; kind 2 restrict from old children
+// src[0..2^D) (child c has bit d = upper half along d).  Interior cells only.
+struct TransferOp {
+    int32_t kind, pos;
+    int32_t src[8];
+};
+
+template <class real, int D>
+__global__ void __launch_bounds__(256) k_transfer(const real *uold, real *unew, const TransferOp *ops, Geom g) {
+    const int b = blockIdx.x;
+    const TransferOp op = ops[b];
+    const int N = g.N;
+    const int ncell = (D == 3) ? N * N * N : N * N;
+    for (int idx = threadIdx.x; idx < ncell * g.V; idx += blockDim.x) {
+        const int v = idx / ncell, c = idx - v * ncell;
+        const int x[3] = {c % N, (c / N) % N, (D == 3) ? c / (N * N) : 0};
+        real val;
+        if (op.kind == 0) {
+            val = uold[int64_t(op.src[0]) * g.bstride + int64_t(v) * g.ncell + cell_index<real>(g, x[0], x[1], x[2])];
+        } else if (op.kind == 1) {
+            int y[3] = {0, 0, 0}, s[3] = {0, 0, 0};
+            for (int d = 0; d < D; ++d) {
+                const int fine = ((op.pos >> d) & 1) * N + x[d];
+                y[d] = fine >> 1;
+                s[d] = fine & 1;
+            }
+            val = prolong_at<real, D>(uold + int64_t(op.src[0]) * g.bstride + int64_t(v) * g.ncell, g, y[0], y[1], y[2], s[0],
+                                      s[1], s[2]);
+        } else {
+            int ch = 0, y[3] = {0, 0, 0};
+            for (int d = 0; d < D; ++d) {
+                const int hi = x[d] >= N / 2;
+                ch |= hi << d;
+                y[d] = 2 * (x[d] - hi * (N / 2));
+            }
+            val = restrict_at<real, D>(uold + int64_t(op.src[ch]) * g.bstride + int64_t(v) * g.ncell, g, y[0], y[1], y[2]);
+        }
+        unew[int64_t(b) * g.bstride + int64_t(v) * g.ncell + cell_index<real>(g, x[0], x[1], x[2])] = val;
+    }
+}
+
+}  // namespace amrb

@@ -1,0 +1,102 @@
+// Face-neighbour walk that classifies every block face as SRL / F2C / C2F /
+// BC (Sec. 2.5).  For block A at level l and face f the same-size box across
+// the face is looked up: a leaf -> SRL; its parent a leaf -> C2F (A is fine);
+// otherwise the 2^(d-1) children facing A must be leaves -> F2C (A is coarse,
+// one entry per fine source).  Outside a non-periodic domain -> BC.
+#include "pattern.hpp"
+
+#include <algorithm>
+
+namespace amrb {
+
+bool build_pattern(const Forest &F, Pattern &P, std::string &err) {
+    const Geometry &G = F.geo;
+    const int D = G.ndim;
+    const int nb = int(F.leaves.size());
+    P = Pattern();
+    P.entries.reserve(size_t(nb) * 2 * D);
+    for (int b = 0; b < nb; ++b) {
+        const Leaf &A = F.leaves[b];
+        for (int f = 0; f < 2 * D; ++f) {
+            const int n = f >> 1, side = f & 1;
+            int t0 = -1, t1 = -1;
+            for (int d = 0, c = 0; d < D; ++d)
+                if (d != n) (c++ == 0 ? t0 : t1) = d;
+            int64_t q[3] = {A.g[0], A.g[1], A.g[2]};
+            q[n] += side ? 1 : -1;
+            if (!F.wrap(n, A.lev, q[n])) {
+                P.entries.push_back({KIND_BC, f, b, -1, 0, 0});
+                continue;
+            }
+            int s = F.find(A.lev, q[0], q[1], q[2]);
+            if (s >= 0) {
+                P.entries.push_back({KIND_SRL, f, b, s, 0, 0});
+                continue;
+            }
+            if (A.lev > 0) {
+                int c = F.find(A.lev - 1, q[0] >> 1, q[1] >> 1, D == 3 ? q[2] >> 1 : 0);
+                if (c >= 0) {
+                    int off = int(A.g[t0] & 1) | (D == 3 ? int(A.g[t1] & 1) << 1 : 0);
+                    P.entries.push_back({KIND_C2F, f, b, c, off, 0});
+                    continue;
+                }
+            }
+            // finer neighbours: children of q adjacent to A
+            for (int o = 0; o < (1 << (D - 1)); ++o) {
+                int64_t ch[3] = {0, 0, 0};
+                ch[n] = 2 * q[n] + (side ? 0 : 1);
+                ch[t0] = 2 * q[t0] + (o & 1);
+                if (D == 3) ch[t1] = 2 * q[t1] + ((o >> 1) & 1);
+                int fs = (A.lev < G.max_level) ? F.find(A.lev + 1, ch[0], ch[1], ch[2]) : -1;
+                if (fs < 0) {
+                    err = "ghost pattern: block " + std::to_string(b) + " face " + std::to_string(f) +
+                          " has no leaf neighbour within one level (2:1 balance broken)";
+                    return false;
+                }
+                P.entries.push_back({KIND_F2C, f, b, fs, o, 0});
+            }
+        }
+    }
+    std::sort(P.entries.begin(), P.entries.end(), [](const Entry &x, const Entry &y) {
+        if (x.kind != y.kind) return x.kind < y.kind;
+        if (x.face != y.face) return x.face < y.face;
+        if (x.dst != y.dst) return x.dst < y.dst;
+        return x.offset < y.offset;
+    });
+    int32_t ibf = 0;
+    for (Entry &e : P.entries)
+        if (e.kind == KIND_BC) e.aux = ibf++;
+    P.n_bc = ibf;
+
+    // execution lists and refinement-face flux slots
+    P.info.assign(size_t(nb), BlockInfo{});
+    for (int b = 0; b < nb; ++b) {
+        P.info[b].level = F.leaves[b].lev;
+        P.info[b].fixmask = 0;
+        for (int f = 0; f < 6; ++f) P.info[b].bslot[f] = -1;
+    }
+    for (const Entry &e : P.entries) {
+        (e.kind == KIND_C2F ? P.round2 : P.round1).push_back(e);
+        if (e.kind == KIND_F2C || e.kind == KIND_C2F) {
+            int32_t &slot = P.info[e.dst].bslot[e.face];
+            if (slot < 0) slot = P.n_slots++;
+            if (e.kind == KIND_F2C) P.info[e.dst].fixmask |= 1 << e.face;
+        }
+    }
+    // fix-up faces: every (coarse block, face) with F2C sources
+    for (const Entry &e : P.entries) {
+        if (e.kind != KIND_F2C) continue;
+        if (P.fix.empty() || P.fix.back().block != e.dst || P.fix.back().face != e.face)
+            P.fix.push_back({e.dst, e.face, P.info[e.dst].bslot[e.face], {-1, -1, -1, -1}});
+        P.fix.back().fslot[e.offset] = P.info[e.src].bslot[e.face ^ 1];
+    }
+    std::sort(P.fix.begin(), P.fix.end(), [](const FixFace &x, const FixFace &y) {
+        return x.block != y.block ? x.block < y.block : x.face < y.face;
+    });
+    for (size_t i = 0; i < P.fix.size(); ++i)
+        if (i == 0 || P.fix[i].block != P.fix[i - 1].block) P.fix_start.push_back(int32_t(i));
+    P.fix_start.push_back(int32_t(P.fix.size()));
+    return true;
+}
+
+}  // namespace amrb

@@ -1,0 +1,50 @@
+// Ghost-cell pattern of Sec. 2.5, built on the host from the forest's face
+// connectivity and executed on the GPU.  Besides the canonical entry list
+// this produces the tables the kernels need: refinement-face flux slots for
+// flux fixing (Sec. 2.6) and the per-coarse-block fix-up lists.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "forest.hpp"
+
+namespace amrb {
+
+enum : int32_t { KIND_SRL = 0, KIND_F2C = 1, KIND_BC = 2, KIND_C2F = 3 };
+
+struct Entry {
+    int32_t kind, face, dst, src, offset, aux;
+};
+
+// One coarse block face that touches 2^(d-1) finer blocks.
+struct FixFace {
+    int32_t block, face;
+    int32_t cslot;      // flux slot of the coarse side
+    int32_t fslot[4];   // flux slots of the fine sides, by offset
+};
+
+// Per-block data read by the stage kernel.
+struct BlockInfo {
+    int32_t level;
+    int32_t fixmask;    // bit f: face f is the coarse side of a refinement face
+    int32_t bslot[6];   // flux slot of face f, -1 if not a refinement face
+};
+
+struct Pattern {
+    std::vector<Entry> entries;   // canonical order (kind, face, dst, offset)
+    std::vector<Entry> round1;    // SRL, F2C, BC
+    std::vector<Entry> round2;    // C2F
+    std::vector<BlockInfo> info;  // per block
+    std::vector<FixFace> fix;     // sorted by (block, face)
+    std::vector<int32_t> fix_start;  // per fix-up block: first index into fix (+ sentinel)
+    int32_t n_slots = 0;
+    int32_t n_bc = 0;
+};
+
+// Returns false (with a message) if some face has no valid neighbour
+// configuration (2:1 balance broken).
+bool build_pattern(const Forest &f, Pattern &out, std::string &err);
+
+}  // namespace amrb

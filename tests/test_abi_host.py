@@ -1,0 +1,122 @@
+"""Host-side checks of the CUDA library (no GPU needed): the shared object
+loads and exports every function include/amr.h declares; configurations are
+validated; the production forest and face-walk ghost pattern builder agree
+bit for bit with the oracle's brute-force classification (Sec. 2.2, 2.5)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+import paper_2605_07612_b300 as amr
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "amr.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(amr_\w+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = amr.load()
+    names = declared_functions()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(names) == sorted(amr.EXPORTED)
+
+
+def test_invalid_configs_are_rejected():
+    lib = amr.load()
+    sp = synth.MeshSpec(ndim=3, N=16, ng=2, ntrees=(2, 2, 2), max_level=1)
+    h = C.c_void_p()
+    for field, value in [("block_n", 12), ("n_ghost", 9), ("n_var", 4), ("precision", 16), ("ndim", 4),
+                         ("max_level", 40), ("max_blocks", 0)]:
+        cfg = amr.config_from_spec(sp, 64, host_only=True)
+        setattr(cfg, field, value)
+        assert lib.amr_create_forest(C.byref(cfg), 0, C.byref(h)) == amr.AMR_EINVAL, field
+    cfg = amr.config_from_spec(sp, 64, host_only=True)
+    cfg.periodic[0] = 0            # non-periodic x without a boundary kind
+    assert lib.amr_create_forest(C.byref(cfg), 0, C.byref(h)) == amr.AMR_EINVAL
+    cfg = amr.config_from_spec(sp, 7, host_only=True)    # 8 blocks at level 0
+    assert lib.amr_create_forest(C.byref(cfg), 0, C.byref(h)) == amr.AMR_ECAPACITY
+    assert lib.amr_create_forest(None, 0, C.byref(h)) == amr.AMR_EINVAL
+
+
+def test_host_only_forest_refuses_block_data():
+    sp = synth.MeshSpec(ndim=2, N=8, ng=2, ntrees=(2, 2, 1), max_level=1)
+    f = amr.Forest(sp, 0, max_blocks=16, host_only=True)
+    with pytest.raises(amr.AmrError) as e:
+        f.fill_ghosts(0)
+    assert e.value.status == amr.AMR_ESTATE
+    with pytest.raises(amr.AmrError) as e:
+        f.regrid(None)
+    assert e.value.status == amr.AMR_ESTATE
+
+
+def test_capacity_overflow_leaves_mesh_unchanged():
+    sp = synth.MeshSpec(ndim=2, N=8, ng=2, ntrees=(2, 2, 1), max_level=2)
+    f = amr.Forest(sp, 0, max_blocks=8, host_only=True)
+    pat0 = f.pattern().copy()
+    with pytest.raises(amr.AmrError) as e:
+        f.regrid(np.ones(4, dtype=np.int8))      # 16 blocks > 8
+    assert e.value.status == amr.AMR_ECAPACITY
+    assert f.n == 4
+    np.testing.assert_array_equal(f.pattern(), pat0)
+
+
+def random_pair(ndim, seed, rounds=3):
+    rng = np.random.default_rng(1000 + seed)
+    if ndim == 2:
+        nt = (int(rng.integers(1, 5)), int(rng.integers(1, 5)), 1)
+        per = (int(rng.integers(2)), int(rng.integers(2)), 1)
+        sp = synth.MeshSpec(ndim=2, N=8, ng=2, ntrees=nt, periodic=per, max_level=3,
+                            bc_type=(1, 1, 2, 2, 0, 0))
+    else:
+        nt = tuple(int(x) for x in rng.integers(1, 4, 3))
+        per = tuple(int(x) for x in rng.integers(0, 2, 3))
+        sp = synth.MeshSpec(ndim=3, N=8, ng=2, ntrees=nt, periodic=per, max_level=3,
+                            bc_type=(1, 2, 1, 2, 3, 3))
+    lvl0 = int(rng.integers(0, 2))
+    om = oracle.Mesh(sp, lvl0)
+    pm = amr.Forest(sp, lvl0, max_blocks=200000, host_only=True)
+    for _ in range(rounds):
+        flags = rng.choice(np.array([-1, 0, 1], dtype=np.int8), size=om.n, p=[0.3, 0.45, 0.25])
+        om = om.adapt(flags)
+        pm.regrid(flags)
+    return sp, om, pm
+
+
+@pytest.mark.parametrize("seed", range(60))
+def test_production_pattern_matches_brute_force_2d(seed):
+    sp, om, pm = random_pair(2, seed)
+    lo, go = om.blocks()
+    lp, gp = pm.blocks()
+    np.testing.assert_array_equal(lo, lp)
+    np.testing.assert_array_equal(go, gp)
+    np.testing.assert_array_equal(om.pattern(), pm.pattern())
+
+
+@pytest.mark.parametrize("seed", range(25))
+def test_production_pattern_matches_brute_force_3d(seed):
+    sp, om, pm = random_pair(3, seed)
+    lo, go = om.blocks()
+    lp, gp = pm.blocks()
+    np.testing.assert_array_equal(lo, lp)
+    np.testing.assert_array_equal(go, gp)
+    np.testing.assert_array_equal(om.pattern(), pm.pattern())
+
+
+def test_uniform_3d_configs_shape():
+    """The 256^3 uniform meshes of the benchmark: 16^3 blocks -> 4096 blocks, 6 SRL faces each."""
+    for n, nt in ((8, 32), (16, 16), (32, 8)):
+        sp = synth.MeshSpec(ndim=3, N=n, ng=2, ntrees=(nt, nt, nt), max_level=0)
+        f = amr.Forest(sp, 0, host_only=True)
+        assert f.n == nt ** 3
+        pat = f.pattern()
+        assert len(pat) == 6 * nt ** 3 and np.all(pat[:, 0] == amr.KIND_SRL)

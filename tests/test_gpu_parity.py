@@ -1,0 +1,263 @@
+"""GPU parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Bars (element by element on identical seeded inputs):
+  * ghost patterns and FP64 ghost values: bit-exact (Sec. 2.5);
+  * FP64 stages: relative L1 <= 1e-12 per variable;
+  * FP32 stages: relative L1 <= 1e-5 after 100 steps against the FP64 oracle;
+  * refinement flags (Eq. 5) and regrid transfer (Sec. 2.2): bit-exact in FP64.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+amr = pytest.importorskip("paper_2605_07612_b300")
+
+
+def rel_l1(a, b, spec):
+    """Per-variable relative L1 over interior cells."""
+    nb = a.shape[0]
+    sl = tuple(slice(spec.ng, spec.ng + spec.N) for _ in range(spec.ndim))
+    A = a.reshape((nb, spec.nvar) + (spec.side,) * spec.ndim)[(slice(None), slice(None)) + sl].astype(np.float64)
+    B = b.reshape((nb, spec.nvar) + (spec.side,) * spec.ndim)[(slice(None), slice(None)) + sl]
+    ax = (0,) + tuple(range(2, 2 + spec.ndim))
+    return np.abs(A - B).sum(axis=ax) / np.maximum(np.abs(B).sum(axis=ax), 1e-300)
+
+
+def face_ghost_mask(spec):
+    m = np.zeros((spec.side,) * spec.ndim, dtype=bool)
+    for idx in np.ndindex(*m.shape):
+        out = sum(1 for c in idx if c < spec.ng or c >= spec.ng + spec.N)
+        m[idx] = out == 1
+    return m.reshape(-1)
+
+
+def make_pair(spec, init_level, flag_rounds=(), precision=64, extra_blocks=0):
+    om = oracle.Mesh(spec, init_level)
+    for fl in flag_rounds:
+        lev, g = om.blocks()
+        om = om.adapt(fl(spec, lev, g))
+    cap = om.n + extra_blocks
+    f = amr.Forest(spec, init_level, max_blocks=max(cap, 1) * 4, n_states=2, precision=precision)
+    for fl in flag_rounds:
+        lev, g = f.blocks()
+        f.regrid(fl(spec, lev, g))
+    lo, go = om.blocks()
+    lp, gp = f.blocks()
+    np.testing.assert_array_equal(lo, lp)
+    np.testing.assert_array_equal(go, gp)
+    return om, f
+
+
+def ball(centre, radii):
+    return lambda sp, lev, g: synth.ball_flags(sp, lev, g, centre, radii)
+
+
+SPEC_2D_AMR = dict(ndim=2, N=16, ng=2, ntrees=(4, 4, 1), max_level=2)
+SPEC_3D_AMR = dict(ndim=3, N=8, ng=2, ntrees=(4, 4, 4), max_level=2)
+AMR2 = [ball((0.4, 0.55), (0.3, 0.15)), ball((0.4, 0.55), (0.3, 0.15))]
+AMR3 = [ball((0.45, 0.5, 0.55), (0.15, 0.05)), ball((0.45, 0.5, 0.55), (0.15, 0.05))]
+
+
+# ------------------------------------------------------------ ghost fill --
+
+@pytest.mark.parametrize("case", ["2d_uniform", "2d_amr", "3d_amr", "2d_bc", "3d_bc_ng3"])
+def test_ghost_fill_fp64_bit_exact(case):
+    if case == "2d_uniform":
+        sp = synth.MeshSpec(ndim=2, N=16, ng=2, ntrees=(16, 16, 1))
+        om, f = make_pair(sp, 0)
+    elif case == "2d_amr":
+        sp = synth.MeshSpec(**SPEC_2D_AMR)
+        om, f = make_pair(sp, 0, AMR2)
+    elif case == "3d_amr":
+        sp = synth.MeshSpec(**SPEC_3D_AMR)
+        om, f = make_pair(sp, 0, AMR3)
+    elif case == "2d_bc":
+        sp = synth.MeshSpec(ndim=2, N=8, ng=2, ntrees=(3, 2, 1), periodic=(0, 0, 1), max_level=2,
+                            bc_type=(1, 2, 2, 1, 0, 0),
+                            bc_val=[[0.3 * (f + 1) + v for v in range(8)] for f in range(6)])
+        om, f = make_pair(sp, 0, [ball((0.2, 0.3), (0.3, 0.12)), ball((0.2, 0.3), (0.3, 0.12))])
+    else:
+        sp = synth.MeshSpec(ndim=3, N=8, ng=3, ntrees=(2, 2, 2), periodic=(1, 0, 0), max_level=2,
+                            bc_type=(0, 0, 2, 1, 1, 2),
+                            bc_val=[[0.1 * (f + 1) - 0.05 * v for v in range(8)] for f in range(6)])
+        om, f = make_pair(sp, 0, [ball((0.3, 0.3, 0.3), (0.2, 0.08)), ball((0.3, 0.3, 0.3), (0.2, 0.08))])
+    lev, g = om.blocks()
+    u = synth.fourier3d(sp, lev, g, seed=11) if sp.ndim == 3 else synth.kelvin_helmholtz(sp, lev, g, seed=5)
+    np.testing.assert_array_equal(om.pattern(), f.pattern())
+    f.set_state(0, u)
+    f.fill_ghosts(0)
+    got = f.get_state(0)
+    om.fill_ghosts(u)
+    m = face_ghost_mask(sp)
+    np.testing.assert_array_equal(got[:, :, m], u[:, :, m])
+
+
+def test_ghost_fill_bc_data_linear_exact():
+    """Linear field with Dirichlet data on every face (Sec. 4.3 test)."""
+    sp = synth.MeshSpec(ndim=3, N=8, ng=2, ntrees=(1, 1, 1), periodic=(0, 0, 0), max_level=3, bc_type=(3,) * 6)
+    pt = (0.5 + 0.49, 0.5, 0.5 - 0.49)
+    flags = [lambda s, lev, g: synth.point_flags(s, lev, g, pt, 3)] * 3
+    om, f = make_pair(sp, 0, flags)
+    lev, g = om.blocks()
+    u = synth.linear_field(sp, lev, g)
+    pat = om.pattern()
+    bce = [(fa, d) for k, fa, d, s, o, a in pat if k == oracle.KIND_BC]
+    bc = synth.linear_face_values(sp, lev, g, bce)
+    f.set_bc_data(bc)
+    f.set_state(0, u)
+    f.fill_ghosts(0)
+    got = f.get_state(0)
+    om.fill_ghosts(u, bc)
+    m = face_ghost_mask(sp)
+    np.testing.assert_array_equal(got[:, :, m], u[:, :, m])
+
+
+# ---------------------------------------------------------------- stages --
+
+def run_gpu_heun(f, u, nsteps, use_graph=False):
+    f.set_state(0, u)
+    f.compute_dt(0)
+    dts = []
+    for _ in range(nsteps):
+        dts.append(f.get_dt())
+        f.step(1, use_graph=use_graph)
+    st = f.sync_status()
+    assert st == amr.AMR_OK, st
+    return f.get_state(0), dts
+
+
+def test_kelvin_helmholtz_fp64_100_steps():
+    """2D KH, 16x16 blocks of 16^2, periodic, 100 Heun steps: FP64 GPU vs oracle."""
+    sp = synth.MeshSpec(ndim=2, N=16, ng=2, ntrees=(16, 16, 1))
+    om, f = make_pair(sp, 0)
+    lev, g = om.blocks()
+    u = synth.kelvin_helmholtz(sp, lev, g, seed=0)
+    got, dts = run_gpu_heun(f, u.copy(), 100)
+    ref = u.copy()
+    odts = oracle.run_heun(om, ref, 100)
+    np.testing.assert_allclose(dts, odts, rtol=1e-13)
+    assert rel_l1(got, ref, sp).max() <= 1e-12
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_amr_fp64_matches_oracle(dim):
+    sp = synth.MeshSpec(**(SPEC_2D_AMR if dim == 2 else SPEC_3D_AMR))
+    om, f = make_pair(sp, 0, AMR2 if dim == 2 else AMR3)
+    lev, g = om.blocks()
+    u = synth.kelvin_helmholtz(sp, lev, g, seed=3) if dim == 2 else synth.fourier3d(sp, lev, g, seed=2)
+    n = 20 if dim == 2 else 6
+    got, dts = run_gpu_heun(f, u.copy(), n)
+    ref = u.copy()
+    odts = oracle.run_heun(om, ref, n)
+    np.testing.assert_allclose(dts, odts, rtol=1e-13)
+    assert rel_l1(got, ref, sp).max() <= 1e-12
+
+
+def test_kelvin_helmholtz_fp32_100_steps():
+    """FP32 state, FP64 dt reduction: relative L1 <= 1e-5 after 100 steps."""
+    sp = synth.MeshSpec(ndim=2, N=16, ng=2, ntrees=(16, 16, 1))
+    om, f = make_pair(sp, 0, precision=32)
+    lev, g = om.blocks()
+    u = synth.kelvin_helmholtz(sp, lev, g, seed=0)
+    got, _ = run_gpu_heun(f, u.astype(np.float32), 100, use_graph=True)
+    ref = u.copy()
+    oracle.run_heun(om, ref, 100)
+    err = rel_l1(got, ref, sp)
+    assert err.max() <= 1e-5, err
+
+
+def test_fp32_3d_amr_against_oracle():
+    sp = synth.MeshSpec(**SPEC_3D_AMR)
+    om, f = make_pair(sp, 0, AMR3, precision=32)
+    lev, g = om.blocks()
+    u = synth.fourier3d(sp, lev, g, seed=4)
+    got, _ = run_gpu_heun(f, u.astype(np.float32), 10, use_graph=True)
+    ref = u.copy()
+    oracle.run_heun(om, ref, 10)
+    assert rel_l1(got, ref, sp).max() <= 1e-5
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_graph_replay_equals_plain_launches(precision):
+    sp = synth.MeshSpec(**SPEC_2D_AMR)
+    om, f1 = make_pair(sp, 0, AMR2, precision=precision)
+    _, f2 = make_pair(sp, 0, AMR2, precision=precision)
+    lev, g = om.blocks()
+    u = synth.kelvin_helmholtz(sp, lev, g, seed=9).astype(f1.dtype)
+    a, _ = run_gpu_heun(f1, u, 7, use_graph=False)
+    b, _ = run_gpu_heun(f2, u, 7, use_graph=True)
+    np.testing.assert_array_equal(a, b)
+
+
+def test_conservation_fp64_periodic_amr():
+    sp = synth.MeshSpec(**SPEC_3D_AMR)
+    om, f = make_pair(sp, 0, AMR3)
+    lev, g = om.blocks()
+    u = synth.fourier3d(sp, lev, g, seed=6)
+    f.set_state(0, u)
+    s0 = f.conserved(0)
+    np.testing.assert_allclose(s0, om.conserved(u), rtol=1e-13, atol=1e-15)
+    scale = om.conserved(np.abs(u))
+    f.compute_dt(0)
+    f.step(10)
+    assert (np.abs(f.conserved(0) - s0) / scale).max() < 1e-13
+
+
+def test_free_stream_fp64_bit_exact():
+    sp = synth.MeshSpec(**SPEC_3D_AMR)
+    om, f = make_pair(sp, 0, AMR3)
+    rho = np.ones([om.n] + [sp.side] * 3)
+    u = synth.mask_interior(sp, synth.primitive_to_state(sp, rho, [0.3 * rho, -0.2 * rho, 0.1 * rho], 0.7 * rho))
+    got, _ = run_gpu_heun(f, u.copy(), 5)
+    assert rel_l1(got, u, sp).max() == 0.0
+
+
+# ------------------------------------------------------- flags and regrid --
+
+def test_lohner_flags_bit_exact():
+    sp = synth.MeshSpec(**SPEC_2D_AMR)
+    om, f = make_pair(sp, 0, AMR2)
+    lev, g = om.blocks()
+    u = synth.kelvin_helmholtz(sp, lev, g, seed=1)
+    f.set_state(0, u)
+    f.fill_ghosts(0)
+    om.fill_ghosts(u)
+    for c_ref, c_deref in ((5e-2, 6.25e-3), (2e-2, 1e-2), (1e-3, 5e-4)):
+        np.testing.assert_array_equal(f.flag(0, c_ref, c_deref), om.lohner_flags(u, c_ref, c_deref))
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_regrid_transfer_bit_exact(dim):
+    sp = synth.MeshSpec(**(SPEC_2D_AMR if dim == 2 else SPEC_3D_AMR))
+    om, f = make_pair(sp, 0, AMR2 if dim == 2 else AMR3, extra_blocks=4096)
+    lev, g = om.blocks()
+    u = synth.kelvin_helmholtz(sp, lev, g, seed=2) if dim == 2 else synth.fourier3d(sp, lev, g, seed=2)
+    f.set_state(0, u)
+    rng = np.random.default_rng(5)
+    for _ in range(3):
+        flags = rng.choice(np.array([-1, 0, 1], dtype=np.int8), size=om.n, p=[0.4, 0.3, 0.3])
+        om.fill_ghosts(u)
+        nm = om.adapt(flags)
+        u = om.transfer(u, nm)
+        om = nm
+        assert f.regrid(flags)
+        np.testing.assert_array_equal(f.blocks()[0], om.blocks()[0])
+        got = f.get_state(0)
+        assert rel_l1(got, u, sp).max() == 0.0
+
+
+def test_nonphysical_state_is_reported():
+    sp = synth.MeshSpec(ndim=2, N=16, ng=2, ntrees=(2, 2, 1))
+    f = amr.Forest(sp, 0, precision=64)
+    lev, g = f.blocks()
+    u = synth.kelvin_helmholtz(sp, lev, g)
+    u.reshape(f.n, sp.nvar, sp.side, sp.side)[1, 0, 5, 5] = -1.0     # negative density
+    f.set_state(0, u)
+    f.set_dt(1e-4)
+    f.step(1)
+    assert f.sync_status() == amr.AMR_ENONPHYS
+    assert f.sync_status() == amr.AMR_OK      # cleared after reading
