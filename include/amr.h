@@ -240,6 +240,33 @@ const char *amr_last_error(const amr_forest *f);
 /* Kernel launches issued by the library since the forest was created. */
 amr_status amr_launch_count(const amr_forest *f, int64_t *n);
 
+/* Largest block count amr_conserved_static() accepts. */
+#define AMR_STATIC_MAX_BLOCKS 65536
+
+/* Conserved integrals of a block array without any device allocation.
+ * The paper has no counterpart: this is for callers that cannot call
+ * cudaMalloc when they need the sums -- their device memory is reserved up
+ * front by another allocator (a framework's caching pool, a fixed arena), or
+ * they must not trigger the device-wide synchronisation that cudaMalloc and
+ * cudaFree may cause.  It computes what amr_conserved() computes, but takes
+ * plain device pointers and needs no forest:
+ *   state       : n_blocks blocks in the layout above (one state slot),
+ *                 float (precision 32) or double (64);
+ *   cell_volume : device array, volume of one cell of each block (double);
+ *   sums        : device array of ndim + 2 doubles, written on `stream`.
+ * The per-block partial sums go to a scratch array of
+ * AMR_STATIC_MAX_BLOCKS x 5 doubles (2.6 MB) that is part of the library's
+ * device image: every GPU that loads the library holds it until the process
+ * exits.  Calls share that array, so calls that overlap on the GPU (on
+ * different streams, or from different threads) race and give wrong sums;
+ * each call overwrites the entries it reads, so nothing carries over between
+ * calls that are ordered.  The first call on a device looks up the array's
+ * device address with that device current; make that first call before any
+ * stream capture.  Errors: AMR_EINVAL (null pointer, bad shape or
+ * precision), AMR_ECAPACITY (n_blocks > AMR_STATIC_MAX_BLOCKS), AMR_ECUDA. */
+amr_status amr_conserved_static(const void *state, int precision, int ndim, int block_n, int n_ghost,
+                                int64_t n_blocks, const double *cell_volume, double *sums, amr_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

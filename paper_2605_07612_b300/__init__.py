@@ -27,7 +27,7 @@ EXPORTED = [
     "amr_get_ghost_pattern", "amr_set_state", "amr_get_state", "amr_state_ptr", "amr_set_bc_data",
     "amr_fill_ghosts", "amr_compute_dt", "amr_set_dt", "amr_get_dt", "amr_advance_stage", "amr_step",
     "amr_conserved", "amr_flag", "amr_flag_and_regrid", "amr_sync_status", "amr_last_error",
-    "amr_launch_count",
+    "amr_launch_count", "amr_conserved_static",
 ]
 
 
