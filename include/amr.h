@@ -118,7 +118,10 @@ typedef struct {
  *   u(s_out) = w_dt * dt * F(u(s_deriv)) + sum_i w_prev[i] u(s_prev[i])
  * dt is the device-resident time step of the forest.  update_dt = 1 marks
  * the last stage of a step: the stage also reduces the CFL limit of its own
- * output (after flux fixing) into the next dt. */
+ * output (after flux fixing) into the next dt.  gather_halo = 1: halo cells
+ * across same-level (SRL) faces are read straight from the neighbour's
+ * interior instead of from s_deriv's ghost cells, which then only need the
+ * non-SRL part of the pattern (amr_step with AMR_STEP_GATHER does that). */
 typedef struct {
     int s_out, s_deriv;
     int n_prev;
@@ -126,7 +129,14 @@ typedef struct {
     double w_prev[4];
     double w_dt;
     int update_dt;
+    int gather_halo;
 } amr_stage;
+
+/* Flags of amr_step(). */
+#define AMR_STEP_GRAPH 1   /* capture one step as a CUDA graph and replay it */
+#define AMR_STEP_GATHER 2  /* stages gather same-level halos from neighbours;
+                              the ghost fill runs only the entries that still
+                              need ghost cells (state ghosts are then stale) */
 
 /* Refinement-criterion constants of Eq. 5 (Sec. 3.3).  The criterion is
  * evaluated on density and pressure; a cell's value is the larger one. */
@@ -206,9 +216,12 @@ amr_status amr_advance_stage(amr_forest *f, const amr_stage *st, amr_stream stre
 
 /* n_steps steps of Heun's method (Eq. 5-6) on slot 0 (slot 1 as the stage
  * state): fill ghosts, stage 1, fill ghosts, stage 2 with the dt update.
- * use_graph = 1 captures one step in a CUDA graph on first use and replays it
- * (re-captured after a regrid).  The dt must be set (amr_compute_dt). */
-amr_status amr_step(amr_forest *f, int n_steps, int use_graph, amr_stream stream);
+ * flags: AMR_STEP_GRAPH captures one step in a CUDA graph on first use and
+ * replays it (re-captured after a regrid or a change of flags);
+ * AMR_STEP_GATHER lets the stage kernel read same-level halos directly (the
+ * ghost cells of the state are not all refreshed; amr_fill_ghosts() refills
+ * them).  The dt must be set (amr_compute_dt). */
+amr_status amr_step(amr_forest *f, int n_steps, int flags, amr_stream stream);
 
 /* Integral of every conserved variable over the leaves of slot s, summed in
  * double on the device in a fixed order (Eq. 12).  Synchronises `stream`. */

@@ -18,6 +18,7 @@ from . import build as _build
 
 AMR_OK, AMR_EINVAL, AMR_ENOMEM, AMR_ECAPACITY, AMR_ECUDA = 0, 1, 2, 3, 4
 AMR_ETIMEOUT, AMR_EBOUNDS, AMR_ENONPHYS, AMR_ESTATE = 5, 6, 7, 8
+AMR_STEP_GRAPH, AMR_STEP_GATHER = 1, 2
 STATUS_NAMES = {0: "AMR_OK", 1: "AMR_EINVAL", 2: "AMR_ENOMEM", 3: "AMR_ECAPACITY", 4: "AMR_ECUDA",
                 5: "AMR_ETIMEOUT", 6: "AMR_EBOUNDS", 7: "AMR_ENONPHYS", 8: "AMR_ESTATE"}
 KIND_SRL, KIND_F2C, KIND_BC, KIND_C2F = 0, 1, 2, 3
@@ -59,7 +60,7 @@ class GhostEntry(C.Structure):
 
 class Stage(C.Structure):
     _fields_ = [("s_out", C.c_int), ("s_deriv", C.c_int), ("n_prev", C.c_int), ("s_prev", C.c_int * 4),
-                ("w_prev", C.c_double * 4), ("w_dt", C.c_double), ("update_dt", C.c_int)]
+                ("w_prev", C.c_double * 4), ("w_dt", C.c_double), ("update_dt", C.c_int), ("gather_halo", C.c_int)]
 
 
 class FlagParams(C.Structure):
@@ -260,7 +261,7 @@ class Forest:
         self._check(self.lib.amr_get_dt(self.h, C.byref(d), _stream_ptr(stream)), "amr_get_dt")
         return float(d.value)
 
-    def advance_stage(self, s_out, s_deriv, prev, weights, w_dt, update_dt=False, stream=None):
+    def advance_stage(self, s_out, s_deriv, prev, weights, w_dt, update_dt=False, gather=False, stream=None):
         st = Stage()
         st.s_out, st.s_deriv, st.n_prev = s_out, s_deriv, len(prev)
         for i, (p, w) in enumerate(zip(prev, weights)):
@@ -268,10 +269,12 @@ class Forest:
             st.w_prev[i] = float(w)
         st.w_dt = float(w_dt)
         st.update_dt = 1 if update_dt else 0
+        st.gather_halo = 1 if gather else 0
         self._check(self.lib.amr_advance_stage(self.h, C.byref(st), _stream_ptr(stream)), "amr_advance_stage")
 
-    def step(self, n_steps=1, use_graph=False, stream=None):
-        self._check(self.lib.amr_step(self.h, int(n_steps), 1 if use_graph else 0, _stream_ptr(stream)), "amr_step")
+    def step(self, n_steps=1, use_graph=False, gather=False, stream=None):
+        flags = (AMR_STEP_GRAPH if use_graph else 0) | (AMR_STEP_GATHER if gather else 0)
+        self._check(self.lib.amr_step(self.h, int(n_steps), flags, _stream_ptr(stream)), "amr_step")
 
     def conserved(self, s, stream=None) -> np.ndarray:
         out = np.zeros(self.spec.nvar)

@@ -39,11 +39,12 @@ struct amr_forest {
     int esize = 8;
     size_t block_bytes = 0;
     void *state = nullptr;
-    DBuf r1, r2, info, fix, fix_start, bflux, bcdata, sc, partial, sums, flags, ops, level;
+    DBuf r1, r2, r1g, info, fix, fix_start, bflux, bcdata, sc, partial, sums, flags, ops, level;
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t gexec = nullptr;
     uint64_t graph_rev = ~0ull;
     int64_t graph_nodes = 0;
+    int graph_flags = -1;
     bool capturing = false;
     int64_t launches = 0;
     std::string err;
@@ -169,6 +170,7 @@ amr_status upload_pattern(amr_forest *f) {
     amr_status s;
     if ((s = upload(f, f->r1, f->pat.round1)) != AMR_OK) return s;
     if ((s = upload(f, f->r2, f->pat.round2)) != AMR_OK) return s;
+    if ((s = upload(f, f->r1g, f->pat.round1_gather)) != AMR_OK) return s;
     if ((s = upload(f, f->info, f->pat.info)) != AMR_OK) return s;
     if ((s = upload(f, f->fix, f->pat.fix)) != AMR_OK) return s;
     if ((s = upload(f, f->fix_start, f->pat.fix_start)) != AMR_OK) return s;
@@ -184,7 +186,7 @@ amr_status upload_pattern(amr_forest *f) {
 
 // ------------------------------------------------------------------ launches
 template <class real, int D>
-amr_status launch_ghosts(amr_forest *f, int s, cudaStream_t st) {
+amr_status launch_ghosts(amr_forest *f, int s, cudaStream_t st, bool gather) {
     GhostArgs<real> a{};
     a.u = static_cast<real *>(slot_ptr(f, s));
     a.bcdata = static_cast<const real *>(f->bcdata.p);
@@ -194,12 +196,23 @@ amr_status launch_ghosts(amr_forest *f, int s, cudaStream_t st) {
         for (int v = 0; v < 8; ++v) a.bc_val[q][v] = real(f->cfg.bc_val[q][v]);
     }
     for (int round = 0; round < 2; ++round) {
-        const auto &lst = round == 0 ? f->pat.round1 : f->pat.round2;
+        const auto &lst = round == 0 ? (gather ? f->pat.round1_gather : f->pat.round1) : f->pat.round2;
         if (lst.empty()) continue;
-        a.list = static_cast<const Entry *>(round == 0 ? f->r1.p : f->r2.p);
+        a.list = static_cast<const Entry *>(round == 0 ? (gather ? f->r1g.p : f->r1.p) : f->r2.p);
         a.n = int(lst.size());
         const int grid = (a.n + 7) / 8;
-        k_ghost<real, D><<<grid, 256, 0, st>>>(a, f->geom);
+        const int N = f->cfg.block_n, NG = f->cfg.n_ghost;
+        bool launched = false;
+#define AMR_GHOST_CASE(n_, g_)                                                   \
+    if (!launched && N == n_ && NG == g_) {                                     \
+        k_ghost<real, D, n_, g_><<<grid, 256, 0, st>>>(a, f->geom);             \
+        launched = true;                                                        \
+    }
+        AMR_GHOST_CASE(8, 1) AMR_GHOST_CASE(8, 2) AMR_GHOST_CASE(8, 3) AMR_GHOST_CASE(8, 4)
+        AMR_GHOST_CASE(16, 1) AMR_GHOST_CASE(16, 2) AMR_GHOST_CASE(16, 3) AMR_GHOST_CASE(16, 4)
+        AMR_GHOST_CASE(32, 1) AMR_GHOST_CASE(32, 2) AMR_GHOST_CASE(32, 3) AMR_GHOST_CASE(32, 4)
+#undef AMR_GHOST_CASE
+        if (!launched) return fail(f, AMR_EINVAL, "no ghost kernel for block_n %d, n_ghost %d", N, NG);
         ++f->launches;
     }
     CU(cudaGetLastError());
@@ -256,6 +269,7 @@ amr_status run_stage(amr_forest *f, const amr_stage *stg, cudaStream_t st) {
     a.info = static_cast<const BlockInfo *>(f->info.p);
     a.bflux = static_cast<real *>(f->bflux.p);
     a.update_dt = stg->update_dt;
+    a.gather = stg->gather_halo;
     a.gamma = real(f->cfg.gamma);
     amr_status s = launch_stage<real, D>(f, a, st);
     if (s != AMR_OK) return s;
@@ -296,7 +310,7 @@ amr_status dispatch(amr_forest *f, Args &&...args) {
 
 template <class real, int D>
 struct GhostFn {
-    static amr_status run(amr_forest *f, int s, cudaStream_t st) { return launch_ghosts<real, D>(f, s, st); }
+    static amr_status run(amr_forest *f, int s, cudaStream_t st, bool gather) { return launch_ghosts<real, D>(f, s, st, gather); }
 };
 template <class real, int D>
 struct StageFn {
@@ -364,13 +378,14 @@ struct TransferFn {
     }
 };
 
-amr_status heun_step(amr_forest *f, cudaStream_t st) {
-    amr_stage s1{1, 0, 1, {0, 0, 0, 0}, {1.0, 0, 0, 0}, 1.0, 0};
-    amr_stage s2{0, 1, 2, {0, 1, 0, 0}, {0.5, 0.5, 0, 0}, 0.5, 1};
+amr_status heun_step(amr_forest *f, cudaStream_t st, bool gather) {
+    const int gh = gather ? 1 : 0;
+    amr_stage s1{1, 0, 1, {0, 0, 0, 0}, {1.0, 0, 0, 0}, 1.0, 0, gh};
+    amr_stage s2{0, 1, 2, {0, 1, 0, 0}, {0.5, 0.5, 0, 0}, 0.5, 1, gh};
     amr_status r;
-    if ((r = dispatch<GhostFn>(f, 0, st)) != AMR_OK) return r;
+    if ((r = dispatch<GhostFn>(f, 0, st, gather)) != AMR_OK) return r;
     if ((r = dispatch<StageFn>(f, &s1, st)) != AMR_OK) return r;
-    if ((r = dispatch<GhostFn>(f, 1, st)) != AMR_OK) return r;
+    if ((r = dispatch<GhostFn>(f, 1, st, gather)) != AMR_OK) return r;
     return dispatch<StageFn>(f, &s2, st);
 }
 
@@ -443,7 +458,7 @@ amr_status amr_destroy_forest(amr_forest *f) {
     if (!f) return AMR_OK;
     if (f->gexec) cudaGraphExecDestroy(f->gexec);
     if (f->cap_stream) cudaStreamDestroy(f->cap_stream);
-    for (DBuf *b : {&f->r1, &f->r2, &f->info, &f->fix, &f->fix_start, &f->bflux, &f->bcdata, &f->sc, &f->partial, &f->sums,
+    for (DBuf *b : {&f->r1, &f->r2, &f->r1g, &f->info, &f->fix, &f->fix_start, &f->bflux, &f->bcdata, &f->sc, &f->partial, &f->sums,
                     &f->flags, &f->ops, &f->level})
         dev_free(f, b->p);
     dev_free(f, f->state);
@@ -536,7 +551,7 @@ amr_status amr_fill_ghosts(amr_forest *f, int s, amr_stream stream) {
     NEED_DEVICE(f);
     amr_status r = upload_pattern(f);
     if (r != AMR_OK) return r;
-    return dispatch<GhostFn>(f, s, static_cast<cudaStream_t>(stream));
+    return dispatch<GhostFn>(f, s, static_cast<cudaStream_t>(stream), false);
 }
 
 amr_status amr_compute_dt(amr_forest *f, int s, amr_stream stream) {
@@ -574,7 +589,7 @@ amr_status amr_advance_stage(amr_forest *f, const amr_stage *st, amr_stream stre
     return dispatch<StageFn>(f, st, static_cast<cudaStream_t>(stream));
 }
 
-amr_status amr_step(amr_forest *f, int n_steps, int use_graph, amr_stream stream) {
+amr_status amr_step(amr_forest *f, int n_steps, int flags, amr_stream stream) {
     if (!f || n_steps < 0) return AMR_EINVAL;
     NEED_DEVICE(f);
     if (f->cfg.n_states < 2) return fail(f, AMR_EINVAL, "Heun's method needs n_states >= 2");
@@ -582,12 +597,13 @@ amr_status amr_step(amr_forest *f, int n_steps, int use_graph, amr_stream stream
     amr_status r = upload_pattern(f);
     if (r != AMR_OK) return r;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (!use_graph) {
+    const bool gather = (flags & AMR_STEP_GATHER) != 0;
+    if (!(flags & AMR_STEP_GRAPH)) {
         for (int i = 0; i < n_steps; ++i)
-            if ((r = heun_step(f, st)) != AMR_OK) return r;
+            if ((r = heun_step(f, st, gather)) != AMR_OK) return r;
         return AMR_OK;
     }
-    if (!f->gexec || f->graph_rev != f->forest.revision) {
+    if (!f->gexec || f->graph_rev != f->forest.revision || f->graph_flags != flags) {
         if (f->gexec) {
             cudaGraphExecDestroy(f->gexec);
             f->gexec = nullptr;
@@ -597,7 +613,7 @@ amr_status amr_step(amr_forest *f, int n_steps, int use_graph, amr_stream stream
         CU(cudaStreamSynchronize(st));
         const int64_t before = f->launches;
         CU(cudaStreamBeginCapture(f->cap_stream, cudaStreamCaptureModeThreadLocal));
-        r = heun_step(f, f->cap_stream);
+        r = heun_step(f, f->cap_stream, gather);
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamEndCapture(f->cap_stream, &graph);
         if (r != AMR_OK) {
@@ -611,6 +627,7 @@ amr_status amr_step(amr_forest *f, int n_steps, int use_graph, amr_stream stream
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) return fail(f, AMR_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
         f->graph_rev = f->forest.revision;
+        f->graph_flags = flags;
     }
     for (int i = 0; i < n_steps; ++i) {
         CU(cudaGraphLaunch(f->gexec, st));

@@ -19,6 +19,14 @@ __device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, 
 __device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
 __device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
 
+// 2-element vector type of a precision (aligned 8 / 16-byte accesses)
+template <class real>
+struct Vec2;
+template <>
+struct Vec2<float> { using type = float2; };
+template <>
+struct Vec2<double> { using type = double2; };
+
 // minmod of Eq. 1 with theta = 1: zero unless both slopes have the same
 // strict sign, else the one of smaller magnitude.
 template <class T>

@@ -56,14 +56,77 @@ __device__ __forceinline__ real prolong_at(const real *cb, const Geom &g, int ci
     return uc + t;
 }
 
-template <class real, int D>
+// Same-level copy of one strip with 2-element vectors (Ng even: every row
+// segment of the strip starts on an even element, so the vectors are
+// aligned).  ND = face-normal dimension.  Each lane keeps 4 independent
+// loads in flight before storing.
+template <class real, int D, int N, int NG, int ND>
+__device__ __forceinline__ void srl_pairs(real *dstb, const real *srcb, int side, int lane) {
+    using V2 = typename Vec2<real>::type;
+    constexpr int S = N + 2 * NG;
+    constexpr int64_t NCc = (D == 3) ? int64_t(S) * S * S : int64_t(S) * S;
+    constexpr int T1 = (D == 3) ? N : 1;
+    constexpr int UPV = (ND == 0) ? N * T1 * (NG / 2) : NG * T1 * (N / 2);
+    constexpr int TOTAL = (D + 2) * UPV;
+    const int lo = side ? N : -NG, shift = side ? -N : N;
+    auto cidx = [](int i, int j, int k) -> int64_t {
+        return (int64_t(D == 3 ? k + NG : 0) * S + (j + NG)) * S + (i + NG);
+    };
+    for (int base = lane; base < TOTAL; base += 128) {
+        V2 val[4];
+        int64_t od[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int u = base + 32 * r;
+            od[r] = -1;
+            if (u < TOTAL) {
+                const int v = u / UPV, rem = u - v * UPV;
+                int i, j, k;
+                if (ND == 0) {
+                    const int pp = rem % (NG / 2), row = rem / (NG / 2);
+                    j = row % N;
+                    k = (D == 3) ? row / N : 0;
+                    i = lo + 2 * pp;
+                } else if (ND == 1) {
+                    const int pp = rem % (N / 2), t = rem / (N / 2);
+                    j = lo + t % NG;
+                    k = (D == 3) ? t / NG : 0;
+                    i = 2 * pp;
+                } else {
+                    const int pp = rem % (N / 2), t = rem / (N / 2);
+                    j = t % N;
+                    k = lo + t / N;
+                    i = 2 * pp;
+                }
+                const int is = ND == 0 ? i + shift : i, js = ND == 1 ? j + shift : j, ks = ND == 2 ? k + shift : k;
+                val[r] = *reinterpret_cast<const V2 *>(srcb + v * NCc + cidx(is, js, ks));
+                od[r] = v * NCc + cidx(i, j, k);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+            if (od[r] >= 0) *reinterpret_cast<V2 *>(dstb + od[r]) = val[r];
+    }
+}
+
+template <class real, int D, int N, int NG>
 __global__ void __launch_bounds__(256) k_ghost(GhostArgs<real> a, Geom g) {
     const int warp = int((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (warp >= a.n) return;
     const Entry e = a.list[warp];
-    const int N = g.N, ng = g.ng;
     const int nd = e.face >> 1, side = e.face & 1;
+    real *dstb = a.u + int64_t(e.dst) * g.bstride;
+    const real *srcb = e.src >= 0 ? a.u + int64_t(e.src) * g.bstride : nullptr;
+    if constexpr (NG % 2 == 0) {
+        if (e.kind == KIND_SRL) {
+            if (nd == 0) srl_pairs<real, D, N, NG, 0>(dstb, srcb, side, lane);
+            else if (nd == 1 || D == 2) srl_pairs<real, D, N, NG, 1>(dstb, srcb, side, lane);
+            else srl_pairs<real, D, N, NG, (D == 3 ? 2 : 1)>(dstb, srcb, side, lane);
+            return;
+        }
+    }
+    constexpr int ng = NG;
     // ghost box of this strip in dst-local coordinates
     int lo[3] = {0, 0, 0}, ext[3] = {N, N, D == 3 ? N : 1};
     lo[nd] = side ? N : -ng;
@@ -82,8 +145,6 @@ __global__ void __launch_bounds__(256) k_ghost(GhostArgs<real> a, Geom g) {
     }
     const int ncells = ext[0] * ext[1] * ext[2];
     const int total = ncells * g.V;
-    real *dstb = a.u + int64_t(e.dst) * g.bstride;
-    const real *srcb = e.src >= 0 ? a.u + int64_t(e.src) * g.bstride : nullptr;
     for (int idx = lane; idx < total; idx += 32) {
         int v = idx / ncells, c = idx - v * ncells;
         int x[3];

@@ -73,10 +73,15 @@ bool build_pattern(const Forest &F, Pattern &P, std::string &err) {
     for (int b = 0; b < nb; ++b) {
         P.info[b].level = F.leaves[b].lev;
         P.info[b].fixmask = 0;
-        for (int f = 0; f < 6; ++f) P.info[b].bslot[f] = -1;
+        for (int f = 0; f < 6; ++f) P.info[b].bslot[f] = P.info[b].nbr[f] = -1;
     }
+    std::vector<char> c2f_src(size_t(nb), 0);
+    for (const Entry &e : P.entries)
+        if (e.kind == KIND_C2F) c2f_src[size_t(e.src)] = 1;
     for (const Entry &e : P.entries) {
         (e.kind == KIND_C2F ? P.round2 : P.round1).push_back(e);
+        if (e.kind == KIND_SRL) P.info[e.dst].nbr[e.face] = e.src;
+        if (e.kind != KIND_C2F && (e.kind != KIND_SRL || c2f_src[size_t(e.dst)])) P.round1_gather.push_back(e);
         if (e.kind == KIND_F2C || e.kind == KIND_C2F) {
             int32_t &slot = P.info[e.dst].bslot[e.face];
             if (slot < 0) slot = P.n_slots++;

@@ -30,12 +30,17 @@ struct BlockInfo {
     int32_t level;
     int32_t fixmask;    // bit f: face f is the coarse side of a refinement face
     int32_t bslot[6];   // flux slot of face f, -1 if not a refinement face
+    int32_t nbr[6];     // same-level neighbour across face f, -1 if none
 };
 
 struct Pattern {
     std::vector<Entry> entries;   // canonical order (kind, face, dst, offset)
     std::vector<Entry> round1;    // SRL, F2C, BC
     std::vector<Entry> round2;    // C2F
+    // round 1 when the stage kernel gathers same-level halos itself: every
+    // non-SRL entry, plus the SRL entries of blocks that are the coarse
+    // source of a C2F entry (their ghosts feed the prolongation)
+    std::vector<Entry> round1_gather;
     std::vector<BlockInfo> info;  // per block
     std::vector<FixFace> fix;     // sorted by (block, face)
     std::vector<int32_t> fix_start;  // per fix-up block: first index into fix (+ sentinel)

@@ -6,12 +6,24 @@
 // Work decomposition (ours, not the paper's gang/collapse loops): one CTA per
 // (block, T x T column tile).  The CTA marches k through the block keeping a
 // ring of 5 planes of primitives (tile plus a 2-cell x/y halo, corners
-// excluded) in shared memory, so each cell is converted to primitives once
-// and each face flux is evaluated once.  The next plane is prefetched into
-// registers while the current plane's fluxes are computed.  The kernel also
-// stores the fluxes of refinement faces for flux fixing (Sec. 2.6) and, on
-// the last stage of a step, reduces the CFL limit of its output (Sec. 3.2).
-// 2D blocks are the single-plane case.
+// excluded) in shared memory, so each cell is converted to primitives once.
+// Per plane:
+//   phase A  every cell's limited face states along x and y (one minmod per
+//            variable and direction) into shared memory; the z face states of
+//            the cell above, in registers;
+//   phase B  every face flux once (x, y from the stored states, z in
+//            registers); the plane three ahead is converted and committed;
+//   phase C  divergence and Runge-Kutta combination, merged with phase A of
+//            the next plane.
+// Two barriers per plane.  Loads of the next plane are issued one phase
+// ahead.  Output rows are written whole (the x-ghost cells of the output
+// are overwritten with zeros) so that every DRAM sector is written
+// completely.  The kernel also stores the fluxes of refinement faces for
+// flux fixing (Sec. 2.6) and, on the last stage of a step, reduces the CFL
+// limit of its output (Sec. 3.2).  2D blocks are the single-plane case.
+//
+// FP32 uses the hardware reciprocal and reciprocal-square-root; FP64 uses
+// IEEE division and square root.
 #pragma once
 
 #include "common.cuh"
@@ -31,7 +43,31 @@ struct StageArgs {
     const BlockInfo *info;
     real *bflux;                 // [slot][V][N^(D-1)]
     int update_dt;
+    int gather;                  // halo cells across SRL faces from the neighbour's interior
     real gamma;
+};
+
+template <class real>
+struct FM;
+template <>
+struct FM<float> {
+    __device__ static __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
+    // sqrt(x) and 1/x for x > 0
+    __device__ static __forceinline__ void sqrt_inv(float x, float &s, float &inv) {
+        const float r = rsqrtf(x);
+        s = x * r;
+        inv = r * r;
+    }
+    __device__ static __forceinline__ float sqrtp(float x) { return x * rsqrtf(x); }   // x > 0
+};
+template <>
+struct FM<double> {
+    __device__ static __forceinline__ double rcp(double x) { return 1.0 / x; }
+    __device__ static __forceinline__ void sqrt_inv(double x, double &s, double &inv) {
+        s = sqrt(x);
+        inv = 1.0 / x;
+    }
+    __device__ static __forceinline__ double sqrtp(double x) { return sqrt(x); }
 };
 
 template <class real, int D>
@@ -41,7 +77,7 @@ struct Euler {
     // primitive (rho, v, p) from conservative (rho, rho v, E)
     __device__ static __forceinline__ void prim(const real *U, real *w, real gam) {
         const real rho = U[0];
-        const real ir = real(1) / rho;
+        const real ir = FM<real>::rcp(rho);
         real ke = real(0);
 #pragma unroll
         for (int d = 0; d < D; ++d) {
@@ -52,37 +88,48 @@ struct Euler {
         w[D + 1] = (gam - real(1)) * (U[D + 1] - real(0.5) * ke);
     }
 
-    // Rusanov flux along normal n (runtime) with the Einfeldt speed
-    // a = |u_roe| + d_roe (Einfeldt 1988, as cited in Sec. 3.5).
-    __device__ static __forceinline__ void flux(const real *wL, const real *wR, int n, real gam, real *F) {
-        real vnL = wL[1], vnR = wR[1];
-        if (D >= 2 && n == 1) { vnL = wL[2]; vnR = wR[2]; }
-        if (D == 3 && n == 2) { vnL = wL[3]; vnR = wR[3]; }
+    // Rusanov flux along normal n with the Einfeldt speed a = |u_roe| + d_roe
+    // (Einfeldt 1988, as cited in Sec. 3.5).  NRM >= 0: compile-time normal;
+    // NRM < 0: runtime normal n.
+    template <int NRM>
+    __device__ static __forceinline__ void flux(const real *wL, const real *wR, int n, real gam, real gm1i, real *F) {
+        const int nn = NRM >= 0 ? NRM : n;
+        real vnL, vnR;
+        if (NRM >= 0) {
+            vnL = wL[1 + (NRM >= 0 ? NRM : 0)];
+            vnR = wR[1 + (NRM >= 0 ? NRM : 0)];
+        } else {
+            vnL = nn == 0 ? wL[1] : (nn == 1 ? wL[2] : wL[D]);
+            vnR = nn == 0 ? wR[1] : (nn == 1 ? wR[2] : wR[D]);
+        }
         const real rL = wL[0], rR = wR[0], pL = wL[D + 1], pR = wR[D + 1];
+        real sL, iL, sR, iR;
+        FM<real>::sqrt_inv(rL, sL, iL);
+        FM<real>::sqrt_inv(rR, sR, iR);
+        const real inv = FM<real>::rcp(sL + sR);
+        const real c2L = gam * pL * iL, c2R = gam * pR * iR;
+        const real uroe = (sL * vnL + sR * vnR) * inv;
+        const real du = vnR - vnL;
+        const real d2 = (sL * c2L + sR * c2R) * inv + real(0.5) * sL * sR * inv * inv * du * du;
+        const real a = fabs(uroe) + FM<real>::sqrtp(d2);
         real v2L = real(0), v2R = real(0);
 #pragma unroll
         for (int d = 0; d < D; ++d) {
             v2L += wL[1 + d] * wL[1 + d];
             v2R += wR[1 + d] * wR[1 + d];
         }
-        const real gm1i = real(1) / (gam - real(1));
         const real EL = pL * gm1i + real(0.5) * rL * v2L;
         const real ER = pR * gm1i + real(0.5) * rR * v2R;
-        const real sL = sqrt(rL), sR = sqrt(rR);
-        const real inv = real(1) / (sL + sR);
-        const real uroe = (sL * vnL + sR * vnR) * inv;
-        const real du = vnR - vnL;
-        const real d2 = (sL * (gam * pL / rL) + sR * (gam * pR / rR)) * inv + real(0.5) * sL * sR * inv * inv * du * du;
-        const real a = fabs(uroe) + sqrt(d2);
+        const real ha = real(0.5) * a;
         const real mL = rL * vnL, mR = rR * vnR;
-        F[0] = real(0.5) * (mL + mR) - real(0.5) * a * (rR - rL);
+        F[0] = real(0.5) * (mL + mR) - ha * (rR - rL);
 #pragma unroll
         for (int d = 0; d < D; ++d) {
-            real fl = mL * wL[1 + d], fr = mR * wR[1 + d];
-            if (d == n) { fl += pL; fr += pR; }
-            F[1 + d] = real(0.5) * (fl + fr) - real(0.5) * a * (rR * wR[1 + d] - rL * wL[1 + d]);
+            real fl = mL * wL[1 + d] + mR * wR[1 + d];
+            if (d == nn) fl += pL + pR;
+            F[1 + d] = real(0.5) * fl - ha * (rR * wR[1 + d] - rL * wL[1 + d]);
         }
-        F[D + 1] = real(0.5) * ((EL + pL) * vnL + (ER + pR) * vnR) - real(0.5) * a * (ER - EL);
+        F[D + 1] = real(0.5) * ((EL + pL) * vnL + (ER + pR) * vnR) - ha * (ER - EL);
     }
 };
 
@@ -93,12 +140,17 @@ struct StageShape {
     static constexpr int R = (D == 3) ? 5 : 1;       // ring depth
     static constexpr int S = N + 2 * NG;
     static constexpr int NT = T * T;                 // threads
-    static constexpr int TILES = (N / T) * (N / T);  // column tiles per block
-    static constexpr int HALO_CELLS = T * P + 4 * T; // cells of a halo plane (corners excluded)
-    static constexpr int LOADS = (HALO_CELLS + NT - 1) / NT;
-    static constexpr int NFACE = T * (T + 1);
+    static constexpr int TILES = (D == 3) ? (N / T) * (N / T) : (N / T) * (N / T);
+    static constexpr int NFX = T * (T + 1);          // faces per direction and plane
+    static constexpr int NFS = T * (T + 2);          // cells with face states per direction and plane
+    static constexpr bool PAIRS = (NG == 2);         // 2-element vector loads (rows start on even elements)
+    static constexpr int HALO_PAIRS = P * P / 2;     // pairs of a halo plane incl. skipped corners
+    static constexpr int GHOST_PAIRS = T * T / 2;    // pairs of a z-ghost plane (tile only)
+    static constexpr int HALO_CELLS = T * P + 4 * T; // scalar path: cells of a halo plane
+    static constexpr int LOADS = PAIRS ? (HALO_PAIRS + NT - 1) / NT : (HALO_CELLS + NT - 1) / NT;
+    static constexpr int ITEMS = 2 * NFS;            // face-state work items per plane
     static constexpr size_t smem_bytes() {
-        return sizeof(real) * (size_t(R) * V * P * P + 2 * size_t(V) * NFACE);
+        return sizeof(real) * (size_t(R) * V * P * P + 4 * size_t(V) * NFS + 2 * size_t(V) * NFX);
     }
 };
 
@@ -106,13 +158,16 @@ template <class real, int D, int N, int NG, int T>
 __global__ void __launch_bounds__(T * T) k_stage(StageArgs<real> a, Geom g) {
     using Sh = StageShape<real, D, N, NG, T>;
     using E = Euler<real, D>;
-    constexpr int V = Sh::V, P = Sh::P, S = Sh::S, NT = Sh::NT;
+    using V2 = typename Vec2<real>::type;
+    constexpr int V = Sh::V, P = Sh::P, S = Sh::S, NT = Sh::NT, NFX = Sh::NFX, NFS = Sh::NFS;
     constexpr int64_t NC = (D == 3) ? int64_t(S) * S * S : int64_t(S) * S;
-    constexpr int NFACE = Sh::NFACE;
+    constexpr int PL = P * P;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    real *ring = reinterpret_cast<real *>(smem_raw);              // [R][V][P*P]
-    real *Fx = ring + Sh::R * V * P * P;                           // [V][T][T+1]
-    real *Fy = Fx + V * NFACE;                                     // [V][T+1][T]
+    real *ring = reinterpret_cast<real *>(smem_raw);          // [R][V][P*P]
+    real *FSm = ring + Sh::R * V * PL;                         // [2][V][NFS] minus states (x, y)
+    real *FSp = FSm + 2 * V * NFS;                             // [2][V][NFS] plus states
+    real *Fx = FSp + 2 * V * NFS;                              // [V][T][T+1]
+    real *Fy = Fx + V * NFX;                                   // [V][T+1][T]
 
     const int tid = threadIdx.x;
     const int b = blockIdx.x / Sh::TILES;
@@ -124,175 +179,266 @@ __global__ void __launch_bounds__(T * T) k_stage(StageArgs<real> a, Geom g) {
     const real idx0 = real(g.inv_dx[lev][0]), idx1 = real(g.inv_dx[lev][1]);
     const real idx2 = (D == 3) ? real(g.inv_dx[lev][2]) : real(0);
     const real gam = a.gamma;
+    const real gm1i = real(1) / (gam - real(1));
     const real dt_eff = real(a.w_dt * a.sc_in->dt);
-    const real *ub = a.deriv + int64_t(b) * V * NC;
+    const real *__restrict__ ub = a.deriv + int64_t(b) * V * NC;
+    // halo source: in gather mode a cell outside the block across a face with
+    // a same-level neighbour is read from that neighbour's interior
+    int nbr[6];
+#pragma unroll
+    for (int f = 0; f < 6; ++f) nbr[f] = a.gather ? info.nbr[f] : -1;
+    auto src_of = [&](int ii, int jj, int k, int64_t &o) -> const real * {
+        int gi = tx0 + ii, gj = ty0 + jj, gk = k, f = -1;
+        if (gi < 0) { f = 0; gi += N; }
+        else if (gi >= N) { f = 1; gi -= N; }
+        else if (gj < 0) { f = 2; gj += N; }
+        else if (gj >= N) { f = 3; gj -= N; }
+        else if (D == 3 && gk < 0) { f = 4; gk += N; }
+        else if (D == 3 && gk >= N) { f = 5; gk -= N; }
+        if (f >= 0 && nbr[f] >= 0) {
+            o = (int64_t(D == 3 ? gk + NG : 0) * S + (gj + NG)) * S + (gi + NG);
+            return a.deriv + int64_t(nbr[f]) * V * NC;
+        }
+        o = (int64_t(D == 3 ? k + NG : 0) * S + (ty0 + jj + NG)) * S + (tx0 + ii + NG);
+        return ub;
+    };
 
     bool nonphys = false;
     real vmax = real(0);
 
-    // cell c of a plane -> tile-relative (ii, jj); halo planes skip corners
-    auto plane_cell = [&](int c, bool halo, int &ii, int &jj) {
-        if (!halo) { ii = c % T; jj = c / T; return; }
-        if (c < T * P) { jj = c / P; ii = c % P - 2; return; }
+    auto gaddr = [&](int ii, int jj, int k) -> int64_t {
+        return (int64_t(D == 3 ? k + NG : 0) * S + (ty0 + jj + NG)) * S + (tx0 + ii + NG);
+    };
+    auto is_halo_plane = [&](int k) { return D == 2 || (k >= 0 && k < N); };
+    auto slot = [&](int k) -> real * { return ring + ((k + 2) % Sh::R) * V * PL; };
+
+    // ------------------------------------------------------ plane loading
+    // Pair path (NG = 2): a halo plane is P rows of P/2 pairs minus the 2x2
+    // corner regions; a z-ghost plane is the T x T tile.  Every pair starts
+    // on an even element, so 8- (float) or 16-byte (double) loads are aligned.
+    real pre[Sh::LOADS][2][V];
+    auto pair_of = [&](int p, bool halo, int &ii, int &jj) -> bool {
+        if (halo) {
+            if (p >= Sh::HALO_PAIRS) return false;
+            jj = p / (P / 2) - 2;
+            ii = 2 * (p % (P / 2)) - 2;
+            return !((jj < 0 || jj >= T) && (ii < 0 || ii >= T));
+        }
+        if (p >= Sh::GHOST_PAIRS) return false;
+        jj = p / (T / 2);
+        ii = 2 * (p % (T / 2));
+        return true;
+    };
+    auto scalar_cell = [&](int c, bool halo, int &ii, int &jj) -> bool {
+        if (!halo) {
+            if (c >= T * T) return false;
+            ii = c % T;
+            jj = c / T;
+            return true;
+        }
+        if (c >= Sh::HALO_CELLS) return false;
+        if (c < T * P) {
+            jj = c / P;
+            ii = c % P - 2;
+            return true;
+        }
         c -= T * P;
         const int r = c / T;
         ii = c % T;
         jj = (r < 2) ? r - 2 : T + r - 2;
+        return true;
     };
-    auto gaddr = [&](int ii, int jj, int k) -> int64_t {
-        return (int64_t(D == 3 ? k + NG : 0) * S + (ty0 + jj + NG)) * S + (tx0 + ii + NG);
-    };
-    // plane k has an x/y halo iff it is an interior plane (z-ghost planes only
-    // feed the z stencil of the tile itself)
-    auto is_halo_plane = [&](int k) { return D == 2 || (k >= 0 && k < N); };
-
-    real pre[Sh::LOADS][V];
     auto prefetch = [&](int k) {
         const bool halo = is_halo_plane(k);
-        const int ncells = halo ? Sh::HALO_CELLS : T * T;
 #pragma unroll
         for (int l = 0; l < Sh::LOADS; ++l) {
-            const int c = tid + l * NT;
-            if (c < ncells) {
-                int ii, jj;
-                plane_cell(c, halo, ii, jj);
-                const int64_t o = gaddr(ii, jj, k);
+            int ii, jj;
+            if (Sh::PAIRS) {
+                if (pair_of(tid + l * NT, halo, ii, jj)) {
+                    int64_t o;
+                    const real *src = src_of(ii, jj, k, o);
 #pragma unroll
-                for (int v = 0; v < V; ++v) pre[l][v] = ub[v * NC + o];
+                    for (int v = 0; v < V; ++v) {
+                        const V2 x = *reinterpret_cast<const V2 *>(src + v * NC + o);
+                        pre[l][0][v] = x.x;
+                        pre[l][1][v] = x.y;
+                    }
+                }
+            } else if (scalar_cell(tid + l * NT, halo, ii, jj)) {
+                int64_t o;
+                const real *src = src_of(ii, jj, k, o);
+#pragma unroll
+                for (int v = 0; v < V; ++v) pre[l][0][v] = src[v * NC + o];
             }
         }
     };
     auto commit = [&](int k) {
-        real *pl = ring + ((k + 2) % Sh::R) * V * P * P;
+        real *pl = slot(k);
         const bool halo = is_halo_plane(k);
-        const int ncells = halo ? Sh::HALO_CELLS : T * T;
 #pragma unroll
         for (int l = 0; l < Sh::LOADS; ++l) {
-            const int c = tid + l * NT;
-            if (c < ncells) {
-                int ii, jj;
-                plane_cell(c, halo, ii, jj);
-                real w[V];
-                E::prim(pre[l], w, gam);
-                nonphys |= !(w[0] > real(0)) || !(w[D + 1] > real(0));
-                const int o = (jj + 2) * P + (ii + 2);
+            int ii, jj;
+            const bool ok = Sh::PAIRS ? pair_of(tid + l * NT, halo, ii, jj) : scalar_cell(tid + l * NT, halo, ii, jj);
+            if (!ok) continue;
+            const int o = (jj + 2) * P + (ii + 2);
 #pragma unroll
-                for (int v = 0; v < V; ++v) pl[v * P * P + o] = w[v];
+            for (int e = 0; e < (Sh::PAIRS ? 2 : 1); ++e) {
+                real w[V];
+                E::prim(pre[l][e], w, gam);
+                nonphys |= !(w[0] > real(0)) || !(w[D + 1] > real(0));
+#pragma unroll
+                for (int v = 0; v < V; ++v) pl[v * PL + o + e] = w[v];
             }
         }
     };
-    // flux through the face between cells c-1 and c along n, reading the
-    // primitive stencil (c-2, c-1, c, c+1) at stride st from plane pointers
-    auto face = [&](const real *p0, const real *p1, const real *p2, const real *p3, int st, int n, real *F) {
-        real wL[V], wR[V];
+
+    // ------------------------------------------------------ phase A: states
+    // item q < NFS: x states of cell (q % (T+2) - 1, q / (T+2));
+    // item q >= NFS: y states of cell (q' % T, q' / T - 1), q' = q - NFS.
+    auto face_states = [&](int k) {
+        const real *pl = slot(k);
+        for (int q = tid; q < Sh::ITEMS; q += NT) {
+            const int dir = q >= NFS;
+            const int qq = q - dir * NFS;
+            int ii, jj, st;
+            if (!dir) {
+                jj = qq / (T + 2);
+                ii = qq - jj * (T + 2) - 1;
+                st = 1;
+            } else {
+                jj = qq / T - 1;
+                ii = qq % T;
+                st = P;
+            }
+            const int c = (jj + 2) * P + (ii + 2);
+            bool bad = false;
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const real w0 = pl[v * PL + c], wm = pl[v * PL + c - st], wp = pl[v * PL + c + st];
+                const real hs = real(0.5) * minmod<real>(w0 - wm, wp - w0);
+                const real lo = w0 - hs, hi = w0 + hs;
+                if (v == 0 || v == D + 1) bad |= !(lo > real(0)) || !(hi > real(0));
+                FSm[(dir * V + v) * NFS + qq] = lo;
+                FSp[(dir * V + v) * NFS + qq] = hi;
+            }
+            nonphys |= bad;
+        }
+    };
+    // z face states of cell (ti, tj, kz) from planes kz-1, kz, kz+1
+    auto z_states = [&](int kz, real *zm, real *zp) {
+        const int c = (tj + 2) * P + (ti + 2);
+        const real *p0 = slot(kz - 1), *p1 = slot(kz), *p2 = slot(kz + 1);
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            const int o = v * P * P;
-            const real a0 = p0[o], a1 = p1[o + st], a2 = p2[o + 2 * st], a3 = p3[o + 3 * st];
-            wL[v] = a1 + real(0.5) * minmod<real>(a1 - a0, a2 - a1);
-            wR[v] = a2 - real(0.5) * minmod<real>(a2 - a1, a3 - a2);
+            const real w0 = p1[v * PL + c], wm = p0[v * PL + c], wp = p2[v * PL + c];
+            const real hs = real(0.5) * minmod<real>(w0 - wm, wp - w0);
+            zm[v] = w0 - hs;
+            zp[v] = w0 + hs;
         }
-        nonphys |= !(wL[0] > real(0)) || !(wL[D + 1] > real(0)) || !(wR[0] > real(0)) || !(wR[D + 1] > real(0));
-        E::flux(wL, wR, n, gam, F);
+        nonphys |= !(zm[0] > real(0)) || !(zp[0] > real(0)) || !(zm[D + 1] > real(0)) || !(zp[D + 1] > real(0));
     };
-    // x- or y-face q of the current plane into Fx / Fy
-    auto xy_face = [&](const real *pl, int q, int n) {
-        real F[V];
-        if (n == 0) {
-            const int jj = q / (T + 1), fi = q - jj * (T + 1);
-            const real *p = pl + (jj + 2) * P + fi;          // cell fi-2
-            face(p, p, p, p, 1, 0, F);
-#pragma unroll
-            for (int v = 0; v < V; ++v) Fx[v * NFACE + jj * (T + 1) + fi] = F[v];
-        } else {
-            const int fj = q / T, ii = q - fj * T;
-            const real *p = pl + fj * P + ii + 2;            // cell (ii, fj-2)
-            face(p, p, p, p, P, 1, F);
-#pragma unroll
-            for (int v = 0; v < V; ++v) Fy[v * NFACE + fj * T + ii] = F[v];
-        }
-    };
+
     const int nface_b = (D == 3) ? N * N : N;
     auto store_bflux = [&](int f, int t, const real *F) {
-        const int slot = info.bslot[f];
-        if (slot < 0) return;
-        real *dst = a.bflux + int64_t(slot) * V * nface_b + t;
+        const int sl = info.bslot[f];
+        if (sl < 0) return;
+        real *dst = a.bflux + int64_t(sl) * V * nface_b + t;
 #pragma unroll
         for (int v = 0; v < V; ++v) dst[v * nface_b] = F[v];
     };
 
-    // ---- prologue: planes -2 .. 2 (3D) or the single plane (2D)
-    real Fz_lo[V];
-    if (D == 3) {
-        for (int k = -2; k <= 2; ++k) { prefetch(k); commit(k); }
-    } else {
-        prefetch(0);
-        commit(0);
-    }
-    __syncthreads();
-    if (D == 3) {
-        const real *c0 = ring + ((-2 + 2) % 5) * V * P * P + (tj + 2) * P + ti + 2;
-        const real *c1 = ring + ((-1 + 2) % 5) * V * P * P + (tj + 2) * P + ti + 2;
-        const real *c2 = ring + ((0 + 2) % 5) * V * P * P + (tj + 2) * P + ti + 2;
-        const real *c3 = ring + ((1 + 2) % 5) * V * P * P + (tj + 2) * P + ti + 2;
-        face(c0, c1 - 1, c2 - 2, c3 - 3, 1, 2, Fz_lo);
-        store_bflux(4, tx0 + ti + N * (ty0 + tj), Fz_lo);
-    }
-
-    const int nk = (D == 3) ? N : 1;
-    for (int k = 0; k < nk; ++k) {
-        if (D == 3 && k + 3 <= N + 1) prefetch(k + 3);
-        const real *pl = ring + ((k + 2) % Sh::R) * V * P * P;
-        xy_face(pl, tid, 0);
-        xy_face(pl, tid, 1);
-        if (tid < 2 * T) xy_face(pl, NT + (tid % T), tid < T ? 0 : 1);
-        real Fz_hi[V];
-        if (D == 3) {
-            const int base = (tj + 2) * P + ti + 2;
-            const real *c0 = ring + ((k - 1 + 2) % 5) * V * P * P + base;
-            const real *c1 = ring + ((k + 0 + 2) % 5) * V * P * P + base;
-            const real *c2 = ring + ((k + 1 + 2) % 5) * V * P * P + base;
-            const real *c3 = ring + ((k + 2 + 2) % 5) * V * P * P + base;
-            face(c0, c1 - 1, c2 - 2, c3 - 3, 1, 2, Fz_hi);
-            if (k == N - 1) store_bflux(5, tx0 + ti + N * (ty0 + tj), Fz_hi);
+    // ------------------------------------------------------ phase B: fluxes
+    auto x_face = [&](int q, int k) {
+        const int jj = q / (T + 1), fi = q - jj * (T + 1);
+        real wL[V], wR[V], F[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            wL[v] = FSp[v * NFS + jj * (T + 2) + fi];
+            wR[v] = FSm[v * NFS + jj * (T + 2) + fi + 1];
         }
-        if (D == 3 && k + 3 <= N + 1) commit(k + 3);
-        __syncthreads();
+        E::template flux<0>(wL, wR, 0, gam, gm1i, F);
+#pragma unroll
+        for (int v = 0; v < V; ++v) Fx[v * NFX + q] = F[v];
+        if (fi == 0 && tx0 == 0) store_bflux(0, ty0 + jj + N * k, F);
+        if (fi == T && tx0 + T == N) store_bflux(1, ty0 + jj + N * k, F);
+    };
+    auto y_face = [&](int q, int k) {
+        const int fj = q / T, ii = q - fj * T;
+        real wL[V], wR[V], F[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            wL[v] = FSp[(V + v) * NFS + fj * T + ii];
+            wR[v] = FSm[(V + v) * NFS + (fj + 1) * T + ii];
+        }
+        E::template flux<1>(wL, wR, 1, gam, gm1i, F);
+#pragma unroll
+        for (int v = 0; v < V; ++v) Fy[v * NFX + q] = F[v];
+        if (fj == 0 && ty0 == 0) store_bflux(2, tx0 + ii + N * k, F);
+        if (fj == T && ty0 + T == N) store_bflux(3, tx0 + ii + N * k, F);
+    };
+    // the 2T faces left over after T*T threads took one x- and one y-face:
+    // lanes < T take an x-face, the others a y-face (runtime normal, so the
+    // warp does not split into two flux evaluations)
+    auto extra_face = [&](int k) {
+        const int dir = tid >= T;
+        const int q = NT + (dir ? tid - T : tid);
+        int iL, iR, fa, fb;
+        if (!dir) {
+            const int jj = q / (T + 1), fi = q - jj * (T + 1);
+            iL = jj * (T + 2) + fi;
+            iR = iL + 1;
+            fa = fi;
+            fb = jj;
+        } else {
+            const int fj = q / T, ii = q - fj * T;
+            iL = fj * T + ii;
+            iR = iL + T;
+            fa = fj;
+            fb = ii;
+        }
+        real wL[V], wR[V], F[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            wL[v] = FSp[(dir * V + v) * NFS + iL];
+            wR[v] = FSm[(dir * V + v) * NFS + iR];
+        }
+        E::template flux<-1>(wL, wR, dir, gam, gm1i, F);
+        real *Fd = dir ? Fy : Fx;
+#pragma unroll
+        for (int v = 0; v < V; ++v) Fd[v * NFX + q] = F[v];
+        // the leftover faces are the last x row / y row of the tile
+        if (!dir) {
+            if (fa == 0 && tx0 == 0) store_bflux(0, ty0 + fb + N * k, F);
+            if (fa == T && tx0 + T == N) store_bflux(1, ty0 + fb + N * k, F);
+        } else {
+            if (fa == 0 && ty0 == 0) store_bflux(2, tx0 + fb + N * k, F);
+            if (fa == T && ty0 + T == N) store_bflux(3, tx0 + fb + N * k, F);
+        }
+    };
 
-        // ---- divergence and Runge-Kutta combination for cell (ti, tj, k)
+    // ------------------------------------------------------ phase C: update
+    real Fz_lo[V], Fz_hi[V];
+    auto update = [&](int k) {
         const int64_t o = gaddr(ti, tj, k);
         const int64_t ob = int64_t(b) * V * NC + o;
         real U[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            real du = (Fx[v * NFACE + tj * (T + 1) + ti] - Fx[v * NFACE + tj * (T + 1) + ti + 1]) * idx0 +
-                      (Fy[v * NFACE + tj * T + ti] - Fy[v * NFACE + (tj + 1) * T + ti]) * idx1;
+            real du = (Fx[v * NFX + tj * (T + 1) + ti] - Fx[v * NFX + tj * (T + 1) + ti + 1]) * idx0 +
+                      (Fy[v * NFX + tj * T + ti] - Fy[v * NFX + (tj + 1) * T + ti]) * idx1;
             if (D == 3) du += (Fz_lo[v] - Fz_hi[v]) * idx2;
             real acc = real(0);
             for (int q = 0; q < a.nprev; ++q) acc += a.wprev[q] * a.prev[q][ob + v * NC];
             U[v] = dt_eff * du + acc;
             a.out[ob + v * NC] = U[v];
         }
-        // refinement-face fluxes of the tile's x/y block edges
-        {
-            const int gj = ty0 + tj, gi = tx0 + ti;
-            real F[V];
-            if (tx0 + ti == 0) {
-                for (int v = 0; v < V; ++v) F[v] = Fx[v * NFACE + tj * (T + 1)];
-                store_bflux(0, gj + N * k, F);
-            }
-            if (tx0 + ti == N - 1) {
-                for (int v = 0; v < V; ++v) F[v] = Fx[v * NFACE + tj * (T + 1) + T];
-                store_bflux(1, gj + N * k, F);
-            }
-            if (ty0 + tj == 0) {
-                for (int v = 0; v < V; ++v) F[v] = Fy[v * NFACE + ti];
-                store_bflux(2, gi + N * k, F);
-            }
-            if (ty0 + tj == N - 1) {
-                for (int v = 0; v < V; ++v) F[v] = Fy[v * NFACE + T * T + ti];
-                store_bflux(3, gi + N * k, F);
-            }
+        // complete the row's DRAM sectors: the output's x-ghost cells
+        if (tx0 + ti == 0 || tx0 + ti == N - 1) {
+            const int64_t og = ob + (tx0 + ti == 0 ? -NG : 1);
+#pragma unroll
+            for (int v = 0; v < V; ++v)
+#pragma unroll
+                for (int e = 0; e < NG; ++e) a.out[og + v * NC + e] = real(0);
         }
         if (a.update_dt) {
             // CFL limit of the new state; cells next to a coarse-side
@@ -305,17 +451,70 @@ __global__ void __launch_bounds__(T * T) k_stage(StageArgs<real> a, Geom g) {
             if (!fixed) {
                 real w[V];
                 E::prim(U, w, gam);
-                const real c = sqrt(gam * w[D + 1] / w[0]);
+                const real c = FM<real>::sqrtp(gam * w[D + 1] * FM<real>::rcp(w[0]));
                 real s = (fabs(w[1]) + c) * idx0 + (fabs(w[2]) + c) * idx1;
                 if (D == 3) s += (fabs(w[3]) + c) * idx2;
                 vmax = s > vmax ? s : vmax;
             }
         }
-        if (D == 3) {
-#pragma unroll
-            for (int v = 0; v < V; ++v) Fz_lo[v] = Fz_hi[v];
+    };
+
+    // ------------------------------------------------------ the march
+    if (D == 3) {
+        for (int k = -2; k <= 2; ++k) {
+            prefetch(k);
+            commit(k);
         }
         __syncthreads();
+        {
+            real zm[V], zp[V], pm1[V];
+            z_states(-1, zm, pm1);          // plus state of cell -1
+            z_states(0, zm, zp);            // minus / plus states of cell 0
+            E::template flux<2>(pm1, zm, 2, gam, gm1i, Fz_lo);
+            store_bflux(4, tx0 + ti + N * (ty0 + tj), Fz_lo);
+#pragma unroll
+            for (int v = 0; v < V; ++v) Fz_hi[v] = zp[v];     // carries plus(0) into the loop
+        }
+        real zplus[V], zm1[V], zp1[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) zplus[v] = Fz_hi[v];
+        prefetch(3);
+        face_states(0);
+        z_states(1, zm1, zp1);
+        __syncthreads();
+        for (int k = 0; k < N; ++k) {
+            // phase B
+            x_face(tid, k);
+            y_face(tid, k);
+            if (tid < 2 * T) extra_face(k);
+            E::template flux<2>(zplus, zm1, 2, gam, gm1i, Fz_hi);
+            if (k == N - 1) store_bflux(5, tx0 + ti + N * (ty0 + tj), Fz_hi);
+#pragma unroll
+            for (int v = 0; v < V; ++v) zplus[v] = zp1[v];
+            if (k + 3 <= N + 1) commit(k + 3);
+            __syncthreads();
+            // phase C (plane k) + phase A (plane k + 1)
+            if (k + 1 < N && k + 4 <= N + 1) prefetch(k + 4);
+            update(k);
+#pragma unroll
+            for (int v = 0; v < V; ++v) Fz_lo[v] = Fz_hi[v];
+            if (k + 1 < N) {
+                face_states(k + 1);
+                z_states(k + 2, zm1, zp1);
+            }
+            __syncthreads();
+        }
+    } else {
+        prefetch(0);
+        commit(0);
+        __syncthreads();
+        face_states(0);
+        __syncthreads();
+        x_face(tid, 0);
+        y_face(tid, 0);
+        if (tid < 2 * T) extra_face(0);
+        __syncthreads();
+        update(0);
     }
 
     // ---- CTA reductions: max speed and non-physical flag
