@@ -7,7 +7,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <cstdlib>
 #include <new>
+#include <type_traits>
 #include <string>
 #include <vector>
 
@@ -18,6 +20,7 @@
 #include "misc.cuh"
 #include "pattern.hpp"
 #include "stage.cuh"
+#include "stage_pair.cuh"
 
 using namespace amrb;
 
@@ -45,6 +48,7 @@ struct amr_forest {
     uint64_t graph_rev = ~0ull;
     int64_t graph_nodes = 0;
     int graph_flags = -1;
+    bool scalar_stage = false;   // force the per-cell FP32 kernel (AMR_SCALAR_STAGE=1)
     bool capturing = false;
     int64_t launches = 0;
     std::string err;
@@ -238,9 +242,35 @@ amr_status launch_stage_t(amr_forest *f, const StageArgs<real> &a, cudaStream_t 
     return AMR_OK;
 }
 
+// FP32, 3D, two ghost layers: the packed cell-pair kernel
+template <int N>
+amr_status launch_stage_pair(amr_forest *f, const StageArgs<float> &a, cudaStream_t st) {
+    using Sh = PairShape<N>;
+    static bool attr_done = false;
+    const size_t smem = Sh::smem_bytes();
+    if (!attr_done) {
+        CU(cudaFuncSetAttribute(k_stage_pair<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        attr_done = true;
+    }
+    const int64_t grid = nblocks(f) * Sh::TILES;
+    if (grid > 0) {
+        k_stage_pair<N><<<unsigned(grid), Sh::NT, smem, st>>>(a, f->geom);
+        ++f->launches;
+    }
+    CU(cudaGetLastError());
+    return AMR_OK;
+}
+
 template <class real, int D>
 amr_status launch_stage(amr_forest *f, const StageArgs<real> &a, cudaStream_t st) {
     const int N = f->cfg.block_n, NG = f->cfg.n_ghost;
+    if constexpr (std::is_same<real, float>::value && D == 3) {
+        if (NG == 2 && !f->scalar_stage) {
+            if (N == 8) return launch_stage_pair<8>(f, a, st);
+            if (N == 16) return launch_stage_pair<16>(f, a, st);
+            if (N == 32) return launch_stage_pair<32>(f, a, st);
+        }
+    }
 #define AMR_STAGE_CASE(n_, g_) \
     if (N == n_ && NG == g_) return launch_stage_t<real, D, n_, g_>(f, a, st);
     AMR_STAGE_CASE(8, 2)
@@ -411,6 +441,7 @@ amr_status amr_create_forest(const amr_config *cfg, int init_level, amr_forest *
     if (!f) return AMR_ENOMEM;
     f->cfg = *cfg;
     f->esize = cfg->precision / 8;
+    if (const char *e = std::getenv("AMR_SCALAR_STAGE")) f->scalar_stage = e[0] == '1';
     fill_geom(f);
     f->block_bytes = size_t(f->geom.bstride) * f->esize;
     Geometry G;

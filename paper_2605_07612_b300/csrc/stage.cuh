@@ -184,20 +184,21 @@ __global__ void __launch_bounds__(T * T) k_stage(StageArgs<real> a, Geom g) {
     const real *__restrict__ ub = a.deriv + int64_t(b) * V * NC;
     // halo source: in gather mode a cell outside the block across a face with
     // a same-level neighbour is read from that neighbour's interior
-    int nbr[6];
-#pragma unroll
-    for (int f = 0; f < 6; ++f) nbr[f] = a.gather ? info.nbr[f] : -1;
+    // same-level neighbours (scalars: a runtime-indexed array would live in local memory)
+    const int nb0 = a.gather ? info.nbr[0] : -1, nb1 = a.gather ? info.nbr[1] : -1;
+    const int nb2 = a.gather ? info.nbr[2] : -1, nb3 = a.gather ? info.nbr[3] : -1;
+    const int nb4 = a.gather ? info.nbr[4] : -1, nb5 = a.gather ? info.nbr[5] : -1;
     auto src_of = [&](int ii, int jj, int k, int64_t &o) -> const real * {
-        int gi = tx0 + ii, gj = ty0 + jj, gk = k, f = -1;
-        if (gi < 0) { f = 0; gi += N; }
-        else if (gi >= N) { f = 1; gi -= N; }
-        else if (gj < 0) { f = 2; gj += N; }
-        else if (gj >= N) { f = 3; gj -= N; }
-        else if (D == 3 && gk < 0) { f = 4; gk += N; }
-        else if (D == 3 && gk >= N) { f = 5; gk -= N; }
-        if (f >= 0 && nbr[f] >= 0) {
+        int gi = tx0 + ii, gj = ty0 + jj, gk = k, nb = -1;
+        if (gi < 0) { nb = nb0; gi += N; }
+        else if (gi >= N) { nb = nb1; gi -= N; }
+        else if (gj < 0) { nb = nb2; gj += N; }
+        else if (gj >= N) { nb = nb3; gj -= N; }
+        else if (D == 3 && gk < 0) { nb = nb4; gk += N; }
+        else if (D == 3 && gk >= N) { nb = nb5; gk -= N; }
+        if (nb >= 0) {
             o = (int64_t(D == 3 ? gk + NG : 0) * S + (gj + NG)) * S + (gi + NG);
-            return a.deriv + int64_t(nbr[f]) * V * NC;
+            return a.deriv + int64_t(nb) * V * NC;
         }
         o = (int64_t(D == 3 ? k + NG : 0) * S + (ty0 + jj + NG)) * S + (tx0 + ii + NG);
         return ub;
@@ -428,7 +429,9 @@ __global__ void __launch_bounds__(T * T) k_stage(StageArgs<real> a, Geom g) {
                       (Fy[v * NFX + tj * T + ti] - Fy[v * NFX + (tj + 1) * T + ti]) * idx1;
             if (D == 3) du += (Fz_lo[v] - Fz_hi[v]) * idx2;
             real acc = real(0);
-            for (int q = 0; q < a.nprev; ++q) acc += a.wprev[q] * a.prev[q][ob + v * NC];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (q < a.nprev) acc += a.wprev[q] * a.prev[q][ob + v * NC];
             U[v] = dt_eff * du + acc;
             a.out[ob + v * NC] = U[v];
         }

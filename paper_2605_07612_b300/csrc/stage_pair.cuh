@@ -1,0 +1,427 @@
+// FP32 stage kernel for 2 ghost layers: the same computation as k_stage
+// (Sec. 3.1-3.5, Eq. 4), organised so that every thread owns two cells that
+// are neighbours along x.  All arithmetic on such a pair runs as packed
+// two-wide FP32 instructions (add/mul/fma .f32x2 of sm_100-class GPUs), and
+// every shared- and global-memory access of a pair is one aligned 8-byte
+// access.
+//
+// One CTA per (block, T x T column tile), T = min(N, 16), T*T/2 threads
+// (128 for T = 16); thread (ip, tj) owns
+// cells (2ip, 2ip+1) of row tj.  The CTA marches k with a 5-plane ring of
+// primitive variables in shared memory.  One barrier per plane:
+//   [update of plane k-1 | fluxes of plane k | commit of plane k+3] barrier
+// with the face fluxes double-buffered between consecutive planes.  Face
+// states (MUSCL with minmod) are formed in the flux phase from the ring: an
+// x-face pair reads three aligned pairs of a row, a y- or z-face pair four.
+// The T x-faces and T y-faces left over at the tile's upper edges are taken
+// by T threads of the first warp.
+#pragma once
+
+#include "stage.cuh"
+
+namespace amrb {
+
+struct PF {
+    __device__ static __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
+    __device__ static __forceinline__ float2 sp(float a) { return make_float2(a, a); }
+    __device__ static __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+    __device__ static __forceinline__ float2 sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+    __device__ static __forceinline__ float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+    __device__ static __forceinline__ float2 fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+    __device__ static __forceinline__ float2 rsqrt(float2 a) { return make_float2(rsqrtf(a.x), rsqrtf(a.y)); }
+    __device__ static __forceinline__ float2 rcp(float2 a) { return make_float2(__fdividef(1.f, a.x), __fdividef(1.f, a.y)); }
+    __device__ static __forceinline__ float2 abs(float2 a) { return make_float2(fabsf(a.x), fabsf(a.y)); }
+    // 0.5 * minmod(a, b): (sign a + sign b) / 4 * min(|a|, |b|) -- zero unless
+    // both have the same strict sign (a zero gives min 0)
+    __device__ static __forceinline__ float2 half_minmod(float2 a, float2 b) {
+        const float2 s = add(make_float2(copysignf(1.f, a.x), copysignf(1.f, a.y)),
+                             make_float2(copysignf(1.f, b.x), copysignf(1.f, b.y)));
+        const float2 m = make_float2(fminf(fabsf(a.x), fabsf(b.x)), fminf(fabsf(a.y), fabsf(b.y)));
+        return mul(mul(s, m), sp(0.25f));
+    }
+    __device__ static __forceinline__ bool positive(float2 a) { return a.x > 0.f && a.y > 0.f; }
+};
+
+constexpr int kPairV = 5;   // 3D Euler variables
+
+// Rusanov / Einfeldt flux of a pair of faces with the same normal n
+// (compile-time NRM >= 0, or runtime n when NRM < 0).
+template <int NRM>
+__device__ __forceinline__ void pair_flux(const float2 *wL, const float2 *wR, int n, float gam, float gm1i, float2 *F) {
+    const int nn = NRM >= 0 ? NRM : n;
+    float2 vnL, vnR;
+    if (NRM >= 0) {
+        vnL = wL[1 + (NRM >= 0 ? NRM : 0)];
+        vnR = wR[1 + (NRM >= 0 ? NRM : 0)];
+    } else {
+        vnL = nn == 0 ? wL[1] : (nn == 1 ? wL[2] : wL[3]);
+        vnR = nn == 0 ? wR[1] : (nn == 1 ? wR[2] : wR[3]);
+    }
+    const float2 rL = wL[0], rR = wR[0], pL = wL[4], pR = wR[4];
+    const float2 qL = PF::rsqrt(rL), qR = PF::rsqrt(rR);
+    const float2 sL = PF::mul(rL, qL), sR = PF::mul(rR, qR);            // sqrt(rho)
+    const float2 iL = PF::mul(qL, qL), iR = PF::mul(qR, qR);            // 1 / rho
+    const float2 inv = PF::rcp(PF::add(sL, sR));
+    const float2 g2 = PF::sp(gam);
+    const float2 c2L = PF::mul(PF::mul(g2, pL), iL), c2R = PF::mul(PF::mul(g2, pR), iR);
+    const float2 uroe = PF::mul(PF::fma(sL, vnL, PF::mul(sR, vnR)), inv);
+    const float2 du = PF::sub(vnR, vnL);
+    const float2 h = PF::mul(PF::mul(PF::mul(sL, sR), PF::mul(inv, inv)), PF::sp(0.5f));
+    const float2 d2 = PF::fma(PF::mul(h, du), du, PF::mul(PF::fma(sL, c2L, PF::mul(sR, c2R)), inv));
+    const float2 d = PF::mul(d2, PF::rsqrt(d2));
+    const float2 a = PF::add(PF::abs(uroe), d);
+    float2 v2L = PF::mul(wL[1], wL[1]), v2R = PF::mul(wR[1], wR[1]);
+    v2L = PF::fma(wL[2], wL[2], v2L);
+    v2R = PF::fma(wR[2], wR[2], v2R);
+    v2L = PF::fma(wL[3], wL[3], v2L);
+    v2R = PF::fma(wR[3], wR[3], v2R);
+    const float2 half = PF::sp(0.5f);
+    const float2 EL = PF::fma(pL, PF::sp(gm1i), PF::mul(PF::mul(half, rL), v2L));
+    const float2 ER = PF::fma(pR, PF::sp(gm1i), PF::mul(PF::mul(half, rR), v2R));
+    const float2 nha = PF::mul(a, PF::sp(-0.5f));
+    const float2 mL = PF::mul(rL, vnL), mR = PF::mul(rR, vnR);
+    F[0] = PF::fma(nha, PF::sub(rR, rL), PF::mul(half, PF::add(mL, mR)));
+#pragma unroll
+    for (int d3 = 0; d3 < 3; ++d3) {
+        float2 fl = PF::fma(mL, wL[1 + d3], PF::mul(mR, wR[1 + d3]));
+        if (d3 == nn) fl = PF::add(fl, PF::add(pL, pR));
+        const float2 jump = PF::sub(PF::mul(rR, wR[1 + d3]), PF::mul(rL, wL[1 + d3]));
+        F[1 + d3] = PF::fma(nha, jump, PF::mul(half, fl));
+    }
+    const float2 fe = PF::fma(PF::add(EL, pL), vnL, PF::mul(PF::add(ER, pR), vnR));
+    F[4] = PF::fma(nha, PF::sub(ER, EL), PF::mul(half, fe));
+}
+
+// face states of a pair of faces from the four pairs of cells around them
+// (c-2, c-1, c, c+1 along the face normal)
+__device__ __forceinline__ void pair_states(float2 w0, float2 w1, float2 w2, float2 w3, float2 &L, float2 &R) {
+    L = PF::add(w1, PF::half_minmod(PF::sub(w1, w0), PF::sub(w2, w1)));
+    R = PF::sub(w2, PF::half_minmod(PF::sub(w2, w1), PF::sub(w3, w2)));
+}
+
+// conservative -> primitive for a pair of cells
+__device__ __forceinline__ void pair_prim(const float2 *U, float2 *w, float gam) {
+    const float2 ir = PF::rcp(U[0]);
+    w[0] = U[0];
+    w[1] = PF::mul(U[1], ir);
+    w[2] = PF::mul(U[2], ir);
+    w[3] = PF::mul(U[3], ir);
+    float2 ke = PF::mul(w[1], U[1]);
+    ke = PF::fma(w[2], U[2], ke);
+    ke = PF::fma(w[3], U[3], ke);
+    w[4] = PF::mul(PF::sp(gam - 1.f), PF::fma(ke, PF::sp(-0.5f), U[4]));
+}
+
+template <int N>
+struct PairShape {
+    static constexpr int T = N < 16 ? N : 16, NG = 2, S = N + 2 * NG, P = T + 4, PL = P * P, R = 5, V = 5;
+    static constexpr int NT = T * T / 2;              // threads: one per cell pair of a plane
+    static constexpr int TILES = (N / T) * (N / T);
+    static constexpr int FXP = T + 2;                 // x-flux row pitch (17 faces + pad)
+    static constexpr int NFX = T * FXP;
+    static constexpr int NFY = (T + 1) * T;
+    static constexpr int FBUF = V * (NFX + NFY);      // one flux buffer
+    static constexpr int HALO_PAIRS = P * P / 2;
+    static constexpr int GHOST_PAIRS = T * T / 2;
+    static constexpr int LOADS = (HALO_PAIRS + NT - 1) / NT;
+    static constexpr size_t smem_bytes() { return sizeof(float) * (size_t(R) * V * PL + 2 * size_t(FBUF)); }
+};
+
+template <int N>
+__global__ void __launch_bounds__(PairShape<N>::NT) k_stage_pair(StageArgs<float> a, Geom g) {
+    using Sh = PairShape<N>;
+    constexpr int T = Sh::T, NG = Sh::NG, S = Sh::S, P = Sh::P, PL = Sh::PL, V = Sh::V, NT = Sh::NT;
+    constexpr int FXP = Sh::FXP, NFX = Sh::NFX, FBUF = Sh::FBUF;
+    constexpr int64_t NC = int64_t(S) * S * S;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *ring = reinterpret_cast<float *>(smem_raw);         // [R][V][P*P]
+    float *fbuf = ring + Sh::R * V * PL;                        // [2][FBUF]: Fx [V][T][FXP], Fy [V][T+1][T]
+
+    const int tid = threadIdx.x;
+    const int b = blockIdx.x / Sh::TILES;
+    const int tile = blockIdx.x - b * Sh::TILES;
+    const int tx0 = (tile % (N / T)) * T, ty0 = (tile / (N / T)) * T;
+    const int ip = tid % (T / 2), tj = tid / (T / 2);
+    const int ci = 2 * ip;                                      // first cell of the pair
+    const BlockInfo info = a.info[b];
+    const int lev = info.level;
+    const float idx0 = float(g.inv_dx[lev][0]), idx1 = float(g.inv_dx[lev][1]), idx2 = float(g.inv_dx[lev][2]);
+    const float gam = a.gamma;
+    const float gm1i = 1.f / (gam - 1.f);
+    const float dt_eff = float(a.w_dt * a.sc_in->dt);
+    const float *__restrict__ ub = a.deriv + int64_t(b) * V * NC;
+    // same-level neighbours (scalars: a runtime-indexed array would live in local memory)
+    const int nb0 = a.gather ? info.nbr[0] : -1, nb1 = a.gather ? info.nbr[1] : -1;
+    const int nb2 = a.gather ? info.nbr[2] : -1, nb3 = a.gather ? info.nbr[3] : -1;
+    const int nb4 = a.gather ? info.nbr[4] : -1, nb5 = a.gather ? info.nbr[5] : -1;
+
+    bool nonphys = false;
+    float vmax = 0.f;
+
+    auto slot = [&](int k) -> float * { return ring + ((k + 2) % Sh::R) * V * PL; };
+    auto gofs = [&](int i, int j, int k) -> int64_t { return (int64_t(k + NG) * S + (j + NG)) * S + (i + NG); };
+    // source of cell (tx0 + ii, ty0 + jj, k): this block, or a same-level
+    // neighbour's interior in gather mode
+    auto src_of = [&](int ii, int jj, int k, int64_t &o) -> const float * {
+        int gi = tx0 + ii, gj = ty0 + jj, gk = k, nb = -1;
+        if (gi < 0) { nb = nb0; gi += N; }
+        else if (gi >= N) { nb = nb1; gi -= N; }
+        else if (gj < 0) { nb = nb2; gj += N; }
+        else if (gj >= N) { nb = nb3; gj -= N; }
+        else if (gk < 0) { nb = nb4; gk += N; }
+        else if (gk >= N) { nb = nb5; gk -= N; }
+        if (nb >= 0) {
+            o = gofs(gi, gj, gk);
+            return a.deriv + int64_t(nb) * V * NC;
+        }
+        o = gofs(tx0 + ii, ty0 + jj, k);
+        return ub;
+    };
+    auto pair_of = [&](int p, bool halo, int &ii, int &jj) -> bool {
+        if (halo) {
+            if (p >= Sh::HALO_PAIRS) return false;
+            jj = p / (P / 2) - 2;
+            ii = 2 * (p % (P / 2)) - 2;
+            return !((jj < 0 || jj >= T) && (ii < 0 || ii >= T));
+        }
+        if (p >= Sh::GHOST_PAIRS) return false;
+        jj = p / (T / 2);
+        ii = 2 * (p % (T / 2));
+        return true;
+    };
+
+    // ---- plane loading: conservative pairs into registers, then primitives into the ring
+    float2 pre[Sh::LOADS][V];
+    auto prefetch = [&](int k) {
+        const bool halo = (k >= 0 && k < N);
+#pragma unroll
+        for (int l = 0; l < Sh::LOADS; ++l) {
+            int ii, jj;
+            if (pair_of(tid + l * NT, halo, ii, jj)) {
+                int64_t o;
+                const float *src = src_of(ii, jj, k, o);
+#pragma unroll
+                for (int v = 0; v < V; ++v) pre[l][v] = *reinterpret_cast<const float2 *>(src + v * NC + o);
+            }
+        }
+    };
+    auto commit = [&](int k) {
+        float *pl = slot(k);
+        const bool halo = (k >= 0 && k < N);
+#pragma unroll
+        for (int l = 0; l < Sh::LOADS; ++l) {
+            int ii, jj;
+            if (!pair_of(tid + l * NT, halo, ii, jj)) continue;
+            float2 w[V];
+            pair_prim(pre[l], w, gam);
+            nonphys |= !PF::positive(w[0]) || !PF::positive(w[4]);
+            const int o = (jj + 2) * P + (ii + 2);
+#pragma unroll
+            for (int v = 0; v < V; ++v) *reinterpret_cast<float2 *>(pl + v * PL + o) = w[v];
+        }
+    };
+    auto ld2 = [&](const float *pl, int v, int jj, int ii) -> float2 {
+        return *reinterpret_cast<const float2 *>(pl + v * PL + (jj + 2) * P + (ii + 2));
+    };
+
+    const int nface_b = N * N;
+    auto store_bflux1 = [&](int f, int t, float Fv0, float Fv1, float Fv2, float Fv3, float Fv4) {
+        const int sl = info.bslot[f];
+        if (sl < 0) return;
+        float *dst = a.bflux + int64_t(sl) * V * nface_b + t;
+        dst[0] = Fv0;
+        dst[nface_b] = Fv1;
+        dst[2 * nface_b] = Fv2;
+        dst[3 * nface_b] = Fv3;
+        dst[4 * nface_b] = Fv4;
+    };
+    // store both faces of a pair (tangential indices t and t + 1)
+    auto store_bflux2 = [&](int f, int t, const float2 *F) {
+        const int sl = info.bslot[f];
+        if (sl < 0) return;
+        float *dst = a.bflux + int64_t(sl) * V * nface_b + t;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            dst[v * nface_b] = F[v].x;
+            dst[v * nface_b + 1] = F[v].y;
+        }
+    };
+
+    // ---- fluxes of plane k into buffer fb
+    float2 FzA[V], FzB[V];   // z fluxes below / above the plane being updated
+    auto fluxes = [&](int k, float *fb, float2 *Fz_new) {
+        float *Fx = fb, *Fy = fb + V * NFX;
+        const float *pl = slot(k);
+        float2 wL[V], wR[V], F[V];
+        // x-faces ci, ci+1 of row tj
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const float2 A = ld2(pl, v, tj, ci - 2), B = ld2(pl, v, tj, ci), C2 = ld2(pl, v, tj, ci + 2);
+            pair_states(A, make_float2(A.y, B.x), B, make_float2(B.y, C2.x), wL[v], wR[v]);
+        }
+        nonphys |= !PF::positive(wL[0]) || !PF::positive(wR[0]) || !PF::positive(wL[4]) || !PF::positive(wR[4]);
+        pair_flux<0>(wL, wR, 0, gam, gm1i, F);
+#pragma unroll
+        for (int v = 0; v < V; ++v) *reinterpret_cast<float2 *>(Fx + v * NFX + tj * FXP + ci) = F[v];
+        if (ci == 0 && tx0 == 0) store_bflux1(0, ty0 + tj + N * k, F[0].x, F[1].x, F[2].x, F[3].x, F[4].x);
+        // y-face tj (between rows tj-1 and tj) of columns ci, ci+1
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+            pair_states(ld2(pl, v, tj - 2, ci), ld2(pl, v, tj - 1, ci), ld2(pl, v, tj, ci), ld2(pl, v, tj + 1, ci), wL[v], wR[v]);
+        nonphys |= !PF::positive(wL[0]) || !PF::positive(wR[0]) || !PF::positive(wL[4]) || !PF::positive(wR[4]);
+        pair_flux<1>(wL, wR, 1, gam, gm1i, F);
+#pragma unroll
+        for (int v = 0; v < V; ++v) *reinterpret_cast<float2 *>(Fy + v * (T + 1) * T + tj * T + ci) = F[v];
+        if (tj == 0 && ty0 == 0) store_bflux2(2, tx0 + ci + N * k, F);
+        // z-face k + 1/2 of cells ci, ci+1
+        {
+            const float *p0 = slot(k - 1), *p1 = pl, *p2 = slot(k + 1), *p3 = slot(k + 2);
+#pragma unroll
+            for (int v = 0; v < V; ++v)
+                pair_states(ld2(p0, v, tj, ci), ld2(p1, v, tj, ci), ld2(p2, v, tj, ci), ld2(p3, v, tj, ci), wL[v], wR[v]);
+            nonphys |= !PF::positive(wL[0]) || !PF::positive(wR[0]) || !PF::positive(wL[4]) || !PF::positive(wR[4]);
+            pair_flux<2>(wL, wR, 2, gam, gm1i, Fz_new);
+            if (k == N - 1) store_bflux2(5, tx0 + ci + N * (ty0 + tj), Fz_new);
+        }
+        // leftovers: x-face T of rows (2r, 2r+1) for tid < 8; y-face T of
+        // columns (2c, 2c+1) for 8 <= tid < 16
+        if (tid < T) {
+            const int dir = tid >= T / 2;
+            const int r = dir ? tid - T / 2 : tid;
+            if (!dir) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    const float *row0 = pl + v * PL + (2 * r + 2) * P + 2, *row1 = row0 + P;
+                    pair_states(make_float2(row0[T - 2], row1[T - 2]), make_float2(row0[T - 1], row1[T - 1]),
+                                make_float2(row0[T], row1[T]), make_float2(row0[T + 1], row1[T + 1]), wL[v], wR[v]);
+                }
+            } else {
+#pragma unroll
+                for (int v = 0; v < V; ++v)
+                    pair_states(ld2(pl, v, T - 2, 2 * r), ld2(pl, v, T - 1, 2 * r), ld2(pl, v, T, 2 * r), ld2(pl, v, T + 1, 2 * r),
+                                wL[v], wR[v]);
+            }
+            nonphys |= !PF::positive(wL[0]) || !PF::positive(wR[0]) || !PF::positive(wL[4]) || !PF::positive(wR[4]);
+            pair_flux<-1>(wL, wR, dir, gam, gm1i, F);
+            if (!dir) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    Fx[v * NFX + (2 * r) * FXP + T] = F[v].x;
+                    Fx[v * NFX + (2 * r + 1) * FXP + T] = F[v].y;
+                }
+                if (tx0 + T == N) {
+                    store_bflux1(1, ty0 + 2 * r + N * k, F[0].x, F[1].x, F[2].x, F[3].x, F[4].x);
+                    store_bflux1(1, ty0 + 2 * r + 1 + N * k, F[0].y, F[1].y, F[2].y, F[3].y, F[4].y);
+                }
+            } else {
+#pragma unroll
+                for (int v = 0; v < V; ++v) *reinterpret_cast<float2 *>(Fy + v * (T + 1) * T + T * T + 2 * r) = F[v];
+                if (ty0 + T == N) store_bflux2(3, tx0 + 2 * r + N * k, F);
+            }
+        }
+    };
+
+    // ---- update of plane k from buffer fb and the z fluxes below / above
+    auto update = [&](int k, const float *fb, const float2 *Fzlo, const float2 *Fzhi) {
+        const float *Fx = fb, *Fy = fb + V * NFX;
+        const int64_t o = gofs(tx0 + ci, ty0 + tj, k);
+        const int64_t ob = int64_t(b) * V * NC + o;
+        const float2 i0 = PF::sp(idx0), i1 = PF::sp(idx1), i2 = PF::sp(idx2), dte = PF::sp(dt_eff);
+        float2 U[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const float2 x0 = *reinterpret_cast<const float2 *>(Fx + v * NFX + tj * FXP + ci);
+            const float2 x1 = *reinterpret_cast<const float2 *>(Fx + v * NFX + tj * FXP + ci + 2);
+            const float2 y0 = *reinterpret_cast<const float2 *>(Fy + v * (T + 1) * T + tj * T + ci);
+            const float2 y1 = *reinterpret_cast<const float2 *>(Fy + v * (T + 1) * T + (tj + 1) * T + ci);
+            float2 du = PF::mul(PF::sub(x0, make_float2(x0.y, x1.x)), i0);
+            du = PF::fma(PF::sub(y0, y1), i1, du);
+            du = PF::fma(PF::sub(Fzlo[v], Fzhi[v]), i2, du);
+            float2 acc = PF::sp(0.f);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (q < a.nprev)
+                    acc = PF::fma(PF::sp(a.wprev[q]), *reinterpret_cast<const float2 *>(a.prev[q] + ob + v * NC), acc);
+            U[v] = PF::fma(dte, du, acc);
+            *reinterpret_cast<float2 *>(a.out + ob + v * NC) = U[v];
+        }
+        // complete the row's DRAM sectors: the output's x-ghost cells
+        if (tx0 + ci == 0 || tx0 + ci + 1 == N - 1) {
+            const int64_t og = ob + (tx0 + ci == 0 ? -NG : 2);
+#pragma unroll
+            for (int v = 0; v < V; ++v) *reinterpret_cast<float2 *>(a.out + og + v * NC) = PF::sp(0.f);
+        }
+        if (a.update_dt) {
+            const int gi = tx0 + ci, gj = ty0 + tj;
+            const int m = info.fixmask;
+            // cells next to a coarse-side refinement face are reduced after flux fixing
+            const bool rowfix = ((m & 4) && gj == 0) || ((m & 8) && gj == N - 1) || ((m & 16) && k == 0) ||
+                                ((m & 32) && k == N - 1);
+            const bool fx0 = rowfix || ((m & 1) && gi == 0);
+            const bool fx1 = rowfix || ((m & 2) && gi + 1 == N - 1);
+            float2 w[V];
+            pair_prim(U, w, gam);
+            const float2 c2 = PF::mul(PF::mul(PF::sp(gam), w[4]), PF::rcp(w[0]));
+            const float2 c = PF::mul(c2, PF::rsqrt(c2));
+            float2 s = PF::mul(PF::add(PF::abs(w[1]), c), i0);
+            s = PF::fma(PF::add(PF::abs(w[2]), c), i1, s);
+            s = PF::fma(PF::add(PF::abs(w[3]), c), i2, s);
+            if (!fx0) vmax = s.x > vmax ? s.x : vmax;
+            if (!fx1) vmax = s.y > vmax ? s.y : vmax;
+        }
+    };
+
+    // ---- the march
+    // prologue: planes -2 .. 2, two loads in flight at a time
+    prefetch(-2);
+    commit(-2);
+    prefetch(-1);
+    commit(-1);
+    prefetch(0);
+    commit(0);
+    prefetch(1);
+    commit(1);
+    prefetch(2);
+    commit(2);
+    prefetch(3);
+    __syncthreads();
+    {
+        // z flux through the block's lower face (k = -1/2)
+        const float *p0 = slot(-2), *p1 = slot(-1), *p2 = slot(0), *p3 = slot(1);
+        float2 wL[V], wR[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+            pair_states(ld2(p0, v, tj, ci), ld2(p1, v, tj, ci), ld2(p2, v, tj, ci), ld2(p3, v, tj, ci), wL[v], wR[v]);
+        nonphys |= !PF::positive(wL[0]) || !PF::positive(wR[0]) || !PF::positive(wL[4]) || !PF::positive(wR[4]);
+        pair_flux<2>(wL, wR, 2, gam, gm1i, FzA);
+        store_bflux2(4, tx0 + ci + N * (ty0 + tj), FzA);
+    }
+    // plane 0's fluxes; plane 3 committed (its slot held plane -2, read above)
+    fluxes(0, fbuf, FzB);
+    __syncthreads();
+    commit(3);
+    if (4 <= N + 1) prefetch(4);
+    __syncthreads();
+    for (int k = 1; k < N; ++k) {
+        float *fb_prev = fbuf + ((k - 1) & 1) * FBUF, *fb_cur = fbuf + (k & 1) * FBUF;
+        update(k - 1, fb_prev, FzA, FzB);
+#pragma unroll
+        for (int v = 0; v < V; ++v) FzA[v] = FzB[v];
+        fluxes(k, fb_cur, FzB);
+        if (k + 3 <= N + 1) {
+            commit(k + 3);
+            if (k + 4 <= N + 1) prefetch(k + 4);
+        }
+        __syncthreads();
+    }
+    update(N - 1, fbuf + ((N - 1) & 1) * FBUF, FzA, FzB);
+
+    if (a.update_dt) {
+        double m = double(vmax);
+        for (int s = 16; s > 0; s >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, s));
+        if ((tid & 31) == 0) atomic_max_nonneg(&a.sc->maxspeed_bits, m);
+    }
+    if (__syncthreads_or(nonphys) && tid == 0) raise_status(&a.sc->status, 7);
+}
+
+}  // namespace amrb
