@@ -7,8 +7,9 @@
 //
 // One CTA per (block, T x T column tile), T = min(N, 16), T*T/2 threads
 // (128 for T = 16); thread (ip, tj) owns
-// cells (2ip, 2ip+1) of row tj.  The CTA marches k with a 5-plane ring of
-// primitive variables in shared memory.  One barrier per plane:
+// cells (2ip, 2ip+1) of row tj.  The CTA marches k with a ring of
+// primitive variables in shared memory (4 planes: the z face state of the
+// plane above is carried in registers).  One barrier per plane:
 //   [update of plane k-1 | fluxes of plane k | commit of plane k+3] barrier
 // with the face fluxes double-buffered between consecutive planes.  Face
 // states (MUSCL with minmod) are formed in the flux phase from the ring: an
@@ -43,6 +44,12 @@ struct PF {
 };
 
 constexpr int kPairV = 5;   // 3D Euler variables
+
+// Bulk prefetch of a contiguous range into L2 by the TMA unit (no registers,
+// no shared memory).  Address and size must be multiples of 16 bytes.
+__device__ __forceinline__ void l2_prefetch(const void *p, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
 
 // Rusanov / Einfeldt flux of a pair of faces with the same normal n
 // (compile-time NRM >= 0, or runtime n when NRM < 0).
@@ -114,7 +121,7 @@ __device__ __forceinline__ void pair_prim(const float2 *U, float2 *w, float gam)
 
 template <int N>
 struct PairShape {
-    static constexpr int T = N < 16 ? N : 16, NG = 2, S = N + 2 * NG, P = T + 4, PL = P * P, R = 5, V = 5;
+    static constexpr int T = N < 16 ? N : 16, NG = 2, S = N + 2 * NG, P = T + 4, PL = P * P, R = 4, V = 5;
     static constexpr int NT = T * T / 2;              // threads: one per cell pair of a plane
     static constexpr int TILES = (N / T) * (N / T);
     static constexpr int FXP = T + 2;                 // x-flux row pitch (17 faces + pad)
@@ -128,7 +135,7 @@ struct PairShape {
 };
 
 template <int N>
-__global__ void __launch_bounds__(PairShape<N>::NT) k_stage_pair(StageArgs<float> a, Geom g) {
+__global__ void __launch_bounds__(PairShape<N>::NT, (N >= 16 ? 4 : 1)) k_stage_pair(StageArgs<float> a, Geom g) {
     using Sh = PairShape<N>;
     constexpr int T = Sh::T, NG = Sh::NG, S = Sh::S, P = Sh::P, PL = Sh::PL, V = Sh::V, NT = Sh::NT;
     constexpr int FXP = Sh::FXP, NFX = Sh::NFX, FBUF = Sh::FBUF;
@@ -249,6 +256,7 @@ __global__ void __launch_bounds__(PairShape<N>::NT) k_stage_pair(StageArgs<float
 
     // ---- fluxes of plane k into buffer fb
     float2 FzA[V], FzB[V];   // z fluxes below / above the plane being updated
+    float2 zP[V];            // plus z state of the pair at the plane whose fluxes come next
     auto fluxes = [&](int k, float *fb, float2 *Fz_new) {
         float *Fx = fb, *Fy = fb + V * NFX;
         const float *pl = slot(k);
@@ -259,7 +267,6 @@ __global__ void __launch_bounds__(PairShape<N>::NT) k_stage_pair(StageArgs<float
             const float2 A = ld2(pl, v, tj, ci - 2), B = ld2(pl, v, tj, ci), C2 = ld2(pl, v, tj, ci + 2);
             pair_states(A, make_float2(A.y, B.x), B, make_float2(B.y, C2.x), wL[v], wR[v]);
         }
-        nonphys |= !PF::positive(wL[0]) || !PF::positive(wR[0]) || !PF::positive(wL[4]) || !PF::positive(wR[4]);
         pair_flux<0>(wL, wR, 0, gam, gm1i, F);
 #pragma unroll
         for (int v = 0; v < V; ++v) *reinterpret_cast<float2 *>(Fx + v * NFX + tj * FXP + ci) = F[v];
@@ -268,18 +275,23 @@ __global__ void __launch_bounds__(PairShape<N>::NT) k_stage_pair(StageArgs<float
 #pragma unroll
         for (int v = 0; v < V; ++v)
             pair_states(ld2(pl, v, tj - 2, ci), ld2(pl, v, tj - 1, ci), ld2(pl, v, tj, ci), ld2(pl, v, tj + 1, ci), wL[v], wR[v]);
-        nonphys |= !PF::positive(wL[0]) || !PF::positive(wR[0]) || !PF::positive(wL[4]) || !PF::positive(wR[4]);
         pair_flux<1>(wL, wR, 1, gam, gm1i, F);
 #pragma unroll
         for (int v = 0; v < V; ++v) *reinterpret_cast<float2 *>(Fy + v * (T + 1) * T + tj * T + ci) = F[v];
         if (tj == 0 && ty0 == 0) store_bflux2(2, tx0 + ci + N * k, F);
-        // z-face k + 1/2 of cells ci, ci+1
+        // z-face k + 1/2 of cells ci, ci+1: the plus state of plane k is
+        // carried from the previous plane, the minus / plus states of plane
+        // k+1 come from planes k .. k+2
         {
-            const float *p0 = slot(k - 1), *p1 = pl, *p2 = slot(k + 1), *p3 = slot(k + 2);
+            const float *p1 = pl, *p2 = slot(k + 1), *p3 = slot(k + 2);
 #pragma unroll
-            for (int v = 0; v < V; ++v)
-                pair_states(ld2(p0, v, tj, ci), ld2(p1, v, tj, ci), ld2(p2, v, tj, ci), ld2(p3, v, tj, ci), wL[v], wR[v]);
-            nonphys |= !PF::positive(wL[0]) || !PF::positive(wR[0]) || !PF::positive(wL[4]) || !PF::positive(wR[4]);
+            for (int v = 0; v < V; ++v) {
+                const float2 w1 = ld2(p1, v, tj, ci), w2 = ld2(p2, v, tj, ci), w3 = ld2(p3, v, tj, ci);
+                const float2 hs = PF::half_minmod(PF::sub(w2, w1), PF::sub(w3, w2));
+                wR[v] = PF::sub(w2, hs);
+                wL[v] = zP[v];
+                zP[v] = PF::add(w2, hs);
+            }
             pair_flux<2>(wL, wR, 2, gam, gm1i, Fz_new);
             if (k == N - 1) store_bflux2(5, tx0 + ci + N * (ty0 + tj), Fz_new);
         }
@@ -301,7 +313,6 @@ __global__ void __launch_bounds__(PairShape<N>::NT) k_stage_pair(StageArgs<float
                     pair_states(ld2(pl, v, T - 2, 2 * r), ld2(pl, v, T - 1, 2 * r), ld2(pl, v, T, 2 * r), ld2(pl, v, T + 1, 2 * r),
                                 wL[v], wR[v]);
             }
-            nonphys |= !PF::positive(wL[0]) || !PF::positive(wR[0]) || !PF::positive(wL[4]) || !PF::positive(wR[4]);
             pair_flux<-1>(wL, wR, dir, gam, gm1i, F);
             if (!dir) {
 #pragma unroll
@@ -319,6 +330,23 @@ __global__ void __launch_bounds__(PairShape<N>::NT) k_stage_pair(StageArgs<float
                 if (ty0 + T == N) store_bflux2(3, tx0 + 2 * r + N * k, F);
             }
         }
+    };
+
+    // ---- L2 prefetch, one plane period ahead: the previous states' plane k
+    // (read by the update of plane k in the next iteration) and this block's
+    // derivative plane k + 5 (loaded into registers two iterations later)
+    auto l2_ahead = [&](int k) {
+        if (tid != 0) return;
+        constexpr unsigned PB = unsigned(S) * S * sizeof(float);
+        const int64_t blk = int64_t(b) * V * NC;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (q < a.nprev)
+#pragma unroll
+                for (int v = 0; v < V; ++v) l2_prefetch(a.prev[q] + blk + v * NC + int64_t(k + NG) * S * S, PB);
+        if (k + 5 <= N + 1)
+#pragma unroll
+            for (int v = 0; v < V; ++v) l2_prefetch(ub + v * NC + int64_t(k + 5 + NG) * S * S, PB);
     };
 
     // ---- update of plane k from buffer fb and the z fluxes below / above
@@ -371,8 +399,8 @@ __global__ void __launch_bounds__(PairShape<N>::NT) k_stage_pair(StageArgs<float
         }
     };
 
-    // ---- the march
-    // prologue: planes -2 .. 2, two loads in flight at a time
+    // ---- the march (ring of 4 planes: the fluxes of plane k read planes
+    // k .. k+2 while plane k+3 is committed into the slot of plane k-1)
     prefetch(-2);
     commit(-2);
     prefetch(-1);
@@ -382,28 +410,35 @@ __global__ void __launch_bounds__(PairShape<N>::NT) k_stage_pair(StageArgs<float
     prefetch(1);
     commit(1);
     prefetch(2);
-    commit(2);
-    prefetch(3);
     __syncthreads();
     {
-        // z flux through the block's lower face (k = -1/2)
+        // z flux through the block's lower face (k = -1/2) and the plus
+        // state of plane 0
         const float *p0 = slot(-2), *p1 = slot(-1), *p2 = slot(0), *p3 = slot(1);
         float2 wL[V], wR[V];
 #pragma unroll
-        for (int v = 0; v < V; ++v)
-            pair_states(ld2(p0, v, tj, ci), ld2(p1, v, tj, ci), ld2(p2, v, tj, ci), ld2(p3, v, tj, ci), wL[v], wR[v]);
-        nonphys |= !PF::positive(wL[0]) || !PF::positive(wR[0]) || !PF::positive(wL[4]) || !PF::positive(wR[4]);
+        for (int v = 0; v < V; ++v) {
+            const float2 w0 = ld2(p0, v, tj, ci), w1 = ld2(p1, v, tj, ci), w2 = ld2(p2, v, tj, ci), w3 = ld2(p3, v, tj, ci);
+            wL[v] = PF::add(w1, PF::half_minmod(PF::sub(w1, w0), PF::sub(w2, w1)));
+            const float2 hs = PF::half_minmod(PF::sub(w2, w1), PF::sub(w3, w2));
+            wR[v] = PF::sub(w2, hs);
+            zP[v] = PF::add(w2, hs);
+        }
         pair_flux<2>(wL, wR, 2, gam, gm1i, FzA);
         store_bflux2(4, tx0 + ci + N * (ty0 + tj), FzA);
     }
-    // plane 0's fluxes; plane 3 committed (its slot held plane -2, read above)
-    fluxes(0, fbuf, FzB);
     __syncthreads();
-    commit(3);
+    commit(2);          // into the slot of plane -2
+    prefetch(3);
+    __syncthreads();
+    l2_ahead(0);
+    fluxes(0, fbuf, FzB);
+    commit(3);          // into the slot of plane -1
     if (4 <= N + 1) prefetch(4);
     __syncthreads();
     for (int k = 1; k < N; ++k) {
         float *fb_prev = fbuf + ((k - 1) & 1) * FBUF, *fb_cur = fbuf + (k & 1) * FBUF;
+        l2_ahead(k);
         update(k - 1, fb_prev, FzA, FzB);
 #pragma unroll
         for (int v = 0; v < V; ++v) FzA[v] = FzB[v];
