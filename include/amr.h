@@ -151,10 +151,30 @@ typedef struct {
  * max_blocks), AMR_ENOMEM, AMR_ECUDA. */
 amr_status amr_create_forest(const amr_config *cfg, int init_level, amr_forest **out);
 
+/* Creates one forest holding n independent mesh instances (many meshes of
+ * uneven size advanced together): instance i is the brick of cfgs[i] refined
+ * uniformly to init_levels[i].  The blocks of all instances are numbered
+ * consecutively in instance order, so every call below works on all of them
+ * at once -- one kernel launch per phase sweeps every block of every
+ * instance.  Each instance keeps its own domain, brick, periodicity,
+ * max_level, boundaries, CFL number and time step; ndim, block_n, n_ghost,
+ * precision, n_states, gamma, host_only and the allocation hook must be the
+ * same for all.  Capacity is the sum of the instances' max_blocks; each
+ * instance is also held to its own max_blocks on regrid.  amr_create_forest
+ * is the n = 1 case.  Errors as amr_create_forest. */
+amr_status amr_create_batch(const amr_config *cfgs, const int *init_levels, int n, amr_forest **out);
+
+/* Number of mesh instances of the forest. */
+amr_status amr_n_instances(const amr_forest *f, int *n);
+
+/* Block range of instance inst: blocks first .. first + n - 1 (either
+ * pointer may be NULL).  Ranges change after a regrid. */
+amr_status amr_instance_blocks(const amr_forest *f, int inst, int64_t *first, int64_t *n);
+
 /* Frees everything the forest owns.  NULL is accepted. */
 amr_status amr_destroy_forest(amr_forest *f);
 
-/* Number of leaf blocks. */
+/* Number of leaf blocks (of all instances). */
 amr_status amr_n_blocks(const amr_forest *f, int64_t *n);
 
 /* Level and integer block coordinates (at the block's own level, counted over
@@ -203,9 +223,13 @@ amr_status amr_fill_ghosts(amr_forest *f, int s, amr_stream stream);
  * sum_d (|v_d| + c) / dx_d of state slot s (Sec. 3.2, step 2c). */
 amr_status amr_compute_dt(amr_forest *f, int s, amr_stream stream);
 
-/* Overwrites / reads the device time step (read synchronises `stream`). */
+/* Overwrites every instance's device time step / reads instance 0's
+ * (synchronises `stream`). */
 amr_status amr_set_dt(amr_forest *f, double dt, amr_stream stream);
 amr_status amr_get_dt(amr_forest *f, double *dt, amr_stream stream);
+
+/* Time step of every instance into dts[0 .. n_instances) (synchronises). */
+amr_status amr_get_dts(amr_forest *f, double *dts, amr_stream stream);
 
 /* One stage of Eq. 4 on every block: primitive reconstruction with the minmod
  * limiter, Rusanov fluxes with Einfeldt wave speeds, divergence, Runge-Kutta
@@ -224,8 +248,12 @@ amr_status amr_advance_stage(amr_forest *f, const amr_stage *st, amr_stream stre
 amr_status amr_step(amr_forest *f, int n_steps, int flags, amr_stream stream);
 
 /* Integral of every conserved variable over the leaves of slot s, summed in
- * double on the device in a fixed order (Eq. 12).  Synchronises `stream`. */
+ * double on the device in a fixed order (Eq. 12), for instance 0 (n_var
+ * values).  Synchronises `stream`. */
 amr_status amr_conserved(amr_forest *f, int s, double *sums, amr_stream stream);
+
+/* The same for every instance: sums[inst * n_var + v]. */
+amr_status amr_conserved_all(amr_forest *f, int s, double *sums, amr_stream stream);
 
 /* Refinement flags of slot s from the criterion of Eq. 5 (ghosts must be
  * filled): +1 refine, -1 derefine, 0 keep, per block.  Copied to flags_out

@@ -28,7 +28,8 @@ EXPORTED = [
     "amr_get_ghost_pattern", "amr_set_state", "amr_get_state", "amr_state_ptr", "amr_set_bc_data",
     "amr_fill_ghosts", "amr_compute_dt", "amr_set_dt", "amr_get_dt", "amr_advance_stage", "amr_step",
     "amr_conserved", "amr_flag", "amr_flag_and_regrid", "amr_sync_status", "amr_last_error",
-    "amr_launch_count", "amr_conserved_static",
+    "amr_launch_count", "amr_conserved_static", "amr_create_batch", "amr_n_instances", "amr_instance_blocks",
+    "amr_get_dts", "amr_conserved_all",
 ]
 
 
@@ -108,6 +109,11 @@ def load(build_if_missing: bool = True):
         "amr_flag_and_regrid": [vp, P(FlagParams), vp, P(C.c_int), vp],
         "amr_sync_status": [vp, vp],
         "amr_launch_count": [vp, P(i64)],
+        "amr_create_batch": [vp, vp, C.c_int, P(vp)],
+        "amr_n_instances": [vp, P(C.c_int)],
+        "amr_instance_blocks": [vp, C.c_int, P(i64), P(i64)],
+        "amr_get_dts": [vp, vp, vp],
+        "amr_conserved_all": [vp, C.c_int, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -152,11 +158,33 @@ class Forest:
     """A forest of blocks on the current CUDA device (Sec. 2.2-2.3)."""
 
     def __init__(self, spec, init_level=0, max_blocks=None, n_states=2, precision=64, config: Config | None = None,
-                 host_only=False):
+                 host_only=False, batch=None):
+        """A forest of one mesh (spec, init_level), or -- with batch = list of
+        (spec, init_level, max_blocks) -- of several independent instances
+        advanced together (amr_create_batch)."""
         self.lib = load()
-        self.spec = spec
         self.precision = precision
         self.dtype = np.float64 if precision == 64 else np.float32
+        h = C.c_void_p()
+        if batch is not None:
+            cfgs = (Config * len(batch))()
+            levels = (C.c_int * len(batch))()
+            for i, (sp, lvl, mb) in enumerate(batch):
+                if mb is None:
+                    mb = int(np.prod([sp.ntrees[d] << lvl for d in range(sp.ndim)]))
+                cfgs[i] = config_from_spec(sp, mb, n_states, precision, host_only)
+                levels[i] = int(lvl)
+            self.spec = batch[0][0]
+            self.specs = [b[0] for b in batch]
+            self.cfg = cfgs[0]
+            self.n_states = n_states
+            st = self.lib.amr_create_batch(cfgs, levels, len(batch), C.byref(h))
+            if st != AMR_OK:
+                raise AmrError(st, "amr_create_batch")
+            self.h = h
+            return
+        self.spec = spec
+        self.specs = [spec]
         if config is None:
             if max_blocks is None:
                 max_blocks = int(np.prod([spec.ntrees[d] << init_level for d in range(spec.ndim)]))
@@ -164,11 +192,32 @@ class Forest:
         self.cfg = config
         self.max_blocks = config.max_blocks
         self.n_states = config.n_states
-        h = C.c_void_p()
         st = self.lib.amr_create_forest(C.byref(config), int(init_level), C.byref(h))
         if st != AMR_OK:
             raise AmrError(st, "amr_create_forest")
         self.h = h
+
+    @property
+    def n_instances(self) -> int:
+        n = C.c_int()
+        self._check(self.lib.amr_n_instances(self.h, C.byref(n)), "amr_n_instances")
+        return int(n.value)
+
+    def instance_blocks(self, inst):
+        """(first block, number of blocks) of an instance."""
+        a, b = C.c_int64(), C.c_int64()
+        self._check(self.lib.amr_instance_blocks(self.h, int(inst), C.byref(a), C.byref(b)), "amr_instance_blocks")
+        return int(a.value), int(b.value)
+
+    def get_dts(self, stream=None) -> np.ndarray:
+        out = np.zeros(self.n_instances)
+        self._check(self.lib.amr_get_dts(self.h, out.ctypes.data, _stream_ptr(stream)), "amr_get_dts")
+        return out
+
+    def conserved_all(self, s, stream=None) -> np.ndarray:
+        out = np.zeros((self.n_instances, self.spec.nvar))
+        self._check(self.lib.amr_conserved_all(self.h, s, out.ctypes.data, _stream_ptr(stream)), "amr_conserved_all")
+        return out
 
     # ---- plumbing
     def _check(self, st, what):

@@ -34,8 +34,11 @@ struct DBuf {
 }  // namespace
 
 struct amr_forest {
-    amr_config cfg{};
-    Forest forest;
+    amr_config cfg{};                 // shared settings; max_blocks = total capacity
+    std::vector<amr_config> icfg;     // per instance
+    std::vector<Forest> inst;         // per instance; blocks numbered consecutively
+    std::vector<int64_t> offset;      // first block of each instance, total at the end
+    uint64_t revision = 1;            // bumped whenever any instance's mesh changes
     Pattern pat;
     uint64_t pattern_rev = ~0ull;
     Geom geom{};
@@ -43,6 +46,7 @@ struct amr_forest {
     size_t block_bytes = 0;
     void *state = nullptr;
     DBuf r1, r2, r1g, info, fix, fix_start, bflux, bcdata, sc, partial, sums, flags, ops, level;
+    DBuf dxtab, invdxtab, bctype, bcval, cfltab, ranges;   // per-instance tables
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t gexec = nullptr;
     uint64_t graph_rev = ~0ull;
@@ -111,7 +115,19 @@ amr_status upload(amr_forest *f, DBuf &b, const std::vector<T> &v) {
     return AMR_OK;
 }
 
-int64_t nblocks(const amr_forest *f) { return int64_t(f->forest.leaves.size()); }
+int64_t nblocks(const amr_forest *f) { return f->offset.empty() ? 0 : f->offset.back(); }
+int n_inst(const amr_forest *f) { return int(f->inst.size()); }
+
+void set_offsets(amr_forest *f) {
+    f->offset.assign(1, 0);
+    for (const Forest &F : f->inst) f->offset.push_back(f->offset.back() + int64_t(F.leaves.size()));
+}
+
+const Leaf &leaf_at(const amr_forest *f, int64_t b, int *which = nullptr) {
+    size_t i = size_t(std::upper_bound(f->offset.begin(), f->offset.end(), b) - f->offset.begin()) - 1;
+    if (which) *which = int(i);
+    return f->inst[i].leaves[size_t(b - f->offset[i])];
+}
 
 void *slot_ptr(const amr_forest *f, int s) { return static_cast<char *>(f->state) + size_t(s) * f->cfg.max_blocks * f->block_bytes; }
 
@@ -126,13 +142,44 @@ void fill_geom(amr_forest *f) {
     g.ncell = 1;
     for (int d = 0; d < c.ndim; ++d) g.ncell *= g.S;
     g.bstride = g.ncell * g.V;
-    for (int l = 0; l < kMaxLevels; ++l)
-        for (int d = 0; d < 3; ++d) {
-            // same evaluation order as a plain len / ntrees / (N 2^l)
-            const double dx = c.len[d] / double(c.ntrees[d]) / (double(c.block_n) * double(1ll << l));
-            g.dx[l][d] = dx;
-            g.inv_dx[l][d] = 1.0 / dx;
+}
+
+// cell sizes per (instance, level), boundary kinds/values and CFL numbers per
+// instance, uploaded once at creation
+amr_status upload_tables(amr_forest *f) {
+    const int ni = n_inst(f);
+    std::vector<double> dx(static_cast<size_t>(ni) * kMaxLevels * 3), idx(dx.size()), cfl(static_cast<size_t>(ni));
+    std::vector<int32_t> bct(size_t(ni) * 6);
+    std::vector<double> bcv(size_t(ni) * 48);
+    for (int i = 0; i < ni; ++i) {
+        const amr_config &c = f->icfg[size_t(i)];
+        for (int l = 0; l < kMaxLevels; ++l)
+            for (int d = 0; d < 3; ++d) {
+                // same evaluation order as a plain len / ntrees / (N 2^l)
+                const double h = c.len[d] / double(c.ntrees[d]) / (double(c.block_n) * double(1ll << l));
+                dx[(size_t(i) * kMaxLevels + l) * 3 + d] = h;
+                idx[(size_t(i) * kMaxLevels + l) * 3 + d] = 1.0 / h;
+            }
+        cfl[size_t(i)] = c.cfl;
+        for (int q = 0; q < 6; ++q) {
+            bct[size_t(i) * 6 + q] = c.bc[q];
+            for (int v = 0; v < 8; ++v) bcv[(size_t(i) * 6 + q) * 8 + v] = c.bc_val[q][v];
         }
+    }
+    amr_status s;
+    if ((s = upload(f, f->dxtab, dx)) != AMR_OK) return s;
+    if ((s = upload(f, f->invdxtab, idx)) != AMR_OK) return s;
+    if ((s = upload(f, f->cfltab, cfl)) != AMR_OK) return s;
+    if ((s = upload(f, f->bctype, bct)) != AMR_OK) return s;
+    if (f->cfg.precision == 64) {
+        if ((s = upload(f, f->bcval, bcv)) != AMR_OK) return s;
+    } else {
+        std::vector<float> b32(bcv.begin(), bcv.end());
+        if ((s = upload(f, f->bcval, b32)) != AMR_OK) return s;
+    }
+    f->geom.dx = static_cast<const double *>(f->dxtab.p);
+    f->geom.inv_dx = static_cast<const double *>(f->invdxtab.p);
+    return AMR_OK;
 }
 
 amr_status validate(const amr_config *c, std::string &why) {
@@ -164,11 +211,13 @@ amr_status validate(const amr_config *c, std::string &why) {
 
 // ------------------------------------------------------------ pattern upload
 amr_status upload_pattern(amr_forest *f) {
-    if (f->pattern_rev == f->forest.revision) return AMR_OK;
+    if (f->pattern_rev == f->revision) return AMR_OK;
     std::string why;
-    if (!build_pattern(f->forest, f->pat, why)) return fail(f, AMR_ESTATE, "%s", why.c_str());
+    std::vector<const Forest *> ptrs;
+    for (const Forest &F : f->inst) ptrs.push_back(&F);
+    if (!build_pattern(ptrs, f->offset, f->pat, why)) return fail(f, AMR_ESTATE, "%s", why.c_str());
     if (f->cfg.host_only) {
-        f->pattern_rev = f->forest.revision;
+        f->pattern_rev = f->revision;
         return AMR_OK;
     }
     amr_status s;
@@ -178,13 +227,11 @@ amr_status upload_pattern(amr_forest *f) {
     if ((s = upload(f, f->info, f->pat.info)) != AMR_OK) return s;
     if ((s = upload(f, f->fix, f->pat.fix)) != AMR_OK) return s;
     if ((s = upload(f, f->fix_start, f->pat.fix_start)) != AMR_OK) return s;
-    std::vector<int32_t> lev(f->forest.leaves.size());
-    for (size_t b = 0; b < lev.size(); ++b) lev[b] = f->forest.leaves[b].lev;
-    if ((s = upload(f, f->level, lev)) != AMR_OK) return s;
+    if ((s = upload(f, f->ranges, f->offset)) != AMR_OK) return s;
     const size_t nface = f->cfg.ndim == 3 ? size_t(f->cfg.block_n) * f->cfg.block_n : size_t(f->cfg.block_n);
     if ((s = ensure(f, f->bflux, size_t(std::max(f->pat.n_slots, 1)) * f->cfg.n_var * nface * f->esize)) != AMR_OK) return s;
     if ((s = ensure(f, f->bcdata, size_t(std::max(f->pat.n_bc, 1)) * f->cfg.n_var * nface * f->esize)) != AMR_OK) return s;
-    f->pattern_rev = f->forest.revision;
+    f->pattern_rev = f->revision;
     return AMR_OK;
 }
 
@@ -194,11 +241,9 @@ amr_status launch_ghosts(amr_forest *f, int s, cudaStream_t st, bool gather) {
     GhostArgs<real> a{};
     a.u = static_cast<real *>(slot_ptr(f, s));
     a.bcdata = static_cast<const real *>(f->bcdata.p);
-    a.level = static_cast<const int32_t *>(f->level.p);
-    for (int q = 0; q < 6; ++q) {
-        a.bc_type[q] = f->cfg.bc[q];
-        for (int v = 0; v < 8; ++v) a.bc_val[q][v] = real(f->cfg.bc_val[q][v]);
-    }
+    a.bc_type = static_cast<const int32_t *>(f->bctype.p);
+    a.bc_val = static_cast<const real *>(f->bcval.p);
+    a.info = static_cast<const BlockInfo *>(f->info.p);
     for (int round = 0; round < 2; ++round) {
         const auto &lst = round == 0 ? (gather ? f->pat.round1_gather : f->pat.round1) : f->pat.round2;
         if (lst.empty()) continue;
@@ -320,7 +365,8 @@ amr_status run_stage(amr_forest *f, const amr_stage *stg, cudaStream_t st) {
         ++f->launches;
     }
     if (stg->update_dt) {
-        k_dt_commit<<<1, 32, 0, st>>>(static_cast<DevScalars *>(f->sc.p), f->cfg.cfl);
+        k_dt_commit<<<(n_inst(f) + 31) / 32, 32, 0, st>>>(static_cast<DevScalars *>(f->sc.p),
+                                                          static_cast<const double *>(f->cfltab.p), n_inst(f));
         ++f->launches;
     }
     CU(cudaGetLastError());
@@ -355,7 +401,8 @@ struct MaxSpeedFn {
                                                                      static_cast<DevScalars *>(f->sc.p), f->geom, real(f->cfg.gamma));
             ++f->launches;
         }
-        k_dt_commit<<<1, 32, 0, st>>>(static_cast<DevScalars *>(f->sc.p), f->cfg.cfl);
+        k_dt_commit<<<(n_inst(f) + 31) / 32, 32, 0, st>>>(static_cast<DevScalars *>(f->sc.p),
+                                                          static_cast<const double *>(f->cfltab.p), n_inst(f));
         ++f->launches;
         CU(cudaGetLastError());
         return AMR_OK;
@@ -366,15 +413,16 @@ struct ConservedFn {
     static amr_status run(amr_forest *f, int s, cudaStream_t st) {
         amr_status r = ensure(f, f->partial, sizeof(double) * std::max<int64_t>(nblocks(f), 1) * f->cfg.n_var);
         if (r != AMR_OK) return r;
-        if ((r = ensure(f, f->sums, sizeof(double) * 8)) != AMR_OK) return r;
+        if ((r = ensure(f, f->sums, sizeof(double) * 8 * size_t(n_inst(f)))) != AMR_OK) return r;
         if (nblocks(f) > 0) {
             k_conserved_block<real, D><<<unsigned(nblocks(f)), 256, 0, st>>>(static_cast<const real *>(slot_ptr(f, s)),
                                                                             static_cast<const BlockInfo *>(f->info.p),
                                                                             static_cast<double *>(f->partial.p), f->geom);
             ++f->launches;
         }
-        k_conserved_final<<<1, 1024, 0, st>>>(static_cast<const double *>(f->partial.p), int(nblocks(f)), f->cfg.n_var,
-                                              static_cast<double *>(f->sums.p));
+        k_conserved_final<<<n_inst(f), 1024, 0, st>>>(static_cast<const double *>(f->partial.p),
+                                                      static_cast<const int64_t *>(f->ranges.p), f->cfg.n_var,
+                                                      static_cast<double *>(f->sums.p));
         ++f->launches;
         CU(cudaGetLastError());
         return AMR_OK;
@@ -431,34 +479,52 @@ bool valid_slot(const amr_forest *f, int s) { return s >= 0 && s < f->cfg.n_stat
 // =================================================================== C ABI
 extern "C" {
 
-amr_status amr_create_forest(const amr_config *cfg, int init_level, amr_forest **out) {
-    if (!cfg || !out) return AMR_EINVAL;
+amr_status amr_create_batch(const amr_config *cfgs, const int *init_levels, int n, amr_forest **out) {
+    if (!cfgs || !init_levels || !out || n < 1) return AMR_EINVAL;
     *out = nullptr;
     std::string why;
-    if (validate(cfg, why) != AMR_OK) return AMR_EINVAL;
-    if (init_level < 0 || init_level > cfg->max_level) return AMR_EINVAL;
+    int64_t capacity = 0;
+    for (int i = 0; i < n; ++i) {
+        const amr_config &c = cfgs[i], &c0 = cfgs[0];
+        if (validate(&c, why) != AMR_OK) return AMR_EINVAL;
+        if (init_levels[i] < 0 || init_levels[i] > c.max_level) return AMR_EINVAL;
+        // settings every instance of one forest shares
+        if (c.ndim != c0.ndim || c.block_n != c0.block_n || c.n_ghost != c0.n_ghost || c.precision != c0.precision ||
+            c.n_states != c0.n_states || c.gamma != c0.gamma || c.host_only != c0.host_only ||
+            c.dev_alloc != c0.dev_alloc || c.dev_free != c0.dev_free || c.alloc_ctx != c0.alloc_ctx)
+            return AMR_EINVAL;
+        capacity += c.max_blocks;
+    }
+    if (capacity > (int64_t(1) << 31) - 1) return AMR_EINVAL;
     amr_forest *f = new (std::nothrow) amr_forest();
     if (!f) return AMR_ENOMEM;
-    f->cfg = *cfg;
-    f->esize = cfg->precision / 8;
+    f->cfg = cfgs[0];
+    f->cfg.max_blocks = int(capacity);
+    f->icfg.assign(cfgs, cfgs + n);
+    f->esize = f->cfg.precision / 8;
     if (const char *e = std::getenv("AMR_SCALAR_STAGE")) f->scalar_stage = e[0] == '1';
     fill_geom(f);
     f->block_bytes = size_t(f->geom.bstride) * f->esize;
-    Geometry G;
-    G.ndim = cfg->ndim;
-    for (int d = 0; d < 3; ++d) {
-        G.ntrees[d] = d < cfg->ndim ? cfg->ntrees[d] : 1;
-        G.periodic[d] = d < cfg->ndim ? (cfg->periodic[d] ? 1 : 0) : 1;
+    f->inst.resize(size_t(n));
+    for (int i = 0; i < n; ++i) {
+        const amr_config &c = cfgs[i];
+        Geometry G;
+        G.ndim = c.ndim;
+        for (int d = 0; d < 3; ++d) {
+            G.ntrees[d] = d < c.ndim ? c.ntrees[d] : 1;
+            G.periodic[d] = d < c.ndim ? (c.periodic[d] ? 1 : 0) : 1;
+        }
+        G.max_level = c.max_level;
+        int64_t n0 = 1;
+        for (int d = 0; d < c.ndim; ++d) n0 *= G.extent(d, init_levels[i]);
+        if (n0 > c.max_blocks) {
+            delete f;
+            return AMR_ECAPACITY;
+        }
+        f->inst[size_t(i)].init_uniform(G, init_levels[i]);
     }
-    G.max_level = cfg->max_level;
-    int64_t n0 = 1;
-    for (int d = 0; d < cfg->ndim; ++d) n0 *= G.extent(d, init_level);
-    if (n0 > cfg->max_blocks) {
-        delete f;
-        return AMR_ECAPACITY;
-    }
-    f->forest.init_uniform(G, init_level);
-    if (cfg->host_only) {
+    set_offsets(f);
+    if (f->cfg.host_only) {
         amr_status s = upload_pattern(f);
         if (s != AMR_OK) {
             delete f;
@@ -467,13 +533,14 @@ amr_status amr_create_forest(const amr_config *cfg, int init_level, amr_forest *
         *out = f;
         return AMR_OK;
     }
-    const size_t bytes = size_t(cfg->n_states) * cfg->max_blocks * f->block_bytes;
+    const size_t bytes = size_t(f->cfg.n_states) * size_t(capacity) * f->block_bytes;
     f->state = dev_alloc(f, bytes);
     amr_status s = AMR_OK;
     if (!f->state) s = AMR_ENOMEM;
     if (s == AMR_OK && cudaMemset(f->state, 0, bytes) != cudaSuccess) s = AMR_ECUDA;
-    if (s == AMR_OK) s = ensure(f, f->sc, sizeof(DevScalars));
-    if (s == AMR_OK && cudaMemset(f->sc.p, 0, sizeof(DevScalars)) != cudaSuccess) s = AMR_ECUDA;
+    if (s == AMR_OK) s = ensure(f, f->sc, sizeof(DevScalars) * size_t(n));
+    if (s == AMR_OK && cudaMemset(f->sc.p, 0, sizeof(DevScalars) * size_t(n)) != cudaSuccess) s = AMR_ECUDA;
+    if (s == AMR_OK) s = upload_tables(f);
     if (s == AMR_OK) s = upload_pattern(f);
     if (s == AMR_OK && cudaStreamCreateWithFlags(&f->cap_stream, cudaStreamNonBlocking) != cudaSuccess) s = AMR_ECUDA;
     if (s != AMR_OK) {
@@ -485,12 +552,29 @@ amr_status amr_create_forest(const amr_config *cfg, int init_level, amr_forest *
     return AMR_OK;
 }
 
+amr_status amr_create_forest(const amr_config *cfg, int init_level, amr_forest **out) {
+    return amr_create_batch(cfg, &init_level, 1, out);
+}
+
+amr_status amr_n_instances(const amr_forest *f, int *n) {
+    if (!f || !n) return AMR_EINVAL;
+    *n = n_inst(f);
+    return AMR_OK;
+}
+
+amr_status amr_instance_blocks(const amr_forest *f, int inst, int64_t *first, int64_t *n) {
+    if (!f || inst < 0 || inst >= n_inst(f)) return AMR_EINVAL;
+    if (first) *first = f->offset[size_t(inst)];
+    if (n) *n = f->offset[size_t(inst) + 1] - f->offset[size_t(inst)];
+    return AMR_OK;
+}
+
 amr_status amr_destroy_forest(amr_forest *f) {
     if (!f) return AMR_OK;
     if (f->gexec) cudaGraphExecDestroy(f->gexec);
     if (f->cap_stream) cudaStreamDestroy(f->cap_stream);
     for (DBuf *b : {&f->r1, &f->r2, &f->r1g, &f->info, &f->fix, &f->fix_start, &f->bflux, &f->bcdata, &f->sc, &f->partial, &f->sums,
-                    &f->flags, &f->ops, &f->level})
+                    &f->flags, &f->ops, &f->level, &f->dxtab, &f->invdxtab, &f->bctype, &f->bcval, &f->cfltab, &f->ranges})
         dev_free(f, b->p);
     dev_free(f, f->state);
     delete f;
@@ -508,7 +592,7 @@ amr_status amr_get_blocks(const amr_forest *f, int32_t *level, int64_t *coords, 
     const int64_t nb = nblocks(f);
     if (n) *n = nb;
     for (int64_t b = 0; b < std::min(cap, nb); ++b) {
-        const Leaf &l = f->forest.leaves[size_t(b)];
+        const Leaf &l = leaf_at(f, b);
         if (level) level[b] = l.lev;
         if (coords)
             for (int d = 0; d < 3; ++d) coords[3 * b + d] = d < f->cfg.ndim ? l.g[d] : 0;
@@ -523,7 +607,7 @@ amr_status amr_build_ghost_pattern(amr_forest *f) {
 
 amr_status amr_get_ghost_pattern(const amr_forest *f, amr_ghost_entry *out, int64_t cap, int64_t *n) {
     if (!f || cap < 0 || (cap > 0 && !out)) return AMR_EINVAL;
-    if (f->pattern_rev != f->forest.revision) return AMR_ESTATE;
+    if (f->pattern_rev != f->revision) return AMR_ESTATE;
     const auto &e = f->pat.entries;
     if (n) *n = int64_t(e.size());
     for (int64_t i = 0; i < std::min<int64_t>(cap, int64_t(e.size())); ++i)
@@ -594,7 +678,19 @@ amr_status amr_compute_dt(amr_forest *f, int s, amr_stream stream) {
 amr_status amr_set_dt(amr_forest *f, double dt, amr_stream stream) {
     if (!f || !(dt >= 0.0)) return AMR_EINVAL;
     NEED_DEVICE(f);
-    CU(cudaMemcpyAsync(f->sc.p, &dt, sizeof(double), cudaMemcpyHostToDevice, static_cast<cudaStream_t>(stream)));
+    // every instance's dt (the first field of each DevScalars)
+    std::vector<double> v(size_t(n_inst(f)), dt);
+    CU(cudaMemcpy2DAsync(f->sc.p, sizeof(DevScalars), v.data(), sizeof(double), sizeof(double), v.size(),
+                         cudaMemcpyHostToDevice, static_cast<cudaStream_t>(stream)));
+    CU(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    return AMR_OK;
+}
+
+amr_status amr_get_dts(amr_forest *f, double *dts, amr_stream stream) {
+    if (!f || !dts) return AMR_EINVAL;
+    NEED_DEVICE(f);
+    CU(cudaMemcpy2DAsync(dts, sizeof(double), f->sc.p, sizeof(DevScalars), sizeof(double), size_t(n_inst(f)),
+                         cudaMemcpyDeviceToHost, static_cast<cudaStream_t>(stream)));
     CU(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
     return AMR_OK;
 }
@@ -634,7 +730,7 @@ amr_status amr_step(amr_forest *f, int n_steps, int flags, amr_stream stream) {
             if ((r = heun_step(f, st, gather)) != AMR_OK) return r;
         return AMR_OK;
     }
-    if (!f->gexec || f->graph_rev != f->forest.revision || f->graph_flags != flags) {
+    if (!f->gexec || f->graph_rev != f->revision || f->graph_flags != flags) {
         if (f->gexec) {
             cudaGraphExecDestroy(f->gexec);
             f->gexec = nullptr;
@@ -657,7 +753,7 @@ amr_status amr_step(amr_forest *f, int n_steps, int flags, amr_stream stream) {
         e = cudaGraphInstantiate(&f->gexec, graph, 0);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) return fail(f, AMR_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
-        f->graph_rev = f->forest.revision;
+        f->graph_rev = f->revision;
         f->graph_flags = flags;
     }
     for (int i = 0; i < n_steps; ++i) {
@@ -678,6 +774,17 @@ amr_status amr_conserved(amr_forest *f, int s, double *sums, amr_stream stream) 
     return AMR_OK;
 }
 
+amr_status amr_conserved_all(amr_forest *f, int s, double *sums, amr_stream stream) {
+    if (!f || !sums || !valid_slot(f, s)) return AMR_EINVAL;
+    NEED_DEVICE(f);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    amr_status r = dispatch<ConservedFn>(f, s, st);
+    if (r != AMR_OK) return r;
+    CU(cudaMemcpyAsync(sums, f->sums.p, sizeof(double) * f->cfg.n_var * size_t(n_inst(f)), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    return AMR_OK;
+}
+
 amr_status amr_flag(amr_forest *f, int s, const amr_flag_params *p, int8_t *flags_out, amr_stream stream) {
     if (!f || !p || !flags_out || !valid_slot(f, s)) return AMR_EINVAL;
     NEED_DEVICE(f);
@@ -694,57 +801,77 @@ amr_status amr_flag_and_regrid(amr_forest *f, const amr_flag_params *p, const in
     if (changed) *changed = 0;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     amr_status r = AMR_OK;
+    const int64_t nb = nblocks(f);
+    const int ni = n_inst(f);
+    std::vector<int8_t> fl(size_t(std::max<int64_t>(nb, 1)));
     if (f->cfg.host_only) {
         if (!flags) return fail(f, AMR_ESTATE, "host-only forest: regrid needs explicit flags");
-        std::vector<int8_t> fl(flags, flags + nblocks(f));
-        std::vector<Leaf> nl = f->forest.adapted(fl);
-        bool same = nl.size() == f->forest.leaves.size();
-        for (size_t i = 0; same && i < nl.size(); ++i) same = pack_key(nl[i]) == pack_key(f->forest.leaves[i]);
-        if (same) return AMR_OK;
-        if (int64_t(nl.size()) > f->cfg.max_blocks)
-            return fail(f, AMR_ECAPACITY, "regrid needs %zu blocks, capacity is %d", nl.size(), f->cfg.max_blocks);
-        f->forest.assign(std::move(nl));
+        std::copy(flags, flags + nb, fl.begin());
+    } else {
+        r = amr_fill_ghosts(f, 0, stream);
+        if (r != AMR_OK) return r;
+        if (flags) std::copy(flags, flags + nb, fl.begin());
+        else if ((r = amr_flag(f, 0, p, fl.data(), stream)) != AMR_OK) return r;
+    }
+    // adapt every instance with its slice of the flags (Sec. 2.2)
+    std::vector<std::vector<Leaf>> nl(static_cast<size_t>(ni));
+    std::vector<char> moved(size_t(ni), 0);
+    int64_t total = 0;
+    bool any = false;
+    for (int i = 0; i < ni; ++i) {
+        const Forest &F = f->inst[size_t(i)];
+        std::vector<int8_t> part(fl.begin() + f->offset[size_t(i)], fl.begin() + f->offset[size_t(i) + 1]);
+        nl[size_t(i)] = F.adapted(part);
+        bool same = nl[size_t(i)].size() == F.leaves.size();
+        for (size_t k = 0; same && k < nl[size_t(i)].size(); ++k) same = pack_key(nl[size_t(i)][k]) == pack_key(F.leaves[k]);
+        moved[size_t(i)] = !same;
+        any = any || !same;
+        total += int64_t(nl[size_t(i)].size());
+        if (int64_t(nl[size_t(i)].size()) > f->icfg[size_t(i)].max_blocks)
+            return fail(f, AMR_ECAPACITY, "regrid of instance %d needs %zu blocks, its capacity is %d", i, nl[size_t(i)].size(),
+                        f->icfg[size_t(i)].max_blocks);
+    }
+    if (!any) return AMR_OK;
+    if (total > f->cfg.max_blocks) return fail(f, AMR_ECAPACITY, "regrid needs %lld blocks, capacity is %d", (long long)total, f->cfg.max_blocks);
+    if (f->cfg.host_only) {
+        for (int i = 0; i < ni; ++i)
+            if (moved[size_t(i)]) f->inst[size_t(i)].assign(std::move(nl[size_t(i)]));
+        set_offsets(f);
+        ++f->revision;
         if ((r = upload_pattern(f)) != AMR_OK) return r;
         if (changed) *changed = 1;
         return AMR_OK;
     }
-    r = amr_fill_ghosts(f, 0, stream);
-    if (r != AMR_OK) return r;
-    const int64_t nb = nblocks(f);
-    std::vector<int8_t> fl(size_t(std::max<int64_t>(nb, 1)));
-    if (flags) std::copy(flags, flags + nb, fl.begin());
-    else if ((r = amr_flag(f, 0, p, fl.data(), stream)) != AMR_OK) return r;
-    fl.resize(size_t(nb));
-    std::vector<Leaf> nl = f->forest.adapted(fl);
-    bool same = nl.size() == f->forest.leaves.size();
-    for (size_t i = 0; same && i < nl.size(); ++i) same = pack_key(nl[i]) == pack_key(f->forest.leaves[i]);
-    if (same) return AMR_OK;
-    if (int64_t(nl.size()) > f->cfg.max_blocks)
-        return fail(f, AMR_ECAPACITY, "regrid needs %zu blocks, capacity is %d", nl.size(), f->cfg.max_blocks);
-    // old -> new map (Sec. 2.2: copied, refined and coarsened blocks)
+    // old -> new map (Sec. 2.2: copied, refined and coarsened blocks); block
+    // indices are global (instance offset + local)
     const int D = f->cfg.ndim;
-    std::vector<TransferOp> ops(nl.size());
-    for (size_t b = 0; b < nl.size(); ++b) {
-        const Leaf &l = nl[b];
-        TransferOp op{};
-        int o = f->forest.find(l.lev, l.g[0], l.g[1], l.g[2]);
-        if (o >= 0) {
-            op.kind = 0;
-            op.src[0] = o;
-        } else if (l.lev > 0 && (o = f->forest.find(l.lev - 1, l.g[0] >> 1, l.g[1] >> 1, D == 3 ? l.g[2] >> 1 : 0)) >= 0) {
-            op.kind = 1;
-            op.src[0] = o;
-            op.pos = int(l.g[0] & 1) | int(l.g[1] & 1) << 1 | (D == 3 ? int(l.g[2] & 1) << 2 : 0);
-        } else {
-            op.kind = 2;
-            for (int c = 0; c < (1 << D); ++c) {
-                int s = f->forest.find(l.lev + 1, 2 * l.g[0] + (c & 1), 2 * l.g[1] + ((c >> 1) & 1),
-                                       D == 3 ? 2 * l.g[2] + ((c >> 2) & 1) : 0);
-                if (s < 0) return fail(f, AMR_ESTATE, "regrid: block %zu changed by more than one level", b);
-                op.src[c] = s;
+    std::vector<TransferOp> ops;
+    ops.reserve(size_t(total));
+    for (int i = 0; i < ni; ++i) {
+        const Forest &F = f->inst[size_t(i)];
+        const int o0 = int(f->offset[size_t(i)]);
+        for (size_t b = 0; b < nl[size_t(i)].size(); ++b) {
+            const Leaf &l = nl[size_t(i)][b];
+            TransferOp op{};
+            int o = F.find(l.lev, l.g[0], l.g[1], l.g[2]);
+            if (o >= 0) {
+                op.kind = 0;
+                op.src[0] = o0 + o;
+            } else if (l.lev > 0 && (o = F.find(l.lev - 1, l.g[0] >> 1, l.g[1] >> 1, D == 3 ? l.g[2] >> 1 : 0)) >= 0) {
+                op.kind = 1;
+                op.src[0] = o0 + o;
+                op.pos = int(l.g[0] & 1) | int(l.g[1] & 1) << 1 | (D == 3 ? int(l.g[2] & 1) << 2 : 0);
+            } else {
+                op.kind = 2;
+                for (int c = 0; c < (1 << D); ++c) {
+                    int sidx = F.find(l.lev + 1, 2 * l.g[0] + (c & 1), 2 * l.g[1] + ((c >> 1) & 1),
+                                      D == 3 ? 2 * l.g[2] + ((c >> 2) & 1) : 0);
+                    if (sidx < 0) return fail(f, AMR_ESTATE, "regrid: a block of instance %d changed by more than one level", i);
+                    op.src[c] = o0 + sidx;
+                }
             }
+            ops.push_back(op);
         }
-        ops[b] = op;
     }
     // temporary copy of the old blocks (slot 1 when available)
     void *tmp = nullptr;
@@ -759,13 +886,16 @@ amr_status amr_flag_and_regrid(amr_forest *f, const amr_flag_params *p, const in
     }
     if ((r = upload(f, f->ops, ops)) != AMR_OK) return r;
     CU(cudaMemcpyAsync(tmp, slot_ptr(f, 0), old_bytes, cudaMemcpyDeviceToDevice, st));
-    r = dispatch<TransferFn>(f, static_cast<const void *>(tmp), int(nl.size()), st);
+    r = dispatch<TransferFn>(f, static_cast<const void *>(tmp), int(total), st);
     if (own_tmp) {
         cudaStreamSynchronize(st);
         dev_free(f, tmp);
     }
     if (r != AMR_OK) return r;
-    f->forest.assign(std::move(nl));
+    for (int i = 0; i < ni; ++i)
+        if (moved[size_t(i)]) f->inst[size_t(i)].assign(std::move(nl[size_t(i)]));
+    set_offsets(f);
+    ++f->revision;
     if ((r = upload_pattern(f)) != AMR_OK) return r;
     CU(cudaStreamSynchronize(st));
     if (changed) *changed = 1;

@@ -8,7 +8,6 @@
 
 namespace amrb {
 
-constexpr int kMaxLevels = 13;
 
 // Rounded operations that the compiler may not contract into an FMA; used
 // where a result must match a plain IEEE evaluation order bit for bit.
@@ -35,13 +34,15 @@ __device__ __forceinline__ T minmod(T a, T b) {
     return (a > T(0) && b > T(0)) ? lo : ((a < T(0) && b < T(0)) ? hi : T(0));
 }
 
-// Geometry of one forest as seen by the kernels.
+// Geometry of one forest as seen by the kernels.  A forest holds one or
+// more independent mesh instances; cell sizes are looked up by geometry
+// class gc = instance * kMaxLevels + level in device tables [gc][3].
 struct Geom {
     int N, ng, S, D, V;
     int64_t ncell;          // S^D
     int64_t bstride;        // V * ncell
-    double dx[kMaxLevels][3];
-    double inv_dx[kMaxLevels][3];
+    const double *dx;       // [n_instances * kMaxLevels][3]
+    const double *inv_dx;
 };
 
 // Device-resident scalars of a forest.

@@ -17,9 +17,9 @@ struct GhostArgs {
     const Entry *list;
     int n;
     const real *bcdata;      // [n_bc][V][N^(D-1)]
-    int bc_type[6];
-    real bc_val[6][8];
-    const int32_t *level;    // per block (BlockInfo would do; a plain array keeps loads small)
+    const int32_t *bc_type;  // [instance][6]
+    const real *bc_val;      // [instance][6][8]
+    const BlockInfo *info;   // per block: instance and geometry class
 };
 
 // Restriction (Sec. 2.2): mean of the 2^D fine cells starting at fine index
@@ -177,12 +177,14 @@ __global__ void __launch_bounds__(256) k_ghost(GhostArgs<real> a, Geom g) {
             int y[3] = {x[0], x[1], x[2]};
             y[nd] = side ? N - k : k - 1;                          // mirror cell
             const real um = dstb[int64_t(v) * g.ncell + cell_index<real>(g, y[0], y[1], y[2])];
-            const int ty = a.bc_type[e.face];
+            const int inst = a.info[e.dst].inst;
+            const int ty = a.bc_type[6 * inst + e.face];
+            const real bv = a.bc_val[(6 * inst + e.face) * 8 + v];
             if (ty == 1) {
-                val = real(2) * a.bc_val[e.face][v] - um;
+                val = real(2) * bv - um;
             } else if (ty == 2) {
-                const real h = mul_rn(real(2 * k - 1), real(g.dx[a.level[e.dst]][nd]));
-                val = add_rn(um, mul_rn(h, a.bc_val[e.face][v]));
+                const real h = mul_rn(real(2 * k - 1), real(g.dx[3 * a.info[e.dst].gclass + nd]));
+                val = add_rn(um, mul_rn(h, bv));
             } else {
                 const int t = x[tdim[0]] + (D == 3 ? N * x[tdim[1]] : 0);
                 const int64_t nface = (D == 3) ? int64_t(N) * N : N;

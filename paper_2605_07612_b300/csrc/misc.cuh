@@ -35,8 +35,8 @@ __global__ void k_fluxfix(FixArgs<real> a, Geom g) {
     const int nface = (D == 3) ? N * N : N;
     const int first = a.fix_start[blockIdx.x], last = a.fix_start[blockIdx.x + 1];
     const int b = a.fix[first].block;
-    const int lev = a.info[b].level;
-    const real dt_eff = real(a.w_dt * a.sc->dt);
+    const int gc = a.info[b].gclass, inst = a.info[b].inst;
+    const real dt_eff = real(a.w_dt * a.sc[inst].dt);
     real *ub = a.u + int64_t(b) * g.bstride;
     real vmax = real(0);
     for (int q = first; q < last; ++q) {
@@ -45,7 +45,7 @@ __global__ void k_fluxfix(FixArgs<real> a, Geom g) {
         int td[2] = {-1, -1};
         for (int d = 0, c = 0; d < D; ++d)
             if (d != n) td[c++] = d;
-        const real coef = dt_eff * real(g.inv_dx[lev][n]);
+        const real coef = dt_eff * real(g.inv_dx[3 * gc + n]);
         for (int t = threadIdx.x; t < nface; t += blockDim.x) {
             const int t0 = t % N, t1 = (D == 3) ? t / N : 0;
             const int o0 = t0 >= N / 2, o1 = (D == 3) ? (t1 >= N / 2) : 0;
@@ -98,13 +98,13 @@ __global__ void k_fluxfix(FixArgs<real> a, Geom g) {
             const real p = (a.gamma - real(1)) * (U[D + 1] - real(0.5) * ke);
             const real c = sqrt(a.gamma * p / rho);
             real s = real(0);
-            for (int d = 0; d < D; ++d) s += (fabs(U[1 + d] * ir) + c) * real(g.inv_dx[lev][d]);
+            for (int d = 0; d < D; ++d) s += (fabs(U[1 + d] * ir) + c) * real(g.inv_dx[3 * gc + d]);
             vmax = s > vmax ? s : vmax;
         }
     }
     double m = double(vmax);
     for (int s = 16; s > 0; s >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, s));
-    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(&a.sc->maxspeed_bits, m);
+    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(&a.sc[inst].maxspeed_bits, m);
 }
 
 // ------------------------------------------------------------------- CFL dt
@@ -114,7 +114,7 @@ __global__ void k_maxspeed(const real *u, const BlockInfo *info, DevScalars *sc,
     const int b = blockIdx.x;
     const int N = g.N;
     const int ncell = (D == 3) ? N * N * N : N * N;
-    const int lev = info[b].level;
+    const int gc = info[b].gclass, inst = info[b].inst;
     const real *ub = u + int64_t(b) * g.bstride;
     real vmax = real(0);
     for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
@@ -128,20 +128,21 @@ __global__ void k_maxspeed(const real *u, const BlockInfo *info, DevScalars *sc,
         const real p = (gam - real(1)) * (U[D + 1] - real(0.5) * ke);
         const real cs = sqrt(gam * p / rho);
         real s = real(0);
-        for (int d = 0; d < D; ++d) s += (fabs(U[1 + d] * ir) + cs) * real(g.inv_dx[lev][d]);
+        for (int d = 0; d < D; ++d) s += (fabs(U[1 + d] * ir) + cs) * real(g.inv_dx[3 * gc + d]);
         vmax = s > vmax ? s : vmax;
     }
     double m = double(vmax);
     for (int s = 16; s > 0; s >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, s));
-    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(&sc->maxspeed_bits, m);
+    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(&sc[inst].maxspeed_bits, m);
 }
 
-// dt = cfl / max speed; resets the accumulator for the next reduction
-__global__ void k_dt_commit(DevScalars *sc, double cfl) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        const double m = __longlong_as_double((long long)sc->maxspeed_bits);
-        sc->dt = (m > 0.0) ? cfl / m : 0.0;
-        sc->maxspeed_bits = 0ull;
+// dt = cfl / max speed per instance; resets the accumulators
+__global__ void k_dt_commit(DevScalars *sc, const double *cfl, int n_inst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_inst) {
+        const double m = __longlong_as_double((long long)sc[i].maxspeed_bits);
+        sc[i].dt = (m > 0.0) ? cfl[i] / m : 0.0;
+        sc[i].maxspeed_bits = 0ull;
     }
 }
 
@@ -155,9 +156,9 @@ __global__ void __launch_bounds__(256) k_conserved_block(const real *u, const Bl
     const int b = blockIdx.x;
     const int N = g.N;
     const int ncell = (D == 3) ? N * N * N : N * N;
-    const int lev = info[b].level;
+    const int gc = info[b].gclass;
     double vol = 1.0;
-    for (int d = 0; d < D; ++d) vol *= g.dx[lev][d];
+    for (int d = 0; d < D; ++d) vol *= g.dx[3 * gc + d];
     for (int v = 0; v < g.V; ++v) {
         const real *ub = u + int64_t(b) * g.bstride + int64_t(v) * g.ncell;
         double s = 0.0;
@@ -176,11 +177,14 @@ __global__ void __launch_bounds__(256) k_conserved_block(const real *u, const Bl
     }
 }
 
-__global__ void __launch_bounds__(1024) k_conserved_final(const double *partial, int nb, int V, double *out) {
+// one CTA per instance: blocks [range[i], range[i+1]) in a fixed tree order
+__global__ void __launch_bounds__(1024) k_conserved_final(const double *partial, const int64_t *range, int V, double *out) {
     __shared__ double red[1024];
+    const int64_t b0 = range[blockIdx.x], b1 = range[blockIdx.x + 1];
+    out += int64_t(blockIdx.x) * V;
     for (int v = 0; v < V; ++v) {
         double s = 0.0;
-        for (int b = threadIdx.x; b < nb; b += blockDim.x) s += partial[int64_t(b) * V + v];
+        for (int64_t b = b0 + threadIdx.x; b < b1; b += blockDim.x) s += partial[b * V + v];
         red[threadIdx.x] = s;
         __syncthreads();
         for (int w = 512; w > 0; w >>= 1) {

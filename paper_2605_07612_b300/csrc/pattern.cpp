@@ -9,14 +9,21 @@
 
 namespace amrb {
 
-bool build_pattern(const Forest &F, Pattern &P, std::string &err) {
+bool build_pattern(const std::vector<const Forest *> &inst, const std::vector<int64_t> &offset, Pattern &P,
+                   std::string &err) {
+    P = Pattern();
+    int nb = 0;
+    for (const Forest *F : inst) nb += int(F->leaves.size());
+    P.entries.reserve(size_t(nb) * 6);
+    for (size_t ii = 0; ii < inst.size(); ++ii) {
+    const Forest &F = *inst[ii];
     const Geometry &G = F.geo;
     const int D = G.ndim;
-    const int nb = int(F.leaves.size());
-    P = Pattern();
-    P.entries.reserve(size_t(nb) * 2 * D);
-    for (int b = 0; b < nb; ++b) {
-        const Leaf &A = F.leaves[b];
+    const int o0 = int(offset[ii]);
+    const int nbi = int(F.leaves.size());
+    for (int bl = 0; bl < nbi; ++bl) {
+        const int b = o0 + bl;
+        const Leaf &A = F.leaves[bl];
         for (int f = 0; f < 2 * D; ++f) {
             const int n = f >> 1, side = f & 1;
             int t0 = -1, t1 = -1;
@@ -30,14 +37,14 @@ bool build_pattern(const Forest &F, Pattern &P, std::string &err) {
             }
             int s = F.find(A.lev, q[0], q[1], q[2]);
             if (s >= 0) {
-                P.entries.push_back({KIND_SRL, f, b, s, 0, 0});
+                P.entries.push_back({KIND_SRL, f, b, o0 + s, 0, 0});
                 continue;
             }
             if (A.lev > 0) {
                 int c = F.find(A.lev - 1, q[0] >> 1, q[1] >> 1, D == 3 ? q[2] >> 1 : 0);
                 if (c >= 0) {
                     int off = int(A.g[t0] & 1) | (D == 3 ? int(A.g[t1] & 1) << 1 : 0);
-                    P.entries.push_back({KIND_C2F, f, b, c, off, 0});
+                    P.entries.push_back({KIND_C2F, f, b, o0 + c, off, 0});
                     continue;
                 }
             }
@@ -53,9 +60,10 @@ bool build_pattern(const Forest &F, Pattern &P, std::string &err) {
                           " has no leaf neighbour within one level (2:1 balance broken)";
                     return false;
                 }
-                P.entries.push_back({KIND_F2C, f, b, fs, o, 0});
+                P.entries.push_back({KIND_F2C, f, b, o0 + fs, o, 0});
             }
         }
+    }
     }
     std::sort(P.entries.begin(), P.entries.end(), [](const Entry &x, const Entry &y) {
         if (x.kind != y.kind) return x.kind < y.kind;
@@ -70,8 +78,14 @@ bool build_pattern(const Forest &F, Pattern &P, std::string &err) {
 
     // execution lists and refinement-face flux slots
     P.info.assign(size_t(nb), BlockInfo{});
+    for (size_t ii = 0; ii < inst.size(); ++ii)
+        for (size_t bl = 0; bl < inst[ii]->leaves.size(); ++bl) {
+            const size_t b = size_t(offset[ii]) + bl;
+            P.info[b].level = inst[ii]->leaves[bl].lev;
+            P.info[b].inst = int32_t(ii);
+            P.info[b].gclass = int32_t(ii) * kMaxLevels + P.info[b].level;
+        }
     for (int b = 0; b < nb; ++b) {
-        P.info[b].level = F.leaves[b].lev;
         P.info[b].fixmask = 0;
         for (int f = 0; f < 6; ++f) P.info[b].bslot[f] = P.info[b].nbr[f] = -1;
     }

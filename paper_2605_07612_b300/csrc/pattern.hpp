@@ -12,6 +12,8 @@
 
 namespace amrb {
 
+constexpr int kMaxLevels = 13;   // levels 0..12 per instance
+
 enum : int32_t { KIND_SRL = 0, KIND_F2C = 1, KIND_BC = 2, KIND_C2F = 3 };
 
 struct Entry {
@@ -31,6 +33,8 @@ struct BlockInfo {
     int32_t fixmask;    // bit f: face f is the coarse side of a refinement face
     int32_t bslot[6];   // flux slot of face f, -1 if not a refinement face
     int32_t nbr[6];     // same-level neighbour across face f, -1 if none
+    int32_t inst;       // mesh instance of the block
+    int32_t gclass;     // inst * kMaxLevels + level: row of the cell-size tables
 };
 
 struct Pattern {
@@ -48,8 +52,11 @@ struct Pattern {
     int32_t n_bc = 0;
 };
 
-// Returns false (with a message) if some face has no valid neighbour
-// configuration (2:1 balance broken).
-bool build_pattern(const Forest &f, Pattern &out, std::string &err);
+// Builds the pattern of one or more independent mesh instances whose blocks
+// are numbered consecutively (instance i owns blocks offset[i] ..
+// offset[i] + n_i - 1).  Returns false (with a message) if some face has no
+// valid neighbour configuration (2:1 balance broken).
+bool build_pattern(const std::vector<const Forest *> &inst, const std::vector<int64_t> &offset, Pattern &out,
+                   std::string &err);
 
 }  // namespace amrb

@@ -38,8 +38,8 @@ struct StageArgs {
     real wprev[4];
     int nprev;
     double w_dt;
-    const DevScalars *sc_in;     // dt
-    DevScalars *sc;              // max speed accumulation, status
+    const DevScalars *sc_in;     // per instance: dt
+    DevScalars *sc;              // per instance: max speed accumulation; status in [0]
     const BlockInfo *info;
     real *bflux;                 // [slot][V][N^(D-1)]
     int update_dt;
@@ -175,12 +175,12 @@ __global__ void __launch_bounds__(T * T) k_stage(StageArgs<real> a, Geom g) {
     const int tx0 = (tile % (N / T)) * T, ty0 = (tile / (N / T)) * T;
     const int ti = tid % T, tj = tid / T;
     const BlockInfo info = a.info[b];
-    const int lev = info.level;
-    const real idx0 = real(g.inv_dx[lev][0]), idx1 = real(g.inv_dx[lev][1]);
-    const real idx2 = (D == 3) ? real(g.inv_dx[lev][2]) : real(0);
+    const int gc = info.gclass;
+    const real idx0 = real(g.inv_dx[3 * gc + 0]), idx1 = real(g.inv_dx[3 * gc + 1]);
+    const real idx2 = (D == 3) ? real(g.inv_dx[3 * gc + 2]) : real(0);
     const real gam = a.gamma;
     const real gm1i = real(1) / (gam - real(1));
-    const real dt_eff = real(a.w_dt * a.sc_in->dt);
+    const real dt_eff = real(a.w_dt * a.sc_in[info.inst].dt);
     const real *__restrict__ ub = a.deriv + int64_t(b) * V * NC;
     // halo source: in gather mode a cell outside the block across a face with
     // a same-level neighbour is read from that neighbour's interior
@@ -524,9 +524,9 @@ __global__ void __launch_bounds__(T * T) k_stage(StageArgs<real> a, Geom g) {
     if (a.update_dt) {
         double m = double(vmax);
         for (int s = 16; s > 0; s >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, s));
-        if ((tid & 31) == 0) atomic_max_nonneg(&a.sc->maxspeed_bits, m);
+        if ((tid & 31) == 0) atomic_max_nonneg(&a.sc[info.inst].maxspeed_bits, m);
     }
-    if (__syncthreads_or(nonphys) && tid == 0) raise_status(&a.sc->status, 7);
+    if (__syncthreads_or(nonphys) && tid == 0) raise_status(&a.sc[0].status, 7);
 }
 
 }  // namespace amrb

@@ -151,11 +151,11 @@ __global__ void __launch_bounds__(PairShape<N>::NT, (N >= 16 ? 4 : 1)) k_stage_p
     const int ip = tid % (T / 2), tj = tid / (T / 2);
     const int ci = 2 * ip;                                      // first cell of the pair
     const BlockInfo info = a.info[b];
-    const int lev = info.level;
-    const float idx0 = float(g.inv_dx[lev][0]), idx1 = float(g.inv_dx[lev][1]), idx2 = float(g.inv_dx[lev][2]);
+    const int gc = info.gclass;
+    const float idx0 = float(g.inv_dx[3 * gc]), idx1 = float(g.inv_dx[3 * gc + 1]), idx2 = float(g.inv_dx[3 * gc + 2]);
     const float gam = a.gamma;
     const float gm1i = 1.f / (gam - 1.f);
-    const float dt_eff = float(a.w_dt * a.sc_in->dt);
+    const float dt_eff = float(a.w_dt * a.sc_in[info.inst].dt);
     const float *__restrict__ ub = a.deriv + int64_t(b) * V * NC;
     // same-level neighbours (scalars: a runtime-indexed array would live in local memory)
     const int nb0 = a.gather ? info.nbr[0] : -1, nb1 = a.gather ? info.nbr[1] : -1;
@@ -454,9 +454,9 @@ __global__ void __launch_bounds__(PairShape<N>::NT, (N >= 16 ? 4 : 1)) k_stage_p
     if (a.update_dt) {
         double m = double(vmax);
         for (int s = 16; s > 0; s >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, s));
-        if ((tid & 31) == 0) atomic_max_nonneg(&a.sc->maxspeed_bits, m);
+        if ((tid & 31) == 0) atomic_max_nonneg(&a.sc[info.inst].maxspeed_bits, m);
     }
-    if (__syncthreads_or(nonphys) && tid == 0) raise_status(&a.sc->status, 7);
+    if (__syncthreads_or(nonphys) && tid == 0) raise_status(&a.sc[0].status, 7);
 }
 
 }  // namespace amrb

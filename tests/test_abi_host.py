@@ -120,3 +120,37 @@ def test_uniform_3d_configs_shape():
         assert f.n == nt ** 3
         pat = f.pattern()
         assert len(pat) == 6 * nt ** 3 and np.all(pat[:, 0] == amr.KIND_SRL)
+
+
+def test_batch_pattern_is_union_of_instance_patterns():
+    """A forest of several independent instances numbers their blocks
+    consecutively; its pattern is every instance's pattern with block
+    indices shifted, in canonical order, and BC rows renumbered."""
+    specs = [synth.MeshSpec(ndim=2, N=8, ng=2, ntrees=(2, 3, 1), max_level=2),
+             synth.MeshSpec(ndim=2, N=8, ng=2, ntrees=(4, 1, 1), periodic=(0, 1, 1), max_level=1,
+                            bc_type=(2, 2, 0, 0, 0, 0)),
+             synth.MeshSpec(ndim=2, N=8, ng=2, ntrees=(1, 1, 1), periodic=(0, 0, 1), max_level=3,
+                            bc_type=(1, 1, 1, 1, 0, 0))]
+    levels = [1, 0, 2]
+    f = amr.Forest(None, batch=[(sp, lv, 4096) for sp, lv in zip(specs, levels)], host_only=True)
+    rng = np.random.default_rng(3)
+    oms = [oracle.Mesh(sp, lv) for sp, lv in zip(specs, levels)]
+    for _ in range(2):
+        flags = [rng.choice(np.array([-1, 0, 1], dtype=np.int8), size=m.n) for m in oms]
+        oms = [m.adapt(fl) for m, fl in zip(oms, flags)]
+        f.regrid(np.concatenate(flags))
+    rows, off = [], 0
+    for i, m in enumerate(oms):
+        first, n = f.instance_blocks(i)
+        assert first == off and n == m.n
+        pat = m.pattern().astype(np.int64)
+        pat[:, 2] += off
+        pat[:, 3] = np.where(pat[:, 3] >= 0, pat[:, 3] + off, -1)
+        rows.append(pat)
+        off += m.n
+    exp = np.concatenate(rows)
+    exp = exp[np.lexsort((exp[:, 4], exp[:, 2], exp[:, 1], exp[:, 0]))]
+    bc = exp[:, 0] == oracle.KIND_BC
+    exp[bc, 5] = np.arange(bc.sum())
+    np.testing.assert_array_equal(f.pattern(), exp)
+    assert f.n_instances == 3
