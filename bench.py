@@ -188,6 +188,7 @@ def run_ours(args, rank, world, dist):
     spec = workload_spec(16)
     cells = spec.ntrees[0] * spec.ntrees[1] * spec.ntrees[2] * spec.N ** 3
     f = make(spec, 32)
+    tune_choice, tune_ms = f.autotune(stream=stream)
     state_bytes = f.n * spec.nvar * spec.ncell * 4
     with ClockSampler(dev) as clk:
         ms, launches = time_steps(f, args.steps, args.warmup, True, True)
@@ -260,6 +261,7 @@ def run_ours(args, rank, world, dist):
             del fb
             torch.cuda.empty_cache()
         extras["block_sizes"] = bs
+        extras["batched_2d"] = run_batched(args, amr, torch, stream, barrier, world)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -278,9 +280,83 @@ def run_ours(args, rank, world, dist):
                 "steps": e2e_steps},
         "gpu_launches": launches,
         "clocks": clocks,
+        "autotune": {"choice": tune_choice, "stage_ms": tune_ms,
+                     "meaning": "0 = persistent grid, k = k (block, tile) items per CTA, +100 = per-cell kernel"},
     }
     line.update(extras)
     return line
+
+
+# ------------------------------------------------ batched 2D instances --
+
+def batched_specs(seed=5, n=64):
+    """64 independent 2D meshes of uneven size: base grids of 4x4 .. 64x64
+    blocks of 16^2 cells (log-uniform), 1-4 levels, half Kelvin-Helmholtz
+    (periodic), half Sod-type tubes along x or y (Neumann ends)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(n):
+        nb = int(2 ** rng.integers(2, 7))          # 4 .. 64 base blocks per side
+        levels = int(rng.integers(1, 5))           # 1 .. 4 levels
+        kind = "kh" if i % 2 == 0 else "tube"
+        if kind == "kh":
+            sp = synth.MeshSpec(ndim=2, N=16, ng=2, ntrees=(nb, nb, 1), max_level=levels - 1)
+        else:
+            axis = int(rng.integers(0, 2))
+            per = [1, 1, 1]
+            per[axis] = 0
+            bct = [0] * 6
+            bct[2 * axis] = bct[2 * axis + 1] = synth.BC_NEUMANN
+            sp = synth.MeshSpec(ndim=2, N=16, ng=2, ntrees=(nb, nb, 1), periodic=tuple(per), max_level=levels - 1,
+                                bc_type=tuple(bct))
+        out.append((sp, kind, float(rng.uniform(0.3, 0.7)), int(rng.integers(0, 2**31)),
+                    (int(np.argmin(sp.periodic[:2])) if kind == "tube" else 0)))
+    return out
+
+
+def run_batched(args, amr, torch, stream, barrier, world):
+    specs = batched_specs()
+    cap = [int(sp.ntrees[0] * sp.ntrees[1] * 4 ** sp.max_level) for sp, *_ in specs]
+    f = amr.Forest(None, batch=[(sp, 0, c) for (sp, *_), c in zip(specs, cap)], precision=32)
+
+    def init():
+        lev, g = f.blocks()
+        parts = []
+        for i, (sp, kind, x0, seed, axis) in enumerate(specs):
+            first, n = f.instance_blocks(i)
+            l, gg = lev[first:first + n], g[first:first + n]
+            if kind == "kh":
+                parts.append(synth.kelvin_helmholtz(sp, l, gg, seed=seed))
+            else:
+                parts.append(synth.shock_tube(sp, l, gg, x0=x0, axis=axis))
+        return np.concatenate(parts).astype(np.float32)
+
+    # initial refinement from the Lohner flags of the initial state (Sec. 3.3)
+    for _ in range(3):
+        f.set_state(0, init())
+        if not f.regrid(None, c_ref=5e-2, c_deref=-1.0):
+            break
+    f.set_state(0, init())
+    f.compute_dt(0, stream=stream)
+    choice, tms = f.autotune(stream=stream)
+    cells = f.n * 16 * 16
+    steps = max(args.steps, 10)
+    f.step(args.warmup, use_graph=True, gather=True, stream=stream)
+    stream.synchronize()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    f.step(steps, use_graph=True, gather=True, stream=stream)
+    e1.record(stream)
+    stream.synchronize()
+    ms = e0.elapsed_time(e1)
+    lev, _ = f.blocks()
+    return {"value": 2.0 * cells * steps * world / (ms * 1e-3), "unit": UNIT, "instances": len(specs),
+            "blocks": f.n, "cells": cells, "levels_max": int(lev.max()) + 1, "ms_per_step": ms / steps,
+            "steps": steps, "autotune_choice": choice,
+            "workload": "64 2D AMR meshes, 4x4..64x64 base blocks of 16^2, 1-4 levels (Lohner-refined), KH or Sod, FP32, "
+                        "one launch per phase over all meshes, step replayed as a CUDA graph"}
 
 
 # ------------------------------------------------------- CPU oracle arm --

@@ -271,6 +271,17 @@ amr_status amr_flag(amr_forest *f, int s, const amr_flag_params *prm, int8_t *fl
 amr_status amr_flag_and_regrid(amr_forest *f, const amr_flag_params *prm, const int8_t *flags,
                                int *changed, amr_stream stream);
 
+/* Autotuner: times the stage kernel on this forest's mesh for each
+ * candidate launch shape -- (block, tile) items per CTA 1, 2 or 4, or a
+ * persistent grid of SMs x resident CTAs sweeping all items -- and, for FP32
+ * 3D with two ghost layers, the staging tile (packed cell-pair kernel versus
+ * one cell per thread); keeps the fastest for later stages and steps.  The
+ * timed stages write slot 1 only: slot 0's interior is not advanced (its
+ * ghost cells are refilled).  *choice (may be
+ * NULL) = 100 x (per-cell kernel) + items per CTA, 0 for persistent; *best_ms
+ * = mean time of one stage launch of the choice. */
+amr_status amr_autotune(amr_forest *f, int *choice, double *best_ms, amr_stream stream);
+
 /* Reads and clears the device status word (synchronises `stream`): AMR_OK or
  * the first device-side error (AMR_ENONPHYS, AMR_ETIMEOUT, AMR_EBOUNDS). */
 amr_status amr_sync_status(amr_forest *f, amr_stream stream);

@@ -29,7 +29,7 @@ EXPORTED = [
     "amr_fill_ghosts", "amr_compute_dt", "amr_set_dt", "amr_get_dt", "amr_advance_stage", "amr_step",
     "amr_conserved", "amr_flag", "amr_flag_and_regrid", "amr_sync_status", "amr_last_error",
     "amr_launch_count", "amr_conserved_static", "amr_create_batch", "amr_n_instances", "amr_instance_blocks",
-    "amr_get_dts", "amr_conserved_all",
+    "amr_get_dts", "amr_conserved_all", "amr_autotune",
 ]
 
 
@@ -114,6 +114,7 @@ def load(build_if_missing: bool = True):
         "amr_instance_blocks": [vp, C.c_int, P(i64), P(i64)],
         "amr_get_dts": [vp, vp, vp],
         "amr_conserved_all": [vp, C.c_int, vp, vp],
+        "amr_autotune": [vp, P(C.c_int), P(C.c_double), vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -343,6 +344,12 @@ class Forest:
         self._check(self.lib.amr_flag_and_regrid(self.h, C.byref(p), None if fl is None else fl.ctypes.data,
                                                  C.byref(ch), _stream_ptr(stream)), "amr_flag_and_regrid")
         return bool(ch.value)
+
+    def autotune(self, stream=None):
+        """Picks the fastest stage launch shape for this mesh; returns (choice, ms)."""
+        ch, ms = C.c_int(), C.c_double()
+        self._check(self.lib.amr_autotune(self.h, C.byref(ch), C.byref(ms), _stream_ptr(stream)), "amr_autotune")
+        return int(ch.value), float(ms.value)
 
     def sync_status(self, stream=None) -> int:
         return int(self.lib.amr_sync_status(self.h, _stream_ptr(stream)))

@@ -52,7 +52,10 @@ struct amr_forest {
     uint64_t graph_rev = ~0ull;
     int64_t graph_nodes = 0;
     int graph_flags = -1;
-    bool scalar_stage = false;   // force the per-cell FP32 kernel (AMR_SCALAR_STAGE=1)
+    bool scalar_stage = false;   // per-cell FP32 kernel instead of the pair kernel (tuning choice)
+    int items_per_cta = 1;       // stage launch: CTAs loop over this many (block, tile) items
+    bool persistent = false;     // stage launch: grid = SMs x resident CTAs, grid-stride sweep
+    int n_sms = 0;
     bool capturing = false;
     int64_t launches = 0;
     std::string err;
@@ -117,6 +120,13 @@ amr_status upload(amr_forest *f, DBuf &b, const std::vector<T> &v) {
 
 int64_t nblocks(const amr_forest *f) { return f->offset.empty() ? 0 : f->offset.back(); }
 int n_inst(const amr_forest *f) { return int(f->inst.size()); }
+
+// grid of a stage launch for `items` (block, tile) items under the forest's tuning
+int64_t stage_grid(const amr_forest *f, int64_t items, int occupancy) {
+    if (f->persistent) return std::max<int64_t>(1, std::min<int64_t>(items, int64_t(f->n_sms) * std::max(occupancy, 1)));
+    return (items + f->items_per_cta - 1) / f->items_per_cta;
+}
+
 
 void set_offsets(amr_forest *f) {
     f->offset.assign(1, 0);
@@ -278,9 +288,14 @@ amr_status launch_stage_t(amr_forest *f, const StageArgs<real> &a, cudaStream_t 
         CU(cudaFuncSetAttribute(k_stage<real, D, N, NG, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
         attr_done = true;
     }
-    const int64_t grid = nblocks(f) * Sh::TILES;
-    if (grid > 0) {
-        k_stage<real, D, N, NG, T><<<unsigned(grid), Sh::NT, smem, st>>>(a, f->geom);
+    const int64_t items = nblocks(f) * Sh::TILES;
+    if (items > 0) {
+        StageArgs<real> b = a;
+        b.n_items = int(items);
+        int occ = 1;
+        if (f->persistent) CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_stage<real, D, N, NG, T>, Sh::NT, smem));
+        const int64_t grid = stage_grid(f, items, occ);
+        k_stage<real, D, N, NG, T><<<unsigned(grid), Sh::NT, smem, st>>>(b, f->geom);
         ++f->launches;
     }
     CU(cudaGetLastError());
@@ -297,9 +312,14 @@ amr_status launch_stage_pair(amr_forest *f, const StageArgs<float> &a, cudaStrea
         CU(cudaFuncSetAttribute(k_stage_pair<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
         attr_done = true;
     }
-    const int64_t grid = nblocks(f) * Sh::TILES;
-    if (grid > 0) {
-        k_stage_pair<N><<<unsigned(grid), Sh::NT, smem, st>>>(a, f->geom);
+    const int64_t items = nblocks(f) * Sh::TILES;
+    if (items > 0) {
+        StageArgs<float> b = a;
+        b.n_items = int(items);
+        int occ = 1;
+        if (f->persistent) CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_stage_pair<N>, Sh::NT, smem));
+        const int64_t grid = stage_grid(f, items, occ);
+        k_stage_pair<N><<<unsigned(grid), Sh::NT, smem, st>>>(b, f->geom);
         ++f->launches;
     }
     CU(cudaGetLastError());
@@ -502,7 +522,11 @@ amr_status amr_create_batch(const amr_config *cfgs, const int *init_levels, int 
     f->cfg.max_blocks = int(capacity);
     f->icfg.assign(cfgs, cfgs + n);
     f->esize = f->cfg.precision / 8;
-    if (const char *e = std::getenv("AMR_SCALAR_STAGE")) f->scalar_stage = e[0] == '1';
+    if (!f->cfg.host_only) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&f->n_sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaGetLastError();
+    }
     fill_geom(f);
     f->block_bytes = size_t(f->geom.bstride) * f->esize;
     f->inst.resize(size_t(n));
@@ -914,6 +938,56 @@ amr_status amr_sync_status(amr_forest *f, amr_stream stream) {
         CU(cudaMemcpy(static_cast<char *>(f->sc.p) + offsetof(DevScalars, status), &zero, sizeof zero, cudaMemcpyHostToDevice));
         return fail(f, amr_status(h.status), "device reported status %d", h.status);
     }
+    return AMR_OK;
+}
+
+amr_status amr_autotune(amr_forest *f, int *choice, double *best_ms, amr_stream stream) {
+    if (!f) return AMR_EINVAL;
+    NEED_DEVICE(f);
+    if (f->cfg.n_states < 2 || f->cfg.n_ghost < 2) return fail(f, AMR_EINVAL, "autotuning times a stage into slot 1 (needs n_states >= 2, n_ghost >= 2)");
+    amr_status r = upload_pattern(f);
+    if (r != AMR_OK) return r;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    struct Cand { bool scalar; int ipc; bool pers; };
+    std::vector<Cand> cands;
+    const bool pair_ok = f->cfg.precision == 32 && f->cfg.ndim == 3 && f->cfg.n_ghost == 2;
+    for (int sc = 0; sc < (pair_ok ? 2 : 1); ++sc) {
+        for (int ipc : {1, 2, 4}) cands.push_back({sc == 1, ipc, false});
+        cands.push_back({sc == 1, 1, true});
+    }
+    // a stage that leaves slot 0 alone: slot 1 = slot 0 (w_dt = 0), halos gathered
+    amr_stage probe{1, 0, 1, {0, 0, 0, 0}, {1.0, 0, 0, 0}, 0.0, 0, 1};
+    if ((r = dispatch<GhostFn>(f, 0, st, true)) != AMR_OK) return r;
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    int best = -1;
+    float best_t = 0.f;
+    for (size_t c = 0; c < cands.size(); ++c) {
+        f->scalar_stage = cands[c].scalar;
+        f->items_per_cta = cands[c].ipc;
+        f->persistent = cands[c].pers;
+        if ((r = dispatch<StageFn>(f, &probe, st)) != AMR_OK) break;      // warm-up
+        cudaEventRecord(e0, st);
+        for (int rep = 0; rep < 3; ++rep)
+            if ((r = dispatch<StageFn>(f, &probe, st)) != AMR_OK) break;
+        cudaEventRecord(e1, st);
+        if (r != AMR_OK) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) { r = AMR_ECUDA; break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= 3.f;
+        if (best < 0 || ms < best_t) { best = int(c); best_t = ms; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (r != AMR_OK) return r;
+    f->scalar_stage = cands[size_t(best)].scalar;
+    f->items_per_cta = cands[size_t(best)].ipc;
+    f->persistent = cands[size_t(best)].pers;
+    f->graph_rev = ~0ull;     // launch shapes changed: re-capture
+    if (choice) *choice = (f->scalar_stage ? 100 : 0) + (f->persistent ? 0 : f->items_per_cta);
+    if (best_ms) *best_ms = best_t;
     return AMR_OK;
 }
 

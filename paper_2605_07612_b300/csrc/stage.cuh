@@ -44,6 +44,7 @@ struct StageArgs {
     real *bflux;                 // [slot][V][N^(D-1)]
     int update_dt;
     int gather;                  // halo cells across SRL faces from the neighbour's interior
+    int n_items;                 // blocks x column tiles; CTAs loop over them with a grid stride
     real gamma;
 };
 
@@ -155,7 +156,7 @@ struct StageShape {
 };
 
 template <class real, int D, int N, int NG, int T>
-__global__ void __launch_bounds__(T * T) k_stage(StageArgs<real> a, Geom g) {
+__device__ __forceinline__ void stage_item(const StageArgs<real> &a, const Geom &g, int item) {
     using Sh = StageShape<real, D, N, NG, T>;
     using E = Euler<real, D>;
     using V2 = typename Vec2<real>::type;
@@ -170,8 +171,8 @@ __global__ void __launch_bounds__(T * T) k_stage(StageArgs<real> a, Geom g) {
     real *Fy = Fx + V * NFX;                                   // [V][T+1][T]
 
     const int tid = threadIdx.x;
-    const int b = blockIdx.x / Sh::TILES;
-    const int tile = blockIdx.x - b * Sh::TILES;
+    const int b = item / Sh::TILES;
+    const int tile = item - b * Sh::TILES;
     const int tx0 = (tile % (N / T)) * T, ty0 = (tile / (N / T)) * T;
     const int ti = tid % T, tj = tid / T;
     const BlockInfo info = a.info[b];
@@ -518,6 +519,7 @@ __global__ void __launch_bounds__(T * T) k_stage(StageArgs<real> a, Geom g) {
         if (tid < 2 * T) extra_face(0);
         __syncthreads();
         update(0);
+        __syncthreads();   // shared memory is reused by the CTA's next item
     }
 
     // ---- CTA reductions: max speed and non-physical flag
@@ -527,6 +529,13 @@ __global__ void __launch_bounds__(T * T) k_stage(StageArgs<real> a, Geom g) {
         if ((tid & 31) == 0) atomic_max_nonneg(&a.sc[info.inst].maxspeed_bits, m);
     }
     if (__syncthreads_or(nonphys) && tid == 0) raise_status(&a.sc[0].status, 7);
+}
+
+// CTAs take items (block, column tile) with a grid stride: one CTA per item
+// when the grid covers them all, a persistent sweep when it is smaller.
+template <class real, int D, int N, int NG, int T>
+__global__ void __launch_bounds__(T * T) k_stage(StageArgs<real> a, Geom g) {
+    for (int item = blockIdx.x; item < a.n_items; item += gridDim.x) stage_item<real, D, N, NG, T>(a, g, item);
 }
 
 }  // namespace amrb

@@ -135,7 +135,7 @@ struct PairShape {
 };
 
 template <int N>
-__global__ void __launch_bounds__(PairShape<N>::NT, (N >= 16 ? 4 : 1)) k_stage_pair(StageArgs<float> a, Geom g) {
+__device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const Geom &g, int item) {
     using Sh = PairShape<N>;
     constexpr int T = Sh::T, NG = Sh::NG, S = Sh::S, P = Sh::P, PL = Sh::PL, V = Sh::V, NT = Sh::NT;
     constexpr int FXP = Sh::FXP, NFX = Sh::NFX, FBUF = Sh::FBUF;
@@ -145,8 +145,8 @@ __global__ void __launch_bounds__(PairShape<N>::NT, (N >= 16 ? 4 : 1)) k_stage_p
     float *fbuf = ring + Sh::R * V * PL;                        // [2][FBUF]: Fx [V][T][FXP], Fy [V][T+1][T]
 
     const int tid = threadIdx.x;
-    const int b = blockIdx.x / Sh::TILES;
-    const int tile = blockIdx.x - b * Sh::TILES;
+    const int b = item / Sh::TILES;
+    const int tile = item - b * Sh::TILES;
     const int tx0 = (tile % (N / T)) * T, ty0 = (tile / (N / T)) * T;
     const int ip = tid % (T / 2), tj = tid / (T / 2);
     const int ci = 2 * ip;                                      // first cell of the pair
@@ -450,6 +450,7 @@ __global__ void __launch_bounds__(PairShape<N>::NT, (N >= 16 ? 4 : 1)) k_stage_p
         __syncthreads();
     }
     update(N - 1, fbuf + ((N - 1) & 1) * FBUF, FzA, FzB);
+    __syncthreads();   // shared memory is reused by the CTA's next item
 
     if (a.update_dt) {
         double m = double(vmax);
@@ -457,6 +458,11 @@ __global__ void __launch_bounds__(PairShape<N>::NT, (N >= 16 ? 4 : 1)) k_stage_p
         if ((tid & 31) == 0) atomic_max_nonneg(&a.sc[info.inst].maxspeed_bits, m);
     }
     if (__syncthreads_or(nonphys) && tid == 0) raise_status(&a.sc[0].status, 7);
+}
+
+template <int N>
+__global__ void __launch_bounds__(PairShape<N>::NT, (N >= 16 ? 4 : 1)) k_stage_pair(StageArgs<float> a, Geom g) {
+    for (int item = blockIdx.x; item < a.n_items; item += gridDim.x) stage_pair_item<N>(a, g, item);
 }
 
 }  // namespace amrb
