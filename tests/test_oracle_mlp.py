@@ -1,0 +1,69 @@
+"""Pins of the learned-flag oracle: back-propagation against central finite
+differences in FP64, BF16 rounding against the format's definition, and the
+feature pooling against direct per-cell averages.  CPU only."""
+import numpy as np
+
+from oracle import mlp
+import synth
+
+
+def test_backprop_matches_finite_differences():
+    rng = np.random.default_rng(0)
+    F = 13
+    p = rng.normal(0, 0.4, mlp.n_params(F))
+    X = rng.normal(0, 1, (20, F))
+    y = rng.integers(0, 3, 20)
+    L, g = mlp.gradients(p, X, y)
+    assert abs(L - mlp.loss(p, X, y)) < 1e-14
+    idx = rng.choice(len(p), 60, replace=False)
+    h = 1e-6
+    for i in idx:
+        e = np.zeros_like(p)
+        e[i] = h
+        fd = (mlp.loss(p + e, X, y) - mlp.loss(p - e, X, y)) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-7 * max(1.0, abs(fd)), (i, fd, g[i])
+
+
+def test_bf16_rounding_definition():
+    # BF16 keeps the top 16 bits of an FP32 value, rounding to nearest even
+    vals = np.array([1.0, 1.0 + 2**-8, 1.0 + 2**-7 + 2**-9, 1.0 + 3 * 2**-8, -3.14159, 1e-3], dtype=np.float32)
+    r = mlp.to_bf16(vals)
+    assert np.all((r.view(np.uint32) & 0xFFFF) == 0)
+    assert r[0] == 1.0
+    assert r[1] == 1.0                      # exactly half an ulp: ties to even (mantissa ...0)
+    assert r[2] == np.float32(1.0 + 2**-7)  # above half: rounds up
+    assert r[3] == np.float32(1.0 + 2**-6)  # half an ulp, odd mantissa: rounds up to even
+    assert np.all(np.abs(r - vals) <= np.abs(vals) * 2**-8)
+
+
+def test_gelu_closed_forms():
+    z = np.array([0.0, 1.0, -1.0])
+    g = mlp.gelu(z)
+    assert g[0] == 0.0
+    assert abs(g[1] - 0.8413447460685429) < 1e-15       # Phi(1)
+    assert abs(g[1] - g[2] - 1.0) < 1e-15                 # gelu(z) - gelu(-z) = z
+    h = 1e-6
+    fd = (mlp.gelu(z + h) - mlp.gelu(z - h)) / (2 * h)
+    assert np.allclose(fd, mlp.gelu_prime(z), atol=1e-9)
+
+
+def test_features_of_uniform_and_pooled_states():
+    sp = synth.MeshSpec(ndim=3, N=16, ng=2, ntrees=(1, 1, 1))
+    lev, g = np.zeros(1, dtype=np.int32), np.zeros((1, 3), dtype=np.int64)
+    rho = np.full((1, 20, 20, 20), 2.0)
+    u = synth.primitive_to_state(sp, rho, [0.3 * rho / rho, 0 * rho, 0 * rho], 5.0 * rho / rho)
+    f = mlp.block_features(sp, u, lev, 3)
+    assert f.shape == (1, 193)
+    assert np.allclose(f[0, :128], 0.0, atol=1e-15)           # pooled / mean - 1
+    c = np.sqrt(1.4 * 5.0 / 2.0)
+    assert np.allclose(f[0, 128:192], 0.3 / c)
+    # a density that varies only along x: pooled values are 4-cell averages
+    X = synth.cell_centres(sp, lev, g)
+    rho = 1.0 + 0.5 * X[0]
+    u = synth.primitive_to_state(sp, rho, [0 * rho] * 3, np.ones_like(rho))
+    f = mlp.block_features(sp, u, lev, 3)
+    x = (np.arange(16) + 0.5) / 16
+    r = 1.0 + 0.5 * x
+    exp_pool = r.reshape(4, 4).mean(axis=1) / r.mean() - 1.0
+    got = f[0, :64].reshape(4, 4, 4)        # (z, y, x) pools
+    assert np.allclose(got, exp_pool[None, None, :], atol=1e-14)
