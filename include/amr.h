@@ -282,6 +282,54 @@ amr_status amr_flag_and_regrid(amr_forest *f, const amr_flag_params *prm, const 
  * = mean time of one stage launch of the choice. */
 amr_status amr_autotune(amr_forest *f, int *choice, double *best_ms, amr_stream stream);
 
+/* ---- learned refinement flags ------------------------------------------
+ * A small network predicts the flags of the criterion of Eq. 5 (Sec. 3.3)
+ * from pooled block data; the criterion stays as fallback for blocks the
+ * network is unsure about and as the judge of its flags.  Network: F inputs
+ * -> 64 -> 64 (GELU) -> 3 logits (derefine / keep / refine) -> softmax; the
+ * forward pass uses BF16 copies of the FP32 master weights with FP32
+ * accumulation.  Parameters are packed FP32 [W1 (F x 64), b1, W2 (64 x 64),
+ * b2, W3 (64 x 3), b3]; labels are classes 0, 1, 2 = flags -1, 0, +1. */
+typedef struct amr_mlp amr_mlp;
+
+/* Features of every block of slot s into device memory x[f * n_blocks + b]
+ * (feature-major): for each of 4^d pools of (N/4)^d cells the mean density
+ * and pressure over the block means, minus one, and the mean speed over the
+ * block-mean sound speed, then level / max_level; F = 3 * 4^d + 1 (193 in
+ * 3D).  x may be NULL to only query *n_features.  Needs block_n % 4 == 0. */
+amr_status amr_features(amr_forest *f, int s, float *x, int *n_features, amr_stream stream);
+
+/* Model on the current device with n_features inputs, weights drawn
+ * uniformly in +-1/sqrt(fan_in) from `seed`, zero biases. */
+amr_status amr_mlp_create(int n_features, uint64_t seed, amr_mlp **out);
+amr_status amr_mlp_destroy(amr_mlp *m);
+amr_status amr_mlp_n_params(const amr_mlp *m, int64_t *n);
+
+/* FP32 master parameters to / from the host (n = amr_mlp_n_params);
+ * setting them also refreshes the BF16 copy and resets the optimiser. */
+amr_status amr_mlp_get_params(const amr_mlp *m, float *host, int64_t n);
+amr_status amr_mlp_set_params(amr_mlp *m, const float *host, int64_t n);
+
+/* Softmax probabilities prob[s * 3 + c] of n samples x[f * n + s] (device). */
+amr_status amr_mlp_forward(amr_mlp *m, const float *x, int64_t n, float *prob, amr_stream stream);
+
+/* Gradient of the mean cross-entropy over all n samples (labels y, device)
+ * into grad[0 .. P) (device), and the loss into grad[P]. */
+amr_status amr_mlp_gradient(amr_mlp *m, const float *x, const int8_t *y, int64_t n, float *grad, amr_stream stream);
+
+/* AdamW (beta 0.9 / 0.999, eps 1e-8, decoupled weight decay) on shuffled
+ * mini-batches for `epochs` passes; *final_loss = mean loss of the last
+ * epoch's batches. */
+amr_status amr_mlp_train(amr_mlp *m, const float *x, const int8_t *y, int64_t n, int epochs, int batch, double lr,
+                         double weight_decay, uint64_t seed, double *final_loss, amr_stream stream);
+
+/* Refinement flags of slot s from the model: the most probable class when
+ * its probability is at least tau, else the criterion of Eq. 5 with `prm`
+ * (ghost cells of slot s are filled for those blocks).  flags_out: host,
+ * one per block; *n_fallback = blocks that used the criterion. */
+amr_status amr_mlp_flags(amr_forest *f, amr_mlp *m, int s, const amr_flag_params *prm, double tau, int8_t *flags_out,
+                         int64_t *n_fallback, amr_stream stream);
+
 /* Reads and clears the device status word (synchronises `stream`): AMR_OK or
  * the first device-side error (AMR_ENONPHYS, AMR_ETIMEOUT, AMR_EBOUNDS). */
 amr_status amr_sync_status(amr_forest *f, amr_stream stream);

@@ -29,7 +29,9 @@ EXPORTED = [
     "amr_fill_ghosts", "amr_compute_dt", "amr_set_dt", "amr_get_dt", "amr_advance_stage", "amr_step",
     "amr_conserved", "amr_flag", "amr_flag_and_regrid", "amr_sync_status", "amr_last_error",
     "amr_launch_count", "amr_conserved_static", "amr_create_batch", "amr_n_instances", "amr_instance_blocks",
-    "amr_get_dts", "amr_conserved_all", "amr_autotune",
+    "amr_get_dts", "amr_conserved_all", "amr_autotune", "amr_features", "amr_mlp_create", "amr_mlp_destroy",
+    "amr_mlp_n_params", "amr_mlp_get_params", "amr_mlp_set_params", "amr_mlp_forward", "amr_mlp_gradient",
+    "amr_mlp_train", "amr_mlp_flags",
 ]
 
 
@@ -115,6 +117,16 @@ def load(build_if_missing: bool = True):
         "amr_get_dts": [vp, vp, vp],
         "amr_conserved_all": [vp, C.c_int, vp, vp],
         "amr_autotune": [vp, P(C.c_int), P(C.c_double), vp],
+        "amr_features": [vp, C.c_int, vp, P(C.c_int), vp],
+        "amr_mlp_create": [C.c_int, C.c_uint64, P(vp)],
+        "amr_mlp_destroy": [vp],
+        "amr_mlp_n_params": [vp, P(i64)],
+        "amr_mlp_get_params": [vp, vp, i64],
+        "amr_mlp_set_params": [vp, vp, i64],
+        "amr_mlp_forward": [vp, vp, i64, vp, vp],
+        "amr_mlp_gradient": [vp, vp, vp, i64, vp, vp],
+        "amr_mlp_train": [vp, vp, vp, i64, C.c_int, C.c_int, C.c_double, C.c_double, C.c_uint64, P(C.c_double), vp],
+        "amr_mlp_flags": [vp, vp, C.c_int, P(FlagParams), C.c_double, vp, P(i64), vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -351,6 +363,25 @@ class Forest:
         self._check(self.lib.amr_autotune(self.h, C.byref(ch), C.byref(ms), _stream_ptr(stream)), "amr_autotune")
         return int(ch.value), float(ms.value)
 
+    def features(self, s, out=None, stream=None):
+        """Block features of slot s as a CUDA tensor [F, n_blocks] (torch)."""
+        import torch
+        F = C.c_int()
+        self._check(self.lib.amr_features(self.h, s, None, C.byref(F), _stream_ptr(stream)), "amr_features")
+        if out is None:
+            out = torch.empty((F.value, self.n), dtype=torch.float32, device="cuda")
+        self._check(self.lib.amr_features(self.h, s, out.data_ptr(), C.byref(F), _stream_ptr(stream)), "amr_features")
+        return out
+
+    def mlp_flags(self, model, s, tau=0.9, c_ref=5e-2, c_deref=6.25e-3, eps=1e-2, eps_abs=1e-10, stream=None):
+        """(flags, number of blocks that fell back to the criterion)."""
+        p = FlagParams(c_ref, c_deref, eps, eps_abs)
+        out = np.zeros(max(self.n, 1), dtype=np.int8)
+        nf = C.c_int64()
+        self._check(self.lib.amr_mlp_flags(self.h, model.h, s, C.byref(p), float(tau), out.ctypes.data, C.byref(nf),
+                                           _stream_ptr(stream)), "amr_mlp_flags")
+        return out[:self.n], int(nf.value)
+
     def sync_status(self, stream=None) -> int:
         return int(self.lib.amr_sync_status(self.h, _stream_ptr(stream)))
 
@@ -358,3 +389,67 @@ class Forest:
         n = C.c_int64()
         self._check(self.lib.amr_launch_count(self.h, C.byref(n)), "amr_launch_count")
         return int(n.value)
+
+
+class Mlp:
+    """Learned refinement-flag predictor (amr_mlp_*): F -> 64 -> 64 -> 3."""
+
+    def __init__(self, n_features, seed=0):
+        self.lib = load()
+        h = C.c_void_p()
+        st = self.lib.amr_mlp_create(int(n_features), C.c_uint64(seed), C.byref(h))
+        if st != AMR_OK:
+            raise AmrError(st, "amr_mlp_create")
+        self.h = h
+        self.F = n_features
+        n = C.c_int64()
+        self.lib.amr_mlp_n_params(self.h, C.byref(n))
+        self.P = int(n.value)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.amr_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, what):
+        if st != AMR_OK:
+            raise AmrError(st, what)
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(self.P, dtype=np.float32)
+        self._check(self.lib.amr_mlp_get_params(self.h, out.ctypes.data, self.P), "amr_mlp_get_params")
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        self._check(self.lib.amr_mlp_set_params(self.h, p.ctypes.data, self.P), "amr_mlp_set_params")
+
+    def forward(self, x, stream=None):
+        """x: CUDA float32 tensor [F, n] -> probabilities [n, 3] (CUDA tensor)."""
+        import torch
+        n = x.shape[1]
+        prob = torch.empty((n, 3), dtype=torch.float32, device=x.device)
+        self._check(self.lib.amr_mlp_forward(self.h, x.data_ptr(), n, prob.data_ptr(), _stream_ptr(stream)), "amr_mlp_forward")
+        return prob
+
+    def gradient(self, x, y, stream=None):
+        """(loss, gradient) of the mean cross-entropy; x [F, n], y [n] int8 classes (CUDA tensors)."""
+        import torch
+        g = torch.empty(self.P + 1, dtype=torch.float32, device=x.device)
+        self._check(self.lib.amr_mlp_gradient(self.h, x.data_ptr(), y.data_ptr(), x.shape[1], g.data_ptr(),
+                                              _stream_ptr(stream)), "amr_mlp_gradient")
+        g = g.cpu().numpy()
+        return float(g[-1]), g[:-1]
+
+    def train(self, x, y, epochs=20, batch=256, lr=3e-3, weight_decay=1e-4, seed=0, stream=None) -> float:
+        loss = C.c_double()
+        self._check(self.lib.amr_mlp_train(self.h, x.data_ptr(), y.data_ptr(), x.shape[1], int(epochs), int(batch), float(lr),
+                                           float(weight_decay), C.c_uint64(seed), C.byref(loss), _stream_ptr(stream)),
+                    "amr_mlp_train")
+        return float(loss.value)

@@ -15,8 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libamr_b300.so")
-UNITS = ["amr_api.cu", "forest.cpp", "pattern.cpp", "noalloc.cu"]
-HEADERS = ["common.cuh", "ghost.cuh", "stage.cuh", "stage_pair.cuh", "misc.cuh", "forest.hpp", "pattern.hpp"]
+UNITS = ["amr_api.cu", "forest.cpp", "pattern.cpp", "noalloc.cu", "mlp.cu"]
+HEADERS = ["common.cuh", "ghost.cuh", "stage.cuh", "stage_pair.cuh", "misc.cuh", "mlp.cuh", "forest.hpp", "pattern.hpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 

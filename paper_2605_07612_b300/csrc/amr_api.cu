@@ -21,6 +21,7 @@
 #include "pattern.hpp"
 #include "stage.cuh"
 #include "stage_pair.cuh"
+#include "mlp.cuh"
 
 using namespace amrb;
 
@@ -47,6 +48,7 @@ struct amr_forest {
     void *state = nullptr;
     DBuf r1, r2, r1g, info, fix, fix_start, bflux, bcdata, sc, partial, sums, flags, ops, level;
     DBuf dxtab, invdxtab, bctype, bcval, cfltab, ranges;   // per-instance tables
+    DBuf feat, prob, mflags, flist;                        // learned-flag predictor
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t gexec = nullptr;
     uint64_t graph_rev = ~0ull;
@@ -456,7 +458,34 @@ struct FlagFn {
         if (nblocks(f) > 0) {
             k_flags<real, D><<<unsigned(nblocks(f)), 256, 0, st>>>(static_cast<const real *>(slot_ptr(f, s)), f->geom, f->cfg.gamma,
                                                                   p->c_refine, p->c_derefine, p->eps, p->eps_abs,
-                                                                  static_cast<int8_t *>(f->flags.p));
+                                                                  static_cast<int8_t *>(f->flags.p), nullptr);
+            ++f->launches;
+        }
+        CU(cudaGetLastError());
+        return AMR_OK;
+    }
+};
+template <class real, int D>
+struct FeatureFn {
+    static amr_status run(amr_forest *f, int s, float *x, cudaStream_t st) {
+        int ml = 1;
+        for (const amr_config &c : f->icfg) ml = std::max(ml, c.max_level);
+        if (nblocks(f) > 0) {
+            k_features<real, D><<<unsigned(nblocks(f)), 64, 0, st>>>(static_cast<const real *>(slot_ptr(f, s)),
+                                                                    static_cast<const BlockInfo *>(f->info.p), f->geom,
+                                                                    f->cfg.gamma, 1.0f / float(ml), x, nblocks(f));
+            ++f->launches;
+        }
+        CU(cudaGetLastError());
+        return AMR_OK;
+    }
+};
+template <class real, int D>
+struct ListFlagFn {
+    static amr_status run(amr_forest *f, int s, const amr_flag_params *p, const int32_t *list, int n, int8_t *out, cudaStream_t st) {
+        if (n > 0) {
+            k_flags<real, D><<<unsigned(n), 256, 0, st>>>(static_cast<const real *>(slot_ptr(f, s)), f->geom, f->cfg.gamma,
+                                                         p->c_refine, p->c_derefine, p->eps, p->eps_abs, out, list);
             ++f->launches;
         }
         CU(cudaGetLastError());
@@ -598,7 +627,8 @@ amr_status amr_destroy_forest(amr_forest *f) {
     if (f->gexec) cudaGraphExecDestroy(f->gexec);
     if (f->cap_stream) cudaStreamDestroy(f->cap_stream);
     for (DBuf *b : {&f->r1, &f->r2, &f->r1g, &f->info, &f->fix, &f->fix_start, &f->bflux, &f->bcdata, &f->sc, &f->partial, &f->sums,
-                    &f->flags, &f->ops, &f->level, &f->dxtab, &f->invdxtab, &f->bctype, &f->bcval, &f->cfltab, &f->ranges})
+                    &f->flags, &f->ops, &f->level, &f->dxtab, &f->invdxtab, &f->bctype, &f->bcval, &f->cfltab, &f->ranges,
+                    &f->feat, &f->prob, &f->mflags, &f->flist})
         dev_free(f, b->p);
     dev_free(f, f->state);
     delete f;
@@ -938,6 +968,57 @@ amr_status amr_sync_status(amr_forest *f, amr_stream stream) {
         CU(cudaMemcpy(static_cast<char *>(f->sc.p) + offsetof(DevScalars, status), &zero, sizeof zero, cudaMemcpyHostToDevice));
         return fail(f, amr_status(h.status), "device reported status %d", h.status);
     }
+    return AMR_OK;
+}
+
+amr_status amr_features(amr_forest *f, int s, float *x, int *n_features, amr_stream stream) {
+    if (!f || !valid_slot(f, s)) return AMR_EINVAL;
+    NEED_DEVICE(f);
+    if (f->cfg.block_n % 4) return fail(f, AMR_EINVAL, "features pool 4 cells per dimension: block_n must be a multiple of 4");
+    const int F = 3 * (f->cfg.ndim == 3 ? 64 : 16) + 1;
+    if (n_features) *n_features = F;
+    if (!x) return AMR_OK;
+    amr_status r = upload_pattern(f);
+    if (r != AMR_OK) return r;
+    return dispatch<FeatureFn>(f, s, x, static_cast<cudaStream_t>(stream));
+}
+
+amr_status amr_mlp_flags(amr_forest *f, amr_mlp *m, int s, const amr_flag_params *p, double tau, int8_t *flags_out,
+                         int64_t *n_fallback, amr_stream stream) {
+    if (!f || !m || !p || !flags_out || !valid_slot(f, s)) return AMR_EINVAL;
+    NEED_DEVICE(f);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int F = 0;
+    amr_status r = amr_features(f, s, nullptr, &F, stream);
+    if (r != AMR_OK) return r;
+    if (F != m->F) return fail(f, AMR_EINVAL, "the model takes %d features, this forest gives %d", m->F, F);
+    const int64_t nb = nblocks(f);
+    if (nb == 0) return AMR_OK;
+    if ((r = ensure(f, f->feat, sizeof(float) * size_t(F) * size_t(nb))) != AMR_OK) return r;
+    if ((r = ensure(f, f->prob, sizeof(float) * 3 * size_t(nb))) != AMR_OK) return r;
+    if ((r = ensure(f, f->mflags, size_t(nb))) != AMR_OK) return r;
+    if ((r = amr_features(f, s, static_cast<float *>(f->feat.p), nullptr, stream)) != AMR_OK) return r;
+    if ((r = amr_mlp_forward(m, static_cast<const float *>(f->feat.p), nb, static_cast<float *>(f->prob.p), stream)) != AMR_OK)
+        return fail(f, r, "model forward pass failed");
+    k_mlp_decide<<<unsigned((nb + 255) / 256), 256, 0, st>>>(static_cast<const float *>(f->prob.p), nb, float(tau),
+                                                             static_cast<int8_t *>(f->mflags.p));
+    f->launches += 2;
+    CU(cudaGetLastError());
+    CU(cudaMemcpyAsync(flags_out, f->mflags.p, size_t(nb), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    // low-confidence blocks fall back to the criterion of Eq. 5
+    std::vector<int32_t> list;
+    for (int64_t b = 0; b < nb; ++b)
+        if (flags_out[b] == 2) list.push_back(int32_t(b));
+    if (n_fallback) *n_fallback = int64_t(list.size());
+    if (list.empty()) return AMR_OK;
+    if ((r = amr_fill_ghosts(f, s, stream)) != AMR_OK) return r;
+    if ((r = upload(f, f->flist, list)) != AMR_OK) return r;
+    if ((r = dispatch<ListFlagFn>(f, s, p, static_cast<const int32_t *>(f->flist.p), int(list.size()),
+                                  static_cast<int8_t *>(f->mflags.p), st)) != AMR_OK)
+        return r;
+    CU(cudaMemcpyAsync(flags_out, f->mflags.p, size_t(nb), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
     return AMR_OK;
 }
 

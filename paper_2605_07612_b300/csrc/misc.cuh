@@ -227,8 +227,8 @@ __device__ __forceinline__ double lohner_1d(double um, double u0, double up, dou
 
 template <class real, int D>
 __global__ void __launch_bounds__(256) k_flags(const real *u, Geom g, double gam, double c_ref, double c_deref, double eps,
-                                               double eps_abs, int8_t *flags) {
-    const int b = blockIdx.x;
+                                               double eps_abs, int8_t *flags, const int32_t *list) {
+    const int b = list ? list[blockIdx.x] : int(blockIdx.x);
     const int N = g.N;
     const int ncell = (D == 3) ? N * N * N : N * N;
     const real *ub = u + int64_t(b) * g.bstride;

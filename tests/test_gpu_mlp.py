@@ -1,0 +1,122 @@
+"""GPU checks of the learned refinement-flag predictor against its FP64
+oracle (features, forward probabilities, gradients), training, the criterion
+fallback, and what the trained network gains over evaluating the criterion
+of Eq. 5 on every block."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp as omlp
+import synth
+
+pytestmark = pytest.mark.gpu
+
+amr = pytest.importorskip("paper_2605_07612_b300")
+torch = pytest.importorskip("torch")
+
+SPEC = dict(ndim=3, N=8, ng=2, ntrees=(4, 4, 4), max_level=2)
+
+
+def sphere_forest(precision=32, steps=0):
+    sp = synth.MeshSpec(**SPEC)
+    f = amr.Forest(sp, 0, max_blocks=4096, precision=precision)
+    for _ in range(2):
+        lev, g = f.blocks()
+        f.regrid(synth.ball_flags(sp, lev, g, (0.5, 0.5, 0.5), (0.3, 0.15)))
+    lev, g = f.blocks()
+    f.set_state(0, synth.over_pressure(sp, lev, g, (0.5, 0.5, 0.5), radius=0.2, p_in=10.0).astype(f.dtype))
+    f.compute_dt(0)
+    if steps:
+        f.step(steps)
+    return sp, f
+
+
+def test_features_match_oracle():
+    sp, f = sphere_forest(precision=64, steps=3)
+    lev, _ = f.blocks()
+    x = f.features(0).cpu().numpy()
+    assert x.shape == (193, f.n)
+    ref = omlp.block_features(sp, f.get_state(0), lev, sp.max_level).T
+    np.testing.assert_allclose(x, ref, rtol=2e-6, atol=2e-6)
+
+
+def test_forward_and_gradient_match_oracle():
+    rng = np.random.default_rng(1)
+    F, n = 193, 300
+    m = amr.Mlp(F, seed=7)
+    p = m.get_params()
+    X = rng.normal(0, 1, (n, F)).astype(np.float32)
+    y = rng.integers(0, 3, n).astype(np.int8)
+    xd = torch.tensor(X.T.copy(), device="cuda")
+    yd = torch.tensor(y, device="cuda")
+    prob = m.forward(xd).cpu().numpy()
+    pb = omlp.to_bf16(p).astype(np.float64)
+    ref, _ = omlp.forward(pb, X.astype(np.float64))
+    np.testing.assert_allclose(prob, ref, atol=2e-5)
+    L, g = m.gradient(xd, yd)
+    Lr, gr = omlp.gradients(pb, X.astype(np.float64), y.astype(np.int64))
+    assert abs(L - Lr) <= 1e-5 * abs(Lr)
+    assert np.linalg.norm(g - gr) <= 1e-4 * np.linalg.norm(gr)
+
+
+def test_training_learns_a_separable_rule():
+    rng = np.random.default_rng(2)
+    F, n = 49, 4000
+    X = rng.normal(0, 1, (n, F)).astype(np.float32)
+    score = X[:, 0] + 0.5 * X[:, 1]
+    y = np.where(score > 0.7, 2, np.where(score < -0.7, 0, 1)).astype(np.int8)
+    m = amr.Mlp(F, seed=3)
+    xd = torch.tensor(X.T.copy(), device="cuda")
+    yd = torch.tensor(y, device="cuda")
+    L0, _ = m.gradient(xd, yd)
+    L = m.train(xd, yd, epochs=30, batch=256, lr=3e-3)
+    acc = (m.forward(xd).argmax(dim=1).cpu().numpy() == y).mean()
+    assert L < 0.3 * L0 and acc > 0.95, (L0, L, acc)
+
+
+def test_fallback_reproduces_the_criterion():
+    sp, f = sphere_forest(steps=4)
+    m = amr.Mlp(193, seed=0)
+    f.fill_ghosts(0)
+    plain = f.flag(0)
+    flags, nfb = f.mlp_flags(m, 0, tau=1.5)     # nothing is that confident
+    assert nfb == f.n
+    np.testing.assert_array_equal(flags, plain)
+    flags, nfb = f.mlp_flags(m, 0, tau=0.0)     # pure network
+    assert nfb == 0 and set(np.unique(flags)) <= {-1, 0, 1}
+
+
+def test_trained_network_replaces_most_criterion_evaluations():
+    """Train on (features, criterion flags) gathered every 3 steps of an
+    over-pressure run with regrids; on later, unseen states the network alone
+    agrees with the criterion on most blocks, and with the fallback for
+    unsure blocks it evaluates the criterion on a minority of them."""
+    sp, f = sphere_forest()
+    xs, ys, held = [], [], []
+    for it in range(12):
+        f.step(3)
+        f.fill_ghosts(0)
+        plain = f.flag(0, c_ref=5e-2, c_deref=6.25e-3)
+        x = f.features(0)
+        if it < 8:
+            xs.append(x)
+            ys.append(torch.tensor(plain + 1, dtype=torch.int8, device="cuda"))
+        else:
+            held.append((x, plain))
+        f.regrid(plain)
+    X = torch.cat(xs, dim=1).contiguous()
+    Y = torch.cat(ys).contiguous()
+    m = amr.Mlp(193, seed=4)
+    m.train(X, Y, epochs=60, batch=128, lr=3e-3)
+    mis = []
+    for x, plain in held:
+        pred = m.forward(x.contiguous()).argmax(dim=1).cpu().numpy() - 1
+        mis.append((pred != plain).mean())
+    majority = np.bincount(Y.cpu().numpy()).argmax() - 1
+    base = np.mean([(plain != majority).mean() for _, plain in held])
+    assert np.mean(mis) < 0.15 and np.mean(mis) < 0.5 * base, (np.mean(mis), base)
+    f.fill_ghosts(0)
+    plain = f.flag(0)
+    flags, nfb = f.mlp_flags(m, 0, tau=0.9)
+    assert nfb < 0.5 * f.n
+    assert (flags != plain).mean() <= max(np.mean(mis), 0.05)
