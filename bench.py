@@ -359,6 +359,171 @@ def run_batched(args, amr, torch, stream, barrier, world):
                         "one launch per phase over all meshes, step replayed as a CUDA graph"}
 
 
+# --------------------------------------------- static and adaptive AMR --
+
+def amr_static_spec():
+    """3D 128^3 base domain of 16^3 blocks (8^3 trees), 3 levels."""
+    return synth.MeshSpec(ndim=3, N=16, ng=2, ntrees=(8, 8, 8), max_level=2)
+
+
+def refine_ball(f, sp, centre, radius, levels):
+    for _ in range(levels):
+        lev, g = f.blocks()
+        f.regrid(synth.ball_flags(sp, lev, g, centre, [radius] * levels))
+
+
+def amr_static_radius(amr, target=20000):
+    """Ball radius (same at levels 0 and 1) whose balanced 3-level mesh has
+    about `target` blocks, by bisection on host-only forests."""
+    sp = amr_static_spec()
+    rng = np.random.Generator(np.random.PCG64(4))
+    centre = tuple(rng.uniform(0.35, 0.65, 3))
+    lo, hi = 0.05, 0.9
+    for _ in range(24):
+        r = 0.5 * (lo + hi)
+        f = amr.Forest(sp, 0, max_blocks=1 << 20, host_only=True)
+        refine_ball(f, sp, centre, r, 2)
+        if f.n < target:
+            lo = r
+        else:
+            hi = r
+    return centre, 0.5 * (lo + hi)
+
+
+def abs_integrals(sp, u, lev):
+    """Integral of |u_v| over the domain per variable (the scale conservation
+    drift is measured against; momentum integrals themselves may be ~0)."""
+    sl = tuple(slice(sp.ng, sp.ng + sp.N) for _ in range(sp.ndim))
+    a = np.abs(u.reshape((u.shape[0], sp.nvar) + (sp.side,) * sp.ndim)[(slice(None), slice(None)) + sl].astype(np.float64))
+    per_block = a.reshape(u.shape[0], sp.nvar, -1).sum(axis=2)
+    vol = np.prod([sp.length[d] / (sp.ntrees[d] * sp.N) for d in range(sp.ndim)]) * (0.5 ** sp.ndim) ** np.asarray(lev)
+    return (per_block * vol[:, None]).sum(axis=0)
+
+
+def run_amr_static(args, amr, torch, stream):
+    """3-level static AMR (about 2e4 blocks of 16^3), over-pressure sphere
+    (radius 0.1, p_in / p_out = 100) at a seeded centre, FP32 with FP64 dt and
+    conserved sums, 50 steps."""
+    sp = amr_static_spec()
+    centre, r = amr_static_radius(amr)
+    f = amr.Forest(sp, 0, max_blocks=40000, precision=32)
+    refine_ball(f, sp, centre, r, 2)
+    lev, g = f.blocks()
+    u = synth.over_pressure(sp, lev, g, centre, radius=0.1, p_in=100.0).astype(np.float32)
+    f.set_state(0, u, stream=stream)
+    s0 = f.conserved(0, stream=stream)
+    f.compute_dt(0, stream=stream)
+    choice, _ = f.autotune(stream=stream)
+    f.step(args.warmup, use_graph=True, gather=True, stream=stream)
+    f.set_state(0, u, stream=stream)
+    f.compute_dt(0, stream=stream)
+    stream.synchronize()
+    steps = 50
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    f.step(steps, use_graph=True, gather=True, stream=stream)
+    e1.record(stream)
+    stream.synchronize()
+    ms = e0.elapsed_time(e1)
+    drift = (np.abs(f.conserved(0, stream=stream) - s0) / abs_integrals(sp, u, lev)).tolist()
+    cells = f.n * sp.N ** 3
+    pat = f.pattern()
+    return {"value": 2.0 * cells * steps / (ms * 1e-3), "unit": UNIT, "blocks": f.n,
+            "blocks_per_level": np.bincount(lev).tolist(), "ball_radius": r, "centre": list(centre),
+            "ghost_entries": {k: int((pat[:, 0] == i).sum()) for i, k in enumerate(["srl", "f2c", "bc", "c2f"])},
+            "ms_per_step": ms / steps, "steps": steps, "autotune_choice": choice,
+            "conservation_rel_drift": drift, "status": f.sync_status(),
+            "workload": "3D 128^3 base of 16^3 blocks, 3 levels (2:1 balanced ball refinement), over-pressure sphere, FP32"}
+
+
+def run_adaptive(args, amr, torch, stream, steps=500, every=10, train_until=200):
+    """3D adaptive run: over-pressure sphere and a Mach-3 planar shock in a
+    128^3 base domain of 16^3 blocks, up to 4 levels, regrid every 10 steps.
+    Run A uses the Lohner criterion throughout; run B uses it for the first
+    200 steps while collecting (features, flags), trains the network, then
+    regrids with the network's flags (criterion fallback below tau = 0.9).
+    Reported: flag mismatch between B's network flags and the criterion on B's
+    states, criterion evaluations skipped, flagging times, and the L1
+    difference of the final densities averaged over the base blocks."""
+    sp = synth.MeshSpec(ndim=3, N=16, ng=2, ntrees=(8, 8, 8), periodic=(0, 0, 0), max_level=3,
+                        bc_type=(1, 2, 2, 2, 2, 2))
+    rho2, u2, p2 = synth.normal_shock_state(3.0, sp.gamma)
+    E2 = p2 / (sp.gamma - 1.0) + 0.5 * rho2 * u2 * u2
+    sp.bc_val = tuple(tuple([rho2, rho2 * u2, 0.0, 0.0, E2, 0, 0, 0]) if fc == 0 else tuple([0.0] * 8) for fc in range(6))
+    rng = np.random.Generator(np.random.PCG64(6))
+    centre = tuple(rng.uniform(0.4, 0.7, 3))
+    prm = dict(c_ref=5e-2, c_deref=6.25e-3)
+
+    def make():
+        f = amr.Forest(sp, 0, max_blocks=120000, precision=32)
+        for _ in range(3):
+            lev, g = f.blocks()
+            f.set_state(0, synth.sphere_and_shock(sp, lev, g, centre).astype(np.float32))
+            if not f.regrid(None, **prm):
+                break
+        lev, g = f.blocks()
+        f.set_state(0, synth.sphere_and_shock(sp, lev, g, centre).astype(np.float32))
+        f.compute_dt(0, stream=stream)
+        return f
+
+    def base_average(f):
+        lev, g = f.blocks()
+        u = f.get_state(0, stream=stream)
+        sl = slice(sp.ng, sp.ng + sp.N)
+        rho = u[:, 0].reshape(-1, sp.side, sp.side, sp.side)[:, sl, sl, sl].mean(axis=(1, 2, 3))
+        out = np.zeros((8, 8, 8))
+        w = np.zeros((8, 8, 8))
+        for b in range(len(lev)):
+            gx, gy, gz = (g[b] >> lev[b])
+            vol = 0.125 ** lev[b]
+            out[gz, gy, gx] += rho[b] * vol
+            w[gz, gy, gx] += vol
+        return out / w
+
+    fa, fb = make(), make()
+    xs, ys = [], []
+    mism, skipped, t_plain, t_net = [], [], [], []
+    model = None
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    for s0 in range(0, steps, every):
+        fa.step(every, use_graph=True, gather=True, stream=stream)
+        fb.step(every, use_graph=True, gather=True, stream=stream)
+        fa.regrid(None, **prm, stream=stream)
+        fb.fill_ghosts(0, stream=stream)
+        ev[0].record(stream)
+        plain = fb.flag(0, **prm, stream=stream)
+        ev[1].record(stream)
+        stream.synchronize()
+        t_plain.append(ev[0].elapsed_time(ev[1]))
+        if s0 + every <= train_until:
+            xs.append(fb.features(0, stream=stream))
+            ys.append(torch.tensor(plain + 1, dtype=torch.int8, device="cuda"))
+            fb.regrid(plain, stream=stream)
+            if s0 + every == train_until:
+                model = amr.Mlp(193, seed=6)
+                model.train(torch.cat(xs, dim=1).contiguous(), torch.cat(ys).contiguous(), epochs=40, batch=256, lr=3e-3)
+            continue
+        ev[2].record(stream)
+        flags, nfb = fb.mlp_flags(model, 0, tau=0.9, **prm, stream=stream)
+        ev[3].record(stream)
+        stream.synchronize()
+        t_net.append(ev[2].elapsed_time(ev[3]))
+        mism.append(float((flags != plain).mean()))
+        skipped.append(1.0 - nfb / fb.n)
+        fb.regrid(flags, stream=stream)
+    ra, rb = base_average(fa), base_average(fb)
+    return {"steps": steps, "regrid_every": every, "blocks_plain_run": fa.n, "blocks_learned_run": fb.n,
+            "levels_plain_run": int(fa.blocks()[0].max()) + 1,
+            "flag_mismatch_vs_criterion": float(np.mean(mism)) if mism else None,
+            "criterion_evaluations_skipped": float(np.mean(skipped)) if skipped else None,
+            "criterion_ms_mean": float(np.mean(t_plain)), "network_flags_ms_mean": float(np.mean(t_net)) if t_net else None,
+            "final_density_rel_l1_vs_plain_run": float(np.abs(ra - rb).sum() / np.abs(ra).sum()),
+            "status": [fa.sync_status(), fb.sync_status()],
+            "workload": "3D over-pressure sphere + Mach-3 shock, 128^3 base of 16^3 blocks, <= 4 levels, FP32; "
+                        "network trained on the first 200 steps' criterion flags"}
+
+
 # ------------------------------------------------------- CPU oracle arm --
 
 def oracle_sample(seconds_hint=15.0):
@@ -413,12 +578,27 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="uniform", choices=["uniform", "amr_static", "adaptive"],
+                    help="uniform: the headline line; the others print their own JSON line")
+    ap.add_argument("--adaptive-steps", type=int, default=500)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
         if rank == 0:
             print(json.dumps(run_reference(args)), flush=True)
+        return
+    if args.workload != "uniform":
+        import torch
+        import paper_2605_07612_b300 as amr
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        stream = torch.cuda.Stream()
+        if args.workload == "amr_static":
+            out = run_amr_static(args, amr, torch, stream)
+        else:
+            out = run_adaptive(args, amr, torch, stream, steps=args.adaptive_steps)
+        out["workload_name"] = args.workload
+        print(json.dumps(out), flush=True)
         return
     dist = None
     if world > 1:

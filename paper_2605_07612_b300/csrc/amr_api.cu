@@ -451,17 +451,25 @@ struct ConservedFn {
     }
 };
 template <class real, int D>
+amr_status launch_flags(amr_forest *f, int s, const amr_flag_params *p, const int32_t *list, int n, int8_t *out, cudaStream_t st) {
+    const int N = f->cfg.block_n;
+    const size_t smem = flags_smem(N, D);
+    if (smem > 48 * 1024) CU(cudaFuncSetAttribute(k_flags<real, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    k_flags<real, D><<<unsigned(n), unsigned(flags_threads(N)), smem, st>>>(static_cast<const real *>(slot_ptr(f, s)), f->geom,
+                                                                         f->cfg.gamma, p->c_refine, p->c_derefine, p->eps,
+                                                                         p->eps_abs, out, list);
+    ++f->launches;
+    CU(cudaGetLastError());
+    return AMR_OK;
+}
+template <class real, int D>
 struct FlagFn {
     static amr_status run(amr_forest *f, int s, const amr_flag_params *p, cudaStream_t st) {
         amr_status r = ensure(f, f->flags, std::max<int64_t>(nblocks(f), 1));
         if (r != AMR_OK) return r;
         if (nblocks(f) > 0) {
-            k_flags<real, D><<<unsigned(nblocks(f)), 256, 0, st>>>(static_cast<const real *>(slot_ptr(f, s)), f->geom, f->cfg.gamma,
-                                                                  p->c_refine, p->c_derefine, p->eps, p->eps_abs,
-                                                                  static_cast<int8_t *>(f->flags.p), nullptr);
-            ++f->launches;
+            return launch_flags<real, D>(f, s, p, nullptr, int(nblocks(f)), static_cast<int8_t *>(f->flags.p), st);
         }
-        CU(cudaGetLastError());
         return AMR_OK;
     }
 };
@@ -471,7 +479,10 @@ struct FeatureFn {
         int ml = 1;
         for (const amr_config &c : f->icfg) ml = std::max(ml, c.max_level);
         if (nblocks(f) > 0) {
-            k_features<real, D><<<unsigned(nblocks(f)), 64, 0, st>>>(static_cast<const real *>(slot_ptr(f, s)),
+            const size_t smem = features_smem<real, D>(f->cfg.block_n);
+            if (smem > 40 * 1024)
+                CU(cudaFuncSetAttribute(k_features<real, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+            k_features<real, D><<<unsigned(nblocks(f)), 256, smem, st>>>(static_cast<const real *>(slot_ptr(f, s)),
                                                                     static_cast<const BlockInfo *>(f->info.p), f->geom,
                                                                     f->cfg.gamma, 1.0f / float(ml), x, nblocks(f));
             ++f->launches;
@@ -484,11 +495,8 @@ template <class real, int D>
 struct ListFlagFn {
     static amr_status run(amr_forest *f, int s, const amr_flag_params *p, const int32_t *list, int n, int8_t *out, cudaStream_t st) {
         if (n > 0) {
-            k_flags<real, D><<<unsigned(n), 256, 0, st>>>(static_cast<const real *>(slot_ptr(f, s)), f->geom, f->cfg.gamma,
-                                                         p->c_refine, p->c_derefine, p->eps, p->eps_abs, out, list);
-            ++f->launches;
+            return launch_flags<real, D>(f, s, p, list, n, out, st);
         }
-        CU(cudaGetLastError());
         return AMR_OK;
     }
 };

@@ -225,40 +225,96 @@ __device__ __forceinline__ double lohner_1d(double um, double u0, double up, dou
     return __ddiv_rn(num, den);
 }
 
+// One CTA per block.  Density and pressure are converted to primitives once
+// per cell into a ring of four z planes in shared memory; each plane holds its
+// interior and the x/y face ghosts (corners are never read), the planes at
+// z = -1 and z = N only their interior.  A cell's score is the larger of the
+// two sums of squared 1D indicators (a NaN sum ignored, as the per-cell
+// maximum of the criterion ignores it); the block keeps the largest score.
+// Round-to-nearest sqrt is monotone, so one square root of the block maximum
+// equals the largest per-cell sqrt and decides both thresholds exactly as a
+// square root per cell would.
+__host__ __device__ constexpr int flags_threads(int N) { return N * N + 4 * N < 384 ? N * N + 4 * N : 384; }
+__host__ __device__ constexpr size_t flags_smem(int N, int D) {
+    return size_t(D == 3 ? 4 : 1) * 2 * size_t(N + 2) * size_t(N + 2) * sizeof(double);
+}
+
 template <class real, int D>
-__global__ void __launch_bounds__(256) k_flags(const real *u, Geom g, double gam, double c_ref, double c_deref, double eps,
+__global__ void __launch_bounds__(384) k_flags(const real *u, Geom g, double gam, double c_ref, double c_deref, double eps,
                                                double eps_abs, int8_t *flags, const int32_t *list) {
+    extern __shared__ double fsm[];
+    __shared__ double red[32];
     const int b = list ? list[blockIdx.x] : int(blockIdx.x);
-    const int N = g.N;
-    const int ncell = (D == 3) ? N * N * N : N * N;
+    const int N = g.N, P = N + 2, plane = P * P;
+    const int nslot = D == 3 ? 4 : 1;
+    double *R = fsm, *Q = fsm + nslot * plane;
     const real *ub = u + int64_t(b) * g.bstride;
-    int any_ref = 0, all_deref = 1;
-    for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
-        const int x[3] = {c % N, (c / N) % N, (D == 3) ? c / (N * N) : 0};
-        double r[3][3], pp[3][3];
-        for (int n = 0; n < D; ++n)
-            for (int q = -1; q <= 1; ++q) {
-                int y[3] = {x[0], x[1], x[2]};
-                y[n] += q;
-                dprim_rn<real, D>(ub, g, cell_index<real>(g, y[0], y[1], y[2]), gam, r[n][q + 1], pp[n][q + 1]);
+    // position t of a plane: t < N^2 interior (i fastest), then the four face
+    // ghost rows i = -1, i = N, j = -1, j = N
+    auto load = [&](int k, int slot) {
+        const int n = (D == 3 && (k < 0 || k >= N)) ? N * N : N * N + 4 * N;
+        for (int t = threadIdx.x; t < n; t += blockDim.x) {
+            int i, j;
+            if (t < N * N) {
+                i = t % N;
+                j = t / N;
+            } else {
+                const int side = (t - N * N) / N, q = (t - N * N) % N;
+                i = side == 0 ? -1 : (side == 1 ? N : q);
+                j = side == 2 ? -1 : (side == 3 ? N : q);
             }
-        double cellmax = 0.0;
-        for (int which = 0; which < 2; ++which) {
-            double e2 = 0.0;
-            for (int n = 0; n < D; ++n) {
-                const double *val = which == 0 ? r[n] : pp[n];
-                const double e = lohner_1d(val[0], val[1], val[2], eps, eps_abs);
-                e2 = __dadd_rn(e2, __dmul_rn(e, e));
-            }
-            const double E = __dsqrt_rn(e2);
-            cellmax = E > cellmax ? E : cellmax;
+            double r, p;
+            dprim_rn<real, D>(ub, g, cell_index<real>(g, i, j, k), gam, r, p);
+            const int c = slot * plane + (j + 1) * P + i + 1;
+            R[c] = r;
+            Q[c] = p;
         }
-        any_ref |= cellmax > c_ref;
-        all_deref &= cellmax < c_deref;
+    };
+    double m2 = 0.0;
+    auto eval = [&](int sm, int s0, int sp) {
+        for (int t = threadIdx.x; t < N * N; t += blockDim.x) {
+            const int c = (t / N + 1) * P + t % N + 1;
+            double best = 0.0;
+            for (int which = 0; which < 2; ++which) {
+                const double *A = which ? Q : R;
+                const double *A0 = A + s0 * plane;
+                const double a0 = A0[c];
+                double e = lohner_1d(A0[c - 1], a0, A0[c + 1], eps, eps_abs);
+                double e2 = __dadd_rn(0.0, __dmul_rn(e, e));
+                e = lohner_1d(A0[c - P], a0, A0[c + P], eps, eps_abs);
+                e2 = __dadd_rn(e2, __dmul_rn(e, e));
+                if (D == 3) {
+                    e = lohner_1d(A[sm * plane + c], a0, A[sp * plane + c], eps, eps_abs);
+                    e2 = __dadd_rn(e2, __dmul_rn(e, e));
+                }
+                best = fmax(best, e2);
+            }
+            m2 = fmax(m2, best);
+        }
+    };
+    if (D == 2) {
+        load(0, 0);
+        __syncthreads();
+        eval(0, 0, 0);
+    } else {
+        // plane z lives in slot (z + 1) & 3; plane k - 1 is scored once plane
+        // k is loaded.  The slot written at step k was last read at step k - 2,
+        // and the barrier of step k - 1 lies between.
+        for (int k = -1; k <= N; ++k) {
+            load(k, (k + 1) & 3);
+            __syncthreads();
+            if (k >= 1) eval((k - 1) & 3, k & 3, (k + 1) & 3);
+        }
     }
-    any_ref = __syncthreads_or(any_ref);
-    all_deref = __syncthreads_and(all_deref);
-    if (threadIdx.x == 0) flags[b] = any_ref ? 1 : (all_deref ? -1 : 0);
+    for (int o = 16; o > 0; o >>= 1) m2 = fmax(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double M = red[0];
+        for (int w = 1; w < int(blockDim.x >> 5); ++w) M = fmax(M, red[w]);
+        const double E = __dsqrt_rn(M);
+        flags[b] = E > c_ref ? 1 : (E < c_deref ? -1 : 0);
+    }
 }
 
 // ---------------------------------------------------------- regrid transfer

@@ -239,53 +239,83 @@ static __global__ void k_mlp_decide(const float *prob, int64_t n, float tau, int
 
 // Block features: 4^d average pools of density, pressure and speed (density
 // and pressure over the block mean, minus one; speed over the sound speed of
-// the block-mean state) and level / max_level.  One CTA of 64 threads per
-// block, thread t owns pool t = px + 4 (py + 4 pz).  Output is feature-major:
-// x[f * nb + b].
+// the block-mean state) and level / max_level, written feature-major
+// x[f * nb + b].  Pool t = px + 4 (py + 4 pz).
+//
+// One CTA of 256 threads per block (N is 8, 16 or 32).  Cells are visited
+// x fastest so that a warp reads whole rows; density, pressure and speed of a
+// cell are formed in the state's precision, summed over the q = N/4 cells of
+// a pool row by a butterfly within q lanes (every lane of the group ends with
+// the same sum), and the row sums go to shared memory.  One thread per (pool,
+// quantity) then adds its q^(d-1) rows in a fixed order in double, and the
+// block means are the fixed-order sums of the pools: the features do not
+// depend on scheduling.
 template <class real, int D>
-__global__ void __launch_bounds__(64) k_features(const real *u, const BlockInfo *info, Geom g, double gam, float inv_levels,
-                                                 float *x, int64_t nb) {
-    __shared__ double red[2][64];
-    const int b = blockIdx.x;
-    const int t = threadIdx.x;
+__host__ __device__ constexpr size_t features_smem(int N) {
+    return size_t(3) * size_t(D == 3 ? N * N : N) * 4 * sizeof(real);
+}
+
+template <class real, int D>
+__global__ void __launch_bounds__(256) k_features(const real *u, const BlockInfo *info, Geom g, double gam, float inv_levels,
+                                                  float *x, int64_t nb) {
+    extern __shared__ double feat_sm[];
+    __shared__ double pools[3][64];
+    real *rowp = reinterpret_cast<real *>(feat_sm);  // [3][rows][4]
+    const int b = blockIdx.x, t = threadIdx.x;
     const int N = g.N, q = N / 4;
-    const int npool = (D == 3) ? 64 : 16;
+    const int rows = D == 3 ? N * N : N, ncell = rows * N;
+    const int npool = D == 3 ? 64 : 16;
     const real *ub = u + int64_t(b) * g.bstride;
-    double sr = 0.0, sp = 0.0, sv = 0.0;
-    if (t < npool) {
-        const int px = t % 4, py = (t / 4) % 4, pz = (D == 3) ? t / 16 : 0;
-        for (int kk = 0; kk < (D == 3 ? q : 1); ++kk)
-            for (int jj = 0; jj < q; ++jj)
-                for (int ii = 0; ii < q; ++ii) {
-                    const int64_t c = cell_index<real>(g, px * q + ii, py * q + jj, pz * q + kk);
-                    const double rho = double(ub[c]);
-                    double ke = 0.0;
-                    for (int d = 0; d < D; ++d) {
-                        const double vd = double(ub[int64_t(1 + d) * g.ncell + c]) / rho;
-                        ke += vd * vd;
-                    }
-                    sr += rho;
-                    sp += (gam - 1.0) * (double(ub[int64_t(D + 1) * g.ncell + c]) - 0.5 * rho * ke);
-                    sv += sqrt(ke);
-                }
-    }
-    red[0][t] = sr;
-    red[1][t] = sp;
-    __syncthreads();
-    for (int w = 32; w > 0; w >>= 1) {
-        if (t < w) {
-            red[0][t] += red[0][t + w];
-            red[1][t] += red[1][t + w];
+    const real gm1 = real(gam - 1.0);
+    for (int c = t; c < ncell; c += blockDim.x) {  // ncell is a multiple of 32: whole warps iterate
+        const int i = c % N, row = c / N;
+        const int64_t ci = cell_index<real>(g, i, row % N, D == 3 ? row / N : 0);
+        const real rho = ub[ci];
+        const real inv = real(1) / rho;
+        real ke = real(0);
+        for (int d = 0; d < D; ++d) {
+            const real w = ub[int64_t(1 + d) * g.ncell + ci] * inv;
+            ke += w * w;
         }
-        __syncthreads();
+        real r = rho;
+        real pr = gm1 * (ub[int64_t(D + 1) * g.ncell + ci] - real(0.5) * rho * ke);
+        real sp = sqrt(ke);
+        for (int o = 1; o < q; o <<= 1) {
+            r += __shfl_xor_sync(0xffffffffu, r, o);
+            pr += __shfl_xor_sync(0xffffffffu, pr, o);
+            sp += __shfl_xor_sync(0xffffffffu, sp, o);
+        }
+        if (i % q == 0) {
+            rowp[(0 * rows + row) * 4 + i / q] = r;
+            rowp[(1 * rows + row) * 4 + i / q] = pr;
+            rowp[(2 * rows + row) * 4 + i / q] = sp;
+        }
     }
-    const double ncell = double((D == 3) ? N * N * N : N * N), cells = double((D == 3) ? q * q * q : q * q);
-    const double rm = red[0][0] / ncell, pm = red[1][0] / ncell;
-    const double cm = sqrt(gam * pm / rm);
+    __syncthreads();
+    if (t < 3 * npool) {
+        const int v = t / npool, pl = t % npool;
+        const int px = pl % 4, py = (pl / 4) % 4, pz = D == 3 ? pl / 16 : 0;
+        double acc = 0.0;
+        for (int kk = 0; kk < (D == 3 ? q : 1); ++kk)
+            for (int jj = 0; jj < q; ++jj) {
+                const int row = D == 3 ? (pz * q + kk) * N + py * q + jj : py * q + jj;
+                acc += double(rowp[(v * rows + row) * 4 + px]);
+            }
+        pools[v][pl] = acc;
+    }
+    __syncthreads();
     if (t < npool) {
-        x[int64_t(t) * nb + b] = float((sr / cells) / rm - 1.0);
-        x[int64_t(npool + t) * nb + b] = float((sp / cells) / pm - 1.0);
-        x[int64_t(2 * npool + t) * nb + b] = float((sv / cells) / cm);
+        double sr = 0.0, sp = 0.0;
+        for (int l = 0; l < npool; ++l) {
+            sr += pools[0][l];
+            sp += pools[1][l];
+        }
+        const double cells = double(D == 3 ? q * q * q : q * q);
+        const double rm = sr / double(ncell), pm = sp / double(ncell);
+        const double cm = sqrt(gam * pm / rm);
+        x[int64_t(t) * nb + b] = float((pools[0][t] / cells) / rm - 1.0);
+        x[int64_t(npool + t) * nb + b] = float((pools[1][t] / cells) / pm - 1.0);
+        x[int64_t(2 * npool + t) * nb + b] = float((pools[2][t] / cells) / cm);
     }
     if (t == 0) x[int64_t(3 * npool) * nb + b] = float(info[b].level) * inv_levels;
 }

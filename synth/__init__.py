@@ -311,3 +311,28 @@ def point_flags(spec: MeshSpec, lev, g, point, max_level):
         if inside:
             flags[b] = 1
     return flags
+
+
+def normal_shock_state(mach, gamma=1.4, rho1=1.0, p1=1.0):
+    """Post-shock (rho, u, p) of a normal shock of Mach number `mach` moving
+    into gas at rest (rho1, p1), from the Rankine-Hugoniot jump conditions:
+    rho2/rho1 = (g+1) M^2 / ((g-1) M^2 + 2), p2/p1 = (2 g M^2 - (g-1)) / (g+1),
+    u2 = M c1 (1 - rho1 / rho2)."""
+    m2 = mach * mach
+    rho2 = rho1 * (gamma + 1.0) * m2 / ((gamma - 1.0) * m2 + 2.0)
+    p2 = p1 * (2.0 * gamma * m2 - (gamma - 1.0)) / (gamma + 1.0)
+    c1 = np.sqrt(gamma * p1 / rho1)
+    return rho2, mach * c1 * (1.0 - rho1 / rho2), p2
+
+
+def sphere_and_shock(spec: MeshSpec, lev, g, centre, radius=0.1, p_in=100.0, shock_x=0.1, mach=3.0):
+    """Over-pressure sphere (rho = 1, p = p_in inside, 1 outside) and a planar
+    shock of Mach `mach` at x = shock_x moving in +x (post-shock state behind)."""
+    X = cell_centres(spec, lev, g)
+    r2 = sum((X[d] - centre[d]) ** 2 for d in range(spec.ndim))
+    rho2, u2, p2 = normal_shock_state(mach, spec.gamma)
+    behind = X[0] < shock_x
+    rho = np.where(behind, rho2, 1.0)
+    p = np.where(behind, p2, np.where(r2 < radius * radius, p_in, 1.0))
+    vel = [np.where(behind, u2, 0.0)] + [np.zeros_like(rho) for _ in range(spec.ndim - 1)]
+    return mask_interior(spec, primitive_to_state(spec, rho, vel, p))

@@ -40,6 +40,34 @@ def test_features_match_oracle():
     np.testing.assert_allclose(x, ref, rtol=2e-6, atol=2e-6)
 
 
+@pytest.mark.parametrize("N", [8, 32])
+def test_features_match_oracle_fp32(N):
+    """FP32 state: per-cell primitives in FP32, pool and block sums in FP64."""
+    sp = synth.MeshSpec(ndim=3, N=N, ng=2, ntrees=(2, 2, 2), max_level=1)
+    f = amr.Forest(sp, 0, max_blocks=64, precision=32)
+    lev, g = f.blocks()
+    f.regrid(synth.ball_flags(sp, lev, g, (0.5, 0.5, 0.5), (0.3,)))
+    lev, g = f.blocks()
+    u = synth.over_pressure(sp, lev, g, (0.5, 0.5, 0.5), radius=0.2, p_in=10.0)
+    u[:, 1:4] += 0.3 * synth.fourier3d(sp, lev, g, seed=5)[:, 1:4]
+    u = u.astype(np.float32)
+    f.set_state(0, u)
+    x = f.features(0).cpu().numpy()
+    ref = omlp.block_features(sp, u, lev, sp.max_level).T
+    np.testing.assert_allclose(x, ref, rtol=2e-5, atol=2e-5)
+
+
+def test_features_2d_match_oracle():
+    sp = synth.MeshSpec(ndim=2, N=16, ng=2, ntrees=(4, 4, 1), max_level=1)
+    f = amr.Forest(sp, 0, max_blocks=256, precision=64)
+    lev, g = f.blocks()
+    u = synth.kelvin_helmholtz(sp, lev, g, seed=3)
+    f.set_state(0, u)
+    x = f.features(0).cpu().numpy()
+    assert x.shape == (49, f.n)
+    np.testing.assert_allclose(x, omlp.block_features(sp, u, lev, sp.max_level).T, rtol=2e-6, atol=2e-6)
+
+
 def test_forward_and_gradient_match_oracle():
     rng = np.random.default_rng(1)
     F, n = 193, 300

@@ -230,6 +230,69 @@ def test_lohner_flags_bit_exact():
         np.testing.assert_array_equal(f.flag(0, c_ref, c_deref), om.lohner_flags(u, c_ref, c_deref))
 
 
+THRESHOLDS = ((5e-2, 6.25e-3), (2e-2, 1e-2), (1e-3, 5e-4), (0.3, 0.1), (1e-9, -1.0))
+
+
+@pytest.mark.parametrize("N", [8, 16])
+def test_lohner_flags_bit_exact_3d_blast(N):
+    """3-level 3D mesh, over-pressure sphere advanced a few steps (shocked
+    density and pressure); FP64 so both sides see identical ghost values."""
+    nt = 64 // (8 * N)
+    sp = synth.MeshSpec(ndim=3, N=N, ng=2, ntrees=(max(nt, 2),) * 3, max_level=2)
+    c = (0.5, 0.52, 0.48)
+    om, f = make_pair(sp, 0, [ball(c, (0.3, 0.3))] * 2)
+    lev, g = om.blocks()
+    u = synth.over_pressure(sp, lev, g, c, radius=0.1, p_in=100.0)
+    u1 = np.zeros_like(u)
+    for _ in range(3):
+        oracle.heun_step(om, u, u1)
+    f.set_state(0, u)
+    f.fill_ghosts(0)
+    om.fill_ghosts(u)
+    seen = set()
+    for c_ref, c_deref in THRESHOLDS:
+        ref = om.lohner_flags(u, c_ref, c_deref)
+        seen |= set(np.unique(ref).tolist())
+        np.testing.assert_array_equal(f.flag(0, c_ref, c_deref), ref)
+    assert seen == {-1, 0, 1}
+
+
+@pytest.mark.parametrize("N", [16, 32])
+def test_lohner_flags_bit_exact_fp32_uniform(N):
+    """FP32 state on a periodic uniform mesh: the ghosts are plain copies, so
+    the oracle sees exactly the GPU's FP32 values widened to FP64."""
+    sp = synth.MeshSpec(ndim=3, N=N, ng=2, ntrees=(128 // N // 2,) * 3)
+    om, f = make_pair(sp, 0, precision=32)
+    lev, g = om.blocks()
+    u = synth.fourier3d(sp, lev, g, seed=3).astype(np.float32)
+    f.set_state(0, u)
+    f.fill_ghosts(0)
+    u64 = u.astype(np.float64)
+    om.fill_ghosts(u64)
+    np.testing.assert_array_equal(f.get_state(0).astype(np.float64), u64)
+    for c_ref, c_deref in THRESHOLDS:
+        np.testing.assert_array_equal(f.flag(0, c_ref, c_deref), om.lohner_flags(u64, c_ref, c_deref))
+
+
+def test_lohner_flags_nan_cells():
+    """NaN cells: the criterion ignores a NaN score, on both sides (periodic
+    uniform mesh, so the ghost fill only copies the NaNs)."""
+    sp = synth.MeshSpec(ndim=3, N=8, ng=2, ntrees=(4, 4, 4))
+    om, f = make_pair(sp, 0)
+    lev, g = om.blocks()
+    u = synth.fourier3d(sp, lev, g, seed=4)
+    rng = np.random.default_rng(9)
+    S = sp.side
+    for b in rng.choice(om.n, size=min(40, om.n), replace=False):
+        i, j, k = rng.integers(sp.ng, sp.ng + sp.N, 3)
+        u[b, rng.integers(0, sp.nvar), (k * S + j) * S + i] = np.nan
+    f.set_state(0, u)
+    f.fill_ghosts(0)
+    om.fill_ghosts(u)
+    for c_ref, c_deref in THRESHOLDS:
+        np.testing.assert_array_equal(f.flag(0, c_ref, c_deref), om.lohner_flags(u, c_ref, c_deref))
+
+
 @pytest.mark.parametrize("dim", [2, 3])
 def test_regrid_transfer_bit_exact(dim):
     sp = synth.MeshSpec(**(SPEC_2D_AMR if dim == 2 else SPEC_3D_AMR))

@@ -312,3 +312,23 @@ def test_lohner_flags_closed_form():
     a, b = 1.0, 0.125
     E = abs(b - a) / (1e-10 + abs(b - a) + 1e-2 * (3 * a + b))
     assert E > 5e-2
+
+
+@pytest.mark.parametrize("mach", [1.0, 1.5, 3.0, 10.0])
+def test_normal_shock_state_rankine_hugoniot(mach):
+    """The post-shock state used by the shock workloads: in the frame of the
+    shock (speed M c1) mass, momentum and energy fluxes agree on both sides;
+    M = 1 is no shock at all, and the density ratio tends to (g+1)/(g-1)."""
+    g = 1.4
+    rho2, u2, p2 = synth.normal_shock_state(mach, g)
+    s = mach * np.sqrt(g)
+    w1, w2 = -s, u2 - s
+    def fluxes(rho, w, p):
+        return np.array([rho * w, rho * w * w + p, w * (p / (g - 1.0) + 0.5 * rho * w * w + p)])
+    np.testing.assert_allclose(fluxes(rho2, w2, p2), fluxes(1.0, w1, 1.0), rtol=1e-12, atol=1e-12)
+    if mach == 1.0:
+        assert np.allclose((rho2, u2, p2), (1.0, 0.0, 1.0))
+    else:
+        assert 1.0 < rho2 < (g + 1.0) / (g - 1.0) and p2 > 1.0 and u2 > 0.0
+    if mach == 10.0:
+        assert abs(rho2 - 240.0 / 42.0) < 1e-12   # (g+1) M^2 / ((g-1) M^2 + 2) at M = 10
