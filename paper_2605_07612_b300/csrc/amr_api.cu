@@ -13,75 +13,13 @@
 #include <string>
 #include <vector>
 
-#include "../../include/amr.h"
-#include "common.cuh"
-#include "forest.hpp"
-#include "ghost.cuh"
+#include "api_internal.cuh"
 #include "misc.cuh"
-#include "pattern.hpp"
-#include "stage.cuh"
-#include "stage_pair.cuh"
 #include "mlp.cuh"
 
 using namespace amrb;
 
 namespace {
-
-struct DBuf {
-    void *p = nullptr;
-    size_t cap = 0;
-};
-
-}  // namespace
-
-struct amr_forest {
-    amr_config cfg{};                 // shared settings; max_blocks = total capacity
-    std::vector<amr_config> icfg;     // per instance
-    std::vector<Forest> inst;         // per instance; blocks numbered consecutively
-    std::vector<int64_t> offset;      // first block of each instance, total at the end
-    uint64_t revision = 1;            // bumped whenever any instance's mesh changes
-    Pattern pat;
-    uint64_t pattern_rev = ~0ull;
-    Geom geom{};
-    int esize = 8;
-    size_t block_bytes = 0;
-    void *state = nullptr;
-    DBuf r1, r2, r1g, info, fix, fix_start, bflux, bcdata, sc, partial, sums, flags, ops, level;
-    DBuf dxtab, invdxtab, bctype, bcval, cfltab, ranges;   // per-instance tables
-    DBuf feat, prob, mflags, flist;                        // learned-flag predictor
-    cudaStream_t cap_stream = nullptr;
-    cudaGraphExec_t gexec = nullptr;
-    uint64_t graph_rev = ~0ull;
-    int64_t graph_nodes = 0;
-    int graph_flags = -1;
-    bool scalar_stage = false;   // per-cell FP32 kernel instead of the pair kernel (tuning choice)
-    int items_per_cta = 1;       // stage launch: CTAs loop over this many (block, tile) items
-    bool persistent = false;     // stage launch: grid = SMs x resident CTAs, grid-stride sweep
-    int n_sms = 0;
-    bool capturing = false;
-    int64_t launches = 0;
-    std::string err;
-};
-
-namespace {
-
-amr_status fail(amr_forest *f, amr_status s, const char *fmt, ...) {
-    if (f) {
-        char buf[512];
-        va_list ap;
-        va_start(ap, fmt);
-        vsnprintf(buf, sizeof buf, fmt, ap);
-        va_end(ap);
-        f->err = buf;
-    }
-    return s;
-}
-
-#define CU(call)                                                                                   \
-    do {                                                                                           \
-        cudaError_t e_ = (call);                                                                   \
-        if (e_ != cudaSuccess) return fail(f, AMR_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
-    } while (0)
 
 void *dev_alloc(amr_forest *f, size_t bytes) {
     if (bytes == 0) bytes = 16;
@@ -120,14 +58,6 @@ amr_status upload(amr_forest *f, DBuf &b, const std::vector<T> &v) {
     return AMR_OK;
 }
 
-int64_t nblocks(const amr_forest *f) { return f->offset.empty() ? 0 : f->offset.back(); }
-int n_inst(const amr_forest *f) { return int(f->inst.size()); }
-
-// grid of a stage launch for `items` (block, tile) items under the forest's tuning
-int64_t stage_grid(const amr_forest *f, int64_t items, int occupancy) {
-    if (f->persistent) return std::max<int64_t>(1, std::min<int64_t>(items, int64_t(f->n_sms) * std::max(occupancy, 1)));
-    return (items + f->items_per_cta - 1) / f->items_per_cta;
-}
 
 
 void set_offsets(amr_forest *f) {
@@ -141,7 +71,6 @@ const Leaf &leaf_at(const amr_forest *f, int64_t b, int *which = nullptr) {
     return f->inst[i].leaves[size_t(b - f->offset[i])];
 }
 
-void *slot_ptr(const amr_forest *f, int s) { return static_cast<char *>(f->state) + size_t(s) * f->cfg.max_blocks * f->block_bytes; }
 
 void fill_geom(amr_forest *f) {
     const amr_config &c = f->cfg;
@@ -248,86 +177,6 @@ amr_status upload_pattern(amr_forest *f) {
 }
 
 // ------------------------------------------------------------------ launches
-template <class real, int D>
-amr_status launch_ghosts(amr_forest *f, int s, cudaStream_t st, bool gather) {
-    GhostArgs<real> a{};
-    a.u = static_cast<real *>(slot_ptr(f, s));
-    a.bcdata = static_cast<const real *>(f->bcdata.p);
-    a.bc_type = static_cast<const int32_t *>(f->bctype.p);
-    a.bc_val = static_cast<const real *>(f->bcval.p);
-    a.info = static_cast<const BlockInfo *>(f->info.p);
-    for (int round = 0; round < 2; ++round) {
-        const auto &lst = round == 0 ? (gather ? f->pat.round1_gather : f->pat.round1) : f->pat.round2;
-        if (lst.empty()) continue;
-        a.list = static_cast<const Entry *>(round == 0 ? (gather ? f->r1g.p : f->r1.p) : f->r2.p);
-        a.n = int(lst.size());
-        const int grid = (a.n + 7) / 8;
-        const int N = f->cfg.block_n, NG = f->cfg.n_ghost;
-        bool launched = false;
-#define AMR_GHOST_CASE(n_, g_)                                                   \
-    if (!launched && N == n_ && NG == g_) {                                     \
-        k_ghost<real, D, n_, g_><<<grid, 256, 0, st>>>(a, f->geom);             \
-        launched = true;                                                        \
-    }
-        AMR_GHOST_CASE(8, 1) AMR_GHOST_CASE(8, 2) AMR_GHOST_CASE(8, 3) AMR_GHOST_CASE(8, 4)
-        AMR_GHOST_CASE(16, 1) AMR_GHOST_CASE(16, 2) AMR_GHOST_CASE(16, 3) AMR_GHOST_CASE(16, 4)
-        AMR_GHOST_CASE(32, 1) AMR_GHOST_CASE(32, 2) AMR_GHOST_CASE(32, 3) AMR_GHOST_CASE(32, 4)
-#undef AMR_GHOST_CASE
-        if (!launched) return fail(f, AMR_EINVAL, "no ghost kernel for block_n %d, n_ghost %d", N, NG);
-        ++f->launches;
-    }
-    CU(cudaGetLastError());
-    return AMR_OK;
-}
-
-template <class real, int D, int N, int NG>
-amr_status launch_stage_t(amr_forest *f, const StageArgs<real> &a, cudaStream_t st) {
-    constexpr int T = N < 16 ? N : 16;
-    using Sh = StageShape<real, D, N, NG, T>;
-    static bool attr_done = false;
-    const size_t smem = Sh::smem_bytes();
-    if (!attr_done) {
-        CU(cudaFuncSetAttribute(k_stage<real, D, N, NG, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-        attr_done = true;
-    }
-    const int64_t items = nblocks(f) * Sh::TILES;
-    if (items > 0) {
-        StageArgs<real> b = a;
-        b.n_items = int(items);
-        int occ = 1;
-        if (f->persistent) CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_stage<real, D, N, NG, T>, Sh::NT, smem));
-        const int64_t grid = stage_grid(f, items, occ);
-        k_stage<real, D, N, NG, T><<<unsigned(grid), Sh::NT, smem, st>>>(b, f->geom);
-        ++f->launches;
-    }
-    CU(cudaGetLastError());
-    return AMR_OK;
-}
-
-// FP32, 3D, two ghost layers: the packed cell-pair kernel
-template <int N>
-amr_status launch_stage_pair(amr_forest *f, const StageArgs<float> &a, cudaStream_t st) {
-    using Sh = PairShape<N>;
-    static bool attr_done = false;
-    const size_t smem = Sh::smem_bytes();
-    if (!attr_done) {
-        CU(cudaFuncSetAttribute(k_stage_pair<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-        attr_done = true;
-    }
-    const int64_t items = nblocks(f) * Sh::TILES;
-    if (items > 0) {
-        StageArgs<float> b = a;
-        b.n_items = int(items);
-        int occ = 1;
-        if (f->persistent) CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_stage_pair<N>, Sh::NT, smem));
-        const int64_t grid = stage_grid(f, items, occ);
-        k_stage_pair<N><<<unsigned(grid), Sh::NT, smem, st>>>(b, f->geom);
-        ++f->launches;
-    }
-    CU(cudaGetLastError());
-    return AMR_OK;
-}
-
 template <class real, int D>
 amr_status launch_stage(amr_forest *f, const StageArgs<real> &a, cudaStream_t st) {
     const int N = f->cfg.block_n, NG = f->cfg.n_ghost;

@@ -1,0 +1,96 @@
+// Internal state of the C ABI's forest object and the helpers shared by the
+// translation units that launch kernels.  Not part of the public interface.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/amr.h"
+#include "common.cuh"
+#include "forest.hpp"
+#include "pattern.hpp"
+#include "stage.cuh"
+
+namespace amrb {
+
+struct DBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+};
+
+}  // namespace amrb
+
+struct amr_forest {
+    amr_config cfg{};                 // shared settings; max_blocks = total capacity
+    std::vector<amr_config> icfg;     // per instance
+    std::vector<amrb::Forest> inst;         // per instance; blocks numbered consecutively
+    std::vector<int64_t> offset;      // first block of each instance, total at the end
+    uint64_t revision = 1;            // bumped whenever any instance's mesh changes
+    amrb::Pattern pat;
+    uint64_t pattern_rev = ~0ull;
+    amrb::Geom geom{};
+    int esize = 8;
+    size_t block_bytes = 0;
+    void *state = nullptr;
+    amrb::DBuf r1, r2, r1g, info, fix, fix_start, bflux, bcdata, sc, partial, sums, flags, ops, level;
+    amrb::DBuf dxtab, invdxtab, bctype, bcval, cfltab, ranges;   // per-instance tables
+    amrb::DBuf feat, prob, mflags, flist;                        // learned-flag predictor
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    uint64_t graph_rev = ~0ull;
+    int64_t graph_nodes = 0;
+    int graph_flags = -1;
+    bool scalar_stage = false;   // per-cell FP32 kernel instead of the pair kernel (tuning choice)
+    int items_per_cta = 1;       // stage launch: CTAs loop over this many (block, tile) items
+    bool persistent = false;     // stage launch: grid = SMs x resident CTAs, grid-stride sweep
+    int n_sms = 0;
+    bool capturing = false;
+    int64_t launches = 0;
+    std::string err;
+};
+
+namespace amrb {
+
+inline amr_status fail(amr_forest *f, amr_status s, const char *fmt, ...) {
+    if (f) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        f->err = buf;
+    }
+    return s;
+}
+
+#define CU(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) return fail(f, AMR_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+inline int64_t nblocks(const amr_forest *f) { return f->offset.empty() ? 0 : f->offset.back(); }
+inline int n_inst(const amr_forest *f) { return int(f->inst.size()); }
+
+// grid of a stage launch for `items` (block, tile) items under the forest's tuning
+inline int64_t stage_grid(const amr_forest *f, int64_t items, int occupancy) {
+    if (f->persistent) return std::max<int64_t>(1, std::min<int64_t>(items, int64_t(f->n_sms) * std::max(occupancy, 1)));
+    return (items + f->items_per_cta - 1) / f->items_per_cta;
+}
+inline void *slot_ptr(const amr_forest *f, int s) { return static_cast<char *>(f->state) + size_t(s) * f->cfg.max_blocks * f->block_bytes; }
+
+// Kernel launchers, each instantiated in its own translation unit so that the
+// library builds in parallel.
+template <class real, int D>
+amr_status launch_ghosts(amr_forest *f, int s, cudaStream_t st, bool gather);
+template <class real, int D, int N, int NG>
+amr_status launch_stage_t(amr_forest *f, const StageArgs<real> &a, cudaStream_t st);
+template <int N>
+amr_status launch_stage_pair(amr_forest *f, const StageArgs<float> &a, cudaStream_t st);
+
+}  // namespace amrb

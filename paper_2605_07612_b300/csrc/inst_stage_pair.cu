@@ -1,0 +1,8 @@
+// Explicit instantiations of kernel launchers (parallel build unit).
+#include "launch_kernels.cuh"
+
+namespace amrb {
+template amr_status launch_stage_pair<8>(amr_forest *, const StageArgs<float> &, cudaStream_t);
+template amr_status launch_stage_pair<16>(amr_forest *, const StageArgs<float> &, cudaStream_t);
+template amr_status launch_stage_pair<32>(amr_forest *, const StageArgs<float> &, cudaStream_t);
+}  // namespace amrb

@@ -1,0 +1,101 @@
+// Definitions of the ghost and stage kernel launchers declared in
+// api_internal.cuh; the inst_*.cu units instantiate them.
+#pragma once
+#include <type_traits>
+
+#include "api_internal.cuh"
+#include "ghost.cuh"
+#include "stage.cuh"
+#include "stage_pair.cuh"
+
+namespace amrb {
+
+template <class real, int D>
+amr_status launch_ghosts(amr_forest *f, int s, cudaStream_t st, bool gather) {
+    GhostArgs<real> a{};
+    a.u = static_cast<real *>(slot_ptr(f, s));
+    a.bcdata = static_cast<const real *>(f->bcdata.p);
+    a.bc_type = static_cast<const int32_t *>(f->bctype.p);
+    a.bc_val = static_cast<const real *>(f->bcval.p);
+    a.info = static_cast<const BlockInfo *>(f->info.p);
+    for (int round = 0; round < 2; ++round) {
+        const auto &lst = round == 0 ? (gather ? f->pat.round1_gather : f->pat.round1) : f->pat.round2;
+        if (lst.empty()) continue;
+        a.list = static_cast<const Entry *>(round == 0 ? (gather ? f->r1g.p : f->r1.p) : f->r2.p);
+        a.n = int(lst.size());
+        const int grid = (a.n + 7) / 8;
+        const int N = f->cfg.block_n, NG = f->cfg.n_ghost;
+        bool launched = false;
+#define AMR_GHOST_CASE(n_, g_)                                                   \
+    if (!launched && N == n_ && NG == g_) {                                     \
+        k_ghost<real, D, n_, g_><<<grid, 256, 0, st>>>(a, f->geom);             \
+        launched = true;                                                        \
+    }
+        AMR_GHOST_CASE(8, 1) AMR_GHOST_CASE(8, 2) AMR_GHOST_CASE(8, 3) AMR_GHOST_CASE(8, 4)
+        AMR_GHOST_CASE(16, 1) AMR_GHOST_CASE(16, 2) AMR_GHOST_CASE(16, 3) AMR_GHOST_CASE(16, 4)
+        AMR_GHOST_CASE(32, 1) AMR_GHOST_CASE(32, 2) AMR_GHOST_CASE(32, 3) AMR_GHOST_CASE(32, 4)
+#undef AMR_GHOST_CASE
+        if (!launched) return fail(f, AMR_EINVAL, "no ghost kernel for block_n %d, n_ghost %d", N, NG);
+        ++f->launches;
+    }
+    CU(cudaGetLastError());
+    return AMR_OK;
+}
+
+template <class real, int D, int N, int NG>
+amr_status launch_stage_t(amr_forest *f, const StageArgs<real> &a, cudaStream_t st) {
+    constexpr int T = N < 16 ? N : 16;
+    using Sh = StageShape<real, D, N, NG, T>;
+    static bool attr_done = false;
+    const size_t smem = Sh::smem_bytes();
+    if (!attr_done) {
+        CU(cudaFuncSetAttribute(k_stage<real, D, N, NG, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        attr_done = true;
+    }
+    const int64_t items = nblocks(f) * Sh::TILES;
+    if (items > 0) {
+        StageArgs<real> b = a;
+        b.n_items = int(items);
+        int occ = 1;
+        if (f->persistent) CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_stage<real, D, N, NG, T>, Sh::NT, smem));
+        const int64_t grid = stage_grid(f, items, occ);
+        k_stage<real, D, N, NG, T><<<unsigned(grid), Sh::NT, smem, st>>>(b, f->geom);
+        ++f->launches;
+    }
+    CU(cudaGetLastError());
+    return AMR_OK;
+}
+
+// FP32, 3D, two ghost layers: the packed cell-pair kernel
+template <int N>
+amr_status launch_stage_pair(amr_forest *f, const StageArgs<float> &a, cudaStream_t st) {
+    using Sh = PairShape<N>;
+    static bool attr_done = false;
+    const size_t smem = Sh::smem_bytes();
+    if (!attr_done) {
+        CU(cudaFuncSetAttribute(k_stage_pair<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        attr_done = true;
+    }
+    const int64_t items = nblocks(f) * Sh::TILES;
+    if (items > 0) {
+        StageArgs<float> b = a;
+        b.n_items = int(items);
+        int occ = 1;
+        if (f->persistent) CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_stage_pair<N>, Sh::NT, smem));
+        const int64_t grid = stage_grid(f, items, occ);
+        k_stage_pair<N><<<unsigned(grid), Sh::NT, smem, st>>>(b, f->geom);
+        ++f->launches;
+    }
+    CU(cudaGetLastError());
+    return AMR_OK;
+}
+
+}  // namespace amrb
+
+#define AMR_INST_STAGE(real, D)                                                                     \
+    template amr_status launch_stage_t<real, D, 8, 2>(amr_forest *, const StageArgs<real> &, cudaStream_t);  \
+    template amr_status launch_stage_t<real, D, 16, 2>(amr_forest *, const StageArgs<real> &, cudaStream_t); \
+    template amr_status launch_stage_t<real, D, 32, 2>(amr_forest *, const StageArgs<real> &, cudaStream_t); \
+    template amr_status launch_stage_t<real, D, 8, 3>(amr_forest *, const StageArgs<real> &, cudaStream_t);  \
+    template amr_status launch_stage_t<real, D, 16, 3>(amr_forest *, const StageArgs<real> &, cudaStream_t); \
+    template amr_status launch_stage_t<real, D, 32, 3>(amr_forest *, const StageArgs<real> &, cudaStream_t);
