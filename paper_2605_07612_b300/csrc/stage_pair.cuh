@@ -15,7 +15,9 @@
 // states (MUSCL with minmod) are formed in the flux phase from the ring: an
 // x-face pair reads three aligned pairs of a row, a y- or z-face pair four.
 // The T x-faces and T y-faces left over at the tile's upper edges are taken
-// by T threads of the first warp.
+// by T/2 threads of the first and T/2 of the second warp; the second round of
+// halo loads goes to the last warps, so that the warps meet at the barrier
+// with similar amounts of work.
 #pragma once
 
 #include "stage.cuh"
@@ -32,13 +34,19 @@ struct PF {
     __device__ static __forceinline__ float2 rsqrt(float2 a) { return make_float2(rsqrtf(a.x), rsqrtf(a.y)); }
     __device__ static __forceinline__ float2 rcp(float2 a) { return make_float2(__fdividef(1.f, a.x), __fdividef(1.f, a.y)); }
     __device__ static __forceinline__ float2 abs(float2 a) { return make_float2(fabsf(a.x), fabsf(a.y)); }
-    // 0.5 * minmod(a, b): (sign a + sign b) / 4 * min(|a|, |b|) -- zero unless
-    // both have the same strict sign (a zero gives min 0)
-    __device__ static __forceinline__ float2 half_minmod(float2 a, float2 b) {
-        const float2 s = add(make_float2(copysignf(1.f, a.x), copysignf(1.f, a.y)),
-                             make_float2(copysignf(1.f, b.x), copysignf(1.f, b.y)));
-        const float2 m = make_float2(fminf(fabsf(a.x), fabsf(b.x)), fminf(fabsf(a.y), fabsf(b.y)));
-        return mul(mul(s, m), sp(0.25f));
+    // 0.5 minmod(a, b) = qs(a, b) * mabs(a, b): qs = (sign a + sign b) / 4 is
+    // +-1/2 when the signs agree and 0 otherwise; mabs = min(|a|, |b|) (a zero
+    // gives 0).  The product is exact, so w + 0.5 minmod(a, b) is the single
+    // rounding fma(qs, mabs, w).
+    __device__ static __forceinline__ float sg(float a) { return __uint_as_float((__float_as_uint(a) & 0x80000000u) | 0x3e800000u); }
+    __device__ static __forceinline__ float2 qs(float2 a, float2 b) {
+        return add(make_float2(sg(a.x), sg(a.y)), make_float2(sg(b.x), sg(b.y)));
+    }
+    __device__ static __forceinline__ float2 mabs(float2 a, float2 b) {
+        return make_float2(fminf(fabsf(a.x), fabsf(b.x)), fminf(fabsf(a.y), fabsf(b.y)));
+    }
+    __device__ static __forceinline__ float2 nmabs(float2 a, float2 b) {
+        return make_float2(fmaxf(-fabsf(a.x), -fabsf(b.x)), fmaxf(-fabsf(a.y), -fabsf(b.y)));
     }
     __device__ static __forceinline__ bool positive(float2 a) { return a.x > 0.f && a.y > 0.f; }
 };
@@ -102,8 +110,9 @@ __device__ __forceinline__ void pair_flux(const float2 *wL, const float2 *wR, in
 // face states of a pair of faces from the four pairs of cells around them
 // (c-2, c-1, c, c+1 along the face normal)
 __device__ __forceinline__ void pair_states(float2 w0, float2 w1, float2 w2, float2 w3, float2 &L, float2 &R) {
-    L = PF::add(w1, PF::half_minmod(PF::sub(w1, w0), PF::sub(w2, w1)));
-    R = PF::sub(w2, PF::half_minmod(PF::sub(w2, w1), PF::sub(w3, w2)));
+    const float2 d01 = PF::sub(w1, w0), d12 = PF::sub(w2, w1), d23 = PF::sub(w3, w2);
+    L = PF::fma(PF::qs(d01, d12), PF::mabs(d01, d12), w1);
+    R = PF::fma(PF::qs(d12, d23), PF::nmabs(d12, d23), w2);
 }
 
 // conservative -> primitive for a pair of cells
@@ -124,17 +133,26 @@ struct PairShape {
     static constexpr int T = N < 16 ? N : 16, NG = 2, S = N + 2 * NG, P = T + 4, PL = P * P, R = 4, V = 5;
     static constexpr int NT = T * T / 2;              // threads: one per cell pair of a plane
     static constexpr int TILES = (N / T) * (N / T);
-    static constexpr int FXP = T + 2;                 // x-flux row pitch (17 faces + pad)
+    // x-flux row pitch (T + 1 faces + pad); for T = 16 it is 20 words, so the
+    // rows r and r + 4 that a half-warp touches fall into opposite bank halves
+    static constexpr int FXP = T == 16 ? 20 : T + 2;
     static constexpr int NFX = T * FXP;
     static constexpr int NFY = (T + 1) * T;
     static constexpr int FBUF = V * (NFX + NFY);      // one flux buffer
-    static constexpr int HALO_PAIRS = P * P / 2;
-    static constexpr int GHOST_PAIRS = T * T / 2;
-    static constexpr int LOADS = (HALO_PAIRS + NT - 1) / NT;
+    static constexpr int LOADS = ((T * T + 8 * T) / 2 + NT - 1) / NT;   // halo pairs without corners
+    // y-flux row `row` (T + 1 rows of T faces): for T = 16 rows 2m and 2m + 1
+    // share a 32-word line, their halves swapped when bit 2 of the row is
+    // set, so rows r and r + 4 (one half-warp) use opposite bank halves
+    __device__ static __forceinline__ int fy(int row, int c) {
+        if constexpr (T == 16) return 32 * (row >> 1) + 16 * ((row ^ (row >> 2)) & 1) + c;
+        else return row * T + c;
+    }
     static constexpr size_t smem_bytes() { return sizeof(float) * (size_t(R) * V * PL + 2 * size_t(FBUF)); }
 };
 
-template <int N>
+// NPREV >= 0: the number of previous states, fixed at compile time (Heun's two
+// stages use 1 and 2); -1 reads it from the arguments.
+template <int N, int NPREV>
 __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const Geom &g, int item) {
     using Sh = PairShape<N>;
     constexpr int T = Sh::T, NG = Sh::NG, S = Sh::S, P = Sh::P, PL = Sh::PL, V = Sh::V, NT = Sh::NT;
@@ -148,7 +166,19 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
     const int b = item / Sh::TILES;
     const int tile = item - b * Sh::TILES;
     const int tx0 = (tile % (N / T)) * T, ty0 = (tile / (N / T)) * T;
-    const int ip = tid % (T / 2), tj = tid / (T / 2);
+    // thread -> (row tj, pair ip).  For T = 16 the two 8-lane row groups of a
+    // half-warp take rows r and r + 4: 80 words apart in the ring (pitch 20),
+    // i.e. opposite halves of the 32 banks, so a half-warp's 8-byte accesses
+    // to a ring row never conflict.
+    int ip, tj;
+    if constexpr (T == 16) {
+        const int lane = tid & 31, q = (tid >> 5) * 2 + (lane >> 4);
+        ip = lane & 7;
+        tj = (q & 3) + (q >> 2) * 8 + ((lane >> 3) & 1) * 4;
+    } else {
+        ip = tid % (T / 2);
+        tj = tid / (T / 2);
+    }
     const int ci = 2 * ip;                                      // first cell of the pair
     const BlockInfo info = a.info[b];
     const int gc = info.gclass;
@@ -184,47 +214,81 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
         o = gofs(tx0 + ii, ty0 + jj, k);
         return ub;
     };
-    auto pair_of = [&](int p, bool halo, int &ii, int &jj) -> bool {
-        if (halo) {
-            if (p >= Sh::HALO_PAIRS) return false;
-            jj = p / (P / 2) - 2;
-            ii = 2 * (p % (P / 2)) - 2;
-            return !((jj < 0 || jj >= T) && (ii < 0 || ii >= T));
+    // ---- plane loading: conservative pairs into registers, then primitives
+    // into the ring.  An interior plane (0 <= k < N) needs the tile and its
+    // x/y halo without the corners: NPAIR = (T^2 + 8T) / 2 pairs, numbered row
+    // by row.  Every thread takes pair tid; the remaining REST pairs go to the
+    // last REST threads (warps 2 and 3 for T = 16, whose first two warps
+    // compute the tile's edge faces).  The source of a thread's pairs does
+    // not change with k, so its address at k = 0 is kept.  The planes k < 0
+    // and k >= N need only the tile: thread tid takes its own pair.
+    constexpr int HP = T / 2, WP = (T + 4) / 2;
+    constexpr int NPAIR = 2 * HP + T * WP + 2 * HP, REST = NPAIR - NT;
+    static_assert(Sh::LOADS == 2 && REST > 0 && REST <= NT, "two load rounds per plane");
+    auto pair_rc = [&](int p, int &ii, int &jj) {
+        if (p < 2 * HP) {
+            jj = p / HP - 2;
+            ii = 2 * (p % HP);
+        } else if (p < 2 * HP + T * WP) {
+            const int q = p - 2 * HP;
+            jj = q / WP;
+            ii = 2 * (q % WP) - 2;
+        } else {
+            const int q = p - 2 * HP - T * WP;
+            jj = T + q / HP;
+            ii = 2 * (q % HP);
         }
-        if (p >= Sh::GHOST_PAIRS) return false;
-        jj = p / (T / 2);
-        ii = 2 * (p % (T / 2));
-        return true;
     };
+    const float *hsrc[2];
+    int hoff[2];
+    bool hval[2];
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+        const int p = l == 0 ? tid : (tid >= NT - REST ? NT + tid - (NT - REST) : -1);
+        hval[l] = p >= 0;
+        hsrc[l] = ub;
+        hoff[l] = 0;
+        if (p >= 0) {
+            int ii, jj;
+            pair_rc(p, ii, jj);
+            int64_t o;
+            hsrc[l] = src_of(ii, jj, 0, o) + o;
+            hoff[l] = (jj + 2) * P + ii + 2;
+        }
+    }
+    const int own_off = (tid / (T / 2) + 2) * P + 2 * (tid % (T / 2)) + 2;
 
-    // ---- plane loading: conservative pairs into registers, then primitives into the ring
     float2 pre[Sh::LOADS][V];
     auto prefetch = [&](int k) {
-        const bool halo = (k >= 0 && k < N);
+        if (k >= 0 && k < N) {
+            const int64_t ko = int64_t(k) * S * S;
 #pragma unroll
-        for (int l = 0; l < Sh::LOADS; ++l) {
-            int ii, jj;
-            if (pair_of(tid + l * NT, halo, ii, jj)) {
-                int64_t o;
-                const float *src = src_of(ii, jj, k, o);
+            for (int l = 0; l < 2; ++l)
+                if (hval[l])
 #pragma unroll
-                for (int v = 0; v < V; ++v) pre[l][v] = *reinterpret_cast<const float2 *>(src + v * NC + o);
-            }
+                    for (int v = 0; v < V; ++v) pre[l][v] = *reinterpret_cast<const float2 *>(hsrc[l] + ko + v * NC);
+        } else {
+            int64_t o;
+            const float *src = src_of(2 * (tid % (T / 2)), tid / (T / 2), k, o);
+#pragma unroll
+            for (int v = 0; v < V; ++v) pre[0][v] = *reinterpret_cast<const float2 *>(src + v * NC + o);
         }
+    };
+    auto commit_pair = [&](float *dst, const float2 *U) {
+        float2 w[V];
+        pair_prim(U, w, gam);
+        nonphys |= !PF::positive(w[0]) || !PF::positive(w[4]);
+#pragma unroll
+        for (int v = 0; v < V; ++v) *reinterpret_cast<float2 *>(dst + v * PL) = w[v];
     };
     auto commit = [&](int k) {
         float *pl = slot(k);
-        const bool halo = (k >= 0 && k < N);
+        if (k >= 0 && k < N) {
 #pragma unroll
-        for (int l = 0; l < Sh::LOADS; ++l) {
-            int ii, jj;
-            if (!pair_of(tid + l * NT, halo, ii, jj)) continue;
-            float2 w[V];
-            pair_prim(pre[l], w, gam);
-            nonphys |= !PF::positive(w[0]) || !PF::positive(w[4]);
-            const int o = (jj + 2) * P + (ii + 2);
-#pragma unroll
-            for (int v = 0; v < V; ++v) *reinterpret_cast<float2 *>(pl + v * PL + o) = w[v];
+            for (int l = 0; l < 2; ++l)
+                if (hval[l]) commit_pair(pl + hoff[l], pre[l]);
+        } else {
+            commit_pair(pl + own_off, pre[0]);
         }
     };
     auto ld2 = [&](const float *pl, int v, int jj, int ii) -> float2 {
@@ -277,7 +341,7 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
             pair_states(ld2(pl, v, tj - 2, ci), ld2(pl, v, tj - 1, ci), ld2(pl, v, tj, ci), ld2(pl, v, tj + 1, ci), wL[v], wR[v]);
         pair_flux<1>(wL, wR, 1, gam, gm1i, F);
 #pragma unroll
-        for (int v = 0; v < V; ++v) *reinterpret_cast<float2 *>(Fy + v * (T + 1) * T + tj * T + ci) = F[v];
+        for (int v = 0; v < V; ++v) *reinterpret_cast<float2 *>(Fy + v * (T + 1) * T + Sh::fy(tj, ci)) = F[v];
         if (tj == 0 && ty0 == 0) store_bflux2(2, tx0 + ci + N * k, F);
         // z-face k + 1/2 of cells ci, ci+1: the plus state of plane k is
         // carried from the previous plane, the minus / plus states of plane
@@ -287,48 +351,46 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
 #pragma unroll
             for (int v = 0; v < V; ++v) {
                 const float2 w1 = ld2(p1, v, tj, ci), w2 = ld2(p2, v, tj, ci), w3 = ld2(p3, v, tj, ci);
-                const float2 hs = PF::half_minmod(PF::sub(w2, w1), PF::sub(w3, w2));
-                wR[v] = PF::sub(w2, hs);
+                const float2 d12 = PF::sub(w2, w1), d23 = PF::sub(w3, w2), q = PF::qs(d12, d23);
+                wR[v] = PF::fma(q, PF::nmabs(d12, d23), w2);
                 wL[v] = zP[v];
-                zP[v] = PF::add(w2, hs);
+                zP[v] = PF::fma(q, PF::mabs(d12, d23), w2);
             }
             pair_flux<2>(wL, wR, 2, gam, gm1i, Fz_new);
             if (k == N - 1) store_bflux2(5, tx0 + ci + N * (ty0 + tj), Fz_new);
         }
-        // leftovers: x-face T of rows (2r, 2r+1) for tid < 8; y-face T of
-        // columns (2c, 2c+1) for 8 <= tid < 16
-        if (tid < T) {
-            const int dir = tid >= T / 2;
-            const int r = dir ? tid - T / 2 : tid;
-            if (!dir) {
+        // the tile's upper edge faces: x-face T of rows (2r, 2r+1) by the first
+        // T/2 threads, y-face T of columns (2r, 2r+1) by T/2 threads of the
+        // next warp (of the same warp when the CTA has one)
+        constexpr int YT = NT > 32 ? 32 : T / 2;
+        if (tid < T / 2) {
+            const int r = tid;
 #pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    const float *row0 = pl + v * PL + (2 * r + 2) * P + 2, *row1 = row0 + P;
-                    pair_states(make_float2(row0[T - 2], row1[T - 2]), make_float2(row0[T - 1], row1[T - 1]),
-                                make_float2(row0[T], row1[T]), make_float2(row0[T + 1], row1[T + 1]), wL[v], wR[v]);
-                }
-            } else {
-#pragma unroll
-                for (int v = 0; v < V; ++v)
-                    pair_states(ld2(pl, v, T - 2, 2 * r), ld2(pl, v, T - 1, 2 * r), ld2(pl, v, T, 2 * r), ld2(pl, v, T + 1, 2 * r),
-                                wL[v], wR[v]);
+            for (int v = 0; v < V; ++v) {
+                const float *row0 = pl + v * PL + (2 * r + 2) * P + 2, *row1 = row0 + P;
+                pair_states(make_float2(row0[T - 2], row1[T - 2]), make_float2(row0[T - 1], row1[T - 1]),
+                            make_float2(row0[T], row1[T]), make_float2(row0[T + 1], row1[T + 1]), wL[v], wR[v]);
             }
-            pair_flux<-1>(wL, wR, dir, gam, gm1i, F);
-            if (!dir) {
+            pair_flux<0>(wL, wR, 0, gam, gm1i, F);
 #pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    Fx[v * NFX + (2 * r) * FXP + T] = F[v].x;
-                    Fx[v * NFX + (2 * r + 1) * FXP + T] = F[v].y;
-                }
-                if (tx0 + T == N) {
-                    store_bflux1(1, ty0 + 2 * r + N * k, F[0].x, F[1].x, F[2].x, F[3].x, F[4].x);
-                    store_bflux1(1, ty0 + 2 * r + 1 + N * k, F[0].y, F[1].y, F[2].y, F[3].y, F[4].y);
-                }
-            } else {
-#pragma unroll
-                for (int v = 0; v < V; ++v) *reinterpret_cast<float2 *>(Fy + v * (T + 1) * T + T * T + 2 * r) = F[v];
-                if (ty0 + T == N) store_bflux2(3, tx0 + 2 * r + N * k, F);
+            for (int v = 0; v < V; ++v) {
+                Fx[v * NFX + (2 * r) * FXP + T] = F[v].x;
+                Fx[v * NFX + (2 * r + 1) * FXP + T] = F[v].y;
             }
+            if (tx0 + T == N) {
+                store_bflux1(1, ty0 + 2 * r + N * k, F[0].x, F[1].x, F[2].x, F[3].x, F[4].x);
+                store_bflux1(1, ty0 + 2 * r + 1 + N * k, F[0].y, F[1].y, F[2].y, F[3].y, F[4].y);
+            }
+        } else if (tid >= YT && tid < YT + T / 2) {
+            const int r = tid - YT;
+#pragma unroll
+            for (int v = 0; v < V; ++v)
+                pair_states(ld2(pl, v, T - 2, 2 * r), ld2(pl, v, T - 1, 2 * r), ld2(pl, v, T, 2 * r), ld2(pl, v, T + 1, 2 * r),
+                            wL[v], wR[v]);
+            pair_flux<1>(wL, wR, 1, gam, gm1i, F);
+#pragma unroll
+            for (int v = 0; v < V; ++v) *reinterpret_cast<float2 *>(Fy + v * (T + 1) * T + Sh::fy(T, 2 * r)) = F[v];
+            if (ty0 + T == N) store_bflux2(3, tx0 + 2 * r + N * k, F);
         }
     };
 
@@ -336,12 +398,12 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
     // (read by the update of plane k in the next iteration) and this block's
     // derivative plane k + 5 (loaded into registers two iterations later)
     auto l2_ahead = [&](int k) {
-        if (tid != 0) return;
+        if (tid != NT - 32) return;   // a thread of the last warp (the first two take the edge faces)
         constexpr unsigned PB = unsigned(S) * S * sizeof(float);
         const int64_t blk = int64_t(b) * V * NC;
 #pragma unroll
         for (int q = 0; q < 4; ++q)
-            if (q < a.nprev)
+            if (q < (NPREV >= 0 ? NPREV : a.nprev))
 #pragma unroll
                 for (int v = 0; v < V; ++v) l2_prefetch(a.prev[q] + blk + v * NC + int64_t(k + NG) * S * S, PB);
         if (k + 5 <= N + 1)
@@ -360,15 +422,15 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
         for (int v = 0; v < V; ++v) {
             const float2 x0 = *reinterpret_cast<const float2 *>(Fx + v * NFX + tj * FXP + ci);
             const float2 x1 = *reinterpret_cast<const float2 *>(Fx + v * NFX + tj * FXP + ci + 2);
-            const float2 y0 = *reinterpret_cast<const float2 *>(Fy + v * (T + 1) * T + tj * T + ci);
-            const float2 y1 = *reinterpret_cast<const float2 *>(Fy + v * (T + 1) * T + (tj + 1) * T + ci);
+            const float2 y0 = *reinterpret_cast<const float2 *>(Fy + v * (T + 1) * T + Sh::fy(tj, ci));
+            const float2 y1 = *reinterpret_cast<const float2 *>(Fy + v * (T + 1) * T + Sh::fy(tj + 1, ci));
             float2 du = PF::mul(PF::sub(x0, make_float2(x0.y, x1.x)), i0);
             du = PF::fma(PF::sub(y0, y1), i1, du);
             du = PF::fma(PF::sub(Fzlo[v], Fzhi[v]), i2, du);
             float2 acc = PF::sp(0.f);
 #pragma unroll
             for (int q = 0; q < 4; ++q)
-                if (q < a.nprev)
+                if (q < (NPREV >= 0 ? NPREV : a.nprev))
                     acc = PF::fma(PF::sp(a.wprev[q]), *reinterpret_cast<const float2 *>(a.prev[q] + ob + v * NC), acc);
             U[v] = PF::fma(dte, du, acc);
             *reinterpret_cast<float2 *>(a.out + ob + v * NC) = U[v];
@@ -419,10 +481,9 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             const float2 w0 = ld2(p0, v, tj, ci), w1 = ld2(p1, v, tj, ci), w2 = ld2(p2, v, tj, ci), w3 = ld2(p3, v, tj, ci);
-            wL[v] = PF::add(w1, PF::half_minmod(PF::sub(w1, w0), PF::sub(w2, w1)));
-            const float2 hs = PF::half_minmod(PF::sub(w2, w1), PF::sub(w3, w2));
-            wR[v] = PF::sub(w2, hs);
-            zP[v] = PF::add(w2, hs);
+            pair_states(w0, w1, w2, w3, wL[v], wR[v]);
+            const float2 d12 = PF::sub(w2, w1), d23 = PF::sub(w3, w2);
+            zP[v] = PF::fma(PF::qs(d12, d23), PF::mabs(d12, d23), w2);
         }
         pair_flux<2>(wL, wR, 2, gam, gm1i, FzA);
         store_bflux2(4, tx0 + ci + N * (ty0 + tj), FzA);
@@ -460,9 +521,9 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
     if (__syncthreads_or(nonphys) && tid == 0) raise_status(&a.sc[0].status, 7);
 }
 
-template <int N>
+template <int N, int NPREV>
 __global__ void __launch_bounds__(PairShape<N>::NT, (N >= 16 ? 4 : 1)) k_stage_pair(StageArgs<float> a, Geom g) {
-    for (int item = blockIdx.x; item < a.n_items; item += gridDim.x) stage_pair_item<N>(a, g, item);
+    for (int item = blockIdx.x; item < a.n_items; item += gridDim.x) stage_pair_item<N, NPREV>(a, g, item);
 }
 
 }  // namespace amrb
