@@ -72,7 +72,7 @@ template <int N, int NPREV>
 amr_status launch_stage_pair_n(amr_forest *f, const StageArgs<float> &a, cudaStream_t st) {
     using Sh = PairShape<N>;
     static bool attr_done = false;
-    const size_t smem = Sh::smem_bytes();
+    const size_t smem = Sh::smem_bytes(NPREV);
     if (!attr_done) {
         CU(cudaFuncSetAttribute(k_stage_pair<N, NPREV>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
         attr_done = true;

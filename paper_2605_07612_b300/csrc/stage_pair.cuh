@@ -9,9 +9,11 @@
 // (128 for T = 16); thread (ip, tj) owns
 // cells (2ip, 2ip+1) of row tj.  The CTA marches k with a ring of
 // primitive variables in shared memory (4 planes: the z face state of the
-// plane above is carried in registers).  One barrier per plane:
-//   [update of plane k-1 | fluxes of plane k | commit of plane k+3] barrier
-// with the face fluxes double-buffered between consecutive planes.  Face
+// plane above is carried in registers).  Per plane k:
+//   [copy of plane k's previous states | fluxes of plane k | commit of plane
+//    k+3] barrier [update of plane k] barrier
+// The previous states travel by cp.async into per-thread shared slots while
+// the fluxes are computed, so the update does not wait on global loads.  Face
 // states (MUSCL with minmod) are formed in the flux phase from the ring: an
 // x-face pair reads three aligned pairs of a row, a y- or z-face pair four.
 // The T x-faces and T y-faces left over at the tile's upper edges are taken
@@ -58,6 +60,15 @@ constexpr int kPairV = 5;   // 3D Euler variables
 __device__ __forceinline__ void l2_prefetch(const void *p, unsigned bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
+
+// 8-byte asynchronous global -> shared copy (cp.async, L1-allocating) and
+// its group commit / wait.
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+    const unsigned d = unsigned(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // Rusanov / Einfeldt flux of a pair of faces with the same normal n
 // (compile-time NRM >= 0, or runtime n when NRM < 0).
@@ -147,7 +158,11 @@ struct PairShape {
         if constexpr (T == 16) return 32 * (row >> 1) + 16 * ((row ^ (row >> 2)) & 1) + c;
         else return row * T + c;
     }
-    static constexpr size_t smem_bytes() { return sizeof(float) * (size_t(R) * V * PL + 2 * size_t(FBUF)); }
+    // ring, one flux buffer, and (nprev > 0) each thread's previous-state
+    // pairs of the plane being updated [nprev][V][NT]
+    static constexpr size_t smem_bytes(int nprev) {
+        return sizeof(float) * (size_t(R) * V * PL + size_t(FBUF)) + sizeof(float2) * size_t(nprev > 0 ? nprev : 0) * V * NT;
+    }
 };
 
 // NPREV >= 0: the number of previous states, fixed at compile time (Heun's two
@@ -160,7 +175,8 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
     constexpr int64_t NC = int64_t(S) * S * S;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float *ring = reinterpret_cast<float *>(smem_raw);         // [R][V][P*P]
-    float *fbuf = ring + Sh::R * V * PL;                        // [2][FBUF]: Fx [V][T][FXP], Fy [V][T+1][T]
+    float *fbuf = ring + Sh::R * V * PL;                        // Fx [V][T][FXP], Fy [V][T+1][T]
+    float2 *stg = reinterpret_cast<float2 *>(fbuf + FBUF);      // [NPREV][V][NT] previous states
 
     const int tid = threadIdx.x;
     const int b = item / Sh::TILES;
@@ -397,22 +413,40 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
     // ---- L2 prefetch, one plane period ahead: the previous states' plane k
     // (read by the update of plane k in the next iteration) and this block's
     // derivative plane k + 5 (loaded into registers two iterations later)
+    // ---- L2 prefetch: the previous states' plane k (copied to shared memory
+    // at the start of the next plane period) and this block's derivative
+    // plane k + 4 (loaded into registers in the next plane period)
     auto l2_ahead = [&](int k) {
         if (tid != NT - 32) return;   // a thread of the last warp (the first two take the edge faces)
         constexpr unsigned PB = unsigned(S) * S * sizeof(float);
         const int64_t blk = int64_t(b) * V * NC;
+        if (k < N) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-            if (q < (NPREV >= 0 ? NPREV : a.nprev))
+            for (int q = 0; q < 4; ++q)
+                if (q < (NPREV >= 0 ? NPREV : a.nprev))
 #pragma unroll
-                for (int v = 0; v < V; ++v) l2_prefetch(a.prev[q] + blk + v * NC + int64_t(k + NG) * S * S, PB);
-        if (k + 5 <= N + 1)
+                    for (int v = 0; v < V; ++v) l2_prefetch(a.prev[q] + blk + v * NC + int64_t(k + NG) * S * S, PB);
+        }
+        if (k + 4 <= N + 1)
 #pragma unroll
-            for (int v = 0; v < V; ++v) l2_prefetch(ub + v * NC + int64_t(k + 5 + NG) * S * S, PB);
+            for (int v = 0; v < V; ++v) l2_prefetch(ub + v * NC + int64_t(k + 4 + NG) * S * S, PB);
     };
 
-    // ---- update of plane k from buffer fb and the z fluxes below / above
+    // ---- previous states of plane k: asynchronous copies of this thread's
+    // pairs into its staging slots, awaited by the update of plane k
+    auto stage_prev = [&](int k) {
+        if constexpr (NPREV > 0) {
+            const int64_t ob = int64_t(b) * V * NC + gofs(tx0 + ci, ty0 + tj, k);
+#pragma unroll
+            for (int q = 0; q < NPREV; ++q)
+#pragma unroll
+                for (int v = 0; v < V; ++v) cp_async8(stg + (q * V + v) * NT + tid, a.prev[q] + ob + v * NC);
+            cp_async_commit();
+        }
+    };
+
     auto update = [&](int k, const float *fb, const float2 *Fzlo, const float2 *Fzhi) {
+        if constexpr (NPREV > 0) cp_async_wait_all();
         const float *Fx = fb, *Fy = fb + V * NFX;
         const int64_t o = gofs(tx0 + ci, ty0 + tj, k);
         const int64_t ob = int64_t(b) * V * NC + o;
@@ -428,10 +462,15 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
             du = PF::fma(PF::sub(y0, y1), i1, du);
             du = PF::fma(PF::sub(Fzlo[v], Fzhi[v]), i2, du);
             float2 acc = PF::sp(0.f);
+            if constexpr (NPREV > 0) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (q < (NPREV >= 0 ? NPREV : a.nprev))
-                    acc = PF::fma(PF::sp(a.wprev[q]), *reinterpret_cast<const float2 *>(a.prev[q] + ob + v * NC), acc);
+                for (int q = 0; q < NPREV; ++q) acc = PF::fma(PF::sp(a.wprev[q]), stg[(q * V + v) * NT + tid], acc);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (q < a.nprev)
+                        acc = PF::fma(PF::sp(a.wprev[q]), *reinterpret_cast<const float2 *>(a.prev[q] + ob + v * NC), acc);
+            }
             U[v] = PF::fma(dte, du, acc);
             *reinterpret_cast<float2 *>(a.out + ob + v * NC) = U[v];
         }
@@ -492,26 +531,23 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
     commit(2);          // into the slot of plane -2
     prefetch(3);
     __syncthreads();
-    l2_ahead(0);
-    fluxes(0, fbuf, FzB);
-    commit(3);          // into the slot of plane -1
-    if (4 <= N + 1) prefetch(4);
-    __syncthreads();
-    for (int k = 1; k < N; ++k) {
-        float *fb_prev = fbuf + ((k - 1) & 1) * FBUF, *fb_cur = fbuf + (k & 1) * FBUF;
-        l2_ahead(k);
-        update(k - 1, fb_prev, FzA, FzB);
-#pragma unroll
-        for (int v = 0; v < V; ++v) FzA[v] = FzB[v];
-        fluxes(k, fb_cur, FzB);
+    // plane k: copy its previous states, compute its x/y fluxes and the z flux
+    // above it, commit plane k+3 into the slot of plane k-1 and load plane
+    // k+4; barrier; update plane k; barrier (flux buffer reused)
+    for (int k = 0; k < N; ++k) {
+        stage_prev(k);
+        l2_ahead(k + 1);
+        fluxes(k, fbuf, FzB);
         if (k + 3 <= N + 1) {
             commit(k + 3);
             if (k + 4 <= N + 1) prefetch(k + 4);
         }
         __syncthreads();
+        update(k, fbuf, FzA, FzB);
+#pragma unroll
+        for (int v = 0; v < V; ++v) FzA[v] = FzB[v];
+        __syncthreads();
     }
-    update(N - 1, fbuf + ((N - 1) & 1) * FBUF, FzA, FzB);
-    __syncthreads();   // shared memory is reused by the CTA's next item
 
     if (a.update_dt) {
         double m = double(vmax);
