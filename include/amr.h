@@ -264,9 +264,11 @@ amr_status amr_flag(amr_forest *f, int s, const amr_flag_params *prm, int8_t *fl
  * when flags is NULL, from amr_flag() on slot 0 after a ghost fill; refine,
  * coarsen (a family only when all of its children are flagged -1), 2:1
  * balance across faces, edges and corners; then, if the mesh changed, moves
- * slot 0's data to the new blocks on the GPU (copy / prolong / restrict) and
- * rebuilds the ghost pattern.  Slot 0's ghosts are filled first.  Other slots
- * are scratch afterwards.  AMR_ECAPACITY leaves mesh and data unchanged.
+ * slot 0's data to the new blocks on the GPU (copy / prolong / restrict),
+ * rebuilds the ghost pattern and sets every instance's dt to the CFL limit of
+ * slot 0 on the new mesh (Sec. 3.2).  Slot 0's ghosts are filled first.
+ * Other slots are scratch afterwards.  AMR_ECAPACITY leaves mesh and data
+ * unchanged.
  * *changed (may be NULL) = 1 when the mesh changed. */
 amr_status amr_flag_and_regrid(amr_forest *f, const amr_flag_params *prm, const int8_t *flags,
                                int *changed, amr_stream stream);

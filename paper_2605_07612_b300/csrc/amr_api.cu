@@ -808,6 +808,9 @@ amr_status amr_flag_and_regrid(amr_forest *f, const amr_flag_params *p, const in
     set_offsets(f);
     ++f->revision;
     if ((r = upload_pattern(f)) != AMR_OK) return r;
+    // the time step of the new mesh: the CFL limit of slot 0 (Sec. 3.2) --
+    // refined blocks have smaller cells than the ones the last stage saw
+    if ((r = dispatch<MaxSpeedFn>(f, 0, st)) != AMR_OK) return r;
     CU(cudaStreamSynchronize(st));
     if (changed) *changed = 1;
     return AMR_OK;

@@ -475,3 +475,51 @@ def test_autotune_keeps_results(case):
     assert fb.sync_status() == amr.AMR_OK
     err = rel_l1(fb.get_state(0), fa.get_state(0).astype(np.float64), spec0).max()
     assert err == 0.0 if choice < 100 else err <= 1e-6, (choice, err)
+
+
+def test_adaptive_sphere_and_shock_fp64_matches_oracle():
+    """Reduced adaptive run: over-pressure sphere and a Mach-3 shock entering
+    through a Dirichlet -x face (Rankine-Hugoniot state), 64^3 base of 16^3
+    blocks, <= 3 levels, regrid from the criterion of Eq. 5 every 10 steps,
+    60 steps.  Both sides flag, adapt and transfer on their own; meshes must
+    agree exactly and the FP64 states to 1e-12 (relative L1)."""
+    sp = synth.MeshSpec(ndim=3, N=16, ng=2, ntrees=(4, 4, 4), periodic=(0, 0, 0), max_level=2,
+                        bc_type=(1, 2, 2, 2, 2, 2))
+    rho2, u2, p2 = synth.normal_shock_state(3.0, sp.gamma)
+    E2 = p2 / (sp.gamma - 1.0) + 0.5 * rho2 * u2 * u2
+    sp.bc_val = tuple(tuple([rho2, rho2 * u2, 0.0, 0.0, E2, 0, 0, 0]) if fc == 0 else tuple([0.0] * 8) for fc in range(6))
+    centre = (0.55, 0.5, 0.45)
+    prm = dict(c_ref=5e-2, c_deref=6.25e-3)
+    om = oracle.Mesh(sp, 0)
+    f = amr.Forest(sp, 0, max_blocks=6000, precision=64)
+    for _ in range(2):                       # initial refinement from the initial state
+        lev, g = om.blocks()
+        u = synth.sphere_and_shock(sp, lev, g, centre, radius=0.15)
+        om.fill_ghosts(u)
+        om = om.adapt(om.lohner_flags(u, **prm))
+        f.set_state(0, u)
+        f.regrid(None, **prm)
+        np.testing.assert_array_equal(f.blocks()[0], om.blocks()[0])
+    lev, g = om.blocks()
+    u = synth.sphere_and_shock(sp, lev, g, centre, radius=0.15)
+    f.set_state(0, u)
+    f.compute_dt(0)
+    u1 = np.zeros_like(u)
+    for block in range(6):
+        for _ in range(10):
+            oracle.heun_step(om, u, u1)
+        f.step(10)
+        assert f.sync_status() == amr.AMR_OK
+        assert rel_l1(f.get_state(0), u, sp).max() <= 1e-12
+        om.fill_ghosts(u)
+        nm = om.adapt(om.lohner_flags(u, **prm))
+        changed = f.regrid(None, **prm)
+        assert changed == (nm.n != om.n or not np.array_equal(nm.blocks()[0], om.blocks()[0])
+                           or not np.array_equal(nm.blocks()[1], om.blocks()[1]))
+        u = om.transfer(u, nm)
+        om = nm
+        u1 = np.zeros_like(u)
+        np.testing.assert_array_equal(f.blocks()[0], om.blocks()[0])
+        np.testing.assert_array_equal(f.blocks()[1], om.blocks()[1])
+    assert len(np.unique(om.blocks()[0])) == 3
+    assert rel_l1(f.get_state(0), u, sp).max() <= 1e-12
