@@ -208,6 +208,54 @@ def heun_step(mesh: Mesh, u0: np.ndarray, u1: np.ndarray, dt: float | None = Non
     return dt
 
 
+def rk_combine(L, u: np.ndarray, dt: float, scheme: str) -> np.ndarray:
+    """One step of an explicit Runge-Kutta method for u' = L(u) (Sec. 3.1
+    lists Heun's method and higher-order SSP and classical schemes):
+      heun  u1 = u + dt L(u);  u+ = (u + u1 + dt L(u1)) / 2            (Eq. 5-6)
+      ssp3  Shu & Osher's three-stage SSP method, in their convex form:
+            u1 = u + dt L(u);  u2 = 3/4 u + 1/4 (u1 + dt L(u1));
+            u+ = 1/3 u + 2/3 (u2 + dt L(u2))
+      rk4   the classical method: k1 = L(u), k2 = L(u + dt/2 k1),
+            k3 = L(u + dt/2 k2), k4 = L(u + dt k3),
+            u+ = u + dt/6 (k1 + 2 k2 + 2 k3 + k4)
+    L is any function of one array; returns the new array."""
+    if scheme == "heun":
+        u1 = u + dt * L(u)
+        return 0.5 * u + 0.5 * (u1 + dt * L(u1))
+    if scheme == "ssp3":
+        u1 = u + dt * L(u)
+        u2 = 0.75 * u + 0.25 * (u1 + dt * L(u1))
+        return u / 3.0 + 2.0 / 3.0 * (u2 + dt * L(u2))
+    if scheme == "rk4":
+        k1 = L(u)
+        k2 = L(u + 0.5 * dt * k1)
+        k3 = L(u + 0.5 * dt * k2)
+        k4 = L(u + dt * k3)
+        return u + dt / 6.0 * (k1 + 2.0 * k2 + 2.0 * k3 + k4)
+    raise ValueError(scheme)
+
+
+def flux_operator(mesh: Mesh, bc_data=None):
+    """L(u): ghost fill, then the flux divergence of Eq. 4 with flux fixing
+    (one stage with no previous states and dt_eff = 1)."""
+    def L(u):
+        mesh.fill_ghosts(u, bc_data)
+        out = np.zeros_like(u)
+        if mesh.stage(u, out, [], [], 1.0):
+            raise FloatingPointError("oracle: non-physical state")
+        return out
+    return L
+
+
+def rk_step(mesh: Mesh, u0: np.ndarray, scheme: str, dt: float | None = None, bc_data=None) -> float:
+    """One time step of `scheme` on u0 in place (interior cells); dt defaults
+    to CFL / max speed of u0 (Sec. 3.2).  Returns the dt used."""
+    if dt is None:
+        dt = mesh.dt(u0)
+    u0[...] = rk_combine(flux_operator(mesh, bc_data), u0, dt, scheme)
+    return dt
+
+
 def run_heun(mesh: Mesh, u0: np.ndarray, nsteps: int, bc_data=None) -> list:
     u1 = np.zeros_like(u0)
     return [heun_step(mesh, u0, u1, bc_data=bc_data) for _ in range(nsteps)]

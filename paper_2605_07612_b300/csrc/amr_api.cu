@@ -362,15 +362,39 @@ struct TransferFn {
     }
 };
 
-amr_status heun_step(amr_forest *f, cudaStream_t st, bool gather) {
+// One time step as a sequence of Eq. 4 sub-steps, each preceded by the ghost
+// fill of the slot it differentiates; the last one updates dt.
+//   Heun (Eq. 5-6):  u1 = u0 + dt L(u0);  u0' = (u0 + u1 + dt L(u1)) / 2
+//   SSP3 (Shu-Osher): u1 = u0 + dt L(u0);  u2 = 3/4 u0 + 1/4 (u1 + dt L(u1));
+//                    u0' = 1/3 u0 + 2/3 (u2 + dt L(u2))
+//   RK4: u1 = u0 + dt/2 L(u0);  u2 = u0 + dt/2 L(u1);  u3 = u0 + dt L(u2);
+//        u0' = u0 + dt/6 (k1 + 2 k2 + 2 k3 + k4) with k1 = 2 (u1 - u0) / dt,
+//        k2 = 2 (u2 - u0) / dt, k3 = (u3 - u0) / dt, k4 = L(u3), i.e.
+//        u0' = -1/3 u0 + 1/3 u1 + 2/3 u2 + 1/3 u3 + dt/6 L(u3)
+int step_slots(int flags) { return (flags & AMR_STEP_RK4) ? 4 : ((flags & AMR_STEP_SSP3) ? 3 : 2); }
+
+amr_status rk_step(amr_forest *f, cudaStream_t st, bool gather, int flags) {
     const int gh = gather ? 1 : 0;
-    amr_stage s1{1, 0, 1, {0, 0, 0, 0}, {1.0, 0, 0, 0}, 1.0, 0, gh};
-    amr_stage s2{0, 1, 2, {0, 1, 0, 0}, {0.5, 0.5, 0, 0}, 0.5, 1, gh};
+    std::vector<amr_stage> seq;
+    if (flags & AMR_STEP_RK4) {
+        seq.push_back({1, 0, 1, {0, 0, 0, 0}, {1.0, 0, 0, 0}, 0.5, 0, gh});
+        seq.push_back({2, 1, 1, {0, 0, 0, 0}, {1.0, 0, 0, 0}, 0.5, 0, gh});
+        seq.push_back({3, 2, 1, {0, 0, 0, 0}, {1.0, 0, 0, 0}, 1.0, 0, gh});
+        seq.push_back({0, 3, 4, {0, 1, 2, 3}, {-1.0 / 3.0, 1.0 / 3.0, 2.0 / 3.0, 1.0 / 3.0}, 1.0 / 6.0, 1, gh});
+    } else if (flags & AMR_STEP_SSP3) {
+        seq.push_back({1, 0, 1, {0, 0, 0, 0}, {1.0, 0, 0, 0}, 1.0, 0, gh});
+        seq.push_back({2, 1, 2, {0, 1, 0, 0}, {0.75, 0.25, 0, 0}, 0.25, 0, gh});
+        seq.push_back({0, 2, 2, {0, 2, 0, 0}, {1.0 / 3.0, 2.0 / 3.0, 0, 0}, 2.0 / 3.0, 1, gh});
+    } else {
+        seq.push_back({1, 0, 1, {0, 0, 0, 0}, {1.0, 0, 0, 0}, 1.0, 0, gh});
+        seq.push_back({0, 1, 2, {0, 1, 0, 0}, {0.5, 0.5, 0, 0}, 0.5, 1, gh});
+    }
     amr_status r;
-    if ((r = dispatch<GhostFn>(f, 0, st, gather)) != AMR_OK) return r;
-    if ((r = dispatch<StageFn>(f, &s1, st)) != AMR_OK) return r;
-    if ((r = dispatch<GhostFn>(f, 1, st, gather)) != AMR_OK) return r;
-    return dispatch<StageFn>(f, &s2, st);
+    for (const amr_stage &s : seq) {
+        if ((r = dispatch<GhostFn>(f, s.s_deriv, st, gather)) != AMR_OK) return r;
+        if ((r = dispatch<StageFn>(f, &s, st)) != AMR_OK) return r;
+    }
+    return AMR_OK;
 }
 
 bool valid_slot(const amr_forest *f, int s) { return s >= 0 && s < f->cfg.n_states; }
@@ -630,7 +654,9 @@ amr_status amr_advance_stage(amr_forest *f, const amr_stage *st, amr_stream stre
 amr_status amr_step(amr_forest *f, int n_steps, int flags, amr_stream stream) {
     if (!f || n_steps < 0) return AMR_EINVAL;
     NEED_DEVICE(f);
-    if (f->cfg.n_states < 2) return fail(f, AMR_EINVAL, "Heun's method needs n_states >= 2");
+    if ((flags & AMR_STEP_SSP3) && (flags & AMR_STEP_RK4)) return fail(f, AMR_EINVAL, "choose one Runge-Kutta scheme");
+    if (f->cfg.n_states < step_slots(flags))
+        return fail(f, AMR_EINVAL, "this Runge-Kutta scheme needs n_states >= %d", step_slots(flags));
     if (f->cfg.n_ghost < 2) return fail(f, AMR_EINVAL, "the Euler stage needs n_ghost >= 2");
     amr_status r = upload_pattern(f);
     if (r != AMR_OK) return r;
@@ -638,7 +664,7 @@ amr_status amr_step(amr_forest *f, int n_steps, int flags, amr_stream stream) {
     const bool gather = (flags & AMR_STEP_GATHER) != 0;
     if (!(flags & AMR_STEP_GRAPH)) {
         for (int i = 0; i < n_steps; ++i)
-            if ((r = heun_step(f, st, gather)) != AMR_OK) return r;
+            if ((r = rk_step(f, st, gather, flags)) != AMR_OK) return r;
         return AMR_OK;
     }
     if (!f->gexec || f->graph_rev != f->revision || f->graph_flags != flags) {
@@ -651,7 +677,7 @@ amr_status amr_step(amr_forest *f, int n_steps, int flags, amr_stream stream) {
         CU(cudaStreamSynchronize(st));
         const int64_t before = f->launches;
         CU(cudaStreamBeginCapture(f->cap_stream, cudaStreamCaptureModeThreadLocal));
-        r = heun_step(f, f->cap_stream, gather);
+        r = rk_step(f, f->cap_stream, gather, flags);
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamEndCapture(f->cap_stream, &graph);
         if (r != AMR_OK) {
