@@ -141,6 +141,8 @@ typedef struct {
                               (Shu-Osher form) instead of Heun; n_states >= 3 */
 #define AMR_STEP_RK4 8     /* classical four-stage RK instead of Heun;
                               n_states >= 4 */
+#define AMR_STEP_SSP43 16  /* optimal four-stage, third-order SSP RK instead
+                              of Heun; n_states >= 3 */
 
 /* Refinement-criterion constants of Eq. 5 (Sec. 3.3).  The criterion is
  * evaluated on density and pressure; a cell's value is the larger one. */
@@ -249,6 +251,8 @@ amr_status amr_advance_stage(amr_forest *f, const amr_stage *st, amr_stream stre
  * a sub-step of Eq. 4 (L = flux divergence with flux fixing):
  *   SSP3: u1 = u0 + dt L(u0); u2 = 3/4 u0 + 1/4 (u1 + dt L(u1));
  *         u0 <- 1/3 u0 + 2/3 (u2 + dt L(u2))                    (slots 1, 2)
+ *   SSP43: u1 = u0 + dt/2 L(u0); u2 = u1 + dt/2 L(u1);
+ *         u1 <- 2/3 u0 + 1/3 u2 + dt/6 L(u2); u0 <- u1 + dt/2 L(u1) (slots 1, 2)
  *   RK4:  u1 = u0 + dt/2 L(u0); u2 = u0 + dt/2 L(u1); u3 = u0 + dt L(u2);
  *         u0 <- -1/3 u0 + 1/3 u1 + 2/3 u2 + 1/3 u3 + dt/6 L(u3)  (slots 1-3),
  * the last form being u0 + dt/6 (k1 + 2 k2 + 2 k3 + k4) written with the
@@ -257,8 +261,8 @@ amr_status amr_advance_stage(amr_forest *f, const amr_stage *st, amr_stream stre
  * replays it (re-captured after a regrid or a change of flags);
  * AMR_STEP_GATHER lets the stage kernel read same-level halos directly (the
  * ghost cells of the state are not all refreshed; amr_fill_ghosts() refills
- * them).  The dt must be set (amr_compute_dt).  Errors: AMR_EINVAL (both
- * scheme flags, or too few state slots for the scheme). */
+ * them).  The dt must be set (amr_compute_dt).  Errors: AMR_EINVAL (more
+ * than one scheme flag, or too few state slots for the scheme). */
 amr_status amr_step(amr_forest *f, int n_steps, int flags, amr_stream stream);
 
 /* Integral of every conserved variable over the leaves of slot s, summed in

@@ -42,7 +42,8 @@ class Params(C.Structure):
                 ("ntrees", C.c_int * 3), ("periodic", C.c_int * 3),
                 ("lo", C.c_double * 3), ("len", C.c_double * 3),
                 ("max_level", C.c_int), ("gamma", C.c_double), ("cfl", C.c_double),
-                ("bc_type", C.c_int * 6), ("bc_val", (C.c_double * 8) * 6)]
+                ("bc_type", C.c_int * 6), ("bc_val", (C.c_double * 8) * 6),
+                ("limiter", C.c_int), ("flux", C.c_int)]
 
 
 def _lib_handle():
@@ -70,6 +71,10 @@ def _lib_handle():
             lib.orc_stage.argtypes = [vp, vp, vp, C.c_int, vp, vp, C.c_double]
             lib.orc_max_speed.restype = C.c_double
             lib.orc_max_speed.argtypes = [vp, vp]
+            lib.orc_limited_slope.restype = C.c_double
+            lib.orc_limited_slope.argtypes = [C.c_int, C.c_double, C.c_double]
+            lib.orc_face_flux.restype = None
+            lib.orc_face_flux.argtypes = [P(Params), C.c_int, vp, vp, vp]
             lib.orc_conserved.argtypes = [vp, vp, vp]
             lib.orc_lohner_flags.argtypes = [vp, vp, C.c_double, C.c_double, C.c_double, C.c_double, vp]
             lib.orc_transfer.restype = C.c_int
@@ -98,7 +103,27 @@ def params_from_spec(spec) -> Params:
         p.bc_type[f] = int(spec.bc_type[f])
         for v in range(8):
             p.bc_val[f][v] = float(spec.bc_val[f][v]) if v < len(spec.bc_val[f]) else 0.0
+    p.limiter = int(getattr(spec, "limiter", 0))
+    p.flux = int(getattr(spec, "flux", 0))
     return p
+
+
+def limited_slope(limiter: int, a: float, b: float) -> float:
+    """The MUSCL slope limiter (0 minmod, 1 MC, 2 van Leer) on one pair of
+    one-sided differences."""
+    return float(_lib_handle().orc_limited_slope(int(limiter), float(a), float(b)))
+
+
+def face_flux(spec, n: int, wL, wR) -> np.ndarray:
+    """The numerical flux (spec.flux: 0 Rusanov, 1 HLL) along dimension n
+    between primitive states wL and wR."""
+    V = spec.ndim + 2
+    a = np.ascontiguousarray(wL, dtype=np.float64)
+    b = np.ascontiguousarray(wR, dtype=np.float64)
+    F = np.zeros(V)
+    p = params_from_spec(spec)
+    _lib_handle().orc_face_flux(C.byref(p), int(n), a.ctypes.data, b.ctypes.data, F.ctypes.data)
+    return F
 
 
 def set_threads(n: int) -> None:
@@ -215,6 +240,9 @@ def rk_combine(L, u: np.ndarray, dt: float, scheme: str) -> np.ndarray:
       ssp3  Shu & Osher's three-stage SSP method, in their convex form:
             u1 = u + dt L(u);  u2 = 3/4 u + 1/4 (u1 + dt L(u1));
             u+ = 1/3 u + 2/3 (u2 + dt L(u2))
+      ssp43 the optimal four-stage, third-order SSP method (Spiteri & Ruuth):
+            u1 = u + dt/2 L(u);  u2 = u1 + dt/2 L(u1);
+            u3 = 2/3 u + 1/3 (u2 + dt/2 L(u2));  u+ = u3 + dt/2 L(u3)
       rk4   the classical method: k1 = L(u), k2 = L(u + dt/2 k1),
             k3 = L(u + dt/2 k2), k4 = L(u + dt k3),
             u+ = u + dt/6 (k1 + 2 k2 + 2 k3 + k4)
@@ -226,6 +254,11 @@ def rk_combine(L, u: np.ndarray, dt: float, scheme: str) -> np.ndarray:
         u1 = u + dt * L(u)
         u2 = 0.75 * u + 0.25 * (u1 + dt * L(u1))
         return u / 3.0 + 2.0 / 3.0 * (u2 + dt * L(u2))
+    if scheme == "ssp43":
+        u1 = u + 0.5 * dt * L(u)
+        u2 = u1 + 0.5 * dt * L(u1)
+        u3 = 2.0 / 3.0 * u + 1.0 / 3.0 * (u2 + 0.5 * dt * L(u2))
+        return u3 + 0.5 * dt * L(u3)
     if scheme == "rk4":
         k1 = L(u)
         k2 = L(u + 0.5 * dt * k1)

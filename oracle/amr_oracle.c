@@ -53,6 +53,8 @@ typedef struct {
     double gamma, cfl;
     int bc_type[6];        /* 0 periodic/none, 1 Dirichlet, 2 Neumann, 3 Dirichlet from bc_data */
     double bc_val[6][8];
+    int limiter;           /* MUSCL slope limiter (Sec. 3.2 list): 0 minmod, 1 MC, 2 van Leer */
+    int flux;              /* 0 Rusanov, 1 HLL (Sec. 3.2 list), both with Einfeldt speeds */
 } orc_params;
 
 enum { BC_NONE = 0, BC_DIRICHLET = 1, BC_NEUMANN = 2, BC_DATA = 3 };
@@ -745,12 +747,70 @@ static void rusanov(int D, double gam, int n, const double *wL, const double *wR
     for (int v = 0; v < D + 2; v++) F[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * a * (UR[v] - UL[v]);
 }
 
+/* HLL flux (Harten, Lax and van Leer) with the same Einfeldt estimates: the
+ * smallest and largest signal speeds are u_roe -/+ d; with
+ *   sL = min(u_roe - d, 0),  sR = max(u_roe + d, 0):
+ *   F = (sR F(wL) - sL F(wR) + sL sR (U_R - U_L)) / (sR - sL),
+ * which is F(wL) when all waves move right and F(wR) when all move left. */
+static void hll(int D, double gam, int n, const double *wL, const double *wR, double *F)
+{
+    double FL[5], FR[5], UL[5], UR[5];
+    phys_flux(D, gam, n, wL, FL);
+    phys_flux(D, gam, n, wR, FR);
+    to_conservative(D, gam, wL, UL);
+    to_conservative(D, gam, wR, UR);
+    double sqL = sqrt(wL[0]), sqR = sqrt(wR[0]);
+    double cL2 = gam * wL[D + 1] / wL[0], cR2 = gam * wR[D + 1] / wR[0];
+    double uL = wL[1 + n], uR = wR[1 + n];
+    double inv = 1.0 / (sqL + sqR);
+    double uroe = (sqL * uL + sqR * uR) * inv;
+    double du = uR - uL;
+    double d = sqrt((sqL * cL2 + sqR * cR2) * inv + 0.5 * sqL * sqR * inv * inv * du * du);
+    double sL = uroe - d, sR = uroe + d;
+    if (sL > 0.0) sL = 0.0;
+    if (sR < 0.0) sR = 0.0;
+    for (int v = 0; v < D + 2; v++) F[v] = (sR * FL[v] - sL * FR[v] + sL * sR * (UR[v] - UL[v])) / (sR - sL);
+}
+
+static void face_flux(const orc_params *p, int n, const double *wL, const double *wR, double *F)
+{
+    if (p->flux == 1) hll(p->ndim, p->gamma, n, wL, wR, F);
+    else rusanov(p->ndim, p->gamma, n, wL, wR, F);
+}
+
+/* Generalized minmod of the paper's Eq. 1: 0 when a and b differ in sign,
+ * else sign(a) min(|theta a|, |theta b|, |a + b| / 2). */
+static double gminmod(double a, double b, double theta)
+{
+    if (!((a > 0.0 && b > 0.0) || (a < 0.0 && b < 0.0))) return 0.0;
+    double m = fabs(theta * a);
+    if (fabs(theta * b) < m) m = fabs(theta * b);
+    if (fabs(a + b) / 2.0 < m) m = fabs(a + b) / 2.0;
+    return a > 0.0 ? m : -m;
+}
+
+/* Limited slope of a cell from its one-sided differences a (left) and b
+ * (right), for the MUSCL face values w -/+ slope/2 (Sec. 3.2):
+ *   0 minmod (Eq. 1, theta = 1); 1 monotonized central (Eq. 1, theta = 2);
+ *   2 van Leer's harmonic mean 2ab / (a + b) when ab > 0, else 0. */
+static double limited_slope(int lim, double a, double b)
+{
+    if (lim == 1) return gminmod(a, b, 2.0);
+    if (lim == 2) return (a * b > 0.0) ? 2.0 * a * b / (a + b) : 0.0;
+    return minmod(a, b);
+}
+
+/* test hooks: the limiter and the face flux on given values */
+double orc_limited_slope(int lim, double a, double b) { return limited_slope(lim, a, b); }
+void orc_face_flux(const orc_params *p, int n, const double *wL, const double *wR, double *F) { face_flux(p, n, wL, wR, F); }
+
 /* ------------------------------------------------------------------------ */
 /* One forward-Euler sub-step of Eq. 4 (Sec. 3.1) with the finite-volume      */
 /* steps of Sec. 3.2:                                                        */
 /*   uo = dt_eff * F(ud) + sum_i w_i up_i                                    */
-/* F: primitives on interior + face ghosts; MUSCL face values with minmod;   */
-/* Rusanov/Einfeldt fluxes; divergence.  Then flux fixing at refinement      */
+/* F: primitives on interior + face ghosts; MUSCL face values with the      */
+/* limiter; Rusanov or HLL fluxes with Einfeldt speeds; divergence.  Then    */
+/* flux fixing at refinement                                                 */
 /* boundaries (Sec. 2.6): the coarse cells next to a face shared with finer  */
 /* blocks get dt_eff/dx (F_coarse - mean F_fine) with the face's sign.        */
 /* ud must have its face ghosts filled.  uo may alias one of up (each output  */
@@ -813,13 +873,13 @@ int orc_stage(const orc_mesh *m, const double *ud, double *uo, int nprev,
                             int64_t c = (int64_t)(x[0] + p->ng) + S * ((int64_t)(x[1] + p->ng) + (D == 3 ? S * (int64_t)(x[2] + p->ng) : 0));
                             for (int v = 0; v < V; v++) dst[q][v] = wp[(int64_t)v * nc + c];
                         }
-                        /* MUSCL reconstruction of primitives with minmod (Sec. 3.2) */
+                        /* MUSCL reconstruction of primitives with the limiter (Sec. 3.2) */
                         for (int v = 0; v < V; v++) {
-                            wL[v] = wm1[v] + 0.5 * minmod(wm1[v] - wm2[v], w0[v] - wm1[v]);
-                            wR[v] = w0[v] - 0.5 * minmod(w0[v] - wm1[v], w1[v] - w0[v]);
+                            wL[v] = wm1[v] + 0.5 * limited_slope(p->limiter, wm1[v] - wm2[v], w0[v] - wm1[v]);
+                            wR[v] = w0[v] - 0.5 * limited_slope(p->limiter, w0[v] - wm1[v], w1[v] - w0[v]);
                         }
                         if (!(wL[0] > 0.0) || !(wL[D + 1] > 0.0) || !(wR[0] > 0.0) || !(wR[D + 1] > 0.0)) bad = 1;
-                        rusanov(D, gam, n, wL, wR, F);
+                        face_flux(p, n, wL, wR, F);
                         int64_t tt = t0 + (int64_t)N * t1;
                         for (int v = 0; v < V; v++) fl[((int64_t)n * V + v) * nfl + fp + (N + 1) * tt] = F[v];
                         if (fp == 0 || fp == N) {

@@ -18,7 +18,7 @@ from . import build as _build
 
 AMR_OK, AMR_EINVAL, AMR_ENOMEM, AMR_ECAPACITY, AMR_ECUDA = 0, 1, 2, 3, 4
 AMR_ETIMEOUT, AMR_EBOUNDS, AMR_ENONPHYS, AMR_ESTATE = 5, 6, 7, 8
-AMR_STEP_GRAPH, AMR_STEP_GATHER, AMR_STEP_SSP3, AMR_STEP_RK4 = 1, 2, 4, 8
+AMR_STEP_GRAPH, AMR_STEP_GATHER, AMR_STEP_SSP3, AMR_STEP_RK4, AMR_STEP_SSP43 = 1, 2, 4, 8, 16
 STATUS_NAMES = {0: "AMR_OK", 1: "AMR_EINVAL", 2: "AMR_ENOMEM", 3: "AMR_ECAPACITY", 4: "AMR_ECUDA",
                 5: "AMR_ETIMEOUT", 6: "AMR_EBOUNDS", 7: "AMR_ENONPHYS", 8: "AMR_ESTATE"}
 KIND_SRL, KIND_F2C, KIND_BC, KIND_C2F = 0, 1, 2, 3
@@ -335,9 +335,9 @@ class Forest:
         self._check(self.lib.amr_advance_stage(self.h, C.byref(st), _stream_ptr(stream)), "amr_advance_stage")
 
     def step(self, n_steps=1, use_graph=False, gather=False, stream=None, scheme="heun"):
-        """n_steps time steps; scheme 'heun' (2 slots), 'ssp3' (3) or 'rk4' (4)."""
+        """n_steps time steps; scheme 'heun' (2 slots), 'ssp3' (3), 'ssp43' (3) or 'rk4' (4)."""
         flags = (AMR_STEP_GRAPH if use_graph else 0) | (AMR_STEP_GATHER if gather else 0)
-        flags |= {"heun": 0, "ssp3": AMR_STEP_SSP3, "rk4": AMR_STEP_RK4}[scheme]
+        flags |= {"heun": 0, "ssp3": AMR_STEP_SSP3, "ssp43": AMR_STEP_SSP43, "rk4": AMR_STEP_RK4}[scheme]
         self._check(self.lib.amr_step(self.h, int(n_steps), flags, _stream_ptr(stream)), "amr_step")
 
     def conserved(self, s, stream=None) -> np.ndarray:

@@ -367,11 +367,14 @@ struct TransferFn {
 //   Heun (Eq. 5-6):  u1 = u0 + dt L(u0);  u0' = (u0 + u1 + dt L(u1)) / 2
 //   SSP3 (Shu-Osher): u1 = u0 + dt L(u0);  u2 = 3/4 u0 + 1/4 (u1 + dt L(u1));
 //                    u0' = 1/3 u0 + 2/3 (u2 + dt L(u2))
+//   SSP43 (four stages, third order): u1 = u0 + dt/2 L(u0);
+//        u2 = u1 + dt/2 L(u1);  u3 = 2/3 u0 + 1/3 u2 + dt/6 L(u2);
+//        u0' = u3 + dt/2 L(u3)   (u3 stored in slot 1)
 //   RK4: u1 = u0 + dt/2 L(u0);  u2 = u0 + dt/2 L(u1);  u3 = u0 + dt L(u2);
 //        u0' = u0 + dt/6 (k1 + 2 k2 + 2 k3 + k4) with k1 = 2 (u1 - u0) / dt,
 //        k2 = 2 (u2 - u0) / dt, k3 = (u3 - u0) / dt, k4 = L(u3), i.e.
 //        u0' = -1/3 u0 + 1/3 u1 + 2/3 u2 + 1/3 u3 + dt/6 L(u3)
-int step_slots(int flags) { return (flags & AMR_STEP_RK4) ? 4 : ((flags & AMR_STEP_SSP3) ? 3 : 2); }
+int step_slots(int flags) { return (flags & AMR_STEP_RK4) ? 4 : ((flags & (AMR_STEP_SSP3 | AMR_STEP_SSP43)) ? 3 : 2); }
 
 amr_status rk_step(amr_forest *f, cudaStream_t st, bool gather, int flags) {
     const int gh = gather ? 1 : 0;
@@ -381,6 +384,11 @@ amr_status rk_step(amr_forest *f, cudaStream_t st, bool gather, int flags) {
         seq.push_back({2, 1, 1, {0, 0, 0, 0}, {1.0, 0, 0, 0}, 0.5, 0, gh});
         seq.push_back({3, 2, 1, {0, 0, 0, 0}, {1.0, 0, 0, 0}, 1.0, 0, gh});
         seq.push_back({0, 3, 4, {0, 1, 2, 3}, {-1.0 / 3.0, 1.0 / 3.0, 2.0 / 3.0, 1.0 / 3.0}, 1.0 / 6.0, 1, gh});
+    } else if (flags & AMR_STEP_SSP43) {
+        seq.push_back({1, 0, 1, {0, 0, 0, 0}, {1.0, 0, 0, 0}, 0.5, 0, gh});
+        seq.push_back({2, 1, 1, {1, 0, 0, 0}, {1.0, 0, 0, 0}, 0.5, 0, gh});
+        seq.push_back({1, 2, 2, {0, 2, 0, 0}, {2.0 / 3.0, 1.0 / 3.0, 0, 0}, 1.0 / 6.0, 0, gh});
+        seq.push_back({0, 1, 1, {1, 0, 0, 0}, {1.0, 0, 0, 0}, 0.5, 1, gh});
     } else if (flags & AMR_STEP_SSP3) {
         seq.push_back({1, 0, 1, {0, 0, 0, 0}, {1.0, 0, 0, 0}, 1.0, 0, gh});
         seq.push_back({2, 1, 2, {0, 1, 0, 0}, {0.75, 0.25, 0, 0}, 0.25, 0, gh});
@@ -654,7 +662,8 @@ amr_status amr_advance_stage(amr_forest *f, const amr_stage *st, amr_stream stre
 amr_status amr_step(amr_forest *f, int n_steps, int flags, amr_stream stream) {
     if (!f || n_steps < 0) return AMR_EINVAL;
     NEED_DEVICE(f);
-    if ((flags & AMR_STEP_SSP3) && (flags & AMR_STEP_RK4)) return fail(f, AMR_EINVAL, "choose one Runge-Kutta scheme");
+    const int schemes = flags & (AMR_STEP_SSP3 | AMR_STEP_RK4 | AMR_STEP_SSP43);
+    if (schemes & (schemes - 1)) return fail(f, AMR_EINVAL, "choose one Runge-Kutta scheme");
     if (f->cfg.n_states < step_slots(flags))
         return fail(f, AMR_EINVAL, "this Runge-Kutta scheme needs n_states >= %d", step_slots(flags));
     if (f->cfg.n_ghost < 2) return fail(f, AMR_EINVAL, "the Euler stage needs n_ghost >= 2");

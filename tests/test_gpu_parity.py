@@ -525,10 +525,10 @@ def test_adaptive_sphere_and_shock_fp64_matches_oracle():
     assert rel_l1(f.get_state(0), u, sp).max() <= 1e-12
 
 
-SLOTS = {"ssp3": 3, "rk4": 4}
+SLOTS = {"ssp3": 3, "ssp43": 3, "rk4": 4}
 
 
-@pytest.mark.parametrize("scheme", ["ssp3", "rk4"])
+@pytest.mark.parametrize("scheme", ["ssp3", "ssp43", "rk4"])
 @pytest.mark.parametrize("dim", [2, 3])
 def test_rk_schemes_fp64_match_oracle(scheme, dim):
     """SSP-RK3 and classical RK4 steps (stages as Eq. 4 sub-steps on the GPU,
@@ -552,7 +552,7 @@ def test_rk_schemes_fp64_match_oracle(scheme, dim):
     assert rel_l1(f.get_state(0), ref, sp).max() <= 1e-12
 
 
-@pytest.mark.parametrize("scheme", ["ssp3", "rk4"])
+@pytest.mark.parametrize("scheme", ["ssp3", "ssp43", "rk4"])
 def test_rk_schemes_fp32_pair_kernel(scheme):
     """The same schemes through the FP32 pair kernel (gathered halos, CUDA
     graph) on a uniform 3D mesh of 16^3 blocks: relative L1 <= 1e-5 after 20

@@ -204,7 +204,7 @@ def test_uniform_refined_equals_single_level():
 
 # ---------------------------------------------------- P5: shock tube --
 
-def sod_l1(ncell, axis=0, ndim=2, t_end=0.2, fixed_dt=None):
+def sod_l1(ncell, axis=0, ndim=2, t_end=0.2, fixed_dt=None, limiter=0, flux=0):
     n_t = ncell // 16
     if ndim == 2:
         ntrees = [1, 1, 1]
@@ -222,6 +222,7 @@ def sod_l1(ncell, axis=0, ndim=2, t_end=0.2, fixed_dt=None):
     sp.periodic = tuple(per)
     sp.length = tuple(1.0 if d == axis else 16.0 / ncell for d in range(3))
     sp.bc_type = tuple(bct)
+    sp.limiter, sp.flux = limiter, flux
     m = oracle.Mesh(sp, 0)
     lev, g = m.blocks()
     u = synth.shock_tube(sp, lev, g, axis=axis)
@@ -233,17 +234,26 @@ def sod_l1(ncell, axis=0, ndim=2, t_end=0.2, fixed_dt=None):
     return np.abs(rho - exact).mean(), rho, X[axis]
 
 
-def test_sod_against_exact_riemann():
+@pytest.mark.parametrize("limiter,flux", [(0, 0), (2, 1), (1, 1)])
+def test_sod_against_exact_riemann(limiter, flux):
+    """Sod's tube against the exact Riemann solution for minmod + Rusanov,
+    van Leer + HLL and MC + HLL."""
     errs = []
     for n in (128, 256, 512):
-        e, rho, x = sod_l1(n)
+        e, rho, x = sod_l1(n, limiter=limiter, flux=flux)
         errs.append(e)
         # y-invariance: every row identical
         r = rho.reshape(rho.shape[0], 16, 16)
         assert np.all(r == r[:, :1, :])
     assert errs[-1] < 1e-2
     orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
-    assert min(orders) >= 0.6, orders
+    # discontinuities bound the order below one (about m / (m + 1) at a
+    # contact for an m-th order scheme)
+    assert min(orders) >= 0.55 and sum(orders) / 2 >= 0.75, orders
+    if (limiter, flux) != (0, 0):
+        # less dissipative than minmod + Rusanov at every resolution
+        base = [sod_l1(n)[0] for n in (128, 256, 512)]
+        assert all(e < b for e, b in zip(errs, base)), (errs, base)
 
 
 def test_shock_tube_axis_permutation_3d():
@@ -264,10 +274,14 @@ def test_shock_tube_axis_permutation_3d():
 
 # ---------------------------------------------- P7: smooth solution order --
 
-def test_density_wave_second_order():
+@pytest.mark.parametrize("limiter,flux", [(0, 0), (2, 0), (1, 1)])
+def test_density_wave_second_order(limiter, flux):
+    """Second-order convergence on a smooth exact solution for minmod,
+    van Leer (the paper reports close to second order in L1 with it) and MC
+    with HLL."""
     errs = []
     for ntr in (2, 4, 8):
-        sp = synth.MeshSpec(ndim=2, N=16, ng=2, ntrees=(ntr, ntr, 1), max_level=0, cfl=0.4)
+        sp = synth.MeshSpec(ndim=2, N=16, ng=2, ntrees=(ntr, ntr, 1), max_level=0, cfl=0.4, limiter=limiter, flux=flux)
         m = oracle.Mesh(sp, 0)
         lev, g = m.blocks()
         u = synth.density_wave(sp, lev, g)
@@ -334,15 +348,19 @@ def test_normal_shock_state_rankine_hugoniot(mach):
         assert abs(rho2 - 240.0 / 42.0) < 1e-12   # (g+1) M^2 / ((g-1) M^2 + 2) at M = 10
 
 
-@pytest.mark.parametrize("scheme,order", [("heun", 2), ("ssp3", 3), ("rk4", 4)])
+@pytest.mark.parametrize("scheme,order", [("heun", 2), ("ssp3", 3), ("ssp43", 3), ("rk4", 4)])
 def test_rk_schemes_stability_function_and_order(scheme, order):
-    """On y' = lambda y one step multiplies by the truncated exponential
-    sum_{k <= order} z^k / k! (z = lambda dt) -- true of Heun, SSP-RK3 and
-    classical RK4 -- and on a rotation the global error falls as dt^order."""
+    """On y' = lambda y one step multiplies by the stability polynomial: the
+    truncated exponential sum_{k <= s} z^k / k! (z = lambda dt) for the
+    s-stage, order-s methods (Heun, SSP-RK3, classical RK4), and
+    1 + z + z^2/2 + z^3/6 + z^4/48 for the four-stage third-order SSP method;
+    on a rotation the global error falls as dt^order."""
     import math
     for z in (-0.3, 0.7, -2.0, 1.3):
         got = oracle.rk_combine(lambda y: z * y, np.array([1.0]), 1.0, scheme)[0]
         want = sum(z ** k / math.factorial(k) for k in range(order + 1))
+        if scheme == "ssp43":
+            want += z ** 4 / 48.0
         assert abs(got - want) <= 1e-14 * max(1.0, abs(want)), (z, got, want)
     A = np.array([[0.0, 1.0], [-1.0, 0.0]])
     exact = np.array([np.cos(1.0), -np.sin(1.0)])
@@ -374,3 +392,54 @@ def test_rk_step_on_mesh_matches_heun_step():
     A = a.reshape(-1, sp.nvar, S, S)[:, :, sl, sl]
     B = b.reshape(-1, sp.nvar, S, S)[:, :, sl, sl]
     assert np.abs(A - B).max() <= 1e-14 * np.abs(A).max()
+
+
+@pytest.mark.parametrize("lim", [0, 1, 2])
+def test_slope_limiters_tvd_region_and_fixed_points(lim):
+    """The MUSCL limiters as functions phi(r) = slope / a of r = b / a:
+    symmetric in (a, b), zero when a and b differ in sign, inside Sweby's
+    second-order TVD region (min(r, 1) <= phi(r) <= min(2r, 2) for r > 0),
+    phi(1) = 1 (linear data reproduced), and their limits for large r:
+    minmod 1, MC 2, van Leer 2."""
+    rng = np.random.default_rng(11)
+    for _ in range(400):
+        a, b = rng.normal(0, 1, 2) * 10.0 ** rng.uniform(-3, 3, 2)
+        s1, s2 = oracle.limited_slope(lim, a, b), oracle.limited_slope(lim, b, a)
+        assert s1 == pytest.approx(s2, rel=1e-15, abs=0.0)
+        if a * b <= 0.0:
+            assert s1 == 0.0
+        else:
+            r = b / a
+            phi = s1 / a
+            assert min(r, 1.0) * (1 - 1e-14) <= phi <= min(2 * r, 2.0) * (1 + 1e-14), (a, b, phi)
+    assert oracle.limited_slope(lim, 0.3, 0.3) == 0.3
+    big = oracle.limited_slope(lim, 1.0, 1e12)
+    assert big == pytest.approx({0: 1.0, 1: 2.0, 2: 2.0}[lim], rel=1e-9)
+
+
+def test_hll_flux_consistency_and_upwinding():
+    """HLL with Einfeldt bounds: F(w, w) is the physical flux; when every
+    signal moves right (supersonic to the right) the flux is F(wL) exactly,
+    to the left F(wR); Rusanov adds dissipation there and does not upwind."""
+    sp = synth.MeshSpec(ndim=3, flux=1)
+    rus = synth.MeshSpec(ndim=3, flux=0)
+    g = sp.gamma
+    def phys(w, n):
+        r, v, p = w[0], np.asarray(w[1:4]), w[4]
+        E = p / (g - 1) + 0.5 * r * v @ v
+        F = np.zeros(5)
+        F[0] = r * v[n]
+        F[1:4] = r * v[n] * v
+        F[1 + n] += p
+        F[4] = (E + p) * v[n]
+        return F
+    w = np.array([1.3, 0.2, -0.1, 0.4, 2.0])
+    for n in range(3):
+        np.testing.assert_allclose(oracle.face_flux(sp, n, w, w), phys(w, n), rtol=1e-14, atol=1e-14)
+    wL = np.array([1.0, 4.0, 0.1, 0.0, 1.0])     # Mach > 3 to the right
+    wR = np.array([0.8, 3.6, 0.0, 0.2, 0.9])
+    np.testing.assert_allclose(oracle.face_flux(sp, 0, wL, wR), phys(wL, 0), rtol=1e-14, atol=1e-14)
+    wLm = wL * np.array([1, -1, 1, 1, 1])
+    wRm = wR * np.array([1, -1, 1, 1, 1])
+    np.testing.assert_allclose(oracle.face_flux(sp, 0, wRm, wLm), phys(wLm, 0), rtol=1e-14, atol=1e-14)
+    assert np.abs(oracle.face_flux(rus, 0, wL, wR) - phys(wL, 0)).max() > 1e-3
