@@ -272,6 +272,16 @@ def run_ours(args, rank, world, dist):
             del fr
             torch.cuda.empty_cache()
         extras["rk_schemes"] = rk
+        # van Leer slopes + HLL flux (the paper's other 2-ghost limiter and flux;
+        # the per-cell kernel runs these)
+        sp_vl = workload_spec(16)
+        sp_vl.limiter, sp_vl.flux = 2, 1
+        fv = make(sp_vl, 32)
+        fv.autotune(stream=stream)
+        msv, _ = time_steps(fv, args.steps, args.warmup, True, True)
+        extras["vanleer_hll"] = {"value": 2.0 * cells * args.steps * world / (msv * 1e-3), "ms_per_step": msv / args.steps}
+        del fv
+        torch.cuda.empty_cache()
         extras["batched_2d"] = run_batched(args, amr, torch, stream, barrier, world)
 
     line = {

@@ -101,7 +101,20 @@ typedef struct {
     int host_only;         /* 1: mesh and ghost pattern only -- no device memory
                               is touched; calls on block data return AMR_ESTATE
                               and amr_flag_and_regrid needs explicit flags */
+    int limiter;           /* amr_limiter: MUSCL slope limiter (Sec. 3.2) */
+    int flux;              /* amr_flux: numerical flux (Sec. 3.2) */
 } amr_config;
+
+/* MUSCL slope limiters of Sec. 3.2 that need two ghost layers.  The slope
+ * of a cell from its one-sided differences a, b: minmod = Eq. 1 with
+ * theta = 1; MC (monotonized central) = Eq. 1 with theta = 2; van Leer =
+ * 2ab / (a + b) when ab > 0, else 0.  Face values are w -/+ slope / 2. */
+typedef enum { AMR_LIM_MINMOD = 0, AMR_LIM_MC = 1, AMR_LIM_VANLEER = 2 } amr_limiter;
+
+/* Numerical fluxes of Sec. 3.2, both with Einfeldt's signal speeds
+ * u_roe -/+ d (Sec. 3.5): Rusanov (local Lax-Friedrichs, a = |u_roe| + d)
+ * and HLL (Harten, Lax and van Leer). */
+typedef enum { AMR_FLUX_RUSANOV = 0, AMR_FLUX_HLL = 1 } amr_flux;
 
 /* One canonical ghost-pattern entry: one per (receiving block, face), and one
  * per fine source block for F2C.  face = direction from dst towards src;
@@ -164,8 +177,8 @@ amr_status amr_create_forest(const amr_config *cfg, int init_level, amr_forest *
  * at once -- one kernel launch per phase sweeps every block of every
  * instance.  Each instance keeps its own domain, brick, periodicity,
  * max_level, boundaries, CFL number and time step; ndim, block_n, n_ghost,
- * precision, n_states, gamma, host_only and the allocation hook must be the
- * same for all.  Capacity is the sum of the instances' max_blocks; each
+ * precision, n_states, gamma, limiter, flux, host_only and the allocation
+ * hook must be the same for all.  Capacity is the sum of the instances' max_blocks; each
  * instance is also held to its own max_blocks on regrid.  amr_create_forest
  * is the n = 1 case.  Errors as amr_create_forest. */
 amr_status amr_create_batch(const amr_config *cfgs, const int *init_levels, int n, amr_forest **out);

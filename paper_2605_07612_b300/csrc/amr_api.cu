@@ -134,6 +134,8 @@ amr_status validate(const amr_config *c, std::string &why) {
     if (c->max_level < 0 || c->max_level >= kMaxLevels) return bad("max_level must be 0..12");
     if (c->max_blocks < 1 || c->n_states < 1) return bad("max_blocks and n_states must be >= 1");
     if (c->precision != 32 && c->precision != 64) return bad("precision must be 32 or 64");
+    if (c->limiter < AMR_LIM_MINMOD || c->limiter > AMR_LIM_VANLEER) return bad("unknown limiter");
+    if (c->flux < AMR_FLUX_RUSANOV || c->flux > AMR_FLUX_HLL) return bad("unknown flux");
     if (!(c->gamma > 1.0) || !(c->cfl > 0.0)) return bad("gamma must be > 1 and cfl > 0");
     for (int d = 0; d < c->ndim; ++d) {
         if (c->ntrees[d] < 1 || (int64_t(c->ntrees[d]) << c->max_level) >= (1 << 19)) return bad("ntrees x 2^max_level must be < 2^19");
@@ -181,14 +183,17 @@ template <class real, int D>
 amr_status launch_stage(amr_forest *f, const StageArgs<real> &a, cudaStream_t st) {
     const int N = f->cfg.block_n, NG = f->cfg.n_ghost;
     if constexpr (std::is_same<real, float>::value && D == 3) {
-        if (NG == 2 && !f->scalar_stage) {
+        // the pair kernel implements minmod + Rusanov only
+        if (NG == 2 && !f->scalar_stage && a.limiter == AMR_LIM_MINMOD && a.flux == AMR_FLUX_RUSANOV) {
             if (N == 8) return launch_stage_pair<8>(f, a, st);
             if (N == 16) return launch_stage_pair<16>(f, a, st);
             if (N == 32) return launch_stage_pair<32>(f, a, st);
         }
     }
-#define AMR_STAGE_CASE(n_, g_) \
-    if (N == n_ && NG == g_) return launch_stage_t<real, D, n_, g_>(f, a, st);
+    const bool gen = a.limiter != AMR_LIM_MINMOD || a.flux != AMR_FLUX_RUSANOV;
+#define AMR_STAGE_CASE(n_, g_)                                                                                   \
+    if (N == n_ && NG == g_)                                                                                     \
+        return gen ? launch_stage_t<real, D, n_, g_, true>(f, a, st) : launch_stage_t<real, D, n_, g_, false>(f, a, st);
     AMR_STAGE_CASE(8, 2)
     AMR_STAGE_CASE(16, 2)
     AMR_STAGE_CASE(32, 2)
@@ -217,6 +222,8 @@ amr_status run_stage(amr_forest *f, const amr_stage *stg, cudaStream_t st) {
     a.update_dt = stg->update_dt;
     a.gather = stg->gather_halo;
     a.gamma = real(f->cfg.gamma);
+    a.limiter = f->cfg.limiter;
+    a.flux = f->cfg.flux;
     amr_status s = launch_stage<real, D>(f, a, st);
     if (s != AMR_OK) return s;
     const int nfix = int(f->pat.fix_start.size()) - 1;
@@ -429,6 +436,7 @@ amr_status amr_create_batch(const amr_config *cfgs, const int *init_levels, int 
         // settings every instance of one forest shares
         if (c.ndim != c0.ndim || c.block_n != c0.block_n || c.n_ghost != c0.n_ghost || c.precision != c0.precision ||
             c.n_states != c0.n_states || c.gamma != c0.gamma || c.host_only != c0.host_only ||
+            c.limiter != c0.limiter || c.flux != c0.flux ||
             c.dev_alloc != c0.dev_alloc || c.dev_free != c0.dev_free || c.alloc_ctx != c0.alloc_ctx)
             return AMR_EINVAL;
         capacity += c.max_blocks;

@@ -34,6 +34,21 @@ __device__ __forceinline__ T minmod(T a, T b) {
     return (a > T(0) && b > T(0)) ? lo : ((a < T(0) && b < T(0)) ? hi : T(0));
 }
 
+// MUSCL slope of a cell from its one-sided differences a (left), b (right):
+// lim 0 minmod; 1 monotonized central = Eq. 1 with theta = 2, i.e. for equal
+// signs sign(a) min(2|a|, 2|b|, |a + b| / 2); 2 van Leer 2ab / (a + b) when
+// ab > 0.  Zero when a and b differ in sign.
+template <class T>
+__device__ __forceinline__ T limited_slope(int lim, T a, T b) {
+    if (lim == 0) return minmod(a, b);
+    if (!((a > T(0) && b > T(0)) || (a < T(0) && b < T(0)))) return T(0);
+    if (lim == 2) return T(2) * a * b / (a + b);
+    T m = fabs(T(2) * a);
+    m = fmin(m, fabs(T(2) * b));
+    m = fmin(m, fabs(a + b) * T(0.5));
+    return a > T(0) ? m : -m;
+}
+
 // Geometry of one forest as seen by the kernels.  A forest holds one or
 // more independent mesh instances; cell sizes are looked up by geometry
 // class gc = instance * kMaxLevels + level in device tables [gc][3].

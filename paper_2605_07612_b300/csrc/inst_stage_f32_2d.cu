@@ -2,5 +2,5 @@
 #include "launch_kernels.cuh"
 
 namespace amrb {
-AMR_INST_STAGE(float, 2)
+AMR_INST_STAGE(float, 2, false)
 }  // namespace amrb

@@ -2,5 +2,5 @@
 #include "launch_kernels.cuh"
 
 namespace amrb {
-AMR_INST_STAGE(double, 3)
+AMR_INST_STAGE(double, 3, false)
 }  // namespace amrb

@@ -42,14 +42,14 @@ amr_status launch_ghosts(amr_forest *f, int s, cudaStream_t st, bool gather) {
     return AMR_OK;
 }
 
-template <class real, int D, int N, int NG>
+template <class real, int D, int N, int NG, bool GEN>
 amr_status launch_stage_t(amr_forest *f, const StageArgs<real> &a, cudaStream_t st) {
     constexpr int T = N < 16 ? N : 16;
     using Sh = StageShape<real, D, N, NG, T>;
     static bool attr_done = false;
     const size_t smem = Sh::smem_bytes();
     if (!attr_done) {
-        CU(cudaFuncSetAttribute(k_stage<real, D, N, NG, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        CU(cudaFuncSetAttribute(k_stage<real, D, N, NG, T, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
         attr_done = true;
     }
     const int64_t items = nblocks(f) * Sh::TILES;
@@ -57,9 +57,9 @@ amr_status launch_stage_t(amr_forest *f, const StageArgs<real> &a, cudaStream_t 
         StageArgs<real> b = a;
         b.n_items = int(items);
         int occ = 1;
-        if (f->persistent) CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_stage<real, D, N, NG, T>, Sh::NT, smem));
+        if (f->persistent) CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_stage<real, D, N, NG, T, GEN>, Sh::NT, smem));
         const int64_t grid = stage_grid(f, items, occ);
-        k_stage<real, D, N, NG, T><<<unsigned(grid), Sh::NT, smem, st>>>(b, f->geom);
+        k_stage<real, D, N, NG, T, GEN><<<unsigned(grid), Sh::NT, smem, st>>>(b, f->geom);
         ++f->launches;
     }
     CU(cudaGetLastError());
@@ -100,10 +100,10 @@ amr_status launch_stage_pair(amr_forest *f, const StageArgs<float> &a, cudaStrea
 
 }  // namespace amrb
 
-#define AMR_INST_STAGE(real, D)                                                                     \
-    template amr_status launch_stage_t<real, D, 8, 2>(amr_forest *, const StageArgs<real> &, cudaStream_t);  \
-    template amr_status launch_stage_t<real, D, 16, 2>(amr_forest *, const StageArgs<real> &, cudaStream_t); \
-    template amr_status launch_stage_t<real, D, 32, 2>(amr_forest *, const StageArgs<real> &, cudaStream_t); \
-    template amr_status launch_stage_t<real, D, 8, 3>(amr_forest *, const StageArgs<real> &, cudaStream_t);  \
-    template amr_status launch_stage_t<real, D, 16, 3>(amr_forest *, const StageArgs<real> &, cudaStream_t); \
-    template amr_status launch_stage_t<real, D, 32, 3>(amr_forest *, const StageArgs<real> &, cudaStream_t);
+#define AMR_INST_STAGE(real, D, GEN)                                                                    \
+    template amr_status launch_stage_t<real, D, 8, 2, GEN>(amr_forest *, const StageArgs<real> &, cudaStream_t);  \
+    template amr_status launch_stage_t<real, D, 16, 2, GEN>(amr_forest *, const StageArgs<real> &, cudaStream_t); \
+    template amr_status launch_stage_t<real, D, 32, 2, GEN>(amr_forest *, const StageArgs<real> &, cudaStream_t); \
+    template amr_status launch_stage_t<real, D, 8, 3, GEN>(amr_forest *, const StageArgs<real> &, cudaStream_t);  \
+    template amr_status launch_stage_t<real, D, 16, 3, GEN>(amr_forest *, const StageArgs<real> &, cudaStream_t); \
+    template amr_status launch_stage_t<real, D, 32, 3, GEN>(amr_forest *, const StageArgs<real> &, cudaStream_t);

@@ -1,15 +1,16 @@
 // Finite-volume Runge-Kutta stage of the Euler equations (Sec. 3.1-3.5):
 //   u_out = w_dt dt F(u_deriv) + sum_i w_i u_prev_i            (Eq. 4)
-// F: primitive variables (Eq. 9), MUSCL face values with the minmod limiter,
-// Rusanov flux with Einfeldt's wave-speed estimate, flux divergence.
+// F: primitive variables (Eq. 9), MUSCL face values with the configured slope
+// limiter (minmod, MC or van Leer), Rusanov or HLL flux with Einfeldt's
+// wave-speed estimate, flux divergence.
 //
 // Work decomposition (ours, not the paper's gang/collapse loops): one CTA per
 // (block, T x T column tile).  The CTA marches k through the block keeping a
 // ring of 5 planes of primitives (tile plus a 2-cell x/y halo, corners
 // excluded) in shared memory, so each cell is converted to primitives once.
 // Per plane:
-//   phase A  every cell's limited face states along x and y (one minmod per
-//            variable and direction) into shared memory; the z face states of
+//   phase A  every cell's limited face states along x and y (one limited
+//            slope per variable and direction) into shared memory; the z face states of
 //            the cell above, in registers;
 //   phase B  every face flux once (x, y from the stored states, z in
 //            registers); the plane three ahead is converted and committed;
@@ -46,6 +47,8 @@ struct StageArgs {
     int gather;                  // halo cells across SRL faces from the neighbour's interior
     int n_items;                 // blocks x column tiles; CTAs loop over them with a grid stride
     real gamma;
+    int limiter;                 // amr_limiter (per-cell kernel; the pair kernel is minmod only)
+    int flux;                    // amr_flux (per-cell kernel; the pair kernel is Rusanov only)
 };
 
 template <class real>
@@ -132,6 +135,60 @@ struct Euler {
         }
         F[D + 1] = real(0.5) * ((EL + pL) * vnL + (ER + pR) * vnR) - ha * (ER - EL);
     }
+
+    // HLL flux with the same Einfeldt speeds: sL = min(u_roe - d, 0),
+    // sR = max(u_roe + d, 0), F = (sR F_L - sL F_R + sL sR (U_R - U_L)) / (sR - sL)
+    template <int NRM>
+    __device__ static __forceinline__ void hll(const real *wL, const real *wR, int n, real gam, real gm1i, real *F) {
+        const int nn = NRM >= 0 ? NRM : n;
+        real vnL, vnR;
+        if (NRM >= 0) {
+            vnL = wL[1 + (NRM >= 0 ? NRM : 0)];
+            vnR = wR[1 + (NRM >= 0 ? NRM : 0)];
+        } else {
+            vnL = nn == 0 ? wL[1] : (nn == 1 ? wL[2] : wL[D]);
+            vnR = nn == 0 ? wR[1] : (nn == 1 ? wR[2] : wR[D]);
+        }
+        const real rL = wL[0], rR = wR[0], pL = wL[D + 1], pR = wR[D + 1];
+        real sqL, iL, sqR, iR;
+        FM<real>::sqrt_inv(rL, sqL, iL);
+        FM<real>::sqrt_inv(rR, sqR, iR);
+        const real inv = FM<real>::rcp(sqL + sqR);
+        const real c2L = gam * pL * iL, c2R = gam * pR * iR;
+        const real uroe = (sqL * vnL + sqR * vnR) * inv;
+        const real du = vnR - vnL;
+        const real d = FM<real>::sqrtp((sqL * c2L + sqR * c2R) * inv + real(0.5) * sqL * sqR * inv * inv * du * du);
+        const real sL = fmin(uroe - d, real(0)), sR = fmax(uroe + d, real(0));
+        const real iw = FM<real>::rcp(sR - sL), sLR = sL * sR;
+        real v2L = real(0), v2R = real(0);
+#pragma unroll
+        for (int dd = 0; dd < D; ++dd) {
+            v2L += wL[1 + dd] * wL[1 + dd];
+            v2R += wR[1 + dd] * wR[1 + dd];
+        }
+        const real EL = pL * gm1i + real(0.5) * rL * v2L;
+        const real ER = pR * gm1i + real(0.5) * rR * v2R;
+        const real mL = rL * vnL, mR = rR * vnR;
+        F[0] = (sR * mL - sL * mR + sLR * (rR - rL)) * iw;
+#pragma unroll
+        for (int dd = 0; dd < D; ++dd) {
+            real fL = mL * wL[1 + dd], fR = mR * wR[1 + dd];
+            if (dd == nn) {
+                fL += pL;
+                fR += pR;
+            }
+            F[1 + dd] = (sR * fL - sL * fR + sLR * (rR * wR[1 + dd] - rL * wL[1 + dd])) * iw;
+        }
+        F[D + 1] = (sR * (EL + pL) * vnL - sL * (ER + pR) * vnR + sLR * (ER - EL)) * iw;
+    }
+
+    // the configured numerical flux
+    template <int NRM>
+    __device__ static __forceinline__ void face_flux(int kind, const real *wL, const real *wR, int n, real gam, real gm1i,
+                                                     real *F) {
+        if (kind == 1) hll<NRM>(wL, wR, n, gam, gm1i, F);
+        else flux<NRM>(wL, wR, n, gam, gm1i, F);
+    }
 };
 
 template <class real, int D, int N, int NG, int T>
@@ -155,7 +212,9 @@ struct StageShape {
     }
 };
 
-template <class real, int D, int N, int NG, int T>
+// GEN = false: minmod and Rusanov fixed at compile time (the default scheme);
+// GEN = true: the limiter and flux named in the arguments.
+template <class real, int D, int N, int NG, int T, bool GEN>
 __device__ __forceinline__ void stage_item(const StageArgs<real> &a, const Geom &g, int item) {
     using Sh = StageShape<real, D, N, NG, T>;
     using E = Euler<real, D>;
@@ -182,6 +241,7 @@ __device__ __forceinline__ void stage_item(const StageArgs<real> &a, const Geom 
     const real gam = a.gamma;
     const real gm1i = real(1) / (gam - real(1));
     const real dt_eff = real(a.w_dt * a.sc_in[info.inst].dt);
+    const int lim = GEN ? a.limiter : 0, flx = GEN ? a.flux : 0;
     const real *__restrict__ ub = a.deriv + int64_t(b) * V * NC;
     // halo source: in gather mode a cell outside the block across a face with
     // a same-level neighbour is read from that neighbour's interior
@@ -317,7 +377,7 @@ __device__ __forceinline__ void stage_item(const StageArgs<real> &a, const Geom 
 #pragma unroll
             for (int v = 0; v < V; ++v) {
                 const real w0 = pl[v * PL + c], wm = pl[v * PL + c - st], wp = pl[v * PL + c + st];
-                const real hs = real(0.5) * minmod<real>(w0 - wm, wp - w0);
+                const real hs = real(0.5) * limited_slope<real>(lim, w0 - wm, wp - w0);
                 const real lo = w0 - hs, hi = w0 + hs;
                 if (v == 0 || v == D + 1) bad |= !(lo > real(0)) || !(hi > real(0));
                 FSm[(dir * V + v) * NFS + qq] = lo;
@@ -333,7 +393,7 @@ __device__ __forceinline__ void stage_item(const StageArgs<real> &a, const Geom 
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             const real w0 = p1[v * PL + c], wm = p0[v * PL + c], wp = p2[v * PL + c];
-            const real hs = real(0.5) * minmod<real>(w0 - wm, wp - w0);
+            const real hs = real(0.5) * limited_slope<real>(lim, w0 - wm, wp - w0);
             zm[v] = w0 - hs;
             zp[v] = w0 + hs;
         }
@@ -358,7 +418,7 @@ __device__ __forceinline__ void stage_item(const StageArgs<real> &a, const Geom 
             wL[v] = FSp[v * NFS + jj * (T + 2) + fi];
             wR[v] = FSm[v * NFS + jj * (T + 2) + fi + 1];
         }
-        E::template flux<0>(wL, wR, 0, gam, gm1i, F);
+        E::template face_flux<0>(flx, wL, wR, 0, gam, gm1i, F);
 #pragma unroll
         for (int v = 0; v < V; ++v) Fx[v * NFX + q] = F[v];
         if (fi == 0 && tx0 == 0) store_bflux(0, ty0 + jj + N * k, F);
@@ -372,7 +432,7 @@ __device__ __forceinline__ void stage_item(const StageArgs<real> &a, const Geom 
             wL[v] = FSp[(V + v) * NFS + fj * T + ii];
             wR[v] = FSm[(V + v) * NFS + (fj + 1) * T + ii];
         }
-        E::template flux<1>(wL, wR, 1, gam, gm1i, F);
+        E::template face_flux<1>(flx, wL, wR, 1, gam, gm1i, F);
 #pragma unroll
         for (int v = 0; v < V; ++v) Fy[v * NFX + q] = F[v];
         if (fj == 0 && ty0 == 0) store_bflux(2, tx0 + ii + N * k, F);
@@ -404,7 +464,7 @@ __device__ __forceinline__ void stage_item(const StageArgs<real> &a, const Geom 
             wL[v] = FSp[(dir * V + v) * NFS + iL];
             wR[v] = FSm[(dir * V + v) * NFS + iR];
         }
-        E::template flux<-1>(wL, wR, dir, gam, gm1i, F);
+        E::template face_flux<-1>(flx, wL, wR, dir, gam, gm1i, F);
         real *Fd = dir ? Fy : Fx;
 #pragma unroll
         for (int v = 0; v < V; ++v) Fd[v * NFX + q] = F[v];
@@ -474,7 +534,7 @@ __device__ __forceinline__ void stage_item(const StageArgs<real> &a, const Geom 
             real zm[V], zp[V], pm1[V];
             z_states(-1, zm, pm1);          // plus state of cell -1
             z_states(0, zm, zp);            // minus / plus states of cell 0
-            E::template flux<2>(pm1, zm, 2, gam, gm1i, Fz_lo);
+            E::template face_flux<2>(flx, pm1, zm, 2, gam, gm1i, Fz_lo);
             store_bflux(4, tx0 + ti + N * (ty0 + tj), Fz_lo);
 #pragma unroll
             for (int v = 0; v < V; ++v) Fz_hi[v] = zp[v];     // carries plus(0) into the loop
@@ -491,7 +551,7 @@ __device__ __forceinline__ void stage_item(const StageArgs<real> &a, const Geom 
             x_face(tid, k);
             y_face(tid, k);
             if (tid < 2 * T) extra_face(k);
-            E::template flux<2>(zplus, zm1, 2, gam, gm1i, Fz_hi);
+            E::template face_flux<2>(flx, zplus, zm1, 2, gam, gm1i, Fz_hi);
             if (k == N - 1) store_bflux(5, tx0 + ti + N * (ty0 + tj), Fz_hi);
 #pragma unroll
             for (int v = 0; v < V; ++v) zplus[v] = zp1[v];
@@ -533,9 +593,9 @@ __device__ __forceinline__ void stage_item(const StageArgs<real> &a, const Geom 
 
 // CTAs take items (block, column tile) with a grid stride: one CTA per item
 // when the grid covers them all, a persistent sweep when it is smaller.
-template <class real, int D, int N, int NG, int T>
+template <class real, int D, int N, int NG, int T, bool GEN>
 __global__ void __launch_bounds__(T * T) k_stage(StageArgs<real> a, Geom g) {
-    for (int item = blockIdx.x; item < a.n_items; item += gridDim.x) stage_item<real, D, N, NG, T>(a, g, item);
+    for (int item = blockIdx.x; item < a.n_items; item += gridDim.x) stage_item<real, D, N, NG, T, GEN>(a, g, item);
 }
 
 }  // namespace amrb
