@@ -43,7 +43,7 @@ class Params(C.Structure):
                 ("lo", C.c_double * 3), ("len", C.c_double * 3),
                 ("max_level", C.c_int), ("gamma", C.c_double), ("cfl", C.c_double),
                 ("bc_type", C.c_int * 6), ("bc_val", (C.c_double * 8) * 6),
-                ("limiter", C.c_int), ("flux", C.c_int)]
+                ("limiter", C.c_int), ("flux", C.c_int), ("gravity", C.c_double * 3)]
 
 
 def _lib_handle():
@@ -105,6 +105,9 @@ def params_from_spec(spec) -> Params:
             p.bc_val[f][v] = float(spec.bc_val[f][v]) if v < len(spec.bc_val[f]) else 0.0
     p.limiter = int(getattr(spec, "limiter", 0))
     p.flux = int(getattr(spec, "flux", 0))
+    gv = getattr(spec, "gravity", (0.0, 0.0, 0.0))
+    for d in range(3):
+        p.gravity[d] = float(gv[d]) if d < spec.ndim else 0.0
     return p
 
 

@@ -55,6 +55,7 @@ typedef struct {
     double bc_val[6][8];
     int limiter;           /* MUSCL slope limiter (Sec. 3.2 list): 0 minmod, 1 MC, 2 van Leer */
     int flux;              /* 0 Rusanov, 1 HLL (Sec. 3.2 list), both with Einfeldt speeds */
+    double gravity[3];     /* g of the source term S = (0, rho g, rho g.u) (Sec. 4.2) */
 } orc_params;
 
 enum { BC_NONE = 0, BC_DIRICHLET = 1, BC_NEUMANN = 2, BC_DATA = 3 };
@@ -904,6 +905,16 @@ int orc_stage(const orc_mesh *m, const double *ud, double *uo, int nprev,
                             double Flo = fl[((int64_t)n * V + v) * nfl + x[n] + (N + 1) * tt];
                             double Fhi = fl[((int64_t)n * V + v) * nfl + x[n] + 1 + (N + 1) * tt];
                             r = r + (Flo - Fhi) / dx_at(p, n, lev);
+                        }
+                        /* gravity source S = (0, rho g, rho g.u) from the
+                         * conservative state of the cell (Sec. 3.2 step order:
+                         * source, then minus the flux divergence) */
+                        if (v >= 1 && v <= D) {
+                            r = r + ud[atv(p, b, 0, x)] * p->gravity[v - 1];
+                        } else if (v == D + 1) {
+                            double sg = 0.0;
+                            for (int d = 0; d < D; d++) sg = sg + ud[atv(p, b, 1 + d, x)] * p->gravity[d];
+                            r = r + sg;
                         }
                         rhs[atv(p, b, v, x)] = r;
                     }

@@ -47,6 +47,7 @@ class MeshSpec:
     bc_val: Sequence[Sequence[float]] = tuple(tuple(0.0 for _ in range(8)) for _ in range(6))
     limiter: int = 0          # MUSCL slope limiter: 0 minmod, 1 MC, 2 van Leer
     flux: int = 0             # 0 Rusanov, 1 HLL
+    gravity: Sequence[float] = (0.0, 0.0, 0.0)   # source term S = (0, rho g, rho g.u)
 
     @property
     def nvar(self) -> int:
@@ -338,3 +339,45 @@ def sphere_and_shock(spec: MeshSpec, lev, g, centre, radius=0.1, p_in=100.0, sho
     p = np.where(behind, p2, np.where(r2 < radius * radius, p_in, 1.0))
     vel = [np.where(behind, u2, 0.0)] + [np.zeros_like(rho) for _ in range(spec.ndim - 1)]
     return mask_interior(spec, primitive_to_state(spec, rho, vel, p))
+
+
+def rayleigh_taylor(spec: MeshSpec, lev, g, h0=0.8, rho_hi=1.0, rho_lo=0.1, delta=0.05, p_top=1.0):
+    """Rayleigh-Taylor state of Sec. 4.2: heavy fluid (rho_hi) above the
+    interface h = h0 + delta sin(2 pi x) [sin(2 pi y) in 3D], light fluid
+    below, at rest, pressure in hydrostatic balance with g = -1 along the last
+    dimension (p = p_top at the top); cell-centre sampling."""
+    X = cell_centres(spec, lev, g)
+    vert = X[spec.ndim - 1]
+    if spec.ndim == 3:
+        h = h0 + delta * np.sin(2.0 * np.pi * X[0]) * np.sin(2.0 * np.pi * X[1])
+    else:
+        h = h0 + delta * np.sin(2.0 * np.pi * X[0])
+    top = spec.lo[spec.ndim - 1] + spec.length[spec.ndim - 1]
+    heavy = vert > h
+    rho = np.where(heavy, rho_hi, rho_lo)
+    p = np.where(heavy, p_top + rho_hi * (top - vert), p_top + rho_hi * (top - h) + rho_lo * (h - vert))
+    vel = [np.zeros_like(rho) for _ in range(spec.ndim)]
+    return mask_interior(spec, primitive_to_state(spec, rho, vel, p))
+
+
+def rayleigh_taylor_spec(ndim=3, N=16, ntrees=None, limiter=2, rho_hi=1.0, rho_lo=0.1, **kw) -> MeshSpec:
+    """Sec. 4.2 setup: unit square/cube, periodic horizontally, gamma = 5/3,
+    g = -1 along the last dimension; the vertical faces are Neumann with the
+    hydrostatic gradient of the energy (outward derivative of E = outward
+    dp/dn / (gamma - 1): rho_lo / (gamma - 1) at the bottom, -rho_hi /
+    (gamma - 1) at the top) and zero gradient for the other variables."""
+    gam = 5.0 / 3.0
+    nt = ntrees if ntrees is not None else tuple([256 // N] * ndim + [1] * (3 - ndim))
+    V = ndim + 2
+    per = [1, 1, 1]
+    per[ndim - 1] = 0
+    bct = [0] * 6
+    bct[2 * (ndim - 1)] = bct[2 * (ndim - 1) + 1] = BC_NEUMANN
+    bcv = [[0.0] * 8 for _ in range(6)]
+    bcv[2 * (ndim - 1)][V - 1] = rho_lo / (gam - 1.0)
+    bcv[2 * (ndim - 1) + 1][V - 1] = -rho_hi / (gam - 1.0)
+    grav = [0.0, 0.0, 0.0]
+    grav[ndim - 1] = -1.0
+    return MeshSpec(ndim=ndim, N=N, ng=2, ntrees=tuple(nt), periodic=tuple(per), gamma=gam, cfl=0.5,
+                    bc_type=tuple(bct), bc_val=tuple(tuple(r) for r in bcv), limiter=limiter,
+                    gravity=tuple(grav), **kw)
