@@ -282,6 +282,27 @@ def run_ours(args, rank, world, dist):
         extras["vanleer_hll"] = {"value": 2.0 * cells * args.steps * world / (msv * 1e-3), "ms_per_step": msv / args.steps}
         del fv
         torch.cuda.empty_cache()
+        # the paper's Rayleigh-Taylor case (Sec. 4.2; Tables 1 and 3 on H100):
+        # 256^3, van Leer, Heun, CFL 0.5, gamma 5/3, gravity source
+        rt = {}
+        for bn, prec in ((32, 32), (16, 32), (8, 32), (16, 64)):
+            sp_rt = synth.rayleigh_taylor_spec(ndim=3, N=bn, limiter=2)
+            fr = amr.Forest(sp_rt, 0, precision=prec)
+            lev_rt, g_rt = fr.blocks()
+            fr.set_state(0, synth.rayleigh_taylor(sp_rt, lev_rt, g_rt).astype(fr.dtype))
+            fr.compute_dt(0, stream=stream)
+            if prec == 32:
+                fr.autotune(stream=stream)
+            nrt = args.steps if prec == 32 else max(2, args.steps // 4)
+            msr, _ = time_steps(fr, nrt, 1 if prec == 64 else args.warmup, prec == 32, prec == 32)
+            st_rt = fr.sync_status()
+            rt["%d^3 fp%d" % (bn, prec)] = {"value": 2.0 * cells * nrt * world / (msr * 1e-3), "ms_per_step": msr / nrt,
+                                             "status": st_rt}
+            del fr
+            torch.cuda.empty_cache()
+        rt["context"] = ("paper, 1x H100, same case: FP64 1.37 / 1.30 / 1.10 and FP32 2.70 / 2.60 / 2.08 GCUPS "
+                         "for 32^3 / 16^3 / 8^3 blocks (Tables 1 and 3); flux scheme not stated there, Rusanov here")
+        extras["rayleigh_taylor_vanleer"] = rt
         extras["batched_2d"] = run_batched(args, amr, torch, stream, barrier, world)
 
     line = {

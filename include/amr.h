@@ -103,6 +103,8 @@ typedef struct {
                               and amr_flag_and_regrid needs explicit flags */
     int limiter;           /* amr_limiter: MUSCL slope limiter (Sec. 3.2) */
     int flux;              /* amr_flux: numerical flux (Sec. 3.2) */
+    double gravity[3];     /* g of the source term S = (0, rho g, rho g.u) added to
+                              every stage (Sec. 4.2); zero: no source */
 } amr_config;
 
 /* MUSCL slope limiters of Sec. 3.2 that need two ghost layers.  The slope
@@ -177,8 +179,8 @@ amr_status amr_create_forest(const amr_config *cfg, int init_level, amr_forest *
  * at once -- one kernel launch per phase sweeps every block of every
  * instance.  Each instance keeps its own domain, brick, periodicity,
  * max_level, boundaries, CFL number and time step; ndim, block_n, n_ghost,
- * precision, n_states, gamma, limiter, flux, host_only and the allocation
- * hook must be the same for all.  Capacity is the sum of the instances' max_blocks; each
+ * precision, n_states, gamma, limiter, flux, gravity, host_only and the
+ * allocation hook must be the same for all.  Capacity is the sum of the instances' max_blocks; each
  * instance is also held to its own max_blocks on regrid.  amr_create_forest
  * is the n = 1 case.  Errors as amr_create_forest. */
 amr_status amr_create_batch(const amr_config *cfgs, const int *init_levels, int n, amr_forest **out);

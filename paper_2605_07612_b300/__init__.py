@@ -53,7 +53,7 @@ class Config(C.Structure):
                 ("gamma", C.c_double), ("cfl", C.c_double),
                 ("bc", C.c_int * 6), ("bc_val", (C.c_double * 8) * 6),
                 ("dev_alloc", AllocFn), ("dev_free", FreeFn), ("alloc_ctx", C.c_void_p),
-                ("host_only", C.c_int), ("limiter", C.c_int), ("flux", C.c_int)]
+                ("host_only", C.c_int), ("limiter", C.c_int), ("flux", C.c_int), ("gravity", C.c_double * 3)]
 
 
 class GhostEntry(C.Structure):
@@ -151,6 +151,9 @@ def config_from_spec(spec, max_blocks, n_states=2, precision=64, host_only=False
     c.host_only = 1 if host_only else 0
     c.limiter = int(getattr(spec, "limiter", 0))
     c.flux = int(getattr(spec, "flux", 0))
+    gv = getattr(spec, "gravity", (0.0, 0.0, 0.0))
+    for d in range(3):
+        c.gravity[d] = float(gv[d]) if d < spec.ndim else 0.0
     c.ndim, c.block_n, c.n_ghost, c.n_var = spec.ndim, spec.N, spec.ng, spec.ndim + 2
     for d in range(3):
         c.ntrees[d] = int(spec.ntrees[d]) if d < spec.ndim else 1

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -137,6 +138,8 @@ amr_status validate(const amr_config *c, std::string &why) {
     if (c->limiter < AMR_LIM_MINMOD || c->limiter > AMR_LIM_VANLEER) return bad("unknown limiter");
     if (c->flux < AMR_FLUX_RUSANOV || c->flux > AMR_FLUX_HLL) return bad("unknown flux");
     if (!(c->gamma > 1.0) || !(c->cfl > 0.0)) return bad("gamma must be > 1 and cfl > 0");
+    for (int d = 0; d < 3; ++d)
+        if (!std::isfinite(c->gravity[d])) return bad("gravity must be finite");
     for (int d = 0; d < c->ndim; ++d) {
         if (c->ntrees[d] < 1 || (int64_t(c->ntrees[d]) << c->max_level) >= (1 << 19)) return bad("ntrees x 2^max_level must be < 2^19");
         if (!(c->len[d] > 0.0)) return bad("len must be > 0");
@@ -183,8 +186,8 @@ template <class real, int D>
 amr_status launch_stage(amr_forest *f, const StageArgs<real> &a, cudaStream_t st) {
     const int N = f->cfg.block_n, NG = f->cfg.n_ghost;
     if constexpr (std::is_same<real, float>::value && D == 3) {
-        // the pair kernel implements minmod + Rusanov only
-        if (NG == 2 && !f->scalar_stage && a.limiter == AMR_LIM_MINMOD && a.flux == AMR_FLUX_RUSANOV) {
+        // the pair kernel implements the Rusanov flux only
+        if (NG == 2 && !f->scalar_stage && a.flux == AMR_FLUX_RUSANOV) {
             if (N == 8) return launch_stage_pair<8>(f, a, st);
             if (N == 16) return launch_stage_pair<16>(f, a, st);
             if (N == 32) return launch_stage_pair<32>(f, a, st);
@@ -224,6 +227,11 @@ amr_status run_stage(amr_forest *f, const amr_stage *stg, cudaStream_t st) {
     a.gamma = real(f->cfg.gamma);
     a.limiter = f->cfg.limiter;
     a.flux = f->cfg.flux;
+    a.gravity_on = 0;
+    for (int d = 0; d < 3; ++d) {
+        a.grav[d] = d < D ? real(f->cfg.gravity[d]) : real(0);
+        if (d < D && f->cfg.gravity[d] != 0.0) a.gravity_on = 1;
+    }
     amr_status s = launch_stage<real, D>(f, a, st);
     if (s != AMR_OK) return s;
     const int nfix = int(f->pat.fix_start.size()) - 1;
@@ -436,7 +444,8 @@ amr_status amr_create_batch(const amr_config *cfgs, const int *init_levels, int 
         // settings every instance of one forest shares
         if (c.ndim != c0.ndim || c.block_n != c0.block_n || c.n_ghost != c0.n_ghost || c.precision != c0.precision ||
             c.n_states != c0.n_states || c.gamma != c0.gamma || c.host_only != c0.host_only ||
-            c.limiter != c0.limiter || c.flux != c0.flux ||
+            c.limiter != c0.limiter || c.flux != c0.flux || c.gravity[0] != c0.gravity[0] ||
+            c.gravity[1] != c0.gravity[1] || c.gravity[2] != c0.gravity[2] ||
             c.dev_alloc != c0.dev_alloc || c.dev_free != c0.dev_free || c.alloc_ctx != c0.alloc_ctx)
             return AMR_EINVAL;
         capacity += c.max_blocks;

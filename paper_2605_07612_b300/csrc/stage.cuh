@@ -49,6 +49,8 @@ struct StageArgs {
     real gamma;
     int limiter;                 // amr_limiter (per-cell kernel; the pair kernel is minmod only)
     int flux;                    // amr_flux (per-cell kernel; the pair kernel is Rusanov only)
+    int gravity_on;              // add the source S = (0, rho g, rho g.u) of u_deriv
+    real grav[3];
 };
 
 template <class real>
@@ -483,12 +485,27 @@ __device__ __forceinline__ void stage_item(const StageArgs<real> &a, const Geom 
     auto update = [&](int k) {
         const int64_t o = gaddr(ti, tj, k);
         const int64_t ob = int64_t(b) * V * NC + o;
-        real U[V];
+        real U[V], src[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) src[v] = real(0);
+        if (a.gravity_on) {
+            // S = (0, rho g, rho g.u) from the conservative state of the cell
+            const real *uc = a.deriv + ob;
+            const real rho = uc[0];
+            real sg = real(0);
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                src[1 + d] = rho * a.grav[d];
+                sg += uc[(1 + d) * NC] * a.grav[d];
+            }
+            src[D + 1] = sg;
+        }
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             real du = (Fx[v * NFX + tj * (T + 1) + ti] - Fx[v * NFX + tj * (T + 1) + ti + 1]) * idx0 +
                       (Fy[v * NFX + tj * T + ti] - Fy[v * NFX + (tj + 1) * T + ti]) * idx1;
             if (D == 3) du += (Fz_lo[v] - Fz_hi[v]) * idx2;
+            du += src[v];
             real acc = real(0);
 #pragma unroll
             for (int q = 0; q < 4; ++q)

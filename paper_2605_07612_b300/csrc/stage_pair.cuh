@@ -118,12 +118,53 @@ __device__ __forceinline__ void pair_flux(const float2 *wL, const float2 *wR, in
     F[4] = PF::fma(nha, PF::sub(ER, EL), PF::mul(half, fe));
 }
 
+// Half of the limited slope of a pair of cells from their one-sided
+// differences a (left) and b (right): LIM 1 monotonized central (Eq. 1 with
+// theta = 2: sign min(|a|, |b|, |a + b| / 4) when the signs agree), LIM 2 van
+// Leer (ab / (a + b) when ab > 0); zero when the signs differ.  (LIM 0,
+// minmod, is fused into the face states below.)
+template <int LIM>
+__device__ __forceinline__ float2 pair_half_slope(float2 a, float2 b) {
+    if constexpr (LIM == 2) {
+        const float2 p = PF::mul(a, b);
+        const float2 h = PF::mul(p, PF::rcp(PF::add(a, b)));
+        return make_float2(p.x > 0.f ? h.x : 0.f, p.y > 0.f ? h.y : 0.f);
+    } else {
+        const float2 q = PF::qs(a, b);                        // +-1/2 or 0
+        const float2 c = PF::mul(PF::add(a, b), PF::sp(0.25f));
+        const float2 m = make_float2(fminf(fminf(fabsf(a.x), fabsf(b.x)), fabsf(c.x)),
+                                     fminf(fminf(fabsf(a.y), fabsf(b.y)), fabsf(c.y)));
+        return PF::mul(PF::add(q, q), m);
+    }
+}
+
 // face states of a pair of faces from the four pairs of cells around them
 // (c-2, c-1, c, c+1 along the face normal)
+template <int LIM>
 __device__ __forceinline__ void pair_states(float2 w0, float2 w1, float2 w2, float2 w3, float2 &L, float2 &R) {
     const float2 d01 = PF::sub(w1, w0), d12 = PF::sub(w2, w1), d23 = PF::sub(w3, w2);
-    L = PF::fma(PF::qs(d01, d12), PF::mabs(d01, d12), w1);
-    R = PF::fma(PF::qs(d12, d23), PF::nmabs(d12, d23), w2);
+    if constexpr (LIM == 0) {
+        L = PF::fma(PF::qs(d01, d12), PF::mabs(d01, d12), w1);
+        R = PF::fma(PF::qs(d12, d23), PF::nmabs(d12, d23), w2);
+    } else {
+        L = PF::add(w1, pair_half_slope<LIM>(d01, d12));
+        R = PF::sub(w2, pair_half_slope<LIM>(d12, d23));
+    }
+}
+
+// minus and plus states of a pair of cells w1 from its neighbours w0, w2
+template <int LIM>
+__device__ __forceinline__ void pair_cell_states(float2 w0, float2 w1, float2 w2, float2 &minus, float2 &plus) {
+    const float2 d01 = PF::sub(w1, w0), d12 = PF::sub(w2, w1);
+    if constexpr (LIM == 0) {
+        const float2 q = PF::qs(d01, d12);
+        minus = PF::fma(q, PF::nmabs(d01, d12), w1);
+        plus = PF::fma(q, PF::mabs(d01, d12), w1);
+    } else {
+        const float2 h = pair_half_slope<LIM>(d01, d12);
+        minus = PF::sub(w1, h);
+        plus = PF::add(w1, h);
+    }
 }
 
 // conservative -> primitive for a pair of cells
@@ -167,7 +208,7 @@ struct PairShape {
 
 // NPREV >= 0: the number of previous states, fixed at compile time (Heun's two
 // stages use 1 and 2); -1 reads it from the arguments.
-template <int N, int NPREV>
+template <int N, int NPREV, int LIM>
 __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const Geom &g, int item) {
     using Sh = PairShape<N>;
     constexpr int T = Sh::T, NG = Sh::NG, S = Sh::S, P = Sh::P, PL = Sh::PL, V = Sh::V, NT = Sh::NT;
@@ -345,7 +386,7 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             const float2 A = ld2(pl, v, tj, ci - 2), B = ld2(pl, v, tj, ci), C2 = ld2(pl, v, tj, ci + 2);
-            pair_states(A, make_float2(A.y, B.x), B, make_float2(B.y, C2.x), wL[v], wR[v]);
+            pair_states<LIM>(A, make_float2(A.y, B.x), B, make_float2(B.y, C2.x), wL[v], wR[v]);
         }
         pair_flux<0>(wL, wR, 0, gam, gm1i, F);
 #pragma unroll
@@ -354,7 +395,7 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
         // y-face tj (between rows tj-1 and tj) of columns ci, ci+1
 #pragma unroll
         for (int v = 0; v < V; ++v)
-            pair_states(ld2(pl, v, tj - 2, ci), ld2(pl, v, tj - 1, ci), ld2(pl, v, tj, ci), ld2(pl, v, tj + 1, ci), wL[v], wR[v]);
+            pair_states<LIM>(ld2(pl, v, tj - 2, ci), ld2(pl, v, tj - 1, ci), ld2(pl, v, tj, ci), ld2(pl, v, tj + 1, ci), wL[v], wR[v]);
         pair_flux<1>(wL, wR, 1, gam, gm1i, F);
 #pragma unroll
         for (int v = 0; v < V; ++v) *reinterpret_cast<float2 *>(Fy + v * (T + 1) * T + Sh::fy(tj, ci)) = F[v];
@@ -367,10 +408,15 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
 #pragma unroll
             for (int v = 0; v < V; ++v) {
                 const float2 w1 = ld2(p1, v, tj, ci), w2 = ld2(p2, v, tj, ci), w3 = ld2(p3, v, tj, ci);
-                const float2 d12 = PF::sub(w2, w1), d23 = PF::sub(w3, w2), q = PF::qs(d12, d23);
-                wR[v] = PF::fma(q, PF::nmabs(d12, d23), w2);
-                wL[v] = zP[v];
-                zP[v] = PF::fma(q, PF::mabs(d12, d23), w2);
+                if constexpr (LIM == 0) {
+                    const float2 d12 = PF::sub(w2, w1), d23 = PF::sub(w3, w2), q = PF::qs(d12, d23);
+                    wR[v] = PF::fma(q, PF::nmabs(d12, d23), w2);
+                    wL[v] = zP[v];
+                    zP[v] = PF::fma(q, PF::mabs(d12, d23), w2);
+                } else {
+                    wL[v] = zP[v];
+                    pair_cell_states<LIM>(w1, w2, w3, wR[v], zP[v]);
+                }
             }
             pair_flux<2>(wL, wR, 2, gam, gm1i, Fz_new);
             if (k == N - 1) store_bflux2(5, tx0 + ci + N * (ty0 + tj), Fz_new);
@@ -384,7 +430,7 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
 #pragma unroll
             for (int v = 0; v < V; ++v) {
                 const float *row0 = pl + v * PL + (2 * r + 2) * P + 2, *row1 = row0 + P;
-                pair_states(make_float2(row0[T - 2], row1[T - 2]), make_float2(row0[T - 1], row1[T - 1]),
+                pair_states<LIM>(make_float2(row0[T - 2], row1[T - 2]), make_float2(row0[T - 1], row1[T - 1]),
                             make_float2(row0[T], row1[T]), make_float2(row0[T + 1], row1[T + 1]), wL[v], wR[v]);
             }
             pair_flux<0>(wL, wR, 0, gam, gm1i, F);
@@ -401,7 +447,7 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
             const int r = tid - YT;
 #pragma unroll
             for (int v = 0; v < V; ++v)
-                pair_states(ld2(pl, v, T - 2, 2 * r), ld2(pl, v, T - 1, 2 * r), ld2(pl, v, T, 2 * r), ld2(pl, v, T + 1, 2 * r),
+                pair_states<LIM>(ld2(pl, v, T - 2, 2 * r), ld2(pl, v, T - 1, 2 * r), ld2(pl, v, T, 2 * r), ld2(pl, v, T + 1, 2 * r),
                             wL[v], wR[v]);
             pair_flux<1>(wL, wR, 1, gam, gm1i, F);
 #pragma unroll
@@ -452,6 +498,17 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
         const int64_t ob = int64_t(b) * V * NC + o;
         const float2 i0 = PF::sp(idx0), i1 = PF::sp(idx1), i2 = PF::sp(idx2), dte = PF::sp(dt_eff);
         float2 U[V];
+        // gravity source S = (0, rho g, rho g.u) of variable v from the
+        // primitives of plane k, still in the ring
+        auto source = [&](int v) -> float2 {
+            const float *pk = slot(k);
+            const float2 rho = ld2(pk, 0, tj, ci);
+            if (v < 4) return PF::mul(rho, PF::sp(a.grav[v - 1]));
+            float2 vg = PF::mul(ld2(pk, 1, tj, ci), PF::sp(a.grav[0]));
+            vg = PF::fma(ld2(pk, 2, tj, ci), PF::sp(a.grav[1]), vg);
+            vg = PF::fma(ld2(pk, 3, tj, ci), PF::sp(a.grav[2]), vg);
+            return PF::mul(rho, vg);
+        };
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             const float2 x0 = *reinterpret_cast<const float2 *>(Fx + v * NFX + tj * FXP + ci);
@@ -461,6 +518,7 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
             float2 du = PF::mul(PF::sub(x0, make_float2(x0.y, x1.x)), i0);
             du = PF::fma(PF::sub(y0, y1), i1, du);
             du = PF::fma(PF::sub(Fzlo[v], Fzhi[v]), i2, du);
+            if (v > 0 && a.gravity_on) du = PF::add(du, source(v));
             float2 acc = PF::sp(0.f);
             if constexpr (NPREV > 0) {
 #pragma unroll
@@ -520,9 +578,14 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             const float2 w0 = ld2(p0, v, tj, ci), w1 = ld2(p1, v, tj, ci), w2 = ld2(p2, v, tj, ci), w3 = ld2(p3, v, tj, ci);
-            pair_states(w0, w1, w2, w3, wL[v], wR[v]);
-            const float2 d12 = PF::sub(w2, w1), d23 = PF::sub(w3, w2);
-            zP[v] = PF::fma(PF::qs(d12, d23), PF::mabs(d12, d23), w2);
+            pair_states<LIM>(w0, w1, w2, w3, wL[v], wR[v]);
+            if constexpr (LIM == 0) {
+                const float2 d12 = PF::sub(w2, w1), d23 = PF::sub(w3, w2);
+                zP[v] = PF::fma(PF::qs(d12, d23), PF::mabs(d12, d23), w2);
+            } else {
+                float2 zm;
+                pair_cell_states<LIM>(w1, w2, w3, zm, zP[v]);
+            }
         }
         pair_flux<2>(wL, wR, 2, gam, gm1i, FzA);
         store_bflux2(4, tx0 + ci + N * (ty0 + tj), FzA);
@@ -557,9 +620,9 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
     if (__syncthreads_or(nonphys) && tid == 0) raise_status(&a.sc[0].status, 7);
 }
 
-template <int N, int NPREV>
+template <int N, int NPREV, int LIM>
 __global__ void __launch_bounds__(PairShape<N>::NT, (N >= 16 ? 4 : 1)) k_stage_pair(StageArgs<float> a, Geom g) {
-    for (int item = blockIdx.x; item < a.n_items; item += gridDim.x) stage_pair_item<N, NPREV>(a, g, item);
+    for (int item = blockIdx.x; item < a.n_items; item += gridDim.x) stage_pair_item<N, NPREV, LIM>(a, g, item);
 }
 
 }  // namespace amrb
