@@ -116,7 +116,7 @@ class ClockSampler:
 # ------------------------------------------------------------ the GPU arm --
 
 def algorithmic_stage_bytes(spec, esize):
-    """Bytes a stage must move per block (Sec. 3.1 Eq. 4 with Heun): stage 1
+    """Bytes a stage must move per block (Sec. 3.1 Eq. 5 with Heun): stage 1
     reads the derivative state's interior and face ghosts and writes the
     output; stage 2 also reads the previous state's interior."""
     N, V, d, ng = spec.N, spec.nvar, spec.ndim, spec.ng
@@ -282,7 +282,7 @@ def run_ours(args, rank, world, dist):
         extras["vanleer_hll"] = {"value": 2.0 * cells * args.steps * world / (msv * 1e-3), "ms_per_step": msv / args.steps}
         del fv
         torch.cuda.empty_cache()
-        # the paper's Rayleigh-Taylor case (Sec. 4.2; Tables 1 and 3 on H100):
+        # the paper's Rayleigh-Taylor case (Sec. 4.2; Tables 1 and 2 on H100):
         # 256^3, van Leer, Heun, CFL 0.5, gamma 5/3, gravity source
         rt = {}
         for bn, prec in ((32, 32), (16, 32), (8, 32), (16, 64)):
@@ -301,7 +301,7 @@ def run_ours(args, rank, world, dist):
             del fr
             torch.cuda.empty_cache()
         rt["context"] = ("paper, 1x H100, same case: FP64 1.37 / 1.30 / 1.10 and FP32 2.70 / 2.60 / 2.08 GCUPS "
-                         "for 32^3 / 16^3 / 8^3 blocks (Tables 1 and 3); flux scheme not stated there, Rusanov here")
+                         "for 32^3 / 16^3 / 8^3 blocks (Tables 1 and 2); flux scheme not stated there, Rusanov here")
         extras["rayleigh_taylor_vanleer"] = rt
         extras["batched_2d"] = run_batched(args, amr, torch, stream, barrier, world)
 
@@ -487,7 +487,7 @@ def run_amr_static(args, amr, torch, stream):
 def run_adaptive(args, amr, torch, stream, steps=500, every=10, train_until=200):
     """3D adaptive run: over-pressure sphere and a Mach-3 planar shock in a
     128^3 base domain of 16^3 blocks, up to 4 levels, regrid every 10 steps.
-    Run A: FP32, the criterion of Eq. 5 throughout.  Run B: FP32, the
+    Run A: FP32, the criterion of Eq. 12 throughout.  Run B: FP32, the
     criterion for the first 200 steps while collecting (features, flags),
     then the trained network's flags (criterion fallback below tau = 0.9).
     Run C: FP64, the criterion throughout -- the judge of both.  Reported:

@@ -5,9 +5,9 @@
  * and the block data on one GPU, and executes the per-time-step work of the
  * method of "foap4: adaptive mesh refinement with OpenACC, MPI, and p4est":
  * the ghost-cell pattern (same-level copies, fine-to-coarse restriction,
- * coarse-to-fine limited prolongation, physical boundaries; Sec. 2.5) and the
+ * coarse-to-fine limited prolongation, physical boundaries; Sec. 2.6) and the
  * explicit finite-volume Runge-Kutta update of the Euler equations with flux
- * fixing at refinement boundaries (Sec. 2.6, Sec. 3.1-3.5).
+ * fixing at refinement boundaries (Sec. 2.7, Sec. 3.1-3.5).
  *
  * Conventions shared by every call:
  *  - Every call returns an amr_status and never aborts the process.  The
@@ -20,7 +20,7 @@
  *    Pointers passed in are borrowed for the duration of the call only.
  *    Streams are owned by the caller; an amr_stream is a cudaStream_t (NULL =
  *    the legacy default stream).
- *  - Block data layout is Eq. 2 of the paper, uu(i, j, k, ivar, iblock) with
+ *  - Block data layout is Eq. 3 of the paper, uu(i, j, k, ivar, iblock) with
  *    i fastest and ghost layers included: element (i, j, k, v, b) of state
  *    slot s sits at index
  *        (((s * max_blocks + b) * n_var + v) * S + (k + ng)) * S + j + ng) * S + i + ng
@@ -61,7 +61,7 @@ typedef enum {
     AMR_BC_DATA = 3        /* Dirichlet values per boundary-face cell, amr_set_bc_data() */
 } amr_bc;
 
-/* Ghost-strip kinds by direction of data flow (Sec. 2.5). */
+/* Ghost-strip kinds by direction of data flow (Sec. 2.6). */
 typedef enum {
     AMR_GHOST_SRL = 0,     /* same refinement level: copy */
     AMR_GHOST_F2C = 1,     /* fine -> coarse: restriction into the coarse block's ghosts */
@@ -124,12 +124,12 @@ typedef enum { AMR_FLUX_RUSANOV = 0, AMR_FLUX_HLL = 1 } amr_flux;
  * lower tangential dimension); aux = boundary-face index for BC entries
  * (row of the bc_data array), else 0; src = -1 for BC.  Entries are sorted by
  * (kind, face, dst, offset) -- the paper sorts its index arrays by neighbour
- * type, face direction, receiving block and hanging offset (Sec. 2.5). */
+ * type, face direction, receiving block and hanging offset (Sec. 2.6). */
 typedef struct {
     int32_t kind, face, dst, src, offset, aux;
 } amr_ghost_entry;
 
-/* One forward-Euler sub-step of Eq. 4 (Sec. 3.1):
+/* One forward-Euler sub-step of Eq. 5 (Sec. 3.1):
  *   u(s_out) = w_dt * dt * F(u(s_deriv)) + sum_i w_prev[i] u(s_prev[i])
  * dt is the device-resident time step of the forest.  update_dt = 1 marks
  * the last stage of a step: the stage also reduces the CFL limit of its own
@@ -159,7 +159,7 @@ typedef struct {
 #define AMR_STEP_SSP43 16  /* optimal four-stage, third-order SSP RK instead
                               of Heun; n_states >= 3 */
 
-/* Refinement-criterion constants of Eq. 5 (Sec. 3.3).  The criterion is
+/* Refinement-criterion constants of Eq. 12 (Sec. 3.3).  The criterion is
  * evaluated on density and pressure; a cell's value is the larger one. */
 typedef struct {
     double c_refine, c_derefine, eps, eps_abs;
@@ -204,7 +204,7 @@ amr_status amr_n_blocks(const amr_forest *f, int64_t *n);
 amr_status amr_get_blocks(const amr_forest *f, int32_t *level, int64_t *coords, int64_t cap, int64_t *n);
 
 /* Classifies every block face as SRL / F2C / C2F / BC from the forest's face
- * connectivity and uploads the index lists to the device (Sec. 2.5: built on
+ * connectivity and uploads the index lists to the device (Sec. 2.6: built on
  * the CPU, executed on the GPU).  A no-op when the mesh revision has not
  * changed since the last build (Sec. 2.2 mesh revision number). */
 amr_status amr_build_ghost_pattern(amr_forest *f);
@@ -227,7 +227,7 @@ amr_status amr_get_state(const amr_forest *f, int s, void *dst, int on_device, a
  * is destroyed. */
 amr_status amr_state_ptr(const amr_forest *f, int s, void **ptr);
 
-/* Dirichlet values for the AMR_BC_DATA faces (Sec. 2.4, Eq. 3 bc_data):
+/* Dirichlet values for the AMR_BC_DATA faces (Sec. 2.4, Eq. 4 bc_data):
  * host array [n_bf][n_var][N^(d-1)] in double, n_bf = number of BC entries of
  * the current pattern in canonical order (row = entry's aux), face-cell index
  * with the lower tangential dimension fastest.  Must be set again after a
@@ -236,7 +236,7 @@ amr_status amr_set_bc_data(amr_forest *f, const double *values, int64_t n_values
 
 /* Fills the face ghost cells of state slot s: round 1 (SRL copies, physical
  * boundaries, F2C restriction), then round 2 (C2F limited prolongation, which
- * reads round-1 ghosts of the coarse blocks) -- Sec. 2.5.  Edge and corner
+ * reads round-1 ghosts of the coarse blocks) -- Sec. 2.6.  Edge and corner
  * ghost cells are not filled (Sec. 2.1). */
 amr_status amr_fill_ghosts(amr_forest *f, int s, amr_stream stream);
 
@@ -252,18 +252,18 @@ amr_status amr_get_dt(amr_forest *f, double *dt, amr_stream stream);
 /* Time step of every instance into dts[0 .. n_instances) (synchronises). */
 amr_status amr_get_dts(amr_forest *f, double *dts, amr_stream stream);
 
-/* One stage of Eq. 4 on every block: primitive reconstruction with the minmod
+/* One stage of Eq. 5 on every block: primitive reconstruction with the minmod
  * limiter, Rusanov fluxes with Einfeldt wave speeds, divergence, Runge-Kutta
- * combination (Sec. 3.2), then flux fixing at refinement boundaries (Sec. 2.6)
+ * combination (Sec. 3.2), then flux fixing at refinement boundaries (Sec. 2.7)
  * with the stage's time step w_dt * dt.  s_deriv's ghosts must be filled.
  * s_out may equal one of s_prev. */
 amr_status amr_advance_stage(amr_forest *f, const amr_stage *st, amr_stream stream);
 
-/* n_steps steps of Heun's method (Eq. 5-6) on slot 0 (slot 1 as the stage
+/* n_steps steps of Heun's method (Eq. 6-7) on slot 0 (slot 1 as the stage
  * state): fill ghosts, stage 1, fill ghosts, stage 2 with the dt update.
  * With AMR_STEP_SSP3 or AMR_STEP_RK4 the step is the three-stage SSP or the
  * classical four-stage Runge-Kutta method (Sec. 3.1 lists both), each stage
- * a sub-step of Eq. 4 (L = flux divergence with flux fixing):
+ * a sub-step of Eq. 5 (L = flux divergence with flux fixing):
  *   SSP3: u1 = u0 + dt L(u0); u2 = 3/4 u0 + 1/4 (u1 + dt L(u1));
  *         u0 <- 1/3 u0 + 2/3 (u2 + dt L(u2))                    (slots 1, 2)
  *   SSP43: u1 = u0 + dt/2 L(u0); u2 = u1 + dt/2 L(u1);
@@ -281,14 +281,14 @@ amr_status amr_advance_stage(amr_forest *f, const amr_stage *st, amr_stream stre
 amr_status amr_step(amr_forest *f, int n_steps, int flags, amr_stream stream);
 
 /* Integral of every conserved variable over the leaves of slot s, summed in
- * double on the device in a fixed order (Eq. 12), for instance 0 (n_var
+ * double on the device in a fixed order (Eq. 18), for instance 0 (n_var
  * values).  Synchronises `stream`. */
 amr_status amr_conserved(amr_forest *f, int s, double *sums, amr_stream stream);
 
 /* The same for every instance: sums[inst * n_var + v]. */
 amr_status amr_conserved_all(amr_forest *f, int s, double *sums, amr_stream stream);
 
-/* Refinement flags of slot s from the criterion of Eq. 5 (ghosts must be
+/* Refinement flags of slot s from the criterion of Eq. 12 (ghosts must be
  * filled): +1 refine, -1 derefine, 0 keep, per block.  Copied to flags_out
  * (host, n_blocks entries); synchronises `stream`. */
 amr_status amr_flag(amr_forest *f, int s, const amr_flag_params *prm, int8_t *flags_out, amr_stream stream);
@@ -318,7 +318,7 @@ amr_status amr_flag_and_regrid(amr_forest *f, const amr_flag_params *prm, const 
 amr_status amr_autotune(amr_forest *f, int *choice, double *best_ms, amr_stream stream);
 
 /* ---- learned refinement flags ------------------------------------------
- * A small network predicts the flags of the criterion of Eq. 5 (Sec. 3.3)
+ * A small network predicts the flags of the criterion of Eq. 12 (Sec. 3.3)
  * from pooled block data; the criterion stays as fallback for blocks the
  * network is unsure about and as the judge of its flags.  Network: F inputs
  * -> 64 -> 64 (GELU) -> 3 logits (derefine / keep / refine) -> softmax; the
@@ -359,7 +359,7 @@ amr_status amr_mlp_train(amr_mlp *m, const float *x, const int8_t *y, int64_t n,
                          double weight_decay, uint64_t seed, double *final_loss, amr_stream stream);
 
 /* Refinement flags of slot s from the model: the most probable class when
- * its probability is at least tau, else the criterion of Eq. 5 with `prm`
+ * its probability is at least tau, else the criterion of Eq. 12 with `prm`
  * (ghost cells of slot s are filled for those blocks).  flags_out: host,
  * one per block; *n_fallback = blocks that used the criterion. */
 amr_status amr_mlp_flags(amr_forest *f, amr_mlp *m, int s, const amr_flag_params *prm, double tau, int8_t *flags_out,
@@ -374,6 +374,40 @@ const char *amr_last_error(const amr_forest *f);
 
 /* Kernel launches issued by the library since the forest was created. */
 amr_status amr_launch_count(const amr_forest *f, int64_t *n);
+
+/* ---- checkpoint, restart and output --------------------------------------
+ * The configuration of instance `inst` as given at creation (the batch
+ * capacity is in f's max_blocks only through amr_n_blocks; here max_blocks
+ * is the instance's own).  Errors: AMR_EINVAL. */
+amr_status amr_get_config(const amr_forest *f, int inst, amr_config *out);
+
+/* Writes a checkpoint of f to the file `path`: per instance its
+ * configuration (allocation hooks excepted), its leaves and its dt, then
+ * state slot 0 of every block including ghost cells (host-only forests: the
+ * meshes only).  Binary, native byte order, versioned ("AMRCKPT1").
+ * Synchronises `stream`.  Errors: AMR_EINVAL (null argument), AMR_ESTATE
+ * (the file cannot be written), AMR_ECUDA. */
+amr_status amr_save(const amr_forest *f, const char *path, amr_stream stream);
+
+/* Creates a forest from a checkpoint written by amr_save: the saved meshes,
+ * configurations, dt and slot 0.  `opts` (may be NULL) supplies n_states,
+ * host_only and the allocation hooks (other fields are ignored); NULL keeps
+ * the saved n_states on the device with cudaMalloc.  Slots other than 0
+ * start zeroed.  Errors: AMR_EINVAL, AMR_ESTATE (unreadable, truncated or
+ * foreign file, or a host-only checkpoint loaded onto the device),
+ * AMR_ECAPACITY, AMR_ENOMEM, AMR_ECUDA. */
+amr_status amr_load(const char *path, const amr_config *opts, amr_forest **out, amr_stream stream);
+
+/* Writes slot s in the XDMF format the paper uses for output (Sec. 2.8):
+ * `base`.bin holds, block after block and variable after variable, the
+ * N^d interior cells of each block (i fastest) in the forest's precision;
+ * `base`.xmf describes every block as a uniform grid (origin and spacing of
+ * its level) whose cell-centred attributes (rho, mx, my[, mz], E) point into
+ * the binary file by byte offset, one spatial collection per instance.  The
+ * data file name is written without directories, so keep both files
+ * together.  Synchronises `stream`.  Errors: AMR_EINVAL, AMR_ESTATE (file),
+ * AMR_ECUDA. */
+amr_status amr_write_xdmf(const amr_forest *f, int s, const char *base, amr_stream stream);
 
 /* Largest block count amr_conserved_static() accepts. */
 #define AMR_STATIC_MAX_BLOCKS 65536

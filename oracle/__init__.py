@@ -191,7 +191,7 @@ class Mesh:
             raise RuntimeError("oracle: ghost fill failed")
 
     def stage(self, ud, uo, prev, weights, dt_eff) -> int:
-        """uo = dt_eff F(ud) + sum_i weights[i] prev[i] (Eq. 4), with flux fixing."""
+        """uo = dt_eff F(ud) + sum_i weights[i] prev[i] (Eq. 5), with flux fixing."""
         arr = (C.c_void_p * max(1, len(prev)))(*[p.ctypes.data for p in prev])
         w = np.ascontiguousarray(weights, dtype=np.float64)
         return int(self._lib.orc_stage(self._h, _ptr(ud), _ptr(uo), len(prev),
@@ -222,7 +222,7 @@ class Mesh:
 
 
 def heun_step(mesh: Mesh, u0: np.ndarray, u1: np.ndarray, dt: float | None = None, bc_data=None) -> float:
-    """One step of Heun's method, Eq. 5-6, with ghost fills before each stage.
+    """One step of Heun's method, Eq. 6-7, with ghost fills before each stage.
 
     dt defaults to CFL / max speed of u0 (Sec. 3.2).  Returns the dt used."""
     mesh.fill_ghosts(u0, bc_data)
@@ -239,7 +239,7 @@ def heun_step(mesh: Mesh, u0: np.ndarray, u1: np.ndarray, dt: float | None = Non
 def rk_combine(L, u: np.ndarray, dt: float, scheme: str) -> np.ndarray:
     """One step of an explicit Runge-Kutta method for u' = L(u) (Sec. 3.1
     lists Heun's method and higher-order SSP and classical schemes):
-      heun  u1 = u + dt L(u);  u+ = (u + u1 + dt L(u1)) / 2            (Eq. 5-6)
+      heun  u1 = u + dt L(u);  u+ = (u + u1 + dt L(u1)) / 2            (Eq. 6-7)
       ssp3  Shu & Osher's three-stage SSP method, in their convex form:
             u1 = u + dt L(u);  u2 = 3/4 u + 1/4 (u1 + dt L(u1));
             u+ = 1/3 u + 2/3 (u2 + dt L(u2))
@@ -272,7 +272,7 @@ def rk_combine(L, u: np.ndarray, dt: float, scheme: str) -> np.ndarray:
 
 
 def flux_operator(mesh: Mesh, bc_data=None):
-    """L(u): ghost fill, then the flux divergence of Eq. 4 with flux fixing
+    """L(u): ghost fill, then the flux divergence of Eq. 5 with flux fixing
     (one stage with no previous states and dt_eff = 1)."""
     def L(u):
         mesh.fill_ghosts(u, bc_data)

@@ -26,7 +26,7 @@
  *   - Rusanov flux with the Einfeldt speed |u_roe| + d_roe (Sec. 3.2-3.5);
  *   - dt = CFL / max over leaf cells of sum_d (|v_d| + c) / dx_d (Sec. 3.2);
  *   - flux fixing is applied after every Runge-Kutta stage with that stage's
- *     time step (Sec. 2.6).
+ *     time step (Sec. 2.7).
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -42,7 +42,7 @@
 
 /* Mirrors the problem statement of Sec. 2.2-2.4: a brick of ntrees[0] x
  * ntrees[1] (x ntrees[2]) trees (Sec. 2.2), blocks of N^d cells plus ng ghost
- * layers (Sec. 2.3, Eq. 2), boundary type per face direction in the order
+ * layers (Sec. 2.3, Eq. 3), boundary type per face direction in the order
  * -x,+x,-y,+y,-z,+z (Sec. 2.4). */
 typedef struct {
     int ndim, N, ng, nvar;
@@ -374,7 +374,7 @@ static int64_t ncell(const orc_params *p)
 }
 
 /* Flat offset of cell (i,j,k) (interior 0..N-1, ghosts outside) of variable v
- * of block b, layout uu(i,j,k,ivar,iblock) of Eq. 2 with i fastest. */
+ * of block b, layout uu(i,j,k,ivar,iblock) of Eq. 3 with i fastest. */
 static int64_t at(const orc_params *p, int b, int v, int i, int j, int k)
 {
     int64_t s = SIDE(p);
@@ -438,7 +438,7 @@ static void tangential(int ndim, int nd, int t[2])
 }
 
 /* ------------------------------------------------------------------------ */
-/* Ghost-cell pattern by brute force (Sec. 2.5): every ghost cell of every    */
+/* Ghost-cell pattern by brute force (Sec. 2.6): every ghost cell of every    */
 /* face strip is located, and the strips are classified as SRL / F2C / C2F /  */
 /* BC from the level of the leaf that holds them.                            */
 /* Canonical export: one entry per (receiving block, face) -- per source      */
@@ -539,7 +539,7 @@ int64_t orc_pattern(const orc_mesh *m, int32_t *out, int64_t cap)
 
 /* Index of the boundary face (block b, face f) among all boundary faces in
  * the order (face direction, block), i.e. the order of the bc_data array
- * (Sec. 2.4, Eq. 3). */
+ * (Sec. 2.4, Eq. 4). */
 static int boundary_face_index(const orc_mesh *m, int b, int f)
 {
     const orc_params *p = &m->p;
@@ -603,7 +603,7 @@ static double prolong_cell(const orc_params *p, const double *u, int cb, int v, 
 }
 
 /* ------------------------------------------------------------------------ */
-/* Ghost fill, one cell at a time, in the two rounds of Sec. 2.5:             */
+/* Ghost fill, one cell at a time, in the two rounds of Sec. 2.6:             */
 /*   R1: same level copies, physical boundaries, fine-to-coarse restriction;  */
 /*   R2: coarse-to-fine limited prolongation (reads R1 ghosts).               */
 /* Only face ghost cells are filled (Sec. 2.1: no edge or corner ghosts).     */
@@ -684,7 +684,7 @@ int orc_fill_ghosts(const orc_mesh *m, double *u, const double *bc_data)
 }
 
 /* ------------------------------------------------------------------------ */
-/* Euler physics (Sec. 3.5, Eq. 8-10)                                        */
+/* Euler physics (Sec. 3.5, Eq. 14-16)                                        */
 /* conservative U = (rho, rho v_0..v_{d-1}, E); primitive w = (rho, v, p)     */
 /* ------------------------------------------------------------------------ */
 
@@ -806,13 +806,13 @@ double orc_limited_slope(int lim, double a, double b) { return limited_slope(lim
 void orc_face_flux(const orc_params *p, int n, const double *wL, const double *wR, double *F) { face_flux(p, n, wL, wR, F); }
 
 /* ------------------------------------------------------------------------ */
-/* One forward-Euler sub-step of Eq. 4 (Sec. 3.1) with the finite-volume      */
+/* One forward-Euler sub-step of Eq. 5 (Sec. 3.1) with the finite-volume      */
 /* steps of Sec. 3.2:                                                        */
 /*   uo = dt_eff * F(ud) + sum_i w_i up_i                                    */
 /* F: primitives on interior + face ghosts; MUSCL face values with the      */
 /* limiter; Rusanov or HLL fluxes with Einfeldt speeds; divergence.  Then    */
 /* flux fixing at refinement                                                 */
-/* boundaries (Sec. 2.6): the coarse cells next to a face shared with finer  */
+/* boundaries (Sec. 2.7): the coarse cells next to a face shared with finer  */
 /* blocks get dt_eff/dx (F_coarse - mean F_fine) with the face's sign.        */
 /* ud must have its face ghosts filled.  uo may alias one of up (each output  */
 /* cell depends only on the same cell of up).                                */
@@ -923,7 +923,7 @@ int orc_stage(const orc_mesh *m, const double *ud, double *uo, int nprev,
         free(wp);
     }
 
-    /* RK combination of Eq. 4 on interior cells */
+    /* RK combination of Eq. 5 on interior cells */
 #pragma omp parallel for schedule(static)
     for (int b = 0; b < m->n; b++) {
         int kr = (D == 3) ? N : 1;
@@ -938,7 +938,7 @@ int orc_stage(const orc_mesh *m, const double *ud, double *uo, int nprev,
                     }
     }
 
-    /* flux fixing at refinement boundaries (Sec. 2.6), faces in order -x..+z */
+    /* flux fixing at refinement boundaries (Sec. 2.7), faces in order -x..+z */
     for (int b = 0; b < m->n; b++) {
         int lev = m->lev[b];
         for (int f = 0; f < 2 * D; f++) {
@@ -992,7 +992,7 @@ int orc_stage(const orc_mesh *m, const double *ud, double *uo, int nprev,
 
 /* ------------------------------------------------------------------------ */
 /* CFL time-step limit (Sec. 3.2 step 2c): max over interior leaf cells of    */
-/* sum_d (|v_d| + c) / dx_d, with c = sqrt(gamma p / rho) (Eq. 10).           */
+/* sum_d (|v_d| + c) / dx_d, with c = sqrt(gamma p / rho) (Eq. 16).           */
 /* dt = cfl / that maximum.                                                  */
 /* ------------------------------------------------------------------------ */
 
@@ -1018,7 +1018,7 @@ double orc_max_speed(const orc_mesh *m, const double *u)
     return best;
 }
 
-/* Integral of every conserved variable over the leaves (Eq. 12 summed over
+/* Integral of every conserved variable over the leaves (Eq. 18 summed over
  * the domain), accumulated in long double. */
 void orc_conserved(const orc_mesh *m, const double *u, double *sums)
 {
@@ -1040,7 +1040,7 @@ void orc_conserved(const orc_mesh *m, const double *u, double *sums)
 }
 
 /* ------------------------------------------------------------------------ */
-/* Refinement flags from the simplified Lohner estimator (Sec. 3.3, Eq. 5):   */
+/* Refinement flags from the simplified Lohner estimator (Sec. 3.3, Eq. 12):   */
 /*   E_n = |u_{n-1} - 2u_n + u_{n+1}| /                                      */
 /*         (eps_abs + |u_n - u_{n-1}| + |u_{n+1} - u_n| + eps u*),             */
 /*   u*  = |u_{n-1}| + 2|u_n| + |u_{n+1}|,  |E| = sqrt(sum_n E_n^2),          */

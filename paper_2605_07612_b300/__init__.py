@@ -31,7 +31,7 @@ EXPORTED = [
     "amr_launch_count", "amr_conserved_static", "amr_create_batch", "amr_n_instances", "amr_instance_blocks",
     "amr_get_dts", "amr_conserved_all", "amr_autotune", "amr_features", "amr_mlp_create", "amr_mlp_destroy",
     "amr_mlp_n_params", "amr_mlp_get_params", "amr_mlp_set_params", "amr_mlp_forward", "amr_mlp_gradient",
-    "amr_mlp_train", "amr_mlp_flags",
+    "amr_mlp_train", "amr_mlp_flags", "amr_get_config", "amr_save", "amr_load", "amr_write_xdmf",
 ]
 
 
@@ -91,6 +91,10 @@ def load(build_if_missing: bool = True):
     P, vp, i64 = C.POINTER, C.c_void_p, C.c_int64
     sig = {
         "amr_create_forest": [P(Config), C.c_int, P(vp)],
+        "amr_get_config": [vp, C.c_int, P(Config)],
+        "amr_save": [vp, C.c_char_p, vp],
+        "amr_load": [C.c_char_p, vp, P(vp), vp],
+        "amr_write_xdmf": [vp, C.c_int, C.c_char_p, vp],
         "amr_destroy_forest": [vp],
         "amr_n_blocks": [vp, P(i64)],
         "amr_get_blocks": [vp, vp, vp, i64, P(i64)],
@@ -144,6 +148,18 @@ def _stream_ptr(stream):
     if isinstance(stream, int):
         return stream
     return int(stream.cuda_stream)
+
+
+def spec_from_config(c: Config):
+    """The synth.MeshSpec of a configuration (inverse of config_from_spec)."""
+    import synth
+    D = int(c.ndim)
+    return synth.MeshSpec(ndim=D, N=int(c.block_n), ng=int(c.n_ghost), ntrees=tuple(int(c.ntrees[d]) for d in range(3)),
+                          periodic=tuple(int(c.periodic[d]) for d in range(3)), lo=tuple(float(c.lo[d]) for d in range(3)),
+                          length=tuple(float(c.len[d]) for d in range(3)), max_level=int(c.max_level),
+                          gamma=float(c.gamma), cfl=float(c.cfl), bc_type=tuple(int(c.bc[f]) for f in range(6)),
+                          bc_val=tuple(tuple(float(c.bc_val[f][v]) for v in range(8)) for f in range(6)),
+                          limiter=int(c.limiter), flux=int(c.flux), gravity=tuple(float(c.gravity[d]) for d in range(3)))
 
 
 def config_from_spec(spec, max_blocks, n_states=2, precision=64, host_only=False) -> Config:
@@ -214,6 +230,51 @@ class Forest:
         if st != AMR_OK:
             raise AmrError(st, "amr_create_forest")
         self.h = h
+
+    # ---- checkpoint, restart, output
+    def save(self, path, stream=None):
+        """Checkpoint: meshes, configurations, dt and slot 0 (amr_save)."""
+        self._check(self.lib.amr_save(self.h, os.fsencode(path), _stream_ptr(stream)), "amr_save")
+
+    @classmethod
+    def load(cls, path, n_states=None, host_only=False, stream=None) -> "Forest":
+        """Restart from a checkpoint written by save() (amr_load)."""
+        lib = load()
+        opts = None
+        if n_states is not None or host_only:
+            opts = Config()
+            opts.n_states = int(n_states) if n_states is not None else 2
+            opts.host_only = 1 if host_only else 0
+        h = C.c_void_p()
+        st = lib.amr_load(os.fsencode(path), C.byref(opts) if opts is not None else None, C.byref(h), _stream_ptr(stream))
+        if st != AMR_OK:
+            raise AmrError(st, "amr_load(%s)" % path)
+        self = cls.__new__(cls)
+        self.lib = lib
+        self.h = h
+        n = C.c_int()
+        self._check(lib.amr_n_instances(h, C.byref(n)), "amr_n_instances")
+        self.specs = []
+        for i in range(n.value):
+            c = Config()
+            self._check(lib.amr_get_config(h, i, C.byref(c)), "amr_get_config")
+            self.specs.append(spec_from_config(c))
+        self.spec = self.specs[0]
+        self.cfg = c
+        self.precision = int(c.precision)
+        self.dtype = np.float64 if self.precision == 64 else np.float32
+        self.n_states = int(c.n_states)
+        self.max_blocks = int(c.max_blocks)
+        return self
+
+    def get_config(self, inst=0) -> Config:
+        c = Config()
+        self._check(self.lib.amr_get_config(self.h, int(inst), C.byref(c)), "amr_get_config")
+        return c
+
+    def write_xdmf(self, s, base, stream=None):
+        """XDMF output of slot s: base.xmf (grid description) and base.bin."""
+        self._check(self.lib.amr_write_xdmf(self.h, int(s), os.fsencode(base), _stream_ptr(stream)), "amr_write_xdmf")
 
     @property
     def n_instances(self) -> int:

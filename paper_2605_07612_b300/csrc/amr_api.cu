@@ -377,9 +377,9 @@ struct TransferFn {
     }
 };
 
-// One time step as a sequence of Eq. 4 sub-steps, each preceded by the ghost
+// One time step as a sequence of Eq. 5 sub-steps, each preceded by the ghost
 // fill of the slot it differentiates; the last one updates dt.
-//   Heun (Eq. 5-6):  u1 = u0 + dt L(u0);  u0' = (u0 + u1 + dt L(u1)) / 2
+//   Heun (Eq. 6-7):  u1 = u0 + dt L(u0);  u0' = (u0 + u1 + dt L(u1)) / 2
 //   SSP3 (Shu-Osher): u1 = u0 + dt L(u0);  u2 = 3/4 u0 + 1/4 (u1 + dt L(u1));
 //                    u0' = 1/3 u0 + 2/3 (u2 + dt L(u2))
 //   SSP43 (four stages, third order): u1 = u0 + dt/2 L(u0);
@@ -918,7 +918,7 @@ amr_status amr_mlp_flags(amr_forest *f, amr_mlp *m, int s, const amr_flag_params
     CU(cudaGetLastError());
     CU(cudaMemcpyAsync(flags_out, f->mflags.p, size_t(nb), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
-    // low-confidence blocks fall back to the criterion of Eq. 5
+    // low-confidence blocks fall back to the criterion of Eq. 12
     std::vector<int32_t> list;
     for (int64_t b = 0; b < nb; ++b)
         if (flags_out[b] == 2) list.push_back(int32_t(b));
@@ -983,6 +983,327 @@ amr_status amr_autotune(amr_forest *f, int *choice, double *best_ms, amr_stream 
     if (best_ms) *best_ms = best_t;
     return AMR_OK;
 }
+
+}  // extern "C"
+
+// ------------------------------------------------------ checkpoint and output
+namespace {
+
+constexpr char kCkptMagic[8] = {'A', 'M', 'R', 'C', 'K', 'P', 'T', '1'};
+constexpr uint32_t kCkptVersion = 1;
+
+struct CkptHead {
+    char magic[8];
+    uint32_t version, n_inst;
+    int32_t precision, ndim, block_n, n_ghost, n_var, n_states, host_only, limiter, flux, pad;
+    double gamma, gravity[3];
+    int64_t n_blocks;
+};
+struct CkptInst {
+    int32_t ntrees[3], periodic[3], max_level, max_blocks, bc[6];
+    double lo[3], len[3], cfl, bc_val[6][8], dt;
+    int64_t n_leaves;
+};
+struct CkptLeaf {
+    int32_t lev, pad;
+    int64_t g[3];
+};
+
+struct CFile {
+    FILE *fp = nullptr;
+    ~CFile() {
+        if (fp) fclose(fp);
+    }
+};
+
+// slot s of every block, copied to the host
+amr_status slot_to_host(amr_forest *f, int s, std::vector<char> &out, cudaStream_t st) {
+    out.resize(size_t(nblocks(f)) * f->block_bytes);
+    if (!out.empty()) CU(cudaMemcpyAsync(out.data(), slot_ptr(f, s), out.size(), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    return AMR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+amr_status amr_get_config(const amr_forest *f, int inst, amr_config *out) {
+    if (!f || !out || inst < 0 || inst >= n_inst(f)) return AMR_EINVAL;
+    *out = f->icfg[size_t(inst)];
+    return AMR_OK;
+}
+
+amr_status amr_save(const amr_forest *fc, const char *path, amr_stream stream) {
+    if (!fc || !path) return AMR_EINVAL;
+    amr_forest *f = const_cast<amr_forest *>(fc);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int ni = n_inst(f);
+    std::vector<double> dts(size_t(ni), 0.0);
+    std::vector<char> state;
+    if (!f->cfg.host_only) {
+        std::vector<DevScalars> sc(static_cast<size_t>(ni));
+        CU(cudaMemcpyAsync(sc.data(), f->sc.p, sizeof(DevScalars) * size_t(ni), cudaMemcpyDeviceToHost, st));
+        amr_status r = slot_to_host(f, 0, state, st);
+        if (r != AMR_OK) return r;
+        for (int i = 0; i < ni; ++i) dts[size_t(i)] = sc[size_t(i)].dt;
+    }
+    CFile out;
+    out.fp = fopen(path, "wb");
+    if (!out.fp) return fail(f, AMR_ESTATE, "cannot open %s for writing", path);
+    CkptHead h{};
+    memcpy(h.magic, kCkptMagic, 8);
+    h.version = kCkptVersion;
+    h.n_inst = uint32_t(ni);
+    const amr_config &c0 = f->cfg;
+    h.precision = c0.precision;
+    h.ndim = c0.ndim;
+    h.block_n = c0.block_n;
+    h.n_ghost = c0.n_ghost;
+    h.n_var = c0.n_var;
+    h.n_states = c0.n_states;
+    h.host_only = c0.host_only;
+    h.limiter = c0.limiter;
+    h.flux = c0.flux;
+    h.gamma = c0.gamma;
+    for (int d = 0; d < 3; ++d) h.gravity[d] = c0.gravity[d];
+    h.n_blocks = nblocks(f);
+    bool ok = fwrite(&h, sizeof h, 1, out.fp) == 1;
+    for (int i = 0; i < ni && ok; ++i) {
+        const amr_config &c = f->icfg[size_t(i)];
+        CkptInst r{};
+        for (int d = 0; d < 3; ++d) {
+            r.ntrees[d] = c.ntrees[d];
+            r.periodic[d] = c.periodic[d];
+            r.lo[d] = c.lo[d];
+            r.len[d] = c.len[d];
+        }
+        r.max_level = c.max_level;
+        r.max_blocks = c.max_blocks;
+        for (int q = 0; q < 6; ++q) {
+            r.bc[q] = c.bc[q];
+            for (int v = 0; v < 8; ++v) r.bc_val[q][v] = c.bc_val[q][v];
+        }
+        r.cfl = c.cfl;
+        r.dt = dts[size_t(i)];
+        const std::vector<Leaf> &L = f->inst[size_t(i)].leaves;
+        r.n_leaves = int64_t(L.size());
+        ok = fwrite(&r, sizeof r, 1, out.fp) == 1;
+        std::vector<CkptLeaf> lv(L.size());
+        for (size_t b = 0; b < L.size(); ++b) {
+            lv[b].lev = L[b].lev;
+            for (int d = 0; d < 3; ++d) lv[b].g[d] = L[b].g[d];
+        }
+        if (ok && !lv.empty()) ok = fwrite(lv.data(), sizeof(CkptLeaf), lv.size(), out.fp) == lv.size();
+    }
+    if (ok && !state.empty()) ok = fwrite(state.data(), 1, state.size(), out.fp) == state.size();
+    if (!ok || fflush(out.fp) != 0) return fail(f, AMR_ESTATE, "short write to %s", path);
+    return AMR_OK;
+}
+
+amr_status amr_load(const char *path, const amr_config *opts, amr_forest **out, amr_stream stream) {
+    if (!path || !out) return AMR_EINVAL;
+    *out = nullptr;
+    CFile in;
+    in.fp = fopen(path, "rb");
+    if (!in.fp) return AMR_ESTATE;
+    CkptHead h{};
+    if (fread(&h, sizeof h, 1, in.fp) != 1 || memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != kCkptVersion ||
+        h.n_inst < 1 || h.n_inst > (1u << 20) || h.n_blocks < 0)
+        return AMR_ESTATE;
+    const int ni = int(h.n_inst);
+    std::vector<amr_config> cfgs(static_cast<size_t>(ni));
+    std::vector<double> dts(static_cast<size_t>(ni));
+    std::vector<std::vector<Leaf>> leaves(static_cast<size_t>(ni));
+    const int host_only = opts ? opts->host_only : 0;
+    if (!host_only && h.host_only) return AMR_ESTATE;   // a mesh-only checkpoint has no state
+    int64_t total = 0;
+    for (int i = 0; i < ni; ++i) {
+        CkptInst r{};
+        if (fread(&r, sizeof r, 1, in.fp) != 1 || r.n_leaves < 1 || r.n_leaves > (int64_t(1) << 31)) return AMR_ESTATE;
+        amr_config &c = cfgs[size_t(i)];
+        c = amr_config{};
+        c.ndim = h.ndim;
+        c.block_n = h.block_n;
+        c.n_ghost = h.n_ghost;
+        c.n_var = h.n_var;
+        c.precision = h.precision;
+        c.gamma = h.gamma;
+        c.limiter = h.limiter;
+        c.flux = h.flux;
+        for (int d = 0; d < 3; ++d) {
+            c.gravity[d] = h.gravity[d];
+            c.ntrees[d] = r.ntrees[d];
+            c.periodic[d] = r.periodic[d];
+            c.lo[d] = r.lo[d];
+            c.len[d] = r.len[d];
+        }
+        c.max_level = r.max_level;
+        c.max_blocks = r.max_blocks;
+        c.cfl = r.cfl;
+        for (int q = 0; q < 6; ++q) {
+            c.bc[q] = r.bc[q];
+            for (int v = 0; v < 8; ++v) c.bc_val[q][v] = r.bc_val[q][v];
+        }
+        c.n_states = opts ? opts->n_states : h.n_states;
+        c.host_only = host_only;
+        if (opts) {
+            c.dev_alloc = opts->dev_alloc;
+            c.dev_free = opts->dev_free;
+            c.alloc_ctx = opts->alloc_ctx;
+        }
+        dts[size_t(i)] = r.dt;
+        std::vector<CkptLeaf> lv(size_t(r.n_leaves));
+        if (fread(lv.data(), sizeof(CkptLeaf), lv.size(), in.fp) != lv.size()) return AMR_ESTATE;
+        std::vector<Leaf> &L = leaves[size_t(i)];
+        L.resize(lv.size());
+        for (size_t b = 0; b < lv.size(); ++b) {
+            if (lv[b].lev < 0 || lv[b].lev > c.max_level) return AMR_ESTATE;
+            L[b].lev = lv[b].lev;
+            for (int d = 0; d < 3; ++d) {
+                const int64_t E = int64_t(d < c.ndim ? c.ntrees[d] : 1) << (d < c.ndim ? lv[b].lev : 0);
+                const int64_t x = d < c.ndim ? lv[b].g[d] : 0;
+                if (x < 0 || x >= E) return AMR_ESTATE;
+                L[b].g[d] = x;
+            }
+        }
+        if (int64_t(L.size()) > c.max_blocks) return AMR_ECAPACITY;
+        total += int64_t(L.size());
+    }
+    if (total != h.n_blocks) return AMR_ESTATE;
+    std::vector<int> levels(size_t(ni), 0);
+    amr_forest *f = nullptr;
+    amr_status r = amr_create_batch(cfgs.data(), levels.data(), ni, &f);
+    if (r != AMR_OK) return r;
+    for (int i = 0; i < ni; ++i) {
+        std::vector<Leaf> saved = leaves[size_t(i)];
+        f->inst[size_t(i)].assign(std::move(leaves[size_t(i)]));
+        const std::vector<Leaf> &now = f->inst[size_t(i)].leaves;
+        bool same = now.size() == saved.size();
+        for (size_t b = 0; same && b < now.size(); ++b)
+            same = now[b].lev == saved[b].lev && now[b].g[0] == saved[b].g[0] && now[b].g[1] == saved[b].g[1] &&
+                   now[b].g[2] == saved[b].g[2];
+        if (!same) {   // not a leaf list this library wrote (block order)
+            amr_destroy_forest(f);
+            return AMR_ESTATE;
+        }
+    }
+    set_offsets(f);
+    ++f->revision;
+    if ((r = upload_pattern(f)) != AMR_OK) {
+        amr_destroy_forest(f);
+        return r;
+    }
+    if (!host_only) {
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        std::vector<char> state(size_t(total) * f->block_bytes);
+        std::vector<DevScalars> sc(static_cast<size_t>(ni));
+        bool ok = h.host_only == 0 && (state.empty() || fread(state.data(), 1, state.size(), in.fp) == state.size());
+        if (ok && !state.empty()) ok = cudaMemcpyAsync(slot_ptr(f, 0), state.data(), state.size(), cudaMemcpyHostToDevice, st) == cudaSuccess;
+        if (ok) ok = cudaMemcpyAsync(sc.data(), f->sc.p, sizeof(DevScalars) * size_t(ni), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+                     cudaStreamSynchronize(st) == cudaSuccess;
+        for (int i = 0; ok && i < ni; ++i) sc[size_t(i)].dt = dts[size_t(i)];
+        if (ok) ok = cudaMemcpyAsync(f->sc.p, sc.data(), sizeof(DevScalars) * size_t(ni), cudaMemcpyHostToDevice, st) == cudaSuccess &&
+                     cudaStreamSynchronize(st) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            amr_destroy_forest(f);
+            return AMR_ESTATE;
+        }
+    }
+    *out = f;
+    return AMR_OK;
+}
+
+amr_status amr_write_xdmf(const amr_forest *fc, int s, const char *base, amr_stream stream) {
+    if (!fc || !base || !valid_slot(fc, s)) return AMR_EINVAL;
+    amr_forest *f = const_cast<amr_forest *>(fc);
+    NEED_DEVICE(f);
+    std::vector<char> state;
+    amr_status r = slot_to_host(f, s, state, static_cast<cudaStream_t>(stream));
+    if (r != AMR_OK) return r;
+    const int D = f->cfg.ndim, N = f->cfg.block_n, V = f->cfg.n_var;
+    const int64_t S = f->geom.S, ng = f->cfg.n_ghost;
+    const int64_t nint = D == 3 ? int64_t(N) * N * N : int64_t(N) * N;
+    const size_t es = size_t(f->esize);
+    const std::string bin = std::string(base) + ".bin", xmf = std::string(base) + ".xmf";
+    std::string binname = bin;
+    const size_t slash = binname.find_last_of('/');
+    if (slash != std::string::npos) binname = binname.substr(slash + 1);
+    {
+        CFile out;
+        out.fp = fopen(bin.c_str(), "wb");
+        if (!out.fp) return fail(f, AMR_ESTATE, "cannot open %s", bin.c_str());
+        std::vector<char> buf(size_t(nint) * es);
+        for (int64_t b = 0; b < nblocks(f); ++b)
+            for (int v = 0; v < V; ++v) {
+                const char *blk = state.data() + size_t(b) * f->block_bytes + size_t(v) * size_t(f->geom.ncell) * es;
+                size_t o = 0;
+                for (int k = 0; k < (D == 3 ? N : 1); ++k)
+                    for (int j = 0; j < N; ++j) {
+                        const int64_t row = ((D == 3 ? k + ng : 0) * S + (j + ng)) * S + ng;
+                        memcpy(buf.data() + o, blk + size_t(row) * es, size_t(N) * es);
+                        o += size_t(N) * es;
+                    }
+                if (fwrite(buf.data(), 1, buf.size(), out.fp) != buf.size()) return fail(f, AMR_ESTATE, "short write to %s", bin.c_str());
+            }
+    }
+    CFile out;
+    out.fp = fopen(xmf.c_str(), "w");
+    if (!out.fp) return fail(f, AMR_ESTATE, "cannot open %s", xmf.c_str());
+    static const char *names3[5] = {"rho", "mx", "my", "mz", "E"};
+    static const char *names2[4] = {"rho", "mx", "my", "E"};
+    const char **names = D == 3 ? names3 : names2;
+    // co-rectilinear grids: dimensions (node counts), origin and spacing are
+    // all listed slowest dimension first (z, y, x)
+    fprintf(out.fp, "<?xml version=\"1.0\" ?>\n<Xdmf Version=\"2.0\">\n <Domain>\n");
+    int64_t b = 0;
+    for (int i = 0; i < n_inst(f); ++i) {
+        const amr_config &c = f->icfg[size_t(i)];
+        fprintf(out.fp, "  <Grid Name=\"instance%d\" GridType=\"Collection\" CollectionType=\"Spatial\">\n", i);
+        for (const Leaf &l : f->inst[size_t(i)].leaves) {
+            double org[3], dx[3];
+            for (int d = 0; d < D; ++d) {
+                dx[d] = c.len[d] / double(c.ntrees[d]) / (double(N) * double(int64_t(1) << l.lev));
+                org[d] = c.lo[d] + double(l.g[d]) * double(N) * dx[d];
+            }
+            fprintf(out.fp, "   <Grid Name=\"b%lld\" GridType=\"Uniform\">\n", (long long)b);
+            if (D == 3) {
+                fprintf(out.fp, "    <Topology TopologyType=\"3DCoRectMesh\" Dimensions=\"%d %d %d\"/>\n", N + 1, N + 1, N + 1);
+                fprintf(out.fp, "    <Geometry GeometryType=\"ORIGIN_DXDYDZ\">\n");
+                fprintf(out.fp, "     <DataItem Dimensions=\"3\" Format=\"XML\">%.17g %.17g %.17g</DataItem>\n", org[2], org[1], org[0]);
+                fprintf(out.fp, "     <DataItem Dimensions=\"3\" Format=\"XML\">%.17g %.17g %.17g</DataItem>\n", dx[2], dx[1], dx[0]);
+            } else {
+                fprintf(out.fp, "    <Topology TopologyType=\"2DCoRectMesh\" Dimensions=\"%d %d\"/>\n", N + 1, N + 1);
+                fprintf(out.fp, "    <Geometry GeometryType=\"ORIGIN_DXDY\">\n");
+                fprintf(out.fp, "     <DataItem Dimensions=\"2\" Format=\"XML\">%.17g %.17g</DataItem>\n", org[1], org[0]);
+                fprintf(out.fp, "     <DataItem Dimensions=\"2\" Format=\"XML\">%.17g %.17g</DataItem>\n", dx[1], dx[0]);
+            }
+            fprintf(out.fp, "    </Geometry>\n");
+            for (int v = 0; v < V; ++v) {
+                const long long seek = (long long)((b * V + v) * nint) * (long long)es;
+                fprintf(out.fp, "    <Attribute Name=\"%s\" AttributeType=\"Scalar\" Center=\"Cell\">\n", names[v]);
+                if (D == 3)
+                    fprintf(out.fp, "     <DataItem Dimensions=\"%d %d %d\"", N, N, N);
+                else
+                    fprintf(out.fp, "     <DataItem Dimensions=\"%d %d\"", N, N);
+                fprintf(out.fp, " NumberType=\"Float\" Precision=\"%d\" Format=\"Binary\" Endian=\"Little\" Seek=\"%lld\">%s</DataItem>\n",
+                        int(es), seek, binname.c_str());
+                fprintf(out.fp, "    </Attribute>\n");
+            }
+            fprintf(out.fp, "   </Grid>\n");
+            ++b;
+        }
+        fprintf(out.fp, "  </Grid>\n");
+    }
+    fprintf(out.fp, " </Domain>\n</Xdmf>\n");
+    if (ferror(out.fp) || fflush(out.fp) != 0) return fail(f, AMR_ESTATE, "short write to %s", xmf.c_str());
+    return AMR_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
 
 const char *amr_last_error(const amr_forest *f) { return f ? f->err.c_str() : "null forest"; }
 

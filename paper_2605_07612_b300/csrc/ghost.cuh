@@ -1,4 +1,4 @@
-// Ghost-pattern executor (Sec. 2.5).  One warp per pattern entry ("strip");
+// Ghost-pattern executor (Sec. 2.6).  One warp per pattern entry ("strip");
 // the lanes walk the strip's ghost cells with x fastest so that both the
 // gather and the scatter are coalesced along rows.  Round 1 executes SRL,
 // F2C and BC entries (they read interior cells only); round 2 executes C2F

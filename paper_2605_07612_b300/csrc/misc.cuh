@@ -1,6 +1,6 @@
-// Kernels around the stage: flux fixing (Sec. 2.6), the CFL time step
-// (Sec. 3.2), conserved integrals (Eq. 12), the refinement criterion of
-// Eq. 5 (Sec. 3.3) and the data transfer after a mesh change (Sec. 2.2).
+// Kernels around the stage: flux fixing (Sec. 2.7), the CFL time step
+// (Sec. 3.2), conserved integrals (Eq. 18), the refinement criterion of
+// Eq. 12 (Sec. 3.3) and the data transfer after a mesh change (Sec. 2.2).
 #pragma once
 
 #include "common.cuh"
@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(1024) k_conserved_final(const double *partial,
 }
 
 // ------------------------------------------------------------------- flags
-// Simplified Lohner estimator (Eq. 5) on density and pressure, evaluated in
+// Simplified Lohner estimator (Eq. 12) on density and pressure, evaluated in
 // double with every operation rounded as written (no contraction), so that
 // the flag decision is the same as a plain double evaluation of the formula
 // on the same stored values.  Per block: +1 if some cell exceeds c_ref, -1 if

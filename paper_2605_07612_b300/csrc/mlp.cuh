@@ -3,7 +3,7 @@
 // weights with FP32 accumulation.  Training kernels compute the mean
 // cross-entropy gradient deterministically (per-CTA partial sums reduced in a
 // fixed order) and apply AdamW to FP32 master weights.  The predictor stands
-// in for the refinement criterion of Sec. 3.3 (Eq. 5), which stays as the
+// in for the refinement criterion of Sec. 3.3 (Eq. 12), which stays as the
 // fallback for low-confidence blocks and as the judge of its flags.
 #pragma once
 

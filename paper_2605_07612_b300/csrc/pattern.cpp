@@ -1,5 +1,5 @@
 // Face-neighbour walk that classifies every block face as SRL / F2C / C2F /
-// BC (Sec. 2.5).  For block A at level l and face f the same-size box across
+// BC (Sec. 2.6).  For block A at level l and face f the same-size box across
 // the face is looked up: a leaf -> SRL; its parent a leaf -> C2F (A is fine);
 // otherwise the 2^(d-1) children facing A must be leaves -> F2C (A is coarse,
 // one entry per fine source).  Outside a non-periodic domain -> BC.

@@ -1,7 +1,7 @@
-// Ghost-cell pattern of Sec. 2.5, built on the host from the forest's face
+// Ghost-cell pattern of Sec. 2.6, built on the host from the forest's face
 // connectivity and executed on the GPU.  Besides the canonical entry list
 // this produces the tables the kernels need: refinement-face flux slots for
-// flux fixing (Sec. 2.6) and the per-coarse-block fix-up lists.
+// flux fixing (Sec. 2.7) and the per-coarse-block fix-up lists.
 #pragma once
 
 #include <cstdint>

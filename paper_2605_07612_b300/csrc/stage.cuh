@@ -1,6 +1,6 @@
 // Finite-volume Runge-Kutta stage of the Euler equations (Sec. 3.1-3.5):
-//   u_out = w_dt dt F(u_deriv) + sum_i w_i u_prev_i            (Eq. 4)
-// F: primitive variables (Eq. 9), MUSCL face values with the configured slope
+//   u_out = w_dt dt F(u_deriv) + sum_i w_i u_prev_i            (Eq. 5)
+// F: primitive variables (Eq. 15), MUSCL face values with the configured slope
 // limiter (minmod, MC or van Leer), Rusanov or HLL flux with Einfeldt's
 // wave-speed estimate, flux divergence.
 //
@@ -20,7 +20,7 @@
 // ahead.  Output rows are written whole (the x-ghost cells of the output
 // are overwritten with zeros) so that every DRAM sector is written
 // completely.  The kernel also stores the fluxes of refinement faces for
-// flux fixing (Sec. 2.6) and, on the last stage of a step, reduces the CFL
+// flux fixing (Sec. 2.7) and, on the last stage of a step, reduces the CFL
 // limit of its output (Sec. 3.2).  2D blocks are the single-plane case.
 //
 // FP32 uses the hardware reciprocal and reciprocal-square-root; FP64 uses

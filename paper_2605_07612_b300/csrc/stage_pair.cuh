@@ -1,5 +1,5 @@
 // FP32 stage kernel for 2 ghost layers: the same computation as k_stage
-// (Sec. 3.1-3.5, Eq. 4), organised so that every thread owns two cells that
+// (Sec. 3.1-3.5, Eq. 5), organised so that every thread owns two cells that
 // are neighbours along x.  All arithmetic on such a pair runs as packed
 // two-wide FP32 instructions (add/mul/fma .f32x2 of sm_100-class GPUs), and
 // every shared- and global-memory access of a pair is one aligned 8-byte

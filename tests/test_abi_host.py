@@ -154,3 +154,29 @@ def test_batch_pattern_is_union_of_instance_patterns():
     exp[bc, 5] = np.arange(bc.sum())
     np.testing.assert_array_equal(f.pattern(), exp)
     assert f.n_instances == 3
+
+
+def test_checkpoint_round_trip_host_only(tmp_path):
+    """amr_save / amr_load of a host-only forest: the same blocks and ghost
+    pattern come back; foreign, truncated and mesh-only files are refused."""
+    sp = synth.MeshSpec(ndim=3, N=8, ng=2, ntrees=(3, 2, 2), periodic=(1, 0, 1), max_level=2,
+                        bc_type=(0, 0, 2, 2, 0, 0))
+    f = amr.Forest(sp, 0, max_blocks=4000, host_only=True)
+    rng = np.random.default_rng(3)
+    for _ in range(3):
+        f.regrid(rng.choice(np.array([-1, 0, 1], dtype=np.int8), size=f.n, p=[0.2, 0.4, 0.4]))
+    path = tmp_path / "mesh.ckpt"
+    f.save(str(path))
+    g = amr.Forest.load(str(path), host_only=True)
+    for a, b in zip(f.blocks(), g.blocks()):
+        np.testing.assert_array_equal(a, b)
+    np.testing.assert_array_equal(f.pattern(), g.pattern())
+    assert g.spec.ntrees == sp.ntrees and g.spec.bc_type == sp.bc_type and g.spec.max_level == 2
+    data = path.read_bytes()
+    (tmp_path / "bad").write_bytes(b"NOTACKPT" + data[8:])
+    (tmp_path / "short").write_bytes(data[: len(data) // 2])
+    for name in ("bad", "short"):
+        with pytest.raises(amr.AmrError):
+            amr.Forest.load(str(tmp_path / name), host_only=True)
+    with pytest.raises(amr.AmrError):       # a mesh-only checkpoint has no state for the device
+        amr.Forest.load(str(path))

@@ -1,7 +1,7 @@
 """GPU checks of the learned refinement-flag predictor against its FP64
 oracle (features, forward probabilities, gradients), training, the criterion
 fallback, and what the trained network gains over evaluating the criterion
-of Eq. 5 on every block."""
+of Eq. 12 on every block."""
 import numpy as np
 import pytest
 

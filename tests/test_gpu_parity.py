@@ -1,10 +1,10 @@
 """GPU parity of the CUDA path (through the C ABI) against the FP64 oracle.
 
 Bars (element by element on identical seeded inputs):
-  * ghost patterns and FP64 ghost values: bit-exact (Sec. 2.5);
+  * ghost patterns and FP64 ghost values: bit-exact (Sec. 2.6);
   * FP64 stages: relative L1 <= 1e-12 per variable;
   * FP32 stages: relative L1 <= 1e-5 after 100 steps against the FP64 oracle;
-  * refinement flags (Eq. 5) and regrid transfer (Sec. 2.2): bit-exact in FP64.
+  * refinement flags (Eq. 12) and regrid transfer (Sec. 2.2): bit-exact in FP64.
 """
 import numpy as np
 import pytest
@@ -480,7 +480,7 @@ def test_autotune_keeps_results(case):
 def test_adaptive_sphere_and_shock_fp64_matches_oracle():
     """Reduced adaptive run: over-pressure sphere and a Mach-3 shock entering
     through a Dirichlet -x face (Rankine-Hugoniot state), 64^3 base of 16^3
-    blocks, <= 3 levels, regrid from the criterion of Eq. 5 every 10 steps,
+    blocks, <= 3 levels, regrid from the criterion of Eq. 12 every 10 steps,
     60 steps.  Both sides flag, adapt and transfer on their own; meshes must
     agree exactly and the FP64 states to 1e-12 (relative L1)."""
     sp = synth.MeshSpec(ndim=3, N=16, ng=2, ntrees=(4, 4, 4), periodic=(0, 0, 0), max_level=2,
@@ -531,7 +531,7 @@ SLOTS = {"ssp3": 3, "ssp43": 3, "rk4": 4}
 @pytest.mark.parametrize("scheme", ["ssp3", "ssp43", "rk4"])
 @pytest.mark.parametrize("dim", [2, 3])
 def test_rk_schemes_fp64_match_oracle(scheme, dim):
-    """SSP-RK3 and classical RK4 steps (stages as Eq. 4 sub-steps on the GPU,
+    """SSP-RK3 and classical RK4 steps (stages as Eq. 5 sub-steps on the GPU,
     RK4's last stage written with the stage states) against the oracle's
     textbook forms on 3-level AMR meshes, FP64."""
     sp = synth.MeshSpec(**(SPEC_2D_AMR if dim == 2 else SPEC_3D_AMR))

@@ -1,5 +1,5 @@
 """Pins of the oracle's forest and ghost-pattern classification (Sec. 2.2,
-Sec. 2.5) against hand enumeration, closed forms and independent geometry.
+Sec. 2.6) against hand enumeration, closed forms and independent geometry.
 CPU only."""
 import itertools
 import os

@@ -1,7 +1,7 @@
 """Pins of the oracle's numerics against what the paper and the mathematics
 fix: exactness of ghost filling / prolongation / restriction for a linear
 field (Sec. 4.3), free-stream preservation, conservation with flux fixing
-(Sec. 2.6, Eq. 12), agreement of a uniformly refined AMR mesh with a single
+(Sec. 2.7, Eq. 18), agreement of a uniformly refined AMR mesh with a single
 level grid, the exact Riemann solution of a shock tube (Sec. 3.5), second
 order on a smooth exact solution (Sec. 4.1.2) and Toro's printed star states.
 CPU only."""
@@ -162,7 +162,7 @@ def test_free_stream_bit_exact(ndim):
 @pytest.mark.parametrize("ndim", [2, 3])
 def test_conservation_periodic_amr(ndim):
     """Flux fixing makes the scheme conservative across refinement faces:
-    sum of U dV drifts only by rounding (Eq. 12, Sec. 2.6)."""
+    sum of U dV drifts only by rounding (Eq. 18, Sec. 2.7)."""
     if ndim == 2:
         sp = synth.MeshSpec(ndim=2, N=8, ng=2, ntrees=(4, 4, 1), max_level=2)
         m = amr_mesh(sp, (0.5, 0.5), 2, (0.3, 0.15))
@@ -376,7 +376,7 @@ def test_rk_schemes_stability_function_and_order(scheme, order):
 
 def test_rk_step_on_mesh_matches_heun_step():
     """The generic driver with the mesh's flux operator reproduces the
-    stage-by-stage Heun step of Eq. 5-6 to rounding."""
+    stage-by-stage Heun step of Eq. 6-7 to rounding."""
     sp = synth.MeshSpec(ndim=2, N=8, ng=2, ntrees=(2, 2, 1), max_level=1)
     m = oracle.Mesh(sp, 0)
     lev, g = m.blocks()
