@@ -1,7 +1,7 @@
 """Parity at the benchmark's full size and launch configuration: the uniform
 periodic 256^3 mesh of 16^3 blocks in FP32, same-level halos gathered by the
 stage kernel, one step replayed as a CUDA graph, launch shape chosen by the
-autotuner.  One Heun step is compared with the FP64 oracle run on the whole
+autotuner.  20 Heun steps are compared with the FP64 oracle run on the whole
 mesh; conservation of the FP64 integrals is checked over 20 steps for 8^3,
 16^3 and 32^3 blocks."""
 import numpy as np
@@ -20,7 +20,9 @@ def spec_of(n):
     return synth.MeshSpec(ndim=3, N=n, ng=2, ntrees=(nt, nt, nt))
 
 
-def test_full_size_step_matches_oracle():
+def test_full_size_20_steps_match_oracle():
+    """The headline configuration for 20 Heun steps (FP32 GPU, FP64 oracle
+    on the host cores)."""
     sp = spec_of(16)
     f = amr.Forest(sp, 0, precision=32)
     lev, g = f.blocks()
@@ -28,18 +30,18 @@ def test_full_size_step_matches_oracle():
     f.set_state(0, u.astype(np.float32))
     f.compute_dt(0)
     f.autotune()
-    f.step(1, use_graph=True, gather=True)
+    f.step(20, use_graph=True, gather=True)
     assert f.sync_status() == amr.AMR_OK
     got = f.get_state(0)
     m = oracle.Mesh(sp, 0)
-    oracle.heun_step(m, u, np.zeros_like(u))
+    oracle.run_heun(m, u, 20)
     del m
     sl = slice(sp.ng, sp.ng + sp.N)
     for v in range(sp.nvar):
         a = got[:, v].reshape(-1, sp.side, sp.side, sp.side)[:, sl, sl, sl].astype(np.float64)
         b = u[:, v].reshape(-1, sp.side, sp.side, sp.side)[:, sl, sl, sl]
         err = np.abs(a - b).sum() / np.abs(b).sum()
-        assert err <= 1e-6, (v, err)
+        assert err <= 1e-5, (v, err)
 
 
 @pytest.mark.parametrize("n", [8, 16, 32])
