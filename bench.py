@@ -323,7 +323,7 @@ def run_ours(args, rank, world, dist):
         "gpu_launches": launches,
         "clocks": clocks,
         "autotune": {"choice": tune_choice, "stage_ms": tune_ms,
-                     "meaning": "0 = persistent grid, k = k (block, tile) items per CTA, +100 = per-cell kernel"},
+                     "meaning": "0 = persistent grid, k = k (block, tile) items per CTA, +100 = per-cell kernel, +1000 = pair kernel with 8x8 staging tiles"},
     }
     line.update(extras)
     return line

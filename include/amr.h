@@ -309,13 +309,20 @@ amr_status amr_flag_and_regrid(amr_forest *f, const amr_flag_params *prm, const 
 /* Autotuner: times the stage kernel on this forest's mesh for each
  * candidate launch shape -- (block, tile) items per CTA 1, 2 or 4, or a
  * persistent grid of SMs x resident CTAs sweeping all items -- and, for FP32
- * 3D with two ghost layers, the staging tile (packed cell-pair kernel versus
- * one cell per thread); keeps the fastest for later stages and steps.  The
- * timed stages write slot 1 only: slot 0's interior is not advanced (its
- * ghost cells are refilled).  *choice (may be
- * NULL) = 100 x (per-cell kernel) + items per CTA, 0 for persistent; *best_ms
- * = mean time of one stage launch of the choice. */
+ * 3D with two ghost layers and the Rusanov flux, the kernel and staging tile
+ * (packed cell-pair kernel with 16 x 16 or, for blocks above 8^3, 8 x 8 column
+ * tiles, versus one cell per thread); keeps the fastest for later stages and
+ * steps.  The timed stages write slot 1 only: slot 0's interior is not
+ * advanced (its ghost cells are refilled).  *choice (may be NULL) =
+ * 1000 x (pair tile 8) + 100 x (per-cell kernel) + items per CTA, 0 for
+ * persistent; *best_ms = mean time of one stage launch of the choice. */
 amr_status amr_autotune(amr_forest *f, int *choice, double *best_ms, amr_stream stream);
+
+/* Sets the stage launch shape directly, with amr_autotune's choice code
+ * (items per CTA 1..64 or 0 for a persistent grid; +100 per-cell kernel;
+ * +1000 pair kernel with 8 x 8 tiles, FP32 3D blocks above 8^3 only).
+ * Errors: AMR_EINVAL (a code this forest cannot run). */
+amr_status amr_set_launch_shape(amr_forest *f, int choice);
 
 /* ---- learned refinement flags ------------------------------------------
  * A small network predicts the flags of the criterion of Eq. 12 (Sec. 3.3)

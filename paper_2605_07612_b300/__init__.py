@@ -31,7 +31,7 @@ EXPORTED = [
     "amr_launch_count", "amr_conserved_static", "amr_create_batch", "amr_n_instances", "amr_instance_blocks",
     "amr_get_dts", "amr_conserved_all", "amr_autotune", "amr_features", "amr_mlp_create", "amr_mlp_destroy",
     "amr_mlp_n_params", "amr_mlp_get_params", "amr_mlp_set_params", "amr_mlp_forward", "amr_mlp_gradient",
-    "amr_mlp_train", "amr_mlp_flags", "amr_get_config", "amr_save", "amr_load", "amr_write_xdmf",
+    "amr_mlp_train", "amr_mlp_flags", "amr_get_config", "amr_save", "amr_load", "amr_write_xdmf", "amr_set_launch_shape",
 ]
 
 
@@ -92,6 +92,7 @@ def load(build_if_missing: bool = True):
     sig = {
         "amr_create_forest": [P(Config), C.c_int, P(vp)],
         "amr_get_config": [vp, C.c_int, P(Config)],
+        "amr_set_launch_shape": [vp, C.c_int],
         "amr_save": [vp, C.c_char_p, vp],
         "amr_load": [C.c_char_p, vp, P(vp), vp],
         "amr_write_xdmf": [vp, C.c_int, C.c_char_p, vp],
@@ -430,6 +431,10 @@ class Forest:
         ch, ms = C.c_int(), C.c_double()
         self._check(self.lib.amr_autotune(self.h, C.byref(ch), C.byref(ms), _stream_ptr(stream)), "amr_autotune")
         return int(ch.value), float(ms.value)
+
+    def set_launch_shape(self, choice):
+        """Stage launch shape by autotune choice code (amr_set_launch_shape)."""
+        self._check(self.lib.amr_set_launch_shape(self.h, int(choice)), "amr_set_launch_shape")
 
     def features(self, s, out=None, stream=None):
         """Block features of slot s as a CUDA tensor [F, n_blocks] (torch)."""

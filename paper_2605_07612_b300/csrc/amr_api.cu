@@ -941,12 +941,21 @@ amr_status amr_autotune(amr_forest *f, int *choice, double *best_ms, amr_stream 
     amr_status r = upload_pattern(f);
     if (r != AMR_OK) return r;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    struct Cand { bool scalar; int ipc; bool pers; };
+    // candidates: blocks (tiles) per CTA 1, 2, 4 or a persistent grid, for
+    // each kernel / staging tile: the FP32 3D pair kernel with tile 16 and,
+    // for blocks above 8^3, tile 8; the per-cell kernel
+    struct Cand { bool scalar; int ipc; bool pers; int tile; };
     std::vector<Cand> cands;
-    const bool pair_ok = f->cfg.precision == 32 && f->cfg.ndim == 3 && f->cfg.n_ghost == 2;
-    for (int sc = 0; sc < (pair_ok ? 2 : 1); ++sc) {
-        for (int ipc : {1, 2, 4}) cands.push_back({sc == 1, ipc, false});
-        cands.push_back({sc == 1, 1, true});
+    const bool pair_ok = f->cfg.precision == 32 && f->cfg.ndim == 3 && f->cfg.n_ghost == 2 && f->cfg.flux == AMR_FLUX_RUSANOV;
+    std::vector<std::pair<bool, int>> kernels;   // (per-cell kernel, pair tile)
+    if (pair_ok) {
+        kernels.push_back({false, 0});
+        if (f->cfg.block_n > 8) kernels.push_back({false, 8});
+    }
+    kernels.push_back({true, 0});
+    for (const auto &k : kernels) {
+        for (int ipc : {1, 2, 4}) cands.push_back({k.first, ipc, false, k.second});
+        cands.push_back({k.first, 1, true, k.second});
     }
     // a stage that leaves slot 0 alone: slot 1 = slot 0 (w_dt = 0), halos gathered
     amr_stage probe{1, 0, 1, {0, 0, 0, 0}, {1.0, 0, 0, 0}, 0.0, 0, 1};
@@ -960,6 +969,7 @@ amr_status amr_autotune(amr_forest *f, int *choice, double *best_ms, amr_stream 
         f->scalar_stage = cands[c].scalar;
         f->items_per_cta = cands[c].ipc;
         f->persistent = cands[c].pers;
+        f->pair_tile = cands[c].tile;
         if ((r = dispatch<StageFn>(f, &probe, st)) != AMR_OK) break;      // warm-up
         cudaEventRecord(e0, st);
         for (int rep = 0; rep < 3; ++rep)
@@ -978,9 +988,25 @@ amr_status amr_autotune(amr_forest *f, int *choice, double *best_ms, amr_stream 
     f->scalar_stage = cands[size_t(best)].scalar;
     f->items_per_cta = cands[size_t(best)].ipc;
     f->persistent = cands[size_t(best)].pers;
+    f->pair_tile = cands[size_t(best)].tile;
     f->graph_rev = ~0ull;     // launch shapes changed: re-capture
-    if (choice) *choice = (f->scalar_stage ? 100 : 0) + (f->persistent ? 0 : f->items_per_cta);
+    if (choice)
+        *choice = (f->scalar_stage ? 100 : 0) + (f->pair_tile == 8 ? 1000 : 0) + (f->persistent ? 0 : f->items_per_cta);
     if (best_ms) *best_ms = best_t;
+    return AMR_OK;
+}
+
+amr_status amr_set_launch_shape(amr_forest *f, int choice) {
+    if (!f || choice < 0) return AMR_EINVAL;
+    const int tile8 = choice / 1000, scalar = (choice % 1000) / 100, ipc = choice % 100;
+    if (tile8 > 1 || scalar > 1 || ipc > 64 || (tile8 && scalar)) return AMR_EINVAL;
+    const bool pair_ok = f->cfg.precision == 32 && f->cfg.ndim == 3 && f->cfg.n_ghost == 2 && f->cfg.flux == AMR_FLUX_RUSANOV;
+    if (tile8 && (!pair_ok || f->cfg.block_n <= 8)) return fail(f, AMR_EINVAL, "8 x 8 tiles need the FP32 3D pair kernel and blocks above 8^3");
+    f->scalar_stage = scalar == 1;
+    f->pair_tile = tile8 ? 8 : 0;
+    f->persistent = ipc == 0;
+    f->items_per_cta = ipc == 0 ? 1 : ipc;
+    f->graph_rev = ~0ull;
     return AMR_OK;
 }
 

@@ -48,6 +48,7 @@ struct amr_forest {
     bool scalar_stage = false;   // per-cell FP32 kernel instead of the pair kernel (tuning choice)
     int items_per_cta = 1;       // stage launch: CTAs loop over this many (block, tile) items
     bool persistent = false;     // stage launch: grid = SMs x resident CTAs, grid-stride sweep
+    int pair_tile = 0;           // FP32 pair kernel staging tile: 0 default (16, N for N = 8), or 8
     int n_sms = 0;
     bool capturing = false;
     int64_t launches = 0;

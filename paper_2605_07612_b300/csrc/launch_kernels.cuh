@@ -67,15 +67,16 @@ amr_status launch_stage_t(amr_forest *f, const StageArgs<real> &a, cudaStream_t 
 }
 
 // FP32, 3D, two ghost layers: the packed cell-pair kernel, specialised for
-// one and two previous states (the two stages of Heun's method) and for the
-// slope limiter (minmod, MC, van Leer); Rusanov flux only
-template <int N, int NPREV, int LIM>
+// one and two previous states (the two stages of Heun's method), for the
+// slope limiter (minmod, MC, van Leer; Rusanov flux only) and for the staging
+// tile (16, or 8 when the autotuner picks it for 16^3 / 32^3 blocks)
+template <int N, int TT, int NPREV, int LIM>
 amr_status launch_stage_pair_n(amr_forest *f, const StageArgs<float> &a, cudaStream_t st) {
-    using Sh = PairShape<N>;
+    using Sh = PairShape<N, TT>;
     static bool attr_done = false;
     const size_t smem = Sh::smem_bytes(NPREV);
     if (!attr_done) {
-        CU(cudaFuncSetAttribute(k_stage_pair<N, NPREV, LIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        CU(cudaFuncSetAttribute(k_stage_pair<N, TT, NPREV, LIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
         attr_done = true;
     }
     const int64_t items = nblocks(f) * Sh::TILES;
@@ -83,27 +84,35 @@ amr_status launch_stage_pair_n(amr_forest *f, const StageArgs<float> &a, cudaStr
         StageArgs<float> b = a;
         b.n_items = int(items);
         int occ = 1;
-        if (f->persistent) CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_stage_pair<N, NPREV, LIM>, Sh::NT, smem));
+        if (f->persistent) CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_stage_pair<N, TT, NPREV, LIM>, Sh::NT, smem));
         const int64_t grid = stage_grid(f, items, occ);
-        k_stage_pair<N, NPREV, LIM><<<unsigned(grid), Sh::NT, smem, st>>>(b, f->geom);
+        k_stage_pair<N, TT, NPREV, LIM><<<unsigned(grid), Sh::NT, smem, st>>>(b, f->geom);
         ++f->launches;
     }
     CU(cudaGetLastError());
     return AMR_OK;
 }
 
-template <int N, int LIM>
+template <int N, int TT, int LIM>
 amr_status launch_stage_pair_l(amr_forest *f, const StageArgs<float> &a, cudaStream_t st) {
-    if (a.nprev == 1) return launch_stage_pair_n<N, 1, LIM>(f, a, st);
-    if (a.nprev == 2) return launch_stage_pair_n<N, 2, LIM>(f, a, st);
-    return launch_stage_pair_n<N, -1, LIM>(f, a, st);
+    if (a.nprev == 1) return launch_stage_pair_n<N, TT, 1, LIM>(f, a, st);
+    if (a.nprev == 2) return launch_stage_pair_n<N, TT, 2, LIM>(f, a, st);
+    return launch_stage_pair_n<N, TT, -1, LIM>(f, a, st);
+}
+
+template <int N, int TT>
+amr_status launch_stage_pair_t(amr_forest *f, const StageArgs<float> &a, cudaStream_t st) {
+    if (a.limiter == AMR_LIM_MC) return launch_stage_pair_l<N, TT, 1>(f, a, st);
+    if (a.limiter == AMR_LIM_VANLEER) return launch_stage_pair_l<N, TT, 2>(f, a, st);
+    return launch_stage_pair_l<N, TT, 0>(f, a, st);
 }
 
 template <int N>
 amr_status launch_stage_pair(amr_forest *f, const StageArgs<float> &a, cudaStream_t st) {
-    if (a.limiter == AMR_LIM_MC) return launch_stage_pair_l<N, 1>(f, a, st);
-    if (a.limiter == AMR_LIM_VANLEER) return launch_stage_pair_l<N, 2>(f, a, st);
-    return launch_stage_pair_l<N, 0>(f, a, st);
+    if constexpr (N > 8) {
+        if (f->pair_tile == 8) return launch_stage_pair_t<N, 8>(f, a, st);
+    }
+    return launch_stage_pair_t<N, (N < 16 ? N : 16)>(f, a, st);
 }
 
 }  // namespace amrb

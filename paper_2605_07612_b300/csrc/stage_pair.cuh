@@ -5,8 +5,8 @@
 // every shared- and global-memory access of a pair is one aligned 8-byte
 // access.
 //
-// One CTA per (block, T x T column tile), T = min(N, 16), T*T/2 threads
-// (128 for T = 16); thread (ip, tj) owns
+// One CTA per (block, T x T column tile), T = min(N, 16) or 8 (autotuned),
+// T*T/2 threads (128 for T = 16); thread (ip, tj) owns
 // cells (2ip, 2ip+1) of row tj.  The CTA marches k with a ring of
 // primitive variables in shared memory (4 planes: the z face state of the
 // plane above is carried in registers).  Per plane k:
@@ -180,9 +180,11 @@ __device__ __forceinline__ void pair_prim(const float2 *U, float2 *w, float gam)
     w[4] = PF::mul(PF::sp(gam - 1.f), PF::fma(ke, PF::sp(-0.5f), U[4]));
 }
 
-template <int N>
+// T: the staging tile (T x T columns per CTA); 16 by default (N for N = 8),
+// 8 as the autotuner's alternative for larger blocks.
+template <int N, int T_ = (N < 16 ? N : 16)>
 struct PairShape {
-    static constexpr int T = N < 16 ? N : 16, NG = 2, S = N + 2 * NG, P = T + 4, PL = P * P, R = 4, V = 5;
+    static constexpr int T = T_, NG = 2, S = N + 2 * NG, P = T + 4, PL = P * P, R = 4, V = 5;
     static constexpr int NT = T * T / 2;              // threads: one per cell pair of a plane
     static constexpr int TILES = (N / T) * (N / T);
     // x-flux row pitch (T + 1 faces + pad); for T = 16 it is 20 words, so the
@@ -208,9 +210,9 @@ struct PairShape {
 
 // NPREV >= 0: the number of previous states, fixed at compile time (Heun's two
 // stages use 1 and 2); -1 reads it from the arguments.
-template <int N, int NPREV, int LIM>
+template <int N, int TT, int NPREV, int LIM>
 __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const Geom &g, int item) {
-    using Sh = PairShape<N>;
+    using Sh = PairShape<N, TT>;
     constexpr int T = Sh::T, NG = Sh::NG, S = Sh::S, P = Sh::P, PL = Sh::PL, V = Sh::V, NT = Sh::NT;
     constexpr int FXP = Sh::FXP, NFX = Sh::NFX, FBUF = Sh::FBUF;
     constexpr int64_t NC = int64_t(S) * S * S;
@@ -620,9 +622,9 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
     if (__syncthreads_or(nonphys) && tid == 0) raise_status(&a.sc[0].status, 7);
 }
 
-template <int N, int NPREV, int LIM>
-__global__ void __launch_bounds__(PairShape<N>::NT, (N >= 16 ? 4 : 1)) k_stage_pair(StageArgs<float> a, Geom g) {
-    for (int item = blockIdx.x; item < a.n_items; item += gridDim.x) stage_pair_item<N, NPREV, LIM>(a, g, item);
+template <int N, int TT, int NPREV, int LIM>
+__global__ void __launch_bounds__(PairShape<N, TT>::NT, (TT >= 16 ? 4 : 1)) k_stage_pair(StageArgs<float> a, Geom g) {
+    for (int item = blockIdx.x; item < a.n_items; item += gridDim.x) stage_pair_item<N, TT, NPREV, LIM>(a, g, item);
 }
 
 }  // namespace amrb

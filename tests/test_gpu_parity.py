@@ -699,3 +699,28 @@ def test_fp32_3d_amr_blast_16cubed_against_oracle():
     ref = u.copy()
     oracle.run_heun(om, ref, 50)
     assert scaled_l1(f.get_state(0), ref, sp).max() <= 1e-5
+
+
+@pytest.mark.parametrize("N", [16, 32])
+def test_launch_shapes_agree(N):
+    """Every launch shape the autotuner can pick gives the same result: the
+    pair kernel with 16 x 16 or 8 x 8 tiles, k items per CTA or a persistent
+    grid bit-identically; the per-cell kernel within FP32 rounding."""
+    sp = synth.MeshSpec(ndim=3, N=N, ng=2, ntrees=(64 // N,) * 3)
+    f = amr.Forest(sp, 0, precision=32)
+    lev, g = f.blocks()
+    u = synth.fourier3d(sp, lev, g, seed=9).astype(np.float32)
+    results = {}
+    for choice in (1, 2, 0, 1001, 1004, 1000, 101, 100):
+        f.set_launch_shape(choice)
+        f.set_state(0, u)
+        f.compute_dt(0)
+        f.step(4, use_graph=True, gather=True)
+        assert f.sync_status() == amr.AMR_OK
+        results[choice] = f.get_state(0)
+    for c in (2, 0, 1001, 1004, 1000):
+        np.testing.assert_array_equal(results[c], results[1])
+    for c in (101, 100):
+        assert rel_l1(results[c], results[1].astype(np.float64), sp).max() <= 1e-6
+    with pytest.raises(amr.AmrError):
+        f.set_launch_shape(1101)
