@@ -73,6 +73,8 @@ def _lib_handle():
             lib.orc_max_speed.argtypes = [vp, vp]
             lib.orc_limited_slope.restype = C.c_double
             lib.orc_limited_slope.argtypes = [C.c_int, C.c_double, C.c_double]
+            lib.orc_weno5.restype = C.c_double
+            lib.orc_weno5.argtypes = [C.c_double] * 5
             lib.orc_face_flux.restype = None
             lib.orc_face_flux.argtypes = [P(Params), C.c_int, vp, vp, vp]
             lib.orc_conserved.argtypes = [vp, vp, vp]
@@ -115,6 +117,11 @@ def limited_slope(limiter: int, a: float, b: float) -> float:
     """The MUSCL slope limiter (0 minmod, 1 MC, 2 van Leer) on one pair of
     one-sided differences."""
     return float(_lib_handle().orc_limited_slope(int(limiter), float(a), float(b)))
+
+
+def weno5(a, b, c, d, e) -> float:
+    """The WENO5 face value right of c from the five cells a..e."""
+    return float(_lib_handle().orc_weno5(float(a), float(b), float(c), float(d), float(e)))
 
 
 def face_flux(spec, n: int, wL, wR) -> np.ndarray:

@@ -53,7 +53,8 @@ typedef struct {
     double gamma, cfl;
     int bc_type[6];        /* 0 periodic/none, 1 Dirichlet, 2 Neumann, 3 Dirichlet from bc_data */
     double bc_val[6][8];
-    int limiter;           /* MUSCL slope limiter (Sec. 3.2 list): 0 minmod, 1 MC, 2 van Leer */
+    int limiter;           /* face reconstruction (Sec. 3.2 list): 0 minmod, 1 MC, 2 van Leer
+                              (MUSCL slopes), 3 WENO5 (needs ng >= 3) */
     int flux;              /* 0 Rusanov, 1 HLL (Sec. 3.2 list), both with Einfeldt speeds */
     double gravity[3];     /* g of the source term S = (0, rho g, rho g.u) (Sec. 4.2) */
 } orc_params;
@@ -801,8 +802,32 @@ static double limited_slope(int lim, double a, double b)
     return minmod(a, b);
 }
 
+/* WENO5 value at the face right of cell c from cells c-2 .. c+2 (Jiang & Shu
+ * 1996): three third-order candidates q_k, smoothness indicators beta_k,
+ * weights gamma = (1/10, 6/10, 3/10) / (eps + beta_k)^2 normalised, eps =
+ * 1e-6.  The value at the face left of cell c is the same with the five
+ * cells in reverse order. */
+static double weno5(double a, double b, double c, double d, double e)
+{
+    double q0 = (2.0 * a - 7.0 * b + 11.0 * c) / 6.0;
+    double q1 = (-b + 5.0 * c + 2.0 * d) / 6.0;
+    double q2 = (2.0 * c + 5.0 * d - e) / 6.0;
+    double t0 = a - 2.0 * b + c, u0 = a - 4.0 * b + 3.0 * c;
+    double t1 = b - 2.0 * c + d, u1 = b - d;
+    double t2 = c - 2.0 * d + e, u2 = 3.0 * c - 4.0 * d + e;
+    double b0 = 13.0 / 12.0 * t0 * t0 + 0.25 * u0 * u0;
+    double b1 = 13.0 / 12.0 * t1 * t1 + 0.25 * u1 * u1;
+    double b2 = 13.0 / 12.0 * t2 * t2 + 0.25 * u2 * u2;
+    const double eps = 1e-6;
+    double a0 = 0.1 / ((eps + b0) * (eps + b0));
+    double a1 = 0.6 / ((eps + b1) * (eps + b1));
+    double a2 = 0.3 / ((eps + b2) * (eps + b2));
+    return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+}
+
 /* test hooks: the limiter and the face flux on given values */
 double orc_limited_slope(int lim, double a, double b) { return limited_slope(lim, a, b); }
+double orc_weno5(double a, double b, double c, double d, double e) { return weno5(a, b, c, d, e); }
 void orc_face_flux(const orc_params *p, int n, const double *wL, const double *wR, double *F) { face_flux(p, n, wL, wR, F); }
 
 /* ------------------------------------------------------------------------ */
@@ -864,20 +889,27 @@ int orc_stage(const orc_mesh *m, const double *ud, double *uo, int nprev,
             for (int t1 = 0; t1 < tn; t1++)
                 for (int t0 = 0; t0 < N; t0++)
                     for (int fp = 0; fp <= N; fp++) {
-                        double wm2[5], wm1[5], w0[5], w1[5], wL[5], wR[5], F[5];
-                        int pos[4] = {fp - 2, fp - 1, fp, fp + 1};
-                        double *dst[4] = {wm2, wm1, w0, w1};
-                        for (int q = 0; q < 4; q++) {
+                        double wm3[5], wm2[5], wm1[5], w0[5], w1[5], w2[5], wL[5], wR[5], F[5];
+                        int weno = p->limiter == 3;
+                        int pos[6] = {fp - 2, fp - 1, fp, fp + 1, fp - 3, fp + 2};
+                        double *dst[6] = {wm2, wm1, w0, w1, wm3, w2};
+                        for (int q = 0; q < (weno ? 6 : 4); q++) {
                             int x[3] = {0, 0, 0};
                             x[n] = pos[q]; x[td[0]] = t0;
                             if (D == 3) x[td[1]] = t1;
                             int64_t c = (int64_t)(x[0] + p->ng) + S * ((int64_t)(x[1] + p->ng) + (D == 3 ? S * (int64_t)(x[2] + p->ng) : 0));
                             for (int v = 0; v < V; v++) dst[q][v] = wp[(int64_t)v * nc + c];
                         }
-                        /* MUSCL reconstruction of primitives with the limiter (Sec. 3.2) */
+                        /* reconstruction of primitives (Sec. 3.2): MUSCL with the
+                         * limiter, or WENO5 from five cells on each side */
                         for (int v = 0; v < V; v++) {
-                            wL[v] = wm1[v] + 0.5 * limited_slope(p->limiter, wm1[v] - wm2[v], w0[v] - wm1[v]);
-                            wR[v] = w0[v] - 0.5 * limited_slope(p->limiter, w0[v] - wm1[v], w1[v] - w0[v]);
+                            if (weno) {
+                                wL[v] = weno5(wm3[v], wm2[v], wm1[v], w0[v], w1[v]);
+                                wR[v] = weno5(w2[v], w1[v], w0[v], wm1[v], wm2[v]);
+                            } else {
+                                wL[v] = wm1[v] + 0.5 * limited_slope(p->limiter, wm1[v] - wm2[v], w0[v] - wm1[v]);
+                                wR[v] = w0[v] - 0.5 * limited_slope(p->limiter, w0[v] - wm1[v], w1[v] - w0[v]);
+                            }
                         }
                         if (!(wL[0] > 0.0) || !(wL[D + 1] > 0.0) || !(wR[0] > 0.0) || !(wR[D + 1] > 0.0)) bad = 1;
                         face_flux(p, n, wL, wR, F);

@@ -492,3 +492,47 @@ def test_rayleigh_taylor_hydrostatic_balance(ndim):
     for v in range(sp.nvar):
         assert np.abs(R[:, v][far]).max() <= 1e-13, v
     assert np.abs(R[:, ndim][~far]).max() > 1e-3      # the interface is not in balance
+
+
+def test_weno5_reconstruction_properties():
+    """WENO5 (Jiang & Shu): constants and linear data reproduced exactly,
+    fifth-order face values from cell averages of a smooth function, no
+    overshoot at a step (the smooth stencil is chosen), mirror symmetry."""
+    assert oracle.weno5(2.0, 2.0, 2.0, 2.0, 2.0) == 2.0
+    assert abs(oracle.weno5(1.0, 2.0, 3.0, 4.0, 5.0) - 3.5) <= 1e-15
+    errs = []
+    for n in (16, 32, 64):
+        h = 1.0 / n
+        avg = lambda i: (math.cos(2 * math.pi * (i - 0.5) * h) - math.cos(2 * math.pi * (i + 0.5) * h)) / (2 * math.pi * h)
+        errs.append(max(abs(oracle.weno5(avg(c - 2), avg(c - 1), avg(c), avg(c + 1), avg(c + 2))
+                            - math.sin(2 * math.pi * (c + 0.5) * h)) for c in range(n)))
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert min(orders) >= 4.8, orders
+    assert abs(oracle.weno5(0.0, 0.0, 0.0, 1.0, 1.0)) < 1e-3
+    assert abs(oracle.weno5(0.0, 0.0, 1.0, 1.0, 1.0) - 1.0) < 1e-3
+    rng = np.random.default_rng(4)
+    for _ in range(50):
+        x = rng.normal(0, 1, 5)
+        assert oracle.weno5(*x) == pytest.approx(-oracle.weno5(*(-x)), rel=1e-13, abs=1e-15)
+
+
+def test_weno5_density_wave_fifth_order():
+    """The paper reports order close to 5 with WENO5 and RK4, CFL scaled as
+    dx^(1/4) (Sec. 4.1): the Euler density wave shows the same."""
+    errs = []
+    for ntr in (1, 2, 4):
+        cfl = 0.5 * (1.0 / ntr) ** 0.25
+        sp = synth.MeshSpec(ndim=2, N=16, ng=3, ntrees=(ntr, ntr, 1), max_level=0, cfl=cfl, limiter=3)
+        m = oracle.Mesh(sp, 0)
+        lev, g = m.blocks()
+        u = synth.density_wave(sp, lev, g)
+        t, t_end = 0.0, 0.1
+        while t < t_end - 1e-15:
+            dt = min(m.dt(u), t_end - t)
+            oracle.rk_step(m, u, "rk4", dt=dt)
+            t += dt
+        exact = synth.density_wave_exact(sp, lev, g, t_end)
+        sl = slice(sp.ng, sp.ng + sp.N)
+        errs.append(np.abs(interior(sp, u)[:, 0] - exact[:, sl, sl]).mean())
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert min(orders) >= 4.6, (errs, orders)
