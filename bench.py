@@ -303,6 +303,22 @@ def run_ours(args, rank, world, dist):
         rt["context"] = ("paper, 1x H100, same case: FP64 1.37 / 1.30 / 1.10 and FP32 2.70 / 2.60 / 2.08 GCUPS "
                          "for 32^3 / 16^3 / 8^3 blocks (Tables 1 and 2); flux scheme not stated there, Rusanov here")
         extras["rayleigh_taylor_vanleer"] = rt
+        # the same case with WENO5 (three ghost layers; Table 1's WENO5 rows)
+        rtw = {}
+        for bn, prec in ((16, 32), (16, 64)):
+            sp_rt = synth.rayleigh_taylor_spec(ndim=3, N=bn, limiter=3)
+            fr = amr.Forest(sp_rt, 0, precision=prec)
+            lev_rt, g_rt = fr.blocks()
+            fr.set_state(0, synth.rayleigh_taylor(sp_rt, lev_rt, g_rt).astype(fr.dtype))
+            fr.compute_dt(0, stream=stream)
+            nrt = max(2, args.steps // (2 if prec == 32 else 8))
+            msr, _ = time_steps(fr, nrt, 1, prec == 32, False)
+            rtw["%d^3 fp%d" % (bn, prec)] = {"value": 2.0 * cells * nrt * world / (msr * 1e-3), "ms_per_step": msr / nrt,
+                                              "status": fr.sync_status()}
+            del fr
+            torch.cuda.empty_cache()
+        rtw["context"] = "paper, 1x H100, FP64: 0.48 GCUPS for 16^3 blocks (Table 1)"
+        extras["rayleigh_taylor_weno5"] = rtw
         extras["batched_2d"] = run_batched(args, amr, torch, stream, barrier, world)
 
     line = {

@@ -107,11 +107,13 @@ typedef struct {
                               every stage (Sec. 4.2); zero: no source */
 } amr_config;
 
-/* MUSCL slope limiters of Sec. 3.2 that need two ghost layers.  The slope
- * of a cell from its one-sided differences a, b: minmod = Eq. 1 with
- * theta = 1; MC (monotonized central) = Eq. 1 with theta = 2; van Leer =
- * 2ab / (a + b) when ab > 0, else 0.  Face values are w -/+ slope / 2. */
-typedef enum { AMR_LIM_MINMOD = 0, AMR_LIM_MC = 1, AMR_LIM_VANLEER = 2 } amr_limiter;
+/* Face reconstructions of Sec. 3.2.  MUSCL slope limiters (two ghost
+ * layers); the slope of a cell from its one-sided differences a, b: minmod =
+ * Eq. 1 with theta = 1; MC (monotonized central) = Eq. 1 with theta = 2; van
+ * Leer = 2ab / (a + b) when ab > 0, else 0; face values w -/+ slope / 2.
+ * WENO5 (Jiang & Shu, weights (1/10, 6/10, 3/10) / (1e-6 + beta)^2) from
+ * five cells on each side: needs n_ghost >= 3 and ignores halo gathering. */
+typedef enum { AMR_LIM_MINMOD = 0, AMR_LIM_MC = 1, AMR_LIM_VANLEER = 2, AMR_LIM_WENO5 = 3 } amr_limiter;
 
 /* Numerical fluxes of Sec. 3.2, both with Einfeldt's signal speeds
  * u_roe -/+ d (Sec. 3.5): Rusanov (local Lax-Friedrichs, a = |u_roe| + d)

@@ -135,7 +135,8 @@ amr_status validate(const amr_config *c, std::string &why) {
     if (c->max_level < 0 || c->max_level >= kMaxLevels) return bad("max_level must be 0..12");
     if (c->max_blocks < 1 || c->n_states < 1) return bad("max_blocks and n_states must be >= 1");
     if (c->precision != 32 && c->precision != 64) return bad("precision must be 32 or 64");
-    if (c->limiter < AMR_LIM_MINMOD || c->limiter > AMR_LIM_VANLEER) return bad("unknown limiter");
+    if (c->limiter < AMR_LIM_MINMOD || c->limiter > AMR_LIM_WENO5) return bad("unknown limiter");
+    if (c->limiter == AMR_LIM_WENO5 && c->n_ghost < 3) return bad("WENO5 needs n_ghost >= 3");
     if (c->flux < AMR_FLUX_RUSANOV || c->flux > AMR_FLUX_HLL) return bad("unknown flux");
     if (!(c->gamma > 1.0) || !(c->cfl > 0.0)) return bad("gamma must be > 1 and cfl > 0");
     for (int d = 0; d < 3; ++d)
@@ -207,6 +208,18 @@ amr_status launch_stage(amr_forest *f, const StageArgs<real> &a, cudaStream_t st
     return fail(f, AMR_EINVAL, "the Euler stage needs n_ghost 2 or 3 (got %d)", NG);
 }
 
+// scratch of the WENO5 stage (primitives and face fluxes of every block);
+// allocated outside stream capture
+amr_status ensure_weno(amr_forest *f) {
+    if (f->cfg.limiter != AMR_LIM_WENO5) return AMR_OK;
+    const int N = f->cfg.block_n, D = f->cfg.ndim;
+    const size_t nfl = size_t(D) * size_t(D + 2) * size_t(N + 1) * size_t(D == 3 ? N * N : N);
+    const size_t nb = size_t(std::max<int64_t>(nblocks(f), 1));
+    amr_status s = ensure(f, f->wprim, nb * f->block_bytes);
+    if (s != AMR_OK) return s;
+    return ensure(f, f->wflux, nb * nfl * size_t(f->esize));
+}
+
 template <class real, int D>
 amr_status run_stage(amr_forest *f, const amr_stage *stg, cudaStream_t st) {
     StageArgs<real> a{};
@@ -232,7 +245,15 @@ amr_status run_stage(amr_forest *f, const amr_stage *stg, cudaStream_t st) {
         a.grav[d] = d < D ? real(f->cfg.gravity[d]) : real(0);
         if (d < D && f->cfg.gravity[d] != 0.0) a.gravity_on = 1;
     }
-    amr_status s = launch_stage<real, D>(f, a, st);
+    amr_status s;
+    if (f->cfg.limiter == AMR_LIM_WENO5) {
+        // three-pass WENO5 stage on the filled ghost cells (no halo gathering)
+        a.gather = 0;
+        if ((s = ensure_weno(f)) != AMR_OK) return s;
+        s = launch_weno<real, D>(f, a, static_cast<real *>(f->wprim.p), static_cast<real *>(f->wflux.p), st);
+    } else {
+        s = launch_stage<real, D>(f, a, st);
+    }
     if (s != AMR_OK) return s;
     const int nfix = int(f->pat.fix_start.size()) - 1;
     if (nfix > 0) {
@@ -392,6 +413,7 @@ struct TransferFn {
 int step_slots(int flags) { return (flags & AMR_STEP_RK4) ? 4 : ((flags & (AMR_STEP_SSP3 | AMR_STEP_SSP43)) ? 3 : 2); }
 
 amr_status rk_step(amr_forest *f, cudaStream_t st, bool gather, int flags) {
+    if (f->cfg.limiter == AMR_LIM_WENO5) gather = false;   // WENO5 reads filled ghost cells
     const int gh = gather ? 1 : 0;
     std::vector<amr_stage> seq;
     if (flags & AMR_STEP_RK4) {
@@ -699,7 +721,9 @@ amr_status amr_step(amr_forest *f, int n_steps, int flags, amr_stream stream) {
             f->gexec = nullptr;
         }
         // capture one step on the library's own stream, after the caller's
-        // stream has drained (capture needs a non-legacy stream)
+        // stream has drained (capture needs a non-legacy stream); buffers
+        // are allocated before the capture
+        if ((r = ensure_weno(f)) != AMR_OK) return r;
         CU(cudaStreamSynchronize(st));
         const int64_t before = f->launches;
         CU(cudaStreamBeginCapture(f->cap_stream, cudaStreamCaptureModeThreadLocal));

@@ -40,6 +40,7 @@ struct amr_forest {
     amrb::DBuf r1, r2, r1g, info, fix, fix_start, bflux, bcdata, sc, partial, sums, flags, ops, level;
     amrb::DBuf dxtab, invdxtab, bctype, bcval, cfltab, ranges;   // per-instance tables
     amrb::DBuf feat, prob, mflags, flist;                        // learned-flag predictor
+    amrb::DBuf wprim, wflux;                                     // WENO5 stage scratch
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t gexec = nullptr;
     uint64_t graph_rev = ~0ull;
@@ -93,5 +94,7 @@ template <class real, int D, int N, int NG, bool GEN>
 amr_status launch_stage_t(amr_forest *f, const StageArgs<real> &a, cudaStream_t st);
 template <int N>
 amr_status launch_stage_pair(amr_forest *f, const StageArgs<float> &a, cudaStream_t st);
+template <class real, int D>
+amr_status launch_weno(amr_forest *f, const StageArgs<real> &a, real *prim, real *flux, cudaStream_t st);
 
 }  // namespace amrb

@@ -1,0 +1,9 @@
+// Explicit instantiations of kernel launchers (parallel build unit).
+#include "launch_kernels.cuh"
+
+namespace amrb {
+template amr_status launch_weno<float, 2>(amr_forest *, const StageArgs<float> &, float *, float *, cudaStream_t);
+template amr_status launch_weno<float, 3>(amr_forest *, const StageArgs<float> &, float *, float *, cudaStream_t);
+template amr_status launch_weno<double, 2>(amr_forest *, const StageArgs<double> &, double *, double *, cudaStream_t);
+template amr_status launch_weno<double, 3>(amr_forest *, const StageArgs<double> &, double *, double *, cudaStream_t);
+}  // namespace amrb

@@ -7,6 +7,7 @@
 #include "ghost.cuh"
 #include "stage.cuh"
 #include "stage_pair.cuh"
+#include "stage_weno.cuh"
 
 namespace amrb {
 
@@ -113,6 +114,26 @@ amr_status launch_stage_pair(amr_forest *f, const StageArgs<float> &a, cudaStrea
         if (f->pair_tile == 8) return launch_stage_pair_t<N, 8>(f, a, st);
     }
     return launch_stage_pair_t<N, (N < 16 ? N : 16)>(f, a, st);
+}
+
+// WENO5 stage: primitives, face fluxes, update (three launches); prim and
+// flux are scratch buffers of n_blocks x bstride and n_blocks x D x V x
+// (N+1) N^(D-1) elements
+template <class real, int D>
+amr_status launch_weno(amr_forest *f, const StageArgs<real> &a, real *prim, real *flux, cudaStream_t st) {
+    const int64_t nb = nblocks(f);
+    if (nb > 0) {
+        const int N = f->cfg.block_n;
+        const int nfaces = D * (N + 1) * (D == 3 ? N * N : N);
+        const int ncint = D == 3 ? N * N * N : N * N;
+        k_weno_prim<real, D><<<unsigned(nb), 256, 0, st>>>(a.deriv, prim, f->geom, a.gamma);
+        k_weno_flux<real, D><<<dim3(unsigned(nb), unsigned((nfaces + 255) / 256)), 256, 0, st>>>(
+            prim, flux, a.info, a.bflux, f->geom, a.gamma, a.flux, a.sc);
+        k_weno_update<real, D><<<dim3(unsigned(nb), unsigned((ncint + 255) / 256)), 256, 0, st>>>(a, flux, f->geom);
+        f->launches += 3;
+    }
+    CU(cudaGetLastError());
+    return AMR_OK;
 }
 
 }  // namespace amrb

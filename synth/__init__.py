@@ -360,7 +360,7 @@ def rayleigh_taylor(spec: MeshSpec, lev, g, h0=0.8, rho_hi=1.0, rho_lo=0.1, delt
     return mask_interior(spec, primitive_to_state(spec, rho, vel, p))
 
 
-def rayleigh_taylor_spec(ndim=3, N=16, ntrees=None, limiter=2, rho_hi=1.0, rho_lo=0.1, **kw) -> MeshSpec:
+def rayleigh_taylor_spec(ndim=3, N=16, ntrees=None, limiter=2, rho_hi=1.0, rho_lo=0.1, ng=None, **kw) -> MeshSpec:
     """Sec. 4.2 setup: unit square/cube, periodic horizontally, gamma = 5/3,
     g = -1 along the last dimension; the vertical faces are Neumann with the
     hydrostatic gradient of the energy (outward derivative of E = outward
@@ -378,6 +378,8 @@ def rayleigh_taylor_spec(ndim=3, N=16, ntrees=None, limiter=2, rho_hi=1.0, rho_l
     bcv[2 * (ndim - 1) + 1][V - 1] = -rho_hi / (gam - 1.0)
     grav = [0.0, 0.0, 0.0]
     grav[ndim - 1] = -1.0
-    return MeshSpec(ndim=ndim, N=N, ng=2, ntrees=tuple(nt), periodic=tuple(per), gamma=gam, cfl=0.5,
+    if ng is None:
+        ng = 3 if limiter == 3 else 2
+    return MeshSpec(ndim=ndim, N=N, ng=ng, ntrees=tuple(nt), periodic=tuple(per), gamma=gam, cfl=0.5,
                     bc_type=tuple(bct), bc_val=tuple(tuple(r) for r in bcv), limiter=limiter,
                     gravity=tuple(grav), **kw)
