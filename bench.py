@@ -597,6 +597,46 @@ def run_adaptive(args, amr, torch, stream, steps=500, every=10, train_until=200)
                         "FP32 learned (network trained on the first 200 steps' criterion flags), FP64 criterion"}
 
 
+def ghost_case_spec():
+    """3D 64^3 base of 16^3 blocks refined twice around a ball: a mesh with
+    every ghost kind, a few hundred MB per state slot (FP32)."""
+    return synth.MeshSpec(ndim=3, N=16, ng=2, ntrees=(4, 4, 4), max_level=2)
+
+
+def run_ncu_case(which="stage"):
+    """For ncu captures (default launch shape, no autotuning, no timing).
+    stage: one Heun step of the headline workload -- exactly two stage
+    launches.  ghost: one full ghost fill (rounds 1 and 2, no halo gathering)
+    of a 3-level FP32 mesh -- exactly two ghost launches."""
+    import torch
+    import paper_2605_07612_b300 as amr
+    if which == "ghost":
+        sp = ghost_case_spec()
+        f = amr.Forest(sp, 0, max_blocks=8000, precision=32)
+        for _ in range(2):
+            lev, g = f.blocks()
+            f.regrid(synth.ball_flags(sp, lev, g, (0.5, 0.5, 0.5), (0.35, 0.35)))
+        lev, g = f.blocks()
+        f.set_state(0, synth.fourier3d(sp, lev, g, seed=1).astype(np.float32))
+        torch.cuda.synchronize()
+        f.fill_ghosts(0)
+        torch.cuda.synchronize()
+        pat = f.pattern()
+        print(json.dumps({"blocks": f.n, "entries": {k: int((pat[:, 0] == i).sum())
+                                                     for i, k in enumerate(["srl", "f2c", "bc", "c2f"])}}))
+        return
+    spec = workload_spec(16)
+    f = amr.Forest(spec, 0, precision=32)
+    lev, g = f.blocks()
+    f.set_state(0, synth.fourier3d(spec, lev, g, seed=1).astype(np.float32))
+    f.compute_dt(0)
+    f.step(1, use_graph=False, gather=True)
+    torch.cuda.synchronize()
+    st = f.sync_status()
+    if st != amr.AMR_OK:
+        raise SystemExit("device status %d" % st)
+
+
 # ------------------------------------------------------- CPU oracle arm --
 
 def oracle_sample(seconds_hint=15.0):
@@ -654,11 +694,12 @@ def main():
     ap.add_argument("--workload", default="uniform", choices=["uniform", "amr_static", "adaptive"],
                     help="uniform: the headline line; the others print their own JSON line")
     ap.add_argument("--adaptive-steps", type=int, default=500)
-    ap.add_argument("--ncu-case", action="store_true",
-                    help="run one Heun step of the headline workload and exit (for ncu captures)")
+    ap.add_argument("--ncu-case", nargs="?", const="stage", default=None, choices=["stage", "ghost"],
+                    help="run one Heun step of the headline workload (stage) or one ghost fill of a 3-level mesh "
+                         "(ghost) and exit, for ncu captures")
     args = ap.parse_args()
     if args.ncu_case:
-        run_ncu_case()
+        run_ncu_case(args.ncu_case)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

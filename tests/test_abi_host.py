@@ -180,3 +180,12 @@ def test_checkpoint_round_trip_host_only(tmp_path):
             amr.Forest.load(str(tmp_path / name), host_only=True)
     with pytest.raises(amr.AmrError):       # a mesh-only checkpoint has no state for the device
         amr.Forest.load(str(path))
+
+
+def test_bench_entry_points_exist():
+    """The functions the bench's command line dispatches to (the profiles in
+    the repository name those command lines) are defined."""
+    import bench
+    for name in ("run_ours", "run_reference", "run_amr_static", "run_adaptive", "run_ncu_case", "oracle_sample",
+                 "ghost_case_spec", "workload_spec", "stage_kernel_hash", "traffic_from_profile"):
+        assert callable(getattr(bench, name)), name
