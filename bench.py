@@ -145,6 +145,23 @@ def traffic_from_profile(workload):
     return ent.get("bytes_per_launch")   # mean of the stage-1 and stage-2 launches
 
 
+def max_over_ranks(x, dist, device="cuda"):
+    """The largest value of x over all ranks (the slowest rank's time); x
+    itself with one process."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, world, ms):
+    """Whole-job rate: the units all ranks processed (each rank advances its
+    own replica) over the slowest rank's time in milliseconds."""
+    return units_per_rank * world / (ms * 1e-3)
+
+
 def run_ours(args, rank, world, dist):
     import torch
     import paper_2605_07612_b300 as amr
@@ -178,12 +195,8 @@ def run_ours(args, rank, world, dist):
         e1.record(stream)
         stream.synchronize()
         barrier()
-        ms = e0.elapsed_time(e1)
+        ms = max_over_ranks(e0.elapsed_time(e1), dist)
         launches = f.launch_count() - l0
-        if dist is not None:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
         return ms, launches
 
     spec = workload_spec(16)
@@ -197,7 +210,7 @@ def run_ours(args, rank, world, dist):
     st = f.sync_status()
     if st != amr.AMR_OK:
         raise SystemExit("device status %d after the timed steps" % st)
-    value = 2.0 * cells * args.steps * world / (ms * 1e-3)
+    value = job_throughput(2.0 * cells * args.steps, world, ms)
 
     # dominant kernel (the stage) timed per launch on its own stream
     s1b, s2b = algorithmic_stage_bytes(spec, 4)
@@ -237,8 +250,8 @@ def run_ours(args, rank, world, dist):
         f.get_state(0, out=host, stream=stream)
     e1.record(stream)
     stream.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
-    e2e_val = 2.0 * cells * e2e_steps * world / (e2e_ms * 1e-3)
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), dist)
+    e2e_val = job_throughput(2.0 * cells * e2e_steps, world, e2e_ms)
     del f
     torch.cuda.empty_cache()
 
