@@ -43,7 +43,7 @@ class Params(C.Structure):
                 ("lo", C.c_double * 3), ("len", C.c_double * 3),
                 ("max_level", C.c_int), ("gamma", C.c_double), ("cfl", C.c_double),
                 ("bc_type", C.c_int * 6), ("bc_val", (C.c_double * 8) * 6),
-                ("limiter", C.c_int), ("flux", C.c_int), ("gravity", C.c_double * 3)]
+                ("limiter", C.c_int), ("flux", C.c_int), ("gravity", C.c_double * 3), ("diagonal", C.c_int)]
 
 
 def _lib_handle():
@@ -110,6 +110,7 @@ def params_from_spec(spec) -> Params:
     gv = getattr(spec, "gravity", (0.0, 0.0, 0.0))
     for d in range(3):
         p.gravity[d] = float(gv[d]) if d < spec.ndim else 0.0
+    p.diagonal = int(getattr(spec, "diagonal_ghosts", 0))
     return p
 
 

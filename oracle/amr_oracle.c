@@ -57,10 +57,16 @@ typedef struct {
                               (MUSCL slopes), 3 WENO5 (needs ng >= 3) */
     int flux;              /* 0 Rusanov, 1 HLL (Sec. 3.2 list), both with Einfeldt speeds */
     double gravity[3];     /* g of the source term S = (0, rho g, rho g.u) (Sec. 4.2) */
+    int diagonal;          /* 1: also fill edge and corner ghost cells that a
+                              same-level leaf holds (the paper fills face ghosts only) */
 } orc_params;
 
 enum { BC_NONE = 0, BC_DIRICHLET = 1, BC_NEUMANN = 2, BC_DATA = 3 };
-enum { K_SRL = 0, K_F2C = 1, K_BC = 2, K_C2F = 3 };
+enum { K_SRL = 0, K_F2C = 1, K_BC = 2, K_C2F = 3, K_DIAG = 4 };
+
+/* a diagonal (edge or corner) direction (dx, dy, dz), two or three of them
+ * nonzero, as the code (dx+1) + 3 (dy+1) + 9 (dz+1) */
+static int diag_code(const int dir[3]) { return (dir[0] + 1) + 3 * (dir[1] + 1) + 9 * (dir[2] + 1); }
 
 #define ORDER_DEPTH 20     /* Morton depth used to order leaves of any level */
 
@@ -467,7 +473,7 @@ int64_t orc_pattern(const orc_mesh *m, int32_t *out, int64_t cap)
 {
     const orc_params *p = &m->p;
     int N = p->N, ng = p->ng, D = p->ndim;
-    int64_t maxe = (int64_t)m->n * 2 * D * (1 << (D - 1)) + 1;
+    int64_t maxe = (int64_t)m->n * (2 * D * (1 << (D - 1)) + 26) + 1;
     entry_t *E = (entry_t *)malloc(sizeof(entry_t) * maxe);
     int64_t ne = 0;
     int tn = (D == 3) ? N : 1;
@@ -524,6 +530,39 @@ int64_t orc_pattern(const orc_mesh *m, int32_t *out, int64_t cap)
                     E[ne++] = e;
                 }
             } else { free(E); return -1; }
+        }
+        /* edge and corner regions: an entry when a same-level leaf holds the
+         * whole region (other levels and non-periodic boundaries stay unfilled) */
+        if (p->diagonal) {
+            for (int dz = (D == 3 ? -1 : 0); dz <= (D == 3 ? 1 : 0); dz++)
+                for (int dy = -1; dy <= 1; dy++)
+                    for (int dx = -1; dx <= 1; dx++) {
+                        int dir[3] = {dx, dy, dz};
+                        int nz = (dx != 0) + (dy != 0) + (dz != 0);
+                        if (nz < 2) continue;
+                        int src = -2, ok = 1, ext[3], lo[3];
+                        for (int d = 0; d < 3; d++) {
+                            lo[d] = dir[d] < 0 ? -ng : (dir[d] > 0 ? N : 0);
+                            ext[d] = d >= D ? 1 : (dir[d] != 0 ? ng : N);
+                            if (d >= D) lo[d] = 0;
+                        }
+                        for (int k = 0; k < ext[2] && ok; k++)
+                            for (int j = 0; j < ext[1] && ok; j++)
+                                for (int i = 0; i < ext[0] && ok; i++) {
+                                    int x[3] = {lo[0] + i, lo[1] + j, lo[2] + k};
+                                    int64_t C[3];
+                                    int fl;
+                                    if (!global_cell(m, b, x, C)) { ok = 0; break; }
+                                    int sblk = locate_cell(m, lev, C, &fl);
+                                    if (sblk < 0 || fl != lev) { ok = 0; break; }
+                                    if (src == -2) src = sblk;
+                                    else if (src != sblk) { ok = 0; break; }
+                                }
+                        if (!ok || src < 0) continue;
+                        if (ne >= maxe) { free(E); return -1; }
+                        entry_t e = {K_DIAG, diag_code(dir), b, src, 0, 0};
+                        E[ne++] = e;
+                    }
         }
     }
     qsort(E, (size_t)ne, sizeof(entry_t), cmp_entry);
@@ -678,9 +717,39 @@ static int fill_round(const orc_mesh *m, double *u, const double *bc_data, int r
     return err ? -1 : 0;
 }
 
+/* Edge and corner ghost cells held by a same-level leaf: copies (only when
+ * the mesh asks for them). */
+static void fill_diagonal(const orc_mesh *m, double *u)
+{
+    const orc_params *p = &m->p;
+    int N = p->N, ng = p->ng, D = p->ndim, V = p->nvar;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int b = 0; b < m->n; b++) {
+        int lev = m->lev[b];
+        int kr0 = (D == 3) ? -ng : 0, kr1 = (D == 3) ? N + ng : 1;
+        for (int k = kr0; k < kr1; k++)
+            for (int j = -ng; j < N + ng; j++)
+                for (int i = -ng; i < N + ng; i++) {
+                    int x[3] = {i, j, D == 3 ? k : 0};
+                    int nout = 0;
+                    for (int d = 0; d < D; d++) if (x[d] < 0 || x[d] >= N) nout++;
+                    if (nout < 2) continue;
+                    int64_t C[3];
+                    int fl;
+                    if (!global_cell(m, b, x, C)) continue;
+                    int s = locate_cell(m, lev, C, &fl);
+                    if (s < 0 || fl != lev) continue;
+                    int xs[3] = {0, 0, 0};
+                    for (int d = 0; d < D; d++) xs[d] = (int)(C[d] - m->g[3 * s + d] * N);
+                    for (int v = 0; v < V; v++) u[atv(p, b, v, x)] = u[atv(p, s, v, xs)];
+                }
+    }
+}
+
 int orc_fill_ghosts(const orc_mesh *m, double *u, const double *bc_data)
 {
     if (fill_round(m, u, bc_data, 1)) return -1;
+    if (m->p.diagonal) fill_diagonal(m, u);
     return fill_round(m, u, bc_data, 2);
 }
 

@@ -48,6 +48,7 @@ class MeshSpec:
     limiter: int = 0          # 0 minmod, 1 MC, 2 van Leer (MUSCL slopes), 3 WENO5 (ng >= 3)
     flux: int = 0             # 0 Rusanov, 1 HLL
     gravity: Sequence[float] = (0.0, 0.0, 0.0)   # source term S = (0, rho g, rho g.u)
+    diagonal_ghosts: int = 0  # 1: also fill edge/corner ghosts held by same-level leaves
 
     @property
     def nvar(self) -> int:

@@ -235,3 +235,80 @@ def test_pattern_invariants(ndim, seed):
     # canonical order
     keys = [tuple(r) for r in pat[:, [0, 1, 2, 4]]]
     assert keys == sorted(keys)
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_diagonal_ghosts_closed_form_on_periodic_mesh(ndim):
+    """Edge and corner ghost cells (an option; the paper fills face ghosts
+    only): on a uniform periodic mesh every ghost cell -- face, edge and
+    corner -- holds the field of its wrapped global cell; without the option
+    the edge and corner cells are left as they were."""
+    nt = (3, 2, 2)[:ndim] + (1,) * (3 - ndim)
+    for diag in (1, 0):
+        sp = synth.MeshSpec(ndim=ndim, N=8, ng=2, ntrees=nt, diagonal_ghosts=diag)
+        m = oracle.Mesh(sp, 0)
+        lev, g = m.blocks()
+        S, N, ng = sp.side, sp.N, sp.ng
+        loc = np.arange(S) - ng
+        coords = []
+        for d in range(ndim):
+            c = (g[:, d, None] * N + loc[None, :]) % (nt[d] * N)
+            shape = [len(lev)] + [1] * ndim
+            shape[ndim - d] = S
+            coords.append(c.reshape(shape))
+        field = sum((7.0 ** d) * coords[d] for d in range(ndim)) + 0.25
+        field = np.broadcast_to(field, [len(lev)] + [S] * ndim)
+        u = np.stack([(v + 1.0) * field for v in range(sp.nvar)], axis=1).reshape(len(lev), sp.nvar, -1).copy()
+        u = synth.mask_interior(sp, u)
+        m.fill_ghosts(u)
+        U = u.reshape((len(lev), sp.nvar) + (S,) * ndim)
+        F = np.stack([(v + 1.0) * field for v in range(sp.nvar)], axis=1)
+        idx = np.indices((S,) * ndim) - ng
+        nout = sum(((idx[d] < 0) | (idx[d] >= N)).astype(int) for d in range(ndim))
+        diagonal = nout >= 2
+        np.testing.assert_array_equal(U[:, :, ~diagonal], F[:, :, ~diagonal])
+        if diag:
+            np.testing.assert_array_equal(U[:, :, diagonal], F[:, :, diagonal])
+        else:
+            assert not U[:, :, diagonal].any()
+
+
+@pytest.mark.parametrize("ndim,seed", [(2, 1), (2, 4), (3, 2)])
+def test_diagonal_pattern_entries_geometry(ndim, seed):
+    """Every diagonal entry names a same-level leaf displaced by its
+    direction code (dx+1) + 3(dy+1) + 9(dz+1), with periodic wrap, and every
+    such same-level neighbour has an entry."""
+    import dataclasses
+    sp, seq = random_meshes(ndim, seed, rounds=3)
+    spd = dataclasses.replace(sp, diagonal_ghosts=1)
+    m = oracle.Mesh(spd, 1)
+    for _, flags, _ in seq:
+        m = m.adapt(flags)
+        lev, g = m.blocks()
+        pat = m.pattern()
+        where = {(int(a), *map(int, b)): i for i, (a, b) in enumerate(zip(lev, g))}
+        expect = set()
+        for b in range(m.n):
+            for dz in ((-1, 0, 1) if ndim == 3 else (0,)):
+                for dy in (-1, 0, 1):
+                    for dx in (-1, 0, 1):
+                        dirs = (dx, dy, dz)
+                        if sum(x != 0 for x in dirs) < 2:
+                            continue
+                        q, ok = [], True
+                        for d in range(ndim):
+                            E = spd.ntrees[d] << int(lev[b])
+                            x = int(g[b][d]) + dirs[d]
+                            if x < 0 or x >= E:
+                                if not spd.periodic[d]:
+                                    ok = False
+                                    break
+                                x %= E
+                            q.append(x)
+                        if not ok:
+                            continue
+                        s = where.get((int(lev[b]), *(q + [0] * (3 - ndim))))
+                        if s is not None:
+                            expect.add(((dx + 1) + 3 * (dy + 1) + 9 * (dz + 1), b, s))
+        got = {(int(e[1]), int(e[2]), int(e[3])) for e in pat[pat[:, 0] == 4]}
+        assert got == expect
