@@ -66,7 +66,10 @@ typedef enum {
     AMR_GHOST_SRL = 0,     /* same refinement level: copy */
     AMR_GHOST_F2C = 1,     /* fine -> coarse: restriction into the coarse block's ghosts */
     AMR_GHOST_BC = 2,      /* physical boundary */
-    AMR_GHOST_C2F = 3      /* coarse -> fine: limited prolongation, second round */
+    AMR_GHOST_C2F = 3,     /* coarse -> fine: limited prolongation, second round */
+    AMR_GHOST_DIAG = 4     /* edge / corner region held by a same-level leaf: copy
+                              (only with amr_config.diagonal_ghosts); face =
+                              (dx+1) + 3 (dy+1) + 9 (dz+1) for the direction */
 } amr_ghost_kind;
 
 typedef struct amr_forest amr_forest;
@@ -105,6 +108,10 @@ typedef struct {
     int flux;              /* amr_flux: numerical flux (Sec. 3.2) */
     double gravity[3];     /* g of the source term S = (0, rho g, rho g.u) added to
                               every stage (Sec. 4.2); zero: no source */
+    int diagonal_ghosts;   /* 1: the pattern also copies edge and corner ghost
+                              regions held by same-level leaves (AMR_GHOST_DIAG
+                              entries, round 1); the paper and the stage kernels
+                              use face ghosts only (Sec. 2.1) */
 } amr_config;
 
 /* Face reconstructions of Sec. 3.2.  MUSCL slope limiters (two ghost
@@ -181,8 +188,8 @@ amr_status amr_create_forest(const amr_config *cfg, int init_level, amr_forest *
  * at once -- one kernel launch per phase sweeps every block of every
  * instance.  Each instance keeps its own domain, brick, periodicity,
  * max_level, boundaries, CFL number and time step; ndim, block_n, n_ghost,
- * precision, n_states, gamma, limiter, flux, gravity, host_only and the
- * allocation hook must be the same for all.  Capacity is the sum of the instances' max_blocks; each
+ * precision, n_states, gamma, limiter, flux, gravity, diagonal_ghosts,
+ * host_only and the allocation hook must be the same for all.  Capacity is the sum of the instances' max_blocks; each
  * instance is also held to its own max_blocks on regrid.  amr_create_forest
  * is the n = 1 case.  Errors as amr_create_forest. */
 amr_status amr_create_batch(const amr_config *cfgs, const int *init_levels, int n, amr_forest **out);

@@ -53,7 +53,8 @@ class Config(C.Structure):
                 ("gamma", C.c_double), ("cfl", C.c_double),
                 ("bc", C.c_int * 6), ("bc_val", (C.c_double * 8) * 6),
                 ("dev_alloc", AllocFn), ("dev_free", FreeFn), ("alloc_ctx", C.c_void_p),
-                ("host_only", C.c_int), ("limiter", C.c_int), ("flux", C.c_int), ("gravity", C.c_double * 3)]
+                ("host_only", C.c_int), ("limiter", C.c_int), ("flux", C.c_int), ("gravity", C.c_double * 3),
+                ("diagonal_ghosts", C.c_int)]
 
 
 class GhostEntry(C.Structure):
@@ -160,7 +161,8 @@ def spec_from_config(c: Config):
                           length=tuple(float(c.len[d]) for d in range(3)), max_level=int(c.max_level),
                           gamma=float(c.gamma), cfl=float(c.cfl), bc_type=tuple(int(c.bc[f]) for f in range(6)),
                           bc_val=tuple(tuple(float(c.bc_val[f][v]) for v in range(8)) for f in range(6)),
-                          limiter=int(c.limiter), flux=int(c.flux), gravity=tuple(float(c.gravity[d]) for d in range(3)))
+                          limiter=int(c.limiter), flux=int(c.flux), gravity=tuple(float(c.gravity[d]) for d in range(3)),
+                          diagonal_ghosts=int(c.diagonal_ghosts))
 
 
 def config_from_spec(spec, max_blocks, n_states=2, precision=64, host_only=False) -> Config:
@@ -171,6 +173,7 @@ def config_from_spec(spec, max_blocks, n_states=2, precision=64, host_only=False
     gv = getattr(spec, "gravity", (0.0, 0.0, 0.0))
     for d in range(3):
         c.gravity[d] = float(gv[d]) if d < spec.ndim else 0.0
+    c.diagonal_ghosts = int(getattr(spec, "diagonal_ghosts", 0))
     c.ndim, c.block_n, c.n_ghost, c.n_var = spec.ndim, spec.N, spec.ng, spec.ndim + 2
     for d in range(3):
         c.ntrees[d] = int(spec.ntrees[d]) if d < spec.ndim else 1

@@ -162,7 +162,7 @@ amr_status upload_pattern(amr_forest *f) {
     std::string why;
     std::vector<const Forest *> ptrs;
     for (const Forest &F : f->inst) ptrs.push_back(&F);
-    if (!build_pattern(ptrs, f->offset, f->pat, why)) return fail(f, AMR_ESTATE, "%s", why.c_str());
+    if (!build_pattern(ptrs, f->offset, f->pat, why, f->cfg.diagonal_ghosts != 0)) return fail(f, AMR_ESTATE, "%s", why.c_str());
     if (f->cfg.host_only) {
         f->pattern_rev = f->revision;
         return AMR_OK;
@@ -467,7 +467,7 @@ amr_status amr_create_batch(const amr_config *cfgs, const int *init_levels, int 
         if (c.ndim != c0.ndim || c.block_n != c0.block_n || c.n_ghost != c0.n_ghost || c.precision != c0.precision ||
             c.n_states != c0.n_states || c.gamma != c0.gamma || c.host_only != c0.host_only ||
             c.limiter != c0.limiter || c.flux != c0.flux || c.gravity[0] != c0.gravity[0] ||
-            c.gravity[1] != c0.gravity[1] || c.gravity[2] != c0.gravity[2] ||
+            c.gravity[1] != c0.gravity[1] || c.gravity[2] != c0.gravity[2] || c.diagonal_ghosts != c0.diagonal_ghosts ||
             c.dev_alloc != c0.dev_alloc || c.dev_free != c0.dev_free || c.alloc_ctx != c0.alloc_ctx)
             return AMR_EINVAL;
         capacity += c.max_blocks;
@@ -1045,7 +1045,7 @@ constexpr uint32_t kCkptVersion = 1;
 struct CkptHead {
     char magic[8];
     uint32_t version, n_inst;
-    int32_t precision, ndim, block_n, n_ghost, n_var, n_states, host_only, limiter, flux, pad;
+    int32_t precision, ndim, block_n, n_ghost, n_var, n_states, host_only, limiter, flux, diagonal_ghosts;
     double gamma, gravity[3];
     int64_t n_blocks;
 };
@@ -1115,6 +1115,7 @@ amr_status amr_save(const amr_forest *fc, const char *path, amr_stream stream) {
     h.host_only = c0.host_only;
     h.limiter = c0.limiter;
     h.flux = c0.flux;
+    h.diagonal_ghosts = c0.diagonal_ghosts;
     h.gamma = c0.gamma;
     for (int d = 0; d < 3; ++d) h.gravity[d] = c0.gravity[d];
     h.n_blocks = nblocks(f);
@@ -1181,6 +1182,7 @@ amr_status amr_load(const char *path, const amr_config *opts, amr_forest **out, 
         c.gamma = h.gamma;
         c.limiter = h.limiter;
         c.flux = h.flux;
+        c.diagonal_ghosts = h.diagonal_ghosts;
         for (int d = 0; d < 3; ++d) {
             c.gravity[d] = h.gravity[d];
             c.ntrees[d] = r.ntrees[d];

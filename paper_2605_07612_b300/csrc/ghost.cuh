@@ -4,7 +4,8 @@
 // F2C and BC entries (they read interior cells only); round 2 executes C2F
 // entries, whose limited prolongation reads round-1 ghosts of the coarse
 // block (the tangential neighbours at the face edge and the ghost layer
-// facing the fine block).  Only face ghost cells are written (Sec. 2.1).
+// facing the fine block).  Face ghost cells only (Sec. 2.1), unless the mesh
+// asks for edge and corner cells held by same-level leaves (DIAG entries).
 #pragma once
 
 #include "common.cuh"
@@ -115,9 +116,33 @@ __global__ void __launch_bounds__(256) k_ghost(GhostArgs<real> a, Geom g) {
     const int lane = threadIdx.x & 31;
     if (warp >= a.n) return;
     const Entry e = a.list[warp];
-    const int nd = e.face >> 1, side = e.face & 1;
     real *dstb = a.u + int64_t(e.dst) * g.bstride;
     const real *srcb = e.src >= 0 ? a.u + int64_t(e.src) * g.bstride : nullptr;
+    if (e.kind == KIND_DIAG) {
+        // edge / corner region in direction (dx, dy, dz): ghost box of the
+        // block, copied from the same-level neighbour's interior
+        const int dir[3] = {e.face % 3 - 1, (e.face / 3) % 3 - 1, e.face / 9 - 1};
+        int lo[3] = {0, 0, 0}, ext[3] = {1, 1, 1};
+        for (int d = 0; d < D; ++d) {
+            lo[d] = dir[d] < 0 ? -NG : (dir[d] > 0 ? N : 0);
+            ext[d] = dir[d] != 0 ? NG : N;
+        }
+        const int ncells = ext[0] * ext[1] * ext[2];
+        for (int idx = lane; idx < ncells * g.V; idx += 32) {
+            const int v = idx / ncells;
+            int c = idx - v * ncells;
+            int x[3];
+            x[0] = lo[0] + c % ext[0];
+            c /= ext[0];
+            x[1] = lo[1] + c % ext[1];
+            x[2] = lo[2] + c / ext[1];
+            const int y0 = x[0] - dir[0] * N, y1 = x[1] - dir[1] * N, y2 = D == 3 ? x[2] - dir[2] * N : 0;
+            dstb[int64_t(v) * g.ncell + cell_index<real>(g, x[0], x[1], x[2])] =
+                srcb[int64_t(v) * g.ncell + cell_index<real>(g, y0, y1, y2)];
+        }
+        return;
+    }
+    const int nd = e.face >> 1, side = e.face & 1;
     if constexpr (NG % 2 == 0) {
         if (e.kind == KIND_SRL) {
             if (nd == 0) srl_pairs<real, D, N, NG, 0>(dstb, srcb, side, lane);

@@ -10,7 +10,7 @@
 namespace amrb {
 
 bool build_pattern(const std::vector<const Forest *> &inst, const std::vector<int64_t> &offset, Pattern &P,
-                   std::string &err) {
+                   std::string &err, bool diagonal) {
     P = Pattern();
     int nb = 0;
     for (const Forest *F : inst) nb += int(F->leaves.size());
@@ -63,6 +63,23 @@ bool build_pattern(const std::vector<const Forest *> &inst, const std::vector<in
                 P.entries.push_back({KIND_F2C, f, b, o0 + fs, o, 0});
             }
         }
+        // edge and corner regions held by a same-level leaf
+        if (diagonal)
+            for (int dz = (D == 3 ? -1 : 0); dz <= (D == 3 ? 1 : 0); ++dz)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        const int dir[3] = {dx, dy, dz};
+                        if ((dx != 0) + (dy != 0) + (dz != 0) < 2) continue;
+                        int64_t q[3] = {A.g[0], A.g[1], A.g[2]};
+                        bool inside = true;
+                        for (int d = 0; d < D && inside; ++d) {
+                            q[d] += dir[d];
+                            inside = F.wrap(d, A.lev, q[d]);
+                        }
+                        if (!inside) continue;
+                        const int s = F.find(A.lev, q[0], q[1], q[2]);
+                        if (s >= 0) P.entries.push_back({KIND_DIAG, (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1), b, o0 + s, 0, 0});
+                    }
     }
     }
     std::sort(P.entries.begin(), P.entries.end(), [](const Entry &x, const Entry &y) {

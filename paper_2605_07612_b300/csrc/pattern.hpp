@@ -14,7 +14,7 @@ namespace amrb {
 
 constexpr int kMaxLevels = 13;   // levels 0..12 per instance
 
-enum : int32_t { KIND_SRL = 0, KIND_F2C = 1, KIND_BC = 2, KIND_C2F = 3 };
+enum : int32_t { KIND_SRL = 0, KIND_F2C = 1, KIND_BC = 2, KIND_C2F = 3, KIND_DIAG = 4 };
 
 struct Entry {
     int32_t kind, face, dst, src, offset, aux;
@@ -39,7 +39,7 @@ struct BlockInfo {
 
 struct Pattern {
     std::vector<Entry> entries;   // canonical order (kind, face, dst, offset)
-    std::vector<Entry> round1;    // SRL, F2C, BC
+    std::vector<Entry> round1;    // SRL, F2C, BC (and DIAG)
     std::vector<Entry> round2;    // C2F
     // round 1 when the stage kernel gathers same-level halos itself: every
     // non-SRL entry, plus the SRL entries of blocks that are the coarse
@@ -56,7 +56,10 @@ struct Pattern {
 // are numbered consecutively (instance i owns blocks offset[i] ..
 // offset[i] + n_i - 1).  Returns false (with a message) if some face has no
 // valid neighbour configuration (2:1 balance broken).
+// diagonal: also emit a KIND_DIAG entry (face = direction code (dx+1) +
+// 3 (dy+1) + 9 (dz+1)) for every edge / corner ghost region that a
+// same-level leaf holds; executed in round 1.
 bool build_pattern(const std::vector<const Forest *> &inst, const std::vector<int64_t> &offset, Pattern &out,
-                   std::string &err);
+                   std::string &err, bool diagonal = false);
 
 }  // namespace amrb

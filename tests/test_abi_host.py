@@ -1,7 +1,7 @@
 """Host-side checks of the CUDA library (no GPU needed): the shared object
 loads and exports every function include/amr.h declares; configurations are
 validated; the production forest and face-walk ghost pattern builder agree
-bit for bit with the oracle's brute-force classification (Sec. 2.2, 2.5)."""
+bit for bit with the oracle's brute-force classification (Sec. 2.2, 2.6)."""
 import ctypes as C
 import os
 import re
@@ -70,7 +70,7 @@ def test_capacity_overflow_leaves_mesh_unchanged():
     np.testing.assert_array_equal(f.pattern(), pat0)
 
 
-def random_pair(ndim, seed, rounds=3):
+def random_pair(ndim, seed, rounds=3, diagonal=0):
     rng = np.random.default_rng(1000 + seed)
     if ndim == 2:
         nt = (int(rng.integers(1, 5)), int(rng.integers(1, 5)), 1)
@@ -82,6 +82,7 @@ def random_pair(ndim, seed, rounds=3):
         per = tuple(int(x) for x in rng.integers(0, 2, 3))
         sp = synth.MeshSpec(ndim=3, N=8, ng=2, ntrees=nt, periodic=per, max_level=3,
                             bc_type=(1, 2, 1, 2, 3, 3))
+    sp.diagonal_ghosts = diagonal
     lvl0 = int(rng.integers(0, 2))
     om = oracle.Mesh(sp, lvl0)
     pm = amr.Forest(sp, lvl0, max_blocks=200000, host_only=True)
@@ -110,6 +111,17 @@ def test_production_pattern_matches_brute_force_3d(seed):
     np.testing.assert_array_equal(lo, lp)
     np.testing.assert_array_equal(go, gp)
     np.testing.assert_array_equal(om.pattern(), pm.pattern())
+
+
+@pytest.mark.parametrize("ndim,seed", [(2, s) for s in range(20)] + [(3, s) for s in range(10)])
+def test_production_pattern_with_diagonal_ghosts_matches_brute_force(ndim, seed):
+    """With edge/corner ghosts switched on, the production pattern (face walk
+    plus same-level diagonal neighbours) equals the oracle's point-location
+    brute force, entry for entry."""
+    sp, om, pm = random_pair(ndim, seed, diagonal=1)
+    po, pp = om.pattern(), pm.pattern()
+    np.testing.assert_array_equal(po, pp)
+    assert (pp[:, 0] == 4).any()
 
 
 def test_uniform_3d_configs_shape():
