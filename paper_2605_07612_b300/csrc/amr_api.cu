@@ -186,12 +186,12 @@ amr_status upload_pattern(amr_forest *f) {
 template <class real, int D>
 amr_status launch_stage(amr_forest *f, const StageArgs<real> &a, cudaStream_t st) {
     const int N = f->cfg.block_n, NG = f->cfg.n_ghost;
-    if constexpr (std::is_same<real, float>::value && D == 3) {
-        // the pair kernel implements the Rusanov flux only
+    if constexpr (std::is_same<real, float>::value) {
+        // the pair kernels implement the Rusanov flux only
         if (NG == 2 && !f->scalar_stage && a.flux == AMR_FLUX_RUSANOV) {
-            if (N == 8) return launch_stage_pair<8>(f, a, st);
-            if (N == 16) return launch_stage_pair<16>(f, a, st);
-            if (N == 32) return launch_stage_pair<32>(f, a, st);
+            if (N == 8) return launch_stage_pair<D, 8>(f, a, st);
+            if (N == 16) return launch_stage_pair<D, 16>(f, a, st);
+            if (N == 32) return launch_stage_pair<D, 32>(f, a, st);
         }
     }
     const bool gen = a.limiter != AMR_LIM_MINMOD || a.flux != AMR_FLUX_RUSANOV;
@@ -966,11 +966,12 @@ amr_status amr_autotune(amr_forest *f, int *choice, double *best_ms, amr_stream 
     if (r != AMR_OK) return r;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // candidates: blocks (tiles) per CTA 1, 2, 4 or a persistent grid, for
-    // each kernel / staging tile: the FP32 3D pair kernel with tile 16 and,
-    // for blocks above 8^3, tile 8; the per-cell kernel
+    // each kernel / staging tile: the FP32 pair kernel (2D or 3D) with tile
+    // 16 and, for blocks above 8 cells a side, tile 8; the per-cell kernel
     struct Cand { bool scalar; int ipc; bool pers; int tile; };
     std::vector<Cand> cands;
-    const bool pair_ok = f->cfg.precision == 32 && f->cfg.ndim == 3 && f->cfg.n_ghost == 2 && f->cfg.flux == AMR_FLUX_RUSANOV;
+    const bool pair_ok = f->cfg.precision == 32 && f->cfg.n_ghost == 2 && f->cfg.flux == AMR_FLUX_RUSANOV &&
+                         f->cfg.limiter != AMR_LIM_WENO5;
     std::vector<std::pair<bool, int>> kernels;   // (per-cell kernel, pair tile)
     if (pair_ok) {
         kernels.push_back({false, 0});
@@ -1024,8 +1025,9 @@ amr_status amr_set_launch_shape(amr_forest *f, int choice) {
     if (!f || choice < 0) return AMR_EINVAL;
     const int tile8 = choice / 1000, scalar = (choice % 1000) / 100, ipc = choice % 100;
     if (tile8 > 1 || scalar > 1 || ipc > 64 || (tile8 && scalar)) return AMR_EINVAL;
-    const bool pair_ok = f->cfg.precision == 32 && f->cfg.ndim == 3 && f->cfg.n_ghost == 2 && f->cfg.flux == AMR_FLUX_RUSANOV;
-    if (tile8 && (!pair_ok || f->cfg.block_n <= 8)) return fail(f, AMR_EINVAL, "8 x 8 tiles need the FP32 3D pair kernel and blocks above 8^3");
+    const bool pair_ok = f->cfg.precision == 32 && f->cfg.n_ghost == 2 && f->cfg.flux == AMR_FLUX_RUSANOV &&
+                         f->cfg.limiter != AMR_LIM_WENO5;
+    if (tile8 && (!pair_ok || f->cfg.block_n <= 8)) return fail(f, AMR_EINVAL, "8 x 8 tiles need an FP32 pair kernel and blocks above 8 cells a side");
     f->scalar_stage = scalar == 1;
     f->pair_tile = tile8 ? 8 : 0;
     f->persistent = ipc == 0;

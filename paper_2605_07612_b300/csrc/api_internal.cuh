@@ -46,7 +46,7 @@ struct amr_forest {
     uint64_t graph_rev = ~0ull;
     int64_t graph_nodes = 0;
     int graph_flags = -1;
-    bool scalar_stage = false;   // per-cell FP32 kernel instead of the pair kernel (tuning choice)
+    bool scalar_stage = false;   // per-cell FP32 kernel instead of a pair kernel (tuning choice)
     int items_per_cta = 1;       // stage launch: CTAs loop over this many (block, tile) items
     bool persistent = false;     // stage launch: grid = SMs x resident CTAs, grid-stride sweep
     int pair_tile = 0;           // FP32 pair kernel staging tile: 0 default (16, N for N = 8), or 8
@@ -92,7 +92,7 @@ template <class real, int D>
 amr_status launch_ghosts(amr_forest *f, int s, cudaStream_t st, bool gather);
 template <class real, int D, int N, int NG, bool GEN>
 amr_status launch_stage_t(amr_forest *f, const StageArgs<real> &a, cudaStream_t st);
-template <int N>
+template <int D, int N>
 amr_status launch_stage_pair(amr_forest *f, const StageArgs<float> &a, cudaStream_t st);
 template <class real, int D>
 amr_status launch_weno(amr_forest *f, const StageArgs<real> &a, real *prim, real *flux, cudaStream_t st);

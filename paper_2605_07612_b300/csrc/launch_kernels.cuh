@@ -7,6 +7,7 @@
 #include "ghost.cuh"
 #include "stage.cuh"
 #include "stage_pair.cuh"
+#include "stage_pair2d.cuh"
 #include "stage_weno.cuh"
 
 namespace amrb {
@@ -67,17 +68,32 @@ amr_status launch_stage_t(amr_forest *f, const StageArgs<real> &a, cudaStream_t 
     return AMR_OK;
 }
 
-// FP32, 3D, two ghost layers: the packed cell-pair kernel, specialised for
-// one and two previous states (the two stages of Heun's method), for the
-// slope limiter (minmod, MC, van Leer; Rusanov flux only) and for the staging
-// tile (16, or 8 when the autotuner picks it for 16^3 / 32^3 blocks)
+// FP32, two ghost layers: the packed cell-pair kernels (3D plane march, 2D
+// single plane), specialised for one and two previous states (the two stages
+// of Heun's method), for the slope limiter (minmod, MC, van Leer; Rusanov
+// flux only) and for the staging tile (16, or 8 when the autotuner picks it
+// for blocks above 8 cells a side)
+template <int D, int N, int TT, int NPREV, int LIM>
+struct PairKernel;
 template <int N, int TT, int NPREV, int LIM>
-amr_status launch_stage_pair_n(amr_forest *f, const StageArgs<float> &a, cudaStream_t st) {
+struct PairKernel<3, N, TT, NPREV, LIM> {
     using Sh = PairShape<N, TT>;
+    static constexpr auto fn = k_stage_pair<N, TT, NPREV, LIM>;
+};
+template <int N, int TT, int NPREV, int LIM>
+struct PairKernel<2, N, TT, NPREV, LIM> {
+    using Sh = PairShape2D<N, TT>;
+    static constexpr auto fn = k_stage_pair2d<N, TT, NPREV, LIM>;
+};
+
+template <int D, int N, int TT, int NPREV, int LIM>
+amr_status launch_stage_pair_n(amr_forest *f, const StageArgs<float> &a, cudaStream_t st) {
+    using K = PairKernel<D, N, TT, NPREV, LIM>;
+    using Sh = typename K::Sh;
     static bool attr_done = false;
     const size_t smem = Sh::smem_bytes(NPREV);
     if (!attr_done) {
-        CU(cudaFuncSetAttribute(k_stage_pair<N, TT, NPREV, LIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        CU(cudaFuncSetAttribute(K::fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
         attr_done = true;
     }
     const int64_t items = nblocks(f) * Sh::TILES;
@@ -85,35 +101,35 @@ amr_status launch_stage_pair_n(amr_forest *f, const StageArgs<float> &a, cudaStr
         StageArgs<float> b = a;
         b.n_items = int(items);
         int occ = 1;
-        if (f->persistent) CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_stage_pair<N, TT, NPREV, LIM>, Sh::NT, smem));
+        if (f->persistent) CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, K::fn, Sh::NT, smem));
         const int64_t grid = stage_grid(f, items, occ);
-        k_stage_pair<N, TT, NPREV, LIM><<<unsigned(grid), Sh::NT, smem, st>>>(b, f->geom);
+        K::fn<<<unsigned(grid), Sh::NT, smem, st>>>(b, f->geom);
         ++f->launches;
     }
     CU(cudaGetLastError());
     return AMR_OK;
 }
 
-template <int N, int TT, int LIM>
+template <int D, int N, int TT, int LIM>
 amr_status launch_stage_pair_l(amr_forest *f, const StageArgs<float> &a, cudaStream_t st) {
-    if (a.nprev == 1) return launch_stage_pair_n<N, TT, 1, LIM>(f, a, st);
-    if (a.nprev == 2) return launch_stage_pair_n<N, TT, 2, LIM>(f, a, st);
-    return launch_stage_pair_n<N, TT, -1, LIM>(f, a, st);
+    if (a.nprev == 1) return launch_stage_pair_n<D, N, TT, 1, LIM>(f, a, st);
+    if (a.nprev == 2) return launch_stage_pair_n<D, N, TT, 2, LIM>(f, a, st);
+    return launch_stage_pair_n<D, N, TT, -1, LIM>(f, a, st);
 }
 
-template <int N, int TT>
+template <int D, int N, int TT>
 amr_status launch_stage_pair_t(amr_forest *f, const StageArgs<float> &a, cudaStream_t st) {
-    if (a.limiter == AMR_LIM_MC) return launch_stage_pair_l<N, TT, 1>(f, a, st);
-    if (a.limiter == AMR_LIM_VANLEER) return launch_stage_pair_l<N, TT, 2>(f, a, st);
-    return launch_stage_pair_l<N, TT, 0>(f, a, st);
+    if (a.limiter == AMR_LIM_MC) return launch_stage_pair_l<D, N, TT, 1>(f, a, st);
+    if (a.limiter == AMR_LIM_VANLEER) return launch_stage_pair_l<D, N, TT, 2>(f, a, st);
+    return launch_stage_pair_l<D, N, TT, 0>(f, a, st);
 }
 
-template <int N>
+template <int D, int N>
 amr_status launch_stage_pair(amr_forest *f, const StageArgs<float> &a, cudaStream_t st) {
     if constexpr (N > 8) {
-        if (f->pair_tile == 8) return launch_stage_pair_t<N, 8>(f, a, st);
+        if (f->pair_tile == 8) return launch_stage_pair_t<D, N, 8>(f, a, st);
     }
-    return launch_stage_pair_t<N, (N < 16 ? N : 16)>(f, a, st);
+    return launch_stage_pair_t<D, N, (N < 16 ? N : 16)>(f, a, st);
 }
 
 // WENO5 stage: primitives, face fluxes, update (three launches); prim and

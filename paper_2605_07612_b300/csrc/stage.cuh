@@ -47,8 +47,8 @@ struct StageArgs {
     int gather;                  // halo cells across SRL faces from the neighbour's interior
     int n_items;                 // blocks x column tiles; CTAs loop over them with a grid stride
     real gamma;
-    int limiter;                 // amr_limiter (per-cell kernel; the pair kernel is minmod only)
-    int flux;                    // amr_flux (per-cell kernel; the pair kernel is Rusanov only)
+    int limiter;                 // amr_limiter (the pair kernels: minmod, MC, van Leer)
+    int flux;                    // amr_flux (the pair kernels: Rusanov only)
     int gravity_on;              // add the source S = (0, rho g, rho g.u) of u_deriv
     real grav[3];
 };
