@@ -43,7 +43,8 @@ class Params(C.Structure):
                 ("lo", C.c_double * 3), ("len", C.c_double * 3),
                 ("max_level", C.c_int), ("gamma", C.c_double), ("cfl", C.c_double),
                 ("bc_type", C.c_int * 6), ("bc_val", (C.c_double * 8) * 6),
-                ("limiter", C.c_int), ("flux", C.c_int), ("gravity", C.c_double * 3), ("diagonal", C.c_int)]
+                ("limiter", C.c_int), ("flux", C.c_int), ("gravity", C.c_double * 3), ("diagonal", C.c_int),
+                ("physics", C.c_int), ("velocity", C.c_double * 3)]
 
 
 def _lib_handle():
@@ -93,7 +94,7 @@ def _ptr(a: np.ndarray):
 
 def params_from_spec(spec) -> Params:
     p = Params()
-    p.ndim, p.N, p.ng, p.nvar = spec.ndim, spec.N, spec.ng, spec.ndim + 2
+    p.ndim, p.N, p.ng, p.nvar = spec.ndim, spec.N, spec.ng, spec.nvar
     for d in range(3):
         p.ntrees[d] = int(spec.ntrees[d]) if d < spec.ndim else 1
         p.periodic[d] = int(spec.periodic[d]) if d < spec.ndim else 1
@@ -111,6 +112,10 @@ def params_from_spec(spec) -> Params:
     for d in range(3):
         p.gravity[d] = float(gv[d]) if d < spec.ndim else 0.0
     p.diagonal = int(getattr(spec, "diagonal_ghosts", 0))
+    p.physics = int(getattr(spec, "physics", 0))
+    vel = getattr(spec, "velocity", (0.0, 0.0, 0.0))
+    for d in range(3):
+        p.velocity[d] = float(vel[d]) if d < spec.ndim else 0.0
     return p
 
 
@@ -127,8 +132,8 @@ def weno5(a, b, c, d, e) -> float:
 
 def face_flux(spec, n: int, wL, wR) -> np.ndarray:
     """The numerical flux (spec.flux: 0 Rusanov, 1 HLL) along dimension n
-    between primitive states wL and wR."""
-    V = spec.ndim + 2
+    between primitive states wL and wR (Euler, or the advected scalar)."""
+    V = spec.nvar
     a = np.ascontiguousarray(wL, dtype=np.float64)
     b = np.ascontiguousarray(wR, dtype=np.float64)
     F = np.zeros(V)

@@ -26,7 +26,9 @@
  *   - Rusanov flux with the Einfeldt speed |u_roe| + d_roe (Sec. 3.2-3.5);
  *   - dt = CFL / max over leaf cells of sum_d (|v_d| + c) / dx_d (Sec. 3.2);
  *   - flux fixing is applied after every Runge-Kutta stage with that stage's
- *     time step (Sec. 2.7).
+ *     time step (Sec. 2.7);
+ *   - scalar advection (Sec. 3.4) uses the same flux schemes with the wave
+ *     speeds min(v_n, 0), max(v_n, 0); its HLL flux is 0 where v_n = 0.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -59,6 +61,9 @@ typedef struct {
     double gravity[3];     /* g of the source term S = (0, rho g, rho g.u) (Sec. 4.2) */
     int diagonal;          /* 1: also fill edge and corner ghost cells that a
                               same-level leaf holds (the paper fills face ghosts only) */
+    int physics;           /* 0 Euler gas dynamics (Sec. 3.5), 1 scalar advection
+                              (Sec. 3.4, Eq. 13; nvar = 1) */
+    double velocity[3];    /* the uniform advection velocity v of Eq. 13 */
 } orc_params;
 
 enum { BC_NONE = 0, BC_DIRICHLET = 1, BC_NEUMANN = 2, BC_DATA = 3 };
@@ -843,10 +848,54 @@ static void hll(int D, double gam, int n, const double *wL, const double *wR, do
     for (int v = 0; v < D + 2; v++) F[v] = (sR * FL[v] - sL * FR[v] + sL * sR * (UR[v] - UL[v])) / (sR - sL);
 }
 
+/* ------------------------------------------------------------------------ */
+/* Scalar advection (Sec. 3.4, Eq. 13): d rho / dt + div(rho v) = 0 with a   */
+/* uniform v.  Primitive and conservative variables are the same; along      */
+/* dimension n the smallest and largest wave speeds are min(v_n, 0) and      */
+/* max(v_n, 0), and the physical flux is rho v_n.  The two flux schemes of   */
+/* Sec. 3.2 with those speeds:                                               */
+/*   Rusanov: a = max(|min(v_n,0)|, |max(v_n,0)|) = |v_n|,                   */
+/*            F = (rL v_n + rR v_n) / 2 - a (rR - rL) / 2                    */
+/*   HLL:     sL = min(v_n,0), sR = max(v_n,0),                              */
+/*            F = (sR rL v_n - sL rR v_n + sL sR (rR - rL)) / (sR - sL),     */
+/*            and F = 0 when v_n = 0 (no wave, no flux).                     */
+/* ------------------------------------------------------------------------ */
+
+static void advection_flux(const orc_params *p, int n, double rL, double rR, double *F)
+{
+    double vn = p->velocity[n];
+    double FL = rL * vn, FR = rR * vn;
+    double sL = vn < 0.0 ? vn : 0.0;
+    double sR = vn > 0.0 ? vn : 0.0;
+    if (p->flux == 1) {
+        if (sR - sL == 0.0) F[0] = 0.0;
+        else F[0] = (sR * FL - sL * FR + sL * sR * (rR - rL)) / (sR - sL);
+    } else {
+        double a = fabs(sL) > fabs(sR) ? fabs(sL) : fabs(sR);
+        F[0] = 0.5 * (FL + FR) - 0.5 * a * (rR - rL);
+    }
+}
+
 static void face_flux(const orc_params *p, int n, const double *wL, const double *wR, double *F)
 {
-    if (p->flux == 1) hll(p->ndim, p->gamma, n, wL, wR, F);
+    if (p->physics == 1) advection_flux(p, n, wL[0], wR[0], F);
+    else if (p->flux == 1) hll(p->ndim, p->gamma, n, wL, wR, F);
     else rusanov(p->ndim, p->gamma, n, wL, wR, F);
+}
+
+/* primitive variables of the configured physics (the identity for advection) */
+static void primitive_of(const orc_params *p, const double *U, double *w)
+{
+    if (p->physics == 1) w[0] = U[0];
+    else to_primitive(p->ndim, p->gamma, U, w);
+}
+
+/* a state the physics cannot hold: Euler with rho <= 0 or p <= 0 (the
+ * advected scalar has no such bound) */
+static int nonphysical(const orc_params *p, const double *w)
+{
+    if (p->physics == 1) return 0;
+    return !(w[0] > 0.0) || !(w[p->ndim + 1] > 0.0);
 }
 
 /* Generalized minmod of the paper's Eq. 1: 0 when a and b differ in sign,
@@ -943,8 +992,8 @@ int orc_stage(const orc_mesh *m, const double *ud, double *uo, int nprev,
                     if (nout > 1) continue;
                     double U[5], W[5];
                     for (int v = 0; v < V; v++) U[v] = ud[atv(p, b, v, x)];
-                    to_primitive(D, gam, U, W);
-                    if (!(W[0] > 0.0) || !(W[D + 1] > 0.0)) bad = 1;
+                    primitive_of(p, U, W);
+                    if (nonphysical(p, W)) bad = 1;
                     int64_t c = (int64_t)ii + S * ((int64_t)jj + S * (int64_t)kk);
                     for (int v = 0; v < V; v++) wp[(int64_t)v * nc + c] = W[v];
                 }
@@ -980,7 +1029,7 @@ int orc_stage(const orc_mesh *m, const double *ud, double *uo, int nprev,
                                 wR[v] = w0[v] - 0.5 * limited_slope(p->limiter, w0[v] - wm1[v], w1[v] - w0[v]);
                             }
                         }
-                        if (!(wL[0] > 0.0) || !(wL[D + 1] > 0.0) || !(wR[0] > 0.0) || !(wR[D + 1] > 0.0)) bad = 1;
+                        if (nonphysical(p, wL) || nonphysical(p, wR)) bad = 1;
                         face_flux(p, n, wL, wR, F);
                         int64_t tt = t0 + (int64_t)N * t1;
                         for (int v = 0; v < V; v++) fl[((int64_t)n * V + v) * nfl + fp + (N + 1) * tt] = F[v];
@@ -1010,7 +1059,9 @@ int orc_stage(const orc_mesh *m, const double *ud, double *uo, int nprev,
                         /* gravity source S = (0, rho g, rho g.u) from the
                          * conservative state of the cell (Sec. 3.2 step order:
                          * source, then minus the flux divergence) */
-                        if (v >= 1 && v <= D) {
+                        if (p->physics == 1) {
+                            /* advection: no source term */
+                        } else if (v >= 1 && v <= D) {
                             r = r + ud[atv(p, b, 0, x)] * p->gravity[v - 1];
                         } else if (v == D + 1) {
                             double sg = 0.0;
@@ -1093,7 +1144,8 @@ int orc_stage(const orc_mesh *m, const double *ud, double *uo, int nprev,
 
 /* ------------------------------------------------------------------------ */
 /* CFL time-step limit (Sec. 3.2 step 2c): max over interior leaf cells of    */
-/* sum_d (|v_d| + c) / dx_d, with c = sqrt(gamma p / rho) (Eq. 16).           */
+/* sum_d (|v_d| + c) / dx_d, with c = sqrt(gamma p / rho) (Eq. 16); for      */
+/* scalar advection sum_d |v_d| / dx_d with the uniform velocity.            */
 /* dt = cfl / that maximum.                                                  */
 /* ------------------------------------------------------------------------ */
 
@@ -1107,12 +1159,17 @@ double orc_max_speed(const orc_mesh *m, const double *u)
         for (int k = 0; k < kr; k++)
             for (int j = 0; j < N; j++)
                 for (int i = 0; i < N; i++) {
-                    double U[5], W[5];
-                    for (int v = 0; v < V; v++) U[v] = u[at(p, b, v, i, j, k)];
-                    to_primitive(D, p->gamma, U, W);
-                    double c = sqrt(p->gamma * W[D + 1] / W[0]);
                     double s = 0.0;
-                    for (int d = 0; d < D; d++) s = s + (fabs(W[1 + d]) + c) / dx_at(p, d, m->lev[b]);
+                    if (p->physics == 1) {
+                        /* advection: the wave speeds are those of v (Sec. 3.4) */
+                        for (int d = 0; d < D; d++) s = s + fabs(p->velocity[d]) / dx_at(p, d, m->lev[b]);
+                    } else {
+                        double U[5], W[5];
+                        for (int v = 0; v < V; v++) U[v] = u[at(p, b, v, i, j, k)];
+                        to_primitive(D, p->gamma, U, W);
+                        double c = sqrt(p->gamma * W[D + 1] / W[0]);
+                        for (int d = 0; d < D; d++) s = s + (fabs(W[1 + d]) + c) / dx_at(p, d, m->lev[b]);
+                    }
                     if (s > best) best = s;
                 }
     }
@@ -1145,7 +1202,8 @@ void orc_conserved(const orc_mesh *m, const double *u, double *sums)
 /*   E_n = |u_{n-1} - 2u_n + u_{n+1}| /                                      */
 /*         (eps_abs + |u_n - u_{n-1}| + |u_{n+1} - u_n| + eps u*),             */
 /*   u*  = |u_{n-1}| + 2|u_n| + |u_{n+1}|,  |E| = sqrt(sum_n E_n^2),          */
-/* evaluated on density and pressure; a cell's value is the larger of the     */
+/* evaluated on density and pressure (on the scalar for advection); a cell's */
+/* value is the larger of the                                                */
 /* two.  +1 if some cell exceeds c_ref, -1 if every cell is below c_deref,    */
 /* else 0.  u must have face ghosts filled.                                   */
 /* ------------------------------------------------------------------------ */
@@ -1179,8 +1237,9 @@ void orc_lohner_flags(const orc_mesh *m, const double *u, double c_ref, double c
                                 x[n] += q;
                                 double U[5], W[5];
                                 for (int v = 0; v < V; v++) U[v] = u[atv(p, b, v, x)];
-                                to_primitive(D, p->gamma, U, W);
-                                val[q + 1] = which == 0 ? W[0] : W[D + 1];
+                                primitive_of(p, U, W);
+                                /* advection: the scalar stands in for both */
+                                val[q + 1] = (which == 0 || p->physics == 1) ? W[0] : W[D + 1];
                             }
                             double e = lohner_1d(val[0], val[1], val[2], eps, eps_abs);
                             e2 = e2 + e * e;

@@ -11,7 +11,9 @@ synthetic initial data:
   * a random smooth 3D density/velocity field (`fourier3d`),
   * a spherical over-pressure region (`over_pressure`),
   * Sod shock tubes (`shock_tube`), a smooth density wave (`density_wave`),
-  * the linear field phi = x + 2y + 3z of the AMR ghost-cell test (Sec. 4.3).
+  * the linear field phi = x + 2y + 3z of the AMR ghost-cell test (Sec. 4.3),
+  * the advected scalar of Sec. 4.1: the smoothed sphere (Eq. 17), the
+    Gaussian (Eq. 19) and a smooth periodic wave, with exact solutions.
 Random numbers come from numpy's PCG64 (mode parameters) or from SplitMix64
 (per-cell noise), so that a cell's noise depends only on its global index.
 """
@@ -49,10 +51,12 @@ class MeshSpec:
     flux: int = 0             # 0 Rusanov, 1 HLL
     gravity: Sequence[float] = (0.0, 0.0, 0.0)   # source term S = (0, rho g, rho g.u)
     diagonal_ghosts: int = 0  # 1: also fill edge/corner ghosts held by same-level leaves
+    physics: int = 0          # 0 Euler gas dynamics, 1 scalar advection (one variable)
+    velocity: Sequence[float] = (0.0, 0.0, 0.0)   # uniform advection velocity
 
     @property
     def nvar(self) -> int:
-        return self.ndim + 2
+        return 1 if self.physics == 1 else self.ndim + 2
 
     @property
     def side(self) -> int:
@@ -384,3 +388,60 @@ def rayleigh_taylor_spec(ndim=3, N=16, ntrees=None, limiter=2, rho_hi=1.0, rho_l
     return MeshSpec(ndim=ndim, N=N, ng=ng, ntrees=tuple(nt), periodic=tuple(per), gamma=gam, cfl=0.5,
                     bc_type=tuple(bct), bc_val=tuple(tuple(r) for r in bcv), limiter=limiter,
                     gravity=tuple(grav), **kw)
+
+
+# ------------------------------------------------------ scalar advection --
+
+def advection_spec(ndim=2, N=16, ntrees=None, limiter=2, velocity=(1.0, 1.0, 1.0), ng=None, **kw) -> MeshSpec:
+    """Sec. 4.1 setup: the scalar advection equation (Eq. 13) on the periodic
+    unit square/cube with a uniform velocity (default v_i = 1)."""
+    nt = ntrees if ntrees is not None else tuple([4] * ndim + [1] * (3 - ndim))
+    if ng is None:
+        ng = 3 if limiter == 3 else 2
+    vel = tuple(float(velocity[d]) if d < ndim else 0.0 for d in range(3))
+    return MeshSpec(ndim=ndim, N=N, ng=ng, ntrees=tuple(nt), periodic=(1, 1, 1), limiter=limiter,
+                    physics=1, velocity=vel, **kw)
+
+
+def _periodic_distance(spec: MeshSpec, X, centre):
+    """Distance to `centre` under the minimum-image convention of the
+    periodic domain."""
+    d2 = 0.0
+    for d in range(spec.ndim):
+        L = spec.length[d]
+        r = X[d] - centre[d]
+        r = r - L * np.round(r / L)
+        d2 = d2 + r * r
+    return np.sqrt(d2)
+
+
+def _moved_centre(spec: MeshSpec, t):
+    return [spec.lo[d] + 0.5 * spec.length[d] + spec.velocity[d] * t for d in range(spec.ndim)]
+
+
+def advection_sphere(spec: MeshSpec, lev, g, t=0.0, R=0.1, delta=0.05):
+    """Eq. 17: 1 inside d < R - delta, 1 - 3q^2 + 2q^3 with q = 1 + (d - R) /
+    delta in the shell, 0 outside; d is the distance from the domain centre
+    (moved by v t, periodic images), sampled at cell centres."""
+    X = cell_centres(spec, lev, g)
+    d = _periodic_distance(spec, X, _moved_centre(spec, t))
+    q = 1.0 + (d - R) / delta
+    rho = np.where(d < R - delta, 1.0, np.where(d < R, 1.0 - 3.0 * q * q + 2.0 * q * q * q, 0.0))
+    return mask_interior(spec, rho.reshape(len(rho), 1, -1).copy())
+
+
+def advection_gaussian(spec: MeshSpec, lev, g, t=0.0, R=0.1):
+    """Eq. 19: exp(-d^2 / R^2) around the domain centre moved by v t."""
+    X = cell_centres(spec, lev, g)
+    d = _periodic_distance(spec, X, _moved_centre(spec, t))
+    rho = np.exp(-(d * d) / (R * R))
+    return mask_interior(spec, rho.reshape(len(rho), 1, -1).copy())
+
+
+def advection_wave(spec: MeshSpec, lev, g, t=0.0, amp=0.5, k=(1, 1, 1)):
+    """rho = 1 + amp sin(2 pi sum_d k_d (x_d - v_d t)): smooth and periodic, the
+    exact solution of Eq. 13 at time t."""
+    X = cell_centres(spec, lev, g)
+    s = sum(k[d] * (X[d] - spec.velocity[d] * t) / spec.length[d] for d in range(spec.ndim))
+    rho = 1.0 + amp * np.sin(2.0 * np.pi * s)
+    return mask_interior(spec, rho.reshape(len(rho), 1, -1).copy())
