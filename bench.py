@@ -333,6 +333,7 @@ def run_ours(args, rank, world, dist):
         rtw["context"] = "paper, 1x H100, FP64: 0.48 GCUPS for 16^3 blocks (Table 1)"
         extras["rayleigh_taylor_weno5"] = rtw
         extras["batched_2d"] = run_batched(args, amr, torch, stream, barrier, world)
+        extras["scalar_advection"] = run_advection(args, amr, torch, stream, barrier, world)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -428,6 +429,58 @@ def run_batched(args, amr, torch, stream, barrier, world):
             "steps": steps, "autotune_choice": choice,
             "workload": "64 2D AMR meshes, 4x4..64x64 base blocks of 16^2, 1-4 levels (Lohner-refined), KH or Sod, FP32, "
                         "one launch per phase over all meshes, step replayed as a CUDA graph"}
+
+
+# ------------------------------------------------------ scalar advection --
+
+# the paper's uniform-grid advection runs on one H100, FP64 (Table 1), in
+# GCUPS: (limiter, ndim, domain cells per side, block size) -> value
+ADVECTION_PAPER = {("vanleer", 2, 2048, 32): 13.33, ("vanleer", 2, 2048, 16): 9.83, ("vanleer", 2, 2048, 8): 4.26,
+                   ("vanleer", 3, 256, 32): 7.59, ("vanleer", 3, 256, 16): 8.64, ("vanleer", 3, 256, 8): 6.95,
+                   ("weno5", 2, 2048, 32): 6.91, ("weno5", 2, 2048, 16): 5.46,
+                   ("weno5", 3, 256, 32): 3.72, ("weno5", 3, 256, 16): 4.23}
+
+
+def run_advection(args, amr, torch, stream, barrier, world):
+    """The scalar advection test of Sec. 4.1 on uniform periodic grids (the
+    first half of Table 1): v_i = 1, the smoothed sphere of Eq. 17, Heun
+    with CFL 0.5, van Leer (2 ghost layers) or WENO5 (3), FP64 as in the
+    paper and FP32.  Steps replayed as a CUDA graph; van Leer gathers halos."""
+    rows = {}
+    cases = [("vanleer", 2, 2048, 32, 64), ("vanleer", 2, 2048, 16, 64), ("vanleer", 2, 2048, 16, 32),
+             ("vanleer", 3, 256, 32, 64), ("vanleer", 3, 256, 16, 64), ("vanleer", 3, 256, 8, 64),
+             ("vanleer", 3, 256, 16, 32),
+             ("weno5", 2, 2048, 16, 64), ("weno5", 3, 256, 16, 64), ("weno5", 3, 256, 16, 32)]
+    for lim, nd, n, bn, prec in cases:
+        limiter = 2 if lim == "vanleer" else 3
+        sp = synth.advection_spec(ndim=nd, N=bn, ntrees=(n // bn,) * nd + (1,) * (3 - nd), limiter=limiter,
+                                  velocity=(1.0, 1.0, 1.0))
+        f = amr.Forest(sp, 0, precision=prec)
+        lev, g = f.blocks()
+        f.set_state(0, synth.advection_sphere(sp, lev, g).astype(f.dtype))
+        f.compute_dt(0, stream=stream)
+        gather = limiter != 3
+        if gather:
+            f.autotune(stream=stream)
+        steps = max(4, args.steps // 2)
+        f.step(2, use_graph=True, gather=gather, stream=stream)
+        stream.synchronize()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        f.step(steps, use_graph=True, gather=gather, stream=stream)
+        e1.record(stream)
+        stream.synchronize()
+        ms = e0.elapsed_time(e1)
+        cells = n ** nd
+        key = "%s %dD %d^%d b%d fp%d" % (lim, nd, n, nd, bn, prec)
+        rows[key] = {"value": 2.0 * cells * steps * world / (ms * 1e-3), "ms_per_step": ms / steps,
+                     "status": f.sync_status(), "paper_h100_fp64_gcups": ADVECTION_PAPER.get((lim, nd, n, bn))}
+        del f
+        torch.cuda.empty_cache()
+    rows["context"] = "paper values: one H100, FP64 (Table 1), other hardware"
+    return rows
 
 
 # --------------------------------------------- static and adaptive AMR --

@@ -87,7 +87,7 @@ typedef struct {
     int ndim;              /* 2 or 3 */
     int block_n;           /* N: 8, 16 or 32 */
     int n_ghost;           /* ghost layers, 1..4 (the Euler stage needs >= 2) */
-    int n_var;             /* ndim + 2 (rho, rho v, E) */
+    int n_var;             /* Euler: ndim + 2 (rho, rho v, E); advection: 1 */
     int ntrees[3];         /* brick of trees (unused entries 1) */
     int periodic[3];
     double lo[3], len[3];  /* domain corner and extent */
@@ -112,7 +112,19 @@ typedef struct {
                               regions held by same-level leaves (AMR_GHOST_DIAG
                               entries, round 1); the paper and the stage kernels
                               use face ghosts only (Sec. 2.1) */
+    int physics;           /* amr_physics: equations of the stage (Sec. 3.4, 3.5) */
+    double velocity[3];    /* uniform velocity of the scalar advection equation
+                              (Eq. 13); ignored for Euler */
 } amr_config;
+
+/* Equations the stage solves.  Euler gas dynamics (Sec. 3.5, Eq. 14-16):
+ * n_var = ndim + 2.  Scalar advection (Sec. 3.4, Eq. 13) with the uniform
+ * velocity amr_config.velocity: n_var = 1, primitive = conservative, wave
+ * speeds min(v_d, 0) and max(v_d, 0) (so Rusanov and HLL both upwind; the
+ * HLL flux is 0 where v_d = 0), CFL limit sum_d |v_d| / dx_d, no gravity;
+ * the refinement criterion looks at the scalar; the learned flag predictor
+ * (whose features are Euler quantities) is refused with AMR_EINVAL. */
+typedef enum { AMR_PHYS_EULER = 0, AMR_PHYS_ADVECTION = 1 } amr_physics;
 
 /* Face reconstructions of Sec. 3.2.  MUSCL slope limiters (two ghost
  * layers); the slope of a cell from its one-sided differences a, b: minmod =
@@ -169,7 +181,8 @@ typedef struct {
                               of Heun; n_states >= 3 */
 
 /* Refinement-criterion constants of Eq. 12 (Sec. 3.3).  The criterion is
- * evaluated on density and pressure; a cell's value is the larger one. */
+ * evaluated on density and pressure; a cell's value is the larger one (for
+ * scalar advection: on the scalar). */
 typedef struct {
     double c_refine, c_derefine, eps, eps_abs;
 } amr_flag_params;
@@ -347,7 +360,8 @@ typedef struct amr_mlp amr_mlp;
  * (feature-major): for each of 4^d pools of (N/4)^d cells the mean density
  * and pressure over the block means, minus one, and the mean speed over the
  * block-mean sound speed, then level / max_level; F = 3 * 4^d + 1 (193 in
- * 3D).  x may be NULL to only query *n_features.  Needs block_n % 4 == 0. */
+ * 3D).  x may be NULL to only query *n_features.  Needs block_n % 4 == 0
+ * and Euler physics (AMR_EINVAL otherwise). */
 amr_status amr_features(amr_forest *f, int s, float *x, int *n_features, amr_stream stream);
 
 /* Model on the current device with n_features inputs, weights drawn
@@ -438,7 +452,8 @@ amr_status amr_write_xdmf(const amr_forest *f, int s, const char *base, amr_stre
  *   state       : n_blocks blocks in the layout above (one state slot),
  *                 float (precision 32) or double (64);
  *   cell_volume : device array, volume of one cell of each block (double);
- *   sums        : device array of ndim + 2 doubles, written on `stream`.
+ *   sums        : device array of ndim + 2 doubles, written on `stream`
+ *                 (the Euler layout; advection states use amr_conserved).
  * The per-block partial sums go to a scratch array of
  * AMR_STATIC_MAX_BLOCKS x 5 doubles (2.6 MB) that is part of the library's
  * device image: every GPU that loads the library holds it until the process

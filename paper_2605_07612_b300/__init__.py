@@ -18,6 +18,7 @@ from . import build as _build
 
 AMR_OK, AMR_EINVAL, AMR_ENOMEM, AMR_ECAPACITY, AMR_ECUDA = 0, 1, 2, 3, 4
 AMR_ETIMEOUT, AMR_EBOUNDS, AMR_ENONPHYS, AMR_ESTATE = 5, 6, 7, 8
+PHYS_EULER, PHYS_ADVECTION = 0, 1
 AMR_STEP_GRAPH, AMR_STEP_GATHER, AMR_STEP_SSP3, AMR_STEP_RK4, AMR_STEP_SSP43 = 1, 2, 4, 8, 16
 STATUS_NAMES = {0: "AMR_OK", 1: "AMR_EINVAL", 2: "AMR_ENOMEM", 3: "AMR_ECAPACITY", 4: "AMR_ECUDA",
                 5: "AMR_ETIMEOUT", 6: "AMR_EBOUNDS", 7: "AMR_ENONPHYS", 8: "AMR_ESTATE"}
@@ -54,7 +55,7 @@ class Config(C.Structure):
                 ("bc", C.c_int * 6), ("bc_val", (C.c_double * 8) * 6),
                 ("dev_alloc", AllocFn), ("dev_free", FreeFn), ("alloc_ctx", C.c_void_p),
                 ("host_only", C.c_int), ("limiter", C.c_int), ("flux", C.c_int), ("gravity", C.c_double * 3),
-                ("diagonal_ghosts", C.c_int)]
+                ("diagonal_ghosts", C.c_int), ("physics", C.c_int), ("velocity", C.c_double * 3)]
 
 
 class GhostEntry(C.Structure):
@@ -162,7 +163,8 @@ def spec_from_config(c: Config):
                           gamma=float(c.gamma), cfl=float(c.cfl), bc_type=tuple(int(c.bc[f]) for f in range(6)),
                           bc_val=tuple(tuple(float(c.bc_val[f][v]) for v in range(8)) for f in range(6)),
                           limiter=int(c.limiter), flux=int(c.flux), gravity=tuple(float(c.gravity[d]) for d in range(3)),
-                          diagonal_ghosts=int(c.diagonal_ghosts))
+                          diagonal_ghosts=int(c.diagonal_ghosts), physics=int(c.physics),
+                          velocity=tuple(float(c.velocity[d]) for d in range(3)))
 
 
 def config_from_spec(spec, max_blocks, n_states=2, precision=64, host_only=False) -> Config:
@@ -174,7 +176,11 @@ def config_from_spec(spec, max_blocks, n_states=2, precision=64, host_only=False
     for d in range(3):
         c.gravity[d] = float(gv[d]) if d < spec.ndim else 0.0
     c.diagonal_ghosts = int(getattr(spec, "diagonal_ghosts", 0))
-    c.ndim, c.block_n, c.n_ghost, c.n_var = spec.ndim, spec.N, spec.ng, spec.ndim + 2
+    c.physics = int(getattr(spec, "physics", 0))
+    vel = getattr(spec, "velocity", (0.0, 0.0, 0.0))
+    for d in range(3):
+        c.velocity[d] = float(vel[d]) if d < spec.ndim else 0.0
+    c.ndim, c.block_n, c.n_ghost, c.n_var = spec.ndim, spec.N, spec.ng, spec.nvar
     for d in range(3):
         c.ntrees[d] = int(spec.ntrees[d]) if d < spec.ndim else 1
         c.periodic[d] = int(spec.periodic[d]) if d < spec.ndim else 1

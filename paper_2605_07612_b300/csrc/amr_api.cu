@@ -84,6 +84,8 @@ void fill_geom(amr_forest *f) {
     g.ncell = 1;
     for (int d = 0; d < c.ndim; ++d) g.ncell *= g.S;
     g.bstride = g.ncell * g.V;
+    g.phys = c.physics;
+    for (int d = 0; d < 3; ++d) g.vel[d] = d < c.ndim ? c.velocity[d] : 0.0;
 }
 
 // cell sizes per (instance, level), boundary kinds/values and CFL numbers per
@@ -131,7 +133,15 @@ amr_status validate(const amr_config *c, std::string &why) {
     if (c->block_n != 8 && c->block_n != 16 && c->block_n != 32) return bad("block_n must be 8, 16 or 32");
     if (c->n_ghost < 1 || c->n_ghost > 4) return bad("n_ghost must be 1..4");
     if (c->block_n < 2 * c->n_ghost) return bad("block_n must be >= 2 n_ghost");
-    if (c->n_var != c->ndim + 2) return bad("n_var must be ndim + 2 (Euler)");
+    if (c->physics != AMR_PHYS_EULER && c->physics != AMR_PHYS_ADVECTION) return bad("unknown physics");
+    if (c->physics == AMR_PHYS_EULER && c->n_var != c->ndim + 2) return bad("n_var must be ndim + 2 (Euler)");
+    if (c->physics == AMR_PHYS_ADVECTION) {
+        if (c->n_var != 1) return bad("n_var must be 1 (scalar advection)");
+        for (int d = 0; d < 3; ++d) {
+            if (!std::isfinite(c->velocity[d])) return bad("velocity must be finite");
+            if (c->gravity[d] != 0.0) return bad("scalar advection has no gravity source");
+        }
+    }
     if (c->max_level < 0 || c->max_level >= kMaxLevels) return bad("max_level must be 0..12");
     if (c->max_blocks < 1 || c->n_states < 1) return bad("max_blocks and n_states must be >= 1");
     if (c->precision != 32 && c->precision != 64) return bad("precision must be 32 or 64");
@@ -186,6 +196,18 @@ amr_status upload_pattern(amr_forest *f) {
 template <class real, int D>
 amr_status launch_stage(amr_forest *f, const StageArgs<real> &a, cudaStream_t st) {
     const int N = f->cfg.block_n, NG = f->cfg.n_ghost;
+    if (f->cfg.physics == AMR_PHYS_ADVECTION) {
+#define AMR_ADV_CASE(n_, g_) \
+    if (N == n_ && NG == g_) return launch_stage_t<real, D, n_, g_, true, 1>(f, a, st);
+        AMR_ADV_CASE(8, 2)
+        AMR_ADV_CASE(16, 2)
+        AMR_ADV_CASE(32, 2)
+        AMR_ADV_CASE(8, 3)
+        AMR_ADV_CASE(16, 3)
+        AMR_ADV_CASE(32, 3)
+#undef AMR_ADV_CASE
+        return fail(f, AMR_EINVAL, "the advection stage needs n_ghost 2 or 3 (got %d)", NG);
+    }
     if constexpr (std::is_same<real, float>::value) {
         // the pair kernels implement the Rusanov flux only
         if (NG == 2 && !f->scalar_stage && a.flux == AMR_FLUX_RUSANOV) {
@@ -197,7 +219,7 @@ amr_status launch_stage(amr_forest *f, const StageArgs<real> &a, cudaStream_t st
     const bool gen = a.limiter != AMR_LIM_MINMOD || a.flux != AMR_FLUX_RUSANOV;
 #define AMR_STAGE_CASE(n_, g_)                                                                                   \
     if (N == n_ && NG == g_)                                                                                     \
-        return gen ? launch_stage_t<real, D, n_, g_, true>(f, a, st) : launch_stage_t<real, D, n_, g_, false>(f, a, st);
+        return gen ? launch_stage_t<real, D, n_, g_, true, 0>(f, a, st) : launch_stage_t<real, D, n_, g_, false, 0>(f, a, st);
     AMR_STAGE_CASE(8, 2)
     AMR_STAGE_CASE(16, 2)
     AMR_STAGE_CASE(32, 2)
@@ -213,7 +235,7 @@ amr_status launch_stage(amr_forest *f, const StageArgs<real> &a, cudaStream_t st
 amr_status ensure_weno(amr_forest *f) {
     if (f->cfg.limiter != AMR_LIM_WENO5) return AMR_OK;
     const int N = f->cfg.block_n, D = f->cfg.ndim;
-    const size_t nfl = size_t(D) * size_t(D + 2) * size_t(N + 1) * size_t(D == 3 ? N * N : N);
+    const size_t nfl = size_t(D) * size_t(f->cfg.n_var) * size_t(N + 1) * size_t(D == 3 ? N * N : N);
     const size_t nb = size_t(std::max<int64_t>(nblocks(f), 1));
     amr_status s = ensure(f, f->wprim, nb * f->block_bytes);
     if (s != AMR_OK) return s;
@@ -244,13 +266,16 @@ amr_status run_stage(amr_forest *f, const amr_stage *stg, cudaStream_t st) {
     for (int d = 0; d < 3; ++d) {
         a.grav[d] = d < D ? real(f->cfg.gravity[d]) : real(0);
         if (d < D && f->cfg.gravity[d] != 0.0) a.gravity_on = 1;
+        a.vel[d] = d < D ? real(f->cfg.velocity[d]) : real(0);
     }
     amr_status s;
     if (f->cfg.limiter == AMR_LIM_WENO5) {
         // three-pass WENO5 stage on the filled ghost cells (no halo gathering)
         a.gather = 0;
         if ((s = ensure_weno(f)) != AMR_OK) return s;
-        s = launch_weno<real, D>(f, a, static_cast<real *>(f->wprim.p), static_cast<real *>(f->wflux.p), st);
+        s = f->cfg.physics == AMR_PHYS_ADVECTION
+                ? launch_weno<real, D, 1>(f, a, static_cast<real *>(f->wprim.p), static_cast<real *>(f->wflux.p), st)
+                : launch_weno<real, D, 0>(f, a, static_cast<real *>(f->wprim.p), static_cast<real *>(f->wflux.p), st);
     } else {
         s = launch_stage<real, D>(f, a, st);
     }
@@ -468,6 +493,8 @@ amr_status amr_create_batch(const amr_config *cfgs, const int *init_levels, int 
             c.n_states != c0.n_states || c.gamma != c0.gamma || c.host_only != c0.host_only ||
             c.limiter != c0.limiter || c.flux != c0.flux || c.gravity[0] != c0.gravity[0] ||
             c.gravity[1] != c0.gravity[1] || c.gravity[2] != c0.gravity[2] || c.diagonal_ghosts != c0.diagonal_ghosts ||
+            c.physics != c0.physics || c.velocity[0] != c0.velocity[0] || c.velocity[1] != c0.velocity[1] ||
+            c.velocity[2] != c0.velocity[2] ||
             c.dev_alloc != c0.dev_alloc || c.dev_free != c0.dev_free || c.alloc_ctx != c0.alloc_ctx)
             return AMR_EINVAL;
         capacity += c.max_blocks;
@@ -911,6 +938,7 @@ amr_status amr_features(amr_forest *f, int s, float *x, int *n_features, amr_str
     if (!f || !valid_slot(f, s)) return AMR_EINVAL;
     NEED_DEVICE(f);
     if (f->cfg.block_n % 4) return fail(f, AMR_EINVAL, "features pool 4 cells per dimension: block_n must be a multiple of 4");
+    if (f->cfg.physics != AMR_PHYS_EULER) return fail(f, AMR_EINVAL, "the flag features are Euler quantities (density, pressure, speed)");
     const int F = 3 * (f->cfg.ndim == 3 ? 64 : 16) + 1;
     if (n_features) *n_features = F;
     if (!x) return AMR_OK;
@@ -971,7 +999,7 @@ amr_status amr_autotune(amr_forest *f, int *choice, double *best_ms, amr_stream 
     struct Cand { bool scalar; int ipc; bool pers; int tile; };
     std::vector<Cand> cands;
     const bool pair_ok = f->cfg.precision == 32 && f->cfg.n_ghost == 2 && f->cfg.flux == AMR_FLUX_RUSANOV &&
-                         f->cfg.limiter != AMR_LIM_WENO5;
+                         f->cfg.limiter != AMR_LIM_WENO5 && f->cfg.physics == AMR_PHYS_EULER;
     std::vector<std::pair<bool, int>> kernels;   // (per-cell kernel, pair tile)
     if (pair_ok) {
         kernels.push_back({false, 0});
@@ -1026,7 +1054,7 @@ amr_status amr_set_launch_shape(amr_forest *f, int choice) {
     const int tile8 = choice / 1000, scalar = (choice % 1000) / 100, ipc = choice % 100;
     if (tile8 > 1 || scalar > 1 || ipc > 64 || (tile8 && scalar)) return AMR_EINVAL;
     const bool pair_ok = f->cfg.precision == 32 && f->cfg.n_ghost == 2 && f->cfg.flux == AMR_FLUX_RUSANOV &&
-                         f->cfg.limiter != AMR_LIM_WENO5;
+                         f->cfg.limiter != AMR_LIM_WENO5 && f->cfg.physics == AMR_PHYS_EULER;
     if (tile8 && (!pair_ok || f->cfg.block_n <= 8)) return fail(f, AMR_EINVAL, "8 x 8 tiles need an FP32 pair kernel and blocks above 8 cells a side");
     f->scalar_stage = scalar == 1;
     f->pair_tile = tile8 ? 8 : 0;
@@ -1042,13 +1070,15 @@ amr_status amr_set_launch_shape(amr_forest *f, int choice) {
 namespace {
 
 constexpr char kCkptMagic[8] = {'A', 'M', 'R', 'C', 'K', 'P', 'T', '1'};
-constexpr uint32_t kCkptVersion = 1;
+constexpr uint32_t kCkptVersion = 2;
 
 struct CkptHead {
     char magic[8];
     uint32_t version, n_inst;
     int32_t precision, ndim, block_n, n_ghost, n_var, n_states, host_only, limiter, flux, diagonal_ghosts;
     double gamma, gravity[3];
+    int32_t physics, pad;
+    double velocity[3];
     int64_t n_blocks;
 };
 struct CkptInst {
@@ -1120,6 +1150,8 @@ amr_status amr_save(const amr_forest *fc, const char *path, amr_stream stream) {
     h.diagonal_ghosts = c0.diagonal_ghosts;
     h.gamma = c0.gamma;
     for (int d = 0; d < 3; ++d) h.gravity[d] = c0.gravity[d];
+    h.physics = c0.physics;
+    for (int d = 0; d < 3; ++d) h.velocity[d] = c0.velocity[d];
     h.n_blocks = nblocks(f);
     bool ok = fwrite(&h, sizeof h, 1, out.fp) == 1;
     for (int i = 0; i < ni && ok; ++i) {
@@ -1185,7 +1217,9 @@ amr_status amr_load(const char *path, const amr_config *opts, amr_forest **out, 
         c.limiter = h.limiter;
         c.flux = h.flux;
         c.diagonal_ghosts = h.diagonal_ghosts;
+        c.physics = h.physics;
         for (int d = 0; d < 3; ++d) {
+            c.velocity[d] = h.velocity[d];
             c.gravity[d] = h.gravity[d];
             c.ntrees[d] = r.ntrees[d];
             c.periodic[d] = r.periodic[d];
@@ -1307,7 +1341,8 @@ amr_status amr_write_xdmf(const amr_forest *fc, int s, const char *base, amr_str
     if (!out.fp) return fail(f, AMR_ESTATE, "cannot open %s", xmf.c_str());
     static const char *names3[5] = {"rho", "mx", "my", "mz", "E"};
     static const char *names2[4] = {"rho", "mx", "my", "E"};
-    const char **names = D == 3 ? names3 : names2;
+    static const char *names1[1] = {"rho"};
+    const char **names = f->cfg.physics == AMR_PHYS_ADVECTION ? names1 : (D == 3 ? names3 : names2);
     // co-rectilinear grids: dimensions (node counts), origin and spacing are
     // all listed slowest dimension first (z, y, x)
     fprintf(out.fp, "<?xml version=\"1.0\" ?>\n<Xdmf Version=\"2.0\">\n <Domain>\n");

@@ -90,11 +90,11 @@ inline void *slot_ptr(const amr_forest *f, int s) { return static_cast<char *>(f
 // library builds in parallel.
 template <class real, int D>
 amr_status launch_ghosts(amr_forest *f, int s, cudaStream_t st, bool gather);
-template <class real, int D, int N, int NG, bool GEN>
+template <class real, int D, int N, int NG, bool GEN, int PH>
 amr_status launch_stage_t(amr_forest *f, const StageArgs<real> &a, cudaStream_t st);
 template <int D, int N>
 amr_status launch_stage_pair(amr_forest *f, const StageArgs<float> &a, cudaStream_t st);
-template <class real, int D>
+template <class real, int D, int PH>
 amr_status launch_weno(amr_forest *f, const StageArgs<real> &a, real *prim, real *flux, cudaStream_t st);
 
 }  // namespace amrb

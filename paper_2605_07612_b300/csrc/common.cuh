@@ -58,6 +58,8 @@ struct Geom {
     int64_t bstride;        // V * ncell
     const double *dx;       // [n_instances * kMaxLevels][3]
     const double *inv_dx;
+    int phys;               // amr_physics: 0 Euler, 1 scalar advection
+    double vel[3];          // advection velocity
 };
 
 // Device-resident scalars of a forest.

@@ -62,13 +62,13 @@ __device__ __forceinline__ real prolong_at(const real *cb, const Geom &g, int ci
 // aligned).  ND = face-normal dimension.  Each lane keeps 4 independent
 // loads in flight before storing.
 template <class real, int D, int N, int NG, int ND>
-__device__ __forceinline__ void srl_pairs(real *dstb, const real *srcb, int side, int lane) {
+__device__ __forceinline__ void srl_pairs(real *dstb, const real *srcb, int side, int lane, int V) {
     using V2 = typename Vec2<real>::type;
     constexpr int S = N + 2 * NG;
     constexpr int64_t NCc = (D == 3) ? int64_t(S) * S * S : int64_t(S) * S;
     constexpr int T1 = (D == 3) ? N : 1;
     constexpr int UPV = (ND == 0) ? N * T1 * (NG / 2) : NG * T1 * (N / 2);
-    constexpr int TOTAL = (D + 2) * UPV;
+    const int TOTAL = V * UPV;
     const int lo = side ? N : -NG, shift = side ? -N : N;
     auto cidx = [](int i, int j, int k) -> int64_t {
         return (int64_t(D == 3 ? k + NG : 0) * S + (j + NG)) * S + (i + NG);
@@ -145,9 +145,9 @@ __global__ void __launch_bounds__(256) k_ghost(GhostArgs<real> a, Geom g) {
     const int nd = e.face >> 1, side = e.face & 1;
     if constexpr (NG % 2 == 0) {
         if (e.kind == KIND_SRL) {
-            if (nd == 0) srl_pairs<real, D, N, NG, 0>(dstb, srcb, side, lane);
-            else if (nd == 1 || D == 2) srl_pairs<real, D, N, NG, 1>(dstb, srcb, side, lane);
-            else srl_pairs<real, D, N, NG, (D == 3 ? 2 : 1)>(dstb, srcb, side, lane);
+            if (nd == 0) srl_pairs<real, D, N, NG, 0>(dstb, srcb, side, lane, g.V);
+            else if (nd == 1 || D == 2) srl_pairs<real, D, N, NG, 1>(dstb, srcb, side, lane, g.V);
+            else srl_pairs<real, D, N, NG, (D == 3 ? 2 : 1)>(dstb, srcb, side, lane, g.V);
             return;
         }
     }

@@ -44,14 +44,15 @@ amr_status launch_ghosts(amr_forest *f, int s, cudaStream_t st, bool gather) {
     return AMR_OK;
 }
 
-template <class real, int D, int N, int NG, bool GEN>
+template <class real, int D, int N, int NG, bool GEN, int PH>
 amr_status launch_stage_t(amr_forest *f, const StageArgs<real> &a, cudaStream_t st) {
     constexpr int T = N < 16 ? N : 16;
-    using Sh = StageShape<real, D, N, NG, T>;
+    using Sh = StageShape<real, D, N, NG, T, PH>;
+    constexpr auto kern = k_stage<real, D, N, NG, T, GEN, PH>;
     static bool attr_done = false;
     const size_t smem = Sh::smem_bytes();
     if (!attr_done) {
-        CU(cudaFuncSetAttribute(k_stage<real, D, N, NG, T, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
         attr_done = true;
     }
     const int64_t items = nblocks(f) * Sh::TILES;
@@ -59,9 +60,9 @@ amr_status launch_stage_t(amr_forest *f, const StageArgs<real> &a, cudaStream_t 
         StageArgs<real> b = a;
         b.n_items = int(items);
         int occ = 1;
-        if (f->persistent) CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_stage<real, D, N, NG, T, GEN>, Sh::NT, smem));
+        if (f->persistent) CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, Sh::NT, smem));
         const int64_t grid = stage_grid(f, items, occ);
-        k_stage<real, D, N, NG, T, GEN><<<unsigned(grid), Sh::NT, smem, st>>>(b, f->geom);
+        kern<<<unsigned(grid), Sh::NT, smem, st>>>(b, f->geom);
         ++f->launches;
     }
     CU(cudaGetLastError());
@@ -132,21 +133,27 @@ amr_status launch_stage_pair(amr_forest *f, const StageArgs<float> &a, cudaStrea
     return launch_stage_pair_t<D, N, (N < 16 ? N : 16)>(f, a, st);
 }
 
-// WENO5 stage: primitives, face fluxes, update (three launches); prim and
-// flux are scratch buffers of n_blocks x bstride and n_blocks x D x V x
-// (N+1) N^(D-1) elements
-template <class real, int D>
+// WENO5 stage: primitives (Euler only), face fluxes, update (three or two
+// launches); prim and flux are scratch buffers of n_blocks x bstride and
+// n_blocks x D x V x (N+1) N^(D-1) elements
+template <class real, int D, int PH>
 amr_status launch_weno(amr_forest *f, const StageArgs<real> &a, real *prim, real *flux, cudaStream_t st) {
     const int64_t nb = nblocks(f);
     if (nb > 0) {
         const int N = f->cfg.block_n;
         const int nfaces = D * (N + 1) * (D == 3 ? N * N : N);
         const int ncint = D == 3 ? N * N * N : N * N;
-        k_weno_prim<real, D><<<unsigned(nb), 256, 0, st>>>(a.deriv, prim, f->geom, a.gamma);
-        k_weno_flux<real, D><<<dim3(unsigned(nb), unsigned((nfaces + 255) / 256)), 256, 0, st>>>(
-            prim, flux, a.info, a.bflux, f->geom, a.gamma, a.flux, a.sc);
-        k_weno_update<real, D><<<dim3(unsigned(nb), unsigned((ncint + 255) / 256)), 256, 0, st>>>(a, flux, f->geom);
-        f->launches += 3;
+        const PhysCtx<real> pc{a.gamma, real(1) / (a.gamma - real(1)), {a.vel[0], a.vel[1], a.vel[2]}};
+        const real *w = a.deriv;       // scalar advection: the state is its own primitive
+        if (PH == 0) {
+            k_weno_prim<real, D><<<unsigned(nb), 256, 0, st>>>(a.deriv, prim, f->geom, a.gamma);
+            ++f->launches;
+            w = prim;
+        }
+        k_weno_flux<real, D, PH><<<dim3(unsigned(nb), unsigned((nfaces + 255) / 256)), 256, 0, st>>>(
+            w, flux, a.info, a.bflux, f->geom, pc, a.flux, a.sc);
+        k_weno_update<real, D, PH><<<dim3(unsigned(nb), unsigned((ncint + 255) / 256)), 256, 0, st>>>(a, flux, f->geom);
+        f->launches += 2;
     }
     CU(cudaGetLastError());
     return AMR_OK;
@@ -154,10 +161,11 @@ amr_status launch_weno(amr_forest *f, const StageArgs<real> &a, real *prim, real
 
 }  // namespace amrb
 
-#define AMR_INST_STAGE(real, D, GEN)                                                                    \
-    template amr_status launch_stage_t<real, D, 8, 2, GEN>(amr_forest *, const StageArgs<real> &, cudaStream_t);  \
-    template amr_status launch_stage_t<real, D, 16, 2, GEN>(amr_forest *, const StageArgs<real> &, cudaStream_t); \
-    template amr_status launch_stage_t<real, D, 32, 2, GEN>(amr_forest *, const StageArgs<real> &, cudaStream_t); \
-    template amr_status launch_stage_t<real, D, 8, 3, GEN>(amr_forest *, const StageArgs<real> &, cudaStream_t);  \
-    template amr_status launch_stage_t<real, D, 16, 3, GEN>(amr_forest *, const StageArgs<real> &, cudaStream_t); \
-    template amr_status launch_stage_t<real, D, 32, 3, GEN>(amr_forest *, const StageArgs<real> &, cudaStream_t);
+#define AMR_INST_STAGE_PH(real, D, GEN, PH)                                                                 \
+    template amr_status launch_stage_t<real, D, 8, 2, GEN, PH>(amr_forest *, const StageArgs<real> &, cudaStream_t);  \
+    template amr_status launch_stage_t<real, D, 16, 2, GEN, PH>(amr_forest *, const StageArgs<real> &, cudaStream_t); \
+    template amr_status launch_stage_t<real, D, 32, 2, GEN, PH>(amr_forest *, const StageArgs<real> &, cudaStream_t); \
+    template amr_status launch_stage_t<real, D, 8, 3, GEN, PH>(amr_forest *, const StageArgs<real> &, cudaStream_t);  \
+    template amr_status launch_stage_t<real, D, 16, 3, GEN, PH>(amr_forest *, const StageArgs<real> &, cudaStream_t); \
+    template amr_status launch_stage_t<real, D, 32, 3, GEN, PH>(amr_forest *, const StageArgs<real> &, cudaStream_t);
+#define AMR_INST_STAGE(real, D, GEN) AMR_INST_STAGE_PH(real, D, GEN, 0)

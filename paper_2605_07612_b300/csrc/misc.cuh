@@ -29,6 +29,14 @@ struct FixArgs {
     real gamma;
 };
 
+// sum_d |v_d| / dx_d: the CFL speed of scalar advection on geometry class gc
+template <class real, int D>
+__device__ __forceinline__ real advection_speed(const Geom &g, int gc) {
+    real s = real(0);
+    for (int d = 0; d < D; ++d) s += fabs(real(g.vel[d])) * real(g.inv_dx[3 * gc + d]);
+    return s;
+}
+
 template <class real, int D>
 __global__ void k_fluxfix(FixArgs<real> a, Geom g) {
     const int N = g.N, V = g.V;
@@ -90,15 +98,19 @@ __global__ void k_fluxfix(FixArgs<real> a, Geom g) {
             x[td[0]] = t % N;
             if (D == 3) x[td[1]] = t / N;
             const int64_t cell = cell_index<real>(g, x[0], x[1], x[2]);
-            real U[5];
-            for (int v = 0; v < V; ++v) U[v] = ub[int64_t(v) * g.ncell + cell];
-            const real rho = U[0], ir = real(1) / rho;
-            real ke = real(0);
-            for (int d = 0; d < D; ++d) ke += U[1 + d] * U[1 + d] * ir;
-            const real p = (a.gamma - real(1)) * (U[D + 1] - real(0.5) * ke);
-            const real c = sqrt(a.gamma * p / rho);
             real s = real(0);
-            for (int d = 0; d < D; ++d) s += (fabs(U[1 + d] * ir) + c) * real(g.inv_dx[3 * gc + d]);
+            if (g.phys == 1) {
+                s = advection_speed<real, D>(g, gc);
+            } else {
+                real U[5];
+                for (int v = 0; v < V; ++v) U[v] = ub[int64_t(v) * g.ncell + cell];
+                const real rho = U[0], ir = real(1) / rho;
+                real ke = real(0);
+                for (int d = 0; d < D; ++d) ke += U[1 + d] * U[1 + d] * ir;
+                const real p = (a.gamma - real(1)) * (U[D + 1] - real(0.5) * ke);
+                const real c = sqrt(a.gamma * p / rho);
+                for (int d = 0; d < D; ++d) s += (fabs(U[1 + d] * ir) + c) * real(g.inv_dx[3 * gc + d]);
+            }
             vmax = s > vmax ? s : vmax;
         }
     }
@@ -108,7 +120,8 @@ __global__ void k_fluxfix(FixArgs<real> a, Geom g) {
 }
 
 // ------------------------------------------------------------------- CFL dt
-// max over interior cells of sum_d (|v_d| + c) / dx_d (Sec. 3.2 step 2c)
+// max over interior cells of sum_d (|v_d| + c) / dx_d (Sec. 3.2 step 2c);
+// for scalar advection sum_d |v_d| / dx_d with the uniform velocity
 template <class real, int D>
 __global__ void k_maxspeed(const real *u, const BlockInfo *info, DevScalars *sc, Geom g, real gam) {
     const int b = blockIdx.x;
@@ -119,6 +132,11 @@ __global__ void k_maxspeed(const real *u, const BlockInfo *info, DevScalars *sc,
     real vmax = real(0);
     for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
         const int i = c % N, j = (c / N) % N, k = (D == 3) ? c / (N * N) : 0;
+        if (g.phys == 1) {
+            const real s = advection_speed<real, D>(g, gc);
+            vmax = s > vmax ? s : vmax;
+            continue;
+        }
         const int64_t cell = cell_index<real>(g, i, j, k);
         real U[5];
         for (int v = 0; v < g.V; ++v) U[v] = ub[int64_t(v) * g.ncell + cell];
@@ -207,6 +225,10 @@ __device__ __forceinline__ void dprim_rn(const real *ub, const Geom &g, int64_t 
     double U[5];
     for (int v = 0; v < g.V; ++v) U[v] = double(ub[int64_t(v) * g.ncell + cell]);
     rho = U[0];
+    if (g.phys == 1) {      // scalar advection: the scalar stands in for both
+        p = rho;
+        return;
+    }
     double ke = 0.0;
     for (int d = 0; d < D; ++d) {
         const double w = __ddiv_rn(U[1 + d], rho);

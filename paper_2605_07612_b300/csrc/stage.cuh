@@ -26,6 +26,7 @@
 // FP32 uses the hardware reciprocal and reciprocal-square-root; FP64 uses
 // IEEE division and square root.
 #pragma once
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -51,6 +52,15 @@ struct StageArgs {
     int flux;                    // amr_flux (the pair kernels: Rusanov only)
     int gravity_on;              // add the source S = (0, rho g, rho g.u) of u_deriv
     real grav[3];
+    real vel[3];                 // advection velocity (scalar advection only)
+};
+
+// Constants a numerical flux needs: gamma and 1 / (gamma - 1) for Euler,
+// the uniform velocity for scalar advection.
+template <class real>
+struct PhysCtx {
+    real gam, gm1i;
+    real vel[3];
 };
 
 template <class real>
@@ -191,11 +201,70 @@ struct Euler {
         if (kind == 1) hll<NRM>(wL, wR, n, gam, gm1i, F);
         else flux<NRM>(wL, wR, n, gam, gm1i, F);
     }
+    template <int NRM>
+    __device__ static __forceinline__ void face_flux(int kind, const real *wL, const real *wR, int n, const PhysCtx<real> &c,
+                                                     real *F) {
+        face_flux<NRM>(kind, wL, wR, n, c.gam, c.gm1i, F);
+    }
+
+    static constexpr bool EULER = true;
+    // rho <= 0 or p <= 0 (also catches NaN)
+    __device__ static __forceinline__ bool nonphys(const real *w) { return !(w[0] > real(0)) || !(w[D + 1] > real(0)); }
+    // variables whose face states must stay positive
+    __device__ static __forceinline__ constexpr bool positive_var(int v) { return v == 0 || v == D + 1; }
+    // sum_d (|v_d| + c) / dx_d of a conservative state (the CFL limit)
+    __device__ static __forceinline__ real speed(const real *U, real gam, const real *idx, const PhysCtx<real> &) {
+        real w[V];
+        prim(U, w, gam);
+        const real cs = FM<real>::sqrtp(gam * w[D + 1] * FM<real>::rcp(w[0]));
+        real s = real(0);
+#pragma unroll
+        for (int d = 0; d < D; ++d) s += (fabs(w[1 + d]) + cs) * idx[d];
+        return s;
+    }
 };
 
-template <class real, int D, int N, int NG, int T>
+// Scalar advection (Sec. 3.4, Eq. 13) with a uniform velocity: one
+// variable, primitive = conservative, physical flux rho v_n, wave speeds
+// min(v_n, 0) and max(v_n, 0).  Rusanov: a = max of their magnitudes = |v_n|;
+// HLL with sL = min(v_n, 0), sR = max(v_n, 0), and no flux where v_n = 0.
+template <class real, int D>
+struct Advect {
+    static constexpr int V = 1;
+    static constexpr bool EULER = false;
+    __device__ static __forceinline__ void prim(const real *U, real *w, real) { w[0] = U[0]; }
+    template <int NRM>
+    __device__ static __forceinline__ void face_flux(int kind, const real *wL, const real *wR, int n, const PhysCtx<real> &c,
+                                                     real *F) {
+        const int nn = NRM >= 0 ? NRM : n;
+        const real vn = nn == 0 ? c.vel[0] : (nn == 1 ? c.vel[1] : c.vel[2]);
+        const real rL = wL[0], rR = wR[0];
+        const real FL = rL * vn, FR = rR * vn;
+        const real sL = vn < real(0) ? vn : real(0), sR = vn > real(0) ? vn : real(0);
+        if (kind == 1) {
+            F[0] = sR - sL == real(0) ? real(0) : (sR * FL - sL * FR + sL * sR * (rR - rL)) / (sR - sL);
+        } else {
+            const real a = fabs(sL) > fabs(sR) ? fabs(sL) : fabs(sR);
+            F[0] = real(0.5) * (FL + FR) - real(0.5) * a * (rR - rL);
+        }
+    }
+    __device__ static __forceinline__ bool nonphys(const real *) { return false; }
+    __device__ static __forceinline__ constexpr bool positive_var(int) { return false; }
+    __device__ static __forceinline__ real speed(const real *, real, const real *idx, const PhysCtx<real> &c) {
+        real s = real(0);
+#pragma unroll
+        for (int d = 0; d < D; ++d) s += fabs(c.vel[d]) * idx[d];
+        return s;
+    }
+};
+
+// physics by code: 0 Euler, 1 scalar advection (amr_physics)
+template <class real, int D, int PH>
+using Phys = typename std::conditional<PH == 1, Advect<real, D>, Euler<real, D>>::type;
+
+template <class real, int D, int N, int NG, int T, int PH = 0>
 struct StageShape {
-    static constexpr int V = D + 2;
+    static constexpr int V = Phys<real, D, PH>::V;
     static constexpr int P = T + 4;                  // plane pitch (tile + 2-cell halo each side)
     static constexpr int R = (D == 3) ? 5 : 1;       // ring depth
     static constexpr int S = N + 2 * NG;
@@ -215,11 +284,12 @@ struct StageShape {
 };
 
 // GEN = false: minmod and Rusanov fixed at compile time (the default scheme);
-// GEN = true: the limiter and flux named in the arguments.
-template <class real, int D, int N, int NG, int T, bool GEN>
+// GEN = true: the limiter and flux named in the arguments.  PH: physics
+// (0 Euler, 1 scalar advection).
+template <class real, int D, int N, int NG, int T, bool GEN, int PH>
 __device__ __forceinline__ void stage_item(const StageArgs<real> &a, const Geom &g, int item) {
-    using Sh = StageShape<real, D, N, NG, T>;
-    using E = Euler<real, D>;
+    using Sh = StageShape<real, D, N, NG, T, PH>;
+    using E = Phys<real, D, PH>;
     using V2 = typename Vec2<real>::type;
     constexpr int V = Sh::V, P = Sh::P, S = Sh::S, NT = Sh::NT, NFX = Sh::NFX, NFS = Sh::NFS;
     constexpr int64_t NC = (D == 3) ? int64_t(S) * S * S : int64_t(S) * S;
@@ -242,6 +312,7 @@ __device__ __forceinline__ void stage_item(const StageArgs<real> &a, const Geom 
     const real idx2 = (D == 3) ? real(g.inv_dx[3 * gc + 2]) : real(0);
     const real gam = a.gamma;
     const real gm1i = real(1) / (gam - real(1));
+    const PhysCtx<real> pc{gam, gm1i, {a.vel[0], a.vel[1], a.vel[2]}};
     const real dt_eff = real(a.w_dt * a.sc_in[info.inst].dt);
     const int lim = GEN ? a.limiter : 0, flx = GEN ? a.flux : 0;
     const real *__restrict__ ub = a.deriv + int64_t(b) * V * NC;
@@ -349,7 +420,7 @@ __device__ __forceinline__ void stage_item(const StageArgs<real> &a, const Geom 
             for (int e = 0; e < (Sh::PAIRS ? 2 : 1); ++e) {
                 real w[V];
                 E::prim(pre[l][e], w, gam);
-                nonphys |= !(w[0] > real(0)) || !(w[D + 1] > real(0));
+                nonphys |= E::nonphys(w);
 #pragma unroll
                 for (int v = 0; v < V; ++v) pl[v * PL + o + e] = w[v];
             }
@@ -381,7 +452,7 @@ __device__ __forceinline__ void stage_item(const StageArgs<real> &a, const Geom 
                 const real w0 = pl[v * PL + c], wm = pl[v * PL + c - st], wp = pl[v * PL + c + st];
                 const real hs = real(0.5) * limited_slope<real>(lim, w0 - wm, wp - w0);
                 const real lo = w0 - hs, hi = w0 + hs;
-                if (v == 0 || v == D + 1) bad |= !(lo > real(0)) || !(hi > real(0));
+                if (E::positive_var(v)) bad |= !(lo > real(0)) || !(hi > real(0));
                 FSm[(dir * V + v) * NFS + qq] = lo;
                 FSp[(dir * V + v) * NFS + qq] = hi;
             }
@@ -399,7 +470,7 @@ __device__ __forceinline__ void stage_item(const StageArgs<real> &a, const Geom 
             zm[v] = w0 - hs;
             zp[v] = w0 + hs;
         }
-        nonphys |= !(zm[0] > real(0)) || !(zp[0] > real(0)) || !(zm[D + 1] > real(0)) || !(zp[D + 1] > real(0));
+        nonphys |= E::nonphys(zm) || E::nonphys(zp);
     };
 
     const int nface_b = (D == 3) ? N * N : N;
@@ -420,7 +491,7 @@ __device__ __forceinline__ void stage_item(const StageArgs<real> &a, const Geom 
             wL[v] = FSp[v * NFS + jj * (T + 2) + fi];
             wR[v] = FSm[v * NFS + jj * (T + 2) + fi + 1];
         }
-        E::template face_flux<0>(flx, wL, wR, 0, gam, gm1i, F);
+        E::template face_flux<0>(flx, wL, wR, 0, pc, F);
 #pragma unroll
         for (int v = 0; v < V; ++v) Fx[v * NFX + q] = F[v];
         if (fi == 0 && tx0 == 0) store_bflux(0, ty0 + jj + N * k, F);
@@ -434,7 +505,7 @@ __device__ __forceinline__ void stage_item(const StageArgs<real> &a, const Geom 
             wL[v] = FSp[(V + v) * NFS + fj * T + ii];
             wR[v] = FSm[(V + v) * NFS + (fj + 1) * T + ii];
         }
-        E::template face_flux<1>(flx, wL, wR, 1, gam, gm1i, F);
+        E::template face_flux<1>(flx, wL, wR, 1, pc, F);
 #pragma unroll
         for (int v = 0; v < V; ++v) Fy[v * NFX + q] = F[v];
         if (fj == 0 && ty0 == 0) store_bflux(2, tx0 + ii + N * k, F);
@@ -466,7 +537,7 @@ __device__ __forceinline__ void stage_item(const StageArgs<real> &a, const Geom 
             wL[v] = FSp[(dir * V + v) * NFS + iL];
             wR[v] = FSm[(dir * V + v) * NFS + iR];
         }
-        E::template face_flux<-1>(flx, wL, wR, dir, gam, gm1i, F);
+        E::template face_flux<-1>(flx, wL, wR, dir, pc, F);
         real *Fd = dir ? Fy : Fx;
 #pragma unroll
         for (int v = 0; v < V; ++v) Fd[v * NFX + q] = F[v];
@@ -488,17 +559,19 @@ __device__ __forceinline__ void stage_item(const StageArgs<real> &a, const Geom 
         real U[V], src[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) src[v] = real(0);
-        if (a.gravity_on) {
-            // S = (0, rho g, rho g.u) from the conservative state of the cell
-            const real *uc = a.deriv + ob;
-            const real rho = uc[0];
-            real sg = real(0);
+        if constexpr (E::EULER) {
+            if (a.gravity_on) {
+                // S = (0, rho g, rho g.u) from the conservative state of the cell
+                const real *uc = a.deriv + ob;
+                const real rho = uc[0];
+                real sg = real(0);
 #pragma unroll
-            for (int d = 0; d < D; ++d) {
-                src[1 + d] = rho * a.grav[d];
-                sg += uc[(1 + d) * NC] * a.grav[d];
+                for (int d = 0; d < D; ++d) {
+                    src[1 + d] = rho * a.grav[d];
+                    sg += uc[(1 + d) * NC] * a.grav[d];
+                }
+                src[V - 1] = sg;
             }
-            src[D + 1] = sg;
         }
 #pragma unroll
         for (int v = 0; v < V; ++v) {
@@ -530,11 +603,8 @@ __device__ __forceinline__ void stage_item(const StageArgs<real> &a, const Geom 
                          ((m & 8) && gj == N - 1);
             if (D == 3) fixed = fixed || ((m & 16) && k == 0) || ((m & 32) && k == N - 1);
             if (!fixed) {
-                real w[V];
-                E::prim(U, w, gam);
-                const real c = FM<real>::sqrtp(gam * w[D + 1] * FM<real>::rcp(w[0]));
-                real s = (fabs(w[1]) + c) * idx0 + (fabs(w[2]) + c) * idx1;
-                if (D == 3) s += (fabs(w[3]) + c) * idx2;
+                const real idx[3] = {idx0, idx1, idx2};
+                const real s = E::speed(U, gam, idx, pc);
                 vmax = s > vmax ? s : vmax;
             }
         }
@@ -551,7 +621,7 @@ __device__ __forceinline__ void stage_item(const StageArgs<real> &a, const Geom 
             real zm[V], zp[V], pm1[V];
             z_states(-1, zm, pm1);          // plus state of cell -1
             z_states(0, zm, zp);            // minus / plus states of cell 0
-            E::template face_flux<2>(flx, pm1, zm, 2, gam, gm1i, Fz_lo);
+            E::template face_flux<2>(flx, pm1, zm, 2, pc, Fz_lo);
             store_bflux(4, tx0 + ti + N * (ty0 + tj), Fz_lo);
 #pragma unroll
             for (int v = 0; v < V; ++v) Fz_hi[v] = zp[v];     // carries plus(0) into the loop
@@ -568,7 +638,7 @@ __device__ __forceinline__ void stage_item(const StageArgs<real> &a, const Geom 
             x_face(tid, k);
             y_face(tid, k);
             if (tid < 2 * T) extra_face(k);
-            E::template face_flux<2>(flx, zplus, zm1, 2, gam, gm1i, Fz_hi);
+            E::template face_flux<2>(flx, zplus, zm1, 2, pc, Fz_hi);
             if (k == N - 1) store_bflux(5, tx0 + ti + N * (ty0 + tj), Fz_hi);
 #pragma unroll
             for (int v = 0; v < V; ++v) zplus[v] = zp1[v];
@@ -610,9 +680,9 @@ __device__ __forceinline__ void stage_item(const StageArgs<real> &a, const Geom 
 
 // CTAs take items (block, column tile) with a grid stride: one CTA per item
 // when the grid covers them all, a persistent sweep when it is smaller.
-template <class real, int D, int N, int NG, int T, bool GEN>
+template <class real, int D, int N, int NG, int T, bool GEN, int PH>
 __global__ void __launch_bounds__(T * T) k_stage(StageArgs<real> a, Geom g) {
-    for (int item = blockIdx.x; item < a.n_items; item += gridDim.x) stage_item<real, D, N, NG, T, GEN>(a, g, item);
+    for (int item = blockIdx.x; item < a.n_items; item += gridDim.x) stage_item<real, D, N, NG, T, GEN, PH>(a, g, item);
 }
 
 }  // namespace amrb

@@ -1,5 +1,6 @@
 // Finite-volume stage with WENO5 face reconstruction (Sec. 3.2 lists WENO5
-// among the limiters; it needs three ghost layers).  The same sub-step of
+// among the limiters; it needs three ghost layers), for Euler and for scalar
+// advection.  The same sub-step of
 // Eq. 5 as stage.cuh, split into three passes over global memory because the
 // five-cell stencils do not fit the two-cell halo of the plane-ring kernels:
 //   k_weno_prim    primitives of every cell of every block (incl. ghosts)
@@ -35,7 +36,8 @@ __device__ __forceinline__ real weno5_face(real a, real b, real c, real d, real 
     return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
 }
 
-// primitives of all S^D cells of every block: prim[b][v][cell]
+// primitives of all S^D cells of every block: prim[b][v][cell] (Euler only:
+// for scalar advection they are the state itself)
 template <class real, int D>
 __global__ void __launch_bounds__(256) k_weno_prim(const real *__restrict__ u, real *__restrict__ prim, Geom g, real gam) {
     using E = Euler<real, D>;
@@ -56,12 +58,12 @@ __global__ void __launch_bounds__(256) k_weno_prim(const real *__restrict__ u, r
 // position fp along n (fastest) and tangential index t = t0 + N t1 (t0 along
 // the lower tangential dimension).  flux[b][n][v][fp + (N+1) t].
 // blockIdx.x = block, blockIdx.y = chunk of 256 faces.
-template <class real, int D>
+template <class real, int D, int PH>
 __global__ void __launch_bounds__(256) k_weno_flux(const real *__restrict__ prim, real *__restrict__ flux,
-                                                   const BlockInfo *__restrict__ info, real *bflux, Geom g, real gam,
-                                                   int flux_kind, DevScalars *sc) {
-    using E = Euler<real, D>;
-    constexpr int V = D + 2;
+                                                   const BlockInfo *__restrict__ info, real *bflux, Geom g,
+                                                   PhysCtx<real> pc, int flux_kind, DevScalars *sc) {
+    using E = Phys<real, D, PH>;
+    constexpr int V = E::V;
     const int N = g.N, NG = g.ng, S = g.S;
     const int nface = D == 3 ? N * N : N;            // tangential faces per position
     const int nf = (N + 1) * nface;                  // faces per direction
@@ -90,10 +92,10 @@ __global__ void __launch_bounds__(256) k_weno_flux(const real *__restrict__ prim
         wL[v] = weno5_face<real>(w0, w1, w2, w3, w4);
         wR[v] = weno5_face<real>(w5, w4, w3, w2, w1);
     }
-    bad = !(wL[0] > real(0)) || !(wL[D + 1] > real(0)) || !(wR[0] > real(0)) || !(wR[D + 1] > real(0));
-    if (n == 0) E::template face_flux<0>(flux_kind, wL, wR, 0, gam, real(1) / (gam - real(1)), F);
-    else if (n == 1) E::template face_flux<1>(flux_kind, wL, wR, 1, gam, real(1) / (gam - real(1)), F);
-    else E::template face_flux<2>(flux_kind, wL, wR, 2, gam, real(1) / (gam - real(1)), F);
+    bad = E::nonphys(wL) || E::nonphys(wR);
+    if (n == 0) E::template face_flux<0>(flux_kind, wL, wR, 0, pc, F);
+    else if (n == 1) E::template face_flux<1>(flux_kind, wL, wR, 1, pc, F);
+    else E::template face_flux<2>(flux_kind, wL, wR, 2, pc, F);
     real *fb = flux + (int64_t(b) * D + n) * V * nf;
 #pragma unroll
     for (int v = 0; v < V; ++v) fb[int64_t(v) * nf + r] = F[v];
@@ -109,10 +111,10 @@ __global__ void __launch_bounds__(256) k_weno_flux(const real *__restrict__ prim
 }
 
 // one thread per interior cell; blockIdx.x = block, blockIdx.y = chunk of 256 cells
-template <class real, int D>
+template <class real, int D, int PH>
 __global__ void __launch_bounds__(256) k_weno_update(StageArgs<real> a, const real *__restrict__ flux, Geom g) {
-    using E = Euler<real, D>;
-    constexpr int V = D + 2;
+    using E = Phys<real, D, PH>;
+    constexpr int V = E::V;
     __shared__ double red[8];
     const int N = g.N, NG = g.ng, S = g.S;
     const int nface = D == 3 ? N * N : N;
@@ -140,14 +142,16 @@ __global__ void __launch_bounds__(256) k_weno_update(StageArgs<real> a, const re
                 const real *fv = fb + (int64_t(n) * V + v) * nf;
                 r += (fv[idx] - fv[idx + 1]) * real(g.inv_dx[3 * gc + n]);
             }
-            if (a.gravity_on && v > 0) {
-                if (v <= D) {
-                    r += a.deriv[ob] * a.grav[v - 1];
-                } else {
-                    real sg = real(0);
+            if constexpr (E::EULER) {
+                if (a.gravity_on && v > 0) {
+                    if (v <= D) {
+                        r += a.deriv[ob] * a.grav[v - 1];
+                    } else {
+                        real sg = real(0);
 #pragma unroll
-                    for (int d = 0; d < D; ++d) sg += a.deriv[ob + int64_t(1 + d) * g.ncell] * a.grav[d];
-                    r += sg;
+                        for (int d = 0; d < D; ++d) sg += a.deriv[ob + int64_t(1 + d) * g.ncell] * a.grav[d];
+                        r += sg;
+                    }
                 }
             }
             real acc = real(0);
@@ -164,13 +168,20 @@ __global__ void __launch_bounds__(256) k_weno_update(StageArgs<real> a, const re
                          ((m & 8) && x[1] == N - 1);
             if (D == 3) fixed = fixed || ((m & 16) && x[2] == 0) || ((m & 32) && x[2] == N - 1);
             if (!fixed) {
-                real w[V];
-                E::prim(U, w, a.gamma);
-                const real cs = sqrt(a.gamma * w[D + 1] / w[0]);
-                real s = real(0);
+                if constexpr (E::EULER) {
+                    real w[V];
+                    E::prim(U, w, a.gamma);
+                    const real cs = sqrt(a.gamma * w[D + 1] / w[0]);
+                    real s = real(0);
 #pragma unroll
-                for (int d = 0; d < D; ++d) s += (fabs(w[1 + d]) + cs) * real(g.inv_dx[3 * gc + d]);
-                vmax = double(s);
+                    for (int d = 0; d < D; ++d) s += (fabs(w[1 + d]) + cs) * real(g.inv_dx[3 * gc + d]);
+                    vmax = double(s);
+                } else {
+                    real s = real(0);
+#pragma unroll
+                    for (int d = 0; d < D; ++d) s += fabs(a.vel[d]) * real(g.inv_dx[3 * gc + d]);
+                    vmax = double(s);
+                }
             }
         }
     }

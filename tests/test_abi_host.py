@@ -199,5 +199,34 @@ def test_bench_entry_points_exist():
     the repository name those command lines) are defined."""
     import bench
     for name in ("run_ours", "run_reference", "run_amr_static", "run_adaptive", "run_ncu_case", "oracle_sample",
-                 "ghost_case_spec", "workload_spec", "stage_kernel_hash", "traffic_from_profile"):
+                 "ghost_case_spec", "workload_spec", "stage_kernel_hash", "traffic_from_profile", "run_advection"):
         assert callable(getattr(bench, name)), name
+
+
+def test_advection_config_validation_and_checkpoint(tmp_path):
+    """Scalar advection forests: one variable, no gravity, finite velocity;
+    the physics and the velocity survive a checkpoint round trip."""
+    lib = amr.load()
+    h = C.c_void_p()
+    sp = synth.advection_spec(ndim=3, N=8, ntrees=(2, 2, 2), velocity=(1.0, -0.5, 0.25), max_level=1)
+    for field, value in [("n_var", 5), ("physics", 2)]:
+        cfg = amr.config_from_spec(sp, 64, host_only=True)
+        setattr(cfg, field, value)
+        assert lib.amr_create_forest(C.byref(cfg), 0, C.byref(h)) == amr.AMR_EINVAL, field
+    cfg = amr.config_from_spec(sp, 64, host_only=True)
+    cfg.gravity[2] = -1.0
+    assert lib.amr_create_forest(C.byref(cfg), 0, C.byref(h)) == amr.AMR_EINVAL
+    cfg = amr.config_from_spec(sp, 64, host_only=True)
+    cfg.velocity[0] = float("nan")
+    assert lib.amr_create_forest(C.byref(cfg), 0, C.byref(h)) == amr.AMR_EINVAL
+    euler = synth.MeshSpec(ndim=3, N=8, ng=2, ntrees=(2, 2, 2))
+    cfg = amr.config_from_spec(euler, 64, host_only=True)
+    cfg.n_var = 1
+    assert lib.amr_create_forest(C.byref(cfg), 0, C.byref(h)) == amr.AMR_EINVAL
+    f = amr.Forest(sp, 0, max_blocks=512, host_only=True)
+    f.regrid(synth.ball_flags(sp, *f.blocks(), (0.3, 0.3, 0.3), (0.2,)))
+    path = tmp_path / "adv.ckpt"
+    f.save(str(path))
+    g = amr.Forest.load(str(path), host_only=True)
+    assert g.spec.physics == 1 and tuple(g.spec.velocity) == (1.0, -0.5, 0.25) and g.spec.nvar == 1
+    np.testing.assert_array_equal(f.pattern(), g.pattern())
