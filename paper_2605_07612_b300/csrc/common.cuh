@@ -62,6 +62,22 @@ struct Geom {
     double vel[3];          // advection velocity
 };
 
+// Approximate reciprocal and reciprocal square root of an FP32 value with
+// denormal inputs and results flushed to zero: one special-function
+// instruction each.  For normal inputs and results they equal the non-flushing
+// forms (rsqrtf, __fdividef(1, x)), which add a denormal check and rescale
+// around the same instruction.
+__device__ __forceinline__ float rsqrt_ftz(float a) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
+__device__ __forceinline__ float rcp_ftz(float a) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
+
 // Device-resident scalars of a forest.
 struct DevScalars {
     double dt;

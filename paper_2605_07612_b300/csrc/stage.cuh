@@ -67,14 +67,14 @@ template <class real>
 struct FM;
 template <>
 struct FM<float> {
-    __device__ static __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
+    __device__ static __forceinline__ float rcp(float x) { return rcp_ftz(x); }
     // sqrt(x) and 1/x for x > 0
     __device__ static __forceinline__ void sqrt_inv(float x, float &s, float &inv) {
-        const float r = rsqrtf(x);
+        const float r = rsqrt_ftz(x);
         s = x * r;
         inv = r * r;
     }
-    __device__ static __forceinline__ float sqrtp(float x) { return x * rsqrtf(x); }   // x > 0
+    __device__ static __forceinline__ float sqrtp(float x) { return x * rsqrt_ftz(x); }   // x > 0
 };
 template <>
 struct FM<double> {

@@ -17,9 +17,9 @@
 // states (MUSCL with minmod) are formed in the flux phase from the ring: an
 // x-face pair reads three aligned pairs of a row, a y- or z-face pair four.
 // The T x-faces and T y-faces left over at the tile's upper edges are taken
-// by T/2 threads of the first and T/2 of the second warp; the second round of
-// halo loads goes to the last warps, so that the warps meet at the barrier
-// with similar amounts of work.
+// by the first warp in one flux evaluation (T/2 lanes per normal, the normal
+// chosen at run time); the second round of halo loads goes to the last
+// warps.
 #pragma once
 
 #include "stage.cuh"
@@ -33,8 +33,8 @@ struct PF {
     __device__ static __forceinline__ float2 sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
     __device__ static __forceinline__ float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
     __device__ static __forceinline__ float2 fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-    __device__ static __forceinline__ float2 rsqrt(float2 a) { return make_float2(rsqrtf(a.x), rsqrtf(a.y)); }
-    __device__ static __forceinline__ float2 rcp(float2 a) { return make_float2(__fdividef(1.f, a.x), __fdividef(1.f, a.y)); }
+    __device__ static __forceinline__ float2 rsqrt(float2 a) { return make_float2(rsqrt_ftz(a.x), rsqrt_ftz(a.y)); }
+    __device__ static __forceinline__ float2 rcp(float2 a) { return make_float2(rcp_ftz(a.x), rcp_ftz(a.y)); }
     __device__ static __forceinline__ float2 abs(float2 a) { return make_float2(fabsf(a.x), fabsf(a.y)); }
     // 0.5 minmod(a, b) = qs(a, b) * mabs(a, b): qs = (sign a + sign b) / 4 is
     // +-1/2 when the signs agree and 0 otherwise; mabs = min(|a|, |b|) (a zero
@@ -277,8 +277,8 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
     // into the ring.  An interior plane (0 <= k < N) needs the tile and its
     // x/y halo without the corners: NPAIR = (T^2 + 8T) / 2 pairs, numbered row
     // by row.  Every thread takes pair tid; the remaining REST pairs go to the
-    // last REST threads (warps 2 and 3 for T = 16, whose first two warps
-    // compute the tile's edge faces).  The source of a thread's pairs does
+    // last REST threads (warps 2 and 3 for T = 16, whose first warp
+    // computes the tile's edge faces).  The source of a thread's pairs does
     // not change with k, so its address at k = 0 is kept.  The planes k < 0
     // and k >= N need only the tile: thread tid takes its own pair.
     constexpr int HP = T / 2, WP = (T + 4) / 2;
@@ -423,38 +423,36 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
             pair_flux<2>(wL, wR, 2, gam, gm1i, Fz_new);
             if (k == N - 1) store_bflux2(5, tx0 + ci + N * (ty0 + tj), Fz_new);
         }
-        // the tile's upper edge faces: x-face T of rows (2r, 2r+1) by the first
-        // T/2 threads, y-face T of columns (2r, 2r+1) by T/2 threads of the
-        // next warp (of the same warp when the CTA has one)
-        constexpr int YT = NT > 32 ? 32 : T / 2;
-        if (tid < T / 2) {
-            const int r = tid;
+        // the tile's upper edge faces, both in the first warp: lanes r < T/2
+        // take x-face T of rows (2r, 2r+1), lanes T/2 + r y-face T of
+        // columns (2r, 2r+1); one flux evaluation with a runtime normal
+        if (tid < T) {
+            const bool isx = tid < T / 2;
+            const int r = isx ? tid : tid - T / 2;
+            const int base = isx ? (2 * r + 2) * P + T : T * P + 2 + 2 * r;
+            const int st = isx ? 1 : P, po = isx ? P : 1;
 #pragma unroll
             for (int v = 0; v < V; ++v) {
-                const float *row0 = pl + v * PL + (2 * r + 2) * P + 2, *row1 = row0 + P;
-                pair_states<LIM>(make_float2(row0[T - 2], row1[T - 2]), make_float2(row0[T - 1], row1[T - 1]),
-                            make_float2(row0[T], row1[T]), make_float2(row0[T + 1], row1[T + 1]), wL[v], wR[v]);
+                const float *b0 = pl + v * PL + base;
+                pair_states<LIM>(make_float2(b0[0], b0[po]), make_float2(b0[st], b0[st + po]),
+                                 make_float2(b0[2 * st], b0[2 * st + po]), make_float2(b0[3 * st], b0[3 * st + po]), wL[v], wR[v]);
             }
-            pair_flux<0>(wL, wR, 0, gam, gm1i, F);
+            pair_flux<-1>(wL, wR, isx ? 0 : 1, gam, gm1i, F);
+            if (isx) {
 #pragma unroll
-            for (int v = 0; v < V; ++v) {
-                Fx[v * NFX + (2 * r) * FXP + T] = F[v].x;
-                Fx[v * NFX + (2 * r + 1) * FXP + T] = F[v].y;
+                for (int v = 0; v < V; ++v) {
+                    Fx[v * NFX + (2 * r) * FXP + T] = F[v].x;
+                    Fx[v * NFX + (2 * r + 1) * FXP + T] = F[v].y;
+                }
+                if (tx0 + T == N) {
+                    store_bflux1(1, ty0 + 2 * r + N * k, F[0].x, F[1].x, F[2].x, F[3].x, F[4].x);
+                    store_bflux1(1, ty0 + 2 * r + 1 + N * k, F[0].y, F[1].y, F[2].y, F[3].y, F[4].y);
+                }
+            } else {
+#pragma unroll
+                for (int v = 0; v < V; ++v) *reinterpret_cast<float2 *>(Fy + v * (T + 1) * T + Sh::fy(T, 2 * r)) = F[v];
+                if (ty0 + T == N) store_bflux2(3, tx0 + 2 * r + N * k, F);
             }
-            if (tx0 + T == N) {
-                store_bflux1(1, ty0 + 2 * r + N * k, F[0].x, F[1].x, F[2].x, F[3].x, F[4].x);
-                store_bflux1(1, ty0 + 2 * r + 1 + N * k, F[0].y, F[1].y, F[2].y, F[3].y, F[4].y);
-            }
-        } else if (tid >= YT && tid < YT + T / 2) {
-            const int r = tid - YT;
-#pragma unroll
-            for (int v = 0; v < V; ++v)
-                pair_states<LIM>(ld2(pl, v, T - 2, 2 * r), ld2(pl, v, T - 1, 2 * r), ld2(pl, v, T, 2 * r), ld2(pl, v, T + 1, 2 * r),
-                            wL[v], wR[v]);
-            pair_flux<1>(wL, wR, 1, gam, gm1i, F);
-#pragma unroll
-            for (int v = 0; v < V; ++v) *reinterpret_cast<float2 *>(Fy + v * (T + 1) * T + Sh::fy(T, 2 * r)) = F[v];
-            if (ty0 + T == N) store_bflux2(3, tx0 + 2 * r + N * k, F);
         }
     };
 
@@ -465,7 +463,7 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
     // at the start of the next plane period) and this block's derivative
     // plane k + 4 (loaded into registers in the next plane period)
     auto l2_ahead = [&](int k) {
-        if (tid != NT - 32) return;   // a thread of the last warp (the first two take the edge faces)
+        if (tid != NT - 32) return;   // a thread of the last warp (the first takes the edge faces)
         constexpr unsigned PB = unsigned(S) * S * sizeof(float);
         const int64_t blk = int64_t(b) * V * NC;
         if (k < N) {
