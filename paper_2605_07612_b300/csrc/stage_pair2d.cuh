@@ -9,19 +9,20 @@
 // shared memory with cp.async -- together with its cells' previous states --
 // converts them to primitives in place, and then
 //   [x and y fluxes of the tile] barrier [update] barrier.
-// The thread mapping, halo numbering, conflict-free pitches and the split of
-// the tile's edge faces over two warps are those of the 3D kernel.
+// The thread mapping, halo numbering, conflict-free pitches and the tile's
+// edge faces in one warp are those of the 3D kernel.
 #pragma once
 
 #include "stage_pair.cuh"
 
 namespace amrb {
 
-// Rusanov / Einfeldt flux of a pair of faces with normal NRM (0 x, 1 y) from
-// primitive states (rho, u, v, p).
+// Rusanov / Einfeldt flux of a pair of faces with normal NRM (0 x, 1 y; or
+// NRM < 0 and the runtime normal n) from primitive states (rho, u, v, p).
 template <int NRM>
-__device__ __forceinline__ void pair_flux2d(const float2 *wL, const float2 *wR, float gam, float gm1i, float2 *F) {
-    const float2 vnL = wL[1 + NRM], vnR = wR[1 + NRM];
+__device__ __forceinline__ void pair_flux2d(const float2 *wL, const float2 *wR, int n, float gam, float gm1i, float2 *F) {
+    const int nn = NRM >= 0 ? NRM : n;
+    const float2 vnL = nn == 0 ? wL[1] : wL[2], vnR = nn == 0 ? wR[1] : wR[2];
     const float2 rL = wL[0], rR = wR[0], pL = wL[3], pR = wR[3];
     const float2 qL = PF::rsqrt(rL), qR = PF::rsqrt(rR);
     const float2 sL = PF::mul(rL, qL), sR = PF::mul(rR, qR);
@@ -46,7 +47,7 @@ __device__ __forceinline__ void pair_flux2d(const float2 *wL, const float2 *wR, 
 #pragma unroll
     for (int d2i = 0; d2i < 2; ++d2i) {
         float2 fl = PF::fma(mL, wL[1 + d2i], PF::mul(mR, wR[1 + d2i]));
-        if (d2i == NRM) fl = PF::add(fl, PF::add(pL, pR));
+        if (d2i == nn) fl = PF::add(fl, PF::add(pL, pR));
         const float2 jump = PF::sub(PF::mul(rR, wR[1 + d2i]), PF::mul(rL, wL[1 + d2i]));
         F[1 + d2i] = PF::fma(nha, jump, PF::mul(half, fl));
     }
@@ -212,48 +213,47 @@ __device__ __forceinline__ void stage_pair2d_item(const StageArgs<float> &a, con
             const float2 A = ld2(v, tj, ci - 2), B = ld2(v, tj, ci), C2 = ld2(v, tj, ci + 2);
             pair_states<LIM>(A, make_float2(A.y, B.x), B, make_float2(B.y, C2.x), wL[v], wR[v]);
         }
-        pair_flux2d<0>(wL, wR, gam, gm1i, F);
+        pair_flux2d<0>(wL, wR, 0, gam, gm1i, F);
 #pragma unroll
         for (int v = 0; v < V; ++v) *reinterpret_cast<float2 *>(Fx + v * NFX + tj * FXP + ci) = F[v];
         if (ci == 0 && tx0 == 0) store_bflux1(0, ty0 + tj, F, false);
 #pragma unroll
         for (int v = 0; v < V; ++v)
             pair_states<LIM>(ld2(v, tj - 2, ci), ld2(v, tj - 1, ci), ld2(v, tj, ci), ld2(v, tj + 1, ci), wL[v], wR[v]);
-        pair_flux2d<1>(wL, wR, gam, gm1i, F);
+        pair_flux2d<1>(wL, wR, 1, gam, gm1i, F);
 #pragma unroll
         for (int v = 0; v < V; ++v) *reinterpret_cast<float2 *>(Fy + v * (T + 1) * T + Sh::fy(tj, ci)) = F[v];
         if (tj == 0 && ty0 == 0) store_bflux2(2, tx0 + ci, F);
-        // the tile's upper edge faces: x-face T of rows (2r, 2r+1) by the first
-        // T/2 threads, y-face T of columns (2r, 2r+1) by T/2 threads of the
-        // next warp (of the same warp when the CTA has one)
-        constexpr int YT = NT > 32 ? 32 : T / 2;
-        if (tid < T / 2) {
-            const int r = tid;
+        // the tile's upper edge faces, both in the first warp: lanes r < T/2
+        // take x-face T of rows (2r, 2r+1), lanes T/2 + r y-face T of
+        // columns (2r, 2r+1); one flux evaluation with a runtime normal
+        if (tid < T) {
+            const bool isx = tid < T / 2;
+            const int r = isx ? tid : tid - T / 2;
+            const int base = isx ? (2 * r + 2) * P + T : T * P + 2 + 2 * r;
+            const int st = isx ? 1 : P, po = isx ? P : 1;
 #pragma unroll
             for (int v = 0; v < V; ++v) {
-                const float *row0 = pl + v * PL + (2 * r + 2) * P + 2, *row1 = row0 + P;
-                pair_states<LIM>(make_float2(row0[T - 2], row1[T - 2]), make_float2(row0[T - 1], row1[T - 1]),
-                                 make_float2(row0[T], row1[T]), make_float2(row0[T + 1], row1[T + 1]), wL[v], wR[v]);
+                const float *b0 = pl + v * PL + base;
+                pair_states<LIM>(make_float2(b0[0], b0[po]), make_float2(b0[st], b0[st + po]),
+                                 make_float2(b0[2 * st], b0[2 * st + po]), make_float2(b0[3 * st], b0[3 * st + po]), wL[v], wR[v]);
             }
-            pair_flux2d<0>(wL, wR, gam, gm1i, F);
+            pair_flux2d<-1>(wL, wR, isx ? 0 : 1, gam, gm1i, F);
+            if (isx) {
 #pragma unroll
-            for (int v = 0; v < V; ++v) {
-                Fx[v * NFX + (2 * r) * FXP + T] = F[v].x;
-                Fx[v * NFX + (2 * r + 1) * FXP + T] = F[v].y;
+                for (int v = 0; v < V; ++v) {
+                    Fx[v * NFX + (2 * r) * FXP + T] = F[v].x;
+                    Fx[v * NFX + (2 * r + 1) * FXP + T] = F[v].y;
+                }
+                if (tx0 + T == N) {
+                    store_bflux1(1, ty0 + 2 * r, F, false);
+                    store_bflux1(1, ty0 + 2 * r + 1, F, true);
+                }
+            } else {
+#pragma unroll
+                for (int v = 0; v < V; ++v) *reinterpret_cast<float2 *>(Fy + v * (T + 1) * T + Sh::fy(T, 2 * r)) = F[v];
+                if (ty0 + T == N) store_bflux2(3, tx0 + 2 * r, F);
             }
-            if (tx0 + T == N) {
-                store_bflux1(1, ty0 + 2 * r, F, false);
-                store_bflux1(1, ty0 + 2 * r + 1, F, true);
-            }
-        } else if (tid >= YT && tid < YT + T / 2) {
-            const int r = tid - YT;
-#pragma unroll
-            for (int v = 0; v < V; ++v)
-                pair_states<LIM>(ld2(v, T - 2, 2 * r), ld2(v, T - 1, 2 * r), ld2(v, T, 2 * r), ld2(v, T + 1, 2 * r), wL[v], wR[v]);
-            pair_flux2d<1>(wL, wR, gam, gm1i, F);
-#pragma unroll
-            for (int v = 0; v < V; ++v) *reinterpret_cast<float2 *>(Fy + v * (T + 1) * T + Sh::fy(T, 2 * r)) = F[v];
-            if (ty0 + T == N) store_bflux2(3, tx0 + 2 * r, F);
         }
     }
     __syncthreads();
