@@ -79,46 +79,127 @@ struct PairShape2D {
         if constexpr (T == 16) return 32 * (row >> 1) + 16 * ((row ^ (row >> 2)) & 1) + c;
         else return row * T + c;
     }
+    // two tile buffers (the next item's copies land in one while the CTA
+    // works on the other), one flux buffer, two previous-state buffers
+    static constexpr int PLB = V * PL;
     static constexpr size_t smem_bytes(int nprev) {
-        return sizeof(float) * (size_t(V) * PL + size_t(FBUF)) + sizeof(float2) * size_t(nprev > 0 ? nprev : 0) * V * NT;
+        return sizeof(float) * (2 * size_t(PLB) + size_t(FBUF)) + 2 * sizeof(float2) * size_t(nprev > 0 ? nprev : 0) * V * NT;
     }
 };
 
-template <int N, int TT, int NPREV, int LIM>
-__device__ __forceinline__ void stage_pair2d_item(const StageArgs<float> &a, const Geom &g, int item) {
+// halo pair p of a tile (0 <= p < NPAIR): the pairs numbered row by row, the
+// tile's rows with their x halo, the two y-halo rows below and above without
+// the corners
+template <int T>
+__device__ __forceinline__ void pair2d_rc(int p, int &ii, int &jj) {
+    constexpr int HP = T / 2, WP = (T + 4) / 2;
+    if (p < 2 * HP) {
+        jj = p / HP - 2;
+        ii = 2 * (p % HP);
+    } else if (p < 2 * HP + T * WP) {
+        const int q = p - 2 * HP;
+        jj = q / WP;
+        ii = 2 * (q % WP) - 2;
+    } else {
+        const int q = p - 2 * HP - T * WP;
+        jj = T + q / HP;
+        ii = 2 * (q % HP);
+    }
+}
+
+// thread -> the pair of cells it updates (row tj, first column ci)
+template <int T>
+__device__ __forceinline__ void pair2d_owner(int tid, int &ci, int &tj) {
+    if constexpr (T == 16) {
+        const int lane = tid & 31, q = (tid >> 5) * 2 + (lane >> 4);
+        ci = 2 * (lane & 7);
+        tj = (q & 3) + (q >> 2) * 8 + ((lane >> 3) & 1) * 4;
+    } else {
+        ci = 2 * (tid % (T / 2));
+        tj = tid / (T / 2);
+    }
+}
+
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// Asynchronous copies of one item into tile buffer `buf`: the tile with its
+// halo (in gather mode from the same-level neighbours) and the previous
+// states of the thread's pair; one commit group.
+template <int N, int TT, int NPREV>
+__device__ __forceinline__ void pair2d_issue(const StageArgs<float> &a, int item, int buf) {
     using Sh = PairShape2D<N, TT>;
     constexpr int T = Sh::T, NG = Sh::NG, S = Sh::S, P = Sh::P, PL = Sh::PL, V = Sh::V, NT = Sh::NT;
-    constexpr int FXP = Sh::FXP, NFX = Sh::NFX, FBUF = Sh::FBUF;
+    constexpr int64_t NC = int64_t(S) * S;
+    constexpr int HP = T / 2, WP = (T + 4) / 2;
+    constexpr int NPAIR = 2 * HP + T * WP + 2 * HP, REST = NPAIR - NT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *pl = reinterpret_cast<float *>(smem_raw) + buf * Sh::PLB;
+    float2 *stg = reinterpret_cast<float2 *>(reinterpret_cast<float *>(smem_raw) + 2 * Sh::PLB + Sh::FBUF) +
+                  buf * (NPREV > 0 ? NPREV : 0) * V * NT;
+    const int tid = threadIdx.x;
+    const int b = item / Sh::TILES;
+    const int tile = item - b * Sh::TILES;
+    const int tx0 = (tile % (N / T)) * T, ty0 = (tile / (N / T)) * T;
+    const BlockInfo &info = a.info[b];
+    const int nb0 = a.gather ? info.nbr[0] : -1, nb1 = a.gather ? info.nbr[1] : -1;
+    const int nb2 = a.gather ? info.nbr[2] : -1, nb3 = a.gather ? info.nbr[3] : -1;
+    const float *ub = a.deriv + int64_t(b) * V * NC;
+    auto gofs = [&](int i, int j) -> int64_t { return int64_t(j + NG) * S + (i + NG); };
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+        const int p = l == 0 ? tid : (tid >= NT - REST ? NT + tid - (NT - REST) : -1);
+        if (p < 0) continue;
+        int ii, jj;
+        pair2d_rc<T>(p, ii, jj);
+        int gi = tx0 + ii, gj = ty0 + jj, nb = -1;
+        if (gi < 0) { nb = nb0; gi += N; }
+        else if (gi >= N) { nb = nb1; gi -= N; }
+        else if (gj < 0) { nb = nb2; gj += N; }
+        else if (gj >= N) { nb = nb3; gj -= N; }
+        const float *src = nb >= 0 ? a.deriv + int64_t(nb) * V * NC + gofs(gi, gj) : ub + gofs(tx0 + ii, ty0 + jj);
+        const int hoff = (jj + 2) * P + ii + 2;
+#pragma unroll
+        for (int v = 0; v < V; ++v) cp_async8(pl + hoff + v * PL, src + v * NC);
+    }
+    if constexpr (NPREV > 0) {
+        int ci, tj;
+        pair2d_owner<T>(tid, ci, tj);
+        const int64_t ob = int64_t(b) * V * NC + gofs(tx0 + ci, ty0 + tj);
+#pragma unroll
+        for (int q = 0; q < NPREV; ++q)
+#pragma unroll
+            for (int v = 0; v < V; ++v) cp_async8(stg + (q * V + v) * NT + tid, a.prev[q] + ob + v * NC);
+    }
+    cp_async_commit();
+}
+
+// One item whose copies (pair2d_issue into buffer `buf`) have arrived:
+// conversion to primitives, fluxes, update.
+template <int N, int TT, int NPREV, int LIM>
+__device__ __forceinline__ void stage_pair2d_item(const StageArgs<float> &a, const Geom &g, int item, int buf) {
+    using Sh = PairShape2D<N, TT>;
+    constexpr int T = Sh::T, NG = Sh::NG, S = Sh::S, P = Sh::P, PL = Sh::PL, V = Sh::V, NT = Sh::NT;
+    constexpr int FXP = Sh::FXP, NFX = Sh::NFX;
     constexpr int64_t NC = int64_t(S) * S;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float *pl = reinterpret_cast<float *>(smem_raw);            // [V][P*P] the tile and its halo
-    float *Fx = pl + V * PL;                                    // [V][T][FXP]
-    float *Fy = Fx + V * NFX;                                   // [V][T+1][T] (rows swizzled)
-    float2 *stg = reinterpret_cast<float2 *>(Fx + FBUF);        // [NPREV][V][NT] previous states
+    float *pl = reinterpret_cast<float *>(smem_raw) + buf * Sh::PLB;        // [V][P*P] the tile and its halo
+    float *Fx = reinterpret_cast<float *>(smem_raw) + 2 * Sh::PLB;          // [V][T][FXP]
+    float *Fy = Fx + V * NFX;                                               // [V][T+1][T] (rows swizzled)
+    const float2 *stg = reinterpret_cast<const float2 *>(Fx + Sh::FBUF) +
+                        buf * (NPREV > 0 ? NPREV : 0) * V * NT;             // [NPREV][V][NT] previous states
 
     const int tid = threadIdx.x;
     const int b = item / Sh::TILES;
     const int tile = item - b * Sh::TILES;
     const int tx0 = (tile % (N / T)) * T, ty0 = (tile / (N / T)) * T;
-    int ip, tj;
-    if constexpr (T == 16) {
-        const int lane = tid & 31, q = (tid >> 5) * 2 + (lane >> 4);
-        ip = lane & 7;
-        tj = (q & 3) + (q >> 2) * 8 + ((lane >> 3) & 1) * 4;
-    } else {
-        ip = tid % (T / 2);
-        tj = tid / (T / 2);
-    }
-    const int ci = 2 * ip;
+    int ci, tj;
+    pair2d_owner<T>(tid, ci, tj);
     const BlockInfo info = a.info[b];
     const int gc = info.gclass;
     const float idx0 = float(g.inv_dx[3 * gc]), idx1 = float(g.inv_dx[3 * gc + 1]);
     const float gam = a.gamma;
     const float gm1i = 1.f / (gam - 1.f);
     const float dt_eff = float(a.w_dt * a.sc_in[info.inst].dt);
-    const float *__restrict__ ub = a.deriv + int64_t(b) * V * NC;
-    const int nb0 = a.gather ? info.nbr[0] : -1, nb1 = a.gather ? info.nbr[1] : -1;
-    const int nb2 = a.gather ? info.nbr[2] : -1, nb3 = a.gather ? info.nbr[3] : -1;
     bool nonphys = false;
     float vmax = 0.f;
 
@@ -127,9 +208,7 @@ __device__ __forceinline__ void stage_pair2d_item(const StageArgs<float> &a, con
         return *reinterpret_cast<const float2 *>(pl + v * PL + (jj + 2) * P + (ii + 2));
     };
 
-    // ---- copies: the tile with its halo (pairs numbered as in the 3D kernel's
-    // interior planes; in gather mode the halo comes from the same-level
-    // neighbours) and this thread's previous states
+    // ---- conversion of the thread's copied pairs to primitives, in place
     constexpr int HP = T / 2, WP = (T + 4) / 2;
     constexpr int NPAIR = 2 * HP + T * WP + 2 * HP, REST = NPAIR - NT;
     static_assert(REST > 0 && REST <= NT, "two load rounds");
@@ -142,37 +221,10 @@ __device__ __forceinline__ void stage_pair2d_item(const StageArgs<float> &a, con
         hoff[l] = 0;
         if (p < 0) continue;
         int ii, jj;
-        if (p < 2 * HP) {
-            jj = p / HP - 2;
-            ii = 2 * (p % HP);
-        } else if (p < 2 * HP + T * WP) {
-            const int q = p - 2 * HP;
-            jj = q / WP;
-            ii = 2 * (q % WP) - 2;
-        } else {
-            const int q = p - 2 * HP - T * WP;
-            jj = T + q / HP;
-            ii = 2 * (q % HP);
-        }
-        int gi = tx0 + ii, gj = ty0 + jj, nb = -1;
-        if (gi < 0) { nb = nb0; gi += N; }
-        else if (gi >= N) { nb = nb1; gi -= N; }
-        else if (gj < 0) { nb = nb2; gj += N; }
-        else if (gj >= N) { nb = nb3; gj -= N; }
-        const float *src = nb >= 0 ? a.deriv + int64_t(nb) * V * NC + gofs(gi, gj) : ub + gofs(tx0 + ii, ty0 + jj);
+        pair2d_rc<T>(p, ii, jj);
         hoff[l] = (jj + 2) * P + ii + 2;
-#pragma unroll
-        for (int v = 0; v < V; ++v) cp_async8(pl + hoff[l] + v * PL, src + v * NC);
     }
     const int64_t ob = int64_t(b) * V * NC + gofs(tx0 + ci, ty0 + tj);
-    if constexpr (NPREV > 0) {
-#pragma unroll
-        for (int q = 0; q < NPREV; ++q)
-#pragma unroll
-            for (int v = 0; v < V; ++v) cp_async8(stg + (q * V + v) * NT + tid, a.prev[q] + ob + v * NC);
-    }
-    cp_async_commit();
-    cp_async_wait_all();
 #pragma unroll
     for (int l = 0; l < 2; ++l) {
         if (!hval[l]) continue;
@@ -325,9 +377,23 @@ __device__ __forceinline__ void stage_pair2d_item(const StageArgs<float> &a, con
     if (__syncthreads_or(nonphys) && tid == 0) raise_status(&a.sc[0].status, 7);
 }
 
+// CTAs take items with a grid stride; the copies of a CTA's next item are
+// issued before it works on the current one.
 template <int N, int TT, int NPREV, int LIM>
 __global__ void __launch_bounds__(PairShape2D<N, TT>::NT, (TT >= 16 ? 5 : 2)) k_stage_pair2d(StageArgs<float> a, Geom g) {
-    for (int item = blockIdx.x; item < a.n_items; item += gridDim.x) stage_pair2d_item<N, TT, NPREV, LIM>(a, g, item);
+    int item = blockIdx.x;
+    if (item >= a.n_items) return;
+    pair2d_issue<N, TT, NPREV>(a, item, 0);
+    for (int buf = 0; item < a.n_items; item += gridDim.x, buf ^= 1) {
+        const int next = item + int(gridDim.x);
+        if (next < a.n_items) {
+            pair2d_issue<N, TT, NPREV>(a, next, buf ^ 1);
+            cp_async_wait_1();
+        } else {
+            cp_async_wait_all();
+        }
+        stage_pair2d_item<N, TT, NPREV, LIM>(a, g, item, buf);
+    }
 }
 
 }  // namespace amrb
