@@ -74,6 +74,8 @@ def _lib_handle():
             lib.orc_max_speed.argtypes = [vp, vp]
             lib.orc_limited_slope.restype = C.c_double
             lib.orc_limited_slope.argtypes = [C.c_int, C.c_double, C.c_double]
+            lib.orc_cell_faces.restype = None
+            lib.orc_cell_faces.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, vp, vp]
             lib.orc_weno5.restype = C.c_double
             lib.orc_weno5.argtypes = [C.c_double] * 5
             lib.orc_face_flux.restype = None
@@ -123,6 +125,15 @@ def limited_slope(limiter: int, a: float, b: float) -> float:
     """The MUSCL slope limiter (0 minmod, 1 MC, 2 van Leer) on one pair of
     one-sided differences."""
     return float(_lib_handle().orc_limited_slope(int(limiter), float(a), float(b)))
+
+
+def cell_faces(limiter: int, wm: float, w0: float, wp: float):
+    """(minus, plus): the values of cell w0 at its left and right faces from
+    its neighbours (limiters 0 minmod, 1 MC, 2 van Leer, 4 Koren, 5 WENO3,
+    6 first-order upwind)."""
+    lo, hi = C.c_double(), C.c_double()
+    _lib_handle().orc_cell_faces(int(limiter), float(wm), float(w0), float(wp), C.byref(lo), C.byref(hi))
+    return lo.value, hi.value
 
 
 def weno5(a, b, c, d, e) -> float:

@@ -56,7 +56,8 @@ typedef struct {
     int bc_type[6];        /* 0 periodic/none, 1 Dirichlet, 2 Neumann, 3 Dirichlet from bc_data */
     double bc_val[6][8];
     int limiter;           /* face reconstruction (Sec. 3.2 list): 0 minmod, 1 MC, 2 van Leer
-                              (MUSCL slopes), 3 WENO5 (needs ng >= 3) */
+                              (MUSCL slopes), 3 WENO5 (needs ng >= 3), 4 Koren,
+                              5 WENO3, 6 first-order upwind */
     int flux;              /* 0 Rusanov, 1 HLL (Sec. 3.2 list), both with Einfeldt speeds */
     double gravity[3];     /* g of the source term S = (0, rho g, rho g.u) (Sec. 4.2) */
     int diagonal;          /* 1: also fill edge and corner ghost cells that a
@@ -943,8 +944,64 @@ static double weno5(double a, double b, double c, double d, double e)
     return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
 }
 
+/* Koren's limiter (Koren 1993), phi(r) = max(0, min(2r, (1 + 2r) / 3, 2)),
+ * applied to the upwind difference: the face value right of a cell whose
+ * left (upwind) and right differences are a and b is w + a phi(b / a) / 2,
+ * and a phi(b / a) is 0 when ab <= 0, else sign(a) min(2|b|, (|a| + 2|b|) / 3,
+ * 2|a|).  The face value left of the cell mirrors it: w - b phi(a / b) / 2. */
+static double koren(double a, double b)
+{
+    if (!(a * b > 0.0)) return 0.0;
+    double m = 2.0 * fabs(b);
+    double t = (fabs(a) + 2.0 * fabs(b)) / 3.0;
+    if (t < m) m = t;
+    if (2.0 * fabs(a) < m) m = 2.0 * fabs(a);
+    return a > 0.0 ? m : -m;
+}
+
+/* WENO3 value at the face right of cell c from cells c-1, c, c+1 (the
+ * three-point member of the Jiang & Shu family): candidates q0 = -a/2 +
+ * 3b/2 on {c-1, c} and q1 = (b + c)/2 on {c, c+1}, smoothness (b - a)^2 and
+ * (c - b)^2, linear weights 1/3 and 2/3 over (eps + beta)^2, eps = 1e-6.  The
+ * value at the face left of the cell takes the three cells in reverse order. */
+static double weno3(double a, double b, double c)
+{
+    double q0 = -0.5 * a + 1.5 * b;
+    double q1 = 0.5 * b + 0.5 * c;
+    double b0 = (b - a) * (b - a), b1 = (c - b) * (c - b);
+    const double eps = 1e-6;
+    double a0 = (1.0 / 3.0) / ((eps + b0) * (eps + b0));
+    double a1 = (2.0 / 3.0) / ((eps + b1) * (eps + b1));
+    return (a0 * q0 + a1 * q1) / (a0 + a1);
+}
+
+/* The values of a cell w0 at its left (minus) and right (plus) faces along
+ * one dimension from its neighbours wm, wp (Sec. 3.2 reconstruction with two
+ * ghost layers): MUSCL w0 -/+ slope / 2 with the limited slope (minmod, MC,
+ * van Leer), Koren's asymmetric limiter, WENO3, or first-order upwind
+ * (the cell value itself, limiter 6). */
+static void cell_faces(int lim, double wm, double w0, double wp, double *minus, double *plus)
+{
+    double a = w0 - wm, b = wp - w0;
+    if (lim == 6) {
+        *minus = w0;
+        *plus = w0;
+    } else if (lim == 4) {
+        *plus = w0 + 0.5 * koren(a, b);
+        *minus = w0 - 0.5 * koren(b, a);
+    } else if (lim == 5) {
+        *plus = weno3(wm, w0, wp);
+        *minus = weno3(wp, w0, wm);
+    } else {
+        double s = 0.5 * limited_slope(lim, a, b);
+        *plus = w0 + s;
+        *minus = w0 - s;
+    }
+}
+
 /* test hooks: the limiter and the face flux on given values */
 double orc_limited_slope(int lim, double a, double b) { return limited_slope(lim, a, b); }
+void orc_cell_faces(int lim, double wm, double w0, double wp, double *minus, double *plus) { cell_faces(lim, wm, w0, wp, minus, plus); }
 double orc_weno5(double a, double b, double c, double d, double e) { return weno5(a, b, c, d, e); }
 void orc_face_flux(const orc_params *p, int n, const double *wL, const double *wR, double *F) { face_flux(p, n, wL, wR, F); }
 
@@ -1025,8 +1082,11 @@ int orc_stage(const orc_mesh *m, const double *ud, double *uo, int nprev,
                                 wL[v] = weno5(wm3[v], wm2[v], wm1[v], w0[v], w1[v]);
                                 wR[v] = weno5(w2[v], w1[v], w0[v], wm1[v], wm2[v]);
                             } else {
-                                wL[v] = wm1[v] + 0.5 * limited_slope(p->limiter, wm1[v] - wm2[v], w0[v] - wm1[v]);
-                                wR[v] = w0[v] - 0.5 * limited_slope(p->limiter, w0[v] - wm1[v], w1[v] - w0[v]);
+                                double lo, hi;
+                                cell_faces(p->limiter, wm2[v], wm1[v], w0[v], &lo, &hi);
+                                wL[v] = hi;     /* right face of cell fp-1 */
+                                cell_faces(p->limiter, wm1[v], w0[v], w1[v], &lo, &hi);
+                                wR[v] = lo;     /* left face of cell fp */
                             }
                         }
                         if (nonphysical(p, wL) || nonphysical(p, wR)) bad = 1;

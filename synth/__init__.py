@@ -47,7 +47,8 @@ class MeshSpec:
     cfl: float = 0.5
     bc_type: Sequence[int] = (0, 0, 0, 0, 0, 0)
     bc_val: Sequence[Sequence[float]] = tuple(tuple(0.0 for _ in range(8)) for _ in range(6))
-    limiter: int = 0          # 0 minmod, 1 MC, 2 van Leer (MUSCL slopes), 3 WENO5 (ng >= 3)
+    limiter: int = 0          # 0 minmod, 1 MC, 2 van Leer (MUSCL slopes), 3 WENO5 (ng >= 3),
+                              # 4 Koren, 5 WENO3, 6 first-order upwind
     flux: int = 0             # 0 Rusanov, 1 HLL
     gravity: Sequence[float] = (0.0, 0.0, 0.0)   # source term S = (0, rho g, rho g.u)
     diagonal_ghosts: int = 0  # 1: also fill edge/corner ghosts held by same-level leaves
