@@ -130,9 +130,18 @@ typedef enum { AMR_PHYS_EULER = 0, AMR_PHYS_ADVECTION = 1 } amr_physics;
  * layers); the slope of a cell from its one-sided differences a, b: minmod =
  * Eq. 1 with theta = 1; MC (monotonized central) = Eq. 1 with theta = 2; van
  * Leer = 2ab / (a + b) when ab > 0, else 0; face values w -/+ slope / 2.
+ * Koren: the right face w + a phi(b/a) / 2, the left face w - b phi(a/b) / 2,
+ * phi(r) = max(0, min(2r, (1 + 2r) / 3, 2)).  WENO3: candidates -a/2 + 3b/2
+ * and (b + c)/2, weights (1/3, 2/3) / (1e-6 + beta)^2.  Upwind: first order
+ * (face values = cell values; this library still needs n_ghost >= 2).
  * WENO5 (Jiang & Shu, weights (1/10, 6/10, 3/10) / (1e-6 + beta)^2) from
- * five cells on each side: needs n_ghost >= 3 and ignores halo gathering. */
-typedef enum { AMR_LIM_MINMOD = 0, AMR_LIM_MC = 1, AMR_LIM_VANLEER = 2, AMR_LIM_WENO5 = 3 } amr_limiter;
+ * five cells on each side: needs n_ghost >= 3 and ignores halo gathering.
+ * The FP32 pair kernels take minmod, MC and van Leer; the others run in the
+ * per-cell kernel. */
+typedef enum {
+    AMR_LIM_MINMOD = 0, AMR_LIM_MC = 1, AMR_LIM_VANLEER = 2, AMR_LIM_WENO5 = 3,
+    AMR_LIM_KOREN = 4, AMR_LIM_WENO3 = 5, AMR_LIM_UPWIND = 6
+} amr_limiter;
 
 /* Numerical fluxes of Sec. 3.2, both with Einfeldt's signal speeds
  * u_roe -/+ d (Sec. 3.5): Rusanov (local Lax-Friedrichs, a = |u_roe| + d)

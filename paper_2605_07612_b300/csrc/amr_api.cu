@@ -145,7 +145,7 @@ amr_status validate(const amr_config *c, std::string &why) {
     if (c->max_level < 0 || c->max_level >= kMaxLevels) return bad("max_level must be 0..12");
     if (c->max_blocks < 1 || c->n_states < 1) return bad("max_blocks and n_states must be >= 1");
     if (c->precision != 32 && c->precision != 64) return bad("precision must be 32 or 64");
-    if (c->limiter < AMR_LIM_MINMOD || c->limiter > AMR_LIM_WENO5) return bad("unknown limiter");
+    if (c->limiter < AMR_LIM_MINMOD || c->limiter > AMR_LIM_UPWIND) return bad("unknown limiter");
     if (c->limiter == AMR_LIM_WENO5 && c->n_ghost < 3) return bad("WENO5 needs n_ghost >= 3");
     if (c->flux < AMR_FLUX_RUSANOV || c->flux > AMR_FLUX_HLL) return bad("unknown flux");
     if (!(c->gamma > 1.0) || !(c->cfl > 0.0)) return bad("gamma must be > 1 and cfl > 0");
@@ -209,8 +209,9 @@ amr_status launch_stage(amr_forest *f, const StageArgs<real> &a, cudaStream_t st
         return fail(f, AMR_EINVAL, "the advection stage needs n_ghost 2 or 3 (got %d)", NG);
     }
     if constexpr (std::is_same<real, float>::value) {
-        // the pair kernels implement the Rusanov flux only
-        if (NG == 2 && !f->scalar_stage && a.flux == AMR_FLUX_RUSANOV) {
+        // the pair kernels implement the Rusanov flux and the MUSCL slopes only
+        if (NG == 2 && !f->scalar_stage && a.flux == AMR_FLUX_RUSANOV &&
+            (a.limiter == AMR_LIM_MINMOD || a.limiter == AMR_LIM_MC || a.limiter == AMR_LIM_VANLEER)) {
             if (N == 8) return launch_stage_pair<D, 8>(f, a, st);
             if (N == 16) return launch_stage_pair<D, 16>(f, a, st);
             if (N == 32) return launch_stage_pair<D, 32>(f, a, st);
@@ -999,7 +1000,7 @@ amr_status amr_autotune(amr_forest *f, int *choice, double *best_ms, amr_stream 
     struct Cand { bool scalar; int ipc; bool pers; int tile; };
     std::vector<Cand> cands;
     const bool pair_ok = f->cfg.precision == 32 && f->cfg.n_ghost == 2 && f->cfg.flux == AMR_FLUX_RUSANOV &&
-                         f->cfg.limiter != AMR_LIM_WENO5 && f->cfg.physics == AMR_PHYS_EULER;
+                         f->cfg.limiter <= AMR_LIM_VANLEER && f->cfg.physics == AMR_PHYS_EULER;
     std::vector<std::pair<bool, int>> kernels;   // (per-cell kernel, pair tile)
     if (pair_ok) {
         kernels.push_back({false, 0});
@@ -1054,7 +1055,7 @@ amr_status amr_set_launch_shape(amr_forest *f, int choice) {
     const int tile8 = choice / 1000, scalar = (choice % 1000) / 100, ipc = choice % 100;
     if (tile8 > 1 || scalar > 1 || ipc > 64 || (tile8 && scalar)) return AMR_EINVAL;
     const bool pair_ok = f->cfg.precision == 32 && f->cfg.n_ghost == 2 && f->cfg.flux == AMR_FLUX_RUSANOV &&
-                         f->cfg.limiter != AMR_LIM_WENO5 && f->cfg.physics == AMR_PHYS_EULER;
+                         f->cfg.limiter <= AMR_LIM_VANLEER && f->cfg.physics == AMR_PHYS_EULER;
     if (tile8 && (!pair_ok || f->cfg.block_n <= 8)) return fail(f, AMR_EINVAL, "8 x 8 tiles need an FP32 pair kernel and blocks above 8 cells a side");
     f->scalar_stage = scalar == 1;
     f->pair_tile = tile8 ? 8 : 0;

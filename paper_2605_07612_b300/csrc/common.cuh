@@ -49,6 +49,54 @@ __device__ __forceinline__ T limited_slope(int lim, T a, T b) {
     return a > T(0) ? m : -m;
 }
 
+// Koren's limiter (Koren 1993) on the upwind difference a with the downwind
+// difference b: a phi(b / a), phi(r) = max(0, min(2r, (1 + 2r) / 3, 2)), i.e.
+// sign(a) min(2|b|, (|a| + 2|b|) / 3, 2|a|) when ab > 0, else 0.
+template <class T>
+__device__ __forceinline__ T koren_slope(T a, T b) {
+    if (!(a * b > T(0))) return T(0);
+    T m = fabs(T(2) * b);
+    m = fmin(m, (fabs(a) + T(2) * fabs(b)) / T(3));
+    m = fmin(m, fabs(T(2) * a));
+    return a > T(0) ? m : -m;
+}
+
+// WENO3 value at the face right of cell b from cells a, b, c: candidates
+// -a/2 + 3b/2 and (b + c)/2, smoothness (b - a)^2 and (c - b)^2, linear
+// weights 1/3 and 2/3 over (1e-6 + beta)^2 (Jiang & Shu).
+template <class T>
+__device__ __forceinline__ T weno3_face(T a, T b, T c) {
+    const T q0 = T(-0.5) * a + T(1.5) * b;
+    const T q1 = T(0.5) * b + T(0.5) * c;
+    const T b0 = (b - a) * (b - a), b1 = (c - b) * (c - b);
+    const T e0 = T(1e-6) + b0, e1 = T(1e-6) + b1;
+    const T a0 = T(1.0 / 3.0) / (e0 * e0), a1 = T(2.0 / 3.0) / (e1 * e1);
+    return (a0 * q0 + a1 * q1) / (a0 + a1);
+}
+
+// Values of cell w0 at its left (lo) and right (hi) faces along one
+// dimension from its neighbours wm, wp (two ghost layers): MUSCL w0 -/+
+// slope / 2 with the limited slope (0 minmod, 1 MC, 2 van Leer), Koren's
+// limiter (4), WENO3 (5) or first-order upwind (6, the cell value).
+template <class T>
+__device__ __forceinline__ void cell_faces(int lim, T wm, T w0, T wp, T &lo, T &hi) {
+    const T a = w0 - wm, b = wp - w0;
+    if (lim == 6) {
+        lo = w0;
+        hi = w0;
+    } else if (lim == 4) {
+        hi = w0 + T(0.5) * koren_slope<T>(a, b);
+        lo = w0 - T(0.5) * koren_slope<T>(b, a);
+    } else if (lim == 5) {
+        hi = weno3_face<T>(wm, w0, wp);
+        lo = weno3_face<T>(wp, w0, wm);
+    } else {
+        const T hs = T(0.5) * limited_slope<T>(lim, a, b);
+        lo = w0 - hs;
+        hi = w0 + hs;
+    }
+}
+
 // Geometry of one forest as seen by the kernels.  A forest holds one or
 // more independent mesh instances; cell sizes are looked up by geometry
 // class gc = instance * kMaxLevels + level in device tables [gc][3].

@@ -450,8 +450,8 @@ __device__ __forceinline__ void stage_item(const StageArgs<real> &a, const Geom 
 #pragma unroll
             for (int v = 0; v < V; ++v) {
                 const real w0 = pl[v * PL + c], wm = pl[v * PL + c - st], wp = pl[v * PL + c + st];
-                const real hs = real(0.5) * limited_slope<real>(lim, w0 - wm, wp - w0);
-                const real lo = w0 - hs, hi = w0 + hs;
+                real lo, hi;
+                cell_faces<real>(lim, wm, w0, wp, lo, hi);
                 if (E::positive_var(v)) bad |= !(lo > real(0)) || !(hi > real(0));
                 FSm[(dir * V + v) * NFS + qq] = lo;
                 FSp[(dir * V + v) * NFS + qq] = hi;
@@ -466,9 +466,7 @@ __device__ __forceinline__ void stage_item(const StageArgs<real> &a, const Geom 
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             const real w0 = p1[v * PL + c], wm = p0[v * PL + c], wp = p2[v * PL + c];
-            const real hs = real(0.5) * limited_slope<real>(lim, w0 - wm, wp - w0);
-            zm[v] = w0 - hs;
-            zp[v] = w0 + hs;
+            cell_faces<real>(lim, wm, w0, wp, zm[v], zp[v]);
         }
         nonphys |= E::nonphys(zm) || E::nonphys(zp);
     };

@@ -38,7 +38,7 @@ def run(f, u, n, scheme="heun", **kw):
 
 
 @pytest.mark.parametrize("ndim", [2, 3])
-@pytest.mark.parametrize("limiter,flux", [(2, 0), (0, 1), (1, 0)])
+@pytest.mark.parametrize("limiter,flux", [(2, 0), (0, 1), (1, 0), (4, 0), (5, 1), (6, 0)])
 @pytest.mark.parametrize("gather", [False, True])
 def test_advection_fp64_amr_matches_oracle(ndim, limiter, flux, gather):
     sp, rounds = refined(ndim, 16 if ndim == 2 else 8, limiter, flux, velocity=(1.0, -0.6, 0.8))

@@ -582,13 +582,13 @@ def test_rk_scheme_needs_enough_slots():
         f.step(1, scheme="rk4")
 
 
-LIMFLUX = [(2, 0), (1, 1), (2, 1), (0, 1)]
+LIMFLUX = [(2, 0), (1, 1), (2, 1), (0, 1), (4, 0), (5, 1), (6, 0), (4, 1)]
 
 
 @pytest.mark.parametrize("limiter,flux", LIMFLUX)
 @pytest.mark.parametrize("dim", [2, 3])
 def test_limiters_and_hll_fp64_match_oracle(limiter, flux, dim):
-    """MC and van Leer slope limiters and the HLL flux (Sec. 3.2) on 3-level
+    """MC, van Leer, Koren, WENO3 and upwind reconstructions and the HLL flux (Sec. 3.2) on 3-level
     AMR meshes, FP64 GPU against the oracle (relative L1 <= 1e-12)."""
     base = SPEC_2D_AMR if dim == 2 else SPEC_3D_AMR
     sp = synth.MeshSpec(**base, limiter=limiter, flux=flux)
@@ -603,7 +603,7 @@ def test_limiters_and_hll_fp64_match_oracle(limiter, flux, dim):
     assert rel_l1(got, ref, sp).max() <= 1e-12
 
 
-@pytest.mark.parametrize("limiter,flux", [(2, 1), (1, 0), (2, 0)])
+@pytest.mark.parametrize("limiter,flux", [(2, 1), (1, 0), (2, 0), (4, 0), (5, 0), (6, 1)])
 def test_limiters_and_hll_fp32_uniform_3d(limiter, flux):
     """FP32, 16^3 blocks (the pair kernel takes MC and van Leer with Rusanov,
     the per-cell kernel HLL), gathered halos and a CUDA graph: relative L1
@@ -622,7 +622,7 @@ def test_limiters_and_hll_fp32_uniform_3d(limiter, flux):
 
 
 def test_unknown_limiter_or_flux_is_rejected():
-    for kw in (dict(limiter=3), dict(flux=2), dict(limiter=-1)):
+    for kw in (dict(limiter=3), dict(flux=2), dict(limiter=-1), dict(limiter=7)):
         sp = synth.MeshSpec(ndim=2, N=8, ng=2, ntrees=(2, 2, 1), **kw)
         with pytest.raises(amr.AmrError):
             amr.Forest(sp, 0)
