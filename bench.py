@@ -673,9 +673,24 @@ def run_ncu_case(which="stage"):
     """For ncu captures (default launch shape, no autotuning, no timing).
     stage: one Heun step of the headline workload -- exactly two stage
     launches.  ghost: one full ghost fill (rounds 1 and 2, no halo gathering)
-    of a 3-level FP32 mesh -- exactly two ghost launches."""
+    of a 3-level FP32 mesh -- exactly two ghost launches.  stage2d: one Heun
+    step of a uniform periodic 4096^2 mesh of 16^2 blocks (65,536 blocks,
+    420 MB per state slot, above L2), FP32, Kelvin-Helmholtz -- exactly two
+    2D stage launches."""
     import torch
     import paper_2605_07612_b300 as amr
+    if which == "stage2d":
+        sp = synth.MeshSpec(ndim=2, N=16, ng=2, ntrees=(256, 256, 1))
+        f = amr.Forest(sp, 0, precision=32)
+        lev, g = f.blocks()
+        f.set_state(0, synth.kelvin_helmholtz(sp, lev, g).astype(np.float32))
+        f.compute_dt(0)
+        f.step(1, use_graph=False, gather=True)
+        torch.cuda.synchronize()
+        st = f.sync_status()
+        if st != amr.AMR_OK:
+            raise SystemExit("device status %d" % st)
+        return
     if which == "ghost":
         sp = ghost_case_spec()
         f = amr.Forest(sp, 0, max_blocks=8000, precision=32)
@@ -760,9 +775,9 @@ def main():
     ap.add_argument("--workload", default="uniform", choices=["uniform", "amr_static", "adaptive"],
                     help="uniform: the headline line; the others print their own JSON line")
     ap.add_argument("--adaptive-steps", type=int, default=500)
-    ap.add_argument("--ncu-case", nargs="?", const="stage", default=None, choices=["stage", "ghost"],
-                    help="run one Heun step of the headline workload (stage) or one ghost fill of a 3-level mesh "
-                         "(ghost) and exit, for ncu captures")
+    ap.add_argument("--ncu-case", nargs="?", const="stage", default=None, choices=["stage", "ghost", "stage2d"],
+                    help="run one Heun step of the headline workload (stage), one ghost fill of a 3-level mesh "
+                         "(ghost) or one Heun step of a uniform 4096^2 2D mesh (stage2d) and exit, for ncu captures")
     args = ap.parse_args()
     if args.ncu_case:
         run_ncu_case(args.ncu_case)
