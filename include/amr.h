@@ -67,9 +67,15 @@ typedef enum {
     AMR_GHOST_F2C = 1,     /* fine -> coarse: restriction into the coarse block's ghosts */
     AMR_GHOST_BC = 2,      /* physical boundary */
     AMR_GHOST_C2F = 3,     /* coarse -> fine: limited prolongation, second round */
-    AMR_GHOST_DIAG = 4     /* edge / corner region held by a same-level leaf: copy
+    AMR_GHOST_DIAG = 4,    /* edge / corner region held by a same-level leaf: copy
                               (only with amr_config.diagonal_ghosts); face =
                               (dx+1) + 3 (dy+1) + 9 (dz+1) for the direction */
+    AMR_GHOST_DIAG_F2C = 5,/* edge / corner region covered by finer leaves:
+                              restriction, round 1, one entry per fine leaf;
+                              offset = its half along a 3D edge (else 0) */
+    AMR_GHOST_DIAG_C2F = 6 /* edge / corner region inside a coarser leaf: limited
+                              prolongation, round 2; offset bit d = parity of the
+                              same-size box's coordinate along dimension d */
 } amr_ghost_kind;
 
 typedef struct amr_forest amr_forest;
@@ -108,10 +114,12 @@ typedef struct {
     int flux;              /* amr_flux: numerical flux (Sec. 3.2) */
     double gravity[3];     /* g of the source term S = (0, rho g, rho g.u) added to
                               every stage (Sec. 4.2); zero: no source */
-    int diagonal_ghosts;   /* 1: the pattern also copies edge and corner ghost
-                              regions held by same-level leaves (AMR_GHOST_DIAG
-                              entries, round 1); the paper and the stage kernels
-                              use face ghosts only (Sec. 2.1) */
+    int diagonal_ghosts;   /* 1: the pattern also fills the edge and corner ghost
+                              regions inside the domain (AMR_GHOST_DIAG copies and
+                              AMR_GHOST_DIAG_F2C restrictions in round 1,
+                              AMR_GHOST_DIAG_C2F prolongations in round 2); the
+                              paper and the stage kernels use face ghosts only
+                              (Sec. 2.1) */
     int physics;           /* amr_physics: equations of the stage (Sec. 3.4, 3.5) */
     double velocity[3];    /* uniform velocity of the scalar advection equation
                               (Eq. 13); ignored for Euler */

@@ -60,15 +60,16 @@ typedef struct {
                               5 WENO3, 6 first-order upwind */
     int flux;              /* 0 Rusanov, 1 HLL (Sec. 3.2 list), both with Einfeldt speeds */
     double gravity[3];     /* g of the source term S = (0, rho g, rho g.u) (Sec. 4.2) */
-    int diagonal;          /* 1: also fill edge and corner ghost cells that a
-                              same-level leaf holds (the paper fills face ghosts only) */
+    int diagonal;          /* 1: also fill edge and corner ghost cells (copy from a
+                              same-level leaf, restriction from finer, prolongation
+                              from coarser ones); the paper fills face ghosts only */
     int physics;           /* 0 Euler gas dynamics (Sec. 3.5), 1 scalar advection
                               (Sec. 3.4, Eq. 13; nvar = 1) */
     double velocity[3];    /* the uniform advection velocity v of Eq. 13 */
 } orc_params;
 
 enum { BC_NONE = 0, BC_DIRICHLET = 1, BC_NEUMANN = 2, BC_DATA = 3 };
-enum { K_SRL = 0, K_F2C = 1, K_BC = 2, K_C2F = 3, K_DIAG = 4 };
+enum { K_SRL = 0, K_F2C = 1, K_BC = 2, K_C2F = 3, K_DIAG = 4, K_DIAG_F2C = 5, K_DIAG_C2F = 6 };
 
 /* a diagonal (edge or corner) direction (dx, dy, dz), two or three of them
  * nonzero, as the code (dx+1) + 3 (dy+1) + 9 (dz+1) */
@@ -537,8 +538,12 @@ int64_t orc_pattern(const orc_mesh *m, int32_t *out, int64_t cap)
                 }
             } else { free(E); return -1; }
         }
-        /* edge and corner regions: an entry when a same-level leaf holds the
-         * whole region (other levels and non-periodic boundaries stay unfilled) */
+        /* edge and corner regions held by leaves of one level: a same-level
+         * leaf (copy), a coarser leaf (prolongation, offset = parity of the
+         * same-size box's coordinates, bit d for dimension d) or finer leaves
+         * (restriction, one entry per fine leaf, offset = its position along
+         * a 3D edge); regions reaching outside a non-periodic domain stay
+         * unfilled */
         if (p->diagonal) {
             for (int dz = (D == 3 ? -1 : 0); dz <= (D == 3 ? 1 : 0); dz++)
                 for (int dy = -1; dy <= 1; dy++)
@@ -546,7 +551,8 @@ int64_t orc_pattern(const orc_mesh *m, int32_t *out, int64_t cap)
                         int dir[3] = {dx, dy, dz};
                         int nz = (dx != 0) + (dy != 0) + (dz != 0);
                         if (nz < 2) continue;
-                        int src = -2, ok = 1, ext[3], lo[3];
+                        int ok = 1, ext[3], lo[3], srcs[2], nsrc = 0, slev = -100;
+                        int64_t C0[3] = {0, 0, 0};
                         for (int d = 0; d < 3; d++) {
                             lo[d] = dir[d] < 0 ? -ng : (dir[d] > 0 ? N : 0);
                             ext[d] = d >= D ? 1 : (dir[d] != 0 ? ng : N);
@@ -560,14 +566,39 @@ int64_t orc_pattern(const orc_mesh *m, int32_t *out, int64_t cap)
                                     int fl;
                                     if (!global_cell(m, b, x, C)) { ok = 0; break; }
                                     int sblk = locate_cell(m, lev, C, &fl);
-                                    if (sblk < 0 || fl != lev) { ok = 0; break; }
-                                    if (src == -2) src = sblk;
-                                    else if (src != sblk) { ok = 0; break; }
+                                    if (sblk < 0 || fl < lev - 1 || fl > lev + 1) { ok = 0; break; }
+                                    if (slev == -100) {
+                                        slev = fl;
+                                        for (int d = 0; d < 3; d++) C0[d] = C[d];
+                                    } else if (slev != fl) { ok = 0; break; }
+                                    int seen = 0;
+                                    for (int q = 0; q < nsrc; q++) if (srcs[q] == sblk) seen = 1;
+                                    if (!seen) {
+                                        if (nsrc == 2) { ok = 0; break; }
+                                        srcs[nsrc++] = sblk;
+                                    }
                                 }
-                        if (!ok || src < 0) continue;
-                        if (ne >= maxe) { free(E); return -1; }
-                        entry_t e = {K_DIAG, diag_code(dir), b, src, 0, 0};
-                        E[ne++] = e;
+                        if (!ok || nsrc == 0) continue;
+                        if (ne + 2 > maxe) { free(E); return -1; }
+                        if (slev == lev) {
+                            if (nsrc != 1) continue;
+                            entry_t e = {K_DIAG, diag_code(dir), b, srcs[0], 0, 0};
+                            E[ne++] = e;
+                        } else if (slev == lev - 1) {
+                            if (nsrc != 1) continue;
+                            int off = 0;
+                            for (int d = 0; d < D; d++) off |= (int)((C0[d] / N) & 1) << d;
+                            entry_t e = {K_DIAG_C2F, diag_code(dir), b, srcs[0], off, 0};
+                            E[ne++] = e;
+                        } else {
+                            int ed = -1;     /* the edge dimension of a 3D edge */
+                            for (int d = 0; d < D; d++) if (dir[d] == 0) ed = d;
+                            for (int q = 0; q < nsrc; q++) {
+                                int off = ed < 0 ? 0 : (int)(m->g[3 * srcs[q] + ed] - 2 * m->g[3 * b + ed]);
+                                entry_t e = {K_DIAG_F2C, diag_code(dir), b, srcs[q], off, 0};
+                                E[ne++] = e;
+                            }
+                        }
                     }
         }
     }
@@ -723,9 +754,12 @@ static int fill_round(const orc_mesh *m, double *u, const double *bc_data, int r
     return err ? -1 : 0;
 }
 
-/* Edge and corner ghost cells held by a same-level leaf: copies (only when
- * the mesh asks for them). */
-static void fill_diagonal(const orc_mesh *m, double *u)
+/* Edge and corner ghost cells (only when the mesh asks for them), one cell
+ * at a time from the leaf that holds the cell's centre: round 1 copies from a
+ * same-level leaf and restricts from a finer one, round 2 prolongs from a
+ * coarser one (the limited prolongation reads the coarse leaf's interior and
+ * round-1 face ghosts).  Cells outside a non-periodic domain stay unfilled. */
+static void fill_diagonal(const orc_mesh *m, double *u, int round)
 {
     const orc_params *p = &m->p;
     int N = p->N, ng = p->ng, D = p->ndim, V = p->nvar;
@@ -744,10 +778,23 @@ static void fill_diagonal(const orc_mesh *m, double *u)
                     int fl;
                     if (!global_cell(m, b, x, C)) continue;
                     int s = locate_cell(m, lev, C, &fl);
-                    if (s < 0 || fl != lev) continue;
-                    int xs[3] = {0, 0, 0};
-                    for (int d = 0; d < D; d++) xs[d] = (int)(C[d] - m->g[3 * s + d] * N);
-                    for (int v = 0; v < V; v++) u[atv(p, b, v, x)] = u[atv(p, s, v, xs)];
+                    if (s < 0) continue;
+                    if (fl == lev && round == 1) {
+                        int xs[3] = {0, 0, 0};
+                        for (int d = 0; d < D; d++) xs[d] = (int)(C[d] - m->g[3 * s + d] * N);
+                        for (int v = 0; v < V; v++) u[atv(p, b, v, x)] = u[atv(p, s, v, xs)];
+                    } else if (fl == lev + 1 && round == 1) {
+                        int base[3] = {0, 0, 0};
+                        for (int d = 0; d < D; d++) base[d] = (int)(2 * C[d] - m->g[3 * s + d] * N);
+                        for (int v = 0; v < V; v++) u[atv(p, b, v, x)] = restrict_cell(p, u, s, v, base);
+                    } else if (fl == lev - 1 && round == 2) {
+                        int xc[3] = {0, 0, 0}, sub[3] = {0, 0, 0};
+                        for (int d = 0; d < D; d++) {
+                            xc[d] = (int)((C[d] >> 1) - m->g[3 * s + d] * N);
+                            sub[d] = (int)(C[d] & 1);
+                        }
+                        for (int v = 0; v < V; v++) u[atv(p, b, v, x)] = prolong_cell(p, u, s, v, xc, sub);
+                    }
                 }
     }
 }
@@ -755,8 +802,10 @@ static void fill_diagonal(const orc_mesh *m, double *u)
 int orc_fill_ghosts(const orc_mesh *m, double *u, const double *bc_data)
 {
     if (fill_round(m, u, bc_data, 1)) return -1;
-    if (m->p.diagonal) fill_diagonal(m, u);
-    return fill_round(m, u, bc_data, 2);
+    if (m->p.diagonal) fill_diagonal(m, u, 1);
+    if (fill_round(m, u, bc_data, 2)) return -1;
+    if (m->p.diagonal) fill_diagonal(m, u, 2);
+    return 0;
 }
 
 /* ------------------------------------------------------------------------ */

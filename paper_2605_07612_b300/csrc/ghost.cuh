@@ -5,7 +5,8 @@
 // entries, whose limited prolongation reads round-1 ghosts of the coarse
 // block (the tangential neighbours at the face edge and the ghost layer
 // facing the fine block).  Face ghost cells only (Sec. 2.1), unless the mesh
-// asks for edge and corner cells held by same-level leaves (DIAG entries).
+// asks for edge and corner cells (DIAG entries: copies and restrictions in
+// round 1, prolongations in round 2).
 #pragma once
 
 #include "common.cuh"
@@ -118,14 +119,21 @@ __global__ void __launch_bounds__(256) k_ghost(GhostArgs<real> a, Geom g) {
     const Entry e = a.list[warp];
     real *dstb = a.u + int64_t(e.dst) * g.bstride;
     const real *srcb = e.src >= 0 ? a.u + int64_t(e.src) * g.bstride : nullptr;
-    if (e.kind == KIND_DIAG) {
+    if (e.kind == KIND_DIAG || e.kind == KIND_DIAG_F2C || e.kind == KIND_DIAG_C2F) {
         // edge / corner region in direction (dx, dy, dz): ghost box of the
-        // block, copied from the same-level neighbour's interior
+        // block, copied from a same-level neighbour's interior, restricted
+        // from a finer neighbour (half the box along a 3D edge per neighbour),
+        // or prolonged from a coarser one (offset bit d: parity of the
+        // same-size box along d, i.e. which half of the coarse block)
         const int dir[3] = {e.face % 3 - 1, (e.face / 3) % 3 - 1, e.face / 9 - 1};
         int lo[3] = {0, 0, 0}, ext[3] = {1, 1, 1};
         for (int d = 0; d < D; ++d) {
             lo[d] = dir[d] < 0 ? -NG : (dir[d] > 0 ? N : 0);
             ext[d] = dir[d] != 0 ? NG : N;
+            if (e.kind == KIND_DIAG_F2C && dir[d] == 0) {
+                lo[d] = e.offset * (N / 2);
+                ext[d] = N / 2;
+            }
         }
         const int ncells = ext[0] * ext[1] * ext[2];
         for (int idx = lane; idx < ncells * g.V; idx += 32) {
@@ -136,9 +144,30 @@ __global__ void __launch_bounds__(256) k_ghost(GhostArgs<real> a, Geom g) {
             c /= ext[0];
             x[1] = lo[1] + c % ext[1];
             x[2] = lo[2] + c / ext[1];
-            const int y0 = x[0] - dir[0] * N, y1 = x[1] - dir[1] * N, y2 = D == 3 ? x[2] - dir[2] * N : 0;
-            dstb[int64_t(v) * g.ncell + cell_index<real>(g, x[0], x[1], x[2])] =
-                srcb[int64_t(v) * g.ncell + cell_index<real>(g, y0, y1, y2)];
+            real val;
+            if (e.kind == KIND_DIAG) {
+                const int y0 = x[0] - dir[0] * N, y1 = x[1] - dir[1] * N, y2 = D == 3 ? x[2] - dir[2] * N : 0;
+                val = srcb[int64_t(v) * g.ncell + cell_index<real>(g, y0, y1, y2)];
+            } else if (e.kind == KIND_DIAG_F2C) {
+                // lower corner of the 2^D fine cells: across the region's
+                // faces as for a face restriction, along an edge shifted by
+                // the fine block's position
+                int y[3] = {0, 0, 0};
+                for (int d = 0; d < D; ++d)
+                    y[d] = dir[d] < 0 ? 2 * x[d] + N : (dir[d] > 0 ? 2 * (x[d] - N) : 2 * x[d] - e.offset * N);
+                val = restrict_at<real, D>(srcb + int64_t(v) * g.ncell, g, y[0], y[1], y[2]);
+            } else {
+                // the cell's position in the same-size box, then the coarse
+                // cell and the sub-cell
+                int y[3] = {0, 0, 0}, sb[3] = {0, 0, 0};
+                for (int d = 0; d < D; ++d) {
+                    const int r = x[d] - dir[d] * N;
+                    y[d] = ((e.offset >> d) & 1) * (N / 2) + (r >> 1);
+                    sb[d] = r & 1;
+                }
+                val = prolong_at<real, D>(srcb + int64_t(v) * g.ncell, g, y[0], y[1], y[2], sb[0], sb[1], sb[2]);
+            }
+            dstb[int64_t(v) * g.ncell + cell_index<real>(g, x[0], x[1], x[2])] = val;
         }
         return;
     }

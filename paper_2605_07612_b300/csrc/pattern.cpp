@@ -63,7 +63,8 @@ bool build_pattern(const std::vector<const Forest *> &inst, const std::vector<in
                 P.entries.push_back({KIND_F2C, f, b, o0 + fs, o, 0});
             }
         }
-        // edge and corner regions held by a same-level leaf
+        // edge and corner regions: held by a same-level leaf, part of a
+        // coarser leaf, or covered by the finer children that touch A
         if (diagonal)
             for (int dz = (D == 3 ? -1 : 0); dz <= (D == 3 ? 1 : 0); ++dz)
                 for (int dy = -1; dy <= 1; ++dy)
@@ -77,8 +78,32 @@ bool build_pattern(const std::vector<const Forest *> &inst, const std::vector<in
                             inside = F.wrap(d, A.lev, q[d]);
                         }
                         if (!inside) continue;
+                        const int code = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
                         const int s = F.find(A.lev, q[0], q[1], q[2]);
-                        if (s >= 0) P.entries.push_back({KIND_DIAG, (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1), b, o0 + s, 0, 0});
+                        if (s >= 0) {
+                            P.entries.push_back({KIND_DIAG, code, b, o0 + s, 0, 0});
+                            continue;
+                        }
+                        if (A.lev > 0) {
+                            const int c = F.find(A.lev - 1, q[0] >> 1, q[1] >> 1, D == 3 ? q[2] >> 1 : 0);
+                            if (c >= 0) {
+                                int par = 0;
+                                for (int d = 0; d < D; ++d) par |= int(q[d] & 1) << d;
+                                P.entries.push_back({KIND_DIAG_C2F, code, b, o0 + c, par, 0});
+                                continue;
+                            }
+                        }
+                        // finer: the children of q touching A (two along a 3D edge)
+                        int ed = -1;
+                        for (int d = 0; d < D; ++d)
+                            if (dir[d] == 0) ed = d;
+                        for (int o = 0; o < (ed >= 0 ? 2 : 1); ++o) {
+                            int64_t ch[3] = {0, 0, 0};
+                            for (int d = 0; d < D; ++d)
+                                ch[d] = dir[d] != 0 ? 2 * q[d] + (dir[d] < 0 ? 1 : 0) : 2 * q[d] + o;
+                            const int fs = A.lev < G.max_level ? F.find(A.lev + 1, ch[0], ch[1], ch[2]) : -1;
+                            if (fs >= 0) P.entries.push_back({KIND_DIAG_F2C, code, b, o0 + fs, o, 0});
+                        }
                     }
     }
     }
@@ -106,13 +131,16 @@ bool build_pattern(const std::vector<const Forest *> &inst, const std::vector<in
         P.info[b].fixmask = 0;
         for (int f = 0; f < 6; ++f) P.info[b].bslot[f] = P.info[b].nbr[f] = -1;
     }
+    // blocks whose face ghosts a prolongation reads (their same-level face
+    // ghosts are filled in gather mode too)
     std::vector<char> c2f_src(size_t(nb), 0);
     for (const Entry &e : P.entries)
-        if (e.kind == KIND_C2F) c2f_src[size_t(e.src)] = 1;
+        if (e.kind == KIND_C2F || e.kind == KIND_DIAG_C2F) c2f_src[size_t(e.src)] = 1;
     for (const Entry &e : P.entries) {
-        (e.kind == KIND_C2F ? P.round2 : P.round1).push_back(e);
+        const bool r2 = e.kind == KIND_C2F || e.kind == KIND_DIAG_C2F;
+        (r2 ? P.round2 : P.round1).push_back(e);
         if (e.kind == KIND_SRL) P.info[e.dst].nbr[e.face] = e.src;
-        if (e.kind != KIND_C2F && (e.kind != KIND_SRL || c2f_src[size_t(e.dst)])) P.round1_gather.push_back(e);
+        if (!r2 && (e.kind != KIND_SRL || c2f_src[size_t(e.dst)])) P.round1_gather.push_back(e);
         if (e.kind == KIND_F2C || e.kind == KIND_C2F) {
             int32_t &slot = P.info[e.dst].bslot[e.face];
             if (slot < 0) slot = P.n_slots++;

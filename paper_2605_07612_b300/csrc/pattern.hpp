@@ -14,7 +14,7 @@ namespace amrb {
 
 constexpr int kMaxLevels = 13;   // levels 0..12 per instance
 
-enum : int32_t { KIND_SRL = 0, KIND_F2C = 1, KIND_BC = 2, KIND_C2F = 3, KIND_DIAG = 4 };
+enum : int32_t { KIND_SRL = 0, KIND_F2C = 1, KIND_BC = 2, KIND_C2F = 3, KIND_DIAG = 4, KIND_DIAG_F2C = 5, KIND_DIAG_C2F = 6 };
 
 struct Entry {
     int32_t kind, face, dst, src, offset, aux;
@@ -56,9 +56,12 @@ struct Pattern {
 // are numbered consecutively (instance i owns blocks offset[i] ..
 // offset[i] + n_i - 1).  Returns false (with a message) if some face has no
 // valid neighbour configuration (2:1 balance broken).
-// diagonal: also emit a KIND_DIAG entry (face = direction code (dx+1) +
-// 3 (dy+1) + 9 (dz+1)) for every edge / corner ghost region that a
-// same-level leaf holds; executed in round 1.
+// diagonal: also emit entries for the edge / corner ghost regions (face =
+// direction code (dx+1) + 3 (dy+1) + 9 (dz+1)) inside the domain: KIND_DIAG
+// (a same-level leaf holds the region: copy, round 1), KIND_DIAG_F2C (finer
+// leaves: restriction, round 1, one entry per fine leaf, offset = its
+// position along a 3D edge), KIND_DIAG_C2F (a coarser leaf: prolongation,
+// round 2, offset bit d = parity of the same-size box along dimension d).
 bool build_pattern(const std::vector<const Forest *> &inst, const std::vector<int64_t> &offset, Pattern &out,
                    std::string &err, bool diagonal = false);
 

@@ -312,3 +312,98 @@ def test_diagonal_pattern_entries_geometry(ndim, seed):
                             expect.add(((dx + 1) + 3 * (dy + 1) + 9 * (dz + 1), b, s))
         got = {(int(e[1]), int(e[2]), int(e[3])) for e in pat[pat[:, 0] == 4]}
         assert got == expect
+
+
+@pytest.mark.parametrize("ndim,seed", [(2, 1), (2, 4), (3, 2)])
+def test_diagonal_pattern_entries_across_levels(ndim, seed):
+    """Edge and corner regions next to other levels: a coarser leaf holding
+    the same-size box q gives one prolongation entry (kind 6) whose offset
+    holds the parity of q per dimension; a refined q gives one restriction
+    entry (kind 5) per child touching the block, offset = the child's
+    position along a 3D edge."""
+    import dataclasses
+    sp, seq = random_meshes(ndim, seed, rounds=3)
+    spd = dataclasses.replace(sp, diagonal_ghosts=1)
+    m = oracle.Mesh(spd, 1)
+    seen = {5: 0, 6: 0}
+    for _, flags, _ in seq:
+        m = m.adapt(flags)
+        lev, g = m.blocks()
+        pat = m.pattern()
+        where = {(int(a), *map(int, b)): i for i, (a, b) in enumerate(zip(lev, g))}
+        exp5, exp6 = set(), set()
+        for b in range(m.n):
+            L = int(lev[b])
+            for dz in ((-1, 0, 1) if ndim == 3 else (0,)):
+                for dy in (-1, 0, 1):
+                    for dx in (-1, 0, 1):
+                        dirs = (dx, dy, dz)
+                        if sum(x != 0 for x in dirs) < 2:
+                            continue
+                        q, ok = [], True
+                        for d in range(ndim):
+                            E = spd.ntrees[d] << L
+                            x = int(g[b][d]) + dirs[d]
+                            if x < 0 or x >= E:
+                                if not spd.periodic[d]:
+                                    ok = False
+                                    break
+                                x %= E
+                            q.append(x)
+                        if not ok or (L, *(q + [0] * (3 - ndim))) in where:
+                            continue
+                        code = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)
+                        par = where.get((L - 1, *([c >> 1 for c in q] + [0] * (3 - ndim))))
+                        if L > 0 and par is not None:
+                            exp6.add((code, b, par, sum((q[d] & 1) << d for d in range(ndim))))
+                            continue
+                        ed = [d for d in range(ndim) if dirs[d] == 0]
+                        for o in ((0, 1) if ed else (0,)):
+                            ch = [2 * q[d] + (1 if dirs[d] < 0 else 0) if dirs[d] != 0 else 2 * q[d] + o
+                                  for d in range(ndim)]
+                            s = where[(L + 1, *(ch + [0] * (3 - ndim)))]
+                            exp5.add((code, b, s, o))
+        got5 = {tuple(int(x) for x in e[[1, 2, 3, 4]]) for e in pat[pat[:, 0] == 5]}
+        got6 = {tuple(int(x) for x in e[[1, 2, 3, 4]]) for e in pat[pat[:, 0] == 6]}
+        assert got5 == exp5 and got6 == exp6
+        seen[5] += len(got5)
+        seen[6] += len(got6)
+    assert seen[5] > 0 and seen[6] > 0
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_diagonal_ghosts_exact_for_linear_field_across_levels(ndim):
+    """With edge and corner ghosts on, every edge and corner ghost cell
+    inside the domain holds the linear field phi = x + 2y (+3z) at its
+    centre up to rounding, whether it was copied, restricted from finer
+    leaves or prolonged from a coarser one (the prolongation reads the
+    coarse leaf's face ghosts, some of them boundary values): both transfers
+    are exact for linear data, as in the test of Sec. 4.3."""
+    sp = synth.MeshSpec(ndim=ndim, N=8, ng=2, ntrees=(2, 2, 2)[:ndim] + (1,) * (3 - ndim), periodic=(0, 0, 0),
+                        max_level=3, bc_type=(3,) * 6, diagonal_ghosts=1)
+    m = oracle.Mesh(sp, 0)
+    for _ in range(3):
+        lev, g = m.blocks()
+        m = m.adapt(synth.point_flags(sp, lev, g, (0.3, 0.62, 0.45)[:ndim] + (0.0,) * (3 - ndim), 3))
+    lev, g = m.blocks()
+    pat = m.pattern()
+    kinds = set(pat[:, 0].tolist())
+    assert {4, 5, 6} <= kinds
+    u = synth.linear_field(sp, lev, g)
+    bce = [(f, d) for k, f, d, s, o, a in pat if k == oracle.KIND_BC]
+    m.fill_ghosts(u, synth.linear_face_values(sp, lev, g, bce))
+    exact = synth.linear_field(sp, lev, g, with_ghosts=True)
+    X = synth.cell_centres(sp, lev, g)
+    inside = np.ones_like(X[0], dtype=bool)
+    for d in range(ndim):
+        inside &= (X[d] > 0.0) & (X[d] < 1.0)
+    S, N, ng = sp.side, sp.N, sp.ng
+    idx = np.indices((S,) * ndim) - ng
+    nout = sum(((idx[d] < 0) | (idx[d] >= N)).astype(int) for d in range(ndim))
+    sel = (nout >= 2)[None] & inside
+    U = u.reshape((m.n, sp.nvar) + (S,) * ndim)
+    Ex = exact.reshape((m.n, sp.nvar) + (S,) * ndim)
+    diff = np.abs(U - Ex)
+    err = diff[np.broadcast_to(sel[:, None], diff.shape)].max() / np.abs(Ex).max()
+    assert err < 4.5e-16 * 8, err
+    assert sel.sum() > 0
