@@ -13,6 +13,8 @@
 // weights (1/10, 6/10, 3/10) / (1e-6 + beta_k)^2 normalised.
 #pragma once
 
+#include <type_traits>
+
 #include "stage.cuh"
 
 namespace amrb {
@@ -30,10 +32,19 @@ __device__ __forceinline__ real weno5_face(real a, real b, real c, real d, real 
     const real b1 = k * t1 * t1 + real(0.25) * u1 * u1;
     const real b2 = k * t2 * t2 + real(0.25) * u2 * u2;
     const real eps = real(1e-6);
-    const real a0 = real(0.1) / ((eps + b0) * (eps + b0));
-    const real a1 = real(0.6) / ((eps + b1) * (eps + b1));
-    const real a2 = real(0.3) / ((eps + b2) * (eps + b2));
-    return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+    if constexpr (std::is_same<real, double>::value) {
+        // one division instead of four: numerator and denominator times
+        // s0 s1 s2, s_k = (eps + beta_k)^2 (FP64 divisions are slow here; the
+        // products stay far inside the FP64 range for any finite state)
+        const real s0 = (eps + b0) * (eps + b0), s1 = (eps + b1) * (eps + b1), s2 = (eps + b2) * (eps + b2);
+        const real a0 = real(0.1) * (s1 * s2), a1 = real(0.6) * (s0 * s2), a2 = real(0.3) * (s0 * s1);
+        return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+    } else {
+        const real a0 = real(0.1) / ((eps + b0) * (eps + b0));
+        const real a1 = real(0.6) / ((eps + b1) * (eps + b1));
+        const real a2 = real(0.3) / ((eps + b2) * (eps + b2));
+        return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+    }
 }
 
 // primitives of all S^D cells of every block: prim[b][v][cell] (Euler only:
@@ -54,10 +65,19 @@ __global__ void __launch_bounds__(256) k_weno_prim(const real *__restrict__ u, r
     }
 }
 
-// Faces of a block: q < D (N+1) N^(D-1); direction n = q / nf, then face
-// position fp along n (fastest) and tangential index t = t0 + N t1 (t0 along
-// the lower tangential dimension).  flux[b][n][v][fp + (N+1) t].
-// blockIdx.x = block, blockIdx.y = chunk of 256 faces.
+// Faces of a block: q < D (N+1) N^(D-1); direction n = q / nf, and within
+// a direction the faces are numbered with x fastest whatever the normal, so
+// that a warp's loads and stores run along rows: r = fp + (N+1)(y + N z)
+// for x-faces, x + N (fp + (N+1) z) for y-faces, x + N (y + N fp) for
+// z-faces (fp: face position along the normal, between cells fp-1 and fp).
+// flux[b][n][v][r].  blockIdx.x = block, blockIdx.y = chunk of 256 faces.
+template <int D>
+__device__ __forceinline__ int weno_face_index(int n, int fp, const int *x, int N) {
+    if (n == 0) return fp + (N + 1) * (x[1] + N * x[2]);
+    if (n == 1) return x[0] + N * (fp + (N + 1) * x[2]);
+    return x[0] + N * (x[1] + N * fp);
+}
+
 template <class real, int D, int PH>
 __global__ void __launch_bounds__(256) k_weno_flux(const real *__restrict__ prim, real *__restrict__ flux,
                                                    const BlockInfo *__restrict__ info, real *bflux, Geom g,
@@ -71,16 +91,28 @@ __global__ void __launch_bounds__(256) k_weno_flux(const real *__restrict__ prim
     const int q = blockIdx.y * blockDim.x + threadIdx.x;
     if (q >= D * nf) return;
     const int n = q / nf, r = q - n * nf;
-    const int fp = r % (N + 1), t = r / (N + 1);
-    const int t0 = t % N, t1 = t / N;
-    const int td0 = n == 0 ? 1 : 0, td1 = n == 2 ? 1 : 2;   // tangential dimensions (lower first)
+    int x[3] = {0, 0, 0}, fp;
+    if (n == 0) {
+        fp = r % (N + 1);
+        const int t = r / (N + 1);
+        x[1] = t % N;
+        x[2] = t / N;
+    } else if (n == 1) {
+        x[0] = r % N;
+        const int t = r / N;
+        fp = t % (N + 1);
+        x[2] = t / (N + 1);
+    } else {
+        x[0] = r % N;
+        x[1] = (r / N) % N;
+        fp = r / (N * N);
+    }
+    // tangential index of the face (lower tangential dimension first)
+    const int t = n == 0 ? x[1] + N * x[2] : (n == 1 ? x[0] + N * x[2] : x[0] + N * x[1]);
     const real *pb = prim + int64_t(b) * g.bstride;
     auto cell = [&](int along) -> int64_t {
-        int x[3] = {0, 0, 0};
-        x[n] = along;
-        x[td0] = t0;
-        if (D == 3) x[td1] = t1;
-        return (int64_t(D == 3 ? x[2] + NG : 0) * S + (x[1] + NG)) * S + (x[0] + NG);
+        const int i = n == 0 ? along : x[0], j = n == 1 ? along : x[1], k = n == 2 ? along : x[2];
+        return (int64_t(D == 3 ? k + NG : 0) * S + (j + NG)) * S + (i + NG);
     };
     real wL[V], wR[V], F[V];
     bool bad = false;
@@ -137,10 +169,9 @@ __global__ void __launch_bounds__(256) k_weno_update(StageArgs<real> a, const re
             real r = real(0);
 #pragma unroll
             for (int n = 0; n < D; ++n) {
-                const int t0 = x[n == 0 ? 1 : 0], t1 = D == 3 ? x[n == 2 ? 1 : 2] : 0;
-                const int idx = x[n] + (N + 1) * (t0 + N * t1);
+                const int lo = weno_face_index<D>(n, x[n], x, N), hi = weno_face_index<D>(n, x[n] + 1, x, N);
                 const real *fv = fb + (int64_t(n) * V + v) * nf;
-                r += (fv[idx] - fv[idx + 1]) * real(g.inv_dx[3 * gc + n]);
+                r += (fv[lo] - fv[hi]) * real(g.inv_dx[3 * gc + n]);
             }
             if constexpr (E::EULER) {
                 if (a.gravity_on && v > 0) {
