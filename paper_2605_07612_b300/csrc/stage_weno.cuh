@@ -40,10 +40,12 @@ __device__ __forceinline__ real weno5_face(real a, real b, real c, real d, real 
         const real a0 = real(0.1) * (s1 * s2), a1 = real(0.6) * (s0 * s2), a2 = real(0.3) * (s0 * s1);
         return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
     } else {
-        const real a0 = real(0.1) / ((eps + b0) * (eps + b0));
-        const real a1 = real(0.6) / ((eps + b1) * (eps + b1));
-        const real a2 = real(0.3) / ((eps + b2) * (eps + b2));
-        return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+        // FP32: approximate reciprocals (the weights are normalised, so their
+        // few-ulp error stays a few ulp of the face value)
+        const real a0 = real(0.1) * rcp_ftz((eps + b0) * (eps + b0));
+        const real a1 = real(0.6) * rcp_ftz((eps + b1) * (eps + b1));
+        const real a2 = real(0.3) * rcp_ftz((eps + b2) * (eps + b2));
+        return (a0 * q0 + a1 * q1 + a2 * q2) * rcp_ftz(a0 + a1 + a2);
     }
 }
 
