@@ -197,6 +197,14 @@ template <class real, int D>
 amr_status launch_stage(amr_forest *f, const StageArgs<real> &a, cudaStream_t st) {
     const int N = f->cfg.block_n, NG = f->cfg.n_ghost;
     if (f->cfg.physics == AMR_PHYS_ADVECTION) {
+        if constexpr (std::is_same<real, float>::value) {
+            // FP32 block kernel: MUSCL slopes, 8^3 / 16^3 (3D) and 8^2 .. 32^2 (2D) blocks
+            if (NG == 2 && !f->scalar_stage && a.limiter <= AMR_LIM_VANLEER) {
+                if (N == 8) return launch_adv_pair<D, 8>(f, a, st);
+                if (N == 16) return launch_adv_pair<D, 16>(f, a, st);
+                if (D == 2 && N == 32) return launch_adv_pair<D, 32>(f, a, st);
+            }
+        }
 #define AMR_ADV_CASE(n_, g_) \
     if (N == n_ && NG == g_) return launch_stage_t<real, D, n_, g_, true, 1>(f, a, st);
         AMR_ADV_CASE(8, 2)
@@ -996,16 +1004,22 @@ amr_status amr_autotune(amr_forest *f, int *choice, double *best_ms, amr_stream 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // candidates: blocks (tiles) per CTA 1, 2, 4 or a persistent grid, for
     // each kernel / staging tile: the FP32 pair kernel (2D or 3D) with tile
-    // 16 and, for blocks above 8 cells a side, tile 8; the per-cell kernel
+    // 16 and, for blocks above 8 cells a side, tile 8, or the FP32 advection
+    // block kernel; the per-cell kernel
     struct Cand { bool scalar; int ipc; bool pers; int tile; };
     std::vector<Cand> cands;
     const bool pair_ok = f->cfg.precision == 32 && f->cfg.n_ghost == 2 && f->cfg.flux == AMR_FLUX_RUSANOV &&
                          f->cfg.limiter <= AMR_LIM_VANLEER && f->cfg.physics == AMR_PHYS_EULER;
+    // the FP32 advection block kernel (any flux: both are upwind)
+    const bool adv_ok = f->cfg.precision == 32 && f->cfg.n_ghost == 2 && f->cfg.limiter <= AMR_LIM_VANLEER &&
+                        f->cfg.physics == AMR_PHYS_ADVECTION &&
+                        (f->cfg.block_n <= 16 || (f->cfg.ndim == 2 && f->cfg.block_n == 32));
     std::vector<std::pair<bool, int>> kernels;   // (per-cell kernel, pair tile)
     if (pair_ok) {
         kernels.push_back({false, 0});
         if (f->cfg.block_n > 8) kernels.push_back({false, 8});
     }
+    if (adv_ok) kernels.push_back({false, 0});
     kernels.push_back({true, 0});
     for (const auto &k : kernels) {
         for (int ipc : {1, 2, 4}) cands.push_back({k.first, ipc, false, k.second});

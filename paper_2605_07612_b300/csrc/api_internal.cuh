@@ -94,6 +94,8 @@ template <class real, int D, int N, int NG, bool GEN, int PH>
 amr_status launch_stage_t(amr_forest *f, const StageArgs<real> &a, cudaStream_t st);
 template <int D, int N>
 amr_status launch_stage_pair(amr_forest *f, const StageArgs<float> &a, cudaStream_t st);
+template <int D, int N>
+amr_status launch_adv_pair(amr_forest *f, const StageArgs<float> &a, cudaStream_t st);
 template <class real, int D, int PH>
 amr_status launch_weno(amr_forest *f, const StageArgs<real> &a, real *prim, real *flux, cudaStream_t st);
 

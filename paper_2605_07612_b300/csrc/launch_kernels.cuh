@@ -8,6 +8,7 @@
 #include "stage.cuh"
 #include "stage_pair.cuh"
 #include "stage_pair2d.cuh"
+#include "stage_adv.cuh"
 #include "stage_weno.cuh"
 
 namespace amrb {
@@ -131,6 +132,38 @@ amr_status launch_stage_pair(amr_forest *f, const StageArgs<float> &a, cudaStrea
         if (f->pair_tile == 8) return launch_stage_pair_t<D, N, 8>(f, a, st);
     }
     return launch_stage_pair_t<D, N, (N < 16 ? N : 16)>(f, a, st);
+}
+
+// FP32 scalar advection with a MUSCL slope limiter: one CTA per block (the
+// block and its face halo in shared memory)
+template <int D, int N, int LIM>
+amr_status launch_adv_pair_l(amr_forest *f, const StageArgs<float> &a, cudaStream_t st) {
+    using Sh = AdvShape<D, N>;
+    static bool attr_done = false;
+    const size_t smem = Sh::smem_bytes();
+    if (!attr_done) {
+        CU(cudaFuncSetAttribute(k_adv_pair<D, N, LIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        attr_done = true;
+    }
+    const int64_t items = nblocks(f);
+    if (items > 0) {
+        StageArgs<float> b = a;
+        b.n_items = int(items);
+        int occ = 1;
+        if (f->persistent) CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_adv_pair<D, N, LIM>, Sh::NT, smem));
+        const int64_t grid = stage_grid(f, items, occ);
+        k_adv_pair<D, N, LIM><<<unsigned(grid), Sh::NT, smem, st>>>(b, f->geom);
+        ++f->launches;
+    }
+    CU(cudaGetLastError());
+    return AMR_OK;
+}
+
+template <int D, int N>
+amr_status launch_adv_pair(amr_forest *f, const StageArgs<float> &a, cudaStream_t st) {
+    if (a.limiter == AMR_LIM_MC) return launch_adv_pair_l<D, N, 1>(f, a, st);
+    if (a.limiter == AMR_LIM_VANLEER) return launch_adv_pair_l<D, N, 2>(f, a, st);
+    return launch_adv_pair_l<D, N, 0>(f, a, st);
 }
 
 // WENO5 stage: primitives (Euler only), face fluxes, update (three or two
