@@ -31,8 +31,9 @@ struct AdvShape {
     static constexpr size_t smem_bytes() { return sizeof(float) * (D == 3 ? size_t(S) * PL : size_t(PL)); }
 };
 
+// 3D 16^3: 6 CTAs of 256 threads per SM (32 KB of shared memory each)
 template <int D, int N, int LIM>
-__global__ void __launch_bounds__(AdvShape<D, N>::NT) k_adv_pair(StageArgs<float> a, Geom g) {
+__global__ void __launch_bounds__(AdvShape<D, N>::NT, (D == 3 && N == 16 ? 6 : 1)) k_adv_pair(StageArgs<float> a, Geom g) {
     using Sh = AdvShape<D, N>;
     constexpr int NG = Sh::NG, S = Sh::S, PL = Sh::PL, NT = Sh::NT, KZ = Sh::KZ;
     constexpr int64_t NCELL = D == 3 ? int64_t(S) * S * S : int64_t(S) * S;
