@@ -144,8 +144,8 @@ typedef enum { AMR_PHYS_EULER = 0, AMR_PHYS_ADVECTION = 1 } amr_physics;
  * (face values = cell values; this library still needs n_ghost >= 2).
  * WENO5 (Jiang & Shu, weights (1/10, 6/10, 3/10) / (1e-6 + beta)^2) from
  * five cells on each side: needs n_ghost >= 3 and ignores halo gathering.
- * The FP32 pair kernels take minmod, MC and van Leer; the others run in the
- * per-cell kernel. */
+ * The FP32 pair kernels take minmod, MC and van Leer (with either flux); the
+ * others run in the per-cell kernel. */
 typedef enum {
     AMR_LIM_MINMOD = 0, AMR_LIM_MC = 1, AMR_LIM_VANLEER = 2, AMR_LIM_WENO5 = 3,
     AMR_LIM_KOREN = 4, AMR_LIM_WENO3 = 5, AMR_LIM_UPWIND = 6

@@ -17,6 +17,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libamr_b300.so")
 UNITS = ["amr_api.cu", "forest.cpp", "pattern.cpp", "noalloc.cu", "mlp.cu", "inst_ghost.cu", "inst_stage_f32_2d.cu",
          "inst_stage_f32_3d.cu", "inst_stage_f64_2d.cu", "inst_stage_f64_3d.cu", "inst_stage_pair.cu", "inst_stage_pair2d.cu",
+         "inst_stage_pair_hll.cu", "inst_stage_pair2d_hll.cu",
          "inst_stage_f32_2d_gen.cu", "inst_stage_f32_3d_gen.cu", "inst_stage_f64_2d_gen.cu", "inst_stage_f64_3d_gen.cu",
          "inst_weno.cu", "inst_stage_adv.cu"]
 HEADERS = ["common.cuh", "ghost.cuh", "stage.cuh", "stage_pair.cuh", "misc.cuh", "mlp.cuh", "forest.hpp", "pattern.hpp",

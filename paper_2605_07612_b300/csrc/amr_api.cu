@@ -217,12 +217,13 @@ amr_status launch_stage(amr_forest *f, const StageArgs<real> &a, cudaStream_t st
         return fail(f, AMR_EINVAL, "the advection stage needs n_ghost 2 or 3 (got %d)", NG);
     }
     if constexpr (std::is_same<real, float>::value) {
-        // the pair kernels implement the Rusanov flux and the MUSCL slopes only
-        if (NG == 2 && !f->scalar_stage && a.flux == AMR_FLUX_RUSANOV &&
+        // the pair kernels implement the MUSCL slopes with the Rusanov or HLL flux
+        if (NG == 2 && !f->scalar_stage &&
             (a.limiter == AMR_LIM_MINMOD || a.limiter == AMR_LIM_MC || a.limiter == AMR_LIM_VANLEER)) {
-            if (N == 8) return launch_stage_pair<D, 8>(f, a, st);
-            if (N == 16) return launch_stage_pair<D, 16>(f, a, st);
-            if (N == 32) return launch_stage_pair<D, 32>(f, a, st);
+            const bool hll = a.flux == AMR_FLUX_HLL;
+            if (N == 8) return hll ? launch_stage_pair<D, 8, 1>(f, a, st) : launch_stage_pair<D, 8, 0>(f, a, st);
+            if (N == 16) return hll ? launch_stage_pair<D, 16, 1>(f, a, st) : launch_stage_pair<D, 16, 0>(f, a, st);
+            if (N == 32) return hll ? launch_stage_pair<D, 32, 1>(f, a, st) : launch_stage_pair<D, 32, 0>(f, a, st);
         }
     }
     const bool gen = a.limiter != AMR_LIM_MINMOD || a.flux != AMR_FLUX_RUSANOV;
@@ -1008,8 +1009,8 @@ amr_status amr_autotune(amr_forest *f, int *choice, double *best_ms, amr_stream 
     // block kernel; the per-cell kernel
     struct Cand { bool scalar; int ipc; bool pers; int tile; };
     std::vector<Cand> cands;
-    const bool pair_ok = f->cfg.precision == 32 && f->cfg.n_ghost == 2 && f->cfg.flux == AMR_FLUX_RUSANOV &&
-                         f->cfg.limiter <= AMR_LIM_VANLEER && f->cfg.physics == AMR_PHYS_EULER;
+    const bool pair_ok = f->cfg.precision == 32 && f->cfg.n_ghost == 2 && f->cfg.limiter <= AMR_LIM_VANLEER &&
+                         f->cfg.physics == AMR_PHYS_EULER;
     // the FP32 advection block kernel (any flux: both are upwind)
     const bool adv_ok = f->cfg.precision == 32 && f->cfg.n_ghost == 2 && f->cfg.limiter <= AMR_LIM_VANLEER &&
                         f->cfg.physics == AMR_PHYS_ADVECTION &&
@@ -1068,8 +1069,8 @@ amr_status amr_set_launch_shape(amr_forest *f, int choice) {
     if (!f || choice < 0) return AMR_EINVAL;
     const int tile8 = choice / 1000, scalar = (choice % 1000) / 100, ipc = choice % 100;
     if (tile8 > 1 || scalar > 1 || ipc > 64 || (tile8 && scalar)) return AMR_EINVAL;
-    const bool pair_ok = f->cfg.precision == 32 && f->cfg.n_ghost == 2 && f->cfg.flux == AMR_FLUX_RUSANOV &&
-                         f->cfg.limiter <= AMR_LIM_VANLEER && f->cfg.physics == AMR_PHYS_EULER;
+    const bool pair_ok = f->cfg.precision == 32 && f->cfg.n_ghost == 2 && f->cfg.limiter <= AMR_LIM_VANLEER &&
+                         f->cfg.physics == AMR_PHYS_EULER;
     if (tile8 && (!pair_ok || f->cfg.block_n <= 8)) return fail(f, AMR_EINVAL, "8 x 8 tiles need an FP32 pair kernel and blocks above 8 cells a side");
     f->scalar_stage = scalar == 1;
     f->pair_tile = tile8 ? 8 : 0;

@@ -92,7 +92,7 @@ template <class real, int D>
 amr_status launch_ghosts(amr_forest *f, int s, cudaStream_t st, bool gather);
 template <class real, int D, int N, int NG, bool GEN, int PH>
 amr_status launch_stage_t(amr_forest *f, const StageArgs<real> &a, cudaStream_t st);
-template <int D, int N>
+template <int D, int N, int FLX>
 amr_status launch_stage_pair(amr_forest *f, const StageArgs<float> &a, cudaStream_t st);
 template <int D, int N>
 amr_status launch_adv_pair(amr_forest *f, const StageArgs<float> &a, cudaStream_t st);

@@ -72,25 +72,25 @@ amr_status launch_stage_t(amr_forest *f, const StageArgs<real> &a, cudaStream_t 
 
 // FP32, two ghost layers: the packed cell-pair kernels (3D plane march, 2D
 // single plane), specialised for one and two previous states (the two stages
-// of Heun's method), for the slope limiter (minmod, MC, van Leer; Rusanov
-// flux only) and for the staging tile (16, or 8 when the autotuner picks it
+// of Heun's method), for the slope limiter (minmod, MC, van Leer), the flux
+// (Rusanov, HLL) and the staging tile (16, or 8 when the autotuner picks it
 // for blocks above 8 cells a side)
-template <int D, int N, int TT, int NPREV, int LIM>
+template <int D, int N, int TT, int NPREV, int LIM, int FLX>
 struct PairKernel;
-template <int N, int TT, int NPREV, int LIM>
-struct PairKernel<3, N, TT, NPREV, LIM> {
+template <int N, int TT, int NPREV, int LIM, int FLX>
+struct PairKernel<3, N, TT, NPREV, LIM, FLX> {
     using Sh = PairShape<N, TT>;
-    static constexpr auto fn = k_stage_pair<N, TT, NPREV, LIM>;
+    static constexpr auto fn = k_stage_pair<N, TT, NPREV, LIM, FLX>;
 };
-template <int N, int TT, int NPREV, int LIM>
-struct PairKernel<2, N, TT, NPREV, LIM> {
+template <int N, int TT, int NPREV, int LIM, int FLX>
+struct PairKernel<2, N, TT, NPREV, LIM, FLX> {
     using Sh = PairShape2D<N, TT>;
-    static constexpr auto fn = k_stage_pair2d<N, TT, NPREV, LIM>;
+    static constexpr auto fn = k_stage_pair2d<N, TT, NPREV, LIM, FLX>;
 };
 
-template <int D, int N, int TT, int NPREV, int LIM>
+template <int D, int N, int TT, int NPREV, int LIM, int FLX>
 amr_status launch_stage_pair_n(amr_forest *f, const StageArgs<float> &a, cudaStream_t st) {
-    using K = PairKernel<D, N, TT, NPREV, LIM>;
+    using K = PairKernel<D, N, TT, NPREV, LIM, FLX>;
     using Sh = typename K::Sh;
     static bool attr_done = false;
     const size_t smem = Sh::smem_bytes(NPREV);
@@ -112,26 +112,27 @@ amr_status launch_stage_pair_n(amr_forest *f, const StageArgs<float> &a, cudaStr
     return AMR_OK;
 }
 
-template <int D, int N, int TT, int LIM>
+template <int D, int N, int TT, int LIM, int FLX>
 amr_status launch_stage_pair_l(amr_forest *f, const StageArgs<float> &a, cudaStream_t st) {
-    if (a.nprev == 1) return launch_stage_pair_n<D, N, TT, 1, LIM>(f, a, st);
-    if (a.nprev == 2) return launch_stage_pair_n<D, N, TT, 2, LIM>(f, a, st);
-    return launch_stage_pair_n<D, N, TT, -1, LIM>(f, a, st);
+    if (a.nprev == 1) return launch_stage_pair_n<D, N, TT, 1, LIM, FLX>(f, a, st);
+    if (a.nprev == 2) return launch_stage_pair_n<D, N, TT, 2, LIM, FLX>(f, a, st);
+    return launch_stage_pair_n<D, N, TT, -1, LIM, FLX>(f, a, st);
 }
 
-template <int D, int N, int TT>
+template <int D, int N, int TT, int FLX>
 amr_status launch_stage_pair_t(amr_forest *f, const StageArgs<float> &a, cudaStream_t st) {
-    if (a.limiter == AMR_LIM_MC) return launch_stage_pair_l<D, N, TT, 1>(f, a, st);
-    if (a.limiter == AMR_LIM_VANLEER) return launch_stage_pair_l<D, N, TT, 2>(f, a, st);
-    return launch_stage_pair_l<D, N, TT, 0>(f, a, st);
+    if (a.limiter == AMR_LIM_MC) return launch_stage_pair_l<D, N, TT, 1, FLX>(f, a, st);
+    if (a.limiter == AMR_LIM_VANLEER) return launch_stage_pair_l<D, N, TT, 2, FLX>(f, a, st);
+    return launch_stage_pair_l<D, N, TT, 0, FLX>(f, a, st);
 }
 
-template <int D, int N>
+// FLX 0: Rusanov, 1: HLL (separate build units)
+template <int D, int N, int FLX>
 amr_status launch_stage_pair(amr_forest *f, const StageArgs<float> &a, cudaStream_t st) {
     if constexpr (N > 8) {
-        if (f->pair_tile == 8) return launch_stage_pair_t<D, N, 8>(f, a, st);
+        if (f->pair_tile == 8) return launch_stage_pair_t<D, N, 8, FLX>(f, a, st);
     }
-    return launch_stage_pair_t<D, N, (N < 16 ? N : 16)>(f, a, st);
+    return launch_stage_pair_t<D, N, (N < 16 ? N : 16), FLX>(f, a, st);
 }
 
 // FP32 scalar advection with a MUSCL slope limiter: one CTA per block (the

@@ -49,7 +49,7 @@ struct StageArgs {
     int n_items;                 // blocks x column tiles; CTAs loop over them with a grid stride
     real gamma;
     int limiter;                 // amr_limiter (the pair kernels: minmod, MC, van Leer)
-    int flux;                    // amr_flux (the pair kernels: Rusanov only)
+    int flux;                    // amr_flux (the pair kernels: Rusanov and HLL)
     int gravity_on;              // add the source S = (0, rho g, rho g.u) of u_deriv
     real grav[3];
     real vel[3];                 // advection velocity (scalar advection only)

@@ -3,7 +3,7 @@
 // are neighbours along x.  All arithmetic on such a pair runs as packed
 // two-wide FP32 instructions (add/mul/fma .f32x2 of sm_100-class GPUs), and
 // every shared- and global-memory access of a pair is one aligned 8-byte
-// access.
+// access.  The flux is Rusanov's or HLL (template parameter).
 //
 // One CTA per (block, T x T column tile), T = min(N, 16) or 8 (autotuned),
 // T*T/2 threads (128 for T = 16); thread (ip, tj) owns
@@ -118,6 +118,69 @@ __device__ __forceinline__ void pair_flux(const float2 *wL, const float2 *wR, in
     F[4] = PF::fma(nha, PF::sub(ER, EL), PF::mul(half, fe));
 }
 
+// HLL flux (Harten, Lax and van Leer) of a pair of faces with the same
+// Einfeldt estimates as pair_flux: sL = min(u_roe - d, 0), sR = max(u_roe + d,
+// 0), F = (sR F_L - sL F_R + sL sR (U_R - U_L)) / (sR - sL).
+template <int NRM>
+__device__ __forceinline__ void pair_flux_hll(const float2 *wL, const float2 *wR, int n, float gam, float gm1i, float2 *F) {
+    const int nn = NRM >= 0 ? NRM : n;
+    float2 vnL, vnR;
+    if (NRM >= 0) {
+        vnL = wL[1 + (NRM >= 0 ? NRM : 0)];
+        vnR = wR[1 + (NRM >= 0 ? NRM : 0)];
+    } else {
+        vnL = nn == 0 ? wL[1] : (nn == 1 ? wL[2] : wL[3]);
+        vnR = nn == 0 ? wR[1] : (nn == 1 ? wR[2] : wR[3]);
+    }
+    const float2 rL = wL[0], rR = wR[0], pL = wL[4], pR = wR[4];
+    const float2 qL = PF::rsqrt(rL), qR = PF::rsqrt(rR);
+    const float2 sqL = PF::mul(rL, qL), sqR = PF::mul(rR, qR);
+    const float2 iL = PF::mul(qL, qL), iR = PF::mul(qR, qR);
+    const float2 inv = PF::rcp(PF::add(sqL, sqR));
+    const float2 g2 = PF::sp(gam);
+    const float2 c2L = PF::mul(PF::mul(g2, pL), iL), c2R = PF::mul(PF::mul(g2, pR), iR);
+    const float2 uroe = PF::mul(PF::fma(sqL, vnL, PF::mul(sqR, vnR)), inv);
+    const float2 du = PF::sub(vnR, vnL);
+    const float2 h = PF::mul(PF::mul(PF::mul(sqL, sqR), PF::mul(inv, inv)), PF::sp(0.5f));
+    const float2 d2 = PF::fma(PF::mul(h, du), du, PF::mul(PF::fma(sqL, c2L, PF::mul(sqR, c2R)), inv));
+    const float2 d = PF::mul(d2, PF::rsqrt(d2));
+    const float2 lo = PF::sub(uroe, d), hi = PF::add(uroe, d);
+    const float2 sL = make_float2(fminf(lo.x, 0.f), fminf(lo.y, 0.f));
+    const float2 sR = make_float2(fmaxf(hi.x, 0.f), fmaxf(hi.y, 0.f));
+    const float2 iw = PF::rcp(PF::sub(sR, sL)), sLR = PF::mul(sL, sR);
+    float2 v2L = PF::mul(wL[1], wL[1]), v2R = PF::mul(wR[1], wR[1]);
+    v2L = PF::fma(wL[2], wL[2], v2L);
+    v2R = PF::fma(wR[2], wR[2], v2R);
+    v2L = PF::fma(wL[3], wL[3], v2L);
+    v2R = PF::fma(wR[3], wR[3], v2R);
+    const float2 half = PF::sp(0.5f);
+    const float2 EL = PF::fma(pL, PF::sp(gm1i), PF::mul(PF::mul(half, rL), v2L));
+    const float2 ER = PF::fma(pR, PF::sp(gm1i), PF::mul(PF::mul(half, rR), v2R));
+    const float2 mL = PF::mul(rL, vnL), mR = PF::mul(rR, vnR);
+    // (sR fL - sL fR + sL sR jump) / (sR - sL)
+    auto comb = [&](float2 fL, float2 fR, float2 jump) {
+        return PF::mul(PF::fma(sLR, jump, PF::sub(PF::mul(sR, fL), PF::mul(sL, fR))), iw);
+    };
+    F[0] = comb(mL, mR, PF::sub(rR, rL));
+#pragma unroll
+    for (int d3 = 0; d3 < 3; ++d3) {
+        float2 fL = PF::mul(mL, wL[1 + d3]), fR = PF::mul(mR, wR[1 + d3]);
+        if (d3 == nn) {
+            fL = PF::add(fL, pL);
+            fR = PF::add(fR, pR);
+        }
+        F[1 + d3] = comb(fL, fR, PF::sub(PF::mul(rR, wR[1 + d3]), PF::mul(rL, wL[1 + d3])));
+    }
+    F[4] = comb(PF::mul(PF::add(EL, pL), vnL), PF::mul(PF::add(ER, pR), vnR), PF::sub(ER, EL));
+}
+
+// the pair flux of the configured scheme (FLX 0 Rusanov, 1 HLL)
+template <int FLX, int NRM>
+__device__ __forceinline__ void pair_face_flux(const float2 *wL, const float2 *wR, int n, float gam, float gm1i, float2 *F) {
+    if constexpr (FLX == 1) pair_flux_hll<NRM>(wL, wR, n, gam, gm1i, F);
+    else pair_flux<NRM>(wL, wR, n, gam, gm1i, F);
+}
+
 // Half of the limited slope of a pair of cells from their one-sided
 // differences a (left) and b (right): LIM 1 monotonized central (Eq. 1 with
 // theta = 2: sign min(|a|, |b|, |a + b| / 4) when the signs agree), LIM 2 van
@@ -209,8 +272,8 @@ struct PairShape {
 };
 
 // NPREV >= 0: the number of previous states, fixed at compile time (Heun's two
-// stages use 1 and 2); -1 reads it from the arguments.
-template <int N, int TT, int NPREV, int LIM>
+// stages use 1 and 2); -1 reads it from the arguments.  FLX: 0 Rusanov, 1 HLL.
+template <int N, int TT, int NPREV, int LIM, int FLX>
 __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const Geom &g, int item) {
     using Sh = PairShape<N, TT>;
     constexpr int T = Sh::T, NG = Sh::NG, S = Sh::S, P = Sh::P, PL = Sh::PL, V = Sh::V, NT = Sh::NT;
@@ -390,7 +453,7 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
             const float2 A = ld2(pl, v, tj, ci - 2), B = ld2(pl, v, tj, ci), C2 = ld2(pl, v, tj, ci + 2);
             pair_states<LIM>(A, make_float2(A.y, B.x), B, make_float2(B.y, C2.x), wL[v], wR[v]);
         }
-        pair_flux<0>(wL, wR, 0, gam, gm1i, F);
+        pair_face_flux<FLX, 0>(wL, wR, 0, gam, gm1i, F);
 #pragma unroll
         for (int v = 0; v < V; ++v) *reinterpret_cast<float2 *>(Fx + v * NFX + tj * FXP + ci) = F[v];
         if (ci == 0 && tx0 == 0) store_bflux1(0, ty0 + tj + N * k, F[0].x, F[1].x, F[2].x, F[3].x, F[4].x);
@@ -398,7 +461,7 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
 #pragma unroll
         for (int v = 0; v < V; ++v)
             pair_states<LIM>(ld2(pl, v, tj - 2, ci), ld2(pl, v, tj - 1, ci), ld2(pl, v, tj, ci), ld2(pl, v, tj + 1, ci), wL[v], wR[v]);
-        pair_flux<1>(wL, wR, 1, gam, gm1i, F);
+        pair_face_flux<FLX, 1>(wL, wR, 1, gam, gm1i, F);
 #pragma unroll
         for (int v = 0; v < V; ++v) *reinterpret_cast<float2 *>(Fy + v * (T + 1) * T + Sh::fy(tj, ci)) = F[v];
         if (tj == 0 && ty0 == 0) store_bflux2(2, tx0 + ci + N * k, F);
@@ -420,7 +483,7 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
                     pair_cell_states<LIM>(w1, w2, w3, wR[v], zP[v]);
                 }
             }
-            pair_flux<2>(wL, wR, 2, gam, gm1i, Fz_new);
+            pair_face_flux<FLX, 2>(wL, wR, 2, gam, gm1i, Fz_new);
             if (k == N - 1) store_bflux2(5, tx0 + ci + N * (ty0 + tj), Fz_new);
         }
         // the tile's upper edge faces, both in the first warp: lanes r < T/2
@@ -437,7 +500,7 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
                 pair_states<LIM>(make_float2(b0[0], b0[po]), make_float2(b0[st], b0[st + po]),
                                  make_float2(b0[2 * st], b0[2 * st + po]), make_float2(b0[3 * st], b0[3 * st + po]), wL[v], wR[v]);
             }
-            pair_flux<-1>(wL, wR, isx ? 0 : 1, gam, gm1i, F);
+            pair_face_flux<FLX, -1>(wL, wR, isx ? 0 : 1, gam, gm1i, F);
             if (isx) {
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
@@ -587,7 +650,7 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
                 pair_cell_states<LIM>(w1, w2, w3, zm, zP[v]);
             }
         }
-        pair_flux<2>(wL, wR, 2, gam, gm1i, FzA);
+        pair_face_flux<FLX, 2>(wL, wR, 2, gam, gm1i, FzA);
         store_bflux2(4, tx0 + ci + N * (ty0 + tj), FzA);
     }
     __syncthreads();
@@ -620,9 +683,9 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
     if (__syncthreads_or(nonphys) && tid == 0) raise_status(&a.sc[0].status, 7);
 }
 
-template <int N, int TT, int NPREV, int LIM>
+template <int N, int TT, int NPREV, int LIM, int FLX>
 __global__ void __launch_bounds__(PairShape<N, TT>::NT, (TT >= 16 ? 4 : 1)) k_stage_pair(StageArgs<float> a, Geom g) {
-    for (int item = blockIdx.x; item < a.n_items; item += gridDim.x) stage_pair_item<N, TT, NPREV, LIM>(a, g, item);
+    for (int item = blockIdx.x; item < a.n_items; item += gridDim.x) stage_pair_item<N, TT, NPREV, LIM, FLX>(a, g, item);
 }
 
 }  // namespace amrb

@@ -55,6 +55,56 @@ __device__ __forceinline__ void pair_flux2d(const float2 *wL, const float2 *wR, 
     F[3] = PF::fma(nha, PF::sub(ER, EL), PF::mul(half, fe));
 }
 
+// HLL flux of a pair of 2D faces with the Einfeldt estimates of pair_flux2d
+template <int NRM>
+__device__ __forceinline__ void pair_flux2d_hll(const float2 *wL, const float2 *wR, int n, float gam, float gm1i, float2 *F) {
+    const int nn = NRM >= 0 ? NRM : n;
+    const float2 vnL = nn == 0 ? wL[1] : wL[2], vnR = nn == 0 ? wR[1] : wR[2];
+    const float2 rL = wL[0], rR = wR[0], pL = wL[3], pR = wR[3];
+    const float2 qL = PF::rsqrt(rL), qR = PF::rsqrt(rR);
+    const float2 sqL = PF::mul(rL, qL), sqR = PF::mul(rR, qR);
+    const float2 iL = PF::mul(qL, qL), iR = PF::mul(qR, qR);
+    const float2 inv = PF::rcp(PF::add(sqL, sqR));
+    const float2 g2 = PF::sp(gam);
+    const float2 c2L = PF::mul(PF::mul(g2, pL), iL), c2R = PF::mul(PF::mul(g2, pR), iR);
+    const float2 uroe = PF::mul(PF::fma(sqL, vnL, PF::mul(sqR, vnR)), inv);
+    const float2 du = PF::sub(vnR, vnL);
+    const float2 h = PF::mul(PF::mul(PF::mul(sqL, sqR), PF::mul(inv, inv)), PF::sp(0.5f));
+    const float2 d2 = PF::fma(PF::mul(h, du), du, PF::mul(PF::fma(sqL, c2L, PF::mul(sqR, c2R)), inv));
+    const float2 d = PF::mul(d2, PF::rsqrt(d2));
+    const float2 lo = PF::sub(uroe, d), hi = PF::add(uroe, d);
+    const float2 sL = make_float2(fminf(lo.x, 0.f), fminf(lo.y, 0.f));
+    const float2 sR = make_float2(fmaxf(hi.x, 0.f), fmaxf(hi.y, 0.f));
+    const float2 iw = PF::rcp(PF::sub(sR, sL)), sLR = PF::mul(sL, sR);
+    const float2 v2L = PF::fma(wL[2], wL[2], PF::mul(wL[1], wL[1]));
+    const float2 v2R = PF::fma(wR[2], wR[2], PF::mul(wR[1], wR[1]));
+    const float2 half = PF::sp(0.5f);
+    const float2 EL = PF::fma(pL, PF::sp(gm1i), PF::mul(PF::mul(half, rL), v2L));
+    const float2 ER = PF::fma(pR, PF::sp(gm1i), PF::mul(PF::mul(half, rR), v2R));
+    const float2 mL = PF::mul(rL, vnL), mR = PF::mul(rR, vnR);
+    auto comb = [&](float2 fL, float2 fR, float2 jump) {
+        return PF::mul(PF::fma(sLR, jump, PF::sub(PF::mul(sR, fL), PF::mul(sL, fR))), iw);
+    };
+    F[0] = comb(mL, mR, PF::sub(rR, rL));
+#pragma unroll
+    for (int d2i = 0; d2i < 2; ++d2i) {
+        float2 fL = PF::mul(mL, wL[1 + d2i]), fR = PF::mul(mR, wR[1 + d2i]);
+        if (d2i == nn) {
+            fL = PF::add(fL, pL);
+            fR = PF::add(fR, pR);
+        }
+        F[1 + d2i] = comb(fL, fR, PF::sub(PF::mul(rR, wR[1 + d2i]), PF::mul(rL, wL[1 + d2i])));
+    }
+    F[3] = comb(PF::mul(PF::add(EL, pL), vnL), PF::mul(PF::add(ER, pR), vnR), PF::sub(ER, EL));
+}
+
+// the pair flux of the configured scheme (FLX 0 Rusanov, 1 HLL)
+template <int FLX, int NRM>
+__device__ __forceinline__ void pair_face_flux2d(const float2 *wL, const float2 *wR, int n, float gam, float gm1i, float2 *F) {
+    if constexpr (FLX == 1) pair_flux2d_hll<NRM>(wL, wR, n, gam, gm1i, F);
+    else pair_flux2d<NRM>(wL, wR, n, gam, gm1i, F);
+}
+
 // conservative (rho, rho u, rho v, E) -> primitive (rho, u, v, p) for a pair
 __device__ __forceinline__ void pair_prim2d(const float2 *U, float2 *w, float gam) {
     const float2 ir = PF::rcp(U[0]);
@@ -175,7 +225,7 @@ __device__ __forceinline__ void pair2d_issue(const StageArgs<float> &a, int item
 
 // One item whose copies (pair2d_issue into buffer `buf`) have arrived:
 // conversion to primitives, fluxes, update.
-template <int N, int TT, int NPREV, int LIM>
+template <int N, int TT, int NPREV, int LIM, int FLX>
 __device__ __forceinline__ void stage_pair2d_item(const StageArgs<float> &a, const Geom &g, int item, int buf) {
     using Sh = PairShape2D<N, TT>;
     constexpr int T = Sh::T, NG = Sh::NG, S = Sh::S, P = Sh::P, PL = Sh::PL, V = Sh::V, NT = Sh::NT;
@@ -265,14 +315,14 @@ __device__ __forceinline__ void stage_pair2d_item(const StageArgs<float> &a, con
             const float2 A = ld2(v, tj, ci - 2), B = ld2(v, tj, ci), C2 = ld2(v, tj, ci + 2);
             pair_states<LIM>(A, make_float2(A.y, B.x), B, make_float2(B.y, C2.x), wL[v], wR[v]);
         }
-        pair_flux2d<0>(wL, wR, 0, gam, gm1i, F);
+        pair_face_flux2d<FLX, 0>(wL, wR, 0, gam, gm1i, F);
 #pragma unroll
         for (int v = 0; v < V; ++v) *reinterpret_cast<float2 *>(Fx + v * NFX + tj * FXP + ci) = F[v];
         if (ci == 0 && tx0 == 0) store_bflux1(0, ty0 + tj, F, false);
 #pragma unroll
         for (int v = 0; v < V; ++v)
             pair_states<LIM>(ld2(v, tj - 2, ci), ld2(v, tj - 1, ci), ld2(v, tj, ci), ld2(v, tj + 1, ci), wL[v], wR[v]);
-        pair_flux2d<1>(wL, wR, 1, gam, gm1i, F);
+        pair_face_flux2d<FLX, 1>(wL, wR, 1, gam, gm1i, F);
 #pragma unroll
         for (int v = 0; v < V; ++v) *reinterpret_cast<float2 *>(Fy + v * (T + 1) * T + Sh::fy(tj, ci)) = F[v];
         if (tj == 0 && ty0 == 0) store_bflux2(2, tx0 + ci, F);
@@ -290,7 +340,7 @@ __device__ __forceinline__ void stage_pair2d_item(const StageArgs<float> &a, con
                 pair_states<LIM>(make_float2(b0[0], b0[po]), make_float2(b0[st], b0[st + po]),
                                  make_float2(b0[2 * st], b0[2 * st + po]), make_float2(b0[3 * st], b0[3 * st + po]), wL[v], wR[v]);
             }
-            pair_flux2d<-1>(wL, wR, isx ? 0 : 1, gam, gm1i, F);
+            pair_face_flux2d<FLX, -1>(wL, wR, isx ? 0 : 1, gam, gm1i, F);
             if (isx) {
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
@@ -379,7 +429,7 @@ __device__ __forceinline__ void stage_pair2d_item(const StageArgs<float> &a, con
 
 // CTAs take items with a grid stride; the copies of a CTA's next item are
 // issued before it works on the current one.
-template <int N, int TT, int NPREV, int LIM>
+template <int N, int TT, int NPREV, int LIM, int FLX>
 __global__ void __launch_bounds__(PairShape2D<N, TT>::NT, (TT >= 16 ? 5 : 2)) k_stage_pair2d(StageArgs<float> a, Geom g) {
     int item = blockIdx.x;
     if (item >= a.n_items) return;
@@ -392,7 +442,7 @@ __global__ void __launch_bounds__(PairShape2D<N, TT>::NT, (TT >= 16 ? 5 : 2)) k_
         } else {
             cp_async_wait_all();
         }
-        stage_pair2d_item<N, TT, NPREV, LIM>(a, g, item, buf);
+        stage_pair2d_item<N, TT, NPREV, LIM, FLX>(a, g, item, buf);
     }
 }
 

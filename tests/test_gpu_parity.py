@@ -605,9 +605,9 @@ def test_limiters_and_hll_fp64_match_oracle(limiter, flux, dim):
 
 @pytest.mark.parametrize("limiter,flux", [(2, 1), (1, 0), (2, 0), (4, 0), (5, 0), (6, 1)])
 def test_limiters_and_hll_fp32_uniform_3d(limiter, flux):
-    """FP32, 16^3 blocks (the pair kernel takes MC and van Leer with Rusanov,
-    the per-cell kernel HLL), gathered halos and a CUDA graph: relative L1
-    <= 1e-5 after 20 steps."""
+    """FP32, 16^3 blocks (the pair kernel takes minmod, MC and van Leer with
+    Rusanov or HLL, the per-cell kernel the other reconstructions), gathered
+    halos and a CUDA graph: relative L1 <= 1e-5 after 20 steps."""
     sp = synth.MeshSpec(ndim=3, N=16, ng=2, ntrees=(4, 4, 4), limiter=limiter, flux=flux)
     om, f = make_pair(sp, 0, precision=32)
     lev, g = om.blocks()
@@ -698,6 +698,26 @@ def test_fp32_3d_amr_blast_16cubed_against_oracle():
     assert f.sync_status() == amr.AMR_OK
     ref = u.copy()
     oracle.run_heun(om, ref, 50)
+    assert scaled_l1(f.get_state(0), ref, sp).max() <= 1e-5
+
+
+@pytest.mark.parametrize("limiter", [0, 2])
+def test_pair_kernel_hll_amr_3d(limiter):
+    """The HLL flux in the FP32 3D pair kernel on a 3-level mesh of 16^3
+    blocks (refinement-face fluxes and flux fixing, gathered halos, CUDA
+    graph): L1 error <= 1e-5 of each variable's scale after 20 steps."""
+    sp = synth.MeshSpec(ndim=3, N=16, ng=2, ntrees=(2, 2, 2), max_level=2, limiter=limiter, flux=1)
+    c = (0.5, 0.52, 0.48)
+    om, f = make_pair(sp, 0, [ball(c, (0.3, 0.2))] * 2, precision=32)
+    lev, g = om.blocks()
+    assert lev.max() == 2
+    u = synth.over_pressure(sp, lev, g, c, radius=0.15, p_in=10.0)
+    f.set_state(0, u.astype(np.float32))
+    f.compute_dt(0)
+    f.step(20, use_graph=True, gather=True)
+    assert f.sync_status() == amr.AMR_OK
+    ref = u.copy()
+    oracle.run_heun(om, ref, 20)
     assert scaled_l1(f.get_state(0), ref, sp).max() <= 1e-5
 
 
