@@ -676,9 +676,23 @@ def run_ncu_case(which="stage"):
     of a 3-level FP32 mesh -- exactly two ghost launches.  stage2d: one Heun
     step of a uniform periodic 4096^2 mesh of 16^2 blocks (65,536 blocks,
     420 MB per state slot, above L2), FP32, Kelvin-Helmholtz -- exactly two
-    2D stage launches."""
+    2D stage launches.  advection: one Heun step of the 256^3 scalar
+    advection case in 16^3 blocks (van Leer, FP32) -- exactly two advection
+    block-kernel launches."""
     import torch
     import paper_2605_07612_b300 as amr
+    if which == "advection":
+        sp = synth.advection_spec(ndim=3, N=16, ntrees=(16, 16, 16), limiter=2, velocity=(1.0, 1.0, 1.0))
+        f = amr.Forest(sp, 0, precision=32)
+        lev, g = f.blocks()
+        f.set_state(0, synth.advection_sphere(sp, lev, g).astype(np.float32))
+        f.compute_dt(0)
+        f.step(1, use_graph=False, gather=True)
+        torch.cuda.synchronize()
+        st = f.sync_status()
+        if st != amr.AMR_OK:
+            raise SystemExit("device status %d" % st)
+        return
     if which == "stage2d":
         sp = synth.MeshSpec(ndim=2, N=16, ng=2, ntrees=(256, 256, 1))
         f = amr.Forest(sp, 0, precision=32)
@@ -775,9 +789,10 @@ def main():
     ap.add_argument("--workload", default="uniform", choices=["uniform", "amr_static", "adaptive"],
                     help="uniform: the headline line; the others print their own JSON line")
     ap.add_argument("--adaptive-steps", type=int, default=500)
-    ap.add_argument("--ncu-case", nargs="?", const="stage", default=None, choices=["stage", "ghost", "stage2d"],
+    ap.add_argument("--ncu-case", nargs="?", const="stage", default=None, choices=["stage", "ghost", "stage2d", "advection"],
                     help="run one Heun step of the headline workload (stage), one ghost fill of a 3-level mesh "
-                         "(ghost) or one Heun step of a uniform 4096^2 2D mesh (stage2d) and exit, for ncu captures")
+                         "(ghost), one Heun step of a uniform 4096^2 2D mesh (stage2d) or of the 256^3 advection case "
+                         "(advection) and exit, for ncu captures")
     args = ap.parse_args()
     if args.ncu_case:
         run_ncu_case(args.ncu_case)
