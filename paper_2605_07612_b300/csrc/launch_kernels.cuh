@@ -137,13 +137,14 @@ amr_status launch_stage_pair(amr_forest *f, const StageArgs<float> &a, cudaStrea
 
 // FP32 scalar advection with a MUSCL slope limiter: one CTA per block (the
 // block and its face halo in shared memory)
-template <int D, int N, int LIM>
-amr_status launch_adv_pair_l(amr_forest *f, const StageArgs<float> &a, cudaStream_t st) {
+template <int D, int N, int LIM, int NPREV>
+amr_status launch_adv_pair_n(amr_forest *f, const StageArgs<float> &a, cudaStream_t st) {
     using Sh = AdvShape<D, N>;
+    constexpr auto kern = k_adv_pair<D, N, LIM, NPREV>;
     static bool attr_done = false;
     const size_t smem = Sh::smem_bytes();
     if (!attr_done) {
-        CU(cudaFuncSetAttribute(k_adv_pair<D, N, LIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
         attr_done = true;
     }
     const int64_t items = nblocks(f);
@@ -151,13 +152,20 @@ amr_status launch_adv_pair_l(amr_forest *f, const StageArgs<float> &a, cudaStrea
         StageArgs<float> b = a;
         b.n_items = int(items);
         int occ = 1;
-        if (f->persistent) CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_adv_pair<D, N, LIM>, Sh::NT, smem));
+        if (f->persistent) CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, Sh::NT, smem));
         const int64_t grid = stage_grid(f, items, occ);
-        k_adv_pair<D, N, LIM><<<unsigned(grid), Sh::NT, smem, st>>>(b, f->geom);
+        kern<<<unsigned(grid), Sh::NT, smem, st>>>(b, f->geom);
         ++f->launches;
     }
     CU(cudaGetLastError());
     return AMR_OK;
+}
+
+template <int D, int N, int LIM>
+amr_status launch_adv_pair_l(amr_forest *f, const StageArgs<float> &a, cudaStream_t st) {
+    if (a.nprev == 1) return launch_adv_pair_n<D, N, LIM, 1>(f, a, st);
+    if (a.nprev == 2) return launch_adv_pair_n<D, N, LIM, 2>(f, a, st);
+    return launch_adv_pair_n<D, N, LIM, -1>(f, a, st);
 }
 
 template <int D, int N>

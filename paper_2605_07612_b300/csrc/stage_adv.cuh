@@ -16,6 +16,12 @@
 
 namespace amrb {
 
+// 16-byte asynchronous global -> shared copy (both addresses 16-byte aligned)
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    const unsigned d = unsigned(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+
 template <int D, int N>
 struct AdvShape {
     static constexpr int NG = 2, S = N + 4, PL = S * S;
@@ -23,16 +29,21 @@ struct AdvShape {
     static constexpr int KZ = D == 3 ? N / ZS : 1;          // planes per segment
     static constexpr int NT = (N / 2) * N * ZS;             // threads
     static constexpr int ROWS = D == 3 ? N * N : N;         // interior rows (j, k)
-    static constexpr int WP = (N + 4) / 2;                  // pairs of a row with its x halo
-    static constexpr int NA = ROWS * WP;                    // interior rows with x halo
-    static constexpr int NB = (D == 3 ? N : 1) * 4 * (N / 2);   // y-halo rows
-    static constexpr int NC = D == 3 ? 4 * N * (N / 2) : 0;      // z-halo planes
-    static constexpr int NPAIRS = NA + NB + NC;
+    // copies of an interior row: 8-byte pairs at i = -2, 0, N-2, N (the x
+    // halo may come from another block) and 16-byte chunks at i = 2, 6, ..,
+    // N-6; of a y- or z-halo row: the S/4 16-byte chunks of the whole row
+    static constexpr int QC = (N - 4) / 4;                  // 16-byte chunks of an interior row
+    static constexpr int IR = 4 + QC;                       // copies per interior row
+    static constexpr int HR = S / 4;                        // copies per halo row
+    static constexpr int HROWS = D == 3 ? 8 * N : 4;        // y-halo rows (4 per plane) + z-halo rows
+    static constexpr int NA = ROWS * IR;
+    static constexpr int NCOPY = NA + HROWS * HR;
     static constexpr size_t smem_bytes() { return sizeof(float) * (D == 3 ? size_t(S) * PL : size_t(PL)); }
 };
 
-// 3D 16^3: 6 CTAs of 256 threads per SM (32 KB of shared memory each)
-template <int D, int N, int LIM>
+// 3D 16^3: 6 CTAs of 256 threads per SM (32 KB of shared memory each).
+// NPREV: previous states fixed at compile time (1 or 2), -1 from the arguments.
+template <int D, int N, int LIM, int NPREV>
 __global__ void __launch_bounds__(AdvShape<D, N>::NT, (D == 3 && N == 16 ? 6 : 1)) k_adv_pair(StageArgs<float> a, Geom g) {
     using Sh = AdvShape<D, N>;
     constexpr int NG = Sh::NG, S = Sh::S, PL = Sh::PL, NT = Sh::NT, KZ = Sh::KZ;
@@ -40,7 +51,18 @@ __global__ void __launch_bounds__(AdvShape<D, N>::NT, (D == 3 && N == 16 ? 6 : 1
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float *sm = reinterpret_cast<float *>(smem_raw);
     const int tid = threadIdx.x;
-    const int ip = tid % (N / 2), tj = (tid / (N / 2)) % N, zs = tid / ((N / 2) * N);
+    int ip, tj;
+    const int zs = tid / ((N / 2) * N);
+    if constexpr (N == 16) {
+        // the two 8-lane row groups of a half-warp take rows r and r + 4
+        // (80 words apart: opposite bank halves, conflict-free 8-byte loads)
+        const int lt = tid % 128, lane = lt & 31, q = (lt >> 5) * 2 + (lane >> 4);
+        ip = lane & 7;
+        tj = (q & 3) + (q >> 2) * 8 + ((lane >> 3) & 1) * 4;
+    } else {
+        ip = tid % (N / 2);
+        tj = (tid / (N / 2)) % N;
+    }
     const int ci = 2 * ip;
     const float cl[3] = {fmaxf(a.vel[0], 0.f), fmaxf(a.vel[1], 0.f), fmaxf(a.vel[2], 0.f)};
     const float cr[3] = {fminf(a.vel[0], 0.f), fminf(a.vel[1], 0.f), fminf(a.vel[2], 0.f)};
@@ -58,34 +80,44 @@ __global__ void __launch_bounds__(AdvShape<D, N>::NT, (D == 3 && N == 16 ? 6 : 1
         const int nb0 = a.gather ? info.nbr[0] : -1, nb1 = a.gather ? info.nbr[1] : -1;
         const int nb2 = a.gather ? info.nbr[2] : -1, nb3 = a.gather ? info.nbr[3] : -1;
         const int nb4 = (D == 3 && a.gather) ? info.nbr[4] : -1, nb5 = (D == 3 && a.gather) ? info.nbr[5] : -1;
-        // ---- copies: interior rows with their x halo, y-halo rows, z-halo planes
-        for (int p = tid; p < Sh::NPAIRS; p += NT) {
-            int i, j, k = 0;
+        // ---- copies: interior rows with their x halo (from the x neighbours
+        // in gather mode), then the y- and z-halo rows (from the neighbours)
+        for (int p = tid; p < Sh::NCOPY; p += NT) {
             if (p < Sh::NA) {
-                const int row = p / Sh::WP;
-                i = 2 * (p - row * Sh::WP) - 2;
-                j = row % N;
-                k = D == 3 ? row / N : 0;
-            } else if (p < Sh::NA + Sh::NB) {
-                const int q = p - Sh::NA, row = q / (N / 2), jr = row % 4;
-                i = 2 * (q - row * (N / 2));
-                j = jr < 2 ? jr - 2 : N + jr - 2;
-                k = D == 3 ? row / 4 : 0;
+                const int row = p / Sh::IR, part = p - row * Sh::IR;
+                const int j = row % N, k = D == 3 ? row / N : 0;
+                if (part >= 2 && part < 2 + Sh::QC) {
+                    const int i = 2 + 4 * (part - 2);
+                    cp_async16(sm + soff(i, j, k), ub + gofs(i, j, k));
+                } else {
+                    const int i = part == 0 ? -2 : (part == 1 ? 0 : (part == 2 + Sh::QC ? N - 2 : N));
+                    const float *src = ub + gofs(i, j, k);
+                    if (i < 0 && nb0 >= 0) src = a.deriv + int64_t(nb0) * NCELL + gofs(i + N, j, k);
+                    if (i >= N && nb1 >= 0) src = a.deriv + int64_t(nb1) * NCELL + gofs(i - N, j, k);
+                    cp_async8(sm + soff(i, j, k), src);
+                }
             } else {
-                const int q = p - Sh::NA - Sh::NB, row = q / (N / 2), kr = row / N;
-                i = 2 * (q - row * (N / 2));
-                j = row % N;
-                k = kr < 2 ? kr - 2 : N + kr - 2;
+                const int q = p - Sh::NA, row = q / Sh::HR, c = q - row * Sh::HR;
+                int j, k, nb, sj, sk;
+                if (row < (D == 3 ? 4 * N : 4)) {        // y halo: 4 rows per plane
+                    const int jr = row % 4;
+                    k = D == 3 ? row / 4 : 0;
+                    j = jr < 2 ? jr - 2 : N + jr - 2;
+                    nb = jr < 2 ? nb2 : nb3;
+                    sj = jr < 2 ? j + N : j - N;
+                    sk = k;
+                } else {                                  // z halo: rows of 4 planes
+                    const int r2 = row - 4 * N, kr = r2 / N;
+                    j = r2 % N;
+                    k = kr < 2 ? kr - 2 : N + kr - 2;
+                    nb = kr < 2 ? nb4 : nb5;
+                    sj = j;
+                    sk = kr < 2 ? k + N : k - N;
+                }
+                const int i = 4 * c - 2;
+                const float *src = nb >= 0 ? a.deriv + int64_t(nb) * NCELL + gofs(i, sj, sk) : ub + gofs(i, j, k);
+                cp_async16(sm + soff(i, j, k), src);
             }
-            int gi = i, gj = j, gk = k, nb = -1;
-            if (gi < 0) { nb = nb0; gi += N; }
-            else if (gi >= N) { nb = nb1; gi -= N; }
-            else if (gj < 0) { nb = nb2; gj += N; }
-            else if (gj >= N) { nb = nb3; gj -= N; }
-            else if (D == 3 && gk < 0) { nb = nb4; gk += N; }
-            else if (D == 3 && gk >= N) { nb = nb5; gk -= N; }
-            const float *src = nb >= 0 ? a.deriv + int64_t(nb) * NCELL + gofs(gi, gj, gk) : ub + gofs(i, j, k);
-            cp_async8(sm + soff(i, j, k), src);
         }
         cp_async_commit();
         cp_async_wait_all();
@@ -155,8 +187,9 @@ __global__ void __launch_bounds__(AdvShape<D, N>::NT, (D == 3 && N == 16 ? 6 : 1
             const int64_t ob = int64_t(b) * NCELL + gofs(ci, tj, k);
             float2 acc = PF::sp(0.f);
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (q < a.nprev) acc = PF::fma(PF::sp(a.wprev[q]), *reinterpret_cast<const float2 *>(a.prev[q] + ob), acc);
+            for (int q = 0; q < (NPREV > 0 ? NPREV : 4); ++q)
+                if (NPREV > 0 || q < a.nprev)
+                    acc = PF::fma(PF::sp(a.wprev[q]), *reinterpret_cast<const float2 *>(a.prev[q] + ob), acc);
             *reinterpret_cast<float2 *>(a.out + ob) = PF::fma(PF::sp(dte), du, acc);
             // complete the row's DRAM sectors: the output's x-ghost cells
             if (ci == 0) *reinterpret_cast<float2 *>(a.out + ob - NG) = PF::sp(0.f);
