@@ -199,53 +199,68 @@ __global__ void __launch_bounds__(256) k_ghost(GhostArgs<real> a, Geom g) {
     }
     const int ncells = ext[0] * ext[1] * ext[2];
     const int total = ncells * g.V;
-    for (int idx = lane; idx < total; idx += 32) {
-        int v = idx / ncells, c = idx - v * ncells;
-        int x[3];
-        x[0] = lo[0] + c % ext[0];
-        c /= ext[0];
-        x[1] = lo[1] + c % ext[1];
-        x[2] = (D == 3) ? lo[2] + c / ext[1] : 0;
-        real val;
-        if (e.kind == KIND_SRL) {
-            int y[3] = {x[0], x[1], x[2]};
-            y[nd] += side ? -N : N;
-            val = srcb[int64_t(v) * g.ncell + cell_index<real>(g, y[0], y[1], y[2])];
-        } else if (e.kind == KIND_F2C) {
-            int y[3] = {0, 0, 0};
-            for (int d = 0; d < D; ++d) y[d] = 2 * x[d] - off[d] * N;
-            y[nd] = side ? 2 * (x[nd] - N) : 2 * x[nd] + N;
-            val = restrict_at<real, D>(srcb + int64_t(v) * g.ncell, g, y[0], y[1], y[2]);
-        } else if (e.kind == KIND_C2F) {
-            int y[3] = {0, 0, 0}, s[3] = {0, 0, 0};
-            for (int d = 0; d < D; ++d) {
-                y[d] = off[d] * (N / 2) + (x[d] >> 1);
-                s[d] = x[d] & 1;
+    // four values per lane per round: all their loads are issued before
+    // the first store, so a warp keeps several loads in flight
+    for (int base = lane; base < total; base += 128) {
+        real vals[4];
+        int64_t dsti[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int idx = base + 32 * r;
+            dsti[r] = -1;
+            vals[r] = real(0);
+            if (idx >= total) continue;
+            int v = idx / ncells, c = idx - v * ncells;
+            int x[3];
+            x[0] = lo[0] + c % ext[0];
+            c /= ext[0];
+            x[1] = lo[1] + c % ext[1];
+            x[2] = (D == 3) ? lo[2] + c / ext[1] : 0;
+            real val;
+            if (e.kind == KIND_SRL) {
+                int y[3] = {x[0], x[1], x[2]};
+                y[nd] += side ? -N : N;
+                val = srcb[int64_t(v) * g.ncell + cell_index<real>(g, y[0], y[1], y[2])];
+            } else if (e.kind == KIND_F2C) {
+                int y[3] = {0, 0, 0};
+                for (int d = 0; d < D; ++d) y[d] = 2 * x[d] - off[d] * N;
+                y[nd] = side ? 2 * (x[nd] - N) : 2 * x[nd] + N;
+                val = restrict_at<real, D>(srcb + int64_t(v) * g.ncell, g, y[0], y[1], y[2]);
+            } else if (e.kind == KIND_C2F) {
+                int y[3] = {0, 0, 0}, s[3] = {0, 0, 0};
+                for (int d = 0; d < D; ++d) {
+                    y[d] = off[d] * (N / 2) + (x[d] >> 1);
+                    s[d] = x[d] & 1;
+                }
+                const int xn = side ? x[nd] - N : x[nd];
+                y[nd] = side ? (xn >> 1) : N + (xn >> 1);
+                s[nd] = xn & 1;
+                val = prolong_at<real, D>(srcb + int64_t(v) * g.ncell, g, y[0], y[1], y[2], s[0], s[1], s[2]);
+            } else {  // physical boundary (Sec. 2.4)
+                const int k = side ? x[nd] - N + 1 : -x[nd];          // layer 1..ng
+                int y[3] = {x[0], x[1], x[2]};
+                y[nd] = side ? N - k : k - 1;                          // mirror cell
+                const real um = dstb[int64_t(v) * g.ncell + cell_index<real>(g, y[0], y[1], y[2])];
+                const int inst = a.info[e.dst].inst;
+                const int ty = a.bc_type[6 * inst + e.face];
+                const real bv = a.bc_val[(6 * inst + e.face) * 8 + v];
+                if (ty == 1) {
+                    val = real(2) * bv - um;
+                } else if (ty == 2) {
+                    const real h = mul_rn(real(2 * k - 1), real(g.dx[3 * a.info[e.dst].gclass + nd]));
+                    val = add_rn(um, mul_rn(h, bv));
+                } else {
+                    const int t = x[tdim[0]] + (D == 3 ? N * x[tdim[1]] : 0);
+                    const int64_t nface = (D == 3) ? int64_t(N) * N : N;
+                    val = real(2) * a.bcdata[(int64_t(e.aux) * g.V + v) * nface + t] - um;
+                }
             }
-            const int xn = side ? x[nd] - N : x[nd];
-            y[nd] = side ? (xn >> 1) : N + (xn >> 1);
-            s[nd] = xn & 1;
-            val = prolong_at<real, D>(srcb + int64_t(v) * g.ncell, g, y[0], y[1], y[2], s[0], s[1], s[2]);
-        } else {  // physical boundary (Sec. 2.4)
-            const int k = side ? x[nd] - N + 1 : -x[nd];          // layer 1..ng
-            int y[3] = {x[0], x[1], x[2]};
-            y[nd] = side ? N - k : k - 1;                          // mirror cell
-            const real um = dstb[int64_t(v) * g.ncell + cell_index<real>(g, y[0], y[1], y[2])];
-            const int inst = a.info[e.dst].inst;
-            const int ty = a.bc_type[6 * inst + e.face];
-            const real bv = a.bc_val[(6 * inst + e.face) * 8 + v];
-            if (ty == 1) {
-                val = real(2) * bv - um;
-            } else if (ty == 2) {
-                const real h = mul_rn(real(2 * k - 1), real(g.dx[3 * a.info[e.dst].gclass + nd]));
-                val = add_rn(um, mul_rn(h, bv));
-            } else {
-                const int t = x[tdim[0]] + (D == 3 ? N * x[tdim[1]] : 0);
-                const int64_t nface = (D == 3) ? int64_t(N) * N : N;
-                val = real(2) * a.bcdata[(int64_t(e.aux) * g.V + v) * nface + t] - um;
-            }
+            vals[r] = val;
+            dsti[r] = int64_t(v) * g.ncell + cell_index<real>(g, x[0], x[1], x[2]);
         }
-        dstb[int64_t(v) * g.ncell + cell_index<real>(g, x[0], x[1], x[2])] = val;
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+            if (dsti[r] >= 0) dstb[dsti[r]] = vals[r];
     }
 }
 
