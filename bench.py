@@ -678,9 +678,38 @@ def run_ncu_case(which="stage"):
     420 MB per state slot, above L2), FP32, Kelvin-Helmholtz -- exactly two
     2D stage launches.  advection: one Heun step of the 256^3 scalar
     advection case in 16^3 blocks (van Leer, FP32) -- exactly two advection
-    block-kernel launches."""
+    block-kernel launches.  batched2d: the 64 batched 2D meshes refined as in
+    the bench (three regrids, five ghost launches), then one Heun step with
+    4 items per CTA -- two ghost rounds and one stage launch per stage."""
     import torch
     import paper_2605_07612_b300 as amr
+    if which == "batched2d":
+        specs = batched_specs()
+        cap = [int(sp.ntrees[0] * sp.ntrees[1] * 4 ** sp.max_level) for sp, *_ in specs]
+        f = amr.Forest(None, batch=[(sp, 0, c) for (sp, *_), c in zip(specs, cap)], precision=32)
+
+        def init():
+            lev, g = f.blocks()
+            parts = []
+            for i, (sp, kind, x0, seed, axis) in enumerate(specs):
+                first, n = f.instance_blocks(i)
+                l, gg = lev[first:first + n], g[first:first + n]
+                parts.append(synth.kelvin_helmholtz(sp, l, gg, seed=seed) if kind == "kh"
+                             else synth.shock_tube(sp, l, gg, x0=x0, axis=axis))
+            return np.concatenate(parts).astype(np.float32)
+        for _ in range(3):
+            f.set_state(0, init())
+            if not f.regrid(None, c_ref=5e-2, c_deref=-1.0):
+                break
+        f.set_state(0, init())
+        f.compute_dt(0)
+        f.set_launch_shape(4)
+        f.step(1, use_graph=False, gather=True)
+        torch.cuda.synchronize()
+        st = f.sync_status()
+        if st != amr.AMR_OK:
+            raise SystemExit("device status %d" % st)
+        return
     if which == "advection":
         sp = synth.advection_spec(ndim=3, N=16, ntrees=(16, 16, 16), limiter=2, velocity=(1.0, 1.0, 1.0))
         f = amr.Forest(sp, 0, precision=32)
@@ -789,10 +818,10 @@ def main():
     ap.add_argument("--workload", default="uniform", choices=["uniform", "amr_static", "adaptive"],
                     help="uniform: the headline line; the others print their own JSON line")
     ap.add_argument("--adaptive-steps", type=int, default=500)
-    ap.add_argument("--ncu-case", nargs="?", const="stage", default=None, choices=["stage", "ghost", "stage2d", "advection"],
+    ap.add_argument("--ncu-case", nargs="?", const="stage", default=None, choices=["stage", "ghost", "stage2d", "advection", "batched2d"],
                     help="run one Heun step of the headline workload (stage), one ghost fill of a 3-level mesh "
-                         "(ghost), one Heun step of a uniform 4096^2 2D mesh (stage2d) or of the 256^3 advection case "
-                         "(advection) and exit, for ncu captures")
+                         "(ghost), one Heun step of a uniform 4096^2 2D mesh (stage2d), of the 256^3 advection case "
+                         "(advection) or of the batched 2D meshes (batched2d) and exit, for ncu captures")
     args = ap.parse_args()
     if args.ncu_case:
         run_ncu_case(args.ncu_case)
