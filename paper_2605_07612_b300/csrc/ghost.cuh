@@ -111,6 +111,99 @@ __device__ __forceinline__ void srl_pairs(real *dstb, const real *srcb, int side
     }
 }
 
+// One face strip of round 1 or 2 (F2C, BC, C2F, and SRL when NG is odd),
+// ND = face-normal dimension, HALF = the F2C strip of one fine block (half
+// the face along each tangential dimension).
+template <class real, int D, int N, int NG, int ND, bool HALF>
+__device__ __forceinline__ void ghost_strip(const GhostArgs<real> &a, const Geom &g, const Entry &e, real *dstb,
+                                            const real *srcb, int lane) {
+    constexpr int ng = NG;
+    constexpr int nd = ND;
+    // tangential dimensions (lower first) and the strip's extents, fixed at
+    // compile time so that no division by a runtime extent is left
+    constexpr int T0 = ND == 0 ? 1 : 0, T1 = ND == 2 ? 1 : 2;
+    constexpr int tdim[2] = {T0, T1};
+    constexpr int E0 = ND == 0 ? NG : (HALF ? N / 2 : N);
+    constexpr int E1 = ND == 1 ? NG : (HALF ? N / 2 : N);
+    constexpr int E2 = D == 3 ? (ND == 2 ? NG : (HALF ? N / 2 : N)) : 1;
+    constexpr int ext[3] = {E0, E1, E2};
+    const int side = e.face & 1;
+    int lo[3] = {0, 0, 0};
+    lo[nd] = side ? N : -ng;
+    int off[3] = {0, 0, 0};   // tangential position of the fine block (F2C/C2F)
+    off[tdim[0]] = e.offset & 1;
+    if (D == 3) off[tdim[1]] = (e.offset >> 1) & 1;
+    if constexpr (HALF) {
+        lo[T0] = off[T0] * (N / 2);
+        if (D == 3) lo[T1] = off[T1] * (N / 2);
+    }
+    constexpr int ncells = E0 * E1 * E2;
+    const int total = ncells * g.V;
+    // four values per lane per round: all their loads are issued before
+    // the first store, so a warp keeps several loads in flight
+    for (int base = lane; base < total; base += 128) {
+        real vals[4];
+        int64_t dsti[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int idx = base + 32 * r;
+            dsti[r] = -1;
+            vals[r] = real(0);
+            if (idx >= total) continue;
+            int v = idx / ncells, c = idx - v * ncells;
+            int x[3];
+            x[0] = lo[0] + c % ext[0];
+            c /= ext[0];
+            x[1] = lo[1] + c % ext[1];
+            x[2] = (D == 3) ? lo[2] + c / ext[1] : 0;
+            real val;
+            if (e.kind == KIND_SRL) {
+                int y[3] = {x[0], x[1], x[2]};
+                y[nd] += side ? -N : N;
+                val = srcb[int64_t(v) * g.ncell + cell_index<real>(g, y[0], y[1], y[2])];
+            } else if (e.kind == KIND_F2C) {
+                int y[3] = {0, 0, 0};
+                for (int d = 0; d < D; ++d) y[d] = 2 * x[d] - off[d] * N;
+                y[nd] = side ? 2 * (x[nd] - N) : 2 * x[nd] + N;
+                val = restrict_at<real, D>(srcb + int64_t(v) * g.ncell, g, y[0], y[1], y[2]);
+            } else if (e.kind == KIND_C2F) {
+                int y[3] = {0, 0, 0}, s[3] = {0, 0, 0};
+                for (int d = 0; d < D; ++d) {
+                    y[d] = off[d] * (N / 2) + (x[d] >> 1);
+                    s[d] = x[d] & 1;
+                }
+                const int xn = side ? x[nd] - N : x[nd];
+                y[nd] = side ? (xn >> 1) : N + (xn >> 1);
+                s[nd] = xn & 1;
+                val = prolong_at<real, D>(srcb + int64_t(v) * g.ncell, g, y[0], y[1], y[2], s[0], s[1], s[2]);
+            } else {  // physical boundary (Sec. 2.4)
+                const int k = side ? x[nd] - N + 1 : -x[nd];          // layer 1..ng
+                int y[3] = {x[0], x[1], x[2]};
+                y[nd] = side ? N - k : k - 1;                          // mirror cell
+                const real um = dstb[int64_t(v) * g.ncell + cell_index<real>(g, y[0], y[1], y[2])];
+                const int inst = a.info[e.dst].inst;
+                const int ty = a.bc_type[6 * inst + e.face];
+                const real bv = a.bc_val[(6 * inst + e.face) * 8 + v];
+                if (ty == 1) {
+                    val = real(2) * bv - um;
+                } else if (ty == 2) {
+                    const real h = mul_rn(real(2 * k - 1), real(g.dx[3 * a.info[e.dst].gclass + nd]));
+                    val = add_rn(um, mul_rn(h, bv));
+                } else {
+                    const int t = x[tdim[0]] + (D == 3 ? N * x[tdim[1]] : 0);
+                    const int64_t nface = (D == 3) ? int64_t(N) * N : N;
+                    val = real(2) * a.bcdata[(int64_t(e.aux) * g.V + v) * nface + t] - um;
+                }
+            }
+            vals[r] = val;
+            dsti[r] = int64_t(v) * g.ncell + cell_index<real>(g, x[0], x[1], x[2]);
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+            if (dsti[r] >= 0) dstb[dsti[r]] = vals[r];
+    }
+}
+
 template <class real, int D, int N, int NG>
 __global__ void __launch_bounds__(256) k_ghost(GhostArgs<real> a, Geom g) {
     const int warp = int((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
@@ -180,87 +273,17 @@ __global__ void __launch_bounds__(256) k_ghost(GhostArgs<real> a, Geom g) {
             return;
         }
     }
-    constexpr int ng = NG;
-    // ghost box of this strip in dst-local coordinates
-    int lo[3] = {0, 0, 0}, ext[3] = {N, N, D == 3 ? N : 1};
-    lo[nd] = side ? N : -ng;
-    ext[nd] = ng;
-    int tdim[2] = {-1, -1};
-    for (int d = 0, c = 0; d < D; ++d)
-        if (d != nd) tdim[c++] = d;
-    int off[3] = {0, 0, 0};   // tangential position of the fine block (F2C/C2F)
-    off[tdim[0]] = e.offset & 1;
-    if (D == 3) off[tdim[1]] = (e.offset >> 1) & 1;
-    if (e.kind == KIND_F2C) {
-        for (int c = 0; c < D - 1; ++c) {
-            lo[tdim[c]] = off[tdim[c]] * (N / 2);
-            ext[tdim[c]] = N / 2;
-        }
-    }
-    const int ncells = ext[0] * ext[1] * ext[2];
-    const int total = ncells * g.V;
-    // four values per lane per round: all their loads are issued before
-    // the first store, so a warp keeps several loads in flight
-    for (int base = lane; base < total; base += 128) {
-        real vals[4];
-        int64_t dsti[4];
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int idx = base + 32 * r;
-            dsti[r] = -1;
-            vals[r] = real(0);
-            if (idx >= total) continue;
-            int v = idx / ncells, c = idx - v * ncells;
-            int x[3];
-            x[0] = lo[0] + c % ext[0];
-            c /= ext[0];
-            x[1] = lo[1] + c % ext[1];
-            x[2] = (D == 3) ? lo[2] + c / ext[1] : 0;
-            real val;
-            if (e.kind == KIND_SRL) {
-                int y[3] = {x[0], x[1], x[2]};
-                y[nd] += side ? -N : N;
-                val = srcb[int64_t(v) * g.ncell + cell_index<real>(g, y[0], y[1], y[2])];
-            } else if (e.kind == KIND_F2C) {
-                int y[3] = {0, 0, 0};
-                for (int d = 0; d < D; ++d) y[d] = 2 * x[d] - off[d] * N;
-                y[nd] = side ? 2 * (x[nd] - N) : 2 * x[nd] + N;
-                val = restrict_at<real, D>(srcb + int64_t(v) * g.ncell, g, y[0], y[1], y[2]);
-            } else if (e.kind == KIND_C2F) {
-                int y[3] = {0, 0, 0}, s[3] = {0, 0, 0};
-                for (int d = 0; d < D; ++d) {
-                    y[d] = off[d] * (N / 2) + (x[d] >> 1);
-                    s[d] = x[d] & 1;
-                }
-                const int xn = side ? x[nd] - N : x[nd];
-                y[nd] = side ? (xn >> 1) : N + (xn >> 1);
-                s[nd] = xn & 1;
-                val = prolong_at<real, D>(srcb + int64_t(v) * g.ncell, g, y[0], y[1], y[2], s[0], s[1], s[2]);
-            } else {  // physical boundary (Sec. 2.4)
-                const int k = side ? x[nd] - N + 1 : -x[nd];          // layer 1..ng
-                int y[3] = {x[0], x[1], x[2]};
-                y[nd] = side ? N - k : k - 1;                          // mirror cell
-                const real um = dstb[int64_t(v) * g.ncell + cell_index<real>(g, y[0], y[1], y[2])];
-                const int inst = a.info[e.dst].inst;
-                const int ty = a.bc_type[6 * inst + e.face];
-                const real bv = a.bc_val[(6 * inst + e.face) * 8 + v];
-                if (ty == 1) {
-                    val = real(2) * bv - um;
-                } else if (ty == 2) {
-                    const real h = mul_rn(real(2 * k - 1), real(g.dx[3 * a.info[e.dst].gclass + nd]));
-                    val = add_rn(um, mul_rn(h, bv));
-                } else {
-                    const int t = x[tdim[0]] + (D == 3 ? N * x[tdim[1]] : 0);
-                    const int64_t nface = (D == 3) ? int64_t(N) * N : N;
-                    val = real(2) * a.bcdata[(int64_t(e.aux) * g.V + v) * nface + t] - um;
-                }
-            }
-            vals[r] = val;
-            dsti[r] = int64_t(v) * g.ncell + cell_index<real>(g, x[0], x[1], x[2]);
-        }
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-            if (dsti[r] >= 0) dstb[dsti[r]] = vals[r];
+    // the general path, with the strip shape fixed per normal and kind
+    const bool half = e.kind == KIND_F2C;
+    if (nd == 0) {
+        if (half) ghost_strip<real, D, N, NG, 0, true>(a, g, e, dstb, srcb, lane);
+        else ghost_strip<real, D, N, NG, 0, false>(a, g, e, dstb, srcb, lane);
+    } else if (nd == 1 || D == 2) {
+        if (half) ghost_strip<real, D, N, NG, 1, true>(a, g, e, dstb, srcb, lane);
+        else ghost_strip<real, D, N, NG, 1, false>(a, g, e, dstb, srcb, lane);
+    } else {
+        if (half) ghost_strip<real, D, N, NG, (D == 3 ? 2 : 1), true>(a, g, e, dstb, srcb, lane);
+        else ghost_strip<real, D, N, NG, (D == 3 ? 2 : 1), false>(a, g, e, dstb, srcb, lane);
     }
 }
 
