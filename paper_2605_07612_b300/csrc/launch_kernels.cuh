@@ -1,6 +1,7 @@
 // Definitions of the ghost and stage kernel launchers declared in
 // api_internal.cuh; the inst_*.cu units instantiate them.
 #pragma once
+#include <atomic>
 #include <type_traits>
 
 #include "api_internal.cuh"
@@ -12,6 +13,20 @@
 #include "stage_weno.cuh"
 
 namespace amrb {
+
+// The dynamic shared-memory limit of a kernel is a per-device setting: it is
+// raised once per (kernel, device) -- `done` holds one bit per device id.
+template <class K>
+cudaError_t smem_attr_once(K kern, size_t smem, std::atomic<unsigned long long> &done) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_release);
+    return e;
+}
 
 template <class real, int D>
 amr_status launch_ghosts(amr_forest *f, int s, cudaStream_t st, bool gather) {
@@ -50,12 +65,9 @@ amr_status launch_stage_t(amr_forest *f, const StageArgs<real> &a, cudaStream_t 
     constexpr int T = N < 16 ? N : 16;
     using Sh = StageShape<real, D, N, NG, T, PH>;
     constexpr auto kern = k_stage<real, D, N, NG, T, GEN, PH>;
-    static bool attr_done = false;
+    static std::atomic<unsigned long long> attr_done{0};
     const size_t smem = Sh::smem_bytes();
-    if (!attr_done) {
-        CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-        attr_done = true;
-    }
+    CU(smem_attr_once(kern, smem, attr_done));
     const int64_t items = nblocks(f) * Sh::TILES;
     if (items > 0) {
         StageArgs<real> b = a;
@@ -92,12 +104,9 @@ template <int D, int N, int TT, int NPREV, int LIM, int FLX>
 amr_status launch_stage_pair_n(amr_forest *f, const StageArgs<float> &a, cudaStream_t st) {
     using K = PairKernel<D, N, TT, NPREV, LIM, FLX>;
     using Sh = typename K::Sh;
-    static bool attr_done = false;
+    static std::atomic<unsigned long long> attr_done{0};
     const size_t smem = Sh::smem_bytes(NPREV);
-    if (!attr_done) {
-        CU(cudaFuncSetAttribute(K::fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-        attr_done = true;
-    }
+    CU(smem_attr_once(K::fn, smem, attr_done));
     const int64_t items = nblocks(f) * Sh::TILES;
     if (items > 0) {
         StageArgs<float> b = a;
@@ -141,12 +150,9 @@ template <int D, int N, int LIM, int NPREV>
 amr_status launch_adv_pair_n(amr_forest *f, const StageArgs<float> &a, cudaStream_t st) {
     using Sh = AdvShape<D, N>;
     constexpr auto kern = k_adv_pair<D, N, LIM, NPREV>;
-    static bool attr_done = false;
+    static std::atomic<unsigned long long> attr_done{0};
     const size_t smem = Sh::smem_bytes();
-    if (!attr_done) {
-        CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-        attr_done = true;
-    }
+    CU(smem_attr_once(kern, smem, attr_done));
     const int64_t items = nblocks(f);
     if (items > 0) {
         StageArgs<float> b = a;
