@@ -145,6 +145,24 @@ def traffic_from_profile(workload):
     return ent.get("bytes_per_launch")   # mean of the stage-1 and stage-2 launches
 
 
+def phase_breakdown(f, stream, gather, steps=2, scheme="heun"):
+    """Device time per step by phase (ghost rounds, stage, flux fix, dt) of
+    plain traced steps after one untimed step, and the ghost rounds' share
+    of it: the counterpart of the paper's foap4 % (time outside the flux
+    computation and the solution update, Sec. 5.2).  Advances the state."""
+    f.trace(True)
+    f.step(1, gather=gather, stream=stream, scheme=scheme)
+    f.trace_read()
+    f.step(steps, gather=gather, stream=stream, scheme=scheme)
+    t = f.trace_read()
+    f.trace(False)
+    dev = {p: ms / steps for p, (ms, n) in t.items() if n and not p.endswith("_host")}
+    total = sum(dev.values())
+    return {"ms_per_step": {p: round(v, 5) for p, v in dev.items()},
+            "ghost_share": (dev.get("ghost_r1", 0.0) + dev.get("ghost_r2", 0.0)) / total if total else 0.0,
+            "gather": gather, "steps": steps}
+
+
 def max_over_ranks(x, dist, device="cuda"):
     """The largest value of x over all ranks (the slowest rank's time); x
     itself with one process."""
@@ -309,12 +327,17 @@ def run_ours(args, rank, world, dist):
             nrt = args.steps if prec == 32 else max(2, args.steps // 4)
             msr, _ = time_steps(fr, nrt, 1 if prec == 64 else args.warmup, prec == 32, prec == 32)
             st_rt = fr.sync_status()
+            ph = {"filled": phase_breakdown(fr, stream, False)}
+            if prec == 32:
+                ph["gathered"] = phase_breakdown(fr, stream, True)
             rt["%d^3 fp%d" % (bn, prec)] = {"value": 2.0 * cells * nrt * world / (msr * 1e-3), "ms_per_step": msr / nrt,
-                                             "status": st_rt}
+                                             "status": st_rt, "phases": ph}
             del fr
             torch.cuda.empty_cache()
         rt["context"] = ("paper, 1x H100, same case: FP64 1.37 / 1.30 / 1.10 and FP32 2.70 / 2.60 / 2.08 GCUPS "
-                         "for 32^3 / 16^3 / 8^3 blocks (Tables 1 and 2); flux scheme not stated there, Rusanov here")
+                         "for 32^3 / 16^3 / 8^3 blocks (Tables 1 and 2); flux scheme not stated there, Rusanov here; "
+                         "ghost-cell share of the time (foap4 %, FP64) 8.8 / 14.3 / 24.0 % (Table 1), against "
+                         "phases.filled.ghost_share here (phases.gathered: same-level halos read by the stage)")
         extras["rayleigh_taylor_vanleer"] = rt
         # the same case with WENO5 (three ghost layers; Table 1's WENO5 rows)
         rtw = {}
@@ -558,7 +581,8 @@ def run_amr_static(args, amr, torch, stream):
     drift = (np.abs(f.conserved(0, stream=stream) - s0) / abs_integrals(sp, u, lev)).tolist()
     cells = f.n * sp.N ** 3
     pat = f.pattern()
-    return {"value": 2.0 * cells * steps / (ms * 1e-3), "unit": UNIT, "blocks": f.n,
+    phases = phase_breakdown(f, stream, True)
+    return {"value": 2.0 * cells * steps / (ms * 1e-3), "unit": UNIT, "blocks": f.n, "phases": phases,
             "blocks_per_level": np.bincount(lev).tolist(), "ball_radius": r, "centre": list(centre),
             "ghost_entries": {k: int((pat[:, 0] == i).sum()) for i, k in enumerate(["srl", "f2c", "bc", "c2f"])},
             "ms_per_step": ms / steps, "steps": steps, "autotune_choice": choice,

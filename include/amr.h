@@ -422,6 +422,41 @@ const char *amr_last_error(const amr_forest *f);
 /* Kernel launches issued by the library since the forest was created. */
 amr_status amr_launch_count(const amr_forest *f, int64_t *n);
 
+/* ---- per-phase timing ----------------------------------------------------
+ * A debug mode that splits the time of the calls above into the phases of
+ * one time step, as the timers of Sec. 2.8 and the breakdowns of Sec. 5.2 and
+ * 5.4 do (ghost-cell updates against the flux computation and solution
+ * update; mesh adaptation and pattern updates in the AMR run).  Device phases are timed by a pair of CUDA events
+ * recorded on the call's stream around their launches, host phases by the
+ * wall clock.  While tracing is on, amr_step runs every step as separate
+ * launches even when AMR_STEP_GRAPH is given (a replayed graph cannot be
+ * split into phases), and amr_autotune pauses it.  Off by default; tracing
+ * never changes results. */
+typedef enum {
+    AMR_PHASE_GHOST_R1 = 0,   /* ghost fill round 1: same level, restriction, boundaries (Sec. 2.6) */
+    AMR_PHASE_GHOST_R2,       /* ghost fill round 2: limited prolongation (Sec. 2.6) */
+    AMR_PHASE_STAGE,          /* flux computation and solution update (Eq. 5), all passes */
+    AMR_PHASE_FLUXFIX,        /* flux fixing at refinement faces (Sec. 2.7) */
+    AMR_PHASE_DT,             /* CFL time step: maximum speed and the per-mesh commit */
+    AMR_PHASE_CONSERVED,      /* conserved sums */
+    AMR_PHASE_FLAGS,          /* refinement flags (Eq. 12) and model features */
+    AMR_PHASE_TRANSFER,       /* regrid data transfer on the device */
+    AMR_PHASE_MESH_HOST,      /* host: adapting and balancing the forest, the old -> new map */
+    AMR_PHASE_PATTERN_HOST,   /* host: building and uploading the ghost-cell pattern */
+    AMR_N_PHASES
+} amr_phase;
+
+/* Switches tracing on (on != 0) or off.  The totals are kept across
+ * switches; amr_trace_read clears them.  Errors: AMR_EINVAL (f NULL). */
+amr_status amr_trace(amr_forest *f, int on);
+
+/* Waits for every phase recorded so far (so it synchronises with the
+ * streams they were recorded on), then writes per phase the total
+ * milliseconds to ms[0 .. AMR_N_PHASES) and the number of timed records to
+ * count[0 .. AMR_N_PHASES) (host arrays; either may be NULL).  reset != 0
+ * clears the totals afterwards.  Errors: AMR_EINVAL. */
+amr_status amr_trace_read(amr_forest *f, double *ms, int64_t *count, int reset);
+
 /* ---- checkpoint, restart and output --------------------------------------
  * The configuration of instance `inst` as given at creation (the batch
  * capacity is in f's max_blocks only through amr_n_blocks; here max_blocks

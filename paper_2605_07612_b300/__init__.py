@@ -20,6 +20,9 @@ AMR_OK, AMR_EINVAL, AMR_ENOMEM, AMR_ECAPACITY, AMR_ECUDA = 0, 1, 2, 3, 4
 AMR_ETIMEOUT, AMR_EBOUNDS, AMR_ENONPHYS, AMR_ESTATE = 5, 6, 7, 8
 PHYS_EULER, PHYS_ADVECTION = 0, 1
 AMR_STEP_GRAPH, AMR_STEP_GATHER, AMR_STEP_SSP3, AMR_STEP_RK4, AMR_STEP_SSP43 = 1, 2, 4, 8, 16
+# the amr_phase order of the per-phase timing
+PHASES = ("ghost_r1", "ghost_r2", "stage", "fluxfix", "dt", "conserved", "flags", "transfer", "mesh_host",
+          "pattern_host")
 STATUS_NAMES = {0: "AMR_OK", 1: "AMR_EINVAL", 2: "AMR_ENOMEM", 3: "AMR_ECAPACITY", 4: "AMR_ECUDA",
                 5: "AMR_ETIMEOUT", 6: "AMR_EBOUNDS", 7: "AMR_ENONPHYS", 8: "AMR_ESTATE"}
 KIND_SRL, KIND_F2C, KIND_BC, KIND_C2F = 0, 1, 2, 3
@@ -33,6 +36,7 @@ EXPORTED = [
     "amr_get_dts", "amr_conserved_all", "amr_autotune", "amr_features", "amr_mlp_create", "amr_mlp_destroy",
     "amr_mlp_n_params", "amr_mlp_get_params", "amr_mlp_set_params", "amr_mlp_forward", "amr_mlp_gradient",
     "amr_mlp_train", "amr_mlp_flags", "amr_get_config", "amr_save", "amr_load", "amr_write_xdmf", "amr_set_launch_shape",
+    "amr_trace", "amr_trace_read",
 ]
 
 
@@ -118,6 +122,8 @@ def load(build_if_missing: bool = True):
         "amr_flag_and_regrid": [vp, P(FlagParams), vp, P(C.c_int), vp],
         "amr_sync_status": [vp, vp],
         "amr_launch_count": [vp, P(i64)],
+        "amr_trace": [vp, C.c_int],
+        "amr_trace_read": [vp, vp, vp, C.c_int],
         "amr_create_batch": [vp, vp, C.c_int, P(vp)],
         "amr_n_instances": [vp, P(C.c_int)],
         "amr_instance_blocks": [vp, C.c_int, P(i64), P(i64)],
@@ -471,6 +477,17 @@ class Forest:
         n = C.c_int64()
         self._check(self.lib.amr_launch_count(self.h, C.byref(n)), "amr_launch_count")
         return int(n.value)
+
+    def trace(self, on=True):
+        """Per-phase timing on or off (steps then run without a CUDA graph)."""
+        self._check(self.lib.amr_trace(self.h, int(bool(on))), "amr_trace")
+
+    def trace_read(self, reset=True) -> dict:
+        """{phase name: (total ms, records)} of everything traced so far."""
+        ms = np.zeros(len(PHASES), dtype=np.float64)
+        n = np.zeros(len(PHASES), dtype=np.int64)
+        self._check(self.lib.amr_trace_read(self.h, ms.ctypes.data, n.ctypes.data, int(bool(reset))), "amr_trace_read")
+        return {p: (float(ms[i]), int(n[i])) for i, p in enumerate(PHASES)}
 
 
 class Mlp:

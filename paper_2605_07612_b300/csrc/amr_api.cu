@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <cstdlib>
+#include <memory>
 #include <new>
 #include <type_traits>
 #include <string>
@@ -169,6 +170,7 @@ amr_status validate(const amr_config *c, std::string &why) {
 // ------------------------------------------------------------ pattern upload
 amr_status upload_pattern(amr_forest *f) {
     if (f->pattern_rev == f->revision) return AMR_OK;
+    HostSpan span(f, AMR_PHASE_PATTERN_HOST);
     std::string why;
     std::vector<const Forest *> ptrs;
     for (const Forest &F : f->inst) ptrs.push_back(&F);
@@ -283,10 +285,12 @@ amr_status run_stage(amr_forest *f, const amr_stage *stg, cudaStream_t st) {
         // three-pass WENO5 stage on the filled ghost cells (no halo gathering)
         a.gather = 0;
         if ((s = ensure_weno(f)) != AMR_OK) return s;
+        TraceSpan span(f, AMR_PHASE_STAGE, st);
         s = f->cfg.physics == AMR_PHYS_ADVECTION
                 ? launch_weno<real, D, 1>(f, a, static_cast<real *>(f->wprim.p), static_cast<real *>(f->wflux.p), st)
                 : launch_weno<real, D, 0>(f, a, static_cast<real *>(f->wprim.p), static_cast<real *>(f->wflux.p), st);
     } else {
+        TraceSpan span(f, AMR_PHASE_STAGE, st);
         s = launch_stage<real, D>(f, a, st);
     }
     if (s != AMR_OK) return s;
@@ -303,10 +307,12 @@ amr_status run_stage(amr_forest *f, const amr_stage *stg, cudaStream_t st) {
         x.update_dt = stg->update_dt;
         x.gamma = a.gamma;
         const int nface = D == 3 ? f->cfg.block_n * f->cfg.block_n : f->cfg.block_n;
+        TraceSpan span(f, AMR_PHASE_FLUXFIX, st);
         k_fluxfix<real, D><<<nfix, std::max(32, std::min(nface, 1024)), 0, st>>>(x, f->geom);
         ++f->launches;
     }
     if (stg->update_dt) {
+        TraceSpan span(f, AMR_PHASE_DT, st);
         k_dt_commit<<<(n_inst(f) + 31) / 32, 32, 0, st>>>(static_cast<DevScalars *>(f->sc.p),
                                                           static_cast<const double *>(f->cfltab.p), n_inst(f));
         ++f->launches;
@@ -337,6 +343,7 @@ struct StageFn {
 template <class real, int D>
 struct MaxSpeedFn {
     static amr_status run(amr_forest *f, int s, cudaStream_t st) {
+        TraceSpan span(f, AMR_PHASE_DT, st);
         if (nblocks(f) > 0) {
             k_maxspeed<real, D><<<unsigned(nblocks(f)), 256, 0, st>>>(static_cast<const real *>(slot_ptr(f, s)),
                                                                      static_cast<const BlockInfo *>(f->info.p),
@@ -356,6 +363,7 @@ struct ConservedFn {
         amr_status r = ensure(f, f->partial, sizeof(double) * std::max<int64_t>(nblocks(f), 1) * f->cfg.n_var);
         if (r != AMR_OK) return r;
         if ((r = ensure(f, f->sums, sizeof(double) * 8 * size_t(n_inst(f)))) != AMR_OK) return r;
+        TraceSpan span(f, AMR_PHASE_CONSERVED, st);
         if (nblocks(f) > 0) {
             k_conserved_block<real, D><<<unsigned(nblocks(f)), 256, 0, st>>>(static_cast<const real *>(slot_ptr(f, s)),
                                                                             static_cast<const BlockInfo *>(f->info.p),
@@ -375,6 +383,7 @@ amr_status launch_flags(amr_forest *f, int s, const amr_flag_params *p, const in
     const int N = f->cfg.block_n;
     const size_t smem = flags_smem(N, D);
     if (smem > 48 * 1024) CU(cudaFuncSetAttribute(k_flags<real, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    TraceSpan span(f, AMR_PHASE_FLAGS, st);
     k_flags<real, D><<<unsigned(n), unsigned(flags_threads(N)), smem, st>>>(static_cast<const real *>(slot_ptr(f, s)), f->geom,
                                                                          f->cfg.gamma, p->c_refine, p->c_derefine, p->eps,
                                                                          p->eps_abs, out, list);
@@ -402,6 +411,7 @@ struct FeatureFn {
             const size_t smem = features_smem<real, D>(f->cfg.block_n);
             if (smem > 40 * 1024)
                 CU(cudaFuncSetAttribute(k_features<real, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+            TraceSpan span(f, AMR_PHASE_FLAGS, st);
             k_features<real, D><<<unsigned(nblocks(f)), 256, smem, st>>>(static_cast<const real *>(slot_ptr(f, s)),
                                                                     static_cast<const BlockInfo *>(f->info.p), f->geom,
                                                                     f->cfg.gamma, 1.0f / float(ml), x, nblocks(f));
@@ -593,9 +603,14 @@ amr_status amr_destroy_forest(amr_forest *f) {
     if (f->cap_stream) cudaStreamDestroy(f->cap_stream);
     for (DBuf *b : {&f->r1, &f->r2, &f->r1g, &f->info, &f->fix, &f->fix_start, &f->bflux, &f->bcdata, &f->sc, &f->partial, &f->sums,
                     &f->flags, &f->ops, &f->level, &f->dxtab, &f->invdxtab, &f->bctype, &f->bcval, &f->cfltab, &f->ranges,
-                    &f->feat, &f->prob, &f->mflags, &f->flist})
+                    &f->feat, &f->prob, &f->mflags, &f->flist, &f->wprim, &f->wflux})
         dev_free(f, b->p);
     dev_free(f, f->state);
+    for (const TraceRec &t : f->trace_open) {
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    for (cudaEvent_t e : f->ev_free) cudaEventDestroy(e);
     delete f;
     return AMR_OK;
 }
@@ -747,7 +762,7 @@ amr_status amr_step(amr_forest *f, int n_steps, int flags, amr_stream stream) {
     if (r != AMR_OK) return r;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const bool gather = (flags & AMR_STEP_GATHER) != 0;
-    if (!(flags & AMR_STEP_GRAPH)) {
+    if (!(flags & AMR_STEP_GRAPH) || f->tracing) {
         for (int i = 0; i < n_steps; ++i)
             if ((r = rk_step(f, st, gather, flags)) != AMR_OK) return r;
         return AMR_OK;
@@ -838,6 +853,7 @@ amr_status amr_flag_and_regrid(amr_forest *f, const amr_flag_params *p, const in
         else if ((r = amr_flag(f, 0, p, fl.data(), stream)) != AMR_OK) return r;
     }
     // adapt every instance with its slice of the flags (Sec. 2.2)
+    std::unique_ptr<HostSpan> mesh_span(new HostSpan(f, AMR_PHASE_MESH_HOST));
     std::vector<std::vector<Leaf>> nl(static_cast<size_t>(ni));
     std::vector<char> moved(size_t(ni), 0);
     int64_t total = 0;
@@ -862,6 +878,7 @@ amr_status amr_flag_and_regrid(amr_forest *f, const amr_flag_params *p, const in
             if (moved[size_t(i)]) f->inst[size_t(i)].assign(std::move(nl[size_t(i)]));
         set_offsets(f);
         ++f->revision;
+        mesh_span.reset();
         if ((r = upload_pattern(f)) != AMR_OK) return r;
         if (changed) *changed = 1;
         return AMR_OK;
@@ -897,6 +914,7 @@ amr_status amr_flag_and_regrid(amr_forest *f, const amr_flag_params *p, const in
             ops.push_back(op);
         }
     }
+    mesh_span.reset();
     // temporary copy of the old blocks (slot 1 when available)
     void *tmp = nullptr;
     bool own_tmp = false;
@@ -909,8 +927,11 @@ amr_status amr_flag_and_regrid(amr_forest *f, const amr_flag_params *p, const in
         own_tmp = true;
     }
     if ((r = upload(f, f->ops, ops)) != AMR_OK) return r;
-    CU(cudaMemcpyAsync(tmp, slot_ptr(f, 0), old_bytes, cudaMemcpyDeviceToDevice, st));
-    r = dispatch<TransferFn>(f, static_cast<const void *>(tmp), int(total), st);
+    {
+        TraceSpan span(f, AMR_PHASE_TRANSFER, st);
+        CU(cudaMemcpyAsync(tmp, slot_ptr(f, 0), old_bytes, cudaMemcpyDeviceToDevice, st));
+        r = dispatch<TransferFn>(f, static_cast<const void *>(tmp), int(total), st);
+    }
     if (own_tmp) {
         cudaStreamSynchronize(st);
         dev_free(f, tmp);
@@ -1003,6 +1024,13 @@ amr_status amr_autotune(amr_forest *f, int *choice, double *best_ms, amr_stream 
     amr_status r = upload_pattern(f);
     if (r != AMR_OK) return r;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // the candidates' timings are not phases of a step: tracing pauses
+    struct Pause {
+        amr_forest *f;
+        bool was;
+        ~Pause() { f->tracing = was; }
+    } pause{f, f->tracing};
+    f->tracing = false;
     // candidates: blocks (tiles) per CTA 1, 2, 4 or a persistent grid, for
     // each kernel / staging tile: the FP32 pair kernel (2D or 3D) with tile
     // 16 and, for blocks above 8 cells a side, tile 8, or the FP32 advection
@@ -1415,6 +1443,26 @@ const char *amr_last_error(const amr_forest *f) { return f ? f->err.c_str() : "n
 amr_status amr_launch_count(const amr_forest *f, int64_t *n) {
     if (!f || !n) return AMR_EINVAL;
     *n = f->launches;
+    return AMR_OK;
+}
+
+amr_status amr_trace(amr_forest *f, int on) {
+    if (!f) return AMR_EINVAL;
+    f->tracing = on != 0;
+    return AMR_OK;
+}
+
+amr_status amr_trace_read(amr_forest *f, double *ms, int64_t *count, int reset) {
+    if (!f) return AMR_EINVAL;
+    trace_drain(f);
+    for (int p = 0; p < AMR_N_PHASES; ++p) {
+        if (ms) ms[p] = f->trace_ms[p];
+        if (count) count[p] = f->trace_n[p];
+        if (reset) {
+            f->trace_ms[p] = 0.0;
+            f->trace_n[p] = 0;
+        }
+    }
     return AMR_OK;
 }
 

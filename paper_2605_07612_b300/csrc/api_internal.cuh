@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cstdarg>
 #include <cstdint>
 #include <cstdio>
@@ -21,6 +22,12 @@ namespace amrb {
 struct DBuf {
     void *p = nullptr;
     size_t cap = 0;
+};
+
+// one timed device phase: events recorded on the launch stream around it
+struct TraceRec {
+    int phase;
+    cudaEvent_t a, b;
 };
 
 }  // namespace amrb
@@ -53,6 +60,11 @@ struct amr_forest {
     int n_sms = 0;
     bool capturing = false;
     int64_t launches = 0;
+    bool tracing = false;                      // per-phase timing on (steps then run without a graph)
+    std::vector<cudaEvent_t> ev_free;          // timing events ready for reuse
+    std::vector<amrb::TraceRec> trace_open;    // recorded phases not yet added to the totals
+    double trace_ms[AMR_N_PHASES] = {};
+    int64_t trace_n[AMR_N_PHASES] = {};
     std::string err;
 };
 
@@ -78,6 +90,83 @@ inline amr_status fail(amr_forest *f, amr_status s, const char *fmt, ...) {
 
 inline int64_t nblocks(const amr_forest *f) { return f->offset.empty() ? 0 : f->offset.back(); }
 inline int n_inst(const amr_forest *f) { return int(f->inst.size()); }
+
+// ---- per-phase timing (tracing): device phases by CUDA events, host phases
+// by the wall clock
+inline void trace_drain(amr_forest *f) {
+    for (const TraceRec &t : f->trace_open) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(t.b) == cudaSuccess && cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) {
+            f->trace_ms[t.phase] += double(ms);
+            f->trace_n[t.phase] += 1;
+        }
+        f->ev_free.push_back(t.a);
+        f->ev_free.push_back(t.b);
+    }
+    f->trace_open.clear();
+}
+
+inline cudaEvent_t trace_event(amr_forest *f) {
+    if (!f->ev_free.empty()) {
+        cudaEvent_t e = f->ev_free.back();
+        f->ev_free.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    return cudaEventCreate(&e) == cudaSuccess ? e : nullptr;
+}
+
+// Times the launches issued during its lifetime on stream st as one record of
+// `phase`; does nothing unless tracing is on and st is not being captured.
+class TraceSpan {
+  public:
+    TraceSpan(amr_forest *f, int phase, cudaStream_t st) : f_(f), st_(st), phase_(phase) {
+        if (!f->tracing) return;
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+        a_ = trace_event(f);
+        if (a_ && cudaEventRecord(a_, st) != cudaSuccess) {
+            f->ev_free.push_back(a_);
+            a_ = nullptr;
+        }
+    }
+    ~TraceSpan() {
+        if (!a_) return;
+        cudaEvent_t b = trace_event(f_);
+        if (!b || cudaEventRecord(b, st_) != cudaSuccess) {
+            f_->ev_free.push_back(a_);
+            if (b) f_->ev_free.push_back(b);
+            return;
+        }
+        f_->trace_open.push_back({phase_, a_, b});
+        if (f_->trace_open.size() >= 4096) trace_drain(f_);   // bounded: a long traced run syncs now and then
+    }
+    TraceSpan(const TraceSpan &) = delete;
+    TraceSpan &operator=(const TraceSpan &) = delete;
+
+  private:
+    amr_forest *f_;
+    cudaStream_t st_;
+    int phase_;
+    cudaEvent_t a_ = nullptr;
+};
+
+class HostSpan {
+  public:
+    HostSpan(amr_forest *f, int phase) : f_(f), phase_(phase), t0_(std::chrono::steady_clock::now()) {}
+    ~HostSpan() {
+        if (!f_->tracing) return;
+        f_->trace_ms[phase_] += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0_).count();
+        f_->trace_n[phase_] += 1;
+    }
+    HostSpan(const HostSpan &) = delete;
+    HostSpan &operator=(const HostSpan &) = delete;
+
+  private:
+    amr_forest *f_;
+    int phase_;
+    std::chrono::steady_clock::time_point t0_;
+};
 
 // grid of a stage launch for `items` (block, tile) items under the forest's tuning
 inline int64_t stage_grid(const amr_forest *f, int64_t items, int occupancy) {

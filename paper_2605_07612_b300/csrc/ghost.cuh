@@ -1,6 +1,9 @@
-// Ghost-pattern executor (Sec. 2.6).  One warp per pattern entry ("strip");
-// the lanes walk the strip's ghost cells with x fastest so that both the
-// gather and the scatter are coalesced along rows.  Round 1 executes SRL,
+// Ghost-pattern executor (Sec. 2.6).  `parts` warps per pattern entry
+// ("strip"), each taking every parts-th group of 128 values (32 for edge and
+// corner regions), so that a few large strips (a boundary face of 32^3
+// blocks) still spread over many warps; the lanes walk the strip's ghost
+// cells with x fastest so that both the gather and the scatter are coalesced
+// along rows.  Round 1 executes SRL,
 // F2C and BC entries (they read interior cells only); round 2 executes C2F
 // entries, whose limited prolongation reads round-1 ghosts of the coarse
 // block (the tangential neighbours at the face edge and the ghost layer
@@ -18,6 +21,7 @@ struct GhostArgs {
     real *u;                 // state slot, max_blocks blocks
     const Entry *list;
     int n;
+    int parts;               // warps per entry
     const real *bcdata;      // [n_bc][V][N^(D-1)]
     const int32_t *bc_type;  // [instance][6]
     const real *bc_val;      // [instance][6][8]
@@ -63,7 +67,7 @@ __device__ __forceinline__ real prolong_at(const real *cb, const Geom &g, int ci
 // aligned).  ND = face-normal dimension.  Each lane keeps 4 independent
 // loads in flight before storing.
 template <class real, int D, int N, int NG, int ND>
-__device__ __forceinline__ void srl_pairs(real *dstb, const real *srcb, int side, int lane, int V) {
+__device__ __forceinline__ void srl_pairs(real *dstb, const real *srcb, int side, int lane, int part, int parts, int V) {
     using V2 = typename Vec2<real>::type;
     constexpr int S = N + 2 * NG;
     constexpr int64_t NCc = (D == 3) ? int64_t(S) * S * S : int64_t(S) * S;
@@ -74,7 +78,7 @@ __device__ __forceinline__ void srl_pairs(real *dstb, const real *srcb, int side
     auto cidx = [](int i, int j, int k) -> int64_t {
         return (int64_t(D == 3 ? k + NG : 0) * S + (j + NG)) * S + (i + NG);
     };
-    for (int base = lane; base < TOTAL; base += 128) {
+    for (int base = lane + 128 * part; base < TOTAL; base += 128 * parts) {
         V2 val[4];
         int64_t od[4];
 #pragma unroll
@@ -116,7 +120,7 @@ __device__ __forceinline__ void srl_pairs(real *dstb, const real *srcb, int side
 // the face along each tangential dimension).
 template <class real, int D, int N, int NG, int ND, bool HALF>
 __device__ __forceinline__ void ghost_strip(const GhostArgs<real> &a, const Geom &g, const Entry &e, real *dstb,
-                                            const real *srcb, int lane) {
+                                            const real *srcb, int lane, int part) {
     constexpr int ng = NG;
     constexpr int nd = ND;
     // tangential dimensions (lower first) and the strip's extents, fixed at
@@ -141,7 +145,7 @@ __device__ __forceinline__ void ghost_strip(const GhostArgs<real> &a, const Geom
     const int total = ncells * g.V;
     // four values per lane per round: all their loads are issued before
     // the first store, so a warp keeps several loads in flight
-    for (int base = lane; base < total; base += 128) {
+    for (int base = lane + 128 * part; base < total; base += 128 * a.parts) {
         real vals[4];
         int64_t dsti[4];
 #pragma unroll
@@ -206,8 +210,9 @@ __device__ __forceinline__ void ghost_strip(const GhostArgs<real> &a, const Geom
 
 template <class real, int D, int N, int NG>
 __global__ void __launch_bounds__(256) k_ghost(GhostArgs<real> a, Geom g) {
-    const int warp = int((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int gw = int((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
+    const int warp = gw / a.parts, part = gw - warp * a.parts;
     if (warp >= a.n) return;
     const Entry e = a.list[warp];
     real *dstb = a.u + int64_t(e.dst) * g.bstride;
@@ -229,7 +234,7 @@ __global__ void __launch_bounds__(256) k_ghost(GhostArgs<real> a, Geom g) {
             }
         }
         const int ncells = ext[0] * ext[1] * ext[2];
-        for (int idx = lane; idx < ncells * g.V; idx += 32) {
+        for (int idx = lane + 32 * part; idx < ncells * g.V; idx += 32 * a.parts) {
             const int v = idx / ncells;
             int c = idx - v * ncells;
             int x[3];
@@ -267,23 +272,23 @@ __global__ void __launch_bounds__(256) k_ghost(GhostArgs<real> a, Geom g) {
     const int nd = e.face >> 1, side = e.face & 1;
     if constexpr (NG % 2 == 0) {
         if (e.kind == KIND_SRL) {
-            if (nd == 0) srl_pairs<real, D, N, NG, 0>(dstb, srcb, side, lane, g.V);
-            else if (nd == 1 || D == 2) srl_pairs<real, D, N, NG, 1>(dstb, srcb, side, lane, g.V);
-            else srl_pairs<real, D, N, NG, (D == 3 ? 2 : 1)>(dstb, srcb, side, lane, g.V);
+            if (nd == 0) srl_pairs<real, D, N, NG, 0>(dstb, srcb, side, lane, part, a.parts, g.V);
+            else if (nd == 1 || D == 2) srl_pairs<real, D, N, NG, 1>(dstb, srcb, side, lane, part, a.parts, g.V);
+            else srl_pairs<real, D, N, NG, (D == 3 ? 2 : 1)>(dstb, srcb, side, lane, part, a.parts, g.V);
             return;
         }
     }
     // the general path, with the strip shape fixed per normal and kind
     const bool half = e.kind == KIND_F2C;
     if (nd == 0) {
-        if (half) ghost_strip<real, D, N, NG, 0, true>(a, g, e, dstb, srcb, lane);
-        else ghost_strip<real, D, N, NG, 0, false>(a, g, e, dstb, srcb, lane);
+        if (half) ghost_strip<real, D, N, NG, 0, true>(a, g, e, dstb, srcb, lane, part);
+        else ghost_strip<real, D, N, NG, 0, false>(a, g, e, dstb, srcb, lane, part);
     } else if (nd == 1 || D == 2) {
-        if (half) ghost_strip<real, D, N, NG, 1, true>(a, g, e, dstb, srcb, lane);
-        else ghost_strip<real, D, N, NG, 1, false>(a, g, e, dstb, srcb, lane);
+        if (half) ghost_strip<real, D, N, NG, 1, true>(a, g, e, dstb, srcb, lane, part);
+        else ghost_strip<real, D, N, NG, 1, false>(a, g, e, dstb, srcb, lane, part);
     } else {
-        if (half) ghost_strip<real, D, N, NG, (D == 3 ? 2 : 1), true>(a, g, e, dstb, srcb, lane);
-        else ghost_strip<real, D, N, NG, (D == 3 ? 2 : 1), false>(a, g, e, dstb, srcb, lane);
+        if (half) ghost_strip<real, D, N, NG, (D == 3 ? 2 : 1), true>(a, g, e, dstb, srcb, lane, part);
+        else ghost_strip<real, D, N, NG, (D == 3 ? 2 : 1), false>(a, g, e, dstb, srcb, lane, part);
     }
 }
 

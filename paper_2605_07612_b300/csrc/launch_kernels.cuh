@@ -41,12 +41,16 @@ amr_status launch_ghosts(amr_forest *f, int s, cudaStream_t st, bool gather) {
         if (lst.empty()) continue;
         a.list = static_cast<const Entry *>(round == 0 ? (gather ? f->r1g.p : f->r1.p) : f->r2.p);
         a.n = int(lst.size());
-        const int grid = (a.n + 7) / 8;
         const int N = f->cfg.block_n, NG = f->cfg.n_ghost;
+        // warps per strip: about 512 values of a full face strip each
+        const int64_t face_vals = int64_t(D == 3 ? N * N : N) * NG * f->cfg.n_var;
+        a.parts = int(std::max<int64_t>(1, std::min<int64_t>(32, face_vals / 512)));
+        const int64_t grid = (int64_t(a.n) * a.parts + 7) / 8;
+        TraceSpan span(f, round == 0 ? AMR_PHASE_GHOST_R1 : AMR_PHASE_GHOST_R2, st);
         bool launched = false;
 #define AMR_GHOST_CASE(n_, g_)                                                   \
     if (!launched && N == n_ && NG == g_) {                                     \
-        k_ghost<real, D, n_, g_><<<grid, 256, 0, st>>>(a, f->geom);             \
+        k_ghost<real, D, n_, g_><<<unsigned(grid), 256, 0, st>>>(a, f->geom);             \
         launched = true;                                                        \
     }
         AMR_GHOST_CASE(8, 1) AMR_GHOST_CASE(8, 2) AMR_GHOST_CASE(8, 3) AMR_GHOST_CASE(8, 4)

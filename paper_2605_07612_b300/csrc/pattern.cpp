@@ -147,6 +147,11 @@ bool build_pattern(const std::vector<const Forest *> &inst, const std::vector<in
             if (e.kind == KIND_F2C) P.info[e.dst].fixmask |= 1 << e.face;
         }
     }
+    // execution order: by receiving block, so that the strips on both sides
+    // of a face (which share the 32-byte sectors of the rows they touch)
+    // run close together in time and meet in L2
+    for (std::vector<Entry> *l : {&P.round1, &P.round2, &P.round1_gather})
+        std::stable_sort(l->begin(), l->end(), [](const Entry &x, const Entry &y) { return x.dst < y.dst; });
     // fix-up faces: every (coarse block, face) with F2C sources
     for (const Entry &e : P.entries) {
         if (e.kind != KIND_F2C) continue;

@@ -230,3 +230,30 @@ def test_advection_config_validation_and_checkpoint(tmp_path):
     g = amr.Forest.load(str(path), host_only=True)
     assert g.spec.physics == 1 and tuple(g.spec.velocity) == (1.0, -0.5, 0.25) and g.spec.nvar == 1
     np.testing.assert_array_equal(f.pattern(), g.pattern())
+
+
+def test_trace_times_host_phases_of_a_regrid():
+    """Per-phase timing on a host-only forest: a regrid adds one mesh-host
+    record and one pattern-build record; nothing is recorded while tracing is
+    off, and reading with reset clears the totals."""
+    sp = synth.MeshSpec(ndim=2, N=8, ng=2, ntrees=(4, 4, 1), max_level=2)
+    f = amr.Forest(sp, 0, max_blocks=1024, host_only=True)
+    flags = np.zeros(f.n, dtype=np.int8)
+    flags[:3] = 1
+    f.regrid(flags)                               # untraced
+    t = f.trace_read()
+    assert set(t) == set(amr.PHASES) and all(v == (0.0, 0) for v in t.values())
+    f.trace(True)
+    flags = np.zeros(f.n, dtype=np.int8)
+    flags[-2:] = 1
+    assert f.regrid(flags)
+    t = f.trace_read(reset=False)
+    assert t["mesh_host"][1] == 1 and t["pattern_host"][1] == 1
+    assert t["mesh_host"][0] >= 0.0 and t["pattern_host"][0] > 0.0
+    assert all(t[p][1] == 0 for p in amr.PHASES if not p.endswith("_host"))
+    f.trace(False)
+    flags = np.zeros(f.n, dtype=np.int8)
+    flags[0] = 1
+    f.regrid(flags)
+    assert f.trace_read() == t                    # off: unchanged; read and reset
+    assert all(v == (0.0, 0) for v in f.trace_read().values())

@@ -114,3 +114,21 @@ def test_failed_regrid_keeps_mesh_and_data():
     np.testing.assert_array_equal(interior(sp, f.get_state(0)), interior(sp, ref.get_state(0)))
     f.close()
     assert not inj.live
+
+
+def test_weno5_scratch_is_returned():
+    """The WENO5 stage's scratch (primitives and face fluxes of every block),
+    allocated on first use, goes back through the hook when the forest is
+    destroyed."""
+    sp = synth.MeshSpec(ndim=2, N=16, ng=3, ntrees=(4, 4, 1), limiter=3)
+    inj = Injector()
+    f = amr.Forest(sp, 0, config=inj.config(sp, 64, precision=64))
+    n0 = len(inj.live)
+    lev, g = f.blocks()
+    f.set_state(0, synth.kelvin_helmholtz(sp, lev, g, seed=43))
+    f.compute_dt(0)
+    f.step(1)
+    assert f.sync_status() == amr.AMR_OK
+    assert len(inj.live) > n0
+    f.close()
+    assert not inj.live
