@@ -350,7 +350,7 @@ def run_ours(args, rank, world, dist):
             nrt = max(2, args.steps // (2 if prec == 32 else 8))
             msr, _ = time_steps(fr, nrt, 1, prec == 32, False)
             rtw["%d^3 fp%d" % (bn, prec)] = {"value": 2.0 * cells * nrt * world / (msr * 1e-3), "ms_per_step": msr / nrt,
-                                              "status": fr.sync_status()}
+                                              "status": fr.sync_status(), "phases": phase_breakdown(fr, stream, False)}
             del fr
             torch.cuda.empty_cache()
         rtw["context"] = "paper, 1x H100, FP64: 0.48 GCUPS for 16^3 blocks (Table 1)"
@@ -702,7 +702,12 @@ def run_ncu_case(which="stage"):
     420 MB per state slot, above L2), FP32, Kelvin-Helmholtz -- exactly two
     2D stage launches.  advection: one Heun step of the 256^3 scalar
     advection case in 16^3 blocks (van Leer, FP32) -- exactly two advection
-    block-kernel launches.  batched2d: the 64 batched 2D meshes refined as in
+    block-kernel launches.  ghost3d: one full ghost fill of the 256^3
+    periodic mesh of 16^3 blocks (24,576 same-level strips, 655 MB per state
+    slot), FP32 -- exactly one ghost launch.  weno: one Heun step of the
+    256^3 Rayleigh-Taylor case in 16^3 blocks with WENO5 (three ghost
+    layers), FP32 -- per stage one ghost fill and the three WENO5 passes.
+    batched2d: the 64 batched 2D meshes refined as in
     the bench (three regrids, five ghost launches), then one Heun step with
     4 items per CTA -- two ghost rounds and one stage launch per stage."""
     import torch
@@ -753,6 +758,30 @@ def run_ncu_case(which="stage"):
         f.set_state(0, synth.kelvin_helmholtz(sp, lev, g).astype(np.float32))
         f.compute_dt(0)
         f.step(1, use_graph=False, gather=True)
+        torch.cuda.synchronize()
+        st = f.sync_status()
+        if st != amr.AMR_OK:
+            raise SystemExit("device status %d" % st)
+        return
+    if which == "weno":
+        sp = synth.rayleigh_taylor_spec(ndim=3, N=16, limiter=3)
+        f = amr.Forest(sp, 0, precision=32)
+        lev, g = f.blocks()
+        f.set_state(0, synth.rayleigh_taylor(sp, lev, g).astype(np.float32))
+        f.compute_dt(0)
+        f.step(1, use_graph=False)
+        torch.cuda.synchronize()
+        st = f.sync_status()
+        if st != amr.AMR_OK:
+            raise SystemExit("device status %d" % st)
+        return
+    if which == "ghost3d":
+        sp = workload_spec(16)
+        f = amr.Forest(sp, 0, precision=32)
+        lev, g = f.blocks()
+        f.set_state(0, synth.fourier3d(sp, lev, g, seed=1).astype(np.float32))
+        torch.cuda.synchronize()
+        f.fill_ghosts(0)
         torch.cuda.synchronize()
         st = f.sync_status()
         if st != amr.AMR_OK:
@@ -842,9 +871,10 @@ def main():
     ap.add_argument("--workload", default="uniform", choices=["uniform", "amr_static", "adaptive"],
                     help="uniform: the headline line; the others print their own JSON line")
     ap.add_argument("--adaptive-steps", type=int, default=500)
-    ap.add_argument("--ncu-case", nargs="?", const="stage", default=None, choices=["stage", "ghost", "stage2d", "advection", "batched2d"],
+    ap.add_argument("--ncu-case", nargs="?", const="stage", default=None, choices=["stage", "ghost", "ghost3d", "weno", "stage2d", "advection", "batched2d"],
                     help="run one Heun step of the headline workload (stage), one ghost fill of a 3-level mesh "
-                         "(ghost), one Heun step of a uniform 4096^2 2D mesh (stage2d), of the 256^3 advection case "
+                         "(ghost) or of the uniform 256^3 mesh (ghost3d), one WENO5 Heun step of the 256^3 Rayleigh-Taylor "
+                         "case (weno), one Heun step of a uniform 4096^2 2D mesh (stage2d), of the 256^3 advection case "
                          "(advection) or of the batched 2D meshes (batched2d) and exit, for ncu captures")
     args = ap.parse_args()
     if args.ncu_case:

@@ -242,15 +242,13 @@ amr_status launch_stage(amr_forest *f, const StageArgs<real> &a, cudaStream_t st
     return fail(f, AMR_EINVAL, "the Euler stage needs n_ghost 2 or 3 (got %d)", NG);
 }
 
-// scratch of the WENO5 stage (primitives and face fluxes of every block);
-// allocated outside stream capture
+// scratch of the WENO5 stage (face fluxes of every block); allocated
+// outside stream capture
 amr_status ensure_weno(amr_forest *f) {
     if (f->cfg.limiter != AMR_LIM_WENO5) return AMR_OK;
     const int N = f->cfg.block_n, D = f->cfg.ndim;
     const size_t nfl = size_t(D) * size_t(f->cfg.n_var) * size_t(N + 1) * size_t(D == 3 ? N * N : N);
     const size_t nb = size_t(std::max<int64_t>(nblocks(f), 1));
-    amr_status s = ensure(f, f->wprim, nb * f->block_bytes);
-    if (s != AMR_OK) return s;
     return ensure(f, f->wflux, nb * nfl * size_t(f->esize));
 }
 
@@ -287,8 +285,8 @@ amr_status run_stage(amr_forest *f, const amr_stage *stg, cudaStream_t st) {
         if ((s = ensure_weno(f)) != AMR_OK) return s;
         TraceSpan span(f, AMR_PHASE_STAGE, st);
         s = f->cfg.physics == AMR_PHYS_ADVECTION
-                ? launch_weno<real, D, 1>(f, a, static_cast<real *>(f->wprim.p), static_cast<real *>(f->wflux.p), st)
-                : launch_weno<real, D, 0>(f, a, static_cast<real *>(f->wprim.p), static_cast<real *>(f->wflux.p), st);
+                ? launch_weno<real, D, 1>(f, a, static_cast<real *>(f->wflux.p), st)
+                : launch_weno<real, D, 0>(f, a, static_cast<real *>(f->wflux.p), st);
     } else {
         TraceSpan span(f, AMR_PHASE_STAGE, st);
         s = launch_stage<real, D>(f, a, st);
@@ -603,7 +601,7 @@ amr_status amr_destroy_forest(amr_forest *f) {
     if (f->cap_stream) cudaStreamDestroy(f->cap_stream);
     for (DBuf *b : {&f->r1, &f->r2, &f->r1g, &f->info, &f->fix, &f->fix_start, &f->bflux, &f->bcdata, &f->sc, &f->partial, &f->sums,
                     &f->flags, &f->ops, &f->level, &f->dxtab, &f->invdxtab, &f->bctype, &f->bcval, &f->cfltab, &f->ranges,
-                    &f->feat, &f->prob, &f->mflags, &f->flist, &f->wprim, &f->wflux})
+                    &f->feat, &f->prob, &f->mflags, &f->flist, &f->wflux})
         dev_free(f, b->p);
     dev_free(f, f->state);
     for (const TraceRec &t : f->trace_open) {

@@ -47,7 +47,7 @@ struct amr_forest {
     amrb::DBuf r1, r2, r1g, info, fix, fix_start, bflux, bcdata, sc, partial, sums, flags, ops, level;
     amrb::DBuf dxtab, invdxtab, bctype, bcval, cfltab, ranges;   // per-instance tables
     amrb::DBuf feat, prob, mflags, flist;                        // learned-flag predictor
-    amrb::DBuf wprim, wflux;                                     // WENO5 stage scratch
+    amrb::DBuf wflux;                                            // WENO5 stage scratch (face fluxes)
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t gexec = nullptr;
     uint64_t graph_rev = ~0ull;
@@ -186,6 +186,6 @@ amr_status launch_stage_pair(amr_forest *f, const StageArgs<float> &a, cudaStrea
 template <int D, int N>
 amr_status launch_adv_pair(amr_forest *f, const StageArgs<float> &a, cudaStream_t st);
 template <class real, int D, int PH>
-amr_status launch_weno(amr_forest *f, const StageArgs<real> &a, real *prim, real *flux, cudaStream_t st);
+amr_status launch_weno(amr_forest *f, const StageArgs<real> &a, real *flux, cudaStream_t st);
 
 }  // namespace amrb

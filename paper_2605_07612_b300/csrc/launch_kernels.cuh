@@ -185,26 +185,20 @@ amr_status launch_adv_pair(amr_forest *f, const StageArgs<float> &a, cudaStream_
     return launch_adv_pair_l<D, N, 0>(f, a, st);
 }
 
-// WENO5 stage: primitives (Euler only), face fluxes, update (three or two
-// launches); prim and flux are scratch buffers of n_blocks x bstride and
-// n_blocks x D x V x (N+1) N^(D-1) elements
+// WENO5 stage: face fluxes, then the update (two launches); flux is a
+// scratch buffer of n_blocks x D x V x (N+1) N^(D-1) elements
 template <class real, int D, int PH>
-amr_status launch_weno(amr_forest *f, const StageArgs<real> &a, real *prim, real *flux, cudaStream_t st) {
+amr_status launch_weno(amr_forest *f, const StageArgs<real> &a, real *flux, cudaStream_t st) {
     const int64_t nb = nblocks(f);
     if (nb > 0) {
         const int N = f->cfg.block_n;
-        const int nfaces = D * (N + 1) * (D == 3 ? N * N : N);
+        const int npen = D * (D == 3 ? N * N : N);   // pencils of faces (one thread each)
         const int ncint = D == 3 ? N * N * N : N * N;
         const PhysCtx<real> pc{a.gamma, real(1) / (a.gamma - real(1)), {a.vel[0], a.vel[1], a.vel[2]}};
-        const real *w = a.deriv;       // scalar advection: the state is its own primitive
-        if (PH == 0) {
-            k_weno_prim<real, D><<<unsigned(nb), 256, 0, st>>>(a.deriv, prim, f->geom, a.gamma);
-            ++f->launches;
-            w = prim;
-        }
-        k_weno_flux<real, D, PH><<<dim3(unsigned(nb), unsigned((nfaces + 255) / 256)), 256, 0, st>>>(
-            w, flux, a.info, a.bflux, f->geom, pc, a.flux, a.sc);
-        k_weno_update<real, D, PH><<<dim3(unsigned(nb), unsigned((ncint + 255) / 256)), 256, 0, st>>>(a, flux, f->geom);
+        // one-dimensional grids: a block's chunks are consecutive CTAs
+        k_weno_flux<real, D, PH><<<unsigned(nb * ((npen + 255) / 256)), 256, 0, st>>>(a.deriv, flux, a.info, a.bflux,
+                                                                                   f->geom, pc, a.flux, a.sc);
+        k_weno_update<real, D, PH><<<unsigned(nb * ((ncint + 255) / 256)), 256, 0, st>>>(a, flux, f->geom);
         f->launches += 2;
     }
     CU(cudaGetLastError());

@@ -1,12 +1,12 @@
 // Finite-volume stage with WENO5 face reconstruction (Sec. 3.2 lists WENO5
 // among the limiters; it needs three ghost layers), for Euler and for scalar
 // advection.  The same sub-step of
-// Eq. 5 as stage.cuh, split into three passes over global memory because the
+// Eq. 5 as stage.cuh, split into two passes over global memory because the
 // five-cell stencils do not fit the two-cell halo of the plane-ring kernels:
-//   k_weno_prim    primitives of every cell of every block (incl. ghosts)
-//   k_weno_flux    one thread per face: WENO5 states from the six cells
-//                  around the face, Rusanov or HLL flux; block-boundary faces
-//                  also go to the refinement-face flux slots
+//   k_weno_flux    one thread per pencil of faces along a direction:
+//                  primitives of each cell as it is loaded, WENO5 states of
+//                  each cell's two faces, Rusanov or HLL flux; block-boundary
+//                  faces also go to the refinement-face flux slots
 //   k_weno_update  one thread per cell: flux divergence, gravity source,
 //                  combination with the previous states, CFL speed.
 // WENO5 (Jiang & Shu 1996): candidates q_k of third order, smoothness beta_k,
@@ -19,11 +19,21 @@
 
 namespace amrb {
 
+// WENO5 values at both faces of the centre cell c of the stencil
+// (a, b, c, d, e) = cells i-2 .. i+2: `right` at face i+1/2 from the
+// candidates of the left-biased stencils, `left` at face i-1/2 from their
+// mirror images.  The smoothness indicators beta_k of the three 3-cell
+// sub-stencils serve both values (the mirror image swaps beta_0 and
+// beta_2), so a cell's stencil is evaluated once for its two faces.
 template <class real>
-__device__ __forceinline__ real weno5_face(real a, real b, real c, real d, real e) {
-    const real q0 = (real(2) * a - real(7) * b + real(11) * c) * real(1.0 / 6.0);
-    const real q1 = (-b + real(5) * c + real(2) * d) * real(1.0 / 6.0);
-    const real q2 = (real(2) * c + real(5) * d - e) * real(1.0 / 6.0);
+__device__ __forceinline__ void weno5_cell(real a, real b, real c, real d, real e, real &left, real &right) {
+    const real r6 = real(1.0 / 6.0);
+    const real q0 = (real(2) * a - real(7) * b + real(11) * c) * r6;
+    const real q1 = (-b + real(5) * c + real(2) * d) * r6;
+    const real q2 = (real(2) * c + real(5) * d - e) * r6;
+    const real p0 = (real(2) * e - real(7) * d + real(11) * c) * r6;   // mirror images
+    const real p1 = (-d + real(5) * c + real(2) * b) * r6;
+    const real p2 = (real(2) * c + real(5) * b - a) * r6;
     const real t0 = a - real(2) * b + c, u0 = a - real(4) * b + real(3) * c;
     const real t1 = b - real(2) * c + d, u1 = b - d;
     const real t2 = c - real(2) * d + e, u2 = real(3) * c - real(4) * d + e;
@@ -33,46 +43,33 @@ __device__ __forceinline__ real weno5_face(real a, real b, real c, real d, real 
     const real b2 = k * t2 * t2 + real(0.25) * u2 * u2;
     const real eps = real(1e-6);
     if constexpr (std::is_same<real, double>::value) {
-        // one division instead of four: numerator and denominator times
+        // one division per value instead of four: weights times
         // s0 s1 s2, s_k = (eps + beta_k)^2 (FP64 divisions are slow here; the
         // products stay far inside the FP64 range for any finite state)
         const real s0 = (eps + b0) * (eps + b0), s1 = (eps + b1) * (eps + b1), s2 = (eps + b2) * (eps + b2);
-        const real a0 = real(0.1) * (s1 * s2), a1 = real(0.6) * (s0 * s2), a2 = real(0.3) * (s0 * s1);
-        return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+        const real s12 = s1 * s2, s02 = s0 * s2, s01 = s0 * s1;
+        const real a0 = real(0.1) * s12, a1 = real(0.6) * s02, a2 = real(0.3) * s01;
+        right = (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+        const real m0 = real(0.1) * s01, m1 = real(0.6) * s02, m2 = real(0.3) * s12;
+        left = (m0 * p0 + m1 * p1 + m2 * p2) / (m0 + m1 + m2);
     } else {
         // FP32: approximate reciprocals (the weights are normalised, so their
         // few-ulp error stays a few ulp of the face value)
-        const real a0 = real(0.1) * rcp_ftz((eps + b0) * (eps + b0));
-        const real a1 = real(0.6) * rcp_ftz((eps + b1) * (eps + b1));
-        const real a2 = real(0.3) * rcp_ftz((eps + b2) * (eps + b2));
-        return (a0 * q0 + a1 * q1 + a2 * q2) * rcp_ftz(a0 + a1 + a2);
+        const real s0 = rcp_ftz((eps + b0) * (eps + b0));
+        const real s1 = rcp_ftz((eps + b1) * (eps + b1));
+        const real s2 = rcp_ftz((eps + b2) * (eps + b2));
+        const real a0 = real(0.1) * s0, a1 = real(0.6) * s1, a2 = real(0.3) * s2;
+        right = (a0 * q0 + a1 * q1 + a2 * q2) * rcp_ftz(a0 + a1 + a2);
+        const real m0 = real(0.1) * s2, m1 = real(0.6) * s1, m2 = real(0.3) * s0;
+        left = (m0 * p0 + m1 * p1 + m2 * p2) * rcp_ftz(m0 + m1 + m2);
     }
 }
 
-// primitives of all S^D cells of every block: prim[b][v][cell] (Euler only:
-// for scalar advection they are the state itself)
-template <class real, int D>
-__global__ void __launch_bounds__(256) k_weno_prim(const real *__restrict__ u, real *__restrict__ prim, Geom g, real gam) {
-    using E = Euler<real, D>;
-    const int b = blockIdx.x;
-    const real *ub = u + int64_t(b) * g.bstride;
-    real *pb = prim + int64_t(b) * g.bstride;
-    for (int64_t c = threadIdx.x; c < g.ncell; c += blockDim.x) {
-        real U[D + 2], w[D + 2];
-#pragma unroll
-        for (int v = 0; v < D + 2; ++v) U[v] = ub[int64_t(v) * g.ncell + c];
-        E::prim(U, w, gam);
-#pragma unroll
-        for (int v = 0; v < D + 2; ++v) pb[int64_t(v) * g.ncell + c] = w[v];
-    }
-}
-
-// Faces of a block: q < D (N+1) N^(D-1); direction n = q / nf, and within
-// a direction the faces are numbered with x fastest whatever the normal, so
-// that a warp's loads and stores run along rows: r = fp + (N+1)(y + N z)
-// for x-faces, x + N (fp + (N+1) z) for y-faces, x + N (y + N fp) for
-// z-faces (fp: face position along the normal, between cells fp-1 and fp).
-// flux[b][n][v][r].  blockIdx.x = block, blockIdx.y = chunk of 256 faces.
+// Faces of a block: D (N+1) N^(D-1), N+1 positions fp per direction n
+// (fp between cells fp-1 and fp) and N^(D-1) tangential positions.  Within
+// a direction the faces are numbered with x fastest whatever the normal:
+// r = fp + (N+1)(y + N z) for x-faces, x + N (fp + (N+1) z) for y-faces,
+// x + N (y + N fp) for z-faces; flux[b][n][v][r].
 template <int D>
 __device__ __forceinline__ int weno_face_index(int n, int fp, const int *x, int N) {
     if (n == 0) return fp + (N + 1) * (x[1] + N * x[2]);
@@ -80,71 +77,100 @@ __device__ __forceinline__ int weno_face_index(int n, int fp, const int *x, int 
     return x[0] + N * (x[1] + N * fp);
 }
 
+// One thread per pencil: the N+1 faces of one direction n at one tangential
+// position t, marched along n with the five-cell stencil of the current
+// cell in registers (one load per variable and cell, each cell's WENO5
+// stencil evaluated once for its two faces).  Consecutive threads take
+// consecutive tangential positions, so the y and z pencils load and store
+// along rows.  The CTAs of one block are adjacent (blockIdx.x = block x
+// chunks + chunk), so a block's cells come from DRAM once.  Each loaded cell
+// is converted to primitives (once per direction).
+// Block-boundary faces also go to the refinement-face flux slots.
 template <class real, int D, int PH>
-__global__ void __launch_bounds__(256) k_weno_flux(const real *__restrict__ prim, real *__restrict__ flux,
+__global__ void __launch_bounds__(256) k_weno_flux(const real *__restrict__ u, real *__restrict__ flux,
                                                    const BlockInfo *__restrict__ info, real *bflux, Geom g,
                                                    PhysCtx<real> pc, int flux_kind, DevScalars *sc) {
     using E = Phys<real, D, PH>;
     constexpr int V = E::V;
     const int N = g.N, NG = g.ng, S = g.S;
-    const int nface = D == 3 ? N * N : N;            // tangential faces per position
+    const int nface = D == 3 ? N * N : N;            // tangential positions per direction
     const int nf = (N + 1) * nface;                  // faces per direction
-    const int b = blockIdx.x;
-    const int q = blockIdx.y * blockDim.x + threadIdx.x;
-    if (q >= D * nf) return;
-    const int n = q / nf, r = q - n * nf;
-    int x[3] = {0, 0, 0}, fp;
+    const int npen = D * nface;
+    const int chunks = (npen + int(blockDim.x) - 1) / int(blockDim.x);
+    const int b = int(blockIdx.x) / chunks;
+    const int p = (int(blockIdx.x) - b * chunks) * int(blockDim.x) + int(threadIdx.x);
+    if (p >= npen) return;
+    const int n = p / nface, t = p - n * nface;      // t: lower tangential dimension fastest
+    const int ta = t % N, tb = t / N;
+    int x[3] = {0, 0, 0};
     if (n == 0) {
-        fp = r % (N + 1);
-        const int t = r / (N + 1);
-        x[1] = t % N;
-        x[2] = t / N;
+        x[1] = ta;
+        x[2] = tb;
     } else if (n == 1) {
-        x[0] = r % N;
-        const int t = r / N;
-        fp = t % (N + 1);
-        x[2] = t / (N + 1);
+        x[0] = ta;
+        x[2] = tb;
     } else {
-        x[0] = r % N;
-        x[1] = (r / N) % N;
-        fp = r / (N * N);
+        x[0] = ta;
+        x[1] = tb;
     }
-    // tangential index of the face (lower tangential dimension first)
-    const int t = n == 0 ? x[1] + N * x[2] : (n == 1 ? x[0] + N * x[2] : x[0] + N * x[1]);
-    const real *pb = prim + int64_t(b) * g.bstride;
-    auto cell = [&](int along) -> int64_t {
-        const int i = n == 0 ? along : x[0], j = n == 1 ? along : x[1], k = n == 2 ? along : x[2];
-        return (int64_t(D == 3 ? k + NG : 0) * S + (j + NG)) * S + (i + NG);
+    // cell `along` of the pencil: o0 + along * step; face fp: fb0 + fp * fstep
+    const int64_t step = n == 0 ? 1 : (n == 1 ? int64_t(S) : int64_t(S) * S);
+    const int64_t o0 = (int64_t(D == 3 ? x[2] + NG : 0) * S + (x[1] + NG)) * S + (x[0] + NG);
+    const real *ub = u + int64_t(b) * g.bstride + o0;
+    // primitives of cell `along` of the pencil
+    auto load = [&](int along, real *w) {
+        real U[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) U[v] = ub[int64_t(v) * g.ncell + along * step];
+        E::prim(U, w, pc.gam);
     };
-    real wL[V], wR[V], F[V];
-    bool bad = false;
-    const int64_t c0 = cell(fp - 3), c1 = cell(fp - 2), c2 = cell(fp - 1), c3 = cell(fp), c4 = cell(fp + 1), c5 = cell(fp + 2);
+    const int fb0 = weno_face_index<D>(n, 0, x, N);
+    const int fstep = n == 0 ? 1 : (n == 1 ? N : N * N);
+    real *fb = flux + (int64_t(b) * D + n) * V * nf + fb0;
+    const int slo = (info[b].bslot[2 * n]), shi = (info[b].bslot[2 * n + 1]);
+    // stencil of the current centre cell (along c-2 .. c+2), per variable
+    real st[V][5], w[V];
 #pragma unroll
-    for (int v = 0; v < V; ++v) {
-        const real *pv = pb + int64_t(v) * g.ncell;
-        const real w0 = pv[c0], w1 = pv[c1], w2 = pv[c2], w3 = pv[c3], w4 = pv[c4], w5 = pv[c5];
-        wL[v] = weno5_face<real>(w0, w1, w2, w3, w4);
-        wR[v] = weno5_face<real>(w5, w4, w3, w2, w1);
+    for (int m = 0; m < 4; ++m) {   // cells -3 .. 0
+        load(m - 3, w);
+#pragma unroll
+        for (int v = 0; v < V; ++v) st[v][m + 1] = w[v];
     }
-    bad = E::nonphys(wL) || E::nonphys(wR);
-    if (n == 0) E::template face_flux<0>(flux_kind, wL, wR, 0, pc, F);
-    else if (n == 1) E::template face_flux<1>(flux_kind, wL, wR, 1, pc, F);
-    else E::template face_flux<2>(flux_kind, wL, wR, 2, pc, F);
-    real *fb = flux + (int64_t(b) * D + n) * V * nf;
+    real wL[V], wR[V], wnext[V], F[V];
+    bool bad = false;
+    for (int fp = -1; fp <= N; ++fp) {
+        // centre cell fp: load cell fp + 2, evaluate its stencil
+        load(fp + 2, w);
 #pragma unroll
-    for (int v = 0; v < V; ++v) fb[int64_t(v) * nf + r] = F[v];
-    if (fp == 0 || fp == N) {
-        const int sl = info[b].bslot[2 * n + (fp == N)];
-        if (sl >= 0) {
-            real *dst = bflux + int64_t(sl) * V * nface + t;
+        for (int v = 0; v < V; ++v) {
 #pragma unroll
-            for (int v = 0; v < V; ++v) dst[int64_t(v) * nface] = F[v];
+            for (int m = 0; m < 4; ++m) st[v][m] = st[v][m + 1];
+            st[v][4] = w[v];
+            weno5_cell<real>(st[v][0], st[v][1], st[v][2], st[v][3], st[v][4], wR[v], wnext[v]);
         }
+        if (fp >= 0) {
+            // face fp: left state from cell fp-1, right state from cell fp
+            bad = bad || E::nonphys(wL) || E::nonphys(wR);
+            if (n == 0) E::template face_flux<0>(flux_kind, wL, wR, 0, pc, F);
+            else if (n == 1) E::template face_flux<1>(flux_kind, wL, wR, 1, pc, F);
+            else E::template face_flux<2>(flux_kind, wL, wR, 2, pc, F);
+#pragma unroll
+            for (int v = 0; v < V; ++v) fb[int64_t(v) * nf + int64_t(fp) * fstep] = F[v];
+            const int sl = fp == 0 ? slo : (fp == N ? shi : -1);
+            if (sl >= 0) {
+                real *dst = bflux + int64_t(sl) * V * nface + t;
+#pragma unroll
+                for (int v = 0; v < V; ++v) dst[int64_t(v) * nface] = F[v];
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < V; ++v) wL[v] = wnext[v];
     }
     if (bad) raise_status(&sc[0].status, 7);
 }
 
-// one thread per interior cell; blockIdx.x = block, blockIdx.y = chunk of 256 cells
+// one thread per interior cell; blockIdx.x = block x chunks + chunk of 256
+// cells (a block's chunks adjacent, for L2 reuse of its face fluxes)
 template <class real, int D, int PH>
 __global__ void __launch_bounds__(256) k_weno_update(StageArgs<real> a, const real *__restrict__ flux, Geom g) {
     using E = Phys<real, D, PH>;
@@ -154,8 +180,9 @@ __global__ void __launch_bounds__(256) k_weno_update(StageArgs<real> a, const re
     const int nface = D == 3 ? N * N : N;
     const int nf = (N + 1) * nface;
     const int ncint = D == 3 ? N * N * N : N * N;
-    const int b = blockIdx.x;
-    const int c = blockIdx.y * blockDim.x + threadIdx.x;
+    const int chunks = (ncint + int(blockDim.x) - 1) / int(blockDim.x);
+    const int b = int(blockIdx.x) / chunks;
+    const int c = (int(blockIdx.x) - b * chunks) * int(blockDim.x) + int(threadIdx.x);
     const BlockInfo info = a.info[b];
     double vmax = 0.0;
     if (c < ncint) {
