@@ -115,7 +115,89 @@ __device__ __forceinline__ void srl_pairs(real *dstb, const real *srcb, int side
     }
 }
 
-// One face strip of round 1 or 2 (F2C, BC, C2F, and SRL when NG is odd),
+// Round-2 strip of one fine block's face (C2F), by coarse cell: each coarse
+// cell's three limited slopes are taken once and give its 2^D fine ghost
+// cells inside the strip (the fine layers nearest the face when Ng is odd),
+// each evaluated exactly as prolong_at does.  ND = face-normal dimension.
+template <class real, int D, int N, int NG, int ND>
+__device__ __forceinline__ void c2f_strip(const Geom &g, const Entry &e, real *dstb, const real *srcb, int lane, int part,
+                                          int parts) {
+    constexpr int T0 = ND == 0 ? 1 : 0, T1 = ND == 2 ? 1 : 2;
+    constexpr int CL = (NG + 1) / 2;                 // coarse layers the strip covers
+    constexpr int H = N / 2;
+    constexpr int UPV = CL * H * (D == 3 ? H : 1);   // coarse cells per variable
+    const int side = e.face & 1;
+    int off[3] = {0, 0, 0};                          // the fine block's half of the coarse face
+    off[T0] = e.offset & 1;
+    if (D == 3) off[T1] = (e.offset >> 1) & 1;
+    const int64_t S = g.S;
+    const int total = UPV * g.V;
+    for (int u = lane + 32 * part; u < total; u += 32 * parts) {
+        const int v = u / UPV;
+        int r = u - v * UPV;
+        const int k = r % CL;
+        r /= CL;
+        const int c0 = r % H, c1 = (D == 3) ? r / H : 0;
+        const int cn = side ? k : -1 - k;            // coarse layer relative to the face
+        int y[3] = {0, 0, 0};
+        y[T0] = off[T0] * H + c0;
+        if (D == 3) y[T1] = off[T1] * H + c1;
+        y[ND] = side ? cn : N + cn;
+        const real *p = srcb + int64_t(v) * g.ncell + cell_index<real>(g, y[0], y[1], y[2]);
+        const real uc = p[0];
+        const real m0 = minmod<real>(uc - p[-1], p[1] - uc);
+        const real m1 = minmod<real>(uc - p[-S], p[S] - uc);
+        const real m2 = D == 3 ? minmod<real>(uc - p[-S * S], p[S * S] - uc) : real(0);
+        real *db = dstb + int64_t(v) * g.ncell;
+        if constexpr (NG % 2 == 0) {
+            // both x children in one aligned 2-element store (Ng even: all
+            // children lie in the strip and x + Ng of the lower one is even)
+            using V2 = typename Vec2<real>::type;
+#pragma unroll
+            for (int ch = 0; ch < (1 << D); ch += 2) {
+                const int sb1 = (ch >> 1) & 1, sb2 = (ch >> 2) & 1;
+                int x[3] = {0, 0, 0};
+                if (ND == 0) {
+                    x[0] = side ? 2 * cn + N : 2 * cn;
+                    x[1] = 2 * c0 + sb1;
+                    if (D == 3) x[2] = 2 * c1 + sb2;
+                } else {
+                    x[0] = 2 * c0;
+                    x[ND] = side ? 2 * cn + (ND == 1 ? sb1 : sb2) + N : 2 * cn + (ND == 1 ? sb1 : sb2);
+                    if (D == 3) x[ND == 1 ? 2 : 1] = 2 * c1 + (ND == 1 ? sb2 : sb1);
+                }
+                real t0 = real(-0.25) * m0, t1 = real(0.25) * m0;
+                t0 = t0 + (sb1 ? real(0.25) : real(-0.25)) * m1;
+                t1 = t1 + (sb1 ? real(0.25) : real(-0.25)) * m1;
+                if (D == 3) {
+                    t0 = t0 + (sb2 ? real(0.25) : real(-0.25)) * m2;
+                    t1 = t1 + (sb2 ? real(0.25) : real(-0.25)) * m2;
+                }
+                V2 pr;
+                pr.x = uc + t0;
+                pr.y = uc + t1;
+                *reinterpret_cast<V2 *>(db + cell_index<real>(g, x[0], x[1], x[2])) = pr;
+            }
+            continue;
+        }
+#pragma unroll
+        for (int ch = 0; ch < (1 << D); ++ch) {
+            const int sb[3] = {ch & 1, (ch >> 1) & 1, (ch >> 2) & 1};
+            const int xn = 2 * cn + sb[ND];          // fine layer relative to the face
+            if (side ? xn >= NG : xn < -NG) continue;
+            int x[3] = {0, 0, 0};
+            x[T0] = 2 * c0 + sb[T0];
+            if (D == 3) x[T1] = 2 * c1 + sb[T1];
+            x[ND] = side ? xn + N : xn;
+            real t = (sb[0] ? real(0.25) : real(-0.25)) * m0;
+            t = t + (sb[1] ? real(0.25) : real(-0.25)) * m1;
+            if (D == 3) t = t + (sb[2] ? real(0.25) : real(-0.25)) * m2;
+            db[cell_index<real>(g, x[0], x[1], x[2])] = uc + t;
+        }
+    }
+}
+
+// One face strip of round 1 (F2C, BC, and SRL when NG is odd),
 // ND = face-normal dimension, HALF = the F2C strip of one fine block (half
 // the face along each tangential dimension).
 template <class real, int D, int N, int NG, int ND, bool HALF>
@@ -170,16 +252,6 @@ __device__ __forceinline__ void ghost_strip(const GhostArgs<real> &a, const Geom
                 for (int d = 0; d < D; ++d) y[d] = 2 * x[d] - off[d] * N;
                 y[nd] = side ? 2 * (x[nd] - N) : 2 * x[nd] + N;
                 val = restrict_at<real, D>(srcb + int64_t(v) * g.ncell, g, y[0], y[1], y[2]);
-            } else if (e.kind == KIND_C2F) {
-                int y[3] = {0, 0, 0}, s[3] = {0, 0, 0};
-                for (int d = 0; d < D; ++d) {
-                    y[d] = off[d] * (N / 2) + (x[d] >> 1);
-                    s[d] = x[d] & 1;
-                }
-                const int xn = side ? x[nd] - N : x[nd];
-                y[nd] = side ? (xn >> 1) : N + (xn >> 1);
-                s[nd] = xn & 1;
-                val = prolong_at<real, D>(srcb + int64_t(v) * g.ncell, g, y[0], y[1], y[2], s[0], s[1], s[2]);
             } else {  // physical boundary (Sec. 2.4)
                 const int k = side ? x[nd] - N + 1 : -x[nd];          // layer 1..ng
                 int y[3] = {x[0], x[1], x[2]};
@@ -277,6 +349,12 @@ __global__ void __launch_bounds__(256) k_ghost(GhostArgs<real> a, Geom g) {
             else srl_pairs<real, D, N, NG, (D == 3 ? 2 : 1)>(dstb, srcb, side, lane, part, a.parts, g.V);
             return;
         }
+    }
+    if (e.kind == KIND_C2F) {
+        if (nd == 0) c2f_strip<real, D, N, NG, 0>(g, e, dstb, srcb, lane, part, a.parts);
+        else if (nd == 1 || D == 2) c2f_strip<real, D, N, NG, 1>(g, e, dstb, srcb, lane, part, a.parts);
+        else c2f_strip<real, D, N, NG, (D == 3 ? 2 : 1)>(g, e, dstb, srcb, lane, part, a.parts);
+        return;
     }
     // the general path, with the strip shape fixed per normal and kind
     const bool half = e.kind == KIND_F2C;
