@@ -58,7 +58,6 @@ struct amr_forest {
     bool persistent = false;     // stage launch: grid = SMs x resident CTAs, grid-stride sweep
     int pair_tile = 0;           // FP32 pair kernel staging tile: 0 default (16, N for N = 8), or 8
     int n_sms = 0;
-    bool capturing = false;
     int64_t launches = 0;
     bool tracing = false;                      // per-phase timing on (steps then run without a graph)
     std::vector<cudaEvent_t> ev_free;          // timing events ready for reuse
