@@ -454,7 +454,9 @@ amr_status amr_trace(amr_forest *f, int on);
  * streams they were recorded on), then writes per phase the total
  * milliseconds to ms[0 .. AMR_N_PHASES) and the number of timed records to
  * count[0 .. AMR_N_PHASES) (host arrays; either may be NULL).  reset != 0
- * clears the totals afterwards.  Errors: AMR_EINVAL. */
+ * clears the totals afterwards.  Errors: AMR_EINVAL; AMR_ECUDA when a
+ * recorded phase could not be timed (it is left out of the totals, which
+ * are still written). */
 amr_status amr_trace_read(amr_forest *f, double *ms, int64_t *count, int reset);
 
 /* ---- checkpoint, restart and output --------------------------------------

@@ -1452,7 +1452,7 @@ amr_status amr_trace(amr_forest *f, int on) {
 
 amr_status amr_trace_read(amr_forest *f, double *ms, int64_t *count, int reset) {
     if (!f) return AMR_EINVAL;
-    trace_drain(f);
+    const bool ok = trace_drain(f);
     for (int p = 0; p < AMR_N_PHASES; ++p) {
         if (ms) ms[p] = f->trace_ms[p];
         if (count) count[p] = f->trace_n[p];
@@ -1461,7 +1461,7 @@ amr_status amr_trace_read(amr_forest *f, double *ms, int64_t *count, int reset) 
             f->trace_n[p] = 0;
         }
     }
-    return AMR_OK;
+    return ok ? AMR_OK : fail(f, AMR_ECUDA, "trace: a recorded phase could not be timed (dropped)");
 }
 
 }  // extern "C"

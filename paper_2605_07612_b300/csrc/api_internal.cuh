@@ -92,17 +92,23 @@ inline int n_inst(const amr_forest *f) { return int(f->inst.size()); }
 
 // ---- per-phase timing (tracing): device phases by CUDA events, host phases
 // by the wall clock
-inline void trace_drain(amr_forest *f) {
+// adds every recorded phase to the totals; false if some record could not
+// be timed (it is dropped)
+inline bool trace_drain(amr_forest *f) {
+    bool ok = true;
     for (const TraceRec &t : f->trace_open) {
         float ms = 0.f;
         if (cudaEventSynchronize(t.b) == cudaSuccess && cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) {
             f->trace_ms[t.phase] += double(ms);
             f->trace_n[t.phase] += 1;
+        } else {
+            ok = false;
         }
         f->ev_free.push_back(t.a);
         f->ev_free.push_back(t.b);
     }
     f->trace_open.clear();
+    return ok;
 }
 
 inline cudaEvent_t trace_event(amr_forest *f) {
