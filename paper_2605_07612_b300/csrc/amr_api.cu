@@ -280,7 +280,7 @@ amr_status run_stage(amr_forest *f, const amr_stage *stg, cudaStream_t st) {
     }
     amr_status s;
     if (f->cfg.limiter == AMR_LIM_WENO5) {
-        // three-pass WENO5 stage on the filled ghost cells (no halo gathering)
+        // two-pass WENO5 stage on the filled ghost cells (no halo gathering)
         a.gather = 0;
         if ((s = ensure_weno(f)) != AMR_OK) return s;
         TraceSpan span(f, AMR_PHASE_STAGE, st);

@@ -748,7 +748,7 @@ def test_launch_shapes_agree(N):
 
 @pytest.mark.parametrize("dim,flux,scheme", [(2, 0, "heun"), (3, 0, "heun"), (2, 1, "rk4"), (3, 1, "heun")])
 def test_weno5_fp64_matches_oracle(dim, flux, scheme):
-    """WENO5 reconstruction (three ghost layers; three-pass GPU stage) on
+    """WENO5 reconstruction (three ghost layers; two-pass GPU stage) on
     3-level AMR meshes with Rusanov or HLL, Heun or RK4: FP64 relative L1
     <= 1e-12 against the oracle."""
     base = dict(SPEC_2D_AMR if dim == 2 else SPEC_3D_AMR)

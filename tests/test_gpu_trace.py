@@ -98,7 +98,8 @@ def test_traced_regrid_reductions_and_autotune():
 
 
 def test_traced_weno5_stage():
-    """The three passes of a WENO5 stage are one stage record."""
+    """The two passes of a WENO5 stage (face fluxes, update) are one stage
+    record."""
     sp = synth.MeshSpec(ndim=2, N=16, ng=3, ntrees=(4, 4, 1), max_level=1, limiter=3)
     f = amr.Forest(sp, 0, max_blocks=256, precision=64)
     lev, g = f.blocks()
