@@ -257,3 +257,25 @@ def test_trace_times_host_phases_of_a_regrid():
     f.regrid(flags)
     assert f.trace_read() == t                    # off: unchanged; read and reset
     assert all(v == (0.0, 0) for v in f.trace_read().values())
+
+
+def test_trace_batched_regrid_records_one_host_phase_per_call():
+    """A regrid of a batch of two host-only meshes adapts both instances in
+    one mesh-host record and rebuilds the pattern once; a regrid that
+    changes nothing records the mesh work but no pattern build; a NULL
+    handle is refused."""
+    sp = synth.MeshSpec(ndim=2, N=8, ng=2, ntrees=(2, 2, 1), max_level=2)
+    f = amr.Forest(None, batch=[(sp, 0, 64), (sp, 1, 64)], host_only=True)
+    f.trace(True)
+    flags = np.zeros(f.n, dtype=np.int8)
+    flags[0] = 1
+    flags[-1] = 1
+    assert f.regrid(flags)
+    t = f.trace_read()
+    assert t["mesh_host"][1] == 1 and t["pattern_host"][1] == 1
+    assert not f.regrid(np.zeros(f.n, dtype=np.int8))
+    t = f.trace_read()
+    assert t["mesh_host"][1] == 1 and t["pattern_host"][1] == 0
+    lib = f.lib
+    assert lib.amr_trace(None, 1) == amr.AMR_EINVAL
+    assert lib.amr_trace_read(None, None, None, 0) == amr.AMR_EINVAL
