@@ -399,6 +399,14 @@ amr_status amr_mlp_forward(amr_mlp *m, const float *x, int64_t n, float *prob, a
  * into grad[0 .. P) (device), and the loss into grad[P]. */
 amr_status amr_mlp_gradient(amr_mlp *m, const float *x, const int8_t *y, int64_t n, float *grad, amr_stream stream);
 
+/* One AdamW step (Loshchilov & Hutter 2019: beta 0.9 / 0.999, eps 1e-8,
+ * bias-corrected moments, decay lr * weight_decay * w decoupled from the
+ * gradient) of the FP32 master weights with the caller's gradient grad[0 ..
+ * P) (device, FP32), then their BF16 copy; the step counter of the bias
+ * correction advances by one (amr_mlp_set_params resets it and the moments).
+ * Enqueued on `stream`.  Errors: AMR_EINVAL, AMR_ECUDA. */
+amr_status amr_mlp_adamw_step(amr_mlp *m, const float *grad, double lr, double weight_decay, amr_stream stream);
+
 /* AdamW (beta 0.9 / 0.999, eps 1e-8, decoupled weight decay) on shuffled
  * mini-batches for `epochs` passes; *final_loss = mean loss of the last
  * epoch's batches. */
@@ -455,8 +463,10 @@ amr_status amr_trace(amr_forest *f, int on);
  * milliseconds to ms[0 .. AMR_N_PHASES) and the number of timed records to
  * count[0 .. AMR_N_PHASES) (host arrays; either may be NULL).  reset != 0
  * clears the totals afterwards.  Errors: AMR_EINVAL; AMR_ECUDA when a
- * recorded phase could not be timed (it is left out of the totals, which
- * are still written). */
+ * phase traced since the last read with reset could not be timed (its
+ * events could not be created or recorded, or not read back, including at
+ * the automatic drain of a long traced run); such phases are left out of the
+ * totals, which are still written, and the condition is cleared by reset. */
 amr_status amr_trace_read(amr_forest *f, double *ms, int64_t *count, int reset);
 
 /* ---- checkpoint, restart and output --------------------------------------
@@ -514,9 +524,11 @@ amr_status amr_write_xdmf(const amr_forest *f, int s, const char *base, amr_stre
  * exits.  Calls share that array, so calls that overlap on the GPU (on
  * different streams, or from different threads) race and give wrong sums;
  * each call overwrites the entries it reads, so nothing carries over between
- * calls that are ordered.  The first call on a device looks up the array's
- * device address with that device current; make that first call before any
- * stream capture.  Errors: AMR_EINVAL (null pointer, bad shape or
+ * calls that are ordered.  Every call looks up the array's device address
+ * on the current device (nothing is cached, so the call stays valid after
+ * cudaDeviceReset or a new primary context); the first call on a device
+ * also loads the library's device code there, so make that first call
+ * before any stream capture.  Errors: AMR_EINVAL (null pointer, bad shape or
  * precision), AMR_ECAPACITY (n_blocks > AMR_STATIC_MAX_BLOCKS), AMR_ECUDA. */
 amr_status amr_conserved_static(const void *state, int precision, int ndim, int block_n, int n_ghost,
                                 int64_t n_blocks, const double *cell_volume, double *sums, amr_stream stream);

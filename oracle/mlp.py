@@ -120,3 +120,24 @@ def block_features(spec, u, lev, max_level):
     f = np.concatenate([pool(rho) / rm[:, None] - 1.0, pool(p) / pm[:, None] - 1.0, pool(speed) / cm[:, None],
                         (np.asarray(lev, dtype=np.float64) / max(1, max_level))[:, None]], axis=1)
     return f
+
+
+def adamw_step(w, m, v, g, t, lr, weight_decay, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One AdamW update (Loshchilov & Hutter, "Decoupled weight decay
+    regularization", ICLR 2019, Adam with decoupled weight decay; the
+    learning rate scales both the Adam step and the decay) of parameters w
+    with moments m, v at step t >= 1 (1-based) from gradient g.  Returns the
+    new (w, m, v); FP64.
+
+      m_t = beta1 m + (1 - beta1) g,       v_t = beta2 v + (1 - beta2) g^2
+      mhat = m_t / (1 - beta1^t),          vhat = v_t / (1 - beta2^t)
+      w_t = w - lr (mhat / (sqrt(vhat) + eps) + weight_decay w)
+    """
+    w = np.asarray(w, dtype=np.float64)
+    g = np.asarray(g, dtype=np.float64)
+    m = beta1 * np.asarray(m, dtype=np.float64) + (1.0 - beta1) * g
+    v = beta2 * np.asarray(v, dtype=np.float64) + (1.0 - beta2) * g * g
+    mhat = m / (1.0 - beta1 ** t)
+    vhat = v / (1.0 - beta2 ** t)
+    w_new = w - lr * (mhat / (np.sqrt(vhat) + eps) + weight_decay * w)
+    return w_new, m, v

@@ -1452,7 +1452,8 @@ amr_status amr_trace(amr_forest *f, int on) {
 
 amr_status amr_trace_read(amr_forest *f, double *ms, int64_t *count, int reset) {
     if (!f) return AMR_EINVAL;
-    const bool ok = trace_drain(f);
+    const bool ok = trace_drain(f) && !f->trace_lost;
+    if (reset) f->trace_lost = false;
     for (int p = 0; p < AMR_N_PHASES; ++p) {
         if (ms) ms[p] = f->trace_ms[p];
         if (count) count[p] = f->trace_n[p];

@@ -62,6 +62,7 @@ struct amr_forest {
     bool tracing = false;                      // per-phase timing on (steps then run without a graph)
     std::vector<cudaEvent_t> ev_free;          // timing events ready for reuse
     std::vector<amrb::TraceRec> trace_open;    // recorded phases not yet added to the totals
+    bool trace_lost = false;                   // a phase went untimed since the last read with reset
     double trace_ms[AMR_N_PHASES] = {};
     int64_t trace_n[AMR_N_PHASES] = {};
     std::string err;
@@ -128,23 +129,34 @@ class TraceSpan {
     TraceSpan(amr_forest *f, int phase, cudaStream_t st) : f_(f), st_(st), phase_(phase) {
         if (!f->tracing) return;
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-        if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+        if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+            cudaGetLastError();
+            f->trace_lost = true;
+            return;
+        }
+        if (cs != cudaStreamCaptureStatusNone) return;   // a captured phase is timed by its replays, not here
         a_ = trace_event(f);
         if (a_ && cudaEventRecord(a_, st) != cudaSuccess) {
+            cudaGetLastError();
             f->ev_free.push_back(a_);
             a_ = nullptr;
         }
+        if (!a_) f->trace_lost = true;   // this phase goes untimed: amr_trace_read reports it
     }
     ~TraceSpan() {
         if (!a_) return;
         cudaEvent_t b = trace_event(f_);
         if (!b || cudaEventRecord(b, st_) != cudaSuccess) {
+            cudaGetLastError();
             f_->ev_free.push_back(a_);
             if (b) f_->ev_free.push_back(b);
+            f_->trace_lost = true;
             return;
         }
         f_->trace_open.push_back({phase_, a_, b});
-        if (f_->trace_open.size() >= 4096) trace_drain(f_);   // bounded: a long traced run syncs now and then
+        // bounded: a long traced run syncs now and then; a record that could
+        // not be timed there is reported by the next amr_trace_read
+        if (f_->trace_open.size() >= 4096 && !trace_drain(f_)) f_->trace_lost = true;
     }
     TraceSpan(const TraceSpan &) = delete;
     TraceSpan &operator=(const TraceSpan &) = delete;

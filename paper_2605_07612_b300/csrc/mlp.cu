@@ -165,6 +165,19 @@ amr_status amr_mlp_gradient(amr_mlp *m, const float *x, const int8_t *y, int64_t
     return AMR_OK;
 }
 
+amr_status amr_mlp_adamw_step(amr_mlp *m, const float *grad, double lr, double weight_decay, amr_stream stream) {
+    if (!m || !grad) return AMR_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    ++m->step;
+    const float c1 = float(1.0 - std::pow(double(b1), double(m->step)));
+    const float c2 = float(1.0 - std::pow(double(b2), double(m->step)));
+    k_adamw<<<int((m->P + 255) / 256), 256, 0, st>>>(m->w, m->m, m->v, m->wb, grad, m->P, float(lr), b1, b2, eps,
+                                                    float(weight_decay), c1, c2);
+    MCU(cudaGetLastError());
+    return AMR_OK;
+}
+
 amr_status amr_mlp_train(amr_mlp *m, const float *x, const int8_t *y, int64_t n, int epochs, int batch, double lr,
                          double weight_decay, uint64_t seed, double *final_loss, amr_stream stream) {
     if (!m || !x || !y || n < 1 || epochs < 1 || batch < 1) return AMR_EINVAL;

@@ -11,7 +11,6 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
-#include <mutex>
 
 #include "../../include/amr.h"
 
@@ -19,15 +18,9 @@ namespace {
 
 constexpr int64_t kStaticMaxBlocks = AMR_STATIC_MAX_BLOCKS;
 constexpr int kStaticMaxVars = 5;
-constexpr int kMaxDevices = 64;
-
 // Per-block, per-variable partial sums.  Each call overwrites the entries it
 // uses before reading them, so nothing has to be cleared between calls.
 static __device__ __align__(256) double g_partials[kStaticMaxBlocks * kStaticMaxVars];
-
-// Device address of g_partials per device, looked up once per device.
-double *g_partials_addr[kMaxDevices] = {nullptr};
-std::mutex g_setup_mutex;
 
 template <class real, int D>
 __global__ void __launch_bounds__(256) k_static_block(const real *u, int N, int ng, const double *vol, double *partial) {
@@ -71,24 +64,18 @@ __global__ void __launch_bounds__(1024) k_static_final(const double *partial, in
     }
 }
 
-// First call on a device: resolve the device address of the scratch array
-// with that device current.
+// Device address of the scratch array on the current device.  Looked up on
+// every call (a host-side lookup once the library's device code is loaded):
+// a cached address would go stale after cudaDeviceReset or when the device
+// gets a new primary context in the same process.  The first lookup on a
+// device loads the library's device code there.
 amr_status scratch_address(double **out) {
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    double *p = nullptr;
+    if (cudaGetSymbolAddress((void **)&p, g_partials) != cudaSuccess || !p) {
         cudaGetLastError();
         return AMR_ECUDA;
     }
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_partials_addr[dev]) {
-        double *p = nullptr;
-        if (cudaGetSymbolAddress((void **)&p, g_partials) != cudaSuccess || !p) {
-            cudaGetLastError();
-            return AMR_ECUDA;
-        }
-        g_partials_addr[dev] = p;
-    }
-    *out = g_partials_addr[dev];
+    *out = p;
     return AMR_OK;
 }
 

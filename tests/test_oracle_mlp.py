@@ -67,3 +67,48 @@ def test_features_of_uniform_and_pooled_states():
     exp_pool = r.reshape(4, 4).mean(axis=1) / r.mean() - 1.0
     got = f[0, :64].reshape(4, 4, 4)        # (z, y, x) pools
     assert np.allclose(got, exp_pool[None, None, :], atol=1e-14)
+
+
+def test_adamw_decay_alone_is_geometric():
+    """With a zero gradient the moments stay zero and only the decoupled
+    decay acts: w_t = w_0 (1 - lr wd)^t."""
+    rng = np.random.default_rng(4)
+    w0 = rng.normal(0, 1, 50)
+    w, m, v = w0.copy(), np.zeros(50), np.zeros(50)
+    lr, wd = 1e-2, 0.3
+    for t in range(1, 8):
+        w, m, v = mlp.adamw_step(w, m, v, np.zeros(50), t, lr, wd)
+        np.testing.assert_allclose(w, w0 * (1 - lr * wd) ** t, rtol=1e-14, atol=0)
+        assert not m.any() and not v.any()
+
+
+def test_adamw_bias_correction_is_exact_for_a_constant_gradient():
+    """For a constant gradient the bias-corrected moments equal g and g^2 at
+    every step, so each step without decay moves w by lr g / (|g| + eps); at
+    step 1 that is lr sign(g) up to eps."""
+    rng = np.random.default_rng(5)
+    g = rng.normal(0, 1e-2, 40)
+    w0 = rng.normal(0, 1, 40)
+    w, m, v = w0.copy(), np.zeros(40), np.zeros(40)
+    lr, eps = 3e-3, 1e-8
+    for t in range(1, 12):
+        w, m, v = mlp.adamw_step(w, m, v, g, t, lr, 0.0, eps=eps)
+        np.testing.assert_allclose(m / (1 - 0.9 ** t), g, rtol=1e-13)
+        np.testing.assert_allclose(v / (1 - 0.999 ** t), g * g, rtol=1e-12)
+        np.testing.assert_allclose(w, w0 - t * lr * g / (np.abs(g) + eps), rtol=1e-12, atol=1e-15)
+    w1, _, _ = mlp.adamw_step(w0, np.zeros(40), np.zeros(40), g, 1, lr, 0.0, eps=eps)
+    assert np.all(np.abs(w1 - (w0 - lr * np.sign(g))) <= 1.01 * lr * eps / np.abs(g))
+
+
+def test_adamw_decay_uses_the_weights_before_the_step():
+    """Decoupled decay: the decay term is lr wd w of the weights before the
+    update, added to the Adam step (not folded into the gradient)."""
+    w0, g = np.array([2.0, -1.0]), np.array([0.5, 0.5])
+    lr, wd = 0.1, 0.2
+    w1, _, _ = mlp.adamw_step(w0, np.zeros(2), np.zeros(2), g, 1, lr, wd)
+    np.testing.assert_allclose(w1, w0 - lr * (g / (np.abs(g) + 1e-8) + wd * w0), rtol=1e-15)
+    # an L2 penalty folded into the gradient would give the same sign step here
+    # but a different size for the weight whose gradient it flips
+    w0, g = np.array([2.0]), np.array([0.1])
+    w1, _, _ = mlp.adamw_step(w0, np.zeros(1), np.zeros(1), g, 1, lr, 1.0)
+    assert abs(w1[0] - (2.0 - 0.1 * (1.0 + 2.0))) < 1e-7

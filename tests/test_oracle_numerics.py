@@ -536,3 +536,113 @@ def test_weno5_density_wave_fifth_order():
         errs.append(np.abs(interior(sp, u)[:, 0] - exact[:, sl, sl]).mean())
     orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
     assert min(orders) >= 4.6, (errs, orders)
+
+
+# ------------------------------------------- Einfeldt wave-speed estimate --
+
+def _euler_flux_and_state(ndim, gam, n, w):
+    """Physical flux along dimension n and conservative state of primitive w
+    = (rho, velocity[ndim], p): the Euler equations of Sec. 3.5."""
+    rho, vel, p = w[0], np.asarray(w[1:1 + ndim], dtype=np.float64), w[1 + ndim]
+    E = p / (gam - 1.0) + 0.5 * rho * float(vel @ vel)
+    U = np.concatenate([[rho], rho * vel, [E]])
+    F = np.concatenate([[rho * vel[n]], rho * vel * vel[n], [(E + p) * vel[n]]])
+    F[1 + n] += p
+    return F, U
+
+
+def _einfeldt_cases():
+    from fractions import Fraction
+    for line in open(os.path.join(GOLDEN, "einfeldt_speeds.txt")):
+        line = line.split("#")[0].strip()
+        if not line:
+            continue
+        head, left, right, speeds = line.split("|")
+        ndim, n = map(int, head.split())
+        L = [float(x) for x in left.split()]
+        R = [float(x) for x in right.split()]
+        ubar, d2 = (float(Fraction(x)) for x in speeds.split())
+        wL = np.array(L[:1 + ndim] + [L[4]])
+        wR = np.array(R[:1 + ndim] + [R[4]])
+        yield ndim, n, wL, wR, ubar, d2
+
+
+@pytest.mark.parametrize("flux", [0, 1])
+def test_einfeldt_speeds_match_hand_derived_values(flux):
+    """The oracle's Rusanov and HLL fluxes use Einfeldt's signal speeds
+    (Sec. 3.2, 3.5): checked against five face states whose speeds were
+    worked out by hand from Einfeldt (1988) as exact rationals
+    (tests/golden/einfeldt_speeds.txt).  Rusanov's dissipation speed is
+    max(|ubar - dbar|, |ubar + dbar|) = |ubar| + dbar; HLL clamps the two
+    signal speeds at zero.  A dropped eta2 term (cases A, C, D) or c in place
+    of c^2 in the weighted mean (cases B-D) changes the flux far beyond
+    rounding."""
+    gam = 1.4
+    ncase = 0
+    for ndim, n, wL, wR, ubar, d2 in _einfeldt_cases():
+        sp = synth.MeshSpec(ndim=ndim, N=8, ng=2, ntrees=(1, 1, 1), gamma=gam, flux=flux)
+        FL, UL = _euler_flux_and_state(ndim, gam, n, wL)
+        FR, UR = _euler_flux_and_state(ndim, gam, n, wR)
+        d = math.sqrt(d2)
+        if flux == 0:
+            a = abs(ubar) + d
+            want = 0.5 * (FL + FR) - 0.5 * a * (UR - UL)
+        else:
+            sL, sR = min(ubar - d, 0.0), max(ubar + d, 0.0)
+            want = (sR * FL - sL * FR + sL * sR * (UR - UL)) / (sR - sL)
+        got = oracle.face_flux(sp, n, wL, wR)
+        scale = np.abs(FL).max() + np.abs(FR).max() + (abs(ubar) + d) * np.abs(UR - UL).max()
+        assert np.abs(got - want).max() <= 1e-14 * scale, (ndim, n, got, want)
+        ncase += 1
+    assert ncase == 5
+
+
+def test_einfeldt_supersonic_hll_is_upwind():
+    """Case E of the golden file: every signal speed is positive, so HLL
+    returns the left state's physical flux (Sec. 3.2)."""
+    cases = list(_einfeldt_cases())
+    ndim, n, wL, wR, ubar, d2 = cases[-1]
+    assert ubar - math.sqrt(d2) > 0
+    sp = synth.MeshSpec(ndim=ndim, N=8, ng=2, ntrees=(1, 1, 1), gamma=1.4, flux=1)
+    FL, _ = _euler_flux_and_state(ndim, 1.4, n, wL)
+    np.testing.assert_allclose(oracle.face_flux(sp, n, wL, wR), FL, rtol=4e-16, atol=0)
+
+
+# ------------------------------------ conserved integrals in closed form --
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_conserved_integrals_closed_form(ndim):
+    """orc_conserved integrates each conserved variable over the domain
+    (Eq. 18 summed over the leaves).  For a field linear in x its cell
+    averages are its values at the cell centres, so on any mesh the sum is
+    exactly |Omega| (c + g . centroid).  Checked on a 3-level mesh of a
+    non-cubic brick with non-unit, shifted extents, so that a missing cell
+    volume, one level's volume used for every block, or a dropped domain
+    length fails."""
+    if ndim == 2:
+        sp = synth.MeshSpec(ndim=2, N=8, ng=2, ntrees=(3, 2, 1), max_level=2, lo=(-0.3, 0.2, 0.0),
+                            length=(1.5, 0.75, 1.0))
+        centre, radii = (0.2, 0.5), (0.4, 0.2)
+    else:
+        sp = synth.MeshSpec(ndim=3, N=8, ng=2, ntrees=(3, 2, 2), max_level=2, lo=(-0.3, 0.2, 1.0),
+                            length=(1.5, 0.75, 1.25))
+        centre, radii = (0.2, 0.5, 1.6), (0.4, 0.2)
+    m = amr_mesh(sp, centre, 2, radii)
+    lev, g = m.blocks()
+    assert set(lev.tolist()) == {0, 1, 2}
+    X = synth.cell_centres(sp, lev, g)
+    rng = np.random.default_rng(11)
+    c = rng.uniform(0.5, 2.0, sp.nvar)
+    grad = rng.uniform(-1.0, 1.0, (sp.nvar, ndim))
+    u = m.new_state()
+    U = u.reshape((m.n, sp.nvar) + (sp.side,) * ndim)
+    for v in range(sp.nvar):
+        U[:, v] = c[v] + sum(grad[v, d] * X[d] for d in range(ndim))
+    vol = float(np.prod(sp.length[:ndim]))
+    centroid = np.array([sp.lo[d] + 0.5 * sp.length[d] for d in range(ndim)])
+    want = vol * (c + grad @ centroid)
+    got = m.conserved(u)
+    np.testing.assert_allclose(got, want, rtol=1e-13, atol=1e-13)
+    # a constant state: every variable integrates to c |Omega|
+    U[:] = c.reshape((1, sp.nvar) + (1,) * ndim)
+    np.testing.assert_allclose(m.conserved(u), vol * c, rtol=1e-14, atol=0)
