@@ -357,6 +357,14 @@ def run_ours(args, rank, world, dist):
         extras["rayleigh_taylor_weno5"] = rtw
         extras["batched_2d"] = run_batched(args, amr, torch, stream, barrier, world)
         extras["scalar_advection"] = run_advection(args, amr, torch, stream, barrier, world)
+        # the 3-level static AMR case (restriction / prolongation ghost
+        # entries, flux fixing) and a shortened adaptive run with the learned
+        # flags (Sec. 5.4's AMR breakdown; the full 500-step run is
+        # `--workload adaptive`)
+        extras["amr_static_3level"] = run_amr_static(args, amr, torch, stream)
+        torch.cuda.empty_cache()
+        extras["adaptive_short"] = run_adaptive(args, amr, torch, stream, steps=100, train_until=50)
+        torch.cuda.empty_cache()
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -552,6 +560,48 @@ def abs_integrals(sp, u, lev):
     return out
 
 
+def amr_step_bytes(sp, lev, pat, esize=4, gather=True):
+    """Algorithmic bytes of one Heun step of an AMR mesh (Sec. 2.6, 2.7, 3.1):
+    two stages (as algorithmic_stage_bytes, every block), two ghost fills
+    and two flux fixes.  Per ghost entry, with a face strip of n_s = N^(d-1)
+    Ng cells of V variables:
+      SRL copy  2 n_s (read the source interior, write the ghosts); with
+                gathered halos only the copies whose receiving block is the
+                coarse source of a prolongation run;
+      BC        2 n_s (read the mirror cells, write the ghosts);
+      F2C       9 n_s / 2^(d-1) in 3D, 5 n_s / 2 in 2D: per coarse ghost
+                cell 2^d fine reads and one write, over a fine block's
+                quarter (half in 2D) of the coarse face;
+      C2F       n_s written, and the coarse cells the limited prolongation
+                reads: (N/2 + 2)^(d-1) (ceil(Ng/2) + 2) with the slope
+                neighbours;
+    flux fixing per coarse-side refinement face: the 2^(d-1) fine blocks'
+    N^(d-1) face fluxes, the coarse face fluxes, and a read and a write of
+    the coarse cells next to the face: (2^(d-1) + 3) N^(d-1) V values."""
+    d, N, ng, V = sp.ndim, sp.N, sp.ng, sp.nvar
+    ns = N ** (d - 1) * ng
+    s1, s2 = algorithmic_stage_bytes(sp, esize)
+    nb = len(lev)
+    kind = pat[:, 0]
+    c2f = pat[kind == 3]
+    srl = pat[kind == 0]
+    if gather:
+        feeders = set(c2f[:, 3].tolist())
+        n_srl = int(np.isin(srl[:, 2], list(feeders)).sum()) if feeders else 0
+    else:
+        n_srl = len(srl)
+    n_bc = int((kind == 2).sum())
+    n_f2c = int((kind == 1).sum())
+    n_c2f = len(c2f)
+    f2c_cells = (N // 2) ** (d - 1) * ng
+    ghost = (2 * ns * (n_srl + n_bc) + n_f2c * f2c_cells * (2 ** d + 1) +
+             n_c2f * (ns + (N // 2 + 2) ** (d - 1) * ((ng + 1) // 2 + 2))) * V * esize
+    fix = n_f2c // (2 ** (d - 1)) * (2 ** (d - 1) + 3) * N ** (d - 1) * V * esize
+    return {"stages": nb * (s1 + s2), "ghost_fills": 2 * ghost, "flux_fix": 2 * fix,
+            "total": nb * (s1 + s2) + 2 * ghost + 2 * fix,
+            "entries": {"srl_run": n_srl, "f2c": n_f2c, "bc": n_bc, "c2f": n_c2f}}
+
+
 def run_amr_static(args, amr, torch, stream):
     """3-level static AMR (about 2e4 blocks of 16^3), over-pressure sphere
     (radius 0.1, p_in / p_out = 100) at a seeded centre, FP32 with FP64 dt and
@@ -582,7 +632,13 @@ def run_amr_static(args, amr, torch, stream):
     cells = f.n * sp.N ** 3
     pat = f.pattern()
     phases = phase_breakdown(f, stream, True)
-    return {"value": 2.0 * cells * steps / (ms * 1e-3), "unit": UNIT, "blocks": f.n, "phases": phases,
+    alg = amr_step_bytes(sp, lev, pat)
+    peak, peak_src = measured_peaks()
+    gbs = alg["total"] / (ms / steps * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": gbs, "peak": peak, "peak_source": peak_src, "unit": "GB/s", "frac": gbs / peak,
+            "algorithmic_bytes_per_step": alg, "note": "whole step (ghost rounds, stages, flux fixing, dt) over the "
+            "graph-timed ms_per_step; per-entry byte counts in bench.amr_step_bytes"}
+    return {"value": 2.0 * cells * steps / (ms * 1e-3), "unit": UNIT, "blocks": f.n, "phases": phases, "roofline": roof,
             "blocks_per_level": np.bincount(lev).tolist(), "ball_radius": r, "centre": list(centre),
             "ghost_entries": {k: int((pat[:, 0] == i).sum()) for i, k in enumerate(["srl", "f2c", "bc", "c2f"])},
             "ms_per_step": ms / steps, "steps": steps, "autotune_choice": choice,
@@ -816,11 +872,28 @@ def run_ncu_case(which="stage"):
 
 # ------------------------------------------------------- CPU oracle arm --
 
-def oracle_sample(seconds_hint=15.0):
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
+def oracle_sample(seconds_hint=15.0, threads=None):
     """FP64 oracle on a bounded sample of the workload: the same 16^3 blocks
     and initial field, 4x4x4 blocks (64 blocks, 262144 cells), whole Heun
-    steps, on every host core the oracle's OpenMP uses."""
+    steps, on every host core the oracle's OpenMP uses (or `threads`)."""
     import oracle
+    if threads is not None:
+        saved = oracle.get_threads()
+        oracle.set_threads(threads)
+        try:
+            return oracle_sample(seconds_hint)
+        finally:
+            oracle.set_threads(saved)
     spec = workload_spec(16, cells=64)
     m = oracle.Mesh(spec, 0)
     lev, g = m.blocks()
@@ -838,7 +911,7 @@ def oracle_sample(seconds_hint=15.0):
             break
     return {"value": 2.0 * cells * steps / el, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
             "sample": "3D 64^3 cells as 4x4x4 periodic blocks of 16^3 (same seeded Fourier field), %d Heun steps, FP64" % steps,
-            "seconds": el}
+            "seconds": el, "cpu_model": cpu_model(), "nproc": os.cpu_count()}
 
 
 def run_reference(args):
@@ -909,6 +982,9 @@ def main():
     if rank == 0:
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = oracle_sample()
+            st1 = oracle_sample(8.0, threads=1)
+            line["cpu_baseline"]["single_thread"] = {"value": st1["value"], "unit": UNIT, "cores": 1,
+                                                     "sample": st1["sample"], "seconds": st1["seconds"]}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

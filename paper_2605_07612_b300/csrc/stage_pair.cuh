@@ -70,115 +70,108 @@ __device__ __forceinline__ void cp_async8(void *dst, const void *src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-// Rusanov / Einfeldt flux of a pair of faces with the same normal n
-// (compile-time NRM >= 0, or runtime n when NRM < 0).
-template <int NRM>
-__device__ __forceinline__ void pair_flux(const float2 *wL, const float2 *wR, int n, float gam, float gm1i, float2 *F) {
+// Rusanov or HLL flux (Sec. 3.2) of a pair of faces with the same normal
+// (compile-time NRM >= 0, or the runtime normal n when NRM < 0) from the
+// primitive states (rho, v_0 .. v_{D-1}, p) on either side, with Einfeldt's
+// signal speeds (Sec. 3.5): u_roe = (sqrt(rL) vnL + sqrt(rR) vnR) / S and
+// d^2 = gamma (pL / sqrt(rL) + pR / sqrt(rR)) / S
+//       + 1/2 sqrt(rL) sqrt(rR) / S^2 (vnR - vnL)^2,  S = sqrt(rL) + sqrt(rR)
+// (the weighted mean of c^2 = gamma p / rho written with p / sqrt(rho)).
+//
+// Both fluxes are evaluated with the terms of each conserved variable
+// grouped by side:
+//   F_rho = B_L + B_R,   B = A rho
+//   F_m   = B_L v_L + B_R v_R + (pi_L p_L + pi_R p_R) e_n
+//   F_E   = p_L (A_L g + pi_L vn_L) + p_R (A_R g + pi_R vn_R)
+//           + (B_L |v_L|^2 + B_R |v_R|^2) / 2,          g = 1 / (gamma - 1)
+// which is F = (F(wL) + F(wR)) / 2 - a (U_R - U_L) / 2 for Rusanov with
+// A_L = (vn_L + a) / 2, A_R = (vn_R - a) / 2, pi = 1/2, a = |u_roe| + d, and
+// F = (sR F(wL) - sL F(wR) + sL sR (U_R - U_L)) / (sR - sL) for HLL with
+// sL = min(u_roe - d, 0), sR = max(u_roe + d, 0), w = 1 / (sR - sL),
+// pi_L = w sR, pi_R = -w sL, A_L = pi_L (vn_L - sL), A_R = pi_R (vn_R - sR)
+// (E = p g + rho |v|^2 / 2 expanded).  The grouped form needs neither the
+// conservative face states nor both physical fluxes.
+template <int D, int FLX, int NRM>
+__device__ __forceinline__ void pair_flux_grouped(const float2 *wL, const float2 *wR, int n, float gam, float gm1i, float2 *F) {
     const int nn = NRM >= 0 ? NRM : n;
     float2 vnL, vnR;
-    if (NRM >= 0) {
-        vnL = wL[1 + (NRM >= 0 ? NRM : 0)];
-        vnR = wR[1 + (NRM >= 0 ? NRM : 0)];
+    if constexpr (NRM >= 0) {
+        vnL = wL[1 + NRM];
+        vnR = wR[1 + NRM];
+    } else if constexpr (D == 2) {
+        vnL = nn == 0 ? wL[1] : wL[2];
+        vnR = nn == 0 ? wR[1] : wR[2];
     } else {
         vnL = nn == 0 ? wL[1] : (nn == 1 ? wL[2] : wL[3]);
         vnR = nn == 0 ? wR[1] : (nn == 1 ? wR[2] : wR[3]);
     }
-    const float2 rL = wL[0], rR = wR[0], pL = wL[4], pR = wR[4];
+    const float2 rL = wL[0], rR = wR[0], pL = wL[D + 1], pR = wR[D + 1];
+    const float2 half = PF::sp(0.5f);
     const float2 qL = PF::rsqrt(rL), qR = PF::rsqrt(rR);
-    const float2 sL = PF::mul(rL, qL), sR = PF::mul(rR, qR);            // sqrt(rho)
-    const float2 iL = PF::mul(qL, qL), iR = PF::mul(qR, qR);            // 1 / rho
-    const float2 inv = PF::rcp(PF::add(sL, sR));
-    const float2 g2 = PF::sp(gam);
-    const float2 c2L = PF::mul(PF::mul(g2, pL), iL), c2R = PF::mul(PF::mul(g2, pR), iR);
+    const float2 sL = PF::mul(rL, qL), sR = PF::mul(rR, qR);               // sqrt(rho)
+    const float2 inv = PF::rcp(PF::add(sL, sR));                           // 1 / S
     const float2 uroe = PF::mul(PF::fma(sL, vnL, PF::mul(sR, vnR)), inv);
     const float2 du = PF::sub(vnR, vnL);
-    const float2 h = PF::mul(PF::mul(PF::mul(sL, sR), PF::mul(inv, inv)), PF::sp(0.5f));
-    const float2 d2 = PF::fma(PF::mul(h, du), du, PF::mul(PF::fma(sL, c2L, PF::mul(sR, c2R)), inv));
+    const float2 P = PF::fma(pR, qR, PF::mul(pL, qL));                     // pL / sqrt(rL) + pR / sqrt(rR)
+    const float2 x = PF::mul(PF::mul(sL, sR), inv);                        // sqrt(rL rR) / S
+    const float2 y = PF::mul(inv, du);                                      // du / S
+    const float2 d2 = PF::fma(PF::mul(x, y), PF::mul(half, du), PF::mul(PF::mul(PF::sp(gam), inv), P));
     const float2 d = PF::mul(d2, PF::rsqrt(d2));
-    const float2 a = PF::add(PF::abs(uroe), d);
-    float2 v2L = PF::mul(wL[1], wL[1]), v2R = PF::mul(wR[1], wR[1]);
-    v2L = PF::fma(wL[2], wL[2], v2L);
-    v2R = PF::fma(wR[2], wR[2], v2R);
-    v2L = PF::fma(wL[3], wL[3], v2L);
-    v2R = PF::fma(wR[3], wR[3], v2R);
-    const float2 half = PF::sp(0.5f);
-    const float2 EL = PF::fma(pL, PF::sp(gm1i), PF::mul(PF::mul(half, rL), v2L));
-    const float2 ER = PF::fma(pR, PF::sp(gm1i), PF::mul(PF::mul(half, rR), v2R));
-    const float2 nha = PF::mul(a, PF::sp(-0.5f));
-    const float2 mL = PF::mul(rL, vnL), mR = PF::mul(rR, vnR);
-    F[0] = PF::fma(nha, PF::sub(rR, rL), PF::mul(half, PF::add(mL, mR)));
-#pragma unroll
-    for (int d3 = 0; d3 < 3; ++d3) {
-        float2 fl = PF::fma(mL, wL[1 + d3], PF::mul(mR, wR[1 + d3]));
-        if (d3 == nn) fl = PF::add(fl, PF::add(pL, pR));
-        const float2 jump = PF::sub(PF::mul(rR, wR[1 + d3]), PF::mul(rL, wL[1 + d3]));
-        F[1 + d3] = PF::fma(nha, jump, PF::mul(half, fl));
+    float2 AL, AR, piL, piR;
+    if constexpr (FLX == 1) {
+        const float2 lo = PF::sub(uroe, d), hi = PF::add(uroe, d);
+        const float2 nsl = make_float2(fmaxf(-lo.x, 0.f), fmaxf(-lo.y, 0.f));   // -sL >= 0
+        const float2 sr = make_float2(fmaxf(hi.x, 0.f), fmaxf(hi.y, 0.f));     // sR >= 0
+        const float2 w = PF::rcp(PF::add(sr, nsl));
+        piL = PF::mul(w, sr);
+        piR = PF::mul(w, nsl);
+        AL = PF::mul(piL, PF::add(vnL, nsl));
+        AR = PF::mul(piR, PF::sub(vnR, sr));
+    } else {
+        const float2 ha = PF::mul(half, PF::add(PF::abs(uroe), d));
+        piL = PF::mul(half, vnL);                                          // here: vn / 2
+        piR = PF::mul(half, vnR);
+        AL = PF::add(piL, ha);
+        AR = PF::sub(piR, ha);
     }
-    const float2 fe = PF::fma(PF::add(EL, pL), vnL, PF::mul(PF::add(ER, pR), vnR));
-    F[4] = PF::fma(nha, PF::sub(ER, EL), PF::mul(half, fe));
+    const float2 BL = PF::mul(AL, rL), BR = PF::mul(AR, rR);
+    F[0] = PF::add(BL, BR);
+    float2 pn;
+    if constexpr (FLX == 1) pn = PF::fma(piR, pR, PF::mul(piL, pL));
+    else pn = PF::mul(half, PF::add(pL, pR));
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+        float2 f = PF::fma(BL, wL[1 + c], PF::mul(BR, wR[1 + c]));
+        if (c == nn) f = PF::add(f, pn);
+        F[1 + c] = f;
+    }
+    float2 v2L = PF::mul(wL[1], wL[1]), v2R = PF::mul(wR[1], wR[1]);
+#pragma unroll
+    for (int c = 1; c < D; ++c) {
+        v2L = PF::fma(wL[1 + c], wL[1 + c], v2L);
+        v2R = PF::fma(wR[1 + c], wR[1 + c], v2R);
+    }
+    const float2 g1 = PF::sp(gm1i);
+    // Rusanov: pi vn = vn^2 / 2 would be wrong -- the pressure work is p vn / 2
+    const float2 cL = FLX == 1 ? PF::fma(AL, g1, PF::mul(piL, vnL)) : PF::fma(AL, g1, piL);
+    const float2 cR = FLX == 1 ? PF::fma(AR, g1, PF::mul(piR, vnR)) : PF::fma(AR, g1, piR);
+    const float2 ke = PF::fma(BR, v2R, PF::mul(BL, v2L));
+    F[D + 1] = PF::fma(half, ke, PF::fma(pR, cR, PF::mul(pL, cL)));
 }
 
-// HLL flux (Harten, Lax and van Leer) of a pair of faces with the same
-// Einfeldt estimates as pair_flux: sL = min(u_roe - d, 0), sR = max(u_roe + d,
-// 0), F = (sR F_L - sL F_R + sL sR (U_R - U_L)) / (sR - sL).
+template <int NRM>
+__device__ __forceinline__ void pair_flux(const float2 *wL, const float2 *wR, int n, float gam, float gm1i, float2 *F) {
+    pair_flux_grouped<3, 0, NRM>(wL, wR, n, gam, gm1i, F);
+}
 template <int NRM>
 __device__ __forceinline__ void pair_flux_hll(const float2 *wL, const float2 *wR, int n, float gam, float gm1i, float2 *F) {
-    const int nn = NRM >= 0 ? NRM : n;
-    float2 vnL, vnR;
-    if (NRM >= 0) {
-        vnL = wL[1 + (NRM >= 0 ? NRM : 0)];
-        vnR = wR[1 + (NRM >= 0 ? NRM : 0)];
-    } else {
-        vnL = nn == 0 ? wL[1] : (nn == 1 ? wL[2] : wL[3]);
-        vnR = nn == 0 ? wR[1] : (nn == 1 ? wR[2] : wR[3]);
-    }
-    const float2 rL = wL[0], rR = wR[0], pL = wL[4], pR = wR[4];
-    const float2 qL = PF::rsqrt(rL), qR = PF::rsqrt(rR);
-    const float2 sqL = PF::mul(rL, qL), sqR = PF::mul(rR, qR);
-    const float2 iL = PF::mul(qL, qL), iR = PF::mul(qR, qR);
-    const float2 inv = PF::rcp(PF::add(sqL, sqR));
-    const float2 g2 = PF::sp(gam);
-    const float2 c2L = PF::mul(PF::mul(g2, pL), iL), c2R = PF::mul(PF::mul(g2, pR), iR);
-    const float2 uroe = PF::mul(PF::fma(sqL, vnL, PF::mul(sqR, vnR)), inv);
-    const float2 du = PF::sub(vnR, vnL);
-    const float2 h = PF::mul(PF::mul(PF::mul(sqL, sqR), PF::mul(inv, inv)), PF::sp(0.5f));
-    const float2 d2 = PF::fma(PF::mul(h, du), du, PF::mul(PF::fma(sqL, c2L, PF::mul(sqR, c2R)), inv));
-    const float2 d = PF::mul(d2, PF::rsqrt(d2));
-    const float2 lo = PF::sub(uroe, d), hi = PF::add(uroe, d);
-    const float2 sL = make_float2(fminf(lo.x, 0.f), fminf(lo.y, 0.f));
-    const float2 sR = make_float2(fmaxf(hi.x, 0.f), fmaxf(hi.y, 0.f));
-    const float2 iw = PF::rcp(PF::sub(sR, sL)), sLR = PF::mul(sL, sR);
-    float2 v2L = PF::mul(wL[1], wL[1]), v2R = PF::mul(wR[1], wR[1]);
-    v2L = PF::fma(wL[2], wL[2], v2L);
-    v2R = PF::fma(wR[2], wR[2], v2R);
-    v2L = PF::fma(wL[3], wL[3], v2L);
-    v2R = PF::fma(wR[3], wR[3], v2R);
-    const float2 half = PF::sp(0.5f);
-    const float2 EL = PF::fma(pL, PF::sp(gm1i), PF::mul(PF::mul(half, rL), v2L));
-    const float2 ER = PF::fma(pR, PF::sp(gm1i), PF::mul(PF::mul(half, rR), v2R));
-    const float2 mL = PF::mul(rL, vnL), mR = PF::mul(rR, vnR);
-    // (sR fL - sL fR + sL sR jump) / (sR - sL)
-    auto comb = [&](float2 fL, float2 fR, float2 jump) {
-        return PF::mul(PF::fma(sLR, jump, PF::sub(PF::mul(sR, fL), PF::mul(sL, fR))), iw);
-    };
-    F[0] = comb(mL, mR, PF::sub(rR, rL));
-#pragma unroll
-    for (int d3 = 0; d3 < 3; ++d3) {
-        float2 fL = PF::mul(mL, wL[1 + d3]), fR = PF::mul(mR, wR[1 + d3]);
-        if (d3 == nn) {
-            fL = PF::add(fL, pL);
-            fR = PF::add(fR, pR);
-        }
-        F[1 + d3] = comb(fL, fR, PF::sub(PF::mul(rR, wR[1 + d3]), PF::mul(rL, wL[1 + d3])));
-    }
-    F[4] = comb(PF::mul(PF::add(EL, pL), vnL), PF::mul(PF::add(ER, pR), vnR), PF::sub(ER, EL));
+    pair_flux_grouped<3, 1, NRM>(wL, wR, n, gam, gm1i, F);
 }
 
 // the pair flux of the configured scheme (FLX 0 Rusanov, 1 HLL)
 template <int FLX, int NRM>
 __device__ __forceinline__ void pair_face_flux(const float2 *wL, const float2 *wR, int n, float gam, float gm1i, float2 *F) {
-    if constexpr (FLX == 1) pair_flux_hll<NRM>(wL, wR, n, gam, gm1i, F);
-    else pair_flux<NRM>(wL, wR, n, gam, gm1i, F);
+    pair_flux_grouped<3, FLX, NRM>(wL, wR, n, gam, gm1i, F);
 }
 
 // Half of the limited slope of a pair of cells from their one-sided
@@ -250,39 +243,50 @@ struct PairShape {
     static constexpr int T = T_, NG = 2, S = N + 2 * NG, P = T + 4, PL = P * P, R = 4, V = 5;
     static constexpr int NT = T * T / 2;              // threads: one per cell pair of a plane
     static constexpr int TILES = (N / T) * (N / T);
-    // x-flux row pitch (T + 1 faces + pad); for T = 16 it is 20 words, so the
-    // rows r and r + 4 that a half-warp touches fall into opposite bank halves
-    static constexpr int FXP = T == 16 ? 20 : T + 2;
-    static constexpr int NFX = T * FXP;
-    static constexpr int NFY = (T + 1) * T;
-    static constexpr int FBUF = V * (NFX + NFY);      // one flux buffer
     static constexpr int LOADS = ((T * T + 8 * T) / 2 + NT - 1) / NT;   // halo pairs without corners
-    // y-flux row `row` (T + 1 rows of T faces): for T = 16 rows 2m and 2m + 1
-    // share a 32-word line, their halves swapped when bit 2 of the row is
-    // set, so rows r and r + 4 (one half-warp) use opposite bank halves
+    // upper y-face of row `row` (T rows of T faces): for T = 16 rows 2m and
+    // 2m + 1 share a 32-word line, their halves swapped when bit 2 of the row
+    // is set, so rows r and r + 4 (one half-warp) use opposite bank halves
     __device__ static __forceinline__ int fy(int row, int c) {
         if constexpr (T == 16) return 32 * (row >> 1) + 16 * ((row ^ (row >> 2)) & 1) + c;
         else return row * T + c;
     }
-    // ring, one flux buffer, and (nprev > 0) each thread's previous-state
-    // pairs of the plane being updated [nprev][V][NT]
+    static constexpr int FYB = V * T * T;             // one y-face buffer
+    static constexpr int EXB = V * T;                 // one buffer of the tile's upper x-faces
+    // ring, two y-face buffers, two upper-x-face buffers, and (nprev > 0)
+    // each thread's previous-state pairs of the plane being updated [nprev][V][NT]
     static constexpr size_t smem_bytes(int nprev) {
-        return sizeof(float) * (size_t(R) * V * PL + size_t(FBUF)) + sizeof(float2) * size_t(nprev > 0 ? nprev : 0) * V * NT;
+        return sizeof(float) * (size_t(R) * V * PL + 2 * size_t(FYB) + 2 * size_t(EXB)) +
+               sizeof(float2) * size_t(nprev > 0 ? nprev : 0) * V * NT;
     }
 };
 
-// NPREV >= 0: the number of previous states, fixed at compile time (Heun's two
-// stages use 1 and 2); -1 reads it from the arguments.  FLX: 0 Rusanov, 1 HLL.
+// One CTA's (block, tile) item.  Per plane k (one barrier):
+//   flux phase:  copy plane k's previous states (cp.async); the x-, y- and
+//                z-face fluxes of the thread's cell pair; its divergence
+//                accumulated in registers except the upper y-face (from
+//                the thread of the next row, through shared memory); the
+//                first warp computes the tile's upper x-faces of plane k+1
+//                and upper y-faces of plane k; commit plane k+3, load k+4
+//   barrier
+//   update:      subtract the upper y-face, combine with the previous
+//                states and store
+// The right x-face of a pair comes from the next lane of the row (shuffle),
+// or for the last pair of a row from the upper x-faces computed one plane
+// ahead; the lower y-face of a row is the thread's own flux.  y- and x-face
+// buffers alternate with the parity of k, so the next plane's flux phase can
+// overwrite nothing the update still reads.
 template <int N, int TT, int NPREV, int LIM, int FLX>
 __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const Geom &g, int item) {
     using Sh = PairShape<N, TT>;
     constexpr int T = Sh::T, NG = Sh::NG, S = Sh::S, P = Sh::P, PL = Sh::PL, V = Sh::V, NT = Sh::NT;
-    constexpr int FXP = Sh::FXP, NFX = Sh::NFX, FBUF = Sh::FBUF;
+    constexpr int FYB = Sh::FYB, EXB = Sh::EXB, HP = T / 2;
     constexpr int64_t NC = int64_t(S) * S * S;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float *ring = reinterpret_cast<float *>(smem_raw);         // [R][V][P*P]
-    float *fbuf = ring + Sh::R * V * PL;                        // Fx [V][T][FXP], Fy [V][T+1][T]
-    float2 *stg = reinterpret_cast<float2 *>(fbuf + FBUF);      // [NPREV][V][NT] previous states
+    float *fyb = ring + Sh::R * V * PL;                         // [2][V][T x T] upper y-faces
+    float *exb = fyb + 2 * FYB;                                 // [2][V][T] upper x-faces
+    float2 *stg = reinterpret_cast<float2 *>(exb + 2 * EXB);    // [NPREV][V][NT] previous states
 
     const int tid = threadIdx.x;
     const int b = item / Sh::TILES;
@@ -298,10 +302,11 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
         ip = lane & 7;
         tj = (q & 3) + (q >> 2) * 8 + ((lane >> 3) & 1) * 4;
     } else {
-        ip = tid % (T / 2);
-        tj = tid / (T / 2);
+        ip = tid % HP;
+        tj = tid / HP;
     }
     const int ci = 2 * ip;                                      // first cell of the pair
+    const bool last = ip == HP - 1;                             // the pair at the tile's upper x edge
     const BlockInfo info = a.info[b];
     const int gc = info.gclass;
     const float idx0 = float(g.inv_dx[3 * gc]), idx1 = float(g.inv_dx[3 * gc + 1]), idx2 = float(g.inv_dx[3 * gc + 2]);
@@ -313,11 +318,15 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
     const int nb0 = a.gather ? info.nbr[0] : -1, nb1 = a.gather ? info.nbr[1] : -1;
     const int nb2 = a.gather ? info.nbr[2] : -1, nb3 = a.gather ? info.nbr[3] : -1;
     const int nb4 = a.gather ? info.nbr[4] : -1, nb5 = a.gather ? info.nbr[5] : -1;
+    // refinement-face flux slots this thread stores into (-1: none)
+    const int bs_x0 = (ci == 0 && tx0 == 0) ? info.bslot[0] : -1;
+    const int bs_y0 = (tj == 0 && ty0 == 0) ? info.bslot[2] : -1;
+    const int bs_z0 = info.bslot[4], bs_z1 = info.bslot[5];
 
     bool nonphys = false;
     float vmax = 0.f;
 
-    auto slot = [&](int k) -> float * { return ring + ((k + 2) % Sh::R) * V * PL; };
+    auto slot = [&](int k) -> float * { return ring + ((k + 2) & (Sh::R - 1)) * V * PL; };
     auto gofs = [&](int i, int j, int k) -> int64_t { return (int64_t(k + NG) * S + (j + NG)) * S + (i + NG); };
     // source of cell (tx0 + ii, ty0 + jj, k): this block, or a same-level
     // neighbour's interior in gather mode
@@ -344,7 +353,7 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
     // computes the tile's edge faces).  The source of a thread's pairs does
     // not change with k, so its address at k = 0 is kept.  The planes k < 0
     // and k >= N need only the tile: thread tid takes its own pair.
-    constexpr int HP = T / 2, WP = (T + 4) / 2;
+    constexpr int WP = (T + 4) / 2;
     constexpr int NPAIR = 2 * HP + T * WP + 2 * HP, REST = NPAIR - NT;
     static_assert(Sh::LOADS == 2 && REST > 0 && REST <= NT, "two load rounds per plane");
     auto pair_rc = [&](int p, int &ii, int &jj) {
@@ -378,7 +387,7 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
             hoff[l] = (jj + 2) * P + ii + 2;
         }
     }
-    const int own_off = (tid / (T / 2) + 2) * P + 2 * (tid % (T / 2)) + 2;
+    const int own_off = (tid / HP + 2) * P + 2 * (tid % HP) + 2;
 
     float2 pre[Sh::LOADS][V];
     auto prefetch = [&](int k) {
@@ -391,7 +400,7 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
                     for (int v = 0; v < V; ++v) pre[l][v] = *reinterpret_cast<const float2 *>(hsrc[l] + ko + v * NC);
         } else {
             int64_t o;
-            const float *src = src_of(2 * (tid % (T / 2)), tid / (T / 2), k, o);
+            const float *src = src_of(2 * (tid % HP), tid / HP, k, o);
 #pragma unroll
             for (int v = 0; v < V; ++v) pre[0][v] = *reinterpret_cast<const float2 *>(src + v * NC + o);
         }
@@ -418,9 +427,7 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
     };
 
     const int nface_b = N * N;
-    auto store_bflux1 = [&](int f, int t, float Fv0, float Fv1, float Fv2, float Fv3, float Fv4) {
-        const int sl = info.bslot[f];
-        if (sl < 0) return;
+    auto store_bflux1 = [&](int sl, int t, float Fv0, float Fv1, float Fv2, float Fv3, float Fv4) {
         float *dst = a.bflux + int64_t(sl) * V * nface_b + t;
         dst[0] = Fv0;
         dst[nface_b] = Fv1;
@@ -429,9 +436,7 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
         dst[4 * nface_b] = Fv4;
     };
     // store both faces of a pair (tangential indices t and t + 1)
-    auto store_bflux2 = [&](int f, int t, const float2 *F) {
-        const int sl = info.bslot[f];
-        if (sl < 0) return;
+    auto store_bflux2 = [&](int sl, int t, const float2 *F) {
         float *dst = a.bflux + int64_t(sl) * V * nface_b + t;
 #pragma unroll
         for (int v = 0; v < V; ++v) {
@@ -440,39 +445,95 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
         }
     };
 
-    // ---- fluxes of plane k into buffer fb
-    float2 FzA[V], FzB[V];   // z fluxes below / above the plane being updated
-    float2 zP[V];            // plus z state of the pair at the plane whose fluxes come next
-    auto fluxes = [&](int k, float *fb, float2 *Fz_new) {
-        float *Fx = fb, *Fy = fb + V * NFX;
-        const float *pl = slot(k);
+    // The first warp's edge faces: lanes r < T/2 the upper x-face of rows
+    // (2r, 2r+1) of plane kx, lanes T/2 + r the upper y-face of columns
+    // (2r, 2r+1) of plane ky; one flux evaluation with a runtime normal.
+    // Lane offsets in a ring plane: base + i st (+ po for the second face).
+    const int bs_x1 = (tx0 + T == N) ? info.bslot[1] : -1;
+    const int bs_y1 = (ty0 + T == N) ? info.bslot[3] : -1;
+    auto edge_faces = [&](int kx, int ky, bool do_x) {
+        const bool e_isx = tid < HP;
+        const int e_r = e_isx ? tid : tid - HP;
+        const int e_base = e_isx ? (2 * e_r + 2) * P + T : T * P + 2 + 2 * e_r;
+        const int e_st = e_isx ? 1 : P, e_po = e_isx ? P : 1;
+        if (e_isx && !do_x) return;
+        const float *pl = (e_isx ? slot(kx) : slot(ky)) + e_base;
         float2 wL[V], wR[V], F[V];
-        // x-faces ci, ci+1 of row tj
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            const float2 A = ld2(pl, v, tj, ci - 2), B = ld2(pl, v, tj, ci), C2 = ld2(pl, v, tj, ci + 2);
-            pair_states<LIM>(A, make_float2(A.y, B.x), B, make_float2(B.y, C2.x), wL[v], wR[v]);
+            const float *b0 = pl + v * PL;
+            pair_states<LIM>(make_float2(b0[0], b0[e_po]), make_float2(b0[e_st], b0[e_st + e_po]),
+                             make_float2(b0[2 * e_st], b0[2 * e_st + e_po]), make_float2(b0[3 * e_st], b0[3 * e_st + e_po]),
+                             wL[v], wR[v]);
+        }
+        pair_face_flux<FLX, -1>(wL, wR, e_isx ? 0 : 1, gam, gm1i, F);
+        if (e_isx) {
+            float *ex = exb + (kx & 1) * EXB + 2 * e_r;
+#pragma unroll
+            for (int v = 0; v < V; ++v) *reinterpret_cast<float2 *>(ex + v * T) = F[v];
+            if (bs_x1 >= 0) {
+                store_bflux1(bs_x1, ty0 + 2 * e_r + N * kx, F[0].x, F[1].x, F[2].x, F[3].x, F[4].x);
+                store_bflux1(bs_x1, ty0 + 2 * e_r + 1 + N * kx, F[0].y, F[1].y, F[2].y, F[3].y, F[4].y);
+            }
+        } else {
+            float *fy = fyb + (ky & 1) * FYB;
+#pragma unroll
+            for (int v = 0; v < V; ++v) *reinterpret_cast<float2 *>(fy + v * T * T + Sh::fy(T - 1, 2 * e_r)) = F[v];
+            if (bs_y1 >= 0) store_bflux2(bs_y1, tx0 + 2 * e_r + N * ky, F);
+        }
+    };
+
+    // ---- flux phase of plane k: the divergence of the pair's fluxes into
+    // du (all faces but the upper y-face); Fz holds the z flux below the
+    // plane on entry and above it on return
+    float2 Fz[V];            // z flux below the plane being updated
+    float2 zP[V];            // plus z state of the pair at the plane whose fluxes come next
+    float2 du[V];
+    const float2 i0 = PF::sp(idx0), i1 = PF::sp(idx1), i2 = PF::sp(idx2);
+    auto fluxes = [&](int k) {
+        const float *pl = slot(k);
+        float2 Bw[V], wL[V], wR[V], F[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) Bw[v] = ld2(pl, v, tj, ci);
+        // x-faces ci - 1/2, ci + 1/2 of row tj
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const float2 A = ld2(pl, v, tj, ci - 2), C2 = ld2(pl, v, tj, ci + 2);
+            pair_states<LIM>(A, make_float2(A.y, Bw[v].x), Bw[v], make_float2(Bw[v].y, C2.x), wL[v], wR[v]);
         }
         pair_face_flux<FLX, 0>(wL, wR, 0, gam, gm1i, F);
+        if (bs_x0 >= 0) store_bflux1(bs_x0, ty0 + tj + N * k, F[0].x, F[1].x, F[2].x, F[3].x, F[4].x);
+        const float *ex = exb + (k & 1) * EXB + tj;
 #pragma unroll
-        for (int v = 0; v < V; ++v) *reinterpret_cast<float2 *>(Fx + v * NFX + tj * FXP + ci) = F[v];
-        if (ci == 0 && tx0 == 0) store_bflux1(0, ty0 + tj + N * k, F[0].x, F[1].x, F[2].x, F[3].x, F[4].x);
-        // y-face tj (between rows tj-1 and tj) of columns ci, ci+1
+        for (int v = 0; v < V; ++v) {
+            // the face right of the pair: the next lane's first face, or the
+            // tile's upper x-face for the last pair of the row
+            const float nx = __shfl_down_sync(0xffffffffu, F[v].x, 1, HP);
+            const float right = last ? ex[v * T] : nx;
+            du[v] = PF::mul(PF::sub(F[v], make_float2(F[v].y, right)), i0);
+        }
+        // y-face tj - 1/2 (between rows tj-1 and tj) of columns ci, ci+1: the
+        // lower face of this row, the upper face of row tj - 1
 #pragma unroll
         for (int v = 0; v < V; ++v)
-            pair_states<LIM>(ld2(pl, v, tj - 2, ci), ld2(pl, v, tj - 1, ci), ld2(pl, v, tj, ci), ld2(pl, v, tj + 1, ci), wL[v], wR[v]);
+            pair_states<LIM>(ld2(pl, v, tj - 2, ci), ld2(pl, v, tj - 1, ci), Bw[v], ld2(pl, v, tj + 1, ci), wL[v], wR[v]);
         pair_face_flux<FLX, 1>(wL, wR, 1, gam, gm1i, F);
+        if (tj > 0) {
+            float *fy = fyb + (k & 1) * FYB + Sh::fy(tj - 1, ci);
 #pragma unroll
-        for (int v = 0; v < V; ++v) *reinterpret_cast<float2 *>(Fy + v * (T + 1) * T + Sh::fy(tj, ci)) = F[v];
-        if (tj == 0 && ty0 == 0) store_bflux2(2, tx0 + ci + N * k, F);
+            for (int v = 0; v < V; ++v) *reinterpret_cast<float2 *>(fy + v * T * T) = F[v];
+        }
+        if (bs_y0 >= 0) store_bflux2(bs_y0, tx0 + ci + N * k, F);
+#pragma unroll
+        for (int v = 0; v < V; ++v) du[v] = PF::fma(F[v], i1, du[v]);
         // z-face k + 1/2 of cells ci, ci+1: the plus state of plane k is
         // carried from the previous plane, the minus / plus states of plane
         // k+1 come from planes k .. k+2
         {
-            const float *p1 = pl, *p2 = slot(k + 1), *p3 = slot(k + 2);
+            const float *p2 = slot(k + 1), *p3 = slot(k + 2);
 #pragma unroll
             for (int v = 0; v < V; ++v) {
-                const float2 w1 = ld2(p1, v, tj, ci), w2 = ld2(p2, v, tj, ci), w3 = ld2(p3, v, tj, ci);
+                const float2 w1 = Bw[v], w2 = ld2(p2, v, tj, ci), w3 = ld2(p3, v, tj, ci);
                 if constexpr (LIM == 0) {
                     const float2 d12 = PF::sub(w2, w1), d23 = PF::sub(w3, w2), q = PF::qs(d12, d23);
                     wR[v] = PF::fma(q, PF::nmabs(d12, d23), w2);
@@ -483,45 +544,26 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
                     pair_cell_states<LIM>(w1, w2, w3, wR[v], zP[v]);
                 }
             }
-            pair_face_flux<FLX, 2>(wL, wR, 2, gam, gm1i, Fz_new);
-            if (k == N - 1) store_bflux2(5, tx0 + ci + N * (ty0 + tj), Fz_new);
-        }
-        // the tile's upper edge faces, both in the first warp: lanes r < T/2
-        // take x-face T of rows (2r, 2r+1), lanes T/2 + r y-face T of
-        // columns (2r, 2r+1); one flux evaluation with a runtime normal
-        if (tid < T) {
-            const bool isx = tid < T / 2;
-            const int r = isx ? tid : tid - T / 2;
-            const int base = isx ? (2 * r + 2) * P + T : T * P + 2 + 2 * r;
-            const int st = isx ? 1 : P, po = isx ? P : 1;
+            pair_face_flux<FLX, 2>(wL, wR, 2, gam, gm1i, F);
+            if (k == N - 1 && bs_z1 >= 0) store_bflux2(bs_z1, tx0 + ci + N * (ty0 + tj), F);
 #pragma unroll
             for (int v = 0; v < V; ++v) {
-                const float *b0 = pl + v * PL + base;
-                pair_states<LIM>(make_float2(b0[0], b0[po]), make_float2(b0[st], b0[st + po]),
-                                 make_float2(b0[2 * st], b0[2 * st + po]), make_float2(b0[3 * st], b0[3 * st + po]), wL[v], wR[v]);
+                du[v] = PF::fma(PF::sub(Fz[v], F[v]), i2, du[v]);
+                Fz[v] = F[v];
             }
-            pair_face_flux<FLX, -1>(wL, wR, isx ? 0 : 1, gam, gm1i, F);
-            if (isx) {
+        }
+        // gravity source S = (0, rho g, rho g.u) of the cells' primitives
+        if (a.gravity_on) {
+            const float2 rho = Bw[0];
+            float2 vg = PF::mul(Bw[1], PF::sp(a.grav[0]));
+            vg = PF::fma(Bw[2], PF::sp(a.grav[1]), vg);
+            vg = PF::fma(Bw[3], PF::sp(a.grav[2]), vg);
 #pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    Fx[v * NFX + (2 * r) * FXP + T] = F[v].x;
-                    Fx[v * NFX + (2 * r + 1) * FXP + T] = F[v].y;
-                }
-                if (tx0 + T == N) {
-                    store_bflux1(1, ty0 + 2 * r + N * k, F[0].x, F[1].x, F[2].x, F[3].x, F[4].x);
-                    store_bflux1(1, ty0 + 2 * r + 1 + N * k, F[0].y, F[1].y, F[2].y, F[3].y, F[4].y);
-                }
-            } else {
-#pragma unroll
-                for (int v = 0; v < V; ++v) *reinterpret_cast<float2 *>(Fy + v * (T + 1) * T + Sh::fy(T, 2 * r)) = F[v];
-                if (ty0 + T == N) store_bflux2(3, tx0 + 2 * r + N * k, F);
-            }
+            for (int c = 0; c < 3; ++c) du[1 + c] = PF::fma(rho, PF::sp(a.grav[c]), du[1 + c]);
+            du[4] = PF::fma(rho, vg, du[4]);
         }
     };
 
-    // ---- L2 prefetch, one plane period ahead: the previous states' plane k
-    // (read by the update of plane k in the next iteration) and this block's
-    // derivative plane k + 5 (loaded into registers two iterations later)
     // ---- L2 prefetch: the previous states' plane k (copied to shared memory
     // at the start of the next plane period) and this block's derivative
     // plane k + 4 (loaded into registers in the next plane period)
@@ -554,34 +596,23 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
         }
     };
 
-    auto update = [&](int k, const float *fb, const float2 *Fzlo, const float2 *Fzhi) {
+    // cells next to a coarse-side refinement face are reduced after flux
+    // fixing (the parts of that test that do not depend on k)
+    const int fmask = info.fixmask;
+    const int gi0 = tx0 + ci, gj0 = ty0 + tj;
+    const bool rowfix_jk = ((fmask & 4) && gj0 == 0) || ((fmask & 8) && gj0 == N - 1);
+    const bool colfix0 = (fmask & 1) && gi0 == 0, colfix1 = (fmask & 2) && gi0 + 1 == N - 1;
+
+    auto update = [&](int k) {
         if constexpr (NPREV > 0) cp_async_wait_all();
-        const float *Fx = fb, *Fy = fb + V * NFX;
-        const int64_t o = gofs(tx0 + ci, ty0 + tj, k);
-        const int64_t ob = int64_t(b) * V * NC + o;
-        const float2 i0 = PF::sp(idx0), i1 = PF::sp(idx1), i2 = PF::sp(idx2), dte = PF::sp(dt_eff);
+        const float *fy = fyb + (k & 1) * FYB + Sh::fy(tj, ci);
+        const int64_t ob = int64_t(b) * V * NC + gofs(tx0 + ci, ty0 + tj, k);
+        const float2 dte = PF::sp(dt_eff);
         float2 U[V];
-        // gravity source S = (0, rho g, rho g.u) of variable v from the
-        // primitives of plane k, still in the ring
-        auto source = [&](int v) -> float2 {
-            const float *pk = slot(k);
-            const float2 rho = ld2(pk, 0, tj, ci);
-            if (v < 4) return PF::mul(rho, PF::sp(a.grav[v - 1]));
-            float2 vg = PF::mul(ld2(pk, 1, tj, ci), PF::sp(a.grav[0]));
-            vg = PF::fma(ld2(pk, 2, tj, ci), PF::sp(a.grav[1]), vg);
-            vg = PF::fma(ld2(pk, 3, tj, ci), PF::sp(a.grav[2]), vg);
-            return PF::mul(rho, vg);
-        };
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            const float2 x0 = *reinterpret_cast<const float2 *>(Fx + v * NFX + tj * FXP + ci);
-            const float2 x1 = *reinterpret_cast<const float2 *>(Fx + v * NFX + tj * FXP + ci + 2);
-            const float2 y0 = *reinterpret_cast<const float2 *>(Fy + v * (T + 1) * T + Sh::fy(tj, ci));
-            const float2 y1 = *reinterpret_cast<const float2 *>(Fy + v * (T + 1) * T + Sh::fy(tj + 1, ci));
-            float2 du = PF::mul(PF::sub(x0, make_float2(x0.y, x1.x)), i0);
-            du = PF::fma(PF::sub(y0, y1), i1, du);
-            du = PF::fma(PF::sub(Fzlo[v], Fzhi[v]), i2, du);
-            if (v > 0 && a.gravity_on) du = PF::add(du, source(v));
+            const float2 up = *reinterpret_cast<const float2 *>(fy + v * T * T);
+            const float2 d = PF::fma(up, PF::sp(-idx1), du[v]);
             float2 acc = PF::sp(0.f);
             if constexpr (NPREV > 0) {
 #pragma unroll
@@ -592,23 +623,17 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
                     if (q < a.nprev)
                         acc = PF::fma(PF::sp(a.wprev[q]), *reinterpret_cast<const float2 *>(a.prev[q] + ob + v * NC), acc);
             }
-            U[v] = PF::fma(dte, du, acc);
+            U[v] = PF::fma(dte, d, acc);
             *reinterpret_cast<float2 *>(a.out + ob + v * NC) = U[v];
         }
         // complete the row's DRAM sectors: the output's x-ghost cells
-        if (tx0 + ci == 0 || tx0 + ci + 1 == N - 1) {
-            const int64_t og = ob + (tx0 + ci == 0 ? -NG : 2);
+        if (gi0 == 0 || gi0 + 1 == N - 1) {
+            const int64_t og = ob + (gi0 == 0 ? -NG : 2);
 #pragma unroll
             for (int v = 0; v < V; ++v) *reinterpret_cast<float2 *>(a.out + og + v * NC) = PF::sp(0.f);
         }
         if (a.update_dt) {
-            const int gi = tx0 + ci, gj = ty0 + tj;
-            const int m = info.fixmask;
-            // cells next to a coarse-side refinement face are reduced after flux fixing
-            const bool rowfix = ((m & 4) && gj == 0) || ((m & 8) && gj == N - 1) || ((m & 16) && k == 0) ||
-                                ((m & 32) && k == N - 1);
-            const bool fx0 = rowfix || ((m & 1) && gi == 0);
-            const bool fx1 = rowfix || ((m & 2) && gi + 1 == N - 1);
+            const bool rowfix = rowfix_jk || ((fmask & 16) && k == 0) || ((fmask & 32) && k == N - 1);
             float2 w[V];
             pair_prim(U, w, gam);
             const float2 c2 = PF::mul(PF::mul(PF::sp(gam), w[4]), PF::rcp(w[0]));
@@ -616,8 +641,8 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
             float2 s = PF::mul(PF::add(PF::abs(w[1]), c), i0);
             s = PF::fma(PF::add(PF::abs(w[2]), c), i1, s);
             s = PF::fma(PF::add(PF::abs(w[3]), c), i2, s);
-            if (!fx0) vmax = s.x > vmax ? s.x : vmax;
-            if (!fx1) vmax = s.y > vmax ? s.y : vmax;
+            if (!(rowfix || colfix0)) vmax = s.x > vmax ? s.x : vmax;
+            if (!(rowfix || colfix1)) vmax = s.y > vmax ? s.y : vmax;
         }
     };
 
@@ -635,7 +660,7 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
     __syncthreads();
     {
         // z flux through the block's lower face (k = -1/2) and the plus
-        // state of plane 0
+        // state of plane 0; the tile's upper x-faces of plane 0
         const float *p0 = slot(-2), *p1 = slot(-1), *p2 = slot(0), *p3 = slot(1);
         float2 wL[V], wR[V];
 #pragma unroll
@@ -650,30 +675,27 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
                 pair_cell_states<LIM>(w1, w2, w3, zm, zP[v]);
             }
         }
-        pair_face_flux<FLX, 2>(wL, wR, 2, gam, gm1i, FzA);
-        store_bflux2(4, tx0 + ci + N * (ty0 + tj), FzA);
+        pair_face_flux<FLX, 2>(wL, wR, 2, gam, gm1i, Fz);
+        if (bs_z0 >= 0) store_bflux2(bs_z0, tx0 + ci + N * (ty0 + tj), Fz);
+        if (tid < HP) edge_faces(0, 0, true);
     }
     __syncthreads();
     commit(2);          // into the slot of plane -2
     prefetch(3);
     __syncthreads();
-    // plane k: copy its previous states, compute its x/y fluxes and the z flux
-    // above it, commit plane k+3 into the slot of plane k-1 and load plane
-    // k+4; barrier; update plane k; barrier (flux buffer reused)
     for (int k = 0; k < N; ++k) {
         stage_prev(k);
         l2_ahead(k + 1);
-        fluxes(k, fbuf, FzB);
+        fluxes(k);
+        if (tid < T) edge_faces(k + 1, k, k + 1 < N);
         if (k + 3 <= N + 1) {
             commit(k + 3);
             if (k + 4 <= N + 1) prefetch(k + 4);
         }
         __syncthreads();
-        update(k, fbuf, FzA, FzB);
-#pragma unroll
-        for (int v = 0; v < V; ++v) FzA[v] = FzB[v];
-        __syncthreads();
+        update(k);
     }
+    __syncthreads();   // the next item's prologue overwrites the ring and the face buffers
 
     if (a.update_dt) {
         double m = double(vmax);

@@ -17,92 +17,12 @@
 
 namespace amrb {
 
-// Rusanov / Einfeldt flux of a pair of faces with normal NRM (0 x, 1 y; or
-// NRM < 0 and the runtime normal n) from primitive states (rho, u, v, p).
-template <int NRM>
-__device__ __forceinline__ void pair_flux2d(const float2 *wL, const float2 *wR, int n, float gam, float gm1i, float2 *F) {
-    const int nn = NRM >= 0 ? NRM : n;
-    const float2 vnL = nn == 0 ? wL[1] : wL[2], vnR = nn == 0 ? wR[1] : wR[2];
-    const float2 rL = wL[0], rR = wR[0], pL = wL[3], pR = wR[3];
-    const float2 qL = PF::rsqrt(rL), qR = PF::rsqrt(rR);
-    const float2 sL = PF::mul(rL, qL), sR = PF::mul(rR, qR);
-    const float2 iL = PF::mul(qL, qL), iR = PF::mul(qR, qR);
-    const float2 inv = PF::rcp(PF::add(sL, sR));
-    const float2 g2 = PF::sp(gam);
-    const float2 c2L = PF::mul(PF::mul(g2, pL), iL), c2R = PF::mul(PF::mul(g2, pR), iR);
-    const float2 uroe = PF::mul(PF::fma(sL, vnL, PF::mul(sR, vnR)), inv);
-    const float2 du = PF::sub(vnR, vnL);
-    const float2 h = PF::mul(PF::mul(PF::mul(sL, sR), PF::mul(inv, inv)), PF::sp(0.5f));
-    const float2 d2 = PF::fma(PF::mul(h, du), du, PF::mul(PF::fma(sL, c2L, PF::mul(sR, c2R)), inv));
-    const float2 d = PF::mul(d2, PF::rsqrt(d2));
-    const float2 a = PF::add(PF::abs(uroe), d);
-    const float2 v2L = PF::fma(wL[2], wL[2], PF::mul(wL[1], wL[1]));
-    const float2 v2R = PF::fma(wR[2], wR[2], PF::mul(wR[1], wR[1]));
-    const float2 half = PF::sp(0.5f);
-    const float2 EL = PF::fma(pL, PF::sp(gm1i), PF::mul(PF::mul(half, rL), v2L));
-    const float2 ER = PF::fma(pR, PF::sp(gm1i), PF::mul(PF::mul(half, rR), v2R));
-    const float2 nha = PF::mul(a, PF::sp(-0.5f));
-    const float2 mL = PF::mul(rL, vnL), mR = PF::mul(rR, vnR);
-    F[0] = PF::fma(nha, PF::sub(rR, rL), PF::mul(half, PF::add(mL, mR)));
-#pragma unroll
-    for (int d2i = 0; d2i < 2; ++d2i) {
-        float2 fl = PF::fma(mL, wL[1 + d2i], PF::mul(mR, wR[1 + d2i]));
-        if (d2i == nn) fl = PF::add(fl, PF::add(pL, pR));
-        const float2 jump = PF::sub(PF::mul(rR, wR[1 + d2i]), PF::mul(rL, wL[1 + d2i]));
-        F[1 + d2i] = PF::fma(nha, jump, PF::mul(half, fl));
-    }
-    const float2 fe = PF::fma(PF::add(EL, pL), vnL, PF::mul(PF::add(ER, pR), vnR));
-    F[3] = PF::fma(nha, PF::sub(ER, EL), PF::mul(half, fe));
-}
-
-// HLL flux of a pair of 2D faces with the Einfeldt estimates of pair_flux2d
-template <int NRM>
-__device__ __forceinline__ void pair_flux2d_hll(const float2 *wL, const float2 *wR, int n, float gam, float gm1i, float2 *F) {
-    const int nn = NRM >= 0 ? NRM : n;
-    const float2 vnL = nn == 0 ? wL[1] : wL[2], vnR = nn == 0 ? wR[1] : wR[2];
-    const float2 rL = wL[0], rR = wR[0], pL = wL[3], pR = wR[3];
-    const float2 qL = PF::rsqrt(rL), qR = PF::rsqrt(rR);
-    const float2 sqL = PF::mul(rL, qL), sqR = PF::mul(rR, qR);
-    const float2 iL = PF::mul(qL, qL), iR = PF::mul(qR, qR);
-    const float2 inv = PF::rcp(PF::add(sqL, sqR));
-    const float2 g2 = PF::sp(gam);
-    const float2 c2L = PF::mul(PF::mul(g2, pL), iL), c2R = PF::mul(PF::mul(g2, pR), iR);
-    const float2 uroe = PF::mul(PF::fma(sqL, vnL, PF::mul(sqR, vnR)), inv);
-    const float2 du = PF::sub(vnR, vnL);
-    const float2 h = PF::mul(PF::mul(PF::mul(sqL, sqR), PF::mul(inv, inv)), PF::sp(0.5f));
-    const float2 d2 = PF::fma(PF::mul(h, du), du, PF::mul(PF::fma(sqL, c2L, PF::mul(sqR, c2R)), inv));
-    const float2 d = PF::mul(d2, PF::rsqrt(d2));
-    const float2 lo = PF::sub(uroe, d), hi = PF::add(uroe, d);
-    const float2 sL = make_float2(fminf(lo.x, 0.f), fminf(lo.y, 0.f));
-    const float2 sR = make_float2(fmaxf(hi.x, 0.f), fmaxf(hi.y, 0.f));
-    const float2 iw = PF::rcp(PF::sub(sR, sL)), sLR = PF::mul(sL, sR);
-    const float2 v2L = PF::fma(wL[2], wL[2], PF::mul(wL[1], wL[1]));
-    const float2 v2R = PF::fma(wR[2], wR[2], PF::mul(wR[1], wR[1]));
-    const float2 half = PF::sp(0.5f);
-    const float2 EL = PF::fma(pL, PF::sp(gm1i), PF::mul(PF::mul(half, rL), v2L));
-    const float2 ER = PF::fma(pR, PF::sp(gm1i), PF::mul(PF::mul(half, rR), v2R));
-    const float2 mL = PF::mul(rL, vnL), mR = PF::mul(rR, vnR);
-    auto comb = [&](float2 fL, float2 fR, float2 jump) {
-        return PF::mul(PF::fma(sLR, jump, PF::sub(PF::mul(sR, fL), PF::mul(sL, fR))), iw);
-    };
-    F[0] = comb(mL, mR, PF::sub(rR, rL));
-#pragma unroll
-    for (int d2i = 0; d2i < 2; ++d2i) {
-        float2 fL = PF::mul(mL, wL[1 + d2i]), fR = PF::mul(mR, wR[1 + d2i]);
-        if (d2i == nn) {
-            fL = PF::add(fL, pL);
-            fR = PF::add(fR, pR);
-        }
-        F[1 + d2i] = comb(fL, fR, PF::sub(PF::mul(rR, wR[1 + d2i]), PF::mul(rL, wL[1 + d2i])));
-    }
-    F[3] = comb(PF::mul(PF::add(EL, pL), vnL), PF::mul(PF::add(ER, pR), vnR), PF::sub(ER, EL));
-}
-
-// the pair flux of the configured scheme (FLX 0 Rusanov, 1 HLL)
+// the pair flux of the configured scheme (FLX 0 Rusanov, 1 HLL) for faces
+// with normal NRM (0 x, 1 y; or NRM < 0 and the runtime normal n) from
+// primitive states (rho, u, v, p): the grouped form of stage_pair.cuh
 template <int FLX, int NRM>
 __device__ __forceinline__ void pair_face_flux2d(const float2 *wL, const float2 *wR, int n, float gam, float gm1i, float2 *F) {
-    if constexpr (FLX == 1) pair_flux2d_hll<NRM>(wL, wR, n, gam, gm1i, F);
-    else pair_flux2d<NRM>(wL, wR, n, gam, gm1i, F);
+    pair_flux_grouped<2, FLX, NRM>(wL, wR, n, gam, gm1i, F);
 }
 
 // conservative (rho, rho u, rho v, E) -> primitive (rho, u, v, p) for a pair
