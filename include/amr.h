@@ -368,9 +368,9 @@ amr_status amr_set_launch_shape(amr_forest *f, int choice);
  * from pooled block data; the criterion stays as fallback for blocks the
  * network is unsure about and as the judge of its flags.  Network: F inputs
  * -> 64 -> 64 (GELU) -> 3 logits (derefine / keep / refine) -> softmax; the
- * forward pass uses BF16 copies of the FP32 master weights with FP32
- * accumulation.  Parameters are packed FP32 [W1 (F x 64), b1, W2 (64 x 64),
- * b2, W3 (64 x 3), b3]; labels are classes 0, 1, 2 = flags -1, 0, +1. */
+ * passes use BF16 copies of the FP32 master weights with FP32 accumulation.
+ * Parameters are packed FP32 [W1 (F x 64), b1, W2 (64 x 64), b2, W3 (64 x
+ * 3), b3]; labels are classes 0, 1, 2 = flags -1, 0, +1. */
 typedef struct amr_mlp amr_mlp;
 
 /* Features of every block of slot s into device memory x[f * n_blocks + b]
@@ -391,6 +391,13 @@ amr_status amr_mlp_n_params(const amr_mlp *m, int64_t *n);
  * setting them also refreshes the BF16 copy and resets the optimiser. */
 amr_status amr_mlp_get_params(const amr_mlp *m, float *host, int64_t n);
 amr_status amr_mlp_set_params(amr_mlp *m, const float *host, int64_t n);
+
+/* Arithmetic of the passes: bits = 16 (the default) runs the products on
+ * BF16 tensor cores (mma.sync m16n8k16, FP32 accumulation), with features,
+ * hidden activations and hidden-layer deltas rounded to BF16 (nearest even)
+ * where they enter a product; bits = 32 runs them on FP32 CUDA cores with
+ * FP32 activations (the weights are BF16 in both).  Errors: AMR_EINVAL. */
+amr_status amr_mlp_set_precision(amr_mlp *m, int bits);
 
 /* Softmax probabilities prob[s * 3 + c] of n samples x[f * n + s] (device). */
 amr_status amr_mlp_forward(amr_mlp *m, const float *x, int64_t n, float *prob, amr_stream stream);

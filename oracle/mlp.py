@@ -11,10 +11,15 @@ criterion of Sec. 3.3 (derefine / keep / refine):
             64 hidden units, GELU(z) = z (1 + erf(z / sqrt 2)) / 2;
   loss      mean cross-entropy against the criterion's flags.
 
-The GPU forward pass uses the weights rounded to BF16 (round to nearest
-even) and accumulates in FP32; `forward`/`gradients` here take the weights as
-given (round them with `to_bf16` to mirror the GPU), in FP64.  Parameters are
-packed as [W1 (F x H), b1, W2 (H x H), b2, W3 (H x 3), b3].
+The GPU passes use the weights rounded to BF16 (round to nearest even) and
+accumulate in FP32; `forward`/`gradients` here take the weights as given
+(round them with `to_bf16` to mirror the GPU), in FP64.  With bf16=True they
+also round every other operand of a matrix product to BF16, as the GPU's
+tensor-core path does: the features, the hidden activations h1 and h2, and in
+back-propagation the deltas d1, d2, d3 entering the weight-gradient products
+and d2 entering d1 = (d2 W2^T) GELU'(z1); biases, GELU, softmax, the output
+delta and the bias gradients (sums of the unrounded deltas) are not rounded.
+Parameters are packed as [W1 (F x H), b1, W2 (H x H), b2, W3 (H x 3), b3].
 """
 from __future__ import annotations
 
@@ -55,15 +60,22 @@ def gelu_prime(z):
     return 0.5 * (1.0 + erf(z / math.sqrt(2.0))) + z * np.exp(-0.5 * z * z) / math.sqrt(2.0 * math.pi)
 
 
-def forward(p, X):
+def _bf16_operand(a):
+    """An FP64 operand rounded to BF16 the way the GPU rounds it: to FP32
+    first (the GPU holds it in FP32), then to BF16."""
+    return to_bf16(np.asarray(a, dtype=np.float32)).astype(np.float64)
+
+
+def forward(p, X, bf16=False):
     """X [n, F] -> (probabilities [n, 3], cache)."""
     F = X.shape[1]
     W1, b1, W2, b2, W3, b3 = [a.astype(np.float64) for a in unpack(p, F)]
-    z1 = X @ W1 + b1
+    r = _bf16_operand if bf16 else (lambda a: a)
+    z1 = r(X) @ W1 + b1
     h1 = gelu(z1)
-    z2 = h1 @ W2 + b2
+    z2 = r(h1) @ W2 + b2
     h2 = gelu(z2)
-    z3 = h2 @ W3 + b3
+    z3 = r(h2) @ W3 + b3
     z3 = z3 - z3.max(axis=1, keepdims=True)
     e = np.exp(z3)
     prob = e / e.sum(axis=1, keepdims=True)
@@ -75,23 +87,24 @@ def loss(p, X, y):
     return -np.mean(np.log(prob[np.arange(len(y)), y]))
 
 
-def gradients(p, X, y):
+def gradients(p, X, y, bf16=False):
     """Mean cross-entropy and its gradient w.r.t. the packed parameters
     (back-propagation written out layer by layer)."""
     F = X.shape[1]
     W1, b1, W2, b2, W3, b3 = [a.astype(np.float64) for a in unpack(p, F)]
-    prob, (X, z1, h1, z2, h2, _) = forward(p, X)
+    prob, (X, z1, h1, z2, h2, _) = forward(p, X, bf16=bf16)
+    r = _bf16_operand if bf16 else (lambda a: a)
     n = len(y)
     d3 = prob.copy()
     d3[np.arange(n), y] -= 1.0
     d3 /= n
-    gW3 = h2.T @ d3
+    gW3 = r(h2).T @ r(d3)
     gb3 = d3.sum(axis=0)
     d2 = (d3 @ W3.T) * gelu_prime(z2)
-    gW2 = h1.T @ d2
+    gW2 = r(h1).T @ r(d2)
     gb2 = d2.sum(axis=0)
-    d1 = (d2 @ W2.T) * gelu_prime(z1)
-    gW1 = X.T @ d1
+    d1 = (r(d2) @ W2.T) * gelu_prime(z1)
+    gW1 = r(X).T @ r(d1)
     gb1 = d1.sum(axis=0)
     L = -np.mean(np.log(prob[np.arange(n), y]))
     return L, np.concatenate([gW1.ravel(), gb1, gW2.ravel(), gb2, gW3.ravel(), gb3])

@@ -35,7 +35,7 @@ EXPORTED = [
     "amr_launch_count", "amr_conserved_static", "amr_create_batch", "amr_n_instances", "amr_instance_blocks",
     "amr_get_dts", "amr_conserved_all", "amr_autotune", "amr_features", "amr_mlp_create", "amr_mlp_destroy",
     "amr_mlp_n_params", "amr_mlp_get_params", "amr_mlp_set_params", "amr_mlp_forward", "amr_mlp_gradient",
-    "amr_mlp_train", "amr_mlp_adamw_step", "amr_mlp_flags", "amr_get_config", "amr_save", "amr_load", "amr_write_xdmf", "amr_set_launch_shape",
+    "amr_mlp_train", "amr_mlp_adamw_step", "amr_mlp_set_precision", "amr_mlp_flags", "amr_get_config", "amr_save", "amr_load", "amr_write_xdmf", "amr_set_launch_shape",
     "amr_trace", "amr_trace_read",
 ]
 
@@ -140,6 +140,7 @@ def load(build_if_missing: bool = True):
         "amr_mlp_gradient": [vp, vp, vp, i64, vp, vp],
         "amr_mlp_train": [vp, vp, vp, i64, C.c_int, C.c_int, C.c_double, C.c_double, C.c_uint64, P(C.c_double), vp],
         "amr_mlp_adamw_step": [vp, vp, C.c_double, C.c_double, vp],
+        "amr_mlp_set_precision": [vp, C.c_int],
         "amr_mlp_flags": [vp, vp, C.c_int, P(FlagParams), C.c_double, vp, P(i64), vp],
     }
     for name, args in sig.items():
@@ -546,6 +547,10 @@ class Mlp:
                                               _stream_ptr(stream)), "amr_mlp_gradient")
         g = g.cpu().numpy()
         return float(g[-1]), g[:-1]
+
+    def set_precision(self, bits):
+        """16: BF16 tensor-core passes (default); 32: FP32 CUDA-core passes."""
+        self._check(self.lib.amr_mlp_set_precision(self.h, int(bits)), "amr_mlp_set_precision")
 
     def adamw_step(self, grad, lr, weight_decay=0.0, stream=None):
         """One AdamW step with a caller-supplied gradient (CUDA float32 tensor [P])."""

@@ -20,7 +20,7 @@ UNITS = ["amr_api.cu", "forest.cpp", "pattern.cpp", "noalloc.cu", "mlp.cu", "ins
          "inst_stage_pair_hll.cu", "inst_stage_pair2d_hll.cu",
          "inst_stage_f32_2d_gen.cu", "inst_stage_f32_3d_gen.cu", "inst_stage_f64_2d_gen.cu", "inst_stage_f64_3d_gen.cu",
          "inst_weno.cu", "inst_stage_adv.cu"]
-HEADERS = ["common.cuh", "ghost.cuh", "stage.cuh", "stage_pair.cuh", "misc.cuh", "mlp.cuh", "forest.hpp", "pattern.hpp",
+HEADERS = ["common.cuh", "ghost.cuh", "stage.cuh", "stage_pair.cuh", "misc.cuh", "mlp.cuh", "mlp_tc.cuh", "forest.hpp", "pattern.hpp",
            "api_internal.cuh", "launch_kernels.cuh", "stage_weno.cuh", "stage_pair2d.cuh", "stage_adv.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")

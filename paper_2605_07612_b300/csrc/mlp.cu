@@ -8,6 +8,7 @@
 
 #include "../../include/amr.h"
 #include "mlp.cuh"
+#include "mlp_tc.cuh"
 
 using namespace amrb;
 
@@ -54,7 +55,10 @@ amr_status gradient(amr_mlp *m, const float *x, int64_t n_total, const int32_t *
     const int64_t n1 = m->P + 1;
     const int rows = int(std::min<int64_t>(kGradRows, (nb + kMlpTile - 1) / kMlpTile));
     MCU(cudaMemsetAsync(m->partial, 0, sizeof(float) * size_t(n1) * size_t(rows), st));
-    k_mlp_grad<<<rows, 128, grad_smem(m->F), st>>>(m->wb, m->F, x, n_total, idx, y, nb, m->partial);
+    if (m->precision == 16)
+        k_mlp_grad_tc<<<rows, 128, TcGradSmem(m->F).end, st>>>(m->wb, m->F, x, n_total, idx, y, nb, m->partial);
+    else
+        k_mlp_grad<<<rows, 128, grad_smem(m->F), st>>>(m->wb, m->F, x, n_total, idx, y, nb, m->partial);
     k_mlp_reduce<<<int((n1 + 255) / 256), 256, 0, st>>>(m->partial, rows, n1, m->grad);
     MCU(cudaGetLastError());
     return AMR_OK;
@@ -78,6 +82,8 @@ amr_status amr_mlp_create(int n_features, uint64_t seed, amr_mlp **out) {
               cudaMalloc(&m->partial, (pb + sizeof(float)) * kGradRows) == cudaSuccess;
     ok = ok && cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, int(grad_smem(n_features))) == cudaSuccess;
     ok = ok && cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pb)) == cudaSuccess;
+    ok = ok && cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(TcSmem(n_features).end)) == cudaSuccess;
+    ok = ok && cudaFuncSetAttribute(k_mlp_grad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(TcGradSmem(n_features).end)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         amr_mlp_destroy(m);
@@ -142,11 +148,23 @@ amr_status amr_mlp_set_params(amr_mlp *m, const float *host, int64_t n) {
     return AMR_OK;
 }
 
+amr_status amr_mlp_set_precision(amr_mlp *m, int bits) {
+    if (!m || (bits != 16 && bits != 32)) return AMR_EINVAL;
+    m->precision = bits;
+    return AMR_OK;
+}
+
 amr_status amr_mlp_forward(amr_mlp *m, const float *x, int64_t n, float *prob, amr_stream stream) {
     if (!m || (n > 0 && (!x || !prob)) || n < 0) return AMR_EINVAL;
     if (n == 0) return AMR_OK;
-    const int grid = int(std::min<int64_t>((n + 127) / 128, 4 * 148));
-    k_mlp_forward<<<grid, 128, sizeof(float) * size_t(m->P), static_cast<cudaStream_t>(stream)>>>(m->wb, m->F, x, n, prob);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (m->precision == 16) {
+        const int grid = int(std::min<int64_t>((n + kTcTile - 1) / kTcTile, 2 * 148));
+        k_mlp_forward_tc<<<grid, 128, TcSmem(m->F).end, st>>>(m->wb, m->F, x, n, prob);
+    } else {
+        const int grid = int(std::min<int64_t>((n + 127) / 128, 4 * 148));
+        k_mlp_forward<<<grid, 128, sizeof(float) * size_t(m->P), st>>>(m->wb, m->F, x, n, prob);
+    }
     MCU(cudaGetLastError());
     return AMR_OK;
 }

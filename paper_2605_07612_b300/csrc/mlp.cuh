@@ -332,5 +332,6 @@ struct amr_mlp {
     int64_t idx_cap = 0;
     int partial_rows = 0;
     int64_t step = 0;
+    int precision = 16;   // 16: BF16 tensor-core kernels, 32: FP32 CUDA-core kernels
     std::string err;
 };

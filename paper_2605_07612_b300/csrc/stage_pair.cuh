@@ -36,19 +36,17 @@ struct PF {
     __device__ static __forceinline__ float2 rsqrt(float2 a) { return make_float2(rsqrt_ftz(a.x), rsqrt_ftz(a.y)); }
     __device__ static __forceinline__ float2 rcp(float2 a) { return make_float2(rcp_ftz(a.x), rcp_ftz(a.y)); }
     __device__ static __forceinline__ float2 abs(float2 a) { return make_float2(fabsf(a.x), fabsf(a.y)); }
-    // 0.5 minmod(a, b) = qs(a, b) * mabs(a, b): qs = (sign a + sign b) / 4 is
-    // +-1/2 when the signs agree and 0 otherwise; mabs = min(|a|, |b|) (a zero
-    // gives 0).  The product is exact, so w + 0.5 minmod(a, b) is the single
-    // rounding fma(qs, mabs, w).
+    // minmod(a, b) (Eq. 1 with theta = 1) as the median of a, b and 0:
+    // min(max(a, b), max(min(a, b), 0)) is the argument of smaller magnitude
+    // when a and b have the same strict sign and 0 otherwise, so
+    // w + 0.5 minmod(a, b) is the single rounding fma(0.5, mm(a, b), w).
+    __device__ static __forceinline__ float mm1(float a, float b) { return fminf(fmaxf(a, b), fmaxf(fminf(a, b), 0.f)); }
+    __device__ static __forceinline__ float2 mm(float2 a, float2 b) { return make_float2(mm1(a.x, b.x), mm1(a.y, b.y)); }
+    // qs = (sign a + sign b) / 4 from the sign bits: +-1/2 when the signs
+    // agree, 0 otherwise (the monotonized-central limiter builds on it)
     __device__ static __forceinline__ float sg(float a) { return __uint_as_float((__float_as_uint(a) & 0x80000000u) | 0x3e800000u); }
     __device__ static __forceinline__ float2 qs(float2 a, float2 b) {
         return add(make_float2(sg(a.x), sg(a.y)), make_float2(sg(b.x), sg(b.y)));
-    }
-    __device__ static __forceinline__ float2 mabs(float2 a, float2 b) {
-        return make_float2(fminf(fabsf(a.x), fabsf(b.x)), fminf(fabsf(a.y), fabsf(b.y)));
-    }
-    __device__ static __forceinline__ float2 nmabs(float2 a, float2 b) {
-        return make_float2(fmaxf(-fabsf(a.x), -fabsf(b.x)), fmaxf(-fabsf(a.y), -fabsf(b.y)));
     }
     __device__ static __forceinline__ bool positive(float2 a) { return a.x > 0.f && a.y > 0.f; }
 };
@@ -200,8 +198,8 @@ template <int LIM>
 __device__ __forceinline__ void pair_states(float2 w0, float2 w1, float2 w2, float2 w3, float2 &L, float2 &R) {
     const float2 d01 = PF::sub(w1, w0), d12 = PF::sub(w2, w1), d23 = PF::sub(w3, w2);
     if constexpr (LIM == 0) {
-        L = PF::fma(PF::qs(d01, d12), PF::mabs(d01, d12), w1);
-        R = PF::fma(PF::qs(d12, d23), PF::nmabs(d12, d23), w2);
+        L = PF::fma(PF::sp(0.5f), PF::mm(d01, d12), w1);
+        R = PF::fma(PF::sp(-0.5f), PF::mm(d12, d23), w2);
     } else {
         L = PF::add(w1, pair_half_slope<LIM>(d01, d12));
         R = PF::sub(w2, pair_half_slope<LIM>(d12, d23));
@@ -213,9 +211,9 @@ template <int LIM>
 __device__ __forceinline__ void pair_cell_states(float2 w0, float2 w1, float2 w2, float2 &minus, float2 &plus) {
     const float2 d01 = PF::sub(w1, w0), d12 = PF::sub(w2, w1);
     if constexpr (LIM == 0) {
-        const float2 q = PF::qs(d01, d12);
-        minus = PF::fma(q, PF::nmabs(d01, d12), w1);
-        plus = PF::fma(q, PF::mabs(d01, d12), w1);
+        const float2 m = PF::mm(d01, d12);
+        minus = PF::fma(PF::sp(-0.5f), m, w1);
+        plus = PF::fma(PF::sp(0.5f), m, w1);
     } else {
         const float2 h = pair_half_slope<LIM>(d01, d12);
         minus = PF::sub(w1, h);
@@ -535,10 +533,10 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
             for (int v = 0; v < V; ++v) {
                 const float2 w1 = Bw[v], w2 = ld2(p2, v, tj, ci), w3 = ld2(p3, v, tj, ci);
                 if constexpr (LIM == 0) {
-                    const float2 d12 = PF::sub(w2, w1), d23 = PF::sub(w3, w2), q = PF::qs(d12, d23);
-                    wR[v] = PF::fma(q, PF::nmabs(d12, d23), w2);
+                    const float2 d12 = PF::sub(w2, w1), d23 = PF::sub(w3, w2), m = PF::mm(d12, d23);
+                    wR[v] = PF::fma(PF::sp(-0.5f), m, w2);
                     wL[v] = zP[v];
-                    zP[v] = PF::fma(q, PF::mabs(d12, d23), w2);
+                    zP[v] = PF::fma(PF::sp(0.5f), m, w2);
                 } else {
                     wL[v] = zP[v];
                     pair_cell_states<LIM>(w1, w2, w3, wR[v], zP[v]);
@@ -669,7 +667,7 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
             pair_states<LIM>(w0, w1, w2, w3, wL[v], wR[v]);
             if constexpr (LIM == 0) {
                 const float2 d12 = PF::sub(w2, w1), d23 = PF::sub(w3, w2);
-                zP[v] = PF::fma(PF::qs(d12, d23), PF::mabs(d12, d23), w2);
+                zP[v] = PF::fma(PF::sp(0.5f), PF::mm(d12, d23), w2);
             } else {
                 float2 zm;
                 pair_cell_states<LIM>(w1, w2, w3, zm, zP[v]);
