@@ -348,9 +348,10 @@ def run_ours(args, rank, world, dist):
             fr.set_state(0, synth.rayleigh_taylor(sp_rt, lev_rt, g_rt).astype(fr.dtype))
             fr.compute_dt(0, stream=stream)
             nrt = max(2, args.steps // (2 if prec == 32 else 8))
-            msr, _ = time_steps(fr, nrt, 1, prec == 32, False)
+            # FP32: the single-pass kernel with gathered halos; FP64: two passes on filled ghosts
+            msr, _ = time_steps(fr, nrt, 1, prec == 32, prec == 32)
             rtw["%d^3 fp%d" % (bn, prec)] = {"value": 2.0 * cells * nrt * world / (msr * 1e-3), "ms_per_step": msr / nrt,
-                                              "status": fr.sync_status(), "phases": phase_breakdown(fr, stream, False)}
+                                              "status": fr.sync_status(), "phases": phase_breakdown(fr, stream, prec == 32)}
             del fr
             torch.cuda.empty_cache()
         rtw["context"] = "paper, 1x H100, FP64: 0.48 GCUPS for 16^3 blocks (Table 1)"
@@ -493,8 +494,9 @@ def run_advection(args, amr, torch, stream, barrier, world):
         lev, g = f.blocks()
         f.set_state(0, synth.advection_sphere(sp, lev, g).astype(f.dtype))
         f.compute_dt(0, stream=stream)
-        gather = limiter != 3
-        if gather:
+        # WENO5 gathers halos only in the single-pass FP32 3D kernel
+        gather = limiter != 3 or (prec == 32 and nd == 3)
+        if limiter != 3:
             f.autotune(stream=stream)
         steps = max(4, args.steps // 2)
         f.step(2, use_graph=True, gather=gather, stream=stream)
@@ -766,7 +768,10 @@ def run_ncu_case(which="stage"):
     periodic mesh of 16^3 blocks (24,576 same-level strips, 655 MB per state
     slot), FP32 -- exactly one ghost launch.  weno: one Heun step of the
     256^3 Rayleigh-Taylor case in 16^3 blocks with WENO5 (three ghost
-    layers), FP32 -- per stage one ghost fill and the three WENO5 passes.
+    layers), FP32, gathered halos -- per stage one ghost fill (the boundary
+    faces) and one single-pass WENO5 launch.  mlp: the learned predictor's
+    forward pass and one gradient over 20,000 random samples of 193
+    features (the tensor-core kernels).
     batched2d: the 64 batched 2D meshes refined as in
     the bench (three regrids, five ghost launches), then one Heun step with
     4 items per CTA -- two ghost rounds and one stage launch per stage."""
@@ -823,13 +828,23 @@ def run_ncu_case(which="stage"):
         if st != amr.AMR_OK:
             raise SystemExit("device status %d" % st)
         return
+    if which == "mlp":
+        rng = np.random.default_rng(0)
+        n = 20000
+        x = torch.tensor(rng.normal(0, 1, (193, n)).astype(np.float32), device="cuda")
+        y = torch.tensor(rng.integers(0, 3, n).astype(np.int8), device="cuda")
+        m = amr.Mlp(193, seed=1)
+        m.forward(x)
+        m.gradient(x, y)
+        torch.cuda.synchronize()
+        return
     if which == "weno":
         sp = synth.rayleigh_taylor_spec(ndim=3, N=16, limiter=3)
         f = amr.Forest(sp, 0, precision=32)
         lev, g = f.blocks()
         f.set_state(0, synth.rayleigh_taylor(sp, lev, g).astype(np.float32))
         f.compute_dt(0)
-        f.step(1, use_graph=False)
+        f.step(1, use_graph=False, gather=True)
         torch.cuda.synchronize()
         st = f.sync_status()
         if st != amr.AMR_OK:
@@ -948,7 +963,7 @@ def main():
     ap.add_argument("--workload", default="uniform", choices=["uniform", "amr_static", "adaptive"],
                     help="uniform: the headline line; the others print their own JSON line")
     ap.add_argument("--adaptive-steps", type=int, default=500)
-    ap.add_argument("--ncu-case", nargs="?", const="stage", default=None, choices=["stage", "ghost", "ghost3d", "weno", "stage2d", "advection", "batched2d"],
+    ap.add_argument("--ncu-case", nargs="?", const="stage", default=None, choices=["stage", "ghost", "ghost3d", "weno", "stage2d", "advection", "batched2d", "mlp"],
                     help="run one Heun step of the headline workload (stage), one ghost fill of a 3-level mesh "
                          "(ghost) or of the uniform 256^3 mesh (ghost3d), one WENO5 Heun step of the 256^3 Rayleigh-Taylor "
                          "case (weno), one Heun step of a uniform 4096^2 2D mesh (stage2d), of the 256^3 advection case "

@@ -245,7 +245,7 @@ amr_status launch_stage(amr_forest *f, const StageArgs<real> &a, cudaStream_t st
 // scratch of the WENO5 stage (face fluxes of every block); allocated
 // outside stream capture
 amr_status ensure_weno(amr_forest *f) {
-    if (f->cfg.limiter != AMR_LIM_WENO5) return AMR_OK;
+    if (f->cfg.limiter != AMR_LIM_WENO5 || weno_fused_applies(f)) return AMR_OK;   // the single pass keeps them on chip
     const int N = f->cfg.block_n, D = f->cfg.ndim;
     const size_t nfl = size_t(D) * size_t(f->cfg.n_var) * size_t(N + 1) * size_t(D == 3 ? N * N : N);
     const size_t nb = size_t(std::max<int64_t>(nblocks(f), 1));
@@ -280,8 +280,9 @@ amr_status run_stage(amr_forest *f, const amr_stage *stg, cudaStream_t st) {
     }
     amr_status s;
     if (f->cfg.limiter == AMR_LIM_WENO5) {
-        // two-pass WENO5 stage on the filled ghost cells (no halo gathering)
-        a.gather = 0;
+        // WENO5: the single-pass kernel (which may gather halos), or two
+        // passes on the filled ghost cells
+        if (!weno_fused_applies(f)) a.gather = 0;
         if ((s = ensure_weno(f)) != AMR_OK) return s;
         TraceSpan span(f, AMR_PHASE_STAGE, st);
         s = f->cfg.physics == AMR_PHYS_ADVECTION
@@ -456,7 +457,7 @@ struct TransferFn {
 int step_slots(int flags) { return (flags & AMR_STEP_RK4) ? 4 : ((flags & (AMR_STEP_SSP3 | AMR_STEP_SSP43)) ? 3 : 2); }
 
 amr_status rk_step(amr_forest *f, cudaStream_t st, bool gather, int flags) {
-    if (f->cfg.limiter == AMR_LIM_WENO5) gather = false;   // WENO5 reads filled ghost cells
+    if (f->cfg.limiter == AMR_LIM_WENO5 && !weno_fused_applies(f)) gather = false;   // the two-pass form reads filled ghosts
     const int gh = gather ? 1 : 0;
     std::vector<amr_stage> seq;
     if (flags & AMR_STEP_RK4) {

@@ -89,6 +89,13 @@ inline amr_status fail(amr_forest *f, amr_status s, const char *fmt, ...) {
     } while (0)
 
 inline int64_t nblocks(const amr_forest *f) { return f->offset.empty() ? 0 : f->offset.back(); }
+
+// WENO5 stages of FP32 3D blocks of 8^3 or 16^3 cells run as one kernel
+// (k_weno_fused), which can gather same-level halos; the others run the
+// two passes on filled ghost cells
+inline bool weno_fused_applies(const amr_forest *f) {
+    return f->cfg.precision == 32 && f->cfg.ndim == 3 && (f->cfg.block_n == 8 || f->cfg.block_n == 16);
+}
 inline int n_inst(const amr_forest *f) { return int(f->inst.size()); }
 
 // ---- per-phase timing (tracing): device phases by CUDA events, host phases

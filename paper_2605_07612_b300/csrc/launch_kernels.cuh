@@ -187,9 +187,38 @@ amr_status launch_adv_pair(amr_forest *f, const StageArgs<float> &a, cudaStream_
 
 // WENO5 stage: face fluxes, then the update (two launches); flux is a
 // scratch buffer of n_blocks x D x V x (N+1) N^(D-1) elements
+template <int N, int PH>
+cudaError_t launch_weno_fused(amr_forest *f, const StageArgs<float> &a, const PhysCtx<float> &pc, cudaStream_t st) {
+    using W = WenoFused<N, PH>;
+    static std::atomic<unsigned long long> attr_done{0};
+    cudaError_t e = smem_attr_once(k_weno_fused<N, PH>, W::smem_bytes(), attr_done);
+    if (e != cudaSuccess) return e;
+    int occ = 1;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_weno_fused<N, PH>, W::NT, W::smem_bytes());
+    if (e != cudaSuccess) return e;
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(a.n_items, int64_t(f->n_sms) * std::max(occ, 1)));
+    k_weno_fused<N, PH><<<unsigned(grid), W::NT, W::smem_bytes(), st>>>(a, f->geom, pc);
+    return cudaGetLastError();
+}
+
 template <class real, int D, int PH>
 amr_status launch_weno(amr_forest *f, const StageArgs<real> &a, real *flux, cudaStream_t st) {
     const int64_t nb = nblocks(f);
+    if constexpr (std::is_same<real, float>::value && D == 3) {
+        if (weno_fused_applies(f)) {
+            const PhysCtx<float> pc{a.gamma, 1.f / (a.gamma - 1.f), {a.vel[0], a.vel[1], a.vel[2]}};
+            StageArgs<float> b = a;
+            b.n_items = int(nb);
+            if (nb > 0) {
+                const cudaError_t e = f->cfg.block_n == 16 ? launch_weno_fused<16, PH>(f, b, pc, st)
+                                                           : launch_weno_fused<8, PH>(f, b, pc, st);
+                CU(e);
+                f->launches += 1;
+            }
+            CU(cudaGetLastError());
+            return AMR_OK;
+        }
+    }
     if (nb > 0) {
         const int N = f->cfg.block_n;
         const int npen = D * (D == 3 ? N * N : N);   // pencils of faces (one thread each)

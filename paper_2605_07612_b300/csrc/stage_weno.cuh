@@ -257,4 +257,179 @@ __global__ void __launch_bounds__(256) k_weno_update(StageArgs<real> a, const re
     }
 }
 
+
+// Single-pass WENO5 stage for 3D blocks of N^3 cells (N = 8 or 16): one CTA
+// of N^2 threads per block.  The CTA sweeps the block three times with one
+// thread per pencil, along x, then y, then z, with the pencil march of
+// k_weno_flux (each cell's five-cell stencil evaluated once for its two
+// faces); instead of going to global memory the face fluxes are differenced
+// at once into the divergence of the pencil's cells, accumulated in shared
+// memory across the three sweeps (barrier between sweeps).  The z sweep
+// finishes each cell: gravity source, combination with the previous states
+// (Eq. 5), output, CFL speed.  The stencil of a pencil end reaches three
+// cells into the neighbour: in gather mode they are read from a same-level
+// neighbour's interior, otherwise (and across refinement faces and domain
+// boundaries) from the block's filled ghost cells.  Block-boundary face
+// fluxes go to the refinement-face slots as in k_weno_flux.
+template <int N, int PH>
+struct WenoFused {
+    static constexpr int NT = N * N;
+    static constexpr int V = Phys<float, 3, PH>::V;
+    // divergence of cell (x, y, z) at x + P (y + N z): rows padded to P = N + 1
+    // words, so that the x sweep (consecutive threads on consecutive rows)
+    // hits distinct banks; the y and z sweeps run along rows
+    static constexpr int P = N + 1, NCP = P * N * N;
+    static constexpr size_t smem_bytes() { return sizeof(float) * size_t(V) * NCP; }
+};
+
+template <int N, int PH>
+__global__ void __launch_bounds__(N * N) k_weno_fused(StageArgs<float> a, Geom g, PhysCtx<float> pc) {
+    using E = Phys<float, 3, PH>;
+    constexpr int V = E::V, NC3 = WenoFused<N, PH>::NCP, PW = WenoFused<N, PH>::P;
+    extern __shared__ __align__(16) float wdu[];     // [V][N^2 rows of P] divergence of the block's cells
+    __shared__ double red[N * N / 32];
+    const int tid = threadIdx.x, ta = tid % N, tb = tid / N;
+    const int S = g.S, NG = g.ng;
+    const int64_t ncell = g.ncell;
+    bool bad = false;
+    for (int b = blockIdx.x; b < a.n_items; b += gridDim.x) {
+        const int gc = a.info[b].gclass, inst = a.info[b].inst, fixmask = a.info[b].fixmask;
+        const float dte = float(a.w_dt * a.sc_in[inst].dt);
+        const float *ub = a.deriv + int64_t(b) * g.bstride;
+        double vmax = 0.0;
+#pragma unroll 1
+        for (int n = 0; n < 3; ++n) {
+            // pencil along n at tangential (ta, tb) (the lower tangential dimension fastest)
+            const int x0 = n == 0 ? 0 : ta, x1 = n == 0 ? ta : (n == 1 ? 0 : tb), x2 = n == 2 ? 0 : tb;
+            const int64_t step = n == 0 ? 1 : (n == 1 ? int64_t(S) : int64_t(S) * S);
+            const int64_t o0 = (int64_t(x2 + NG) * S + (x1 + NG)) * S + (x0 + NG);
+            const int cstep = n == 0 ? 1 : (n == 1 ? PW : PW * N);
+            const int c0 = x0 + PW * (x1 + N * x2);
+            const float idx = float(g.inv_dx[3 * gc + n]);
+            const BlockInfo *ib = a.info + b;   // fields indexed by the direction: read from memory
+            const int nlo = a.gather ? ib->nbr[2 * n] : -1, nhi = a.gather ? ib->nbr[2 * n + 1] : -1;
+            const float *lob = nlo >= 0 ? a.deriv + int64_t(nlo) * g.bstride + o0 + int64_t(N) * step : ub + o0;
+            const float *hib = nhi >= 0 ? a.deriv + int64_t(nhi) * g.bstride + o0 - int64_t(N) * step : ub + o0;
+            // primitives of cell `along` of the pencil (-3 .. N + 2)
+            auto load = [&](int along, float *w) {
+                const float *src = along < 0 ? lob : (along >= N ? hib : ub + o0);
+                float U[V];
+#pragma unroll
+                for (int v = 0; v < V; ++v) U[v] = src[int64_t(v) * ncell + along * step];
+                E::prim(U, w, pc.gam);
+            };
+            const int slo = ib->bslot[2 * n], shi = ib->bslot[2 * n + 1];
+            const int tface = ta + N * tb;
+            float st[V][5], w[V], wL[V], wR[V], wnext[V], F[V], Fp[V];
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                load(m - 3, w);
+#pragma unroll
+                for (int v = 0; v < V; ++v) st[v][m + 1] = w[v];
+            }
+#pragma unroll 1
+            for (int fp = -1; fp <= N; ++fp) {
+                load(fp + 2, w);
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) st[v][m] = st[v][m + 1];
+                    st[v][4] = w[v];
+                    weno5_cell<float>(st[v][0], st[v][1], st[v][2], st[v][3], st[v][4], wR[v], wnext[v]);
+                }
+                if (fp >= 0) {
+                    bad = bad || E::nonphys(wL) || E::nonphys(wR);
+                    if (n == 0) E::template face_flux<0>(a.flux, wL, wR, 0, pc, F);
+                    else if (n == 1) E::template face_flux<1>(a.flux, wL, wR, 1, pc, F);
+                    else E::template face_flux<2>(a.flux, wL, wR, 2, pc, F);
+                    const int sl = fp == 0 ? slo : (fp == N ? shi : -1);
+                    if (sl >= 0) {
+                        float *dst = a.bflux + int64_t(sl) * V * (N * N) + tface;
+#pragma unroll
+                        for (int v = 0; v < V; ++v) dst[int64_t(v) * (N * N)] = F[v];
+                    }
+                    if (fp >= 1) {
+                        // cell fp - 1: its lower face flux Fp, upper face F
+                        const int c = c0 + (fp - 1) * cstep;
+                        float du[V];
+#pragma unroll
+                        for (int v = 0; v < V; ++v) {
+                            du[v] = (Fp[v] - F[v]) * idx;
+                            if (n > 0) du[v] += wdu[v * NC3 + c];
+                        }
+                        if (n < 2) {
+#pragma unroll
+                            for (int v = 0; v < V; ++v) wdu[v * NC3 + c] = du[v];
+                        } else {
+                            // the cell is complete: source, Eq. 5, output, CFL speed
+                            if constexpr (E::EULER) {
+                                if (a.gravity_on) {
+                                    // S = (0, rho g, (rho v) . g) of the cell's conservative state
+                                    const int64_t oc = int64_t(b) * g.bstride + o0 + int64_t(fp - 1) * step;
+                                    float sgv = 0.f;
+#pragma unroll
+                                    for (int d = 0; d < 3; ++d) {
+                                        du[1 + d] += a.deriv[oc] * a.grav[d];
+                                        sgv += a.deriv[oc + int64_t(1 + d) * ncell] * a.grav[d];
+                                    }
+                                    du[4] += sgv;
+                                }
+                            }
+                            const int64_t ob = int64_t(b) * g.bstride + o0 + int64_t(fp - 1) * step;
+                            float U[V];
+#pragma unroll
+                            for (int v = 0; v < V; ++v) {
+                                float acc = 0.f;
+#pragma unroll
+                                for (int q = 0; q < 4; ++q)
+                                    if (q < a.nprev) acc += a.wprev[q] * a.prev[q][ob + int64_t(v) * ncell];
+                                U[v] = dte * du[v] + acc;
+                                a.out[ob + int64_t(v) * ncell] = U[v];
+                            }
+                            if (a.update_dt) {
+                                const int m = fixmask, k = fp - 1;
+                                const bool fixed = ((m & 1) && x0 == 0) || ((m & 2) && x0 == N - 1) || ((m & 4) && x1 == 0) ||
+                                                   ((m & 8) && x1 == N - 1) || ((m & 16) && k == 0) || ((m & 32) && k == N - 1);
+                                if (!fixed) {
+                                    if constexpr (E::EULER) {
+                                        float wv[V];
+                                        E::prim(U, wv, a.gamma);
+                                        const float cs = sqrtf(a.gamma * wv[4] / wv[0]);
+                                        float sp = 0.f;
+#pragma unroll
+                                        for (int d = 0; d < 3; ++d) sp += (fabsf(wv[1 + d]) + cs) * float(g.inv_dx[3 * gc + d]);
+                                        vmax = fmax(vmax, double(sp));
+                                    } else {
+                                        float sp = 0.f;
+#pragma unroll
+                                        for (int d = 0; d < 3; ++d) sp += fabsf(a.vel[d]) * float(g.inv_dx[3 * gc + d]);
+                                        vmax = fmax(vmax, double(sp));
+                                    }
+                                }
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int v = 0; v < V; ++v) Fp[v] = F[v];
+                }
+#pragma unroll
+                for (int v = 0; v < V; ++v) wL[v] = wnext[v];
+            }
+            __syncthreads();   // the sweep's divergence is complete (and the next block may overwrite it after z)
+        }
+        if (a.update_dt) {
+            for (int o = 16; o > 0; o >>= 1) vmax = fmax(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+            if ((tid & 31) == 0) red[tid >> 5] = vmax;
+            __syncthreads();
+            if (tid == 0) {
+                double m = red[0];
+                for (int w2 = 1; w2 < N * N / 32; ++w2) m = fmax(m, red[w2]);
+                atomic_max_nonneg(&a.sc[inst].maxspeed_bits, m);
+            }
+            __syncthreads();
+        }
+    }
+    if (__syncthreads_or(bad) && tid == 0) raise_status(&a.sc[0].status, 7);
+}
+
 }  // namespace amrb
