@@ -461,8 +461,8 @@ def test_batch_fp32_graph_matches_oracle_100_steps():
     Kelvin-Helmholtz band is a seeded perturbation two orders of magnitude
     below the shear flow that the instability amplifies, together with
     every rounding difference in it; its component-wise relative error
-    reaches 1.1e-5 after 100 steps on the refined 5x5 instance, while that
-    of the momentum vector stays near 2e-7."""
+    reached 1.1e-5 after 100 steps on the refined 5x5 instance, while its
+    density and energy were at 2e-7 and 1e-7."""
     kh = [synth.MeshSpec(ndim=2, N=16, ng=2, ntrees=(n, n, 1), max_level=2) for n in (2, 5, 3)]
     sodx = synth.MeshSpec(ndim=2, N=16, ng=2, ntrees=(6, 1, 1), periodic=(0, 1, 1), max_level=2,
                           bc_type=(2, 2, 0, 0, 0, 0), length=(1.0, 1.0 / 6, 1.0))
