@@ -181,14 +181,21 @@ def test_kelvin_helmholtz_fp32_100_steps():
 
 
 def test_fp32_3d_amr_against_oracle():
+    """3-level 3D mesh of 8^3 blocks (refinement-face flux fixing, both
+    ghost rounds), FP32 pair kernel with gathered halos in a CUDA graph:
+    relative L1 <= 1e-5 per variable after 100 Heun steps."""
     sp = synth.MeshSpec(**SPEC_3D_AMR)
     om, f = make_pair(sp, 0, AMR3, precision=32)
     lev, g = om.blocks()
+    assert lev.max() == 2
     u = synth.fourier3d(sp, lev, g, seed=4)
-    got, _ = run_gpu_heun(f, u.astype(np.float32), 10, use_graph=True)
+    f.set_state(0, u.astype(np.float32))
+    f.compute_dt(0)
+    f.step(100, use_graph=True, gather=True)
+    assert f.sync_status() == amr.AMR_OK
     ref = u.copy()
-    oracle.run_heun(om, ref, 10)
-    assert rel_l1(got, ref, sp).max() <= 1e-5
+    oracle.run_heun(om, ref, 100)
+    assert rel_l1(f.get_state(0), ref, sp).max() <= 1e-5
 
 
 @pytest.mark.parametrize("precision", [32, 64])
@@ -462,7 +469,10 @@ def test_batch_fp32_graph_matches_oracle_100_steps():
     below the shear flow that the instability amplifies, together with
     every rounding difference in it; its component-wise relative error
     reached 1.1e-5 after 100 steps on the refined 5x5 instance, while its
-    density and energy were at 2e-7 and 1e-7."""
+    density and energy were at 2e-7 and 1e-7.  The autotuner may pick the
+    per-cell kernel here, whose textbook flux leaves FP32 rounding noise
+    (|rho v_y| < 1e-7) in a Sod tube's transverse momentum that the oracle
+    keeps at exactly 0."""
     kh = [synth.MeshSpec(ndim=2, N=16, ng=2, ntrees=(n, n, 1), max_level=2) for n in (2, 5, 3)]
     sodx = synth.MeshSpec(ndim=2, N=16, ng=2, ntrees=(6, 1, 1), periodic=(0, 1, 1), max_level=2,
                           bc_type=(2, 2, 0, 0, 0, 0), length=(1.0, 1.0 / 6, 1.0))
@@ -512,9 +522,22 @@ def test_batch_fp32_graph_matches_oracle_100_steps():
         oracle.run_heun(om, ref, 100)
         first, n = fb.instance_blocks(i)
         err = rel_l1(got[first:first + n], ref, sp)
-        assert err.max() <= 1e-4, (i, err)
         assert err[0] <= 1e-5 and err[-1] <= 1e-5, (i, err)
         assert momentum_rel_l1(got[first:first + n], ref, sp) <= 1e-5, (i, err)
+        # each momentum component on its own; a component that stays exactly
+        # zero in the oracle (the transverse momentum of a shock tube) is held
+        # to 1e-5 of the momentum's L1 norm instead of a relative error
+        nb = n
+        sl = (slice(None), slice(1, 1 + sp.ndim)) + tuple(slice(sp.ng, sp.ng + sp.N) for _ in range(sp.ndim))
+        A = got[first:first + n].reshape((nb, sp.nvar) + (sp.side,) * sp.ndim)[sl].astype(np.float64)
+        B = ref.reshape((nb, sp.nvar) + (sp.side,) * sp.ndim)[sl]
+        mscale = np.abs(B).sum()
+        for d in range(sp.ndim):
+            bd = np.abs(B[:, d]).sum()
+            if bd > 0:
+                assert err[1 + d] <= 1e-4, (i, d, err)
+            else:
+                assert np.abs(A[:, d]).sum() <= 1e-5 * mscale, (i, d, np.abs(A[:, d]).sum(), mscale)
 
 
 @pytest.mark.parametrize("case", ["3d_fp32", "3d_fp64", "2d_batch_fp32"])
