@@ -946,7 +946,9 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "uniform3d-256-b16-fp32", "sample": cpu["sample"]},
+        "config": {"workload": "uniform3d-256-b16-fp32", "sample": cpu["sample"],
+                   "bounded_sample": "the FP64 oracle times a 64^3 sample of the 256^3 workload (same blocks, field and "
+                                     "scheme, whole Heun steps), not the full mesh"},
         "cpu_baseline": cpu,
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
