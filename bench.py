@@ -382,7 +382,10 @@ def run_ours(args, rank, world, dist):
                      "avg_launch_ms": (t1 + t2) / 2.0,
                      # the same algorithmic bytes (two stages) over the graph-timed step
                      "achieved_step": 2.0 * per_launch_bytes / (ms / args.steps * 1e-3) / 1e9,
-                     "frac_step": 2.0 * per_launch_bytes / (ms / args.steps * 1e-3) / 1e9 / peak},
+                     "frac_step": 2.0 * per_launch_bytes / (ms / args.steps * 1e-3) / 1e9 / peak,
+                     # DRAM bytes actually moved (ncu) over the live launch time
+                     "dram_gbs": (traffic / ((t1 + t2) / 2.0 * 1e-3) / 1e9) if traffic else None,
+                     "frac_dram": (traffic / ((t1 + t2) / 2.0 * 1e-3) / 1e9 / peak) if traffic else None},
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
                 "steps": e2e_steps},
         "gpu_launches": launches,

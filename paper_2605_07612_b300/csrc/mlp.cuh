@@ -133,7 +133,7 @@ static __global__ void __launch_bounds__(128) k_mlp_grad(const __nv_bfloat16 *wb
             mlp_sample(sw, L, xs, kMlpTile, s, z1, z2, p);
             const bool valid = s0 + s < nb;
             float e3[kMlpO];
-            const int lab = valid ? int(y[idx[s0 + s]]) : 0;
+            const int lab = valid ? min(max(int(y[idx[s0 + s]]), 0), kMlpO - 1) : 0;   // classes 0..2
 #pragma unroll
             for (int o = 0; o < kMlpO; ++o) e3[o] = valid ? (p[o] - (o == lab ? 1.f : 0.f)) * inv_nb : 0.f;
             if (valid) my_loss -= logf(p[lab]) * inv_nb;

@@ -366,7 +366,9 @@ static __global__ void __launch_bounds__(128) k_mlp_grad_tc(const __nv_bfloat16 
         // output delta and loss of rows g, g + 8 (every lane of the quad)
         const int64_t sa = s0 + m0 + g, sb = sa + 8;
         const bool va = sa < nb, vb = sb < nb;
-        const int la = va ? int(y[idx[sa]]) : 0, lb = vb ? int(y[idx[sb]]) : 0;
+        // classes 0..2 (a label outside them is clamped rather than read past the row)
+        const int la = va ? min(max(int(y[idx[sa]]), 0), kMlpO - 1) : 0;
+        const int lb = vb ? min(max(int(y[idx[sb]]), 0), kMlpO - 1) : 0;
         float d3a[3], d3b[3];
 #pragma unroll
         for (int o = 0; o < 3; ++o) {
