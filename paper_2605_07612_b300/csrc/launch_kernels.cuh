@@ -91,22 +91,26 @@ amr_status launch_stage_t(amr_forest *f, const StageArgs<real> &a, cudaStream_t 
 // of Heun's method), for the slope limiter (minmod, MC, van Leer), the flux
 // (Rusanov, HLL) and the staging tile (16, or 8 when the autotuner picks it
 // for blocks above 8 cells a side)
-template <int D, int N, int TT, int NPREV, int LIM, int FLX>
+// (3D: FIX = the mesh has refinement faces; the 2D kernel has one form)
+template <int D, int N, int TT, int NPREV, int LIM, int FLX, bool FIX>
 struct PairKernel;
-template <int N, int TT, int NPREV, int LIM, int FLX>
-struct PairKernel<3, N, TT, NPREV, LIM, FLX> {
+template <int N, int TT, int NPREV, int LIM, int FLX, bool FIX>
+struct PairKernel<3, N, TT, NPREV, LIM, FLX, FIX> {
     using Sh = PairShape<N, TT>;
-    static constexpr auto fn = k_stage_pair<N, TT, NPREV, LIM, FLX>;
+    static constexpr auto fn = k_stage_pair<N, TT, NPREV, LIM, FLX, FIX>;
 };
-template <int N, int TT, int NPREV, int LIM, int FLX>
-struct PairKernel<2, N, TT, NPREV, LIM, FLX> {
+template <int N, int TT, int NPREV, int LIM, int FLX, bool FIX>
+struct PairKernel<2, N, TT, NPREV, LIM, FLX, FIX> {
     using Sh = PairShape2D<N, TT>;
     static constexpr auto fn = k_stage_pair2d<N, TT, NPREV, LIM, FLX>;
 };
 
-template <int D, int N, int TT, int NPREV, int LIM, int FLX>
-amr_status launch_stage_pair_n(amr_forest *f, const StageArgs<float> &a, cudaStream_t st) {
-    using K = PairKernel<D, N, TT, NPREV, LIM, FLX>;
+// the mesh has refinement faces: flux stores and flux fixing
+inline bool has_refinement_faces(const amr_forest *f) { return f->pat.n_slots > 0 || f->pat.fix_start.size() > 1; }
+
+template <int D, int N, int TT, int NPREV, int LIM, int FLX, bool FIX>
+amr_status launch_stage_pair_f(amr_forest *f, const StageArgs<float> &a, cudaStream_t st) {
+    using K = PairKernel<D, N, TT, NPREV, LIM, FLX, FIX>;
     using Sh = typename K::Sh;
     static std::atomic<unsigned long long> attr_done{0};
     const size_t smem = Sh::smem_bytes(NPREV);
@@ -123,6 +127,16 @@ amr_status launch_stage_pair_n(amr_forest *f, const StageArgs<float> &a, cudaStr
     }
     CU(cudaGetLastError());
     return AMR_OK;
+}
+
+template <int D, int N, int TT, int NPREV, int LIM, int FLX>
+amr_status launch_stage_pair_n(amr_forest *f, const StageArgs<float> &a, cudaStream_t st) {
+    if constexpr (D == 2) {
+        return launch_stage_pair_f<D, N, TT, NPREV, LIM, FLX, true>(f, a, st);
+    } else {
+        if (has_refinement_faces(f)) return launch_stage_pair_f<D, N, TT, NPREV, LIM, FLX, true>(f, a, st);
+        return launch_stage_pair_f<D, N, TT, NPREV, LIM, FLX, false>(f, a, st);
+    }
 }
 
 template <int D, int N, int TT, int LIM, int FLX>

@@ -42,6 +42,14 @@ struct PF {
     // w + 0.5 minmod(a, b) is the single rounding fma(0.5, mm(a, b), w).
     __device__ static __forceinline__ float mm1(float a, float b) { return fminf(fmaxf(a, b), fmaxf(fminf(a, b), 0.f)); }
     __device__ static __forceinline__ float2 mm(float2 a, float2 b) { return make_float2(mm1(a.x, b.x), mm1(a.y, b.y)); }
+    // minmod(a, b) and minmod(c, b) with the middle difference b shared:
+    // the median of (x, b, 0) is max(min(x, max(b, 0)), min(b, 0)), so the
+    // two limited slopes of a face take six min/max per lane instead of eight
+    __device__ static __forceinline__ void mm2(float2 a, float2 b, float2 c, float2 &mab, float2 &mcb) {
+        const float px = fmaxf(b.x, 0.f), py = fmaxf(b.y, 0.f), nx = fminf(b.x, 0.f), ny = fminf(b.y, 0.f);
+        mab = make_float2(fmaxf(fminf(a.x, px), nx), fmaxf(fminf(a.y, py), ny));
+        mcb = make_float2(fmaxf(fminf(c.x, px), nx), fmaxf(fminf(c.y, py), ny));
+    }
     // qs = (sign a + sign b) / 4 from the sign bits: +-1/2 when the signs
     // agree, 0 otherwise (the monotonized-central limiter builds on it)
     __device__ static __forceinline__ float sg(float a) { return __uint_as_float((__float_as_uint(a) & 0x80000000u) | 0x3e800000u); }
@@ -67,6 +75,7 @@ __device__ __forceinline__ void cp_async8(void *dst, const void *src) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 // Rusanov or HLL flux (Sec. 3.2) of a pair of faces with the same normal
 // (compile-time NRM >= 0, or the runtime normal n when NRM < 0) from the
@@ -198,8 +207,10 @@ template <int LIM>
 __device__ __forceinline__ void pair_states(float2 w0, float2 w1, float2 w2, float2 w3, float2 &L, float2 &R) {
     const float2 d01 = PF::sub(w1, w0), d12 = PF::sub(w2, w1), d23 = PF::sub(w3, w2);
     if constexpr (LIM == 0) {
-        L = PF::fma(PF::sp(0.5f), PF::mm(d01, d12), w1);
-        R = PF::fma(PF::sp(-0.5f), PF::mm(d12, d23), w2);
+        float2 m01, m23;
+        PF::mm2(d01, d12, d23, m01, m23);
+        L = PF::fma(PF::sp(0.5f), m01, w1);
+        R = PF::fma(PF::sp(-0.5f), m23, w2);
     } else {
         L = PF::add(w1, pair_half_slope<LIM>(d01, d12));
         R = PF::sub(w2, pair_half_slope<LIM>(d12, d23));
@@ -251,11 +262,15 @@ struct PairShape {
     }
     static constexpr int FYB = V * T * T;             // one y-face buffer
     static constexpr int EXB = V * T;                 // one buffer of the tile's upper x-faces
+    // planes whose previous states are staged ahead: one (the plane being
+    // updated), or two for two previous states (the next plane's copies are
+    // issued a plane period before they are needed)
+    static constexpr int stg_bufs(int nprev) { return nprev == 2 ? 2 : 1; }
     // ring, two y-face buffers, two upper-x-face buffers, and (nprev > 0)
-    // each thread's previous-state pairs of the plane being updated [nprev][V][NT]
+    // each thread's previous-state pairs [stg_bufs][nprev][V][NT]
     static constexpr size_t smem_bytes(int nprev) {
         return sizeof(float) * (size_t(R) * V * PL + 2 * size_t(FYB) + 2 * size_t(EXB)) +
-               sizeof(float2) * size_t(nprev > 0 ? nprev : 0) * V * NT;
+               sizeof(float2) * size_t(stg_bufs(nprev)) * size_t(nprev > 0 ? nprev : 0) * V * NT;
     }
 };
 
@@ -273,8 +288,10 @@ struct PairShape {
 // or for the last pair of a row from the upper x-faces computed one plane
 // ahead; the lower y-face of a row is the thread's own flux.  y- and x-face
 // buffers alternate with the parity of k, so the next plane's flux phase can
-// overwrite nothing the update still reads.
-template <int N, int TT, int NPREV, int LIM, int FLX>
+// overwrite nothing the update still reads.  FIX: the mesh has refinement
+// faces (flux stores for the flux fix, cells excluded from the CFL maximum);
+// without them that code is compiled out.
+template <int N, int TT, int NPREV, int LIM, int FLX, bool FIX>
 __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const Geom &g, int item) {
     using Sh = PairShape<N, TT>;
     constexpr int T = Sh::T, NG = Sh::NG, S = Sh::S, P = Sh::P, PL = Sh::PL, V = Sh::V, NT = Sh::NT;
@@ -317,9 +334,9 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
     const int nb2 = a.gather ? info.nbr[2] : -1, nb3 = a.gather ? info.nbr[3] : -1;
     const int nb4 = a.gather ? info.nbr[4] : -1, nb5 = a.gather ? info.nbr[5] : -1;
     // refinement-face flux slots this thread stores into (-1: none)
-    const int bs_x0 = (ci == 0 && tx0 == 0) ? info.bslot[0] : -1;
-    const int bs_y0 = (tj == 0 && ty0 == 0) ? info.bslot[2] : -1;
-    const int bs_z0 = info.bslot[4], bs_z1 = info.bslot[5];
+    const int bs_x0 = (FIX && ci == 0 && tx0 == 0) ? info.bslot[0] : -1;
+    const int bs_y0 = (FIX && tj == 0 && ty0 == 0) ? info.bslot[2] : -1;
+    const int bs_z0 = FIX ? info.bslot[4] : -1, bs_z1 = FIX ? info.bslot[5] : -1;
 
     bool nonphys = false;
     float vmax = 0.f;
@@ -447,8 +464,8 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
     // (2r, 2r+1) of plane kx, lanes T/2 + r the upper y-face of columns
     // (2r, 2r+1) of plane ky; one flux evaluation with a runtime normal.
     // Lane offsets in a ring plane: base + i st (+ po for the second face).
-    const int bs_x1 = (tx0 + T == N) ? info.bslot[1] : -1;
-    const int bs_y1 = (ty0 + T == N) ? info.bslot[3] : -1;
+    const int bs_x1 = (FIX && tx0 + T == N) ? info.bslot[1] : -1;
+    const int bs_y1 = (FIX && ty0 + T == N) ? info.bslot[3] : -1;
     auto edge_faces = [&](int kx, int ky, bool do_x) {
         const bool e_isx = tid < HP;
         const int e_r = e_isx ? tid : tid - HP;
@@ -582,27 +599,40 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
     };
 
     // ---- previous states of plane k: asynchronous copies of this thread's
-    // pairs into its staging slots, awaited by the update of plane k
+    // pairs into its staging slots (buffer k & 1 for two previous states),
+    // awaited by the update of plane k.  The slots are the thread's own, so
+    // a copy may be issued as soon as the thread has read the slots' last
+    // contents.
+    constexpr int SB = Sh::stg_bufs(NPREV);
+    auto stg_at = [&](int k, int q, int v) -> float2 * {
+        return stg + (((SB > 1 ? (k & 1) : 0) * (NPREV > 0 ? NPREV : 1) + q) * V + v) * NT + tid;
+    };
     auto stage_prev = [&](int k) {
         if constexpr (NPREV > 0) {
             const int64_t ob = int64_t(b) * V * NC + gofs(tx0 + ci, ty0 + tj, k);
 #pragma unroll
             for (int q = 0; q < NPREV; ++q)
 #pragma unroll
-                for (int v = 0; v < V; ++v) cp_async8(stg + (q * V + v) * NT + tid, a.prev[q] + ob + v * NC);
+                for (int v = 0; v < V; ++v) cp_async8(stg_at(k, q, v), a.prev[q] + ob + v * NC);
             cp_async_commit();
         }
     };
 
     // cells next to a coarse-side refinement face are reduced after flux
     // fixing (the parts of that test that do not depend on k)
-    const int fmask = info.fixmask;
+    const int fmask = FIX ? info.fixmask : 0;
     const int gi0 = tx0 + ci, gj0 = ty0 + tj;
     const bool rowfix_jk = ((fmask & 4) && gj0 == 0) || ((fmask & 8) && gj0 == N - 1);
     const bool colfix0 = (fmask & 1) && gi0 == 0, colfix1 = (fmask & 2) && gi0 + 1 == N - 1;
 
     auto update = [&](int k) {
-        if constexpr (NPREV > 0) cp_async_wait_all();
+        if constexpr (SB > 1) {
+            // the copies of plane k + 1 may stay in flight
+            if (k + 1 < N) cp_async_wait_one();
+            else cp_async_wait_all();
+        } else if constexpr (NPREV > 0) {
+            cp_async_wait_all();
+        }
         const float *fy = fyb + (k & 1) * FYB + Sh::fy(tj, ci);
         const int64_t ob = int64_t(b) * V * NC + gofs(tx0 + ci, ty0 + tj, k);
         const float2 dte = PF::sp(dt_eff);
@@ -614,7 +644,7 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
             float2 acc = PF::sp(0.f);
             if constexpr (NPREV > 0) {
 #pragma unroll
-                for (int q = 0; q < NPREV; ++q) acc = PF::fma(PF::sp(a.wprev[q]), stg[(q * V + v) * NT + tid], acc);
+                for (int q = 0; q < NPREV; ++q) acc = PF::fma(PF::sp(a.wprev[q]), *stg_at(k, q, v), acc);
             } else {
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
@@ -681,8 +711,13 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
     commit(2);          // into the slot of plane -2
     prefetch(3);
     __syncthreads();
+    if constexpr (SB > 1) stage_prev(0);
     for (int k = 0; k < N; ++k) {
-        stage_prev(k);
+        if constexpr (SB > 1) {
+            if (k + 1 < N) stage_prev(k + 1);
+        } else {
+            stage_prev(k);
+        }
         l2_ahead(k + 1);
         fluxes(k);
         if (tid < T) edge_faces(k + 1, k, k + 1 < N);
@@ -703,9 +738,12 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
     if (__syncthreads_or(nonphys) && tid == 0) raise_status(&a.sc[0].status, 7);
 }
 
-template <int N, int TT, int NPREV, int LIM, int FLX>
-__global__ void __launch_bounds__(PairShape<N, TT>::NT, (TT >= 16 ? 4 : 1)) k_stage_pair(StageArgs<float> a, Geom g) {
-    for (int item = blockIdx.x; item < a.n_items; item += gridDim.x) stage_pair_item<N, TT, NPREV, LIM, FLX>(a, g, item);
+// 16 x 16 tiles: four CTAs per SM (128 registers a thread), or three with
+// two previous states (160 registers: that stage waits on memory rather
+// than on the number of resident warps)
+template <int N, int TT, int NPREV, int LIM, int FLX, bool FIX>
+__global__ void __launch_bounds__(PairShape<N, TT>::NT, (TT >= 16 ? (NPREV == 2 ? 3 : 4) : 1)) k_stage_pair(StageArgs<float> a, Geom g) {
+    for (int item = blockIdx.x; item < a.n_items; item += gridDim.x) stage_pair_item<N, TT, NPREV, LIM, FLX, FIX>(a, g, item);
 }
 
 }  // namespace amrb
