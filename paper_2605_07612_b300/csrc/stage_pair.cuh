@@ -262,15 +262,18 @@ struct PairShape {
     }
     static constexpr int FYB = V * T * T;             // one y-face buffer
     static constexpr int EXB = V * T;                 // one buffer of the tile's upper x-faces
-    // planes whose previous states are staged ahead: one (the plane being
-    // updated), or two for two previous states (the next plane's copies are
-    // issued a plane period before they are needed)
-    static constexpr int stg_bufs(int nprev) { return nprev == 2 ? 2 : 1; }
-    // ring, two y-face buffers, two upper-x-face buffers, and (nprev > 0)
-    // each thread's previous-state pairs [stg_bufs][nprev][V][NT]
+    // y-face buffers: two, alternating with the parity of k, or one for two
+    // previous states (a second barrier per plane instead; the shared memory
+    // saved goes to the L1 cache)
+    static constexpr int fy_bufs(int nprev) { return nprev == 2 ? 1 : 2; }
+    // staging slots of a thread's previous-state pairs: one per state, and
+    // for two states a second slot for the first state, whose copies of the
+    // next plane are issued a plane period ahead
+    static constexpr int stg_slots(int nprev) { return nprev == 2 ? 3 : (nprev > 0 ? nprev : 0); }
+    // ring, y-face buffers, two upper-x-face buffers and the staging slots [stg_slots][V][NT]
     static constexpr size_t smem_bytes(int nprev) {
-        return sizeof(float) * (size_t(R) * V * PL + 2 * size_t(FYB) + 2 * size_t(EXB)) +
-               sizeof(float2) * size_t(stg_bufs(nprev)) * size_t(nprev > 0 ? nprev : 0) * V * NT;
+        return sizeof(float) * (size_t(R) * V * PL + size_t(fy_bufs(nprev)) * size_t(FYB) + 2 * size_t(EXB)) +
+               sizeof(float2) * size_t(stg_slots(nprev)) * V * NT;
     }
 };
 
@@ -300,7 +303,8 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float *ring = reinterpret_cast<float *>(smem_raw);         // [R][V][P*P]
     float *fyb = ring + Sh::R * V * PL;                         // [2][V][T x T] upper y-faces
-    float *exb = fyb + 2 * FYB;                                 // [2][V][T] upper x-faces
+    constexpr int FYN = Sh::fy_bufs(NPREV);
+    float *exb = fyb + FYN * FYB;                               // [2][V][T] upper x-faces
     float2 *stg = reinterpret_cast<float2 *>(exb + 2 * EXB);    // [NPREV][V][NT] previous states
 
     const int tid = threadIdx.x;
@@ -491,7 +495,7 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
                 store_bflux1(bs_x1, ty0 + 2 * e_r + 1 + N * kx, F[0].y, F[1].y, F[2].y, F[3].y, F[4].y);
             }
         } else {
-            float *fy = fyb + (ky & 1) * FYB;
+            float *fy = fyb + (FYN == 2 ? (ky & 1) : 0) * FYB;
 #pragma unroll
             for (int v = 0; v < V; ++v) *reinterpret_cast<float2 *>(fy + v * T * T + Sh::fy(T - 1, 2 * e_r)) = F[v];
             if (bs_y1 >= 0) store_bflux2(bs_y1, tx0 + 2 * e_r + N * ky, F);
@@ -534,7 +538,7 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
             pair_states<LIM>(ld2(pl, v, tj - 2, ci), ld2(pl, v, tj - 1, ci), Bw[v], ld2(pl, v, tj + 1, ci), wL[v], wR[v]);
         pair_face_flux<FLX, 1>(wL, wR, 1, gam, gm1i, F);
         if (tj > 0) {
-            float *fy = fyb + (k & 1) * FYB + Sh::fy(tj - 1, ci);
+            float *fy = fyb + (FYN == 2 ? (k & 1) : 0) * FYB + Sh::fy(tj - 1, ci);
 #pragma unroll
             for (int v = 0; v < V; ++v) *reinterpret_cast<float2 *>(fy + v * T * T) = F[v];
         }
@@ -599,13 +603,21 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
     };
 
     // ---- previous states of plane k: asynchronous copies of this thread's
-    // pairs into its staging slots (buffer k & 1 for two previous states),
-    // awaited by the update of plane k.  The slots are the thread's own, so
-    // a copy may be issued as soon as the thread has read the slots' last
-    // contents.
-    constexpr int SB = Sh::stg_bufs(NPREV);
+    // pairs into its staging slots, awaited by the update of plane k.  The
+    // slots are the thread's own, so a copy may be issued as soon as the
+    // thread has read the slot's last contents.  With two previous states
+    // the first one's copies of plane k + 1 go out a plane period ahead
+    // (slot k & 1), the second's at the start of period k (slot 2).
     auto stg_at = [&](int k, int q, int v) -> float2 * {
-        return stg + (((SB > 1 ? (k & 1) : 0) * (NPREV > 0 ? NPREV : 1) + q) * V + v) * NT + tid;
+        return stg + (((NPREV == 2) ? (q == 0 ? (k & 1) : 2) : q) * V + v) * NT + tid;
+    };
+    auto stage_prev_q = [&](int k, int q) {
+        if (k < N) {
+            const int64_t ob = int64_t(b) * V * NC + gofs(tx0 + ci, ty0 + tj, k);
+#pragma unroll
+            for (int v = 0; v < V; ++v) cp_async8(stg_at(k, q, v), a.prev[q] + ob + v * NC);
+        }
+        cp_async_commit();
     };
     auto stage_prev = [&](int k) {
         if constexpr (NPREV > 0) {
@@ -626,14 +638,12 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
     const bool colfix0 = (fmask & 1) && gi0 == 0, colfix1 = (fmask & 2) && gi0 + 1 == N - 1;
 
     auto update = [&](int k) {
-        if constexpr (SB > 1) {
-            // the copies of plane k + 1 may stay in flight
-            if (k + 1 < N) cp_async_wait_one();
-            else cp_async_wait_all();
+        if constexpr (NPREV == 2) {
+            cp_async_wait_one();      // the first state's copies of plane k + 1 may stay in flight
         } else if constexpr (NPREV > 0) {
             cp_async_wait_all();
         }
-        const float *fy = fyb + (k & 1) * FYB + Sh::fy(tj, ci);
+        const float *fy = fyb + (FYN == 2 ? (k & 1) : 0) * FYB + Sh::fy(tj, ci);
         const int64_t ob = int64_t(b) * V * NC + gofs(tx0 + ci, ty0 + tj, k);
         const float2 dte = PF::sp(dt_eff);
         float2 U[V];
@@ -711,10 +721,16 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
     commit(2);          // into the slot of plane -2
     prefetch(3);
     __syncthreads();
-    if constexpr (SB > 1) stage_prev(0);
+    // copy groups of a thread with two previous states, oldest first, at
+    // the update of plane k: [state 0, plane k][state 1, plane k][state 0,
+    // plane k + 1] (empty beyond the block), so waiting for all but the
+    // newest group leaves only the copies of plane k + 1 in flight
+    if constexpr (NPREV == 2) stage_prev_q(0, 0);
     for (int k = 0; k < N; ++k) {
-        if constexpr (SB > 1) {
-            if (k + 1 < N) stage_prev(k + 1);
+        if constexpr (NPREV == 2) {
+            if (k > 0) __syncthreads();     // every update of plane k - 1 has read the y-face buffer
+            stage_prev_q(k, 1);
+            stage_prev_q(k + 1, 0);
         } else {
             stage_prev(k);
         }
@@ -739,8 +755,8 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
 }
 
 // 16 x 16 tiles: four CTAs per SM (128 registers a thread), or three with
-// two previous states (160 registers: that stage waits on memory rather
-// than on the number of resident warps)
+// two previous states (about 160 registers: that stage gains more from
+// longer-lived registers and the L1 cache than from resident warps)
 template <int N, int TT, int NPREV, int LIM, int FLX, bool FIX>
 __global__ void __launch_bounds__(PairShape<N, TT>::NT, (TT >= 16 ? (NPREV == 2 ? 3 : 4) : 1)) k_stage_pair(StageArgs<float> a, Geom g) {
     for (int item = blockIdx.x; item < a.n_items; item += gridDim.x) stage_pair_item<N, TT, NPREV, LIM, FLX, FIX>(a, g, item);
