@@ -348,9 +348,11 @@ __device__ __forceinline__ void stage_pair2d_item(const StageArgs<float> &a, con
 }
 
 // CTAs take items with a grid stride; the copies of a CTA's next item are
-// issued before it works on the current one.
+// issued before it works on the current one.  16 x 16 tiles: six CTAs per SM
+// for one previous state (80 registers), five for two (their staging takes
+// more shared memory).
 template <int N, int TT, int NPREV, int LIM, int FLX>
-__global__ void __launch_bounds__(PairShape2D<N, TT>::NT, (TT >= 16 ? 5 : 2)) k_stage_pair2d(StageArgs<float> a, Geom g) {
+__global__ void __launch_bounds__(PairShape2D<N, TT>::NT, (TT >= 16 ? (NPREV == 1 ? 6 : 5) : 2)) k_stage_pair2d(StageArgs<float> a, Geom g) {
     int item = blockIdx.x;
     if (item >= a.n_items) return;
     pair2d_issue<N, TT, NPREV>(a, item, 0);

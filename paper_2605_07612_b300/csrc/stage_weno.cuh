@@ -310,26 +310,34 @@ __global__ void __launch_bounds__(N * N) k_weno_fused(StageArgs<float> a, Geom g
             const int nlo = a.gather ? ib->nbr[2 * n] : -1, nhi = a.gather ? ib->nbr[2 * n + 1] : -1;
             const float *lob = nlo >= 0 ? a.deriv + int64_t(nlo) * g.bstride + o0 + int64_t(N) * step : ub + o0;
             const float *hib = nhi >= 0 ? a.deriv + int64_t(nhi) * g.bstride + o0 - int64_t(N) * step : ub + o0;
-            // primitives of cell `along` of the pencil (-3 .. N + 2)
-            auto load = [&](int along, float *w) {
+            // conservative state of cell `along` of the pencil (-3 .. N + 2)
+            auto fetch = [&](int along, float *U) {
                 const float *src = along < 0 ? lob : (along >= N ? hib : ub + o0);
-                float U[V];
 #pragma unroll
                 for (int v = 0; v < V; ++v) U[v] = src[int64_t(v) * ncell + along * step];
+            };
+            auto load = [&](int along, float *w) {
+                float U[V];
+                fetch(along, U);
                 E::prim(U, w, pc.gam);
             };
             const int slo = ib->bslot[2 * n], shi = ib->bslot[2 * n + 1];
             const int tface = ta + N * tb;
-            float st[V][5], w[V], wL[V], wR[V], wnext[V], F[V], Fp[V];
+            float st[V][5], w[V], wL[V], wR[V], wnext[V], F[V], Fp[V], Un[V];
 #pragma unroll
             for (int m = 0; m < 4; ++m) {
                 load(m - 3, w);
 #pragma unroll
                 for (int v = 0; v < V; ++v) st[v][m + 1] = w[v];
             }
+            fetch(1, Un);
 #pragma unroll 1
             for (int fp = -1; fp <= N; ++fp) {
-                load(fp + 2, w);
+                // the cell entering the stencil was fetched one position
+                // ahead; fetch the next one (its loads stay in flight
+                // through this position's arithmetic)
+                E::prim(Un, w, pc.gam);
+                if (fp + 3 <= N + 2) fetch(fp + 3, Un);
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
 #pragma unroll
