@@ -16,6 +16,7 @@
 #include <type_traits>
 
 #include "stage.cuh"
+#include "stage_pair.cuh"
 
 namespace amrb {
 
@@ -63,6 +64,33 @@ __device__ __forceinline__ void weno5_cell(real a, real b, real c, real d, real 
         const real m0 = real(0.1) * s2, m1 = real(0.6) * s1, m2 = real(0.3) * s0;
         left = (m0 * p0 + m1 * p1 + m2 * p2) * rcp_ftz(m0 + m1 + m2);
     }
+}
+
+// weno5_cell for two FP32 stencils at once (two variables of one cell) in
+// packed two-wide arithmetic: the same formulas, each product and sum an
+// explicit rounded operation
+__device__ __forceinline__ void weno5_cell2(float2 a, float2 b, float2 c, float2 d, float2 e, float2 &left, float2 &right) {
+    const float2 r6 = PF::sp(1.f / 6.f);
+    const float2 two = PF::sp(2.f), five = PF::sp(5.f);
+    const float2 q0 = PF::mul(PF::fma(two, a, PF::fma(PF::sp(-7.f), b, PF::mul(PF::sp(11.f), c))), r6);
+    const float2 q1 = PF::mul(PF::fma(five, c, PF::fma(two, d, PF::mul(PF::sp(-1.f), b))), r6);
+    const float2 q2 = PF::mul(PF::fma(two, c, PF::fma(five, d, PF::mul(PF::sp(-1.f), e))), r6);
+    const float2 p0 = PF::mul(PF::fma(two, e, PF::fma(PF::sp(-7.f), d, PF::mul(PF::sp(11.f), c))), r6);   // mirror images
+    const float2 p1 = PF::mul(PF::fma(five, c, PF::fma(two, b, PF::mul(PF::sp(-1.f), d))), r6);
+    const float2 p2 = PF::mul(PF::fma(two, c, PF::fma(five, b, PF::mul(PF::sp(-1.f), a))), r6);
+    const float2 t0 = PF::add(PF::fma(PF::sp(-2.f), b, a), c), u0 = PF::fma(PF::sp(3.f), c, PF::fma(PF::sp(-4.f), b, a));
+    const float2 t1 = PF::add(PF::fma(PF::sp(-2.f), c, b), d), u1 = PF::sub(b, d);
+    const float2 t2 = PF::add(PF::fma(PF::sp(-2.f), d, c), e), u2 = PF::add(PF::fma(PF::sp(-4.f), d, PF::mul(PF::sp(3.f), c)), e);
+    const float2 k = PF::sp(13.f / 12.f), q4 = PF::sp(0.25f), eps = PF::sp(1e-6f);
+    const float2 e0 = PF::add(eps, PF::fma(k, PF::mul(t0, t0), PF::mul(q4, PF::mul(u0, u0))));
+    const float2 e1 = PF::add(eps, PF::fma(k, PF::mul(t1, t1), PF::mul(q4, PF::mul(u1, u1))));
+    const float2 e2 = PF::add(eps, PF::fma(k, PF::mul(t2, t2), PF::mul(q4, PF::mul(u2, u2))));
+    // 1 / (eps + beta_k)^2 by approximate reciprocals, as in weno5_cell
+    const float2 s0 = PF::rcp(PF::mul(e0, e0)), s1 = PF::rcp(PF::mul(e1, e1)), s2 = PF::rcp(PF::mul(e2, e2));
+    const float2 a0 = PF::mul(PF::sp(0.1f), s0), a1 = PF::mul(PF::sp(0.6f), s1), a2 = PF::mul(PF::sp(0.3f), s2);
+    right = PF::mul(PF::fma(a2, q2, PF::fma(a1, q1, PF::mul(a0, q0))), PF::rcp(PF::add(PF::add(a0, a1), a2)));
+    const float2 m0 = PF::mul(PF::sp(0.1f), s2), m2 = PF::mul(PF::sp(0.3f), s0);
+    left = PF::mul(PF::fma(m2, p2, PF::fma(a1, p1, PF::mul(m0, p0))), PF::rcp(PF::add(PF::add(m0, a1), m2)));
 }
 
 // Faces of a block: D (N+1) N^(D-1), N+1 positions fp per direction n
@@ -343,7 +371,24 @@ __global__ void __launch_bounds__(N * N) k_weno_fused(StageArgs<float> a, Geom g
 #pragma unroll
                     for (int m = 0; m < 4; ++m) st[v][m] = st[v][m + 1];
                     st[v][4] = w[v];
-                    weno5_cell<float>(st[v][0], st[v][1], st[v][2], st[v][3], st[v][4], wR[v], wnext[v]);
+                }
+                if constexpr (V == 5) {
+                    // variables (0, 1) and (2, 3) as packed pairs, 4 alone
+#pragma unroll
+                    for (int v = 0; v < 4; v += 2) {
+                        float2 l2, r2;
+                        weno5_cell2(make_float2(st[v][0], st[v + 1][0]), make_float2(st[v][1], st[v + 1][1]),
+                                    make_float2(st[v][2], st[v + 1][2]), make_float2(st[v][3], st[v + 1][3]),
+                                    make_float2(st[v][4], st[v + 1][4]), l2, r2);
+                        wR[v] = l2.x;
+                        wR[v + 1] = l2.y;
+                        wnext[v] = r2.x;
+                        wnext[v + 1] = r2.y;
+                    }
+                    weno5_cell<float>(st[4][0], st[4][1], st[4][2], st[4][3], st[4][4], wR[4], wnext[4]);
+                } else {
+#pragma unroll
+                    for (int v = 0; v < V; ++v) weno5_cell<float>(st[v][0], st[v][1], st[v][2], st[v][3], st[v][4], wR[v], wnext[v]);
                 }
                 if (fp >= 0) {
                     bad = bad || E::nonphys(wL) || E::nonphys(wR);
