@@ -69,7 +69,7 @@ typedef struct {
 } orc_params;
 
 enum { BC_NONE = 0, BC_DIRICHLET = 1, BC_NEUMANN = 2, BC_DATA = 3 };
-enum { K_SRL = 0, K_F2C = 1, K_BC = 2, K_C2F = 3, K_DIAG = 4, K_DIAG_F2C = 5, K_DIAG_C2F = 6 };
+enum { K_SRL = 0, K_F2C = 1, K_BC = 2, K_C2F = 3, K_DIAG = 4, K_DIAG_F2C = 5, K_DIAG_C2F = 6, K_DIAG_BC = 7 };
 
 /* a diagonal (edge or corner) direction (dx, dy, dz), two or three of them
  * nonzero, as the code (dx+1) + 3 (dy+1) + 9 (dz+1) */
@@ -443,6 +443,20 @@ static int global_cell(const orc_mesh *m, int b, const int x[3], int64_t C[3])
     return 1;
 }
 
+/* The lowest dimension in which block-local cell x lies outside block b
+ * across a non-periodic domain boundary, or -1 if there is none. */
+static int outside_dim(const orc_mesh *m, int b, const int x[3])
+{
+    const orc_params *p = &m->p;
+    for (int d = 0; d < p->ndim; d++) {
+        if (x[d] >= 0 && x[d] < p->N) continue;
+        int64_t E = blocks_at(p, d, m->lev[b]);
+        int64_t q = m->g[3 * b + d] + (x[d] < 0 ? -1 : 1);
+        if (!p->periodic[d] && (q < 0 || q >= E)) return d;
+    }
+    return -1;
+}
+
 /* the tangential dimensions of face direction f, lower dimension first */
 static void tangential(int ndim, int nd, int t[2])
 {
@@ -542,8 +556,9 @@ int64_t orc_pattern(const orc_mesh *m, int32_t *out, int64_t cap)
          * leaf (copy), a coarser leaf (prolongation, offset = parity of the
          * same-size box's coordinates, bit d for dimension d) or finer leaves
          * (restriction, one entry per fine leaf, offset = its position along
-         * a 3D edge); regions reaching outside a non-periodic domain stay
-         * unfilled */
+         * a 3D edge); a region reaching outside a non-periodic domain takes
+         * the boundary formula of the face across its lowest such dimension
+         * (offset = that face, aux = its boundary-face index) */
         if (p->diagonal) {
             for (int dz = (D == 3 ? -1 : 0); dz <= (D == 3 ? 1 : 0); dz++)
                 for (int dy = -1; dy <= 1; dy++)
@@ -557,6 +572,13 @@ int64_t orc_pattern(const orc_mesh *m, int32_t *out, int64_t cap)
                             lo[d] = dir[d] < 0 ? -ng : (dir[d] > 0 ? N : 0);
                             ext[d] = d >= D ? 1 : (dir[d] != 0 ? ng : N);
                             if (d >= D) lo[d] = 0;
+                        }
+                        int dout = outside_dim(m, b, lo);
+                        if (dout >= 0) {
+                            if (ne + 1 > maxe) { free(E); return -1; }
+                            entry_t e = {K_DIAG_BC, diag_code(dir), b, -1, 2 * dout + (dir[dout] > 0), -1};
+                            E[ne++] = e;
+                            continue;
                         }
                         for (int k = 0; k < ext[2] && ok; k++)
                             for (int j = 0; j < ext[1] && ok; j++)
@@ -605,6 +627,12 @@ int64_t orc_pattern(const orc_mesh *m, int32_t *out, int64_t cap)
     qsort(E, (size_t)ne, sizeof(entry_t), cmp_entry);
     int32_t ibf = 0;
     for (int64_t i = 0; i < ne; i++) if (E[i].kind == K_BC) E[i].aux = ibf++;
+    /* a boundary-formula edge or corner entry refers to its face's index */
+    for (int64_t i = 0; i < ne; i++) {
+        if (E[i].kind != K_DIAG_BC) continue;
+        for (int64_t j = 0; j < ne; j++)
+            if (E[j].kind == K_BC && E[j].dst == E[i].dst && E[j].face == E[i].offset) { E[i].aux = E[j].aux; break; }
+    }
     int64_t w = ne < cap ? ne : cap;
     for (int64_t i = 0; i < w; i++) {
         out[6 * i + 0] = E[i].kind; out[6 * i + 1] = E[i].face; out[6 * i + 2] = E[i].dst;
@@ -758,7 +786,8 @@ static int fill_round(const orc_mesh *m, double *u, const double *bc_data, int r
  * at a time from the leaf that holds the cell's centre: round 1 copies from a
  * same-level leaf and restricts from a finer one, round 2 prolongs from a
  * coarser one (the limited prolongation reads the coarse leaf's interior and
- * round-1 face ghosts).  Cells outside a non-periodic domain stay unfilled. */
+ * round-1 face ghosts).  Cells outside a non-periodic domain are left to
+ * fill_outside, which runs after both rounds. */
 static void fill_diagonal(const orc_mesh *m, double *u, int round)
 {
     const orc_params *p = &m->p;
@@ -799,12 +828,69 @@ static void fill_diagonal(const orc_mesh *m, double *u, int round)
     }
 }
 
+/* Edge and corner ghost cells outside a non-periodic domain (only when the
+ * mesh asks for edge and corner cells): each takes the boundary formula of
+ * the face across its lowest dimension that leaves the domain, applied to
+ * the cell mirrored across that face -- one dimension further in, so a face
+ * ghost for an edge cell and an edge cell for a corner; edges are filled
+ * before corners.  For per-cell boundary data the tangential position is
+ * clamped to the face. */
+static int fill_outside(const orc_mesh *m, double *u, const double *bc_data)
+{
+    const orc_params *p = &m->p;
+    int N = p->N, ng = p->ng, D = p->ndim, V = p->nvar;
+    int err = 0;
+    for (int pass = 2; pass <= D; pass++) {
+#pragma omp parallel for schedule(dynamic, 4) reduction(|| : err)
+        for (int b = 0; b < m->n; b++) {
+            int lev = m->lev[b];
+            int kr0 = (D == 3) ? -ng : 0, kr1 = (D == 3) ? N + ng : 1;
+            for (int k = kr0; k < kr1; k++)
+                for (int j = -ng; j < N + ng; j++)
+                    for (int i = -ng; i < N + ng; i++) {
+                        int x[3] = {i, j, D == 3 ? k : 0};
+                        int nout = 0;
+                        for (int d = 0; d < D; d++) if (x[d] < 0 || x[d] >= N) nout++;
+                        if (nout != pass) continue;
+                        int d = outside_dim(m, b, x);
+                        if (d < 0) continue;
+                        int side = x[d] >= N ? 1 : 0, f = 2 * d + side;
+                        int kk = side ? x[d] - N + 1 : -x[d];
+                        int xm[3] = {x[0], x[1], x[2]};
+                        xm[d] = side ? N - kk : kk - 1;
+                        int ty = p->bc_type[f];
+                        double dxn = dx_at(p, d, lev);
+                        int td[2];
+                        tangential(D, d, td);
+                        int t0 = x[td[0]] < 0 ? 0 : (x[td[0]] >= N ? N - 1 : x[td[0]]);
+                        int t1 = 0;
+                        if (D == 3) t1 = x[td[1]] < 0 ? 0 : (x[td[1]] >= N ? N - 1 : x[td[1]]);
+                        int64_t tt = t0 + (int64_t)N * t1;
+                        int64_t nface = (D == 3) ? (int64_t)N * N : N;
+                        int ibf = ty == BC_DATA ? boundary_face_index(m, b, f) : -1;
+                        for (int v = 0; v < V; v++) {
+                            double um = u[atv(p, b, v, xm)], g;
+                            if (ty == BC_DIRICHLET) g = 2.0 * p->bc_val[f][v] - um;
+                            else if (ty == BC_NEUMANN) g = um + ((double)(2 * kk - 1) * dxn) * p->bc_val[f][v];
+                            else if (ty == BC_DATA) g = 2.0 * bc_data[((int64_t)ibf * V + v) * nface + tt] - um;
+                            else { err = 1; g = 0.0; }
+                            u[atv(p, b, v, x)] = g;
+                        }
+                    }
+        }
+    }
+    return err ? -1 : 0;
+}
+
 int orc_fill_ghosts(const orc_mesh *m, double *u, const double *bc_data)
 {
     if (fill_round(m, u, bc_data, 1)) return -1;
     if (m->p.diagonal) fill_diagonal(m, u, 1);
     if (fill_round(m, u, bc_data, 2)) return -1;
-    if (m->p.diagonal) fill_diagonal(m, u, 2);
+    if (m->p.diagonal) {
+        fill_diagonal(m, u, 2);
+        if (fill_outside(m, u, bc_data)) return -1;
+    }
     return 0;
 }
 

@@ -407,3 +407,51 @@ def test_diagonal_ghosts_exact_for_linear_field_across_levels(ndim):
     err = diff[np.broadcast_to(sel[:, None], diff.shape)].max() / np.abs(Ex).max()
     assert err < 4.5e-16 * 8, err
     assert sel.sum() > 0
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_outside_edge_and_corner_ghosts_exact_for_linear_field(ndim):
+    """Edge and corner ghost cells outside a non-periodic domain (a reading
+    added here; the paper fills face ghosts only) take the boundary formula
+    of the face across their lowest dimension that leaves the domain,
+    applied to the cell mirrored across that face: a face ghost for an edge
+    cell, an edge cell for a corner.  With Neumann values equal to the
+    outward derivative of the linear field of Sec. 4.3, reflection is exact,
+    so every ghost cell of every block -- face, edge and corner, inside or
+    outside the domain -- holds the field, on a 4-level mesh refined toward
+    a corner of the domain.  A mirror cell off by one layer, the wrong face's
+    value or corners filled before edges break it."""
+    coef = (1.0, 2.0, 3.0)
+    bcv = tuple(tuple(((v + 1.0) * coef[f // 2] * (1.0 if f % 2 else -1.0)) if f // 2 < ndim else 0.0
+                      for v in range(8)) for f in range(6))
+    sp = synth.MeshSpec(ndim=ndim, N=8, ng=2, ntrees=(2, 2, 2)[:ndim] + (1,) * (3 - ndim), periodic=(0, 0, 0),
+                        max_level=3, bc_type=(2,) * 6, bc_val=bcv, diagonal_ghosts=1)
+    m = oracle.Mesh(sp, 0)
+    for _ in range(3):
+        lev, g = m.blocks()
+        m = m.adapt(synth.point_flags(sp, lev, g, (0.02, 0.97, 0.03)[:ndim] + (0.0,) * (3 - ndim), 3))
+    lev, g = m.blocks()
+    assert int(lev.max()) == 3
+    pat = m.pattern()
+    diag_bc = pat[pat[:, 0] == 7]
+    assert len(diag_bc) > 0
+    # a boundary entry's offset names a face of its block that is a domain boundary
+    bc_faces = {(int(e[2]), int(e[1])) for e in pat if e[0] == oracle.KIND_BC}
+    assert all((int(e[2]), int(e[4])) in bc_faces for e in diag_bc)
+    exact = synth.linear_field(sp, lev, g, with_ghosts=True)
+    # every ghost cell starts far from the field, so one left unfilled fails
+    S = sp.side
+    idx = np.indices((S,) * ndim) - sp.ng
+    nout = sum(((idx[d] < 0) | (idx[d] >= sp.N)).astype(int) for d in range(ndim))
+    u = exact.copy().reshape((m.n, sp.nvar) + (S,) * ndim)
+    u[:, :, nout > 0] = 1e6
+    u = u.reshape(exact.shape)
+    m.fill_ghosts(u)
+    err = np.abs(u - exact).max() / np.abs(exact).max()
+    assert err < 4.5e-16 * 16, err
+    # the check covers edge and corner cells outside the domain
+    X = synth.cell_centres(sp, lev, g)
+    outside = np.zeros_like(X[0], dtype=bool)
+    for d in range(ndim):
+        outside |= (X[d] < 0.0) | (X[d] > 1.0)
+    assert ((nout >= 2)[None] & outside).sum() > 0
