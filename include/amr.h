@@ -73,9 +73,17 @@ typedef enum {
     AMR_GHOST_DIAG_F2C = 5,/* edge / corner region covered by finer leaves:
                               restriction, round 1, one entry per fine leaf;
                               offset = its half along a 3D edge (else 0) */
-    AMR_GHOST_DIAG_C2F = 6 /* edge / corner region inside a coarser leaf: limited
+    AMR_GHOST_DIAG_C2F = 6,/* edge / corner region inside a coarser leaf: limited
                               prolongation, round 2; offset bit d = parity of the
                               same-size box's coordinate along dimension d */
+    AMR_GHOST_DIAG_BC = 7  /* edge / corner region outside a non-periodic domain
+                              (no counterpart in the paper, which fills face
+                              ghosts only): the boundary formula of face
+                              `offset` -- the face across the region's lowest
+                              dimension that leaves the domain -- applied to
+                              the cell mirrored across it; src = -1, aux = that
+                              face's boundary-face index; after round 2, edges
+                              before corners */
 } amr_ghost_kind;
 
 typedef struct amr_forest amr_forest;
@@ -115,11 +123,12 @@ typedef struct {
     double gravity[3];     /* g of the source term S = (0, rho g, rho g.u) added to
                               every stage (Sec. 4.2); zero: no source */
     int diagonal_ghosts;   /* 1: the pattern also fills the edge and corner ghost
-                              regions inside the domain (AMR_GHOST_DIAG copies and
+                              regions (AMR_GHOST_DIAG copies and
                               AMR_GHOST_DIAG_F2C restrictions in round 1,
-                              AMR_GHOST_DIAG_C2F prolongations in round 2); the
-                              paper and the stage kernels use face ghosts only
-                              (Sec. 2.1) */
+                              AMR_GHOST_DIAG_C2F prolongations in round 2,
+                              AMR_GHOST_DIAG_BC boundary formulas outside a
+                              non-periodic domain after them); the paper and the
+                              stage kernels use face ghosts only (Sec. 2.1) */
     int physics;           /* amr_physics: equations of the stage (Sec. 3.4, 3.5) */
     double velocity[3];    /* uniform velocity of the scalar advection equation
                               (Eq. 13); ignored for Euler */

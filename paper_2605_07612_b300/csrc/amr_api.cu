@@ -183,6 +183,7 @@ amr_status upload_pattern(amr_forest *f) {
     if ((s = upload(f, f->r1, f->pat.round1)) != AMR_OK) return s;
     if ((s = upload(f, f->r2, f->pat.round2)) != AMR_OK) return s;
     if ((s = upload(f, f->r1g, f->pat.round1_gather)) != AMR_OK) return s;
+    if (!f->pat.round3.empty() && (s = upload(f, f->r3, f->pat.round3)) != AMR_OK) return s;
     if ((s = upload(f, f->info, f->pat.info)) != AMR_OK) return s;
     if ((s = upload(f, f->fix, f->pat.fix)) != AMR_OK) return s;
     if ((s = upload(f, f->fix_start, f->pat.fix_start)) != AMR_OK) return s;
@@ -600,7 +601,7 @@ amr_status amr_destroy_forest(amr_forest *f) {
     if (!f) return AMR_OK;
     if (f->gexec) cudaGraphExecDestroy(f->gexec);
     if (f->cap_stream) cudaStreamDestroy(f->cap_stream);
-    for (DBuf *b : {&f->r1, &f->r2, &f->r1g, &f->info, &f->fix, &f->fix_start, &f->bflux, &f->bcdata, &f->sc, &f->partial, &f->sums,
+    for (DBuf *b : {&f->r1, &f->r2, &f->r1g, &f->r3, &f->info, &f->fix, &f->fix_start, &f->bflux, &f->bcdata, &f->sc, &f->partial, &f->sums,
                     &f->flags, &f->ops, &f->level, &f->dxtab, &f->invdxtab, &f->bctype, &f->bcval, &f->cfltab, &f->ranges,
                     &f->feat, &f->prob, &f->mflags, &f->flist, &f->wflux})
         dev_free(f, b->p);

@@ -44,7 +44,7 @@ struct amr_forest {
     int esize = 8;
     size_t block_bytes = 0;
     void *state = nullptr;
-    amrb::DBuf r1, r2, r1g, info, fix, fix_start, bflux, bcdata, sc, partial, sums, flags, ops, level;
+    amrb::DBuf r1, r2, r1g, r3, info, fix, fix_start, bflux, bcdata, sc, partial, sums, flags, ops, level;
     amrb::DBuf dxtab, invdxtab, bctype, bcval, cfltab, ranges;   // per-instance tables
     amrb::DBuf feat, prob, mflags, flist;                        // learned-flag predictor
     amrb::DBuf wflux;                                            // WENO5 stage scratch (face fluxes)

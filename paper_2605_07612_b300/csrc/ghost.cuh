@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(256) k_ghost(GhostArgs<real> a, Geom g) {
     const Entry e = a.list[warp];
     real *dstb = a.u + int64_t(e.dst) * g.bstride;
     const real *srcb = e.src >= 0 ? a.u + int64_t(e.src) * g.bstride : nullptr;
-    if (e.kind == KIND_DIAG || e.kind == KIND_DIAG_F2C || e.kind == KIND_DIAG_C2F) {
+    if (e.kind == KIND_DIAG || e.kind == KIND_DIAG_F2C || e.kind == KIND_DIAG_C2F || e.kind == KIND_DIAG_BC) {
         // edge / corner region in direction (dx, dy, dz): ghost box of the
         // block, copied from a same-level neighbour's interior, restricted
         // from a finer neighbour (half the box along a 3D edge per neighbour),
@@ -318,6 +318,36 @@ __global__ void __launch_bounds__(256) k_ghost(GhostArgs<real> a, Geom g) {
             if (e.kind == KIND_DIAG) {
                 const int y0 = x[0] - dir[0] * N, y1 = x[1] - dir[1] * N, y2 = D == 3 ? x[2] - dir[2] * N : 0;
                 val = srcb[int64_t(v) * g.ncell + cell_index<real>(g, y0, y1, y2)];
+            } else if (e.kind == KIND_DIAG_BC) {
+                // outside a non-periodic domain: the boundary formula of face
+                // e.offset applied to the cell mirrored across it (a face
+                // ghost for an edge cell, filled before; an edge cell for a
+                // corner, filled by the launch before); per-cell boundary
+                // data at the tangential position clamped to the face
+                const int fb = e.offset, nb = fb >> 1, sb = fb & 1;
+                const int k = sb ? x[nb] - N + 1 : -x[nb];
+                int y[3] = {x[0], x[1], x[2]};
+                y[nb] = sb ? N - k : k - 1;
+                const real um = dstb[int64_t(v) * g.ncell + cell_index<real>(g, y[0], y[1], y[2])];
+                const int inst = a.info[e.dst].inst;
+                const int ty = a.bc_type[6 * inst + fb];
+                const real bv = a.bc_val[(6 * inst + fb) * 8 + v];
+                if (ty == 1) {
+                    val = real(2) * bv - um;
+                } else if (ty == 2) {
+                    const real h = mul_rn(real(2 * k - 1), real(g.dx[3 * a.info[e.dst].gclass + nb]));
+                    val = add_rn(um, mul_rn(h, bv));
+                } else {
+                    int t = 0, scale = 1;
+                    for (int d = 0; d < D; ++d) {
+                        if (d == nb) continue;
+                        const int c = x[d] < 0 ? 0 : (x[d] >= N ? N - 1 : x[d]);
+                        t += c * scale;
+                        scale *= N;
+                    }
+                    const int64_t nface = (D == 3) ? int64_t(N) * N : N;
+                    val = real(2) * a.bcdata[(int64_t(e.aux) * g.V + v) * nface + t] - um;
+                }
             } else if (e.kind == KIND_DIAG_F2C) {
                 // lower corner of the 2^D fine cells: across the region's
                 // faces as for a face restriction, along an edge shifted by

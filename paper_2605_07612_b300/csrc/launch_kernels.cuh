@@ -36,17 +36,28 @@ amr_status launch_ghosts(amr_forest *f, int s, cudaStream_t st, bool gather) {
     a.bc_type = static_cast<const int32_t *>(f->bctype.p);
     a.bc_val = static_cast<const real *>(f->bcval.p);
     a.info = static_cast<const BlockInfo *>(f->info.p);
-    for (int round = 0; round < 2; ++round) {
-        const auto &lst = round == 0 ? (gather ? f->pat.round1_gather : f->pat.round1) : f->pat.round2;
-        if (lst.empty()) continue;
-        a.list = static_cast<const Entry *>(round == 0 ? (gather ? f->r1g.p : f->r1.p) : f->r2.p);
-        a.n = int(lst.size());
+    // rounds 1 and 2, then the edge and the corner regions outside the domain
+    const int n3 = int(f->pat.round3.size()), n3e = f->pat.n_round3_edges;
+    for (int round = 0; round < 4; ++round) {
+        const Entry *list;
+        int n;
+        if (round < 2) {
+            const auto &lst = round == 0 ? (gather ? f->pat.round1_gather : f->pat.round1) : f->pat.round2;
+            list = static_cast<const Entry *>(round == 0 ? (gather ? f->r1g.p : f->r1.p) : f->r2.p);
+            n = int(lst.size());
+        } else {
+            list = static_cast<const Entry *>(f->r3.p) + (round == 3 ? n3e : 0);
+            n = round == 2 ? n3e : n3 - n3e;
+        }
+        if (n == 0) continue;
+        a.list = list;
+        a.n = n;
         const int N = f->cfg.block_n, NG = f->cfg.n_ghost;
         // warps per strip: about 512 values of a full face strip each
         const int64_t face_vals = int64_t(D == 3 ? N * N : N) * NG * f->cfg.n_var;
         a.parts = int(std::max<int64_t>(1, std::min<int64_t>(32, face_vals / 512)));
         const int64_t grid = (int64_t(a.n) * a.parts + 7) / 8;
-        TraceSpan span(f, round == 0 ? AMR_PHASE_GHOST_R1 : AMR_PHASE_GHOST_R2, st);
+        TraceSpan span(f, round == 0 ? AMR_PHASE_GHOST_R1 : AMR_PHASE_GHOST_R2, st);   // rounds 3-4 count as round 2
         bool launched = false;
 #define AMR_GHOST_CASE(n_, g_)                                                   \
     if (!launched && N == n_ && NG == g_) {                                     \

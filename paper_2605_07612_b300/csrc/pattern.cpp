@@ -71,14 +71,23 @@ bool build_pattern(const std::vector<const Forest *> &inst, const std::vector<in
                     for (int dx = -1; dx <= 1; ++dx) {
                         const int dir[3] = {dx, dy, dz};
                         if ((dx != 0) + (dy != 0) + (dz != 0) < 2) continue;
-                        int64_t q[3] = {A.g[0], A.g[1], A.g[2]};
-                        bool inside = true;
-                        for (int d = 0; d < D && inside; ++d) {
-                            q[d] += dir[d];
-                            inside = F.wrap(d, A.lev, q[d]);
-                        }
-                        if (!inside) continue;
                         const int code = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
+                        // outside a non-periodic domain: the boundary formula
+                        // of the face across the lowest such dimension
+                        int dout = -1;
+                        for (int d = 0; d < D && dout < 0; ++d) {
+                            int64_t qd = A.g[d] + dir[d];
+                            if (dir[d] != 0 && !F.wrap(d, A.lev, qd)) dout = d;
+                        }
+                        if (dout >= 0) {
+                            P.entries.push_back({KIND_DIAG_BC, code, b, -1, 2 * dout + (dir[dout] > 0 ? 1 : 0), -1});
+                            continue;
+                        }
+                        int64_t q[3] = {A.g[0], A.g[1], A.g[2]};
+                        for (int d = 0; d < D; ++d) {
+                            q[d] += dir[d];
+                            F.wrap(d, A.lev, q[d]);
+                        }
                         const int s = F.find(A.lev, q[0], q[1], q[2]);
                         if (s >= 0) {
                             P.entries.push_back({KIND_DIAG, code, b, o0 + s, 0, 0});
@@ -114,9 +123,15 @@ bool build_pattern(const std::vector<const Forest *> &inst, const std::vector<in
         return x.offset < y.offset;
     });
     int32_t ibf = 0;
+    std::vector<int32_t> bc_index(size_t(nb) * 6, -1);   // (block, face) -> boundary-face index
     for (Entry &e : P.entries)
-        if (e.kind == KIND_BC) e.aux = ibf++;
+        if (e.kind == KIND_BC) {
+            bc_index[size_t(e.dst) * 6 + size_t(e.face)] = ibf;
+            e.aux = ibf++;
+        }
     P.n_bc = ibf;
+    for (Entry &e : P.entries)
+        if (e.kind == KIND_DIAG_BC) e.aux = bc_index[size_t(e.dst) * 6 + size_t(e.offset)];
 
     // execution lists and refinement-face flux slots
     P.info.assign(size_t(nb), BlockInfo{});
@@ -133,10 +148,19 @@ bool build_pattern(const std::vector<const Forest *> &inst, const std::vector<in
     }
     // blocks whose face ghosts a prolongation reads (their same-level face
     // ghosts are filled in gather mode too)
+    // (and blocks whose outside edge and corner cells mirror their face ghosts)
     std::vector<char> c2f_src(size_t(nb), 0);
-    for (const Entry &e : P.entries)
-        if (e.kind == KIND_C2F || e.kind == KIND_DIAG_C2F) c2f_src[size_t(e.src)] = 1;
     for (const Entry &e : P.entries) {
+        if (e.kind == KIND_C2F || e.kind == KIND_DIAG_C2F) c2f_src[size_t(e.src)] = 1;
+        if (e.kind == KIND_DIAG_BC) c2f_src[size_t(e.dst)] = 1;
+    }
+    std::vector<Entry> corners;
+    for (const Entry &e : P.entries) {
+        if (e.kind == KIND_DIAG_BC) {
+            const bool corner = e.face != 13 && (e.face % 3) != 1 && ((e.face / 3) % 3) != 1 && (e.face / 9) != 1;
+            (corner ? corners : P.round3).push_back(e);
+            continue;
+        }
         const bool r2 = e.kind == KIND_C2F || e.kind == KIND_DIAG_C2F;
         (r2 ? P.round2 : P.round1).push_back(e);
         if (e.kind == KIND_SRL) P.info[e.dst].nbr[e.face] = e.src;
@@ -152,6 +176,8 @@ bool build_pattern(const std::vector<const Forest *> &inst, const std::vector<in
     // run close together in time and meet in L2
     for (std::vector<Entry> *l : {&P.round1, &P.round2, &P.round1_gather})
         std::stable_sort(l->begin(), l->end(), [](const Entry &x, const Entry &y) { return x.dst < y.dst; });
+    P.n_round3_edges = int32_t(P.round3.size());
+    P.round3.insert(P.round3.end(), corners.begin(), corners.end());
     // fix-up faces: every (coarse block, face) with F2C sources
     for (const Entry &e : P.entries) {
         if (e.kind != KIND_F2C) continue;

@@ -14,7 +14,8 @@ namespace amrb {
 
 constexpr int kMaxLevels = 13;   // levels 0..12 per instance
 
-enum : int32_t { KIND_SRL = 0, KIND_F2C = 1, KIND_BC = 2, KIND_C2F = 3, KIND_DIAG = 4, KIND_DIAG_F2C = 5, KIND_DIAG_C2F = 6 };
+enum : int32_t { KIND_SRL = 0, KIND_F2C = 1, KIND_BC = 2, KIND_C2F = 3, KIND_DIAG = 4, KIND_DIAG_F2C = 5, KIND_DIAG_C2F = 6,
+                 KIND_DIAG_BC = 7 };
 
 struct Entry {
     int32_t kind, face, dst, src, offset, aux;
@@ -45,6 +46,11 @@ struct Pattern {
     // non-SRL entry, plus the SRL entries of blocks that are the coarse
     // source of a C2F entry (their ghosts feed the prolongation)
     std::vector<Entry> round1_gather;
+    // edge and corner regions outside a non-periodic domain (KIND_DIAG_BC),
+    // after rounds 1 and 2: the edges first (their mirror cells are face
+    // ghosts), then the 3D corners (their mirror cells are edge cells)
+    std::vector<Entry> round3;
+    int32_t n_round3_edges = 0;
     std::vector<BlockInfo> info;  // per block
     std::vector<FixFace> fix;     // sorted by (block, face)
     std::vector<int32_t> fix_start;  // per fix-up block: first index into fix (+ sentinel)
@@ -61,7 +67,11 @@ struct Pattern {
 // (a same-level leaf holds the region: copy, round 1), KIND_DIAG_F2C (finer
 // leaves: restriction, round 1, one entry per fine leaf, offset = its
 // position along a 3D edge), KIND_DIAG_C2F (a coarser leaf: prolongation,
-// round 2, offset bit d = parity of the same-size box along dimension d).
+// round 2, offset bit d = parity of the same-size box along dimension d);
+// a region reaching outside a non-periodic domain gets KIND_DIAG_BC (the
+// boundary formula of face `offset`, the face across the region's lowest
+// dimension that leaves the domain, applied to the mirrored cell; aux = that
+// face's boundary-face index; round 3).
 bool build_pattern(const std::vector<const Forest *> &inst, const std::vector<int64_t> &offset, Pattern &out,
                    std::string &err, bool diagonal = false);
 

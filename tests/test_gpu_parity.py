@@ -976,6 +976,43 @@ def test_ghost_fill_with_diagonal_ghosts_bit_exact(dim):
 
 
 @pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("bc", [2, 3])
+def test_outside_edge_and_corner_ghosts_bit_exact(dim, bc):
+    """Edge and corner ghosts outside a non-periodic domain (kind 7: the
+    boundary formula of the face across the region's lowest outside
+    dimension, applied to the mirrored cell; edges, then corners) on a
+    4-level mesh refined toward a corner of a box with boundaries on every
+    side: the GPU fill equals the oracle's bit for bit in FP64, with Neumann
+    values (bc 2; they are the outward derivatives of the linear field of
+    Sec. 4.3, so the oracle reproduces that field in every ghost cell) and
+    with per-cell Dirichlet data (bc 3; tangential positions clamped to the
+    face)."""
+    coef = (1.0, 2.0, 3.0)
+    bcv = tuple(tuple(((v + 1.0) * coef[fa // 2] * (1.0 if fa % 2 else -1.0)) if fa // 2 < dim else 0.0
+                      for v in range(8)) for fa in range(6))
+    sp = synth.MeshSpec(ndim=dim, N=8, ng=2, ntrees=(2, 2, 2)[:dim] + (1,) * (3 - dim), periodic=(0, 0, 0),
+                        max_level=3, bc_type=(bc,) * 6, bc_val=bcv, diagonal_ghosts=1)
+    pt = (0.02, 0.97, 0.03)[:dim] + (0.0,) * (3 - dim)
+    om, f = make_pair(sp, 0, [lambda s, lev, g: synth.point_flags(s, lev, g, pt, 3)] * 3)
+    lev, g = om.blocks()
+    pat = f.pattern()
+    assert (pat[:, 0] == 7).sum() > 0
+    u = synth.linear_field(sp, lev, g)
+    bcd = None
+    if bc == 3:
+        bce = [(fa, d) for k, fa, d, s_, o, a_ in om.pattern() if k == oracle.KIND_BC]
+        bcd = synth.linear_face_values(sp, lev, g, bce)
+        f.set_bc_data(bcd)
+    f.set_state(0, u)
+    f.fill_ghosts(0)
+    om.fill_ghosts(u, bcd)
+    np.testing.assert_array_equal(f.get_state(0), u)
+    if bc == 2:
+        exact = synth.linear_field(sp, lev, g, with_ghosts=True)
+        assert np.abs(u - exact).max() <= 4.5e-16 * 16 * np.abs(exact).max()
+
+
+@pytest.mark.parametrize("dim", [2, 3])
 def test_diagonal_ghosts_in_gather_steps(dim):
     """Edge and corner ghosts on while stepping with gathered halos (the
     gather-mode ghost list keeps the face ghosts the prolongations read):
