@@ -57,7 +57,8 @@ amr_status launch_ghosts(amr_forest *f, int s, cudaStream_t st, bool gather) {
         const int64_t face_vals = int64_t(D == 3 ? N * N : N) * NG * f->cfg.n_var;
         a.parts = int(std::max<int64_t>(1, std::min<int64_t>(32, face_vals / 512)));
         const int64_t grid = (int64_t(a.n) * a.parts + 7) / 8;
-        TraceSpan span(f, round == 0 ? AMR_PHASE_GHOST_R1 : AMR_PHASE_GHOST_R2, st);   // rounds 3-4 count as round 2
+        // the edge and corner launches after round 2 are timed as round 2
+        TraceSpan span(f, round == 0 ? AMR_PHASE_GHOST_R1 : AMR_PHASE_GHOST_R2, st);
         bool launched = false;
 #define AMR_GHOST_CASE(n_, g_)                                                   \
     if (!launched && N == n_ && NG == g_) {                                     \
