@@ -82,6 +82,7 @@ def _lib_handle():
             lib.orc_face_flux.argtypes = [P(Params), C.c_int, vp, vp, vp]
             lib.orc_conserved.argtypes = [vp, vp, vp]
             lib.orc_lohner_flags.argtypes = [vp, vp, C.c_double, C.c_double, C.c_double, C.c_double, vp]
+            lib.orc_lohner_scores.argtypes = [vp, vp, C.c_double, C.c_double, vp]
             lib.orc_transfer.restype = C.c_int
             lib.orc_transfer.argtypes = [vp, vp, vp, vp]
             lib.orc_set_threads.argtypes = [C.c_int]
@@ -236,6 +237,13 @@ class Mesh:
         f = np.zeros(self.n, dtype=np.int8)
         self._lib.orc_lohner_flags(self._h, _ptr(u), c_ref, c_deref, eps, eps_abs, _ptr(f))
         return f
+
+    def lohner_scores(self, u, eps=1e-2, eps_abs=1e-10) -> np.ndarray:
+        """Largest criterion value of each block (what lohner_flags compares
+        with the thresholds)."""
+        sc = np.zeros(self.n, dtype=np.float64)
+        self._lib.orc_lohner_scores(self._h, _ptr(u), eps, eps_abs, _ptr(sc))
+        return sc
 
     def transfer(self, u_old, new_mesh: "Mesh") -> np.ndarray:
         out = new_mesh.new_state()

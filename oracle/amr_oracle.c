@@ -1449,6 +1449,45 @@ void orc_lohner_flags(const orc_mesh *m, const double *u, double c_ref, double c
     }
 }
 
+/* The largest criterion value of each block (the quantity orc_lohner_flags
+ * compares with c_ref and c_deref), computed by the same loops: per cell the
+ * larger of the density and pressure values of |E|, per block the largest of
+ * those.  Tests use it to put the thresholds exactly on a block's value. */
+void orc_lohner_scores(const orc_mesh *m, const double *u, double eps, double eps_abs, double *scores)
+{
+    const orc_params *p = &m->p;
+    int N = p->N, D = p->ndim, V = p->nvar;
+    for (int b = 0; b < m->n; b++) {
+        double bmax = 0.0;
+        int kr = (D == 3) ? N : 1;
+        for (int k = 0; k < kr; k++)
+            for (int j = 0; j < N; j++)
+                for (int i = 0; i < N; i++) {
+                    double cellmax = 0.0;
+                    for (int which = 0; which < 2; which++) {
+                        double e2 = 0.0;
+                        for (int n = 0; n < D; n++) {
+                            double val[3];
+                            for (int q = -1; q <= 1; q++) {
+                                int x[3] = {i, j, k};
+                                x[n] += q;
+                                double U[5], W[5];
+                                for (int v = 0; v < V; v++) U[v] = u[atv(p, b, v, x)];
+                                primitive_of(p, U, W);
+                                val[q + 1] = (which == 0 || p->physics == 1) ? W[0] : W[D + 1];
+                            }
+                            double e = lohner_1d(val[0], val[1], val[2], eps, eps_abs);
+                            e2 = e2 + e * e;
+                        }
+                        double E = sqrt(e2);
+                        if (E > cellmax) cellmax = E;
+                    }
+                    if (cellmax > bmax) bmax = cellmax;
+                }
+        scores[b] = bmax;
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Data transfer after a mesh change (Sec. 2.2): blocks that kept their level */
 /* and position are copied; refined blocks are prolonged from the old parent  */

@@ -326,6 +326,20 @@ def test_lohner_flags_closed_form():
     a, b = 1.0, 0.125
     E = abs(b - a) / (1e-10 + abs(b - a) + 1e-2 * (3 * a + b))
     assert E > 5e-2
+    # the largest value per block: the pressure jump (1 | 0.1) seen from the
+    # last cell before it (the stencil a, a, b) and the first cell after it
+    # (a, b, b); the uniform blocks give exactly 0
+    pa, pb = 1.0, 0.1
+    e_before = abs(pb - pa) / (1e-10 + abs(pb - pa) + 1e-2 * (3 * pa + pb))
+    e_after = abs(pb - pa) / (1e-10 + abs(pb - pa) + 1e-2 * (pa + 3 * pb))
+    np.testing.assert_allclose(m.lohner_scores(u), [0.0, e_before, e_after, 0.0], rtol=1e-14, atol=0.0)
+    # the flags are the scores against the thresholds
+    sc = m.lohner_scores(u)
+    for b in (1, 2):
+        assert m.lohner_flags(u, c_ref=sc[b])[b] != 1
+        assert m.lohner_flags(u, c_ref=np.nextafter(sc[b], 0.0))[b] == 1
+        assert m.lohner_flags(u, c_ref=2.0, c_deref=np.nextafter(sc[b], 2.0))[b] == -1
+        assert m.lohner_flags(u, c_ref=2.0, c_deref=sc[b])[b] == 0
 
 
 @pytest.mark.parametrize("mach", [1.0, 1.5, 3.0, 10.0])
