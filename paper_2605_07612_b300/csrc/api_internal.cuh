@@ -47,6 +47,7 @@ struct amr_forest {
     amrb::DBuf r1, r2, r1g, r3, info, fix, fix_start, bflux, bcdata, sc, partial, sums, flags, ops, level;
     amrb::DBuf dxtab, invdxtab, bctype, bcval, cfltab, ranges;   // per-instance tables
     amrb::DBuf feat, prob, mflags, flist;                        // learned-flag predictor
+    amrb::DBuf slist;                                           // criterion: FP32 screen count + FP64 list
     amrb::DBuf wflux;                                            // WENO5 stage scratch (face fluxes)
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t gexec = nullptr;

@@ -263,9 +263,12 @@ __host__ __device__ constexpr size_t flags_smem(int N, int D) {
 
 template <class real, int D>
 __global__ void __launch_bounds__(384) k_flags(const real *u, Geom g, double gam, double c_ref, double c_deref, double eps,
-                                               double eps_abs, int8_t *flags, const int32_t *list) {
+                                               double eps_abs, int8_t *flags, const int32_t *list,
+                                               const int32_t *count = nullptr) {
     extern __shared__ double fsm[];
     __shared__ double red[32];
+    // with a device-side count, CTAs beyond it have no block
+    if (count && int(blockIdx.x) >= *count) return;
     const int b = list ? list[blockIdx.x] : int(blockIdx.x);
     const int N = g.N, P = N + 2, plane = P * P;
     const int nslot = D == 3 ? 4 : 1;
@@ -336,6 +339,164 @@ __global__ void __launch_bounds__(384) k_flags(const real *u, Geom g, double gam
         for (int w = 1; w < int(blockDim.x >> 5); ++w) M = fmax(M, red[w]);
         const double E = __dsqrt_rn(M);
         flags[b] = E > c_ref ? 1 : (E < c_deref ? -1 : 0);
+    }
+}
+
+// ------------------------------------------------- criterion, FP32 screen
+// Exact flags at a fraction of the FP64 work for FP32 states: one CTA per
+// block evaluates every cell's criterion in FP32 as an interval that holds
+// the exact value (and the FP64 value k_flags computes) for sure, and
+// decides the block's flag when the interval of the block's largest value
+// lies clear of both thresholds; otherwise the block goes to a list that
+// k_flags then evaluates in FP64.  Bounds, with u = 2^-24:
+//   rho: exact (the FP32 state value); p: |p - p~| <= 2^-18 ((g-1) ke + |p|)
+//   + 1e-30 (rcp.approx.f32 errs by at most 2 u, each rounding by u; the
+//   floor covers values flushed to zero in the range the screen admits);
+//   indicator of (a-, a0, a+) with input bounds (b-, b0, b+), B = b- + 2 b0 + b+:
+//   |num - num~| <= B + 2^-21 u*,  |den - den~| <= (1 + eps) B + 2^-20 den~,
+//   so e lies in [(num~ - Bn) / (den~ + Bd), (num~ + Bn) / (den~ - Bd)],
+//   widened by (1 -/+ 2^-19) for the rounding of the bounds themselves.
+// A block is left to the FP64 pass when any input is not finite or outside
+// 1e-6 <= rho <= 1e6, |U| <= 1e12, or some den~ <= 2 Bd.  thr: the squares
+// of c_ref and c_deref (-1 for a negative threshold), each with the margin
+// 2^-40 that keeps the FP64 square root's rounding on the decided side.
+struct ScreenThresholds {
+    double ref2_lo, ref2_hi, deref2_lo, deref2_hi;
+};
+
+template <int D>
+__global__ void __launch_bounds__(384) k_flags_screen(const float *u, Geom g, float gm1, float eps, float eps_abs,
+                                                      ScreenThresholds thr, int8_t *flags, int32_t *list, int32_t *count) {
+    extern __shared__ float fss[];
+    __shared__ float rlo[32], rhi[32];
+    __shared__ int rbad;
+    const int b = int(blockIdx.x);
+    const int N = g.N, P = N + 2, plane = P * P;
+    const int nslot = D == 3 ? 4 : 1;
+    float *R = fss, *Q = fss + nslot * plane, *Bq = fss + 2 * nslot * plane;
+    const float *ub = u + int64_t(b) * g.bstride;
+    if (threadIdx.x == 0) rbad = 0;
+    bool bad = false;
+    auto load = [&](int k, int slot) {
+        const int n = (D == 3 && (k < 0 || k >= N)) ? N * N : N * N + 4 * N;
+        for (int t = threadIdx.x; t < n; t += blockDim.x) {
+            int i, j;
+            if (t < N * N) {
+                i = t % N;
+                j = t / N;
+            } else {
+                const int side = (t - N * N) / N, q = (t - N * N) % N;
+                i = side == 0 ? -1 : (side == 1 ? N : q);
+                j = side == 2 ? -1 : (side == 3 ? N : q);
+            }
+            const int64_t cell = cell_index<float>(g, i, j, k);
+            float U[5];
+            for (int v = 0; v < g.V; ++v) U[v] = ub[int64_t(v) * g.ncell + cell];
+            const float rho = U[0];
+            float p = rho, bp = 0.f;
+            bool ok = rho >= 1e-6f && rho <= 1e6f;
+            if (g.phys != 1) {
+                const float r = rcp_ftz(rho);
+                float ke = 0.f;
+                for (int d = 0; d < D; ++d) {
+                    ok = ok && fabsf(U[1 + d]) <= 1e12f;
+                    const float w = U[1 + d] * r;
+                    ke = fmaf(w, w, ke);
+                }
+                ok = ok && fabsf(U[D + 1]) <= 1e12f;
+                ke = 0.5f * rho * ke;
+                p = gm1 * (U[D + 1] - ke);
+                bp = 0x1p-18f * fmaf(gm1, ke, fabsf(p)) + 1e-30f;
+                ok = ok && isfinite(p) && isfinite(ke);
+            }
+            bad = bad || !ok;
+            const int c = slot * plane + (j + 1) * P + i + 1;
+            R[c] = rho;
+            Q[c] = p;
+            Bq[c] = bp;
+        }
+    };
+    // interval of the 1D indicator of (am, a0, ap) with bounds (bm, b0, bq)
+    auto interval = [&](float am, float a0, float ap, float bm, float b0, float bq, float &lo, float &hi) {
+        const float num = fabsf(am - 2.f * a0 + ap);
+        const float ustar = fabsf(am) + 2.f * fabsf(a0) + fabsf(ap);
+        const float den = eps_abs + fabsf(a0 - am) + fabsf(ap - a0) + eps * ustar;
+        const float B = bm + 2.f * b0 + bq;
+        const float Bn = B + 0x1p-21f * ustar;
+        const float Bd = (1.f + eps) * B + 0x1p-20f * den;
+        bad = bad || !(den > 2.f * Bd);
+        hi = (num + Bn) * rcp_ftz(den - Bd) * (1.f + 0x1p-19f);
+        lo = fmaxf(num - Bn, 0.f) * rcp_ftz(den + Bd) * (1.f - 0x1p-19f);
+    };
+    float mlo = 0.f, mhi = 0.f;
+    auto eval = [&](int sm, int s0, int sp) {
+        for (int t = threadIdx.x; t < N * N; t += blockDim.x) {
+            const int c = (t / N + 1) * P + t % N + 1;
+            for (int which = 0; which < 2; ++which) {
+                const float *A = which ? Q : R;
+                const float *A0 = A + s0 * plane;
+                const float *BB = Bq + s0 * plane;
+                float lo, hi, e2lo = 0.f, e2hi = 0.f;
+                interval(A0[c - 1], A0[c], A0[c + 1], which ? BB[c - 1] : 0.f, which ? BB[c] : 0.f,
+                         which ? BB[c + 1] : 0.f, lo, hi);
+                e2lo = fmaf(lo, lo, e2lo);
+                e2hi = fmaf(hi, hi, e2hi);
+                interval(A0[c - P], A0[c], A0[c + P], which ? BB[c - P] : 0.f, which ? BB[c] : 0.f,
+                         which ? BB[c + P] : 0.f, lo, hi);
+                e2lo = fmaf(lo, lo, e2lo);
+                e2hi = fmaf(hi, hi, e2hi);
+                if (D == 3) {
+                    interval(A[sm * plane + c], A0[c], A[sp * plane + c], which ? Bq[sm * plane + c] : 0.f,
+                             which ? BB[c] : 0.f, which ? Bq[sp * plane + c] : 0.f, lo, hi);
+                    e2lo = fmaf(lo, lo, e2lo);
+                    e2hi = fmaf(hi, hi, e2hi);
+                }
+                mlo = fmaxf(mlo, e2lo * (1.f - 0x1p-19f));
+                mhi = fmaxf(mhi, e2hi * (1.f + 0x1p-19f));
+                bad = bad || !isfinite(e2hi);
+            }
+        }
+    };
+    __syncthreads();
+    if (D == 2) {
+        load(0, 0);
+        __syncthreads();
+        eval(0, 0, 0);
+    } else {
+        for (int k = -1; k <= N; ++k) {
+            load(k, (k + 1) & 3);
+            __syncthreads();
+            if (k >= 1) eval((k - 1) & 3, k & 3, (k + 1) & 3);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        mlo = fmaxf(mlo, __shfl_xor_sync(0xffffffffu, mlo, o));
+        mhi = fmaxf(mhi, __shfl_xor_sync(0xffffffffu, mhi, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        rlo[threadIdx.x >> 5] = mlo;
+        rhi[threadIdx.x >> 5] = mhi;
+    }
+    if (bad) atomicOr(&rbad, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float L = rlo[0], H = rhi[0];
+        for (int w = 1; w < int(blockDim.x >> 5); ++w) {
+            L = fmaxf(L, rlo[w]);
+            H = fmaxf(H, rhi[w]);
+        }
+        // the block's largest squared value M (FP64, as k_flags computes it) lies in [L, H]
+        const double lo = double(L), hi = double(H);
+        int flag = 2;   // undecided
+        if (!rbad) {
+            const bool is_ref = lo > thr.ref2_hi, not_ref = hi < thr.ref2_lo;          // sqrt(M) > c_ref, <= c_ref
+            const bool is_deref = hi < thr.deref2_lo, not_deref = lo > thr.deref2_hi;  // sqrt(M) < c_deref, >= c_deref
+            if (is_ref) flag = 1;
+            else if (not_ref && is_deref) flag = -1;
+            else if (not_ref && not_deref) flag = 0;
+        }
+        if (flag != 2) flags[b] = int8_t(flag);
+        else list[atomicAdd(count, 1)] = b;
     }
 }
 

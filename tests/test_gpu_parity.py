@@ -291,6 +291,49 @@ def test_lohner_flags_bit_exact_fp32_uniform(N):
         np.testing.assert_array_equal(f.flag(0, c_ref, c_deref), om.lohner_flags(u64, c_ref, c_deref))
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+def test_fp32_flags_with_thresholds_on_block_values(dim):
+    """The criterion of an FP32 state first runs an FP32 interval screen and
+    hands the blocks it cannot decide to the FP64 kernel.  With c_ref or
+    c_deref placed exactly on a block's largest value (from the oracle) and
+    one FP64 step either side -- where only the FP64 evaluation can tell the
+    flags apart -- every block's flag equals the oracle's; the same holds at
+    the usual thresholds.  Periodic uniform meshes, so both sides see the same
+    ghost values."""
+    if dim == 2:
+        sp = synth.MeshSpec(ndim=2, N=16, ng=2, ntrees=(8, 8, 1))
+    else:
+        sp = synth.MeshSpec(ndim=3, N=8, ng=2, ntrees=(4, 4, 4))
+    om, f = make_pair(sp, 0, precision=32)
+    lev, g = om.blocks()
+    u = (synth.kelvin_helmholtz(sp, lev, g, seed=7) if dim == 2 else synth.fourier3d(sp, lev, g, seed=7)).astype(np.float32)
+    f.set_state(0, u)
+    f.fill_ghosts(0)
+    u64 = f.get_state(0).astype(np.float64)
+    om.fill_ghosts(u64)
+    np.testing.assert_array_equal(f.get_state(0).astype(np.float64), u64)
+    sc = om.lohner_scores(u64)
+    order = np.argsort(sc)
+    picks = order[np.linspace(0, len(sc) - 1, 9).astype(int)]
+    cases = list(THRESHOLDS)
+    for b in picks:
+        s_b = float(sc[b])
+        for c in (s_b, float(np.nextafter(s_b, 0.0)), float(np.nextafter(s_b, np.inf))):
+            cases.append((c, -1.0))          # refine or not, right at the value
+            cases.append((10.0, c))          # derefine or not
+    changed = 0
+    for c_ref, c_deref in cases:
+        ref = om.lohner_flags(u64, c_ref, c_deref)
+        np.testing.assert_array_equal(f.flag(0, c_ref, c_deref), ref, err_msg="c_ref %r c_deref %r" % (c_ref, c_deref))
+    for b in picks:
+        s_b = float(sc[b])
+        if s_b > 0.0:
+            lo = om.lohner_flags(u64, float(np.nextafter(s_b, 0.0)), -1.0)[b]
+            at = om.lohner_flags(u64, s_b, -1.0)[b]
+            changed += int(lo != at)
+    assert changed >= 5, changed
+
+
 def test_lohner_flags_nan_cells():
     """NaN cells: the criterion ignores a NaN score, on both sides (periodic
     uniform mesh, so the ghost fill only copies the NaNs)."""
