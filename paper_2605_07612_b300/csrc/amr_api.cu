@@ -391,32 +391,33 @@ amr_status launch_flags(amr_forest *f, int s, const amr_flag_params *p, const in
     CU(cudaGetLastError());
     return AMR_OK;
 }
-// The criterion of an FP32 state: the FP32 interval screen decides the
-// blocks whose largest value lies clear of both thresholds, the FP64 kernel
-// the rest (the same flags as the FP64 kernel alone, bit for bit).
+// The criterion: the FP32 interval screen decides the blocks whose largest
+// value lies clear of both thresholds, the FP64 kernel the rest (the same
+// flags as the FP64 kernel alone, bit for bit).
 double screen_square(double c, double scale) { return c > 0.0 ? c * c * scale : (c == 0.0 ? 0.0 : -1.0); }
-template <int D>
+template <class real, int D>
 amr_status screen_flags(amr_forest *f, int s, const amr_flag_params *p, cudaStream_t st) {
     const int64_t nb = nblocks(f);
     amr_status r = ensure(f, f->slist, sizeof(int32_t) * size_t(nb + 1));
     if (r != AMR_OK) return r;
     int32_t *cnt = static_cast<int32_t *>(f->slist.p), *list = cnt + 1;
     int8_t *out = static_cast<int8_t *>(f->flags.p);
-    const float *u = static_cast<const float *>(slot_ptr(f, s));
+    const real *u = static_cast<const real *>(slot_ptr(f, s));
     const int N = f->cfg.block_n;
     const size_t smem = size_t(D == 3 ? 4 : 1) * 3 * size_t(N + 2) * size_t(N + 2) * sizeof(float);
-    if (smem > 48 * 1024) CU(cudaFuncSetAttribute(k_flags_screen<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    if (smem > 48 * 1024)
+        CU(cudaFuncSetAttribute(k_flags_screen<real, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
     const size_t smem64 = flags_smem(N, D);
-    if (smem64 > 48 * 1024) CU(cudaFuncSetAttribute(k_flags<float, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem64)));
+    if (smem64 > 48 * 1024) CU(cudaFuncSetAttribute(k_flags<real, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem64)));
     const double lo = 1.0 - 0x1p-40, hi = 1.0 + 0x1p-40;
     const ScreenThresholds thr{screen_square(p->c_refine, lo), screen_square(p->c_refine, hi), screen_square(p->c_derefine, lo),
                                screen_square(p->c_derefine, hi)};
     TraceSpan span(f, AMR_PHASE_FLAGS, st);
     CU(cudaMemsetAsync(cnt, 0, sizeof(int32_t), st));
-    k_flags_screen<D><<<unsigned(nb), unsigned(flags_threads(N)), smem, st>>>(
+    k_flags_screen<real, D><<<unsigned(nb), unsigned(flags_threads(N)), smem, st>>>(
         u, f->geom, float(f->cfg.gamma - 1.0), float(p->eps), float(p->eps_abs), thr, out, list, cnt);
     // the undecided blocks: CTAs beyond the device-side count return at once
-    k_flags<float, D><<<unsigned(nb), unsigned(flags_threads(N)), smem64, st>>>(u, f->geom, f->cfg.gamma, p->c_refine,
+    k_flags<real, D><<<unsigned(nb), unsigned(flags_threads(N)), smem64, st>>>(u, f->geom, f->cfg.gamma, p->c_refine,
                                                                               p->c_derefine, p->eps, p->eps_abs, out, list, cnt);
     f->launches += 2;
     CU(cudaGetLastError());
@@ -428,8 +429,7 @@ struct FlagFn {
         amr_status r = ensure(f, f->flags, std::max<int64_t>(nblocks(f), 1));
         if (r != AMR_OK) return r;
         if (nblocks(f) > 0) {
-            if constexpr (std::is_same<real, float>::value) return screen_flags<D>(f, s, p, st);
-            return launch_flags<real, D>(f, s, p, nullptr, int(nblocks(f)), static_cast<int8_t *>(f->flags.p), st);
+            return screen_flags<real, D>(f, s, p, st);
         }
         return AMR_OK;
     }

@@ -343,15 +343,17 @@ __global__ void __launch_bounds__(384) k_flags(const real *u, Geom g, double gam
 }
 
 // ------------------------------------------------- criterion, FP32 screen
-// Exact flags at a fraction of the FP64 work for FP32 states: one CTA per
-// block evaluates every cell's criterion in FP32 as an interval that holds
-// the exact value (and the FP64 value k_flags computes) for sure, and
+// Exact flags at a fraction of the FP64 work: one CTA per block evaluates
+// every cell's criterion in FP32 as an interval that holds the value from
+// the state's own numbers (and the FP64 value k_flags computes) for sure, and
 // decides the block's flag when the interval of the block's largest value
 // lies clear of both thresholds; otherwise the block goes to a list that
 // k_flags then evaluates in FP64.  Bounds, with u = 2^-24:
-//   rho: exact (the FP32 state value); p: |p - p~| <= 2^-18 ((g-1) ke + |p|)
-//   + 1e-30 (rcp.approx.f32 errs by at most 2 u, each rounding by u; the
-//   floor covers values flushed to zero in the range the screen admits);
+//   rho: exact for an FP32 state, within 2^-23 |rho| for an FP64 state
+//   rounded to FP32; p: |p - p~| <= 2^-18 ((g-1) ke + |p|) + 1e-30, twice
+//   that for an FP64 state (rcp.approx.f32 errs by at most 2 u, each
+//   rounding and each input's conversion by u; the floor covers values
+//   flushed to zero in the range the screen admits);
 //   indicator of (a-, a0, a+) with input bounds (b-, b0, b+), B = b- + 2 b0 + b+:
 //   |num - num~| <= B + 2^-21 u*,  |den - den~| <= (1 + eps) B + 2^-20 den~,
 //   so e lies in [(num~ - Bn) / (den~ + Bd), (num~ + Bn) / (den~ - Bd)],
@@ -364,9 +366,12 @@ struct ScreenThresholds {
     double ref2_lo, ref2_hi, deref2_lo, deref2_hi;
 };
 
-template <int D>
-__global__ void __launch_bounds__(384) k_flags_screen(const float *u, Geom g, float gm1, float eps, float eps_abs,
+template <class real, int D>
+__global__ void __launch_bounds__(384) k_flags_screen(const real *u, Geom g, float gm1, float eps, float eps_abs,
                                                       ScreenThresholds thr, int8_t *flags, int32_t *list, int32_t *count) {
+    constexpr bool WIDE = sizeof(real) == 8;                 // an FP64 state, rounded to FP32 here
+    constexpr float KR = WIDE ? 0x1p-23f : 0.f;              // density bound per |rho|
+    constexpr float KP = WIDE ? 0x1p-17f : 0x1p-18f;         // pressure bound factor
     extern __shared__ float fss[];
     __shared__ float rlo[32], rhi[32];
     __shared__ int rbad;
@@ -374,7 +379,7 @@ __global__ void __launch_bounds__(384) k_flags_screen(const float *u, Geom g, fl
     const int N = g.N, P = N + 2, plane = P * P;
     const int nslot = D == 3 ? 4 : 1;
     float *R = fss, *Q = fss + nslot * plane, *Bq = fss + 2 * nslot * plane;
-    const float *ub = u + int64_t(b) * g.bstride;
+    const real *ub = u + int64_t(b) * g.bstride;
     if (threadIdx.x == 0) rbad = 0;
     bool bad = false;
     auto load = [&](int k, int slot) {
@@ -389,12 +394,21 @@ __global__ void __launch_bounds__(384) k_flags_screen(const float *u, Geom g, fl
                 i = side == 0 ? -1 : (side == 1 ? N : q);
                 j = side == 2 ? -1 : (side == 3 ? N : q);
             }
-            const int64_t cell = cell_index<float>(g, i, j, k);
+            const int64_t cell = cell_index<real>(g, i, j, k);
             float U[5];
-            for (int v = 0; v < g.V; ++v) U[v] = ub[int64_t(v) * g.ncell + cell];
+            bool ok = true;
+            for (int v = 0; v < g.V; ++v) {
+                const real x = ub[int64_t(v) * g.ncell + cell];
+                // (false for NaN too; an FP32 state is range-checked in FP32,
+                // since FP64 instructions run at a small fraction of the FP32
+                // rate on B300)
+                if constexpr (WIDE) ok = ok && fabs(x) <= 1e12;
+                else ok = ok && fabsf(x) <= 1e12f;
+                U[v] = ok ? float(x) : 0.f;
+            }
             const float rho = U[0];
-            float p = rho, bp = 0.f;
-            bool ok = rho >= 1e-6f && rho <= 1e6f;
+            float p = rho, bp = KR * rho;
+            ok = ok && rho >= 1e-6f && rho <= 1e6f;
             if (g.phys != 1) {
                 const float r = rcp_ftz(rho);
                 float ke = 0.f;
@@ -406,7 +420,7 @@ __global__ void __launch_bounds__(384) k_flags_screen(const float *u, Geom g, fl
                 ok = ok && fabsf(U[D + 1]) <= 1e12f;
                 ke = 0.5f * rho * ke;
                 p = gm1 * (U[D + 1] - ke);
-                bp = 0x1p-18f * fmaf(gm1, ke, fabsf(p)) + 1e-30f;
+                bp = KP * fmaf(gm1, ke, fabsf(p)) + 1e-30f;
                 ok = ok && isfinite(p) && isfinite(ke);
             }
             bad = bad || !ok;
@@ -437,17 +451,17 @@ __global__ void __launch_bounds__(384) k_flags_screen(const float *u, Geom g, fl
                 const float *A0 = A + s0 * plane;
                 const float *BB = Bq + s0 * plane;
                 float lo, hi, e2lo = 0.f, e2hi = 0.f;
-                interval(A0[c - 1], A0[c], A0[c + 1], which ? BB[c - 1] : 0.f, which ? BB[c] : 0.f,
-                         which ? BB[c + 1] : 0.f, lo, hi);
+                interval(A0[c - 1], A0[c], A0[c + 1], which ? BB[c - 1] : KR * A0[c - 1], which ? BB[c] : KR * A0[c],
+                         which ? BB[c + 1] : KR * A0[c + 1], lo, hi);
                 e2lo = fmaf(lo, lo, e2lo);
                 e2hi = fmaf(hi, hi, e2hi);
-                interval(A0[c - P], A0[c], A0[c + P], which ? BB[c - P] : 0.f, which ? BB[c] : 0.f,
-                         which ? BB[c + P] : 0.f, lo, hi);
+                interval(A0[c - P], A0[c], A0[c + P], which ? BB[c - P] : KR * A0[c - P], which ? BB[c] : KR * A0[c],
+                         which ? BB[c + P] : KR * A0[c + P], lo, hi);
                 e2lo = fmaf(lo, lo, e2lo);
                 e2hi = fmaf(hi, hi, e2hi);
                 if (D == 3) {
-                    interval(A[sm * plane + c], A0[c], A[sp * plane + c], which ? Bq[sm * plane + c] : 0.f,
-                             which ? BB[c] : 0.f, which ? Bq[sp * plane + c] : 0.f, lo, hi);
+                    interval(A[sm * plane + c], A0[c], A[sp * plane + c], which ? Bq[sm * plane + c] : KR * A[sm * plane + c],
+                             which ? BB[c] : KR * A0[c], which ? Bq[sp * plane + c] : KR * A[sp * plane + c], lo, hi);
                     e2lo = fmaf(lo, lo, e2lo);
                     e2hi = fmaf(hi, hi, e2hi);
                 }

@@ -291,22 +291,35 @@ def test_lohner_flags_bit_exact_fp32_uniform(N):
         np.testing.assert_array_equal(f.flag(0, c_ref, c_deref), om.lohner_flags(u64, c_ref, c_deref))
 
 
-@pytest.mark.parametrize("dim", [2, 3])
-def test_fp32_flags_with_thresholds_on_block_values(dim):
-    """The criterion of an FP32 state first runs an FP32 interval screen and
-    hands the blocks it cannot decide to the FP64 kernel.  With c_ref or
-    c_deref placed exactly on a block's largest value (from the oracle) and
-    one FP64 step either side -- where only the FP64 evaluation can tell the
-    flags apart -- every block's flag equals the oracle's; the same holds at
-    the usual thresholds.  Periodic uniform meshes, so both sides see the same
-    ghost values."""
-    if dim == 2:
-        sp = synth.MeshSpec(ndim=2, N=16, ng=2, ntrees=(8, 8, 1))
+@pytest.mark.parametrize("dim,precision", [(2, 32), (3, 32), (2, 64), (3, 64)])
+def test_flags_with_thresholds_on_block_values(dim, precision):
+    """The criterion first runs an FP32 interval screen and hands the blocks
+    it cannot decide to the FP64 kernel.  With c_ref or c_deref placed exactly
+    on a block's largest value (from the oracle) and one FP64 step either
+    side -- where only the FP64 evaluation can tell the flags apart -- every
+    block's flag equals the oracle's; the same holds at the usual thresholds.
+    FP32 states on periodic uniform meshes (both sides see the same ghost
+    values); FP64 states on 3-level meshes (the FP64 ghost fill is bit-exact),
+    a 3D one with a shocked over-pressure sphere."""
+    if precision == 32:
+        if dim == 2:
+            sp = synth.MeshSpec(ndim=2, N=16, ng=2, ntrees=(8, 8, 1))
+        else:
+            sp = synth.MeshSpec(ndim=3, N=8, ng=2, ntrees=(4, 4, 4))
+        om, f = make_pair(sp, 0, precision=32)
+        lev, g = om.blocks()
+        u = (synth.kelvin_helmholtz(sp, lev, g, seed=7) if dim == 2 else synth.fourier3d(sp, lev, g, seed=7)).astype(np.float32)
     else:
-        sp = synth.MeshSpec(ndim=3, N=8, ng=2, ntrees=(4, 4, 4))
-    om, f = make_pair(sp, 0, precision=32)
-    lev, g = om.blocks()
-    u = (synth.kelvin_helmholtz(sp, lev, g, seed=7) if dim == 2 else synth.fourier3d(sp, lev, g, seed=7)).astype(np.float32)
+        sp = synth.MeshSpec(**(SPEC_2D_AMR if dim == 2 else SPEC_3D_AMR))
+        om, f = make_pair(sp, 0, AMR2 if dim == 2 else AMR3)
+        lev, g = om.blocks()
+        if dim == 2:
+            u = synth.kelvin_helmholtz(sp, lev, g, seed=7)
+        else:
+            u = synth.over_pressure(sp, lev, g, (0.5, 0.52, 0.48), radius=0.2, p_in=100.0)
+            u1 = np.zeros_like(u)
+            for _ in range(2):
+                oracle.heun_step(om, u, u1)
     f.set_state(0, u)
     f.fill_ghosts(0)
     u64 = f.get_state(0).astype(np.float64)
