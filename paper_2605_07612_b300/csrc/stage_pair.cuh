@@ -10,10 +10,12 @@
 // cells (2ip, 2ip+1) of row tj.  The CTA marches k with a ring of
 // primitive variables in shared memory (4 planes: the z face state of the
 // plane above is carried in registers).  Per plane k:
-//   [copy of plane k's previous states | fluxes of plane k | commit of plane
-//    k+3] barrier [update of plane k] barrier
-// The previous states travel by cp.async into per-thread shared slots while
-// the fluxes are computed, so the update does not wait on global loads.  Face
+//   [copies of previous states | fluxes of plane k | commit of plane k+3]
+//   barrier [update of plane k]
+// (with two previous states a second barrier opens each plane: their single
+// y-face buffer must be read by every update before the next fluxes).  The
+// previous states travel by cp.async into per-thread shared slots while the
+// fluxes are computed, so the update does not wait on global loads.  Face
 // states (MUSCL with minmod) are formed in the flux phase from the ring: an
 // x-face pair reads three aligned pairs of a row, a y- or z-face pair four.
 // The T x-faces and T y-faces left over at the tile's upper edges are taken
@@ -291,7 +293,9 @@ struct PairShape {
 // or for the last pair of a row from the upper x-faces computed one plane
 // ahead; the lower y-face of a row is the thread's own flux.  y- and x-face
 // buffers alternate with the parity of k, so the next plane's flux phase can
-// overwrite nothing the update still reads.  FIX: the mesh has refinement
+// overwrite nothing the update still reads (with two previous states there is
+// one y-face buffer and a second barrier before each flux phase instead).
+// FIX: the mesh has refinement
 // faces (flux stores for the flux fix, cells excluded from the CFL maximum);
 // without them that code is compiled out.
 template <int N, int TT, int NPREV, int LIM, int FLX, bool FIX>
@@ -302,10 +306,10 @@ __device__ __forceinline__ void stage_pair_item(const StageArgs<float> &a, const
     constexpr int64_t NC = int64_t(S) * S * S;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float *ring = reinterpret_cast<float *>(smem_raw);         // [R][V][P*P]
-    float *fyb = ring + Sh::R * V * PL;                         // [2][V][T x T] upper y-faces
+    float *fyb = ring + Sh::R * V * PL;                         // [fy_bufs][V][T x T] upper y-faces
     constexpr int FYN = Sh::fy_bufs(NPREV);
     float *exb = fyb + FYN * FYB;                               // [2][V][T] upper x-faces
-    float2 *stg = reinterpret_cast<float2 *>(exb + 2 * EXB);    // [NPREV][V][NT] previous states
+    float2 *stg = reinterpret_cast<float2 *>(exb + 2 * EXB);    // [stg_slots][V][NT] previous states
 
     const int tid = threadIdx.x;
     const int b = item / Sh::TILES;
